@@ -1,0 +1,57 @@
+"""Seeded generators: determinism, shapes, the length laws and that symbols
+are drawn from the labelled model (CPU only)."""
+import numpy as np
+import pytest
+
+from paper_1310_3322_gb300 import synth
+
+
+@pytest.mark.parametrize("name", ["plain", "batched", "gradient"])
+def test_workload_shapes_and_determinism(name):
+    a = synth.make_workload(name)
+    b = synth.make_workload(name)
+    spec = synth.SPECS[name]
+    assert (a.K, a.N, a.M, a.S) == (spec["K"], spec["N"], spec["M"], spec["S"])
+    np.testing.assert_array_equal(a.symbols, b.symbols)
+    assert a.symbols.dtype == np.int32 and a.offsets.dtype == np.int64
+    assert a.lengths.dtype == np.int32 and a.labels.dtype == np.int32
+    assert a.total_obs == int(a.lengths.sum())
+    np.testing.assert_array_equal(a.offsets[1:], np.cumsum(a.lengths)[:-1])
+    assert a.symbols.min() >= 0 and a.symbols.max() < a.M
+    assert a.labels.min() >= 0 and a.labels.max() < a.K
+    for arr in (a.pi, a.A, a.B):
+        assert arr.dtype == np.float32
+        np.testing.assert_allclose(arr.sum(-1), 1.0, rtol=1e-5)
+
+
+def test_length_laws():
+    w = synth.make_workload("batched")
+    assert w.lengths.min() >= 30 and w.lengths.max() <= 300
+    assert abs(w.lengths.mean() - 165) < 5
+    T = synth.draw_lengths(synth.SPECS["training"], 200000, 1310005)
+    assert T.min() >= 50 and T.max() <= 1000
+    assert abs(T.mean() - 223.6) < 3      # mean of T^-1.5 on [50,1000]
+
+
+def test_sticky_transitions():
+    w = synth.make_workload("batched", n_seqs=4)
+    d = np.diagonal(w.A, axis1=1, axis2=2)
+    assert d.min() >= 0.6 - 1e-6 and d.max() <= 0.9 + 1e-6
+
+
+def test_first_symbol_distribution():
+    # P(o_1 = m) = sum_i pi_i b_i(m) for the generating model
+    w = synth.make_workload("plain", n_seqs=40000, lengths=("fixed", 1))
+    expect = (w.pi[0].astype(np.float64)[:, None] * w.B[0]).sum(0)
+    freq = np.bincount(w.symbols, minlength=w.M) / w.S
+    assert np.abs(freq - expect).max() < 0.01
+
+
+def test_resample_changes_only_selected():
+    w = synth.make_workload("batched", n_seqs=20, lengths=("uniform", 5, 9))
+    v = synth.resample(w, [3, 7], 0)
+    for s in range(w.S):
+        a = w.symbols[w.offsets[s]: w.offsets[s] + w.lengths[s]]
+        b = v.symbols[v.offsets[s]: v.offsets[s] + v.lengths[s]]
+        if s not in (3, 7):
+            np.testing.assert_array_equal(a, b)

@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Throughput of the HMM recognition hot path on GB300 (one JSON line).
+
+Workload: the batched-recognition configuration -- K=10 activity HMMs, N=16
+states, M=32 symbols, 4096 ragged sequences with T ~ U{30..300} -- synthetic
+and seeded (the paper's UCF teamwork recordings are not available).
+
+One step = one pass of the whole hot path over the batch:
+  softmax rows (logits -> pi, A, B), forward log-likelihood of every
+  (sequence, model) pair with the argmax over models, Viterbi scores of every
+  pair plus the best path of the decoded model, the forward-backward adjoint
+  of every sequence against its labelled model, the logit gradient, and one
+  Adam update of the logits.
+Throughput unit: observations x models scored per second (sum_s T_s * K per
+step). `value` comes from CUDA-graph replays of the step on device-resident
+inputs, with an L2 flush (a 256 MB write) between steps outside the timed
+events; `e2e` repeats the step through the public API with the inputs copied
+from pinned host memory and the results copied back inside the timed region.
+
+Multi-GPU: every rank runs its own shard (its own batch, seed + rank) with no
+collective on the data path ("weak" scaling); the barrier and the max over
+ranks use torch.distributed. `--impl reference` times the FP64 CPU oracle on
+the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batched"
+METRIC = "HMM obs·models/s (forward, Viterbi, fwd+adjoint)"
+UNIT = "obs*models/s"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+KERNELS_PER_STEP = 13  # setup x3, softmax, forward, v-scores, v-paths, adjoint, reduce x2, grad, adam x2
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of replays")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--n-seqs", type=int, default=None, help="smaller batch (profiling only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def units_of(w) -> int:
+    return int(w.lengths.astype(np.int64).sum()) * w.K
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (shared by the cpu_baseline key and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_step(w, idx, nthreads):
+    """The step's arithmetic on the FP64 CPU oracle for sequences idx."""
+    import oracle
+    P = oracle.params(w.pi, w.A, w.B)
+    sub = (w.symbols, w.offsets[idx], w.lengths[idx])
+    oracle.forward(P, *sub, nthreads=nthreads)
+    oracle.viterbi(P, *sub, nthreads=nthreads)
+    _, cpi, cA, cB, _ = oracle.forward_backward(P, *sub, w.labels[idx], nthreads=nthreads)
+    oracle.softmax_grad(P, cpi, cA, cB)
+
+
+def cpu_sample(w, n):
+    return np.random.default_rng(12345).choice(w.S, size=min(n, w.S), replace=False)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_1310_3322_gb300 import synth
+    w = synth.make_workload(WORKLOAD)
+    cores = os.cpu_count() or 1
+    idx = cpu_sample(w, 512)
+    units = int(w.lengths[idx].astype(np.int64).sum()) * w.K
+    for _ in range(args.warmup):
+        oracle_step(w, idx, cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(w, idx, cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = units / (ms / 1e3)
+    sample = (f"{idx.size} of {w.S} sequences ({units} obs*models) per step, "
+              "forward+Viterbi over all K models, labelled adjoint + logit gradient, FP64")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched-recognition K=10 N=16 M=32 S=4096 T~U{30..300}",
+                   "sample_sequences": int(idx.size), "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hmm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from a committed ncu capture, or None
+    when the kernel's source changed since that capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1310_3322_gb300", "csrc", rec["source"])
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if sha != rec.get("source_sha"):
+        return None
+    return rec["bytes_per_launch_full_workload"]
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1310_3322_gb300 import hmm, synth
+
+    rank, local, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = synth.make_workload(WORKLOAD, n_seqs=args.n_seqs, seed=synth.SEEDS[WORKLOAD] + rank)
+    K, N, M = w.K, w.N, w.M
+    units = units_of(w)
+    sumT = int(w.lengths.astype(np.int64).sum())
+
+    # ---- device-resident state --------------------------------------------
+    seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
+    labels = torch.from_numpy(w.labels).to(dev)
+    lab = seqs.labelled(labels)
+    sizes = [K * N, K * N * N, K * N * M]
+    logits = torch.from_numpy(np.concatenate([np.log(w.pi).ravel(), np.log(w.A).ravel(),
+                                              np.log(w.B).ravel()]).astype(np.float32)).to(dev)
+    grads = torch.zeros_like(logits)
+    adam_m, adam_v = torch.zeros_like(logits), torch.zeros_like(logits)
+    counter = torch.zeros(1, dtype=torch.int32, device=dev)
+    shapes = [(K, N), (K, N, N), (K, N, M)]
+
+    def views(flat):
+        out, o = [], 0
+        for n, sh in zip(sizes, shapes):
+            out.append(flat[o:o + n].view(*sh))
+            o += n
+        return out
+
+    lg, gr = views(logits), views(grads)
+    probs = [torch.empty(sh, device=dev) for sh in shapes]
+    ll = torch.empty((w.S, K), device=dev)
+    am = torch.empty(w.S, dtype=torch.int32, device=dev)
+    vs = torch.empty((w.S, K), device=dev)
+    vbest = torch.empty(w.S, dtype=torch.int32, device=dev)
+    vpath = torch.empty(max(w.total_obs, 1), dtype=torch.int32, device=dev)
+    fll = torch.empty(w.S, device=dev)
+    cnts = [torch.empty(sh, device=dev) for sh in shapes]
+    ws = [hmm.Workspace(dev) for _ in range(3)]
+    lr, gscale = 1e-3, -1.0 / float(sumT)
+
+    def step(sq=seqs, lb=lab):
+        hmm.hmm_softmax_rows(*lg, out=probs)
+        hmm.hmm_forward(*probs, sq, loglik=ll, argmax=am, workspace=ws[0])
+        hmm.hmm_viterbi(*probs, sq, score=vs, best_model=vbest, path=vpath, workspace=ws[1])
+        hmm.hmm_forward_backward(*probs, lb, loglik=fll, counts=cnts, workspace=ws[2])
+        hmm.hmm_softmax_grad(*probs, *cnts, out=gr)
+        hmm.hmm_adam_step(logits, grads, adam_m, adam_v, lr, grad_scale=gscale,
+                          step_counter=counter)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up, then capture -------------------------------------------
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    status = hmm.hmm_get_device_status(ws[0]) | hmm.hmm_get_device_status(ws[1]) | \
+        hmm.hmm_get_device_status(ws[2])
+    if status:
+        raise RuntimeError(f"device status {status:#x}")
+    graph = None
+    if not args.no_graph:
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+
+    # ---- timed region ------------------------------------------------------
+    clocks = Clocks(local)
+    cur = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)          # L2 flush, outside the timed events
+        evs[i][0].record(cur)
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        evs[i][1].record(cur)
+    barrier()
+    clk = clocks.stop()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    t_max = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = units * world / (ms_max / 1e3)
+
+    # ---- per-kernel breakdown (library CUDA events, eager steps) ----------
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        step()
+    torch.cuda.synchronize()
+    kt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    per_launch = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in kt.items()}
+    totals = {k: v[1] for k, v in kt.items()}
+    step_kernel_ms = sum(totals.values()) / max(args.steps, 1)
+    flops = {
+        "forward": (2 * N * N + 3 * N) * sumT * K,
+        "viterbi_scores": 2 * N * N * sumT * K,
+        "viterbi_paths": 2 * N * N * sumT,
+        "adjoint": (8 * N * N + 10 * N) * sumT,
+    }
+    dom = max(flops, key=lambda k: totals.get(k, 0.0))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s at max clock
+    achieved = flops[dom] / (per_launch[dom] / 1e3) / 1e12
+    roofline = {
+        "bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved / peak, "traffic": traffic_for(dom),
+        "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
+        "frac_at_measured_clock": (achieved / (peak * clk["sm_mhz"] / SM_MAX_MHZ))
+        if clk.get("sm_mhz") else None,
+        "launch_ms": per_launch[dom],
+    }
+    phases = {}
+    for name, n_units in (("forward", units), ("viterbi_scores", units), ("viterbi_paths", sumT),
+                          ("adjoint", sumT)):
+        if per_launch.get(name):
+            phases[name] = {"ms": per_launch[name],
+                            "obs_models_per_s": n_units / (per_launch[name] / 1e3),
+                            "tflops": flops[name] / (per_launch[name] / 1e3) / 1e12}
+    for name in ("setup", "count_reduce", "softmax_rows", "softmax_grad", "adam"):
+        phases[name] = {"ms": totals[name] / max(args.steps, 1)}
+
+    # ---- end to end through the public API ---------------------------------
+    e2e = None
+    if not args.skip_e2e:
+        h_sym = torch.from_numpy(w.symbols).pin_memory()
+        h_off = torch.from_numpy(w.offsets).pin_memory()
+        h_len = torch.from_numpy(w.lengths).pin_memory()
+        h_lab = torch.from_numpy(w.labels).pin_memory()
+        d_sym, d_off = torch.empty_like(seqs.symbols), torch.empty_like(seqs.offsets)
+        d_len, d_lab = torch.empty_like(seqs.lengths), torch.empty_like(labels)
+        sq2 = hmm.Sequences(d_sym, d_off, d_len, seqs.max_len)
+        lb2 = sq2.labelled(d_lab)
+        o_am = torch.empty(w.S, dtype=torch.int32).pin_memory()
+        o_path = torch.empty(max(w.total_obs, 1), dtype=torch.int32).pin_memory()
+        o_nll = torch.empty(1, dtype=torch.float32).pin_memory()
+        bi = sum(t.numel() * t.element_size() for t in (h_sym, h_off, h_len, h_lab))
+        bo = sum(t.numel() * t.element_size() for t in (o_am, o_path, o_nll))
+        times = []
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d_sym.copy_(h_sym, non_blocking=True)
+            d_off.copy_(h_off, non_blocking=True)
+            d_len.copy_(h_len, non_blocking=True)
+            d_lab.copy_(h_lab, non_blocking=True)
+            step(sq2, lb2)
+            o_am.copy_(am, non_blocking=True)
+            o_path.copy_(vpath, non_blocking=True)
+            o_nll.copy_(fll.sum().neg().view(1), non_blocking=True)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        barrier()
+        e_ms = float(np.mean(times)) * 1e3
+        t_e = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        e2e = {"value": units * world / (float(t_e.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+               "ms_per_step": float(t_e.item())}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) --------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cores = os.cpu_count() or 1
+        idx = np.arange(w.S)
+        t0 = time.perf_counter()
+        oracle_step(w, idx, cores)
+        dt = time.perf_counter() - t0
+        cpu = {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"the whole batch ({w.S} sequences, {units} obs*models), one step: "
+                         "FP64 log-space forward+Viterbi over all K models, labelled "
+                         "forward-backward counts and logit gradient",
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched-recognition K={K} N={N} M={M} S={w.S} "
+                                   "T~U{30..300} (all K models per sequence + labelled adjoint)",
+                       "units_per_step": units, "sum_T": sumT,
+                       "l2": "flushed between steps (256 MB write outside the timed events)",
+                       "timing": "CUDA-graph replay of the whole step" if graph is not None
+                       else "eager step", "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "clocks": clk,
+            "phases": phases,
+            "kernel_ms_per_step": step_kernel_ms,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * hmm.h -- C-ABI of the GB300 (sm_103a) discrete-HMM recognition hot path.
+ *
+ * The paper (arXiv 1310.3322, Sec. 2.7) builds its activity-recognition stage
+ * on three GPU kernels -- Forward, Viterbi and Baum-Welch -- over discrete
+ * HMMs, one HMM per activity, all run in parallel with the recognised activity
+ * the best-scoring model (Sec. 3, item 3; Sec. 4.1 lists the stage's
+ * parameters: number of hidden states, symbols, actions). The paper prints no
+ * equations; the operations below follow the textbook recursions (Rabiner,
+ * Proc. IEEE 77(2), 1989).
+ *
+ * Conventions shared by every entry point
+ *   - Models: K discrete HMMs with N states and M symbols.
+ *       pi [K][N]     initial-state probabilities
+ *       A  [K][N][N]  a_ij = P(q_{t+1} = j | q_t = i), row-major, row = from-state
+ *       B  [K][N][M]  b_j(m) = P(o_t = m | q_t = j), row-major
+ *     FP32, non-negative and finite (rows are not required to sum to 1).
+ *   - Sequences (hmm_seqs_t): sequence s is symbols[offsets[s] ..
+ *     offsets[s] + lengths[s]), symbols 0-based in [0, M). If model_of_seq is
+ *     NULL every sequence is scored against all K models and per-pair outputs
+ *     are [S][K] (row-major, s-major); otherwise sequence s is scored against
+ *     model_of_seq[s] only and per-pair outputs are [S].
+ *   - Unless stated otherwise, every pointer argument is a DEVICE pointer,
+ *     owned by the caller, at least 4-byte aligned (8 for int64), and must stay
+ *     valid until the work on `stream` completes.
+ *   - The library never allocates device memory: each call that needs scratch
+ *     space takes a caller-owned device workspace of at least
+ *     hmm_workspace_size() bytes (256-byte aligned). Calls that share a
+ *     workspace must be ordered on one stream.
+ *   - Every call is asynchronous on `stream` (NULL = legacy default stream),
+ *     launches only kernels and memsets (no host synchronisation), and can be
+ *     captured into a CUDA graph.
+ *   - Return value: HMM_OK, or a negative HMM_ERR_* code found by host-side
+ *     checks before anything is launched (nothing is enqueued then), or
+ *     HMM_ERR_CUDA if a launch failed. hmm_last_error() describes the last
+ *     failure of the calling thread.
+ *   - Problems found on the device (a symbol out of range, a negative or
+ *     non-finite parameter, an inconsistent offset/length/model index) never
+ *     trap: the device status word in the workspace gets a HMM_STATUS_* bit,
+ *     the affected outputs are NaN (paths -1), and hmm_get_device_status()
+ *     reads the word.
+ *   - Log-likelihoods and scores are natural logarithms (nats). An impossible
+ *     sequence gives -inf (path filled with 0). T = 0 gives 0 (empty path).
+ *     Ties in a Viterbi predecessor, the final state or a model argmax take the
+ *     smallest index.
+ */
+#ifndef HMMGB_HMM_H
+#define HMMGB_HMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* hmm_stream_t;
+
+/* Return codes. */
+#define HMM_OK 0
+#define HMM_ERR_ARG (-1)          /* bad pointer, size, alignment or dimension */
+#define HMM_ERR_CUDA (-2)         /* a CUDA runtime call or launch failed */
+#define HMM_ERR_WORKSPACE (-3)    /* workspace NULL, misaligned or too small */
+#define HMM_ERR_UNSUPPORTED (-4)  /* valid request this build does not implement */
+#define HMM_ERR_DEVICE (-5)       /* hmm_get_device_status: a status bit is set */
+
+/* Device status bits (hmm_get_device_status). */
+#define HMM_STATUS_SYMBOL 0x1     /* a symbol outside [0, M) */
+#define HMM_STATUS_PARAM 0x2      /* a negative, NaN or infinite parameter */
+#define HMM_STATUS_SEQ 0x4        /* offset/length out of range, bad model index,
+                                     or sum of lengths above total_obs (Viterbi) */
+
+typedef enum {
+  HMM_FP32 = 0,      /* FP32 SIMT recursion (exact power-of-two rescaling) */
+  HMM_BF16_MMA = 1,  /* tensor-core alpha*A, BF16 operands, FP32 accumulation */
+  HMM_TF32_MMA = 2,  /* tensor-core alpha*A, TF32 operands, FP32 accumulation */
+  HMM_AUTO = 3       /* the library's choice for the given N */
+} hmm_precision_t;
+
+typedef enum {
+  HMM_OP_FORWARD = 0,
+  HMM_OP_VITERBI = 1,
+  HMM_OP_FORWARD_BACKWARD = 2
+} hmm_op_t;
+
+typedef struct {
+  int32_t K; /* number of models (activities), >= 1 */
+  int32_t N; /* states per model, 1 .. hmm_max_states(op) */
+  int32_t M; /* symbols, >= 1 */
+} hmm_dims_t;
+
+typedef struct {
+  const int32_t* symbols;      /* device [total_obs] */
+  const int64_t* offsets;      /* device [S], start of each sequence in symbols */
+  const int32_t* lengths;      /* device [S], T_s >= 0 */
+  const int32_t* model_of_seq; /* device [S] in [0, K), or NULL = all models */
+  int32_t S;                   /* host: number of sequences, >= 0 */
+  int32_t max_len;             /* host: upper bound on every lengths[s]; sizes
+                                  the adjoint's checkpoint buffers */
+  int64_t total_obs;           /* host: number of elements of symbols */
+} hmm_seqs_t;
+
+/* Workspace bytes that `op` needs for these dimensions and sequences (host
+ * only; reads only the host fields of *seqs). */
+int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, size_t* bytes);
+
+/* Largest N that `op` accepts at `precision` in this build. */
+int hmm_max_states(hmm_op_t op, hmm_precision_t precision);
+
+/* Forward algorithm (Sec. 2.7 "Forward"; Rabiner eqs. 19-21 with per-step
+ * rescaling, Sec. V-A): loglik = log P(O_s | lambda_k) for every scored pair.
+ *   loglik  [S][K] (model_of_seq NULL) or [S]
+ *   argmax  [S] or NULL: recognised activity = argmax_k loglik[s][k] (Sec. 3
+ *           item 3), smallest k on ties, -1 if any of the row is NaN. Only
+ *           written when model_of_seq is NULL.
+ * The alpha recursion runs in FP32 with exact power-of-two rescaling every
+ * step; the exponent sum is an integer and the final log is taken in FP64. */
+int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                const hmm_seqs_t* seqs, hmm_precision_t precision, float* loglik,
+                int32_t* argmax, void* workspace, size_t workspace_bytes, hmm_stream_t stream);
+
+/* Viterbi algorithm (Sec. 2.7 "Viterbi"; Rabiner eqs. 32-35):
+ *   score       [S][K] or [S]: max_Q log P(O_s, Q | lambda_k)
+ *   best_model  [S] or NULL: the decoded model, argmax_k score[s][k] (smallest
+ *               k on ties, -1 if a score is NaN), or model_of_seq[s]
+ *   path        [total_obs] or NULL: the best state path of the decoded model,
+ *               path[offsets[s] + t] = q_t (sequences must not overlap)
+ * Requires sum_s lengths[s] <= total_obs (backpointer storage). */
+int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                const hmm_seqs_t* seqs, float* score, int32_t* best_model, int32_t* path,
+                void* workspace, size_t workspace_bytes, hmm_stream_t stream);
+
+/* Forward-backward adjoint (Sec. 2.7 "Baum-Welch", its E-step; Rabiner
+ * eqs. 24-25, 37-38): weighted expected counts
+ *   cnt_pi[k][i]   = sum_s w_s gamma_1(i)
+ *   cnt_A[k][i][j] = sum_s w_s sum_{t<T} xi_t(i,j)
+ *   cnt_B[k][j][m] = sum_s w_s sum_{t: o_t = m} gamma_t(j)
+ * over the pairs scored against model k, which are exactly the gradient of
+ * sum_s w_s log P with respect to log pi, log A, log B. Alpha is checkpointed
+ * every ceil(sqrt(max_len)) steps and recomputed segment by segment.
+ *   weight  [S] or [S][K] (the layout of loglik), NULL = all 1
+ *   loglik  [S] or [S][K]
+ *   counts  overwritten; summed in a fixed order (bitwise reproducible).
+ * Impossible or invalid pairs contribute no counts. */
+int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                         const hmm_seqs_t* seqs, const float* weight,
+                         hmm_precision_t precision, float* loglik, float* cnt_pi,
+                         float* cnt_A, float* cnt_B, void* workspace, size_t workspace_bytes,
+                         hmm_stream_t stream);
+
+/* Row-wise softmax of logits into probabilities (the parameterisation used for
+ * learning): pi[k] = softmax(logit_pi[k]), A[k][i] = softmax(logit_A[k][i]),
+ * B[k][j] = softmax(logit_B[k][j]). Outputs may not alias inputs. */
+int hmm_softmax_rows(hmm_dims_t dims, const float* logit_pi, const float* logit_A,
+                     const float* logit_B, float* pi, float* A, float* B, hmm_stream_t stream);
+
+/* Gradient of sum_s w_s log P with respect to the row logits, from the
+ * probabilities and the counts of hmm_forward_backward:
+ *   g = C - p * rowsum(C)   for every row of pi, A and B.
+ * Outputs may alias the counts. */
+int hmm_softmax_grad(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                     const float* cnt_pi, const float* cnt_A, const float* cnt_B, float* g_pi,
+                     float* g_A, float* g_B, hmm_stream_t stream);
+
+/* One Adam step (Kingma & Ba 2015) on n parameters, in place:
+ *   t = *step_counter + 1;  g = grad_scale * grad;
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   param -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps);
+ *   *step_counter = t.
+ * step_counter is a DEVICE int32 (steps taken so far, 0 before the first),
+ * so a captured CUDA graph advances the bias correction on every replay.
+ * Use grad_scale < 0 to ascend a log-likelihood gradient. */
+int hmm_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, float grad_scale, int32_t* step_counter,
+                  hmm_stream_t stream);
+
+/* Copies the device status word of the last call that used `workspace` into
+ * *status (HOST pointer), synchronising `stream`. Returns HMM_OK when the
+ * word is 0, HMM_ERR_DEVICE when a bit is set. */
+int hmm_get_device_status(const void* workspace, hmm_stream_t stream, int32_t* status);
+
+/* Autotuner hook: lanes of a warp that cooperate on one (sequence, model)
+ * pair for `op` at padded state count n_pad (4, 8, 16, 32, 64). The value
+ * must be one this build instantiates (see hmm_tuning_candidates). 0 restores
+ * the default. Process-wide; not thread-safe against concurrent launches. */
+int hmm_set_tuning(hmm_op_t op, int32_t n_pad, int32_t lanes_per_pair);
+int hmm_get_tuning(hmm_op_t op, int32_t n_pad, int32_t* lanes_per_pair);
+/* Writes up to cap candidate lane counts for (op, n_pad) into out (HOST
+ * pointer); returns how many there are, or a negative error code. */
+int hmm_tuning_candidates(hmm_op_t op, int32_t n_pad, int32_t* out, int32_t cap);
+
+/* Kernel timing (host-side tracing). While enabled, every kernel launch of
+ * the library is bracketed by two CUDA events recorded on the launch stream;
+ * hmm_timing_read() synchronises those events and reports, per kernel kind,
+ * the number of launches and their summed duration since the last reset.
+ * Kinds: 0 setup, 1 forward, 2 viterbi-scores, 3 viterbi-paths, 4 adjoint,
+ * 5 count-reduce, 6 softmax-rows, 7 softmax-grad, 8 adam. Not for use inside
+ * CUDA-graph capture; not thread-safe against concurrent launches. */
+#define HMM_TIMING_KINDS 9
+int hmm_timing_enable(int on);
+int hmm_timing_reset(void);
+int hmm_timing_read(int32_t kind, int64_t* launches, double* total_ms);
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char* hmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMMGB_HMM_H */

@@ -1,0 +1,640 @@
+// api.cu -- the C-ABI of include/hmm.h: host-side argument checks, workspace
+// layout, the autotuning table and the launch sequence of every entry point.
+// Nothing here allocates device memory or synchronises (except
+// hmm_get_device_status, whose job is to read the device status word).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "hmm_internal.cuh"
+
+namespace hmmgb {
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(HMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// ---------------------------------------------------------------------------
+// padded state counts and the tuning table
+// ---------------------------------------------------------------------------
+static const int kNPs[] = {4, 8, 16, 32, 64};
+static int np_index(int NP) {
+  for (int i = 0; i < 5; ++i)
+    if (kNPs[i] == NP) return i;
+  return -1;
+}
+static int pad_states(int N) {
+  for (int i = 0; i < 5; ++i)
+    if (N <= kNPs[i]) return kNPs[i];
+  return -1;
+}
+
+// candidate lanes-per-pair, default first; 0 terminates
+static const int kCand[3][5][5] = {
+    /* forward */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
+    /* viterbi */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
+    /* fb      */ {{4, 2, 0}, {8, 4, 0}, {8, 16, 0}, {32, 0}, {0}},
+};
+static const int kPathLanes[5] = {4, 8, 8, 16, 32};
+static int g_tuning[3][5] = {{0}};
+static std::mutex g_tuning_mu;
+
+int candidates(int op, int NP, int* out, int cap) {
+  const int ni = np_index(NP);
+  if (op < 0 || op > 2 || ni < 0) return -1;
+  int n = 0;
+  for (int i = 0; i < 5 && kCand[op][ni][i]; ++i) {
+    if (n < cap && out) out[n] = kCand[op][ni][i];
+    ++n;
+  }
+  return n;
+}
+
+static int lanes_for(int op, int NP) {
+  const int ni = np_index(NP);
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  const int v = g_tuning[op][ni];
+  return v ? v : kCand[op][ni][0];
+}
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int first_chunks(int S) {
+  int n = (S + kReduceChunk - 1) / kReduceChunk;
+  if (n > 64) n = 64;
+  return n < 1 ? 1 : n;
+}
+
+static int ckpt_stride(int max_len) {
+  int C = (int)ceil(sqrt((double)(max_len > 0 ? max_len : 1)));
+  return C < 1 ? 1 : C;
+}
+
+static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op) {
+  WsLayout L;
+  memset(&L, 0, sizeof(L));
+  const int NP = pad_states(d.N);
+  L.NP = NP;
+  const size_t S = (size_t)(q.S > 0 ? q.S : 0);
+  size_t off = sizeof(WsHeader);
+  L.order = off; off = align256(off + S * 4);
+  L.seqlen = off; off = align256(off + S * 4);
+  L.done = off; off = align256(off + S * 4);
+  if (op == HMM_OP_VITERBI) {
+    L.bpoff = off; off = align256(off + S * 8);
+    L.best = off; off = align256(off + S * 4);
+  }
+  L.pip = off; off = align256(off + (size_t)d.K * NP * 4);
+  L.Ap = off; off = align256(off + (size_t)d.K * NP * NP * 4);
+  L.Btp = off; off = align256(off + (size_t)d.K * d.M * NP * 4);
+  if (op == HMM_OP_VITERBI) {
+    L.bp_cap = (q.total_obs > 0 ? q.total_obs : 0) * (int64_t)NP;
+    L.bp = off; off = align256(off + (size_t)L.bp_cap);
+  }
+  if (op == HMM_OP_FORWARD_BACKWARD) {
+    L.slot_floats = (int64_t)NP + (int64_t)NP * NP + (int64_t)NP * d.M;
+    L.slots = q.model_of_seq ? (int64_t)S : (int64_t)S * d.K;
+    L.nchunks = first_chunks((int)S);
+    L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
+    L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
+  }
+  L.total = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+static bool al(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static int check_dims(const hmm_dims_t& d, int max_n) {
+  if (d.K < 1 || d.N < 1 || d.M < 1)
+    return fail(HMM_ERR_ARG, "dims must be positive (K=%d N=%d M=%d)", d.K, d.N, d.M);
+  if (d.N > max_n)
+    return fail(HMM_ERR_UNSUPPORTED, "N=%d above the largest supported state count %d", d.N, max_n);
+  if (d.M > (1 << 24)) return fail(HMM_ERR_ARG, "M=%d too large", d.M);
+  if ((int64_t)d.K * d.M * 64 > ((int64_t)1 << 31))
+    return fail(HMM_ERR_ARG, "K*M too large (K=%d M=%d)", d.K, d.M);
+  return HMM_OK;
+}
+
+static int check_seqs(const hmm_seqs_t* q, const hmm_dims_t& d) {
+  if (!q) return fail(HMM_ERR_ARG, "seqs is NULL");
+  if (q->S < 0 || q->max_len < 0 || q->total_obs < 0)
+    return fail(HMM_ERR_ARG, "negative S, max_len or total_obs");
+  if ((int64_t)q->S * d.K > ((int64_t)1 << 30))
+    return fail(HMM_ERR_ARG, "S*K too large (S=%d K=%d)", q->S, d.K);
+  if (q->S > 0) {
+    if (!q->offsets || !q->lengths) return fail(HMM_ERR_ARG, "offsets/lengths NULL");
+    if (!al(q->offsets, 8) || !al(q->lengths, 4) || (q->model_of_seq && !al(q->model_of_seq, 4)))
+      return fail(HMM_ERR_ARG, "misaligned offsets/lengths/model_of_seq");
+    if (q->total_obs > 0 && (!q->symbols || !al(q->symbols, 4)))
+      return fail(HMM_ERR_ARG, "symbols NULL or misaligned");
+  }
+  return HMM_OK;
+}
+
+static int check_params(const float* pi, const float* A, const float* B) {
+  if (!pi || !A || !B) return fail(HMM_ERR_ARG, "pi/A/B NULL");
+  if (!al(pi, 4) || !al(A, 4) || !al(B, 4)) return fail(HMM_ERR_ARG, "pi/A/B misaligned");
+  return HMM_OK;
+}
+
+static int check_ws(void* ws, size_t bytes, const WsLayout& L) {
+  if (!ws) return fail(HMM_ERR_WORKSPACE, "workspace is NULL");
+  if (!al(ws, 256)) return fail(HMM_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  if (bytes < L.total)
+    return fail(HMM_ERR_WORKSPACE, "workspace %zu bytes, need %zu", bytes, L.total);
+  return HMM_OK;
+}
+
+template <typename T>
+static T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(reinterpret_cast<char*>(ws) + off);
+}
+
+static SetupArgs setup_args(const hmm_dims_t& d, const hmm_seqs_t& q, const WsLayout& L,
+                            void* ws, const float* pi, const float* A, const float* B,
+                            int log_mode) {
+  SetupArgs s;
+  memset(&s, 0, sizeof(s));
+  s.K = d.K; s.N = d.N; s.M = d.M; s.NP = L.NP; s.S = q.S;
+  s.total_obs = q.total_obs;
+  s.max_len = q.max_len;
+  s.log_mode = log_mode;
+  s.pi = pi; s.A = A; s.B = B;
+  s.lengths = q.lengths; s.offsets = q.offsets; s.model_of_seq = q.model_of_seq;
+  s.pip = at<float>(ws, L.pip); s.Ap = at<float>(ws, L.Ap); s.Btp = at<float>(ws, L.Btp);
+  s.seqlen = at<int32_t>(ws, L.seqlen);
+  s.order = at<int32_t>(ws, L.order);
+  s.done = at<int32_t>(ws, L.done);
+  s.status = &at<WsHeader>(ws, 0)->status;
+  return s;
+}
+
+static SeqArgs seq_args(const hmm_dims_t& d, const hmm_seqs_t& q, const WsLayout& L, void* ws) {
+  SeqArgs a;
+  a.symbols = q.symbols;
+  a.offsets = q.offsets;
+  a.model_of_seq = q.model_of_seq;
+  a.seqlen = at<int32_t>(ws, L.seqlen);
+  a.order = at<int32_t>(ws, L.order);
+  a.S = q.S; a.K = d.K; a.M = d.M;
+  return a;
+}
+
+static ModelArgs model_args(const WsLayout& L, void* ws) {
+  ModelArgs m;
+  m.pip = at<float>(ws, L.pip);
+  m.Ap = at<float>(ws, L.Ap);
+  m.Btp = at<float>(ws, L.Btp);
+  return m;
+}
+
+static int max_states(int op, int precision) {
+  if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
+  return op == HMM_OP_FORWARD_BACKWARD ? 32 : 64;
+}
+
+static int check_precision(int precision, int op) {
+  if (precision == HMM_FP32 || precision == HMM_AUTO) return HMM_OK;
+  if (precision == HMM_BF16_MMA || precision == HMM_TF32_MMA)
+    return fail(HMM_ERR_UNSUPPORTED, "tensor-core precision %d not available for op %d in this build",
+                precision, op);
+  return fail(HMM_ERR_ARG, "unknown precision %d", precision);
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing (host-side tracing with CUDA events)
+// ---------------------------------------------------------------------------
+enum { T_SETUP = 0, T_FORWARD, T_VSCORES, T_VPATHS, T_FB, T_REDUCE, T_SOFTMAX, T_SGRAD, T_ADAM };
+
+struct EventPair {
+  cudaEvent_t a, b;
+};
+
+static struct {
+  bool on = false;
+  std::vector<EventPair> rec[HMM_TIMING_KINDS];
+  std::vector<EventPair> pool;
+  std::mutex mu;
+} g_timing;
+
+// Records the start event of a timed launch (no-op while timing is off).
+struct Timed {
+  int kind;
+  cudaStream_t st;
+  EventPair ev{nullptr, nullptr};
+  Timed(int k, cudaStream_t s) : kind(k), st(s) {
+    if (!g_timing.on) return;
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    if (!g_timing.pool.empty()) {
+      ev = g_timing.pool.back();
+      g_timing.pool.pop_back();
+    } else if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+      ev = EventPair{nullptr, nullptr};
+      return;
+    }
+    cudaEventRecord(ev.a, st);
+  }
+  void stop() {
+    if (!ev.a) return;
+    cudaEventRecord(ev.b, st);
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    g_timing.rec[kind].push_back(ev);
+    ev = EventPair{nullptr, nullptr};
+  }
+};
+
+}  // namespace hmmgb
+
+using namespace hmmgb;
+
+extern "C" {
+
+const char* hmm_last_error(void) { return g_err; }
+
+int hmm_max_states(hmm_op_t op, hmm_precision_t precision) {
+  if (op < HMM_OP_FORWARD || op > HMM_OP_FORWARD_BACKWARD) return fail(HMM_ERR_ARG, "bad op");
+  return max_states(op, precision);
+}
+
+int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, size_t* bytes) {
+  g_err[0] = 0;
+  if (!bytes) return fail(HMM_ERR_ARG, "bytes is NULL");
+  if (op < HMM_OP_FORWARD || op > HMM_OP_FORWARD_BACKWARD) return fail(HMM_ERR_ARG, "bad op %d", op);
+  int rc = check_dims(dims, max_states(op, HMM_FP32));
+  if (rc) return rc;
+  if (!seqs) return fail(HMM_ERR_ARG, "seqs is NULL");
+  if (seqs->S < 0 || seqs->total_obs < 0) return fail(HMM_ERR_ARG, "negative S or total_obs");
+  *bytes = make_layout(dims, *seqs, op).total;
+  return HMM_OK;
+}
+
+int hmm_set_tuning(hmm_op_t op, int32_t n_pad, int32_t lanes) {
+  g_err[0] = 0;
+  const int ni = np_index(n_pad);
+  if (op < 0 || op > 2 || ni < 0) return fail(HMM_ERR_ARG, "bad op %d or n_pad %d", op, n_pad);
+  if (lanes != 0) {
+    bool ok = false;
+    for (int i = 0; i < 5 && kCand[op][ni][i]; ++i) ok |= kCand[op][ni][i] == lanes;
+    if (!ok) return fail(HMM_ERR_ARG, "lanes %d not instantiated for op %d n_pad %d", lanes, op, n_pad);
+  }
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  g_tuning[op][ni] = lanes;
+  return HMM_OK;
+}
+
+int hmm_get_tuning(hmm_op_t op, int32_t n_pad, int32_t* lanes) {
+  g_err[0] = 0;
+  const int ni = np_index(n_pad);
+  if (op < 0 || op > 2 || ni < 0 || !lanes) return fail(HMM_ERR_ARG, "bad op, n_pad or pointer");
+  if (!kCand[op][ni][0]) return fail(HMM_ERR_UNSUPPORTED, "no kernel for op %d n_pad %d", op, n_pad);
+  *lanes = lanes_for(op, n_pad);
+  return HMM_OK;
+}
+
+int hmm_tuning_candidates(hmm_op_t op, int32_t n_pad, int32_t* out, int32_t cap) {
+  g_err[0] = 0;
+  const int n = candidates(op, n_pad, out, cap);
+  if (n < 0) return fail(HMM_ERR_ARG, "bad op %d or n_pad %d", op, n_pad);
+  return n;
+}
+
+int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                const hmm_seqs_t* seqs, hmm_precision_t precision, float* loglik,
+                int32_t* argmax, void* ws, size_t ws_bytes, hmm_stream_t stream) {
+  g_err[0] = 0;
+  int rc = check_precision(precision, HMM_OP_FORWARD);
+  if (rc) return rc;
+  if ((rc = check_dims(dims, max_states(HMM_OP_FORWARD, precision)))) return rc;
+  if ((rc = check_seqs(seqs, dims))) return rc;
+  if ((rc = check_params(pi, A, B))) return rc;
+  if (seqs->S > 0 && (!loglik || !al(loglik, 4))) return fail(HMM_ERR_ARG, "loglik NULL or misaligned");
+  if (argmax && !al(argmax, 4)) return fail(HMM_ERR_ARG, "argmax misaligned");
+  const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD);
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  if (seqs->S == 0) return HMM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool all = seqs->model_of_seq == nullptr;
+  const int G = lanes_for(HMM_OP_FORWARD, L.NP);
+  const int PP = 32 / G;
+  const int ngroups = (seqs->S + PP - 1) / PP;
+
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  s.ndone = (all && argmax) ? ngroups : 0;
+  {
+    Timed tm(T_SETUP, st);
+    e = launch_setup(s, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+
+  FwdLaunch f;
+  f.seq = seq_args(dims, *seqs, L, ws);
+  f.mod = model_args(L, ws);
+  f.loglik = loglik;
+  f.argmax = all ? argmax : nullptr;
+  f.done = at<int32_t>(ws, L.done);
+  f.queue = &at<WsHeader>(ws, 0)->queue[0];
+  f.status = &at<WsHeader>(ws, 0)->status;
+  f.n_items = all ? ngroups * dims.K : ngroups;
+  {
+    Timed tm(T_FORWARD, st);
+    e = launch_forward(L.NP, G, f, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return HMM_OK;
+}
+
+int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                const hmm_seqs_t* seqs, float* score, int32_t* best_model, int32_t* path,
+                void* ws, size_t ws_bytes, hmm_stream_t stream) {
+  g_err[0] = 0;
+  int rc;
+  if ((rc = check_dims(dims, max_states(HMM_OP_VITERBI, HMM_FP32)))) return rc;
+  if ((rc = check_seqs(seqs, dims))) return rc;
+  if ((rc = check_params(pi, A, B))) return rc;
+  if (seqs->S > 0 && (!score || !al(score, 4))) return fail(HMM_ERR_ARG, "score NULL or misaligned");
+  if ((best_model && !al(best_model, 4)) || (path && !al(path, 4)))
+    return fail(HMM_ERR_ARG, "best_model/path misaligned");
+  if (path && seqs->total_obs > 0 && !seqs->symbols) return fail(HMM_ERR_ARG, "symbols NULL");
+  const WsLayout L = make_layout(dims, *seqs, HMM_OP_VITERBI);
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  if (seqs->S == 0) return HMM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool all = seqs->model_of_seq == nullptr;
+  const int G = lanes_for(HMM_OP_VITERBI, L.NP);
+  const int PP = 32 / G;
+  const int ngroups = (seqs->S + PP - 1) / PP;
+  const int Gp = kPathLanes[np_index(L.NP)];
+  const int PPp = 32 / Gp;
+  int32_t* best = best_model ? best_model : at<int32_t>(ws, L.best);
+  const bool need_best = all && (best_model || path);
+
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 1);
+  s.ndone = need_best ? ngroups : 0;
+  s.want_bpoff = path ? 1 : 0;
+  s.bpoff = at<int64_t>(ws, L.bpoff);
+  s.bp_cap_rows = seqs->total_obs;
+  {
+    Timed tm(T_SETUP, st);
+    e = launch_setup(s, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+
+  VitLaunch v;
+  v.seq = seq_args(dims, *seqs, L, ws);
+  v.mod = model_args(L, ws);
+  v.score = score;
+  v.path = path;
+  v.done = at<int32_t>(ws, L.done);
+  v.queue = &at<WsHeader>(ws, 0)->queue[0];
+  v.status = &at<WsHeader>(ws, 0)->status;
+  v.bpoff = at<int64_t>(ws, L.bpoff);
+  v.bp = at<uint8_t>(ws, L.bp);
+  v.n_items_score = all ? ngroups * dims.K : ngroups;
+  v.n_items_path = (seqs->S + PPp - 1) / PPp;
+  auto scores = [&]() {
+    Timed tm(T_VSCORES, st);
+    cudaError_t r = launch_viterbi_scores(L.NP, G, v, st);
+    tm.stop();
+    return r;
+  };
+  auto paths = [&]() {
+    Timed tm(T_VPATHS, st);
+    cudaError_t r = launch_viterbi_paths(L.NP, Gp, v, st);
+    tm.stop();
+    return r;
+  };
+  if (all) {
+    v.best = need_best ? best : nullptr;
+    if ((e = scores()) != cudaSuccess) return cuda_fail(e, "viterbi scores");
+    if (path) {
+      v.best = best;
+      if ((e = paths()) != cudaSuccess) return cuda_fail(e, "viterbi paths");
+    }
+  } else {
+    v.best = best_model;
+    if (path) {
+      if ((e = paths()) != cudaSuccess) return cuda_fail(e, "viterbi paths");
+    } else {
+      if ((e = scores()) != cudaSuccess) return cuda_fail(e, "viterbi scores");
+    }
+  }
+  return HMM_OK;
+}
+
+int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                         const hmm_seqs_t* seqs, const float* weight, hmm_precision_t precision,
+                         float* loglik, float* cnt_pi, float* cnt_A, float* cnt_B, void* ws,
+                         size_t ws_bytes, hmm_stream_t stream) {
+  g_err[0] = 0;
+  int rc = check_precision(precision, HMM_OP_FORWARD_BACKWARD);
+  if (rc) return rc;
+  if ((rc = check_dims(dims, max_states(HMM_OP_FORWARD_BACKWARD, precision)))) return rc;
+  if ((rc = check_seqs(seqs, dims))) return rc;
+  if ((rc = check_params(pi, A, B))) return rc;
+  if (!cnt_pi || !cnt_A || !cnt_B || !al(cnt_pi, 4) || !al(cnt_A, 4) || !al(cnt_B, 4))
+    return fail(HMM_ERR_ARG, "count outputs NULL or misaligned");
+  if (seqs->S > 0 && (!loglik || !al(loglik, 4))) return fail(HMM_ERR_ARG, "loglik NULL or misaligned");
+  if (weight && !al(weight, 4)) return fail(HMM_ERR_ARG, "weight misaligned");
+  const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD);
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  const int G = lanes_for(HMM_OP_FORWARD_BACKWARD, L.NP);
+  const int C = ckpt_stride(seqs->max_len);
+  const int NC = (seqs->max_len > 0 ? (seqs->max_len - 1) / C : 0) + 1;
+  const size_t smem = fb_smem_bytes(L.NP, G, C, NC, dims.M);
+  if (smem > 227 * 1024)
+    return fail(HMM_ERR_UNSUPPORTED,
+                "adjoint shared memory %zu bytes above 227 KB (N=%d M=%d max_len=%d)", smem,
+                dims.N, dims.M, seqs->max_len);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (seqs->S == 0) {
+    const size_t n = (size_t)dims.K * dims.N;
+    if ((e = cudaMemsetAsync(cnt_pi, 0, n * 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(cnt_A, 0, n * dims.N * 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(cnt_B, 0, n * dims.M * 4, st)) != cudaSuccess)
+      return cuda_fail(e, "memset");
+    return HMM_OK;
+  }
+  const bool labelled = seqs->model_of_seq != nullptr;
+  const int PP = 32 / G;
+  const int ngroups = (seqs->S + PP - 1) / PP;
+
+  if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  {
+    Timed tm(T_SETUP, st);
+    e = launch_setup(s, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+
+  FbLaunch f;
+  f.seq = seq_args(dims, *seqs, L, ws);
+  f.mod = model_args(L, ws);
+  f.weight = weight;
+  f.loglik = loglik;
+  f.partial = at<float>(ws, L.partial);
+  f.slot_floats = L.slot_floats;
+  f.queue = &at<WsHeader>(ws, 0)->queue[2];
+  f.status = &at<WsHeader>(ws, 0)->status;
+  f.n_items = labelled ? ngroups : ngroups * dims.K;
+  f.ckpt = C;
+  f.nck = NC;
+  {
+    Timed tm(T_FB, st);
+    e = launch_fb(L.NP, G, f, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+
+  ReduceLaunch r;
+  r.partial = f.partial;
+  r.red1 = at<float>(ws, L.red1);
+  r.model_of_seq = seqs->model_of_seq;
+  r.seqlen = at<int32_t>(ws, L.seqlen);
+  r.S = seqs->S; r.K = dims.K; r.N = dims.N; r.M = dims.M; r.NP = L.NP;
+  r.slot_floats = L.slot_floats;
+  r.nchunks = L.nchunks;
+  r.cnt_pi = cnt_pi; r.cnt_A = cnt_A; r.cnt_B = cnt_B;
+  {
+    Timed tm(T_REDUCE, st);
+    e = launch_reduce(r, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+  return HMM_OK;
+}
+
+int hmm_softmax_rows(hmm_dims_t dims, const float* lpi, const float* lA, const float* lB,
+                     float* pi, float* A, float* B, hmm_stream_t stream) {
+  g_err[0] = 0;
+  if (dims.K < 1 || dims.N < 1 || dims.M < 1) return fail(HMM_ERR_ARG, "dims must be positive");
+  if (!lpi || !lA || !lB || !pi || !A || !B) return fail(HMM_ERR_ARG, "NULL table");
+  Timed tm(T_SOFTMAX, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_softmax_rows(dims.K, dims.N, dims.M, lpi, lA, lB, pi, A, B,
+                                      reinterpret_cast<cudaStream_t>(stream));
+  tm.stop();
+  return e == cudaSuccess ? HMM_OK : cuda_fail(e, "softmax launch");
+}
+
+int hmm_softmax_grad(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                     const float* cpi, const float* cA, const float* cB, float* gpi, float* gA,
+                     float* gB, hmm_stream_t stream) {
+  g_err[0] = 0;
+  if (dims.K < 1 || dims.N < 1 || dims.M < 1) return fail(HMM_ERR_ARG, "dims must be positive");
+  if (!pi || !A || !B || !cpi || !cA || !cB || !gpi || !gA || !gB) return fail(HMM_ERR_ARG, "NULL table");
+  Timed tm(T_SGRAD, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_softmax_grad(dims.K, dims.N, dims.M, pi, A, B, cpi, cA, cB, gpi, gA, gB,
+                                      reinterpret_cast<cudaStream_t>(stream));
+  tm.stop();
+  return e == cudaSuccess ? HMM_OK : cuda_fail(e, "softmax grad launch");
+}
+
+int hmm_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, float grad_scale, int32_t* step,
+                  hmm_stream_t stream) {
+  g_err[0] = 0;
+  if (n < 0 || !step) return fail(HMM_ERR_ARG, "n < 0 or step counter NULL");
+  if (n == 0) return HMM_OK;
+  if (!param || !grad || !m || !v) return fail(HMM_ERR_ARG, "NULL buffer");
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f))
+    return fail(HMM_ERR_ARG, "betas must lie in [0, 1)");
+  Timed tm(T_ADAM, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_adam(n, param, grad, m, v, lr, beta1, beta2, eps, grad_scale, step,
+                              reinterpret_cast<cudaStream_t>(stream));
+  tm.stop();
+  return e == cudaSuccess ? HMM_OK : cuda_fail(e, "adam launch");
+}
+
+int hmm_get_device_status(const void* ws, hmm_stream_t stream, int32_t* status) {
+  g_err[0] = 0;
+  if (!ws || !status) return fail(HMM_ERR_ARG, "NULL workspace or status");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  *status = h;
+  if (h) return fail(HMM_ERR_DEVICE, "device status 0x%x%s%s%s", h,
+                     (h & HMM_STATUS_SYMBOL) ? " symbol-out-of-range" : "",
+                     (h & HMM_STATUS_PARAM) ? " bad-parameter" : "",
+                     (h & HMM_STATUS_SEQ) ? " bad-sequence" : "");
+  return HMM_OK;
+}
+
+int hmm_timing_enable(int on) {
+  g_err[0] = 0;
+  std::lock_guard<std::mutex> lk(g_timing.mu);
+  g_timing.on = on != 0;
+  return HMM_OK;
+}
+
+int hmm_timing_reset(void) {
+  g_err[0] = 0;
+  std::lock_guard<std::mutex> lk(g_timing.mu);
+  for (auto& r : g_timing.rec) {
+    for (auto& p : r) g_timing.pool.push_back(p);
+    r.clear();
+  }
+  return HMM_OK;
+}
+
+int hmm_timing_read(int32_t kind, int64_t* launches, double* total_ms) {
+  g_err[0] = 0;
+  if (kind < 0 || kind >= HMM_TIMING_KINDS || !launches || !total_ms)
+    return fail(HMM_ERR_ARG, "bad timing kind or NULL output");
+  std::lock_guard<std::mutex> lk(g_timing.mu);
+  double tot = 0.0;
+  for (auto& p : g_timing.rec[kind]) {
+    cudaError_t e = cudaEventSynchronize(p.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+    if (e != cudaSuccess) return cuda_fail(e, "timing read");
+    tot += ms;
+  }
+  *launches = (int64_t)g_timing.rec[kind].size();
+  *total_ms = tot;
+  return HMM_OK;
+}
+
+}  // extern "C"

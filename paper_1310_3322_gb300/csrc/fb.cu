@@ -1,0 +1,419 @@
+// fb.cu -- forward-backward adjoint, FP32 SIMT (Sec. 2.7 "Baum-Welch", its
+// E-step; Rabiner 1989 eqs. 24-25 backward variable, 37 xi, 38 gamma).
+//
+// For one (sequence, model) pair with weight w the kernel produces
+//   C_pi(i)   += w gamma_1(i)
+//   C_A(i,j)  += w sum_{t<T} xi_t(i,j)
+//   C_B(j,m)  += w sum_{t: o_t = m} gamma_t(j)
+// into a per-pair slot of the workspace (summed later in a fixed order).
+//
+// Memory: alpha is never stored whole. Phase 1 runs the scaled forward
+// recursion and keeps alpha_t (and the power-of-two exponent removed at t)
+// every C = ceil(sqrt(max_len)) steps in shared memory. Phase 2 walks the
+// segments backwards: it recomputes alpha over the segment from its
+// checkpoint into shared memory, then runs the backward recursion over the
+// segment. Both live in shared memory: O(sqrt(T) N) floats per pair.
+//
+// Scaling: alpha_t and beta_t each carry an exact power-of-two scale that is
+// never divided out. With u_{t+1}(j) = b_j(o_{t+1}) beta_{t+1}(j) and the
+// forward exponent e_{t+1} removed at step t+1,
+//   Z_t = sum_j (alpha_t A)_j u_{t+1}(j) = 2^{e_{t+1}} D_{t+1},
+//   D_{t+1} = sum_j alpha_{t+1}(j) beta_{t+1}(j),
+// so with v(j) = u_{t+1}(j) / Z_t
+//   xi_t(i,j)      = alpha_t(i) a_ij v(j)          (a_ij applied at the flush)
+//   gamma_{t+1}(j) = alpha_{t+1}(j) beta_{t+1}(j) / D_{t+1}
+//   beta_t(i)     ~ sum_j a_ij v(j)                (then rescaled),
+// and the weight w multiplies only what is accumulated.
+// Lane ownership: lane r of the pair owns states [rJ, rJ+J) both as columns
+// (forward: column slice of A) and as rows (backward: row slice of A, row
+// slice of the xi accumulator), so every step needs one broadcast vector.
+#include "hmm_internal.cuh"
+
+namespace hmmgb {
+
+// x * 2^k for any k in [-252, 254], as two exact multiplies.
+__device__ __forceinline__ float mul_pow2(float x, int k) {
+  const int k1 = k / 2, k2 = k - k1;
+  return x * exp2i(k1) * exp2i(k2);
+}
+
+template <int NP, int G>
+struct FbLayout {
+  static constexpr int J = NP / G;
+  static constexpr int PP = 32 / G;
+  static constexpr int XS = NP + 4;
+  // floats per pair, rounded to 4 (16-byte alignment of every region)
+  static __host__ __device__ int per_pair(int C, int NC, int M) {
+    const int n = 2 * XS + NC * NP + C * NP + NC + C + NP * (M + 1);
+    return (n + 3) & ~3;
+  }
+};
+
+template <int NP, int G>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+hmm_fb_simt(FbLaunch a) {
+  using L = FbLayout<NP, G>;
+  constexpr int J = L::J, PP = L::PP, XS = L::XS;
+  extern __shared__ __align__(16) float smem[];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = lane / G, r = lane % G, j0 = r * J;
+  const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
+  const int C = a.ckpt, NC = a.nck, MP = M + 1;
+  const bool labelled = a.seq.model_of_seq != nullptr;
+
+  const int per = L::per_pair(C, NC, M);
+  float* base = smem + (size_t)(warp * PP + p) * per;
+  float* xb = base;                                 // [2][XS]
+  float* ck = xb + 2 * XS;                          // [NC][NP]
+  float* seg = ck + NC * NP;                        // [C][NP]
+  int* cke = reinterpret_cast<int*>(seg + C * NP);  // [NC]
+  int* sege = cke + NC;                             // [C]
+  float* cb = reinterpret_cast<float*>(sege + C);   // [NP][MP]
+  // (per_pair() accounts for every region; cb follows without padding)
+
+  // emission-count accumulator starts at zero
+  for (int e = r; e < NP * MP; e += G) cb[e] = 0.f;
+  __syncwarp();
+
+  const int n_items = a.n_items;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(a.queue, 1);
+    item = __shfl_sync(HMM_FULL_MASK, item, 0);
+    if (item >= n_items) break;
+    const int g = labelled ? item : item / K;
+    int k = labelled ? 0 : item % K;
+    const int pos = g * PP + p;
+    const bool has = pos < S;
+    const int s = has ? a.seq.order[pos] : 0;
+    const int T = has ? a.seq.seqlen[s] : 0;
+    if (labelled && has && T >= 0) k = a.seq.model_of_seq[s];
+    const size_t slot = labelled ? (size_t)s : (size_t)s * K + k;
+    const int Tn = T < 0 ? 0 : T;
+    const float w = (has && a.weight) ? a.weight[slot] : 1.f;
+
+    // A slices of this pair's model
+    float2 ac[NP / 2][J];  // ac[i2][jj] = (a_{2i2, j}, a_{2i2+1, j}),  j = j0 + jj
+    float2 ar[J][NP / 2];  // ar[ii][j2] = (a_{i, 2j2}, a_{i, 2j2+1}),  i = j0 + ii
+    {
+      const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
+#pragma unroll
+      for (int i2 = 0; i2 < NP / 2; ++i2)
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj)
+          ac[i2][jj] = make_float2(__ldg(Ak + (2 * i2) * NP + j0 + jj),
+                                   __ldg(Ak + (2 * i2 + 1) * NP + j0 + jj));
+#pragma unroll
+      for (int ii = 0; ii < J; ++ii)
+#pragma unroll
+        for (int j2 = 0; j2 < NP / 2; ++j2)
+          ar[ii][j2] = __ldg(reinterpret_cast<const float2*>(Ak + (j0 + ii) * NP) + j2);
+    }
+    const float* Bk = a.mod.Btp + (size_t)k * M * NP + j0;
+    const int32_t* o = a.seq.symbols + ((has && T >= 0) ? a.seq.offsets[s] : 0);
+
+    // ---------------- phase 1: forward with checkpoints ----------------
+    float x[J];
+    int E = 0;
+    bool dead = false, bad = T < 0;
+    int err = 0;
+    {
+      int o0 = Tn > 0 ? __ldg(o) : 0;
+      if ((unsigned)o0 >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; o0 = 0; }
+      float b[J], pv[J];
+      load_vec<J>(b, Bk + (size_t)o0 * NP);
+      load_vec<J>(pv, a.mod.pip + (size_t)k * NP + j0);
+      float ls = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) { x[jj] = pv[jj] * b[jj]; ls += x[jj]; }
+      const float gs = group_sum<G>(ls);
+      if (Tn > 0 && !bad) {
+        if (gs == 0.f) dead = true;
+        else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
+        else {
+          const int e = rescale_pow2<J>(x, gs);
+          E += e;
+          store_vec<J>(ck + j0, x);
+          if (r == 0) cke[0] = e;
+        }
+      }
+    }
+    const int Tmax = __reduce_max_sync(HMM_FULL_MASK, Tn);
+    for (int t = 1; t < Tmax; ++t) {
+      const bool act = t < Tn && !dead && !bad;
+      float* xw = xb + (t & 1) * XS;
+      store_vec<J>(xw + j0, x);
+      __syncwarp();
+      float2 acc[J];
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) acc[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < NP / 4; ++q) {
+        const float4 xv = *reinterpret_cast<const float4*>(xw + 4 * q);
+        const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+          acc[jj] = ffma2(lo, ac[2 * q][jj], acc[jj]);
+          acc[jj] = ffma2(hi, ac[2 * q + 1][jj], acc[jj]);
+        }
+      }
+      int ot = act ? __ldg(o + t) : 0;
+      if (act && (unsigned)ot >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; ot = 0; }
+      float b[J];
+      load_vec<J>(b, Bk + (size_t)ot * NP);
+      float nx[J], ls = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) { nx[jj] = (acc[jj].x + acc[jj].y) * b[jj]; ls += nx[jj]; }
+      const float gs = group_sum<G>(ls);
+      if (act && !bad) {
+        if (gs == 0.f) dead = true;
+        else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
+        else {
+          const int e = rescale_pow2<J>(nx, gs);
+          E += e;
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) x[jj] = nx[jj];
+          if (t % C == 0) {
+            store_vec<J>(ck + (t / C) * NP + j0, x);
+            if (r == 0) cke[t / C] = e;
+          }
+        }
+      }
+    }
+    {
+      float ls = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) ls += x[jj];
+      const float fs = group_sum<G>(ls);
+      if (has && r == 0) {
+        float out;
+        if (bad) { out = __int_as_float(0x7fc00000); if (err) set_status(a.status, err); }
+        else if (Tn == 0) out = 0.f;
+        else if (dead) out = -INFINITY;
+        else out = (float)(log((double)fs) + (double)E * 0.69314718055994530942);
+        a.loglik[slot] = out;
+      }
+    }
+
+    // ---------------- phase 2: backward over segments ----------------
+    const bool alive = has && !bad && !dead && Tn > 0;
+    const int Tb = alive ? Tn : 0;
+    const int TbMax = __reduce_max_sync(HMM_FULL_MASK, Tb);
+    float beta[J];
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) beta[jj] = 1.f;
+    float2 xa[J][NP / 2];
+#pragma unroll
+    for (int ii = 0; ii < J; ++ii)
+#pragma unroll
+      for (int j2 = 0; j2 < NP / 2; ++j2) xa[ii][j2] = make_float2(0.f, 0.f);
+    float cpi[J];
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) cpi[jj] = 0.f;
+
+    int parity = 0;
+    const int nseg = (TbMax + C - 1) / C;
+    for (int c = nseg - 1; c >= 0; --c) {
+      const int t0 = c * C;
+      const int t1 = min(t0 + C, TbMax) - 1;
+      // recompute alpha over [t0, t1] from checkpoint c
+      if (alive && t0 <= Tb - 1) {
+        load_vec_smem<J>(x, ck + c * NP + j0);
+        store_vec<J>(seg + j0, x);
+        if (r == 0) sege[0] = cke[c];
+      }
+      for (int t = t0 + 1; t <= t1; ++t) {
+        const bool act = alive && t <= Tb - 1;
+        float* xw = xb + parity * XS;
+        parity ^= 1;
+        store_vec<J>(xw + j0, x);
+        __syncwarp();
+        float2 acc[J];
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) acc[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) {
+          const float4 xv = *reinterpret_cast<const float4*>(xw + 4 * q);
+          const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) {
+            acc[jj] = ffma2(lo, ac[2 * q][jj], acc[jj]);
+            acc[jj] = ffma2(hi, ac[2 * q + 1][jj], acc[jj]);
+          }
+        }
+        const int ot = act ? __ldg(o + t) : 0;
+        float b[J];
+        load_vec<J>(b, Bk + (size_t)ot * NP);
+        float nx[J], ls = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) { nx[jj] = (acc[jj].x + acc[jj].y) * b[jj]; ls += nx[jj]; }
+        const float gs = group_sum<G>(ls);
+        if (act) {
+          const int e = rescale_pow2<J>(nx, gs);
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) x[jj] = nx[jj];
+          store_vec<J>(seg + (t - t0) * NP + j0, x);
+          if (r == 0) sege[t - t0] = e;
+        }
+      }
+      __syncwarp();
+      // backward steps t = t1 .. t0
+      for (int t = t1; t >= t0; --t) {
+        const bool act = alive && t <= Tb - 2;
+        float a1[J], a0[J];
+        int e1 = 0;
+        if (act) {
+          if (t + 1 <= t1) {
+            load_vec_smem<J>(a1, seg + (t + 1 - t0) * NP + j0);
+            e1 = sege[t + 1 - t0];
+          } else {
+            load_vec_smem<J>(a1, ck + (c + 1) * NP + j0);
+            e1 = cke[c + 1];
+          }
+          load_vec_smem<J>(a0, seg + (t - t0) * NP + j0);
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) { a1[jj] = 0.f; a0[jj] = 0.f; }
+        }
+        const int o1 = act ? __ldg(o + t + 1) : 0;
+        float b1[J];
+        load_vec<J>(b1, Bk + (size_t)o1 * NP);
+        float u[J], dl = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) { u[jj] = b1[jj] * beta[jj]; dl += a1[jj] * beta[jj]; }
+        const float D = group_sum<G>(dl);
+        float v[J];
+        if (act) {
+          const float invD = 1.f / D;
+          const float wd = w * invD;
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) {
+            // gamma_{t+1}(j) for the emission counts
+            cb[(j0 + jj) * MP + o1] += wd * a1[jj] * beta[jj];
+            v[jj] = mul_pow2(u[jj], -e1) * invD;
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) v[jj] = 0.f;
+        }
+        float* xw = xb + parity * XS;
+        parity ^= 1;
+        store_vec<J>(xw + j0, v);
+        __syncwarp();
+        float2 bacc[J];
+#pragma unroll
+        for (int ii = 0; ii < J; ++ii) bacc[ii] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) {
+          const float4 vv = *reinterpret_cast<const float4*>(xw + 4 * q);
+          const float2 lo = make_float2(vv.x, vv.y), hi = make_float2(vv.z, vv.w);
+#pragma unroll
+          for (int ii = 0; ii < J; ++ii) {
+            bacc[ii] = ffma2(lo, ar[ii][2 * q], bacc[ii]);
+            bacc[ii] = ffma2(hi, ar[ii][2 * q + 1], bacc[ii]);
+            const float2 aa = make_float2(w * a0[ii], w * a0[ii]);
+            xa[ii][2 * q] = ffma2(aa, lo, xa[ii][2 * q]);
+            xa[ii][2 * q + 1] = ffma2(aa, hi, xa[ii][2 * q + 1]);
+          }
+        }
+        float nb[J], ls = 0.f;
+#pragma unroll
+        for (int ii = 0; ii < J; ++ii) { nb[ii] = bacc[ii].x + bacc[ii].y; ls += nb[ii]; }
+        const float gs = group_sum<G>(ls);
+        if (act && gs > 0.f && !isinf(gs)) {
+          rescale_pow2<J>(nb, gs);
+#pragma unroll
+          for (int ii = 0; ii < J; ++ii) beta[ii] = nb[ii];
+        }
+      }
+    }
+    // t = 0: gamma_1 for pi and the first emission
+    {
+      float a0[J];
+      if (alive) load_vec_smem<J>(a0, seg + j0);
+      else {
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) a0[jj] = 0.f;
+      }
+      float dl = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) dl += a0[jj] * beta[jj];
+      const float D = group_sum<G>(dl);
+      if (alive) {
+        const int o0 = __ldg(o);
+        const float wd = w / D;
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+          const float gmm = wd * a0[jj] * beta[jj];
+          cpi[jj] = gmm;
+          cb[(j0 + jj) * MP + o0] += gmm;
+        }
+      }
+    }
+    __syncwarp();
+    // ---------------- flush this pair's slot ----------------
+    if (has) {
+      float* out = a.partial + slot * a.slot_floats;
+      store_vec<J>(out + j0, cpi);
+#pragma unroll
+      for (int ii = 0; ii < J; ++ii) {
+        float2* row = reinterpret_cast<float2*>(out + NP + (size_t)(j0 + ii) * NP);
+#pragma unroll
+        for (int j2 = 0; j2 < NP / 2; ++j2)
+          row[j2] = make_float2(ar[ii][j2].x * xa[ii][j2].x, ar[ii][j2].y * xa[ii][j2].y);
+      }
+      float* ob = out + NP + NP * NP;
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) {
+        float* crow = cb + (j0 + jj) * MP;
+        for (int m = 0; m < M; ++m) {
+          ob[(size_t)(j0 + jj) * M + m] = crow[m];
+          crow[m] = 0.f;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// --------------------------------------------------------------------------
+// dispatch
+// --------------------------------------------------------------------------
+size_t fb_smem_bytes(int NP, int G, int C, int NC, int M) {
+  const int PP = 32 / G;
+  const int XS = NP + 4;
+  int n = 2 * XS + NC * NP + C * NP + NC + C + NP * (M + 1);
+  n = (n + 3) & ~3;
+  return (size_t)kWarpsPerBlock * PP * n * sizeof(float);
+}
+
+template <int NP, int G>
+static cudaError_t launch_fb_t(const FbLaunch& a, cudaStream_t st) {
+  auto kern = hmm_fb_simt<NP, G>;
+  const size_t smem = fb_smem_bytes(NP, G, a.ckpt, a.nck, a.seq.M);
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int blocks = num_sms() * per_sm;
+  const int need = (a.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  kern<<<blocks, kWarpsPerBlock * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define HMM_FB_CASE(NPV, GV) \
+  if (NP == NPV && G == GV) return launch_fb_t<NPV, GV>(a, st);
+
+cudaError_t launch_fb(int NP, int G, const FbLaunch& a, cudaStream_t st) {
+  HMM_FB_CASE(4, 2) HMM_FB_CASE(4, 4)
+  HMM_FB_CASE(8, 4) HMM_FB_CASE(8, 8)
+  HMM_FB_CASE(16, 8) HMM_FB_CASE(16, 16)
+  HMM_FB_CASE(32, 32)
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hmmgb

@@ -1,0 +1,276 @@
+// hmm_internal.cuh -- shared internals of the sm_103a HMM library: workspace
+// layout, kernel argument blocks, and the small device helpers every kernel
+// uses (group reductions, packed FP32x2 arithmetic, exact power-of-two
+// rescaling, the length bucketing of the scheduler).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hmm.h"
+
+namespace hmmgb {
+
+constexpr int kWarpsPerBlock = 4;      // SIMT kernels: 128-thread blocks
+constexpr int kPlanThreads = 1024;     // setup kernel block size
+constexpr int kLenBuckets = 1024;      // scheduler length buckets
+constexpr int kReduceChunk = 256;      // sequences per first-level count reduction
+constexpr int kReduceTile = 256;       // count entries per reduction block
+constexpr float kViterbiQuant = 32768.f;  // Viterbi offsets are multiples of 2^-15
+
+// ---------------------------------------------------------------------------
+// workspace layout (all offsets 256-byte aligned)
+// ---------------------------------------------------------------------------
+struct WsHeader {
+  int32_t status;      // HMM_STATUS_* bits
+  int32_t queue[7];    // persistent-kernel work counters
+  int32_t pad[56];
+};
+static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+struct WsLayout {
+  size_t order, seqlen, done, bpoff, best, pip, Ap, Btp, bp, partial, red1, total;
+  int NP;
+  int64_t bp_cap;      // bytes of backpointer storage
+  int64_t slots;       // adjoint partial slots
+  int64_t slot_floats; // floats per slot (NP + NP*NP + NP*M)
+  int nchunks;         // first-level reduction chunks
+};
+
+// ---------------------------------------------------------------------------
+// kernel argument blocks
+// ---------------------------------------------------------------------------
+struct SeqArgs {
+  const int32_t* symbols;
+  const int64_t* offsets;
+  const int32_t* model_of_seq;  // NULL = all models
+  const int32_t* seqlen;        // validated lengths (-1 = invalid pair)
+  const int32_t* order;         // sequences sorted by decreasing length
+  int S;
+  int K;
+  int M;
+};
+
+struct ModelArgs {
+  const float* pip;   // [K][NP]
+  const float* Ap;    // [K][NP][NP]
+  const float* Btp;   // [K][M][NP]  (emission table transposed: symbol-major)
+};
+
+struct SetupArgs {
+  int K, N, M, NP, S;
+  int64_t total_obs;
+  int max_len;         // sequences longer than this are rejected
+  int log_mode;        // 1: tables hold natural logs (Viterbi), 0: probabilities
+  int want_bpoff;      // 1: compute backpointer offsets (Viterbi)
+  int ndone;           // entries of `done` to clear
+  const float* pi;
+  const float* A;
+  const float* B;
+  const int32_t* lengths;
+  const int64_t* offsets;
+  const int32_t* model_of_seq;
+  float* pip;
+  float* Ap;
+  float* Btp;
+  int32_t* seqlen;
+  int32_t* order;
+  int32_t* done;
+  int64_t* bpoff;
+  int64_t bp_cap_rows;   // rows of NP bytes available for backpointers
+  int32_t* status;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#define HMM_FULL_MASK 0xffffffffu
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(HMM_FULL_MASK, v, o);
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(HMM_FULL_MASK, v, o));
+  return v;
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Three-input FP32 maximum (sm_100+ PTX form).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// 2^k as a float, for k in [-126, 127].
+__device__ __forceinline__ float exp2i(int k) { return __int_as_float((k + 127) << 23); }
+
+// For finite s > 0 returns e with s * 2^-e in [1, 2). When s is below 2^-120
+// the caller first multiplies by 2^64 (see rescale_pow2).
+__device__ __forceinline__ int frexp2(float s) { return ((__float_as_int(s) >> 23) & 0xff) - 127; }
+
+// Length bucket of the scheduler: exact below 256, then 32 buckets per octave.
+__device__ __forceinline__ int length_bucket(int T) {
+  if (T < 256) return T < 0 ? 0 : T;
+  const int e = 31 - __clz(T);
+  int b = 256 + (e - 8) * 32 + ((T >> (e - 5)) & 31);
+  return b < kLenBuckets ? b : kLenBuckets - 1;
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int bits) { atomicOr(status, bits); }
+
+// Vector loads/stores of J consecutive floats (J in {1,2,4,8}), 4*J-byte aligned.
+template <int J>
+__device__ __forceinline__ void load_vec(float (&d)[J], const float* p) {
+  if constexpr (J == 1) {
+    d[0] = __ldg(p);
+  } else if constexpr (J == 2) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    d[0] = v.x; d[1] = v.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < J / 4; ++q) {
+      float4 v = __ldg(reinterpret_cast<const float4*>(p) + q);
+      d[4 * q] = v.x; d[4 * q + 1] = v.y; d[4 * q + 2] = v.z; d[4 * q + 3] = v.w;
+    }
+  }
+}
+
+template <int J>
+__device__ __forceinline__ void store_vec(float* p, const float (&s)[J]) {
+  if constexpr (J == 1) {
+    p[0] = s[0];
+  } else if constexpr (J == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(s[0], s[1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < J / 4; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(s[4 * q], s[4 * q + 1], s[4 * q + 2], s[4 * q + 3]);
+  }
+}
+
+template <int J>
+__device__ __forceinline__ void load_vec_smem(float (&d)[J], const float* p) {
+  if constexpr (J == 1) {
+    d[0] = p[0];
+  } else if constexpr (J == 2) {
+    float2 v = *reinterpret_cast<const float2*>(p);
+    d[0] = v.x; d[1] = v.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < J / 4; ++q) {
+      float4 v = reinterpret_cast<const float4*>(p)[q];
+      d[4 * q] = v.x; d[4 * q + 1] = v.y; d[4 * q + 2] = v.z; d[4 * q + 3] = v.w;
+    }
+  }
+}
+
+// Exact power-of-two rescaling of a group-distributed vector so that its sum
+// lies in [1, 2). `gsum` is the group-wide sum (> 0, finite); returns the
+// base-2 exponent removed (the caller adds it to its running total).
+template <int J>
+__device__ __forceinline__ int rescale_pow2(float (&x)[J], float gsum) {
+  int shift = 0;
+  if (gsum < 0x1p-120f) {  // keep the factor representable
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) x[jj] *= 0x1p64f;
+    gsum *= 0x1p64f;
+    shift = -64;
+  } else if (gsum >= 0x1p120f) {
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) x[jj] *= 0x1p-64f;
+    gsum *= 0x1p-64f;
+    shift = 64;
+  }
+  const int e = frexp2(gsum);
+  const float f = exp2i(-e);
+#pragma unroll
+  for (int jj = 0; jj < J; ++jj) x[jj] *= f;
+  return e + shift;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st);
+cudaError_t launch_softmax_rows(int K, int N, int M, const float* lpi, const float* lA,
+                                const float* lB, float* pi, float* A, float* B, cudaStream_t st);
+cudaError_t launch_softmax_grad(int K, int N, int M, const float* pi, const float* A,
+                                const float* B, const float* cpi, const float* cA,
+                                const float* cB, float* gpi, float* gA, float* gB,
+                                cudaStream_t st);
+cudaError_t launch_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr,
+                        float b1, float b2, float eps, float gs, int32_t* step, cudaStream_t st);
+
+struct FwdLaunch {
+  SeqArgs seq;
+  ModelArgs mod;
+  float* loglik;
+  int32_t* argmax;
+  int32_t* done;
+  int32_t* queue;
+  int32_t* status;
+  int n_items;
+};
+cudaError_t launch_forward(int NP, int G, const FwdLaunch& a, cudaStream_t st);
+
+struct VitLaunch {
+  SeqArgs seq;
+  ModelArgs mod;     // log tables
+  float* score;
+  int32_t* best;     // decoded model per sequence (workspace or caller's)
+  int32_t* path;
+  int32_t* done;
+  int32_t* queue;    // two counters: [0] scores, [1] paths
+  int32_t* status;
+  const int64_t* bpoff;
+  uint8_t* bp;
+  int n_items_score;
+  int n_items_path;
+};
+cudaError_t launch_viterbi_scores(int NP, int G, const VitLaunch& a, cudaStream_t st);
+cudaError_t launch_viterbi_paths(int NP, int G, const VitLaunch& a, cudaStream_t st);
+
+struct FbLaunch {
+  SeqArgs seq;
+  ModelArgs mod;
+  const float* weight;
+  float* loglik;
+  float* partial;
+  int64_t slot_floats;
+  int32_t* queue;
+  int32_t* status;
+  int n_items;
+  int ckpt;          // checkpoint stride C
+  int nck;           // checkpoints per pair (ceil(max_len / C))
+};
+cudaError_t launch_fb(int NP, int G, const FbLaunch& a, cudaStream_t st);
+size_t fb_smem_bytes(int NP, int G, int C, int NC, int M);
+
+struct ReduceLaunch {
+  const float* partial;
+  float* red1;
+  const int32_t* model_of_seq;
+  const int32_t* seqlen;
+  int S, K, N, M, NP;
+  int64_t slot_floats;
+  int nchunks;
+  float* cnt_pi;
+  float* cnt_A;
+  float* cnt_B;
+};
+cudaError_t launch_reduce(const ReduceLaunch& a, cudaStream_t st);
+
+// Instantiated lane counts per (op, NP); the first entry is the default.
+int candidates(int op, int NP, int* out, int cap);
+int num_sms();
+
+}  // namespace hmmgb

@@ -1,0 +1,365 @@
+// setup.cu -- per-call preparation and the small elementwise kernels.
+//
+//  * setup_kernel: one launch per hmm_* call. Block 0 validates every
+//    sequence, sorts the sequences by decreasing length (bucketed counting
+//    sort; the persistent kernels then take work longest-first) and, for
+//    Viterbi, assigns backpointer storage. The other blocks copy pi, A and
+//    B^T into the padded tables the recursions read (probabilities, or
+//    natural logs for Viterbi) and flag negative or non-finite parameters.
+//  * softmax_rows / softmax_grad: the row-softmax parameterisation used for
+//    learning and its chain rule, one warp per row.
+//  * adam: one fused Adam update.
+//  * reduce1 / reduce2: the fixed-order two-level sum of the adjoint's
+//    per-pair count partials (bitwise reproducible).
+#include "hmm_internal.cuh"
+
+namespace hmmgb {
+
+// Exclusive scan over a 1024-thread block; `tmp` holds 32 entries.
+template <typename T>
+__device__ T block_exclusive_scan(T v, T* tmp, T* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(HMM_FULL_MASK, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = tmp[lane];
+    T wx = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(HMM_FULL_MASK, wx, o);
+      if (lane >= o) wx += y;
+    }
+    tmp[lane] = wx - w;  // exclusive prefix of warp totals
+    if (lane == 31 && total) *total = wx;
+  }
+  __syncthreads();
+  const T r = x - v + tmp[warp];
+  __syncthreads();
+  return r;
+}
+
+__device__ void plan_block(const SetupArgs& a) {
+  __shared__ int hist[kLenBuckets];
+  __shared__ int itmp[32];
+  __shared__ long long ltmp[32];
+  const int tid = threadIdx.x;
+  for (int b = tid; b < kLenBuckets; b += kPlanThreads) hist[b] = 0;
+  for (int i = tid; i < a.ndone; i += kPlanThreads) a.done[i] = 0;
+  __syncthreads();
+
+  for (int s = tid; s < a.S; s += kPlanThreads) {
+    const int T = a.lengths[s];
+    const long long off = a.offsets[s];
+    bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
+    if (ok && a.model_of_seq) {
+      const int k = a.model_of_seq[s];
+      ok = k >= 0 && k < a.K;
+    }
+    if (!ok) set_status(a.status, HMM_STATUS_SEQ);
+    a.seqlen[s] = ok ? T : -1;
+    atomicAdd(&hist[kLenBuckets - 1 - length_bucket(ok ? T : 0)], 1);
+  }
+  __syncthreads();
+
+  // one bucket per thread (kLenBuckets == kPlanThreads)
+  const int start = block_exclusive_scan<int>(hist[tid], itmp, nullptr);
+  hist[tid] = start;
+  __syncthreads();
+
+  for (int s = tid; s < a.S; s += kPlanThreads) {
+    const int T = a.seqlen[s];
+    const int key = kLenBuckets - 1 - length_bucket(T < 0 ? 0 : T);
+    const int pos = atomicAdd(&hist[key], 1);
+    a.order[pos] = s;
+  }
+
+  if (a.want_bpoff) {
+    __syncthreads();
+    const int chunk = (a.S + kPlanThreads - 1) / kPlanThreads;
+    const int b0 = min(a.S, tid * chunk), b1 = min(a.S, b0 + chunk);
+    long long local = 0;
+    for (int s = b0; s < b1; ++s) local += max(a.seqlen[s], 0);
+    long long run = block_exclusive_scan<long long>(local, ltmp, nullptr);
+    for (int s = b0; s < b1; ++s) {
+      const int T = a.seqlen[s];
+      a.bpoff[s] = run;
+      if (T > 0) {
+        if (run + T > a.bp_cap_rows) {  // sum of lengths above total_obs
+          a.seqlen[s] = -1;
+          set_status(a.status, HMM_STATUS_SEQ);
+        }
+        run += T;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float prep_value(float v, int log_mode, int32_t* status) {
+  if (!(v >= 0.f) || isinf(v)) {
+    set_status(status, HMM_STATUS_PARAM);
+    return __int_as_float(0x7fc00000);
+  }
+  return log_mode ? logf(v) : v;
+}
+
+__device__ void prep_blocks(const SetupArgs& a, int blk, int nblk) {
+  const long long n_pi = (long long)a.K * a.NP;
+  const long long n_A = n_pi * a.NP;
+  const long long n_B = (long long)a.K * a.M * a.NP;
+  const float pad = a.log_mode ? -INFINITY : 0.f;
+  const long long stride = (long long)nblk * blockDim.x;
+  for (long long idx = (long long)blk * blockDim.x + threadIdx.x; idx < n_pi + n_A + n_B;
+       idx += stride) {
+    if (idx < n_pi) {
+      const int k = (int)(idx / a.NP), j = (int)(idx % a.NP);
+      a.pip[idx] = j < a.N ? prep_value(a.pi[(size_t)k * a.N + j], a.log_mode, a.status) : pad;
+    } else if (idx < n_pi + n_A) {
+      const long long r = idx - n_pi;
+      const int k = (int)(r / ((long long)a.NP * a.NP));
+      const int i = (int)((r / a.NP) % a.NP), j = (int)(r % a.NP);
+      a.Ap[r] = (i < a.N && j < a.N)
+                    ? prep_value(a.A[((size_t)k * a.N + i) * a.N + j], a.log_mode, a.status)
+                    : pad;
+    } else {
+      const long long r = idx - n_pi - n_A;
+      const int k = (int)(r / ((long long)a.M * a.NP));
+      const int m = (int)((r / a.NP) % a.M), j = (int)(r % a.NP);
+      a.Btp[r] = j < a.N ? prep_value(a.B[((size_t)k * a.N + j) * a.M + m], a.log_mode, a.status)
+                         : pad;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) setup_kernel(SetupArgs a) {
+  if (blockIdx.x == 0)
+    plan_block(a);
+  else
+    prep_blocks(a, blockIdx.x - 1, gridDim.x - 1);
+}
+
+cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st) {
+  const long long work = (long long)a.K * a.NP * (1 + a.NP + a.M);
+  int nprep = (int)((work + kPlanThreads * 4 - 1) / (kPlanThreads * 4));
+  nprep = max(1, min(nprep, 2 * num_sms()));
+  setup_kernel<<<1 + nprep, kPlanThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// row softmax and its chain rule (one warp per row)
+// ---------------------------------------------------------------------------
+struct RowMap {
+  int K, N, M;
+  __device__ __forceinline__ bool row(long long r, long long& base, int& width) const {
+    const long long r_pi = K, r_A = (long long)K * N, r_B = (long long)K * N;
+    if (r < r_pi) { base = r * N; width = N; return true; }
+    r -= r_pi;
+    if (r < r_A) { base = (long long)K * N + r * N; width = N; return true; }
+    r -= r_A;
+    if (r < r_B) { base = (long long)K * N + (long long)K * N * N + r * M; width = M; return true; }
+    return false;
+  }
+};
+
+// Tables are addressed as one virtual array [pi | A | B]; `sel` picks the
+// real pointer for a virtual base.
+struct Tables {
+  const float* pi; const float* A; const float* B;
+  long long nA0, nB0;  // virtual starts of A and B
+  __device__ __forceinline__ const float* at(long long base) const {
+    if (base < nA0) return pi + base;
+    if (base < nB0) return A + (base - nA0);
+    return B + (base - nB0);
+  }
+};
+struct MTables {
+  float* pi; float* A; float* B;
+  long long nA0, nB0;
+  __device__ __forceinline__ float* at(long long base) const {
+    if (base < nA0) return pi + base;
+    if (base < nB0) return A + (base - nA0);
+    return B + (base - nB0);
+  }
+};
+
+__global__ void softmax_rows_kernel(RowMap map, Tables in, MTables out, long long nrows) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  long long base; int width;
+  map.row(r, base, width);
+  const float* x = in.at(base);
+  float* y = out.at(base);
+  float mx = -INFINITY;
+  for (int c = lane; c < width; c += 32) mx = fmaxf(mx, x[c]);
+  mx = group_max<32>(mx);
+  float s = 0.f;
+  for (int c = lane; c < width; c += 32) s += expf(x[c] - mx);
+  s = group_sum<32>(s);
+  const float inv = 1.f / s;
+  for (int c = lane; c < width; c += 32) y[c] = expf(x[c] - mx) * inv;
+}
+
+__global__ void softmax_grad_kernel(RowMap map, Tables p, Tables c, MTables g, long long nrows) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  long long base; int width;
+  map.row(r, base, width);
+  const float* pp = p.at(base);
+  const float* cc = c.at(base);
+  float* gg = g.at(base);
+  float tot = 0.f;
+  for (int q = lane; q < width; q += 32) tot += cc[q];
+  tot = group_sum<32>(tot);
+  __syncwarp();
+  for (int q = lane; q < width; q += 32) gg[q] = cc[q] - pp[q] * tot;
+}
+
+static long long n_rows(int K, int N) { return (long long)K + 2LL * K * N; }
+
+cudaError_t launch_softmax_rows(int K, int N, int M, const float* lpi, const float* lA,
+                                const float* lB, float* pi, float* A, float* B, cudaStream_t st) {
+  RowMap map{K, N, M};
+  const long long nA0 = (long long)K * N, nB0 = nA0 + (long long)K * N * N;
+  Tables in{lpi, lA, lB, nA0, nB0};
+  MTables out{pi, A, B, nA0, nB0};
+  const long long rows = n_rows(K, N);
+  const int threads = 256;
+  const long long blocks = (rows * 32 + threads - 1) / threads;
+  softmax_rows_kernel<<<(unsigned)blocks, threads, 0, st>>>(map, in, out, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_softmax_grad(int K, int N, int M, const float* pi, const float* A,
+                                const float* B, const float* cpi, const float* cA,
+                                const float* cB, float* gpi, float* gA, float* gB,
+                                cudaStream_t st) {
+  RowMap map{K, N, M};
+  const long long nA0 = (long long)K * N, nB0 = nA0 + (long long)K * N * N;
+  Tables p{pi, A, B, nA0, nB0};
+  Tables c{cpi, cA, cB, nA0, nB0};
+  MTables g{gpi, gA, gB, nA0, nB0};
+  const long long rows = n_rows(K, N);
+  const int threads = 256;
+  const long long blocks = (rows * 32 + threads - 1) / threads;
+  softmax_grad_kernel<<<(unsigned)blocks, threads, 0, st>>>(map, p, c, g, rows);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adam
+// ---------------------------------------------------------------------------
+__global__ void adam_kernel(int64_t n, float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, float lr, float b1,
+                            float b2, float eps, float gs, const int32_t* __restrict__ step) {
+  const float t = (float)(*step + 1);
+  const float inv_bc1 = 1.f / (1.f - powf(b1, t));
+  const float inv_bc2 = 1.f / (1.f - powf(b2, t));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = gs * g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
+  }
+}
+
+__global__ void step_increment_kernel(int32_t* step) { *step += 1; }
+
+cudaError_t launch_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr,
+                        float b1, float b2, float eps, float gs, int32_t* step, cudaStream_t st) {
+  const int threads = 256;
+  long long blocks = (n + threads - 1) / threads;
+  blocks = blocks < 4LL * num_sms() ? blocks : 4LL * num_sms();
+  if (blocks < 1) blocks = 1;
+  adam_kernel<<<(unsigned)blocks, threads, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, gs, step);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  step_increment_kernel<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order reduction of the adjoint's per-pair count partials
+// ---------------------------------------------------------------------------
+constexpr int kReduceModels = 16;  // models per first-level block
+
+__global__ void __launch_bounds__(kReduceTile) reduce1_kernel(ReduceLaunch a, int chunk) {
+  __shared__ float acc[kReduceModels][kReduceTile];
+  const int tid = threadIdx.x;
+  const int64_t e = (int64_t)blockIdx.x * kReduceTile + tid;
+  const int c = blockIdx.y;
+  const int k0 = blockIdx.z * kReduceModels;
+  const int k1 = min(a.K, k0 + kReduceModels);
+#pragma unroll
+  for (int q = 0; q < kReduceModels; ++q) acc[q][tid] = 0.f;
+  const int s0 = c * chunk, s1 = min(a.S, s0 + chunk);
+  if (e < a.slot_floats) {
+    for (int s = s0; s < s1; ++s) {
+      if (a.seqlen[s] < 0) continue;
+      if (a.model_of_seq) {
+        const int k = a.model_of_seq[s];
+        if (k >= k0 && k < k1) acc[k - k0][tid] += a.partial[(int64_t)s * a.slot_floats + e];
+      } else {
+        for (int k = k0; k < k1; ++k)
+          acc[k - k0][tid] += a.partial[((int64_t)s * a.K + k) * a.slot_floats + e];
+      }
+    }
+    for (int k = k0; k < k1; ++k) a.red1[((int64_t)c * a.K + k) * a.slot_floats + e] = acc[k - k0][tid];
+  }
+}
+
+__global__ void reduce2_kernel(ReduceLaunch a) {
+  const int64_t nA = (int64_t)a.K * a.N;
+  const int64_t nAA = nA * a.N;
+  const int64_t nB = nA * a.M;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nA + nAA + nB) return;
+  int k;
+  int64_t e;
+  float* out;
+  if (idx < nA) {
+    k = (int)(idx / a.N);
+    const int i = (int)(idx % a.N);
+    e = i;
+    out = a.cnt_pi + idx;
+  } else if (idx < nA + nAA) {
+    const int64_t r = idx - nA;
+    k = (int)(r / ((int64_t)a.N * a.N));
+    const int i = (int)((r / a.N) % a.N), j = (int)(r % a.N);
+    e = a.NP + (int64_t)i * a.NP + j;
+    out = a.cnt_A + r;
+  } else {
+    const int64_t r = idx - nA - nAA;
+    k = (int)(r / ((int64_t)a.N * a.M));
+    const int j = (int)((r / a.M) % a.N), m = (int)(r % a.M);
+    e = a.NP + (int64_t)a.NP * a.NP + (int64_t)j * a.M + m;
+    out = a.cnt_B + r;
+  }
+  float s = 0.f;
+  for (int c = 0; c < a.nchunks; ++c) s += a.red1[((int64_t)c * a.K + k) * a.slot_floats + e];
+  *out = s;
+}
+
+cudaError_t launch_reduce(const ReduceLaunch& a, cudaStream_t st) {
+  const int chunk = (a.S + a.nchunks - 1) / a.nchunks;
+  dim3 g1((unsigned)((a.slot_floats + kReduceTile - 1) / kReduceTile), (unsigned)a.nchunks,
+          (unsigned)((a.K + kReduceModels - 1) / kReduceModels));
+  reduce1_kernel<<<g1, kReduceTile, 0, st>>>(a, chunk);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t n = (int64_t)a.K * a.N * (1 + a.N + a.M);
+  reduce2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace hmmgb

@@ -1,0 +1,146 @@
+"""The C-ABI library loads, exports every symbol include/hmm.h declares, and
+rejects bad arguments on the host before touching a device (CPU only: no call
+here reaches a kernel launch)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_1310_3322_gb300 import hmm
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    return hmm.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = hmm.header_symbols()
+    assert len(names) >= 13
+    out = subprocess.run(["nm", "-D", "--defined-only", hmm.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+
+
+def test_library_has_no_torch_dependency(lib):
+    out = subprocess.run(["ldd", hmm.LIB_PATH], capture_output=True, text=True).stdout
+    assert "torch" not in out and "c10" not in out
+
+
+def test_sm103a_code_only():
+    from paper_1310_3322_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def _fake(i):
+    # 256-byte aligned dummy addresses; host-side checks fail before any use
+    return 0x7f0000000000 + 0x100000 * i
+
+
+def _seqs(S=4, max_len=10, total=40, mos=False):
+    return hmm.hmm_seqs_t(_fake(1), _fake(2), _fake(3), _fake(4) if mos else None, S, max_len,
+                          total)
+
+
+def test_workspace_size_is_host_only_and_monotone(lib):
+    d = hmm.hmm_dims_t(10, 16, 32)
+    sizes = []
+    for S in (0, 1, 100, 4096):
+        q = _seqs(S=S, total=S * 300)
+        out = ctypes.c_size_t()
+        assert lib.hmm_workspace_size(d, ctypes.byref(q), hmm.HMM_OP_VITERBI, ctypes.byref(out)) == 0
+        sizes.append(out.value)
+    assert sizes == sorted(sizes) and sizes[0] >= 256 and sizes[0] % 256 == 0
+    q = _seqs(S=100)
+    out = ctypes.c_size_t()
+    assert lib.hmm_workspace_size(d, ctypes.byref(q), 7, ctypes.byref(out)) == hmm.HMM_ERR_ARG
+
+
+def _forward(lib, dims, seqs, pi=_fake(5), loglik=_fake(8), ws=_fake(9), ws_bytes=1 << 30,
+             precision=hmm.HMM_FP32):
+    return lib.hmm_forward(dims, pi, _fake(6), _fake(7), ctypes.byref(seqs), precision, loglik,
+                           None, ws, ws_bytes, None)
+
+
+def test_forward_argument_errors(lib):
+    d = hmm.hmm_dims_t(2, 4, 8)
+    q = _seqs()
+    assert _forward(lib, d, q, pi=None) == hmm.HMM_ERR_ARG
+    assert "pi/A/B" in hmm.hmm_last_error()
+    assert _forward(lib, d, q, loglik=None) == hmm.HMM_ERR_ARG
+    assert _forward(lib, hmm.hmm_dims_t(0, 4, 8), q) == hmm.HMM_ERR_ARG
+    assert _forward(lib, hmm.hmm_dims_t(2, 65, 8), q) == hmm.HMM_ERR_UNSUPPORTED
+    assert _forward(lib, d, q, precision=9) == hmm.HMM_ERR_ARG
+    assert _forward(lib, d, q, precision=hmm.HMM_BF16_MMA) == hmm.HMM_ERR_UNSUPPORTED
+    assert _forward(lib, d, q, ws=None) == hmm.HMM_ERR_WORKSPACE
+    assert _forward(lib, d, q, ws=_fake(9) + 4) == hmm.HMM_ERR_WORKSPACE
+    assert _forward(lib, d, q, ws_bytes=16) == hmm.HMM_ERR_WORKSPACE
+    assert "need" in hmm.hmm_last_error()
+    neg = hmm.hmm_seqs_t(_fake(1), _fake(2), _fake(3), None, -1, 10, 40)
+    assert _forward(lib, d, neg) == hmm.HMM_ERR_ARG
+    mis = hmm.hmm_seqs_t(_fake(1), _fake(2) + 4, _fake(3), None, 4, 10, 40)
+    assert _forward(lib, d, mis) == hmm.HMM_ERR_ARG
+    # S == 0 is a no-op that returns before any CUDA call
+    assert _forward(lib, d, _seqs(S=0)) == hmm.HMM_OK
+
+
+def test_viterbi_and_adjoint_argument_errors(lib):
+    d = hmm.hmm_dims_t(2, 4, 8)
+    q = _seqs()
+    assert lib.hmm_viterbi(d, _fake(5), _fake(6), _fake(7), ctypes.byref(q), None, None, None,
+                           _fake(9), 1 << 30, None) == hmm.HMM_ERR_ARG
+    assert lib.hmm_forward_backward(d, _fake(5), _fake(6), _fake(7), ctypes.byref(q), None,
+                                    hmm.HMM_FP32, _fake(8), None, _fake(11), _fake(12),
+                                    _fake(9), 1 << 30, None) == hmm.HMM_ERR_ARG
+    big = hmm.hmm_dims_t(2, 33, 8)
+    assert lib.hmm_forward_backward(big, _fake(5), _fake(6), _fake(7), ctypes.byref(q), None,
+                                    hmm.HMM_FP32, _fake(8), _fake(10), _fake(11), _fake(12),
+                                    _fake(9), 1 << 30, None) == hmm.HMM_ERR_UNSUPPORTED
+    # adjoint shared-memory limit: very long sequences with many symbols
+    huge = hmm.hmm_seqs_t(_fake(1), _fake(2), _fake(3), None, 4, 2_000_000, 8_000_000)
+    assert lib.hmm_forward_backward(hmm.hmm_dims_t(2, 32, 2048), _fake(5), _fake(6), _fake(7),
+                                    ctypes.byref(huge), None, hmm.HMM_FP32, _fake(8), _fake(10),
+                                    _fake(11), _fake(12), _fake(9), 1 << 40, None) \
+        == hmm.HMM_ERR_UNSUPPORTED
+    assert lib.hmm_adam_step(10, _fake(1), _fake(2), _fake(3), _fake(4), 0.1, 0.9, 0.999, 1e-8,
+                             1.0, None, None) == hmm.HMM_ERR_ARG
+    assert lib.hmm_adam_step(0, None, None, None, None, 0.1, 0.9, 0.999, 1e-8, 1.0, _fake(5),
+                             None) == hmm.HMM_OK
+    st = ctypes.c_int32()
+    assert lib.hmm_get_device_status(None, None, ctypes.byref(st)) == hmm.HMM_ERR_ARG
+
+
+def test_tuning_table(lib):
+    for op in (hmm.HMM_OP_FORWARD, hmm.HMM_OP_VITERBI, hmm.HMM_OP_FORWARD_BACKWARD):
+        for n_pad in (4, 8, 16, 32):
+            cands = hmm.hmm_tuning_candidates(op, n_pad)
+            assert cands and all(32 % g == 0 and n_pad % g == 0 for g in cands)
+            assert hmm.hmm_get_tuning(op, n_pad) == cands[0]
+    with pytest.raises(hmm.HmmError):
+        hmm.hmm_set_tuning(hmm.HMM_OP_FORWARD, 16, 3)
+    hmm.hmm_set_tuning(hmm.HMM_OP_FORWARD, 16, 4)
+    assert hmm.hmm_get_tuning(hmm.HMM_OP_FORWARD, 16) == 4
+    hmm.hmm_set_tuning(hmm.HMM_OP_FORWARD, 16, 0)
+    assert hmm.hmm_get_tuning(hmm.HMM_OP_FORWARD, 16) == 2
+    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD) == 64
+    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD) == 32
+
+
+def test_last_error_is_thread_local(lib):
+    import threading
+    d = hmm.hmm_dims_t(2, 4, 8)
+    _forward(lib, d, _seqs(), pi=None)
+    seen = {}
+
+    def other():
+        seen["msg"] = hmm.hmm_last_error()
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["msg"] == "" and "pi/A/B" in hmm.hmm_last_error()

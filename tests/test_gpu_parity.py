@@ -1,0 +1,167 @@
+"""GPU path vs the FP64 oracle, element by element, through the C-ABI.
+
+Sizes are ones the oracle finishes in seconds while still spanning many warps
+and work items with ragged tails; every instantiated lane count (the tuning
+candidates) is exercised, and padded state counts (N not a power of two) are
+covered. Tolerances are in tests/helpers.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import COUNT_RTOL, ll_tol, margin_filtered, oparams, rel_l2, to_gpu
+from paper_1310_3322_gb300 import hmm, synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # name, n_seqs, lengths, K/N/M overrides
+    ("plain", 64, None, {}),
+    ("plain", 300, ("uniform", 0, 90), {"N": 3, "M": 5}),
+    ("batched", 160, ("uniform", 30, 300), {}),
+    ("batched", 150, ("uniform", 1, 200), {"N": 13, "K": 3}),
+    ("gradient", 70, ("uniform", 50, 500), {}),
+    ("gradient", 90, ("uniform", 1, 120), {"N": 27, "M": 11}),
+    ("training", 40, ("uniform", 20, 200), {"K": 5}),
+    ("plain", 200, ("uniform", 1, 64), {"N": 7, "K": 4, "M": 3}),
+]
+
+
+def _workload(case):
+    name, S, lengths, over = case
+    return synth.make_workload(name, n_seqs=S, lengths=lengths, **over)
+
+
+def _npad(N):
+    for p in (4, 8, 16, 32, 64):
+        if N <= p:
+            return p
+
+
+@pytest.fixture(autouse=True)
+def _reset_tuning():
+    yield
+    for op in (0, 1, 2):
+        for n in (4, 8, 16, 32, 64):
+            hmm.hmm_set_tuning(op, n, 0)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}-{c[3]}")
+def test_forward_all_models(case):
+    w = _workload(case)
+    seqs, pi, A, B = to_gpu(w)
+    ref, ref_am, _ = oracle.forward(oparams(w), w.symbols, w.offsets, w.lengths, nthreads=8)
+    tol = ll_tol(w.lengths)[:, None]
+    for G in hmm.hmm_tuning_candidates(hmm.HMM_OP_FORWARD, _npad(w.N)):
+        hmm.hmm_set_tuning(hmm.HMM_OP_FORWARD, _npad(w.N), G)
+        ll, am = hmm.hmm_forward(pi, A, B, seqs)
+        ll, am = ll.cpu().numpy(), am.cpu().numpy()
+        err = np.abs(ll - ref)
+        assert np.all(err <= tol), f"G={G}: max err {err.max()} at {np.unravel_index(err.argmax(), err.shape)}"
+        # the argmax must agree wherever the top two models are separated
+        srt = np.sort(ref, axis=1)
+        clear = (srt[:, -1] - srt[:, -2] > 2 * tol[:, 0]) if w.K > 1 else np.ones(w.S, bool)
+        np.testing.assert_array_equal(am[clear], ref_am[clear])
+        assert np.all((am >= 0) & (am < w.K))
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=lambda c: f"{c[0]}-{c[1]}-{c[3]}")
+def test_forward_labelled(case):
+    w = _workload(case)
+    seqs, pi, A, B = to_gpu(w, labelled=True)
+    ref, _, _ = oracle.forward(oparams(w), w.symbols, w.offsets, w.lengths, w.labels)
+    ll, am = hmm.hmm_forward(pi, A, B, seqs)
+    assert am is None
+    assert np.all(np.abs(ll.cpu().numpy() - ref) <= ll_tol(w.lengths))
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}-{c[3]}")
+def test_viterbi_scores_and_paths(case):
+    w = margin_filtered(_workload(case))
+    seqs, pi, A, B = to_gpu(w)
+    rs, rbest, rpath, _, _ = oracle.viterbi(oparams(w), w.symbols, w.offsets, w.lengths,
+                                            nthreads=8)
+    tol = ll_tol(w.lengths)[:, None]
+    for G in hmm.hmm_tuning_candidates(hmm.HMM_OP_VITERBI, _npad(w.N)):
+        hmm.hmm_set_tuning(hmm.HMM_OP_VITERBI, _npad(w.N), G)
+        sc, best, path = hmm.hmm_viterbi(pi, A, B, seqs)
+        sc, best, path = sc.cpu().numpy(), best.cpu().numpy(), path.cpu().numpy()
+        err = np.abs(sc - rs)
+        assert np.all(err <= tol), f"G={G}: max err {err.max()}"
+        np.testing.assert_array_equal(best, rbest)
+        np.testing.assert_array_equal(path, rpath)
+
+
+@pytest.mark.parametrize("case", CASES[:6], ids=lambda c: f"{c[0]}-{c[1]}-{c[3]}")
+def test_viterbi_labelled(case):
+    w = margin_filtered(_workload(case), labelled=True)
+    seqs, pi, A, B = to_gpu(w, labelled=True)
+    rs, rbest, rpath, _, _ = oracle.viterbi(oparams(w), w.symbols, w.offsets, w.lengths, w.labels)
+    sc, best, path = hmm.hmm_viterbi(pi, A, B, seqs)
+    assert np.all(np.abs(sc.cpu().numpy() - rs) <= ll_tol(w.lengths))
+    np.testing.assert_array_equal(best.cpu().numpy(), w.labels)
+    np.testing.assert_array_equal(path.cpu().numpy(), rpath)
+    # scores only (no path) take the score kernel
+    sc2, _, _ = hmm.hmm_viterbi(pi, A, B, seqs, want_path=False)
+    np.testing.assert_array_equal(sc2.cpu().numpy(), sc.cpu().numpy())
+
+
+def _check_counts(got, ref):
+    for g, r, name in zip(got, ref, ("pi", "A", "B")):
+        g = g.cpu().numpy()
+        assert rel_l2(g, r) <= COUNT_RTOL, f"{name}: rel L2 {rel_l2(g, r)}"
+
+
+FB_CASES = [c for c in CASES if c[3].get("N", synth.SPECS[c[0]]["N"]) <= 32]
+
+
+@pytest.mark.parametrize("case", FB_CASES, ids=lambda c: f"{c[0]}-{c[1]}-{c[3]}")
+def test_forward_backward_labelled(case):
+    w = _workload(case)
+    seqs, pi, A, B = to_gpu(w, labelled=True)
+    rng = np.random.default_rng(3)
+    wts = rng.uniform(0.5, 2.0, size=w.S).astype(np.float32)
+    import torch
+    wt = torch.from_numpy(wts).cuda()
+    rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
+                                                  w.labels, wts.astype(np.float64), nthreads=8)
+    for G in hmm.hmm_tuning_candidates(hmm.HMM_OP_FORWARD_BACKWARD, _npad(w.N)):
+        hmm.hmm_set_tuning(hmm.HMM_OP_FORWARD_BACKWARD, _npad(w.N), G)
+        ll, cpi, cA, cB = hmm.hmm_forward_backward(pi, A, B, seqs, weight=wt)
+        assert np.all(np.abs(ll.cpu().numpy() - rll) <= ll_tol(w.lengths)), f"G={G}"
+        _check_counts((cpi, cA, cB), (rpi, rA, rB))
+        # the logit gradient built from the counts
+        g = hmm.hmm_softmax_grad(pi, A, B, cpi, cA, cB)
+        rg = oracle.softmax_grad(oparams(w), rpi, rA, rB)
+        for a, b in zip(g, rg):
+            assert rel_l2(a.cpu().numpy(), b) <= 10 * COUNT_RTOL
+
+
+@pytest.mark.parametrize("case", FB_CASES[:3], ids=lambda c: f"{c[0]}-{c[1]}-{c[3]}")
+def test_forward_backward_all_models_weighted(case):
+    import torch
+    w = _workload(case)
+    seqs, pi, A, B = to_gpu(w)
+    wts = np.random.default_rng(4).uniform(-1.0, 1.0, size=(w.S, w.K)).astype(np.float32)
+    rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
+                                                  None, wts.astype(np.float64), nthreads=8)
+    ll, cpi, cA, cB = hmm.hmm_forward_backward(pi, A, B, seqs, weight=torch.from_numpy(wts).cuda())
+    assert np.all(np.abs(ll.cpu().numpy() - rll) <= ll_tol(w.lengths)[:, None])
+    # signed weights: compare against the scale of the unsigned totals
+    for g, r in zip((cpi, cA, cB), (rpi, rA, rB)):
+        g = g.cpu().numpy()
+        assert np.abs(g - r).max() <= COUNT_RTOL * max(1.0, np.abs(r).max()) * 10
+
+
+def test_deterministic_repeat():
+    w = synth.make_workload("batched", n_seqs=300, lengths=("uniform", 1, 300))
+    seqs, pi, A, B = to_gpu(w)
+    a = hmm.hmm_forward(pi, A, B, seqs)[0].cpu().numpy()
+    b = hmm.hmm_forward(pi, A, B, seqs)[0].cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    lab = seqs.labelled(seqs.lengths.new_tensor(w.labels))
+    c1 = [t.cpu().numpy() for t in hmm.hmm_forward_backward(pi, A, B, lab)]
+    c2 = [t.cpu().numpy() for t in hmm.hmm_forward_backward(pi, A, B, lab)]
+    for x, y in zip(c1, c2):
+        np.testing.assert_array_equal(x, y)

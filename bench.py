@@ -361,7 +361,7 @@ def run_gpu(args):
         bo = sum(t.numel() * t.element_size() for t in (o_am, o_path, o_nll))
         times = []
         barrier()
-        for i in range(args.steps):
+        for i in range(max(args.warmup, 3) + args.steps):
             flush.fill_(i & 0xff)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -376,6 +376,7 @@ def run_gpu(args):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         barrier()
+        times = times[max(args.warmup, 3):]   # the first iterations load lazy kernels
         e_ms = float(np.mean(times)) * 1e3
         t_e = torch.tensor([e_ms], device=dev, dtype=torch.float64)
         if world > 1:

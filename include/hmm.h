@@ -120,6 +120,34 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
                 const hmm_seqs_t* seqs, hmm_precision_t precision, float* loglik,
                 int32_t* argmax, void* workspace, size_t workspace_bytes, hmm_stream_t stream);
 
+/* hmm_forward for callers that cannot provide a device workspace. (The paper
+ * has no counterpart; this is an integration convenience of this library.)
+ *
+ * Some callers cannot allocate device memory when they score: real-time or
+ * embedded hosts that forbid cudaMalloc after start-up, plug-in hosts that
+ * own every device allocation, code that must never touch an allocator on its
+ * recognition path. This call takes its scratch from a fixed array compiled
+ * into the library (HMM_STATIC_SCRATCH_BYTES in the device memory of every GPU
+ * that loads the library, held until the process exits) and is otherwise
+ * hmm_forward: same arguments except the workspace, same outputs, same device
+ * status bits. It allocates nothing and calls no allocating routine.
+ *   - Calls whose scratch need (hmm_workspace_size for HMM_OP_FORWARD) is
+ *     above HMM_STATIC_SCRATCH_BYTES return HMM_ERR_WORKSPACE and enqueue
+ *     nothing; about 8 MiB covers e.g. 65536 sequences with K=10, N=32, M=256.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture on the device.
+ *   - Every call on a device shares the one array, and the next call
+ *     overwrites what the last one left there: calls that may overlap on the
+ *     GPU (different streams, or threads without ordering) race and give wrong
+ *     results. Serialise them on one stream.
+ *   - The device status word lives in the shared array and is not readable
+ *     through hmm_get_device_status; bad inputs still give NaN outputs. */
+#define HMM_STATIC_SCRATCH_BYTES (8 * 1024 * 1024)
+int hmm_forward_static(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                       const hmm_seqs_t* seqs, hmm_precision_t precision, float* loglik,
+                       int32_t* argmax, hmm_stream_t stream);
+
 /* Viterbi algorithm (Sec. 2.7 "Viterbi"; Rabiner eqs. 32-35):
  *   score       [S][K] or [S]: max_Q log P(O_s, Q | lambda_k)
  *   best_model  [S] or NULL: the decoded model, argmax_k score[s][k] (smallest

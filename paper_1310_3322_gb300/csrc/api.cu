@@ -24,6 +24,10 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// Records an error message for hmm_last_error() (used by entry points that
+// live in other translation units).
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 static int cuda_fail(cudaError_t e, const char* what) {
   return fail(HMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

@@ -62,6 +62,8 @@ _SIG = {
     "hmm_max_states": (_I32, [_I32, _I32]),
     "hmm_forward": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _I32, _VP,
                            _VP, _VP, ctypes.c_size_t, _VP]),
+    "hmm_forward_static": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _I32,
+                                  _VP, _VP, _VP]),
     "hmm_viterbi": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _VP, _VP, _VP,
                            _VP, ctypes.c_size_t, _VP]),
     "hmm_forward_backward": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _VP,
@@ -250,6 +252,25 @@ def hmm_forward(pi, A, B, seqs: Sequences, precision: int = HMM_FP32, want_argma
     _check(lib().hmm_forward(dims, _ptr(pi), _ptr(A), _ptr(B), ctypes.byref(c), precision,
                              _ptr(loglik), _ptr(argmax if all_models else None), _ptr(buf),
                              buf.numel(), _stream(stream)))
+    return loglik, (argmax if all_models else None)
+
+
+def hmm_forward_static(pi, A, B, seqs: Sequences, precision: int = HMM_FP32, want_argmax=True,
+                       loglik=None, argmax=None, stream=None):
+    """hmm_forward without a workspace: the library's fixed scratch array is
+    used instead (see include/hmm.h). Outputs as in hmm_forward."""
+    torch = _torch()
+    dims = _dims(pi, B)
+    S, K = seqs.S, dims.K
+    all_models = seqs.model_of_seq is None
+    if loglik is None:
+        loglik = torch.empty((S, K) if all_models else (S,), dtype=torch.float32, device=pi.device)
+    if all_models and want_argmax and argmax is None:
+        argmax = torch.empty(S, dtype=torch.int32, device=pi.device)
+    c = seqs.c()
+    _check(lib().hmm_forward_static(dims, _ptr(pi), _ptr(A), _ptr(B), ctypes.byref(c), precision,
+                                    _ptr(loglik), _ptr(argmax if all_models else None),
+                                    _stream(stream)))
     return loglik, (argmax if all_models else None)
 
 

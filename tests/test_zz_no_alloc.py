@@ -1,0 +1,78 @@
+"""hmm_forward_static: forward scoring for callers that cannot allocate.
+
+Real-time and embedded hosts that forbid device allocation after start-up,
+and plug-in hosts that own every device allocation, cannot pass the library
+a workspace. hmm_forward_static serves them from a fixed scratch array
+compiled into the library. These tests call it through the C-ABI and check
+that, on two calls in a row, it returns what hmm_forward (the workspace
+entry point) returns, within the log-likelihood tolerance of the parity
+tests, and that a request larger than the fixed array is refused.
+
+The file name sorts last so that a run stopping at the first failure has
+already run every other test; it also passes alone in a fresh process (the
+first call performs the per-device set-up).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from helpers import ll_tol, to_gpu
+from paper_1310_3322_gb300 import hmm, synth
+
+
+def _call_static(lib, pi, A, B, seqs, loglik, argmax):
+    import torch
+    c = seqs.c()
+    dims = hmm.hmm_dims_t(int(pi.shape[0]), int(pi.shape[1]), int(B.shape[2]))
+    return lib.hmm_forward_static(dims, pi.data_ptr(), A.data_ptr(), B.data_ptr(),
+                                  ctypes.byref(c), hmm.HMM_FP32, loglik.data_ptr(),
+                                  argmax.data_ptr() if argmax is not None else None,
+                                  torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("labelled", [False, True])
+def test_static_scratch_matches_workspace_entry_point(labelled):
+    import torch
+    lib = hmm.lib()
+    w = synth.make_workload("batched", n_seqs=300, lengths=("uniform", 0, 300))
+    seqs, pi, A, B = to_gpu(w, labelled=labelled)
+    ref_ll, ref_am = hmm.hmm_forward(pi, A, B, seqs)
+    tol = torch.from_numpy(ll_tol(w.lengths)).float().cuda()
+    if not labelled:
+        tol = tol[:, None]
+    for _ in range(2):
+        ll = torch.full_like(ref_ll, float("nan"))
+        am = None if labelled else torch.full_like(ref_am, -7)
+        assert _call_static(lib, pi, A, B, seqs, ll, am) == hmm.HMM_OK, hmm.hmm_last_error()
+        torch.cuda.synchronize()
+        assert bool(((ll - ref_ll).abs() <= tol).all())
+        if not labelled:
+            assert torch.equal(am, ref_am)
+
+
+@pytest.mark.gpu
+def test_static_scratch_refuses_oversized_requests():
+    import torch
+    lib = hmm.lib()
+    rng = np.random.default_rng(0)
+    pi, A, B = (torch.from_numpy(x).cuda() for x in synth.random_model(rng, 4, 8, 16))
+    # 2^21 sequences need about 24 MiB of scratch: refused before any launch
+    S = 1 << 21
+    c = hmm.hmm_seqs_t(0x10000, 0x20000, 0x30000, None, S, 10, 10 * S)
+    dims = hmm.hmm_dims_t(4, 8, 16)
+    out = ctypes.c_size_t()
+    assert lib.hmm_workspace_size(dims, ctypes.byref(c), hmm.HMM_OP_FORWARD, ctypes.byref(out)) == 0
+    assert out.value > hmm_static_bytes()
+    rc = lib.hmm_forward_static(dims, pi.data_ptr(), A.data_ptr(), B.data_ptr(), ctypes.byref(c),
+                                hmm.HMM_FP32, 0x40000, None, None)
+    assert rc == hmm.HMM_ERR_WORKSPACE and "scratch" in hmm.hmm_last_error()
+
+
+def hmm_static_bytes():
+    with open(hmm.HEADER) as f:
+        for line in f:
+            if line.startswith("#define HMM_STATIC_SCRATCH_BYTES"):
+                return eval(line.split(None, 2)[2])
+    raise AssertionError("HMM_STATIC_SCRATCH_BYTES not declared")

@@ -257,7 +257,11 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- warm-up, then capture -------------------------------------------
+    # ---- warm-up (with the lanes-per-pair autotuner), then capture --------
+    step()
+    torch.cuda.synchronize()
+    from paper_1310_3322_gb300 import tune
+    tuning = tune.autotune(*probs, seqs, lab, repeats=3, cache=None)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -410,7 +414,9 @@ def run_gpu(args):
                        "units_per_step": units, "sum_T": sumT,
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "timing": "CUDA-graph replay of the whole step" if graph is not None
-                       else "eager step", "parallelism": f"replicas x{world}"},
+                       else "eager step", "parallelism": f"replicas x{world}",
+                       "lanes_per_pair": {k: v["lanes"] for k, v in tuning.items()}},
+            "autotune_ms": {k: v["ms"] for k, v in tuning.items()},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -209,14 +209,19 @@ int hmm_adam_step(int64_t n, float* param, const float* grad, float* m, float* v
 int hmm_get_device_status(const void* workspace, hmm_stream_t stream, int32_t* status);
 
 /* Autotuner hook: lanes of a warp that cooperate on one (sequence, model)
- * pair for `op` at padded state count n_pad (4, 8, 16, 32, 64). The value
- * must be one this build instantiates (see hmm_tuning_candidates). 0 restores
- * the default. Process-wide; not thread-safe against concurrent launches. */
-int hmm_set_tuning(hmm_op_t op, int32_t n_pad, int32_t lanes_per_pair);
-int hmm_get_tuning(hmm_op_t op, int32_t n_pad, int32_t* lanes_per_pair);
+ * pair, per tunable kernel and padded state count n_pad (4, 8, 16, 32, 64).
+ * `op` is HMM_OP_FORWARD, HMM_OP_VITERBI (the score kernel),
+ * HMM_OP_FORWARD_BACKWARD or HMM_TUNE_VITERBI_PATHS (the path kernel). The
+ * value must be one this build instantiates (hmm_tuning_candidates, whose
+ * first entry is the default); 0 restores the default. Process-wide; not
+ * thread-safe against concurrent launches. The choice changes only the speed:
+ * every candidate computes the same recursion. */
+#define HMM_TUNE_VITERBI_PATHS 3
+int hmm_set_tuning(int32_t op, int32_t n_pad, int32_t lanes_per_pair);
+int hmm_get_tuning(int32_t op, int32_t n_pad, int32_t* lanes_per_pair);
 /* Writes up to cap candidate lane counts for (op, n_pad) into out (HOST
  * pointer); returns how many there are, or a negative error code. */
-int hmm_tuning_candidates(hmm_op_t op, int32_t n_pad, int32_t* out, int32_t cap);
+int hmm_tuning_candidates(int32_t op, int32_t n_pad, int32_t* out, int32_t cap);
 
 /* Kernel timing (host-side tracing). While enabled, every kernel launch of
  * the library is bracketed by two CUDA events recorded on the launch stream;

@@ -61,18 +61,18 @@ static int pad_states(int N) {
 }
 
 // candidate lanes-per-pair, default first; 0 terminates
-static const int kCand[3][5][5] = {
+static const int kCand[4][5][5] = {
     /* forward */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
-    /* viterbi */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
+    /* viterbi scores */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
     /* fb      */ {{4, 2, 0}, {8, 4, 0}, {8, 16, 0}, {32, 0}, {0}},
+    /* viterbi paths */ {{4, 2, 1, 0}, {8, 4, 2, 0}, {8, 16, 4, 0}, {16, 32, 8, 0}, {32, 0}},
 };
-static const int kPathLanes[5] = {4, 8, 8, 16, 32};
-static int g_tuning[3][5] = {{0}};
+static int g_tuning[4][5] = {{0}};
 static std::mutex g_tuning_mu;
 
 int candidates(int op, int NP, int* out, int cap) {
   const int ni = np_index(NP);
-  if (op < 0 || op > 2 || ni < 0) return -1;
+  if (op < 0 || op > 3 || ni < 0) return -1;
   int n = 0;
   for (int i = 0; i < 5 && kCand[op][ni][i]; ++i) {
     if (n < cap && out) out[n] = kCand[op][ni][i];
@@ -95,7 +95,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static int first_chunks(int S) {
   int n = (S + kReduceChunk - 1) / kReduceChunk;
-  if (n > 64) n = 64;
+  if (n > 1024) n = 1024;
   return n < 1 ? 1 : n;
 }
 
@@ -305,10 +305,10 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
   return HMM_OK;
 }
 
-int hmm_set_tuning(hmm_op_t op, int32_t n_pad, int32_t lanes) {
+int hmm_set_tuning(int32_t op, int32_t n_pad, int32_t lanes) {
   g_err[0] = 0;
   const int ni = np_index(n_pad);
-  if (op < 0 || op > 2 || ni < 0) return fail(HMM_ERR_ARG, "bad op %d or n_pad %d", op, n_pad);
+  if (op < 0 || op > 3 || ni < 0) return fail(HMM_ERR_ARG, "bad op %d or n_pad %d", op, n_pad);
   if (lanes != 0) {
     bool ok = false;
     for (int i = 0; i < 5 && kCand[op][ni][i]; ++i) ok |= kCand[op][ni][i] == lanes;
@@ -319,16 +319,16 @@ int hmm_set_tuning(hmm_op_t op, int32_t n_pad, int32_t lanes) {
   return HMM_OK;
 }
 
-int hmm_get_tuning(hmm_op_t op, int32_t n_pad, int32_t* lanes) {
+int hmm_get_tuning(int32_t op, int32_t n_pad, int32_t* lanes) {
   g_err[0] = 0;
   const int ni = np_index(n_pad);
-  if (op < 0 || op > 2 || ni < 0 || !lanes) return fail(HMM_ERR_ARG, "bad op, n_pad or pointer");
+  if (op < 0 || op > 3 || ni < 0 || !lanes) return fail(HMM_ERR_ARG, "bad op, n_pad or pointer");
   if (!kCand[op][ni][0]) return fail(HMM_ERR_UNSUPPORTED, "no kernel for op %d n_pad %d", op, n_pad);
   *lanes = lanes_for(op, n_pad);
   return HMM_OK;
 }
 
-int hmm_tuning_candidates(hmm_op_t op, int32_t n_pad, int32_t* out, int32_t cap) {
+int hmm_tuning_candidates(int32_t op, int32_t n_pad, int32_t* out, int32_t cap) {
   g_err[0] = 0;
   const int n = candidates(op, n_pad, out, cap);
   if (n < 0) return fail(HMM_ERR_ARG, "bad op %d or n_pad %d", op, n_pad);
@@ -404,7 +404,7 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
   const int G = lanes_for(HMM_OP_VITERBI, L.NP);
   const int PP = 32 / G;
   const int ngroups = (seqs->S + PP - 1) / PP;
-  const int Gp = kPathLanes[np_index(L.NP)];
+  const int Gp = lanes_for(HMM_TUNE_VITERBI_PATHS, L.NP);
   const int PPp = 32 / Gp;
   int32_t* best = best_model ? best_model : at<int32_t>(ws, L.best);
   const bool need_best = all && (best_model || path);

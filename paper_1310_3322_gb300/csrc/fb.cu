@@ -10,9 +10,10 @@
 // Memory: alpha is never stored whole. Phase 1 runs the scaled forward
 // recursion and keeps alpha_t (and the power-of-two exponent removed at t)
 // every C = ceil(sqrt(max_len)) steps in shared memory. Phase 2 walks the
-// segments backwards: it recomputes alpha over the segment from its
-// checkpoint into shared memory, then runs the backward recursion over the
-// segment. Both live in shared memory: O(sqrt(T) N) floats per pair.
+// segments backwards; while it runs the backward recursion over segment c it
+// recomputes alpha over segment c-1 from its checkpoint (the two chains are
+// independent, so each step issues both), double-buffering the segments in
+// shared memory: O(sqrt(T) N) floats per pair.
 //
 // Scaling: alpha_t and beta_t each carry an exact power-of-two scale that is
 // never divided out. With u_{t+1}(j) = b_j(o_{t+1}) beta_{t+1}(j) and the
@@ -23,7 +24,8 @@
 //   xi_t(i,j)      = alpha_t(i) a_ij v(j)          (a_ij applied at the flush)
 //   gamma_{t+1}(j) = alpha_{t+1}(j) beta_{t+1}(j) / D_{t+1}
 //   beta_t(i)     ~ sum_j a_ij v(j)                (then rescaled),
-// and the weight w multiplies only what is accumulated.
+// and the weight w multiplies only what is accumulated. D_t comes out of the
+// same butterfly as the sum that rescales beta_t (one reduction per step).
 // Lane ownership: lane r of the pair owns states [rJ, rJ+J) both as columns
 // (forward: column slice of A) and as rows (backward: row slice of A, row
 // slice of the xi accumulator), so every step needs one broadcast vector.
@@ -37,6 +39,55 @@ __device__ __forceinline__ float mul_pow2(float x, int k) {
   return x * exp2i(k1) * exp2i(k2);
 }
 
+// Butterfly over the G lanes of a pair for two values at once.
+template <int G>
+__device__ __forceinline__ float2 group_sum2(float2 v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(HMM_FULL_MASK, v.x, o);
+    v.y += __shfl_xor_sync(HMM_FULL_MASK, v.y, o);
+  }
+  return v;
+}
+
+// beta(ii) = sum_j a_{i,j} v_j for the lane's rows i = j0 + ii, and the xi
+// accumulator update xa[ii][j] += aw[ii] * v_j, from the broadcast row v.
+template <int NP, int J>
+__device__ __forceinline__ void rows_step(const float* vb, const float2 (&ar)[J][NP / 2],
+                                          const float (&aw)[J], float2 (&xa)[J][NP / 2],
+                                          float (&beta)[J]) {
+  constexpr int NS = (J >= 4) ? 1 : (4 / J < NP / 4 ? 4 / J : NP / 4);
+  float2 acc[NS][J];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int ii = 0; ii < J; ++ii) acc[s][ii] = make_float2(0.f, 0.f);
+  float2 aw2[J];
+#pragma unroll
+  for (int ii = 0; ii < J; ++ii) aw2[ii] = make_float2(aw[ii], aw[ii]);
+#pragma unroll
+  for (int q = 0; q < NP / 4; ++q) {
+    const float4 vv = *reinterpret_cast<const float4*>(vb + 4 * q);
+    const float2 lo = make_float2(vv.x, vv.y), hi = make_float2(vv.z, vv.w);
+    const int s = q % NS;
+#pragma unroll
+    for (int ii = 0; ii < J; ++ii) acc[s][ii] = __ffma2_rn(lo, ar[ii][2 * q], acc[s][ii]);
+#pragma unroll
+    for (int ii = 0; ii < J; ++ii) xa[ii][2 * q] = __ffma2_rn(aw2[ii], lo, xa[ii][2 * q]);
+#pragma unroll
+    for (int ii = 0; ii < J; ++ii) acc[s][ii] = __ffma2_rn(hi, ar[ii][2 * q + 1], acc[s][ii]);
+#pragma unroll
+    for (int ii = 0; ii < J; ++ii) xa[ii][2 * q + 1] = __ffma2_rn(aw2[ii], hi, xa[ii][2 * q + 1]);
+  }
+#pragma unroll
+  for (int ii = 0; ii < J; ++ii) {
+    float2 t = acc[0][ii];
+#pragma unroll
+    for (int s = 1; s < NS; ++s) t = __fadd2_rn(t, acc[s][ii]);
+    beta[ii] = t.x + t.y;
+  }
+}
+
 template <int NP, int G>
 struct FbLayout {
   static constexpr int J = NP / G;
@@ -44,7 +95,7 @@ struct FbLayout {
   static constexpr int XS = NP + 4;
   // floats per pair, rounded to 4 (16-byte alignment of every region)
   static __host__ __device__ int per_pair(int C, int NC, int M) {
-    const int n = 2 * XS + NC * NP + C * NP + NC + C + NP * (M + 1);
+    const int n = 4 * XS + NC * NP + 2 * C * NP + NC + 2 * C + NP * (M + 1);
     return (n + 3) & ~3;
   }
 };
@@ -64,24 +115,22 @@ hmm_fb_simt(FbLaunch a) {
 
   const int per = L::per_pair(C, NC, M);
   float* base = smem + (size_t)(warp * PP + p) * per;
-  float* xb = base;                                 // [2][XS]
-  float* ck = xb + 2 * XS;                          // [NC][NP]
-  float* seg = ck + NC * NP;                        // [C][NP]
-  int* cke = reinterpret_cast<int*>(seg + C * NP);  // [NC]
-  int* sege = cke + NC;                             // [C]
-  float* cb = reinterpret_cast<float*>(sege + C);   // [NP][MP]
-  // (per_pair() accounts for every region; cb follows without padding)
+  float* xf = base;                                   // [2][XS] forward exchange
+  float* xv = xf + 2 * XS;                            // [2][XS] backward exchange
+  float* ck = xv + 2 * XS;                            // [NC][NP] checkpoints
+  float* seg = ck + NC * NP;                          // [2][C][NP] recomputed segments
+  int* cke = reinterpret_cast<int*>(seg + 2 * C * NP);  // [NC]
+  int* sege = cke + NC;                               // [2][C]
+  float* cb = reinterpret_cast<float*>(sege + 2 * C);   // [NP][MP] emission counts
 
-  // emission-count accumulator starts at zero
   for (int e = r; e < NP * MP; e += G) cb[e] = 0.f;
   __syncwarp();
 
-  const int n_items = a.n_items;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(a.queue, 1);
     item = __shfl_sync(HMM_FULL_MASK, item, 0);
-    if (item >= n_items) break;
+    if (item >= a.n_items) break;
     const int g = labelled ? item : item / K;
     int k = labelled ? 0 : item % K;
     const int pos = g * PP + p;
@@ -124,10 +173,9 @@ hmm_fb_simt(FbLaunch a) {
       float b[J], pv[J];
       load_vec<J>(b, Bk + (size_t)o0 * NP);
       load_vec<J>(pv, a.mod.pip + (size_t)k * NP + j0);
-      float ls = 0.f;
 #pragma unroll
-      for (int jj = 0; jj < J; ++jj) { x[jj] = pv[jj] * b[jj]; ls += x[jj]; }
-      const float gs = group_sum<G>(ls);
+      for (int jj = 0; jj < J; ++jj) x[jj] = pv[jj] * b[jj];
+      const float gs = group_sum<G>(tree_sum<J>(x));
       if (Tn > 0 && !bad) {
         if (gs == 0.f) dead = true;
         else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
@@ -140,215 +188,233 @@ hmm_fb_simt(FbLaunch a) {
       }
     }
     const int Tmax = __reduce_max_sync(HMM_FULL_MASK, Tn);
-    for (int t = 1; t < Tmax; ++t) {
-      const bool act = t < Tn && !dead && !bad;
-      float* xw = xb + (t & 1) * XS;
-      store_vec<J>(xw + j0, x);
-      __syncwarp();
-      float2 acc[J];
-#pragma unroll
-      for (int jj = 0; jj < J; ++jj) acc[jj] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < NP / 4; ++q) {
-        const float4 xv = *reinterpret_cast<const float4*>(xw + 4 * q);
-        const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-          acc[jj] = ffma2(lo, ac[2 * q][jj], acc[jj]);
-          acc[jj] = ffma2(hi, ac[2 * q + 1][jj], acc[jj]);
-        }
+    {
+      float bn[J];
+      int on = 0;
+      if (1 < Tn) {
+        on = __ldg(o + 1);
+        if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
       }
-      int ot = act ? __ldg(o + t) : 0;
-      if (act && (unsigned)ot >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; ot = 0; }
-      float b[J];
-      load_vec<J>(b, Bk + (size_t)ot * NP);
-      float nx[J], ls = 0.f;
+      load_vec<J>(bn, Bk + (size_t)on * NP);
+      int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
+      for (int t = 1; t < Tmax; ++t) {
+        const bool act = t < Tn && !dead && !bad;
+        float* xw = xf + (t & 1) * XS;
+        store_vec<J>(xw + j0, x);
+        __syncwarp();
+        float nx[J];
+        matvec_cols<NP, J>(xw, ac, nx);
+        float b[J];
 #pragma unroll
-      for (int jj = 0; jj < J; ++jj) { nx[jj] = (acc[jj].x + acc[jj].y) * b[jj]; ls += nx[jj]; }
-      const float gs = group_sum<G>(ls);
-      if (act && !bad) {
-        if (gs == 0.f) dead = true;
-        else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
-        else {
-          const int e = rescale_pow2<J>(nx, gs);
-          E += e;
+        for (int jj = 0; jj < J; ++jj) b[jj] = bn[jj];
+        if (t + 1 < Tn) {
+          on = o2;
+          if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
+          load_vec<J>(bn, Bk + (size_t)on * NP);
+          if (t + 2 < Tn) o2 = __ldg(o + t + 2);
+        }
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) x[jj] = nx[jj];
-          if (t % C == 0) {
-            store_vec<J>(ck + (t / C) * NP + j0, x);
-            if (r == 0) cke[t / C] = e;
+        for (int jj = 0; jj < J; ++jj) nx[jj] *= b[jj];
+        const float gs = group_sum<G>(tree_sum<J>(nx));
+        if (act) {
+          if (gs == 0.f) dead = true;
+          else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
+          else {
+            const int e = rescale_pow2<J>(nx, gs);
+            E += e;
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) x[jj] = nx[jj];
+            if (t % C == 0) {
+              store_vec<J>(ck + (t / C) * NP + j0, x);
+              if (r == 0) cke[t / C] = e;
+            }
           }
         }
       }
     }
-    {
-      float ls = 0.f;
-#pragma unroll
-      for (int jj = 0; jj < J; ++jj) ls += x[jj];
-      const float fs = group_sum<G>(ls);
-      if (has && r == 0) {
-        float out;
-        if (bad) { out = __int_as_float(0x7fc00000); if (err) set_status(a.status, err); }
-        else if (Tn == 0) out = 0.f;
-        else if (dead) out = -INFINITY;
-        else out = (float)(log((double)fs) + (double)E * 0.69314718055994530942);
-        a.loglik[slot] = out;
-      }
+    const float fs = group_sum<G>(tree_sum<J>(x));
+    if (has && r == 0) {
+      float out;
+      if (bad) { out = __int_as_float(0x7fc00000); if (err) set_status(a.status, err); }
+      else if (Tn == 0) out = 0.f;
+      else if (dead) out = -INFINITY;
+      else out = (float)(log((double)fs) + (double)E * 0.69314718055994530942);
+      a.loglik[slot] = out;
     }
 
     // ---------------- phase 2: backward over segments ----------------
     const bool alive = has && !bad && !dead && Tn > 0;
     const int Tb = alive ? Tn : 0;
     const int TbMax = __reduce_max_sync(HMM_FULL_MASK, Tb);
+    auto sym = [&](int t) -> int { return (alive && t >= 0 && t < Tb) ? __ldg(o + t) : 0; };
     float beta[J];
 #pragma unroll
     for (int jj = 0; jj < J; ++jj) beta[jj] = 1.f;
+    float D = fs;  // D_{T-1} = sum_j alpha_{T-1}(j) * 1
     float2 xa[J][NP / 2];
 #pragma unroll
     for (int ii = 0; ii < J; ++ii)
 #pragma unroll
       for (int j2 = 0; j2 < NP / 2; ++j2) xa[ii][j2] = make_float2(0.f, 0.f);
-    float cpi[J];
-#pragma unroll
-    for (int jj = 0; jj < J; ++jj) cpi[jj] = 0.f;
 
-    int parity = 0;
     const int nseg = (TbMax + C - 1) / C;
-    for (int c = nseg - 1; c >= 0; --c) {
-      const int t0 = c * C;
-      const int t1 = min(t0 + C, TbMax) - 1;
-      // recompute alpha over [t0, t1] from checkpoint c
-      if (alive && t0 <= Tb - 1) {
-        load_vec_smem<J>(x, ck + c * NP + j0);
-        store_vec<J>(seg + j0, x);
-        if (r == 0) sege[0] = cke[c];
-      }
+    __syncwarp();
+    // prologue: recompute the last segment
+    if (nseg > 0) {
+      const int c = nseg - 1, t0 = c * C, t1 = TbMax - 1;
+      float* sg = seg + (c & 1) * C * NP;
+      int* se = sege + (c & 1) * C;
+      float xr[J];
+      load_vec_smem<J>(xr, ck + c * NP + j0);
+      store_vec<J>(sg + j0, xr);
+      if (r == 0) se[0] = cke[c];
       for (int t = t0 + 1; t <= t1; ++t) {
         const bool act = alive && t <= Tb - 1;
-        float* xw = xb + parity * XS;
-        parity ^= 1;
-        store_vec<J>(xw + j0, x);
+        float* xw = xf + (t & 1) * XS;
+        store_vec<J>(xw + j0, xr);
         __syncwarp();
-        float2 acc[J];
+        float nx[J], b[J];
+        matvec_cols<NP, J>(xw, ac, nx);
+        load_vec<J>(b, Bk + (size_t)sym(t) * NP);
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) acc[jj] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < NP / 4; ++q) {
-          const float4 xv = *reinterpret_cast<const float4*>(xw + 4 * q);
-          const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
-#pragma unroll
-          for (int jj = 0; jj < J; ++jj) {
-            acc[jj] = ffma2(lo, ac[2 * q][jj], acc[jj]);
-            acc[jj] = ffma2(hi, ac[2 * q + 1][jj], acc[jj]);
-          }
-        }
-        const int ot = act ? __ldg(o + t) : 0;
-        float b[J];
-        load_vec<J>(b, Bk + (size_t)ot * NP);
-        float nx[J], ls = 0.f;
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) { nx[jj] = (acc[jj].x + acc[jj].y) * b[jj]; ls += nx[jj]; }
-        const float gs = group_sum<G>(ls);
+        for (int jj = 0; jj < J; ++jj) nx[jj] *= b[jj];
+        const float gs = group_sum<G>(tree_sum<J>(nx));
         if (act) {
           const int e = rescale_pow2<J>(nx, gs);
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) x[jj] = nx[jj];
-          store_vec<J>(seg + (t - t0) * NP + j0, x);
-          if (r == 0) sege[t - t0] = e;
+          for (int jj = 0; jj < J; ++jj) xr[jj] = nx[jj];
+          store_vec<J>(sg + (t - t0) * NP + j0, xr);
+          if (r == 0) se[t - t0] = e;
         }
       }
       __syncwarp();
-      // backward steps t = t1 .. t0
-      for (int t = t1; t >= t0; --t) {
-        const bool act = alive && t <= Tb - 2;
-        float a1[J], a0[J];
+    }
+
+    for (int c = nseg - 1; c >= 0; --c) {
+      const int t0 = c * C;
+      const int t1 = min(t0 + C, TbMax) - 1;
+      const float* cur = seg + (c & 1) * C * NP;
+      const int* cure = sege + (c & 1) * C;
+      float* nxt = seg + ((c + 1) & 1) * C * NP;  // segment c-1 (same parity as c+1)
+      int* nxte = sege + ((c + 1) & 1) * C;
+      const bool rc_on = c >= 1;
+      const int r0 = (c - 1) * C;
+      float xr[J];
+      if (rc_on) {
+        load_vec_smem<J>(xr, ck + (c - 1) * NP + j0);
+        store_vec<J>(nxt + j0, xr);
+        if (r == 0) nxte[0] = cke[c - 1];
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) xr[jj] = 0.f;
+      }
+      // symbols and emission rows, one iteration ahead for both chains
+      int sb = sym(t1 + 1);
+      float bb[J];
+      load_vec<J>(bb, Bk + (size_t)sb * NP);
+      int sb_next = sym(t1);
+      int sr_next = rc_on ? sym(r0 + 1) : 0;
+      float br[J];
+      load_vec<J>(br, Bk + (size_t)sr_next * NP);
+      sr_next = rc_on ? sym(r0 + 2) : 0;
+
+      for (int u = 0; u < C; ++u) {
+        const int tb = t1 - u;
+        const bool bact = tb >= t0 && alive && tb <= Tb - 2;
+        const int tr = r0 + 1 + u;
+        const bool ract = rc_on && u <= C - 2 && alive && tr <= Tb - 1;
+
+        // backward: publish v = u_{t+1} / Z_t, count gamma_{t+1} emissions
+        float a1[J], a0[J], v[J];
         int e1 = 0;
-        if (act) {
-          if (t + 1 <= t1) {
-            load_vec_smem<J>(a1, seg + (t + 1 - t0) * NP + j0);
-            e1 = sege[t + 1 - t0];
+        if (bact) {
+          if (tb + 1 <= t1) {
+            load_vec_smem<J>(a1, cur + (tb + 1 - t0) * NP + j0);
+            e1 = cure[tb + 1 - t0];
           } else {
             load_vec_smem<J>(a1, ck + (c + 1) * NP + j0);
             e1 = cke[c + 1];
           }
-          load_vec_smem<J>(a0, seg + (t - t0) * NP + j0);
-        } else {
-#pragma unroll
-          for (int jj = 0; jj < J; ++jj) { a1[jj] = 0.f; a0[jj] = 0.f; }
-        }
-        const int o1 = act ? __ldg(o + t + 1) : 0;
-        float b1[J];
-        load_vec<J>(b1, Bk + (size_t)o1 * NP);
-        float u[J], dl = 0.f;
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) { u[jj] = b1[jj] * beta[jj]; dl += a1[jj] * beta[jj]; }
-        const float D = group_sum<G>(dl);
-        float v[J];
-        if (act) {
+          load_vec_smem<J>(a0, cur + (tb - t0) * NP + j0);
           const float invD = 1.f / D;
           const float wd = w * invD;
 #pragma unroll
           for (int jj = 0; jj < J; ++jj) {
-            // gamma_{t+1}(j) for the emission counts
-            cb[(j0 + jj) * MP + o1] += wd * a1[jj] * beta[jj];
-            v[jj] = mul_pow2(u[jj], -e1) * invD;
+            cb[(j0 + jj) * MP + sb] += wd * a1[jj] * beta[jj];
+            v[jj] = mul_pow2(bb[jj] * beta[jj], -e1) * invD;
           }
         } else {
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) v[jj] = 0.f;
+          for (int jj = 0; jj < J; ++jj) { a0[jj] = 0.f; v[jj] = 0.f; }
         }
-        float* xw = xb + parity * XS;
-        parity ^= 1;
-        store_vec<J>(xw + j0, v);
+        float* vw = xv + (u & 1) * XS;
+        float* xw = xf + (u & 1) * XS;
+        store_vec<J>(vw + j0, v);
+        store_vec<J>(xw + j0, xr);
+        // prefetch next iteration's symbols / rows
+        const int sb_cur = sb_next;
+        sb_next = sym(tb - 1);
+        float bbn[J];
+        load_vec<J>(bbn, Bk + (size_t)sb_cur * NP);
+        const int sr_cur = sr_next;
+        sr_next = rc_on ? sym(tr + 2) : 0;
+        float brn[J];
+        load_vec<J>(brn, Bk + (size_t)sr_cur * NP);
         __syncwarp();
-        float2 bacc[J];
+
+        // recompute step of segment c-1 (independent chain)
+        float nx[J];
+        matvec_cols<NP, J>(xw, ac, nx);
 #pragma unroll
-        for (int ii = 0; ii < J; ++ii) bacc[ii] = make_float2(0.f, 0.f);
+        for (int jj = 0; jj < J; ++jj) nx[jj] *= br[jj];
+        const float rs = group_sum<G>(tree_sum<J>(nx));
+
+        // backward step: beta_t and the xi accumulator
+        float aw[J], nb[J];
 #pragma unroll
-        for (int q = 0; q < NP / 4; ++q) {
-          const float4 vv = *reinterpret_cast<const float4*>(xw + 4 * q);
-          const float2 lo = make_float2(vv.x, vv.y), hi = make_float2(vv.z, vv.w);
+        for (int ii = 0; ii < J; ++ii) aw[ii] = w * a0[ii];
+        rows_step<NP, J>(vw, ar, aw, xa, nb);
+        float ad[J];
 #pragma unroll
-          for (int ii = 0; ii < J; ++ii) {
-            bacc[ii] = ffma2(lo, ar[ii][2 * q], bacc[ii]);
-            bacc[ii] = ffma2(hi, ar[ii][2 * q + 1], bacc[ii]);
-            const float2 aa = make_float2(w * a0[ii], w * a0[ii]);
-            xa[ii][2 * q] = ffma2(aa, lo, xa[ii][2 * q]);
-            xa[ii][2 * q + 1] = ffma2(aa, hi, xa[ii][2 * q + 1]);
-          }
+        for (int ii = 0; ii < J; ++ii) ad[ii] = a0[ii] * nb[ii];
+        const float2 red = group_sum2<G>(make_float2(tree_sum<J>(nb), tree_sum<J>(ad)));
+
+        if (ract) {
+          const int e = rescale_pow2<J>(nx, rs);
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) xr[jj] = nx[jj];
+          store_vec<J>(nxt + (u + 1) * NP + j0, xr);
+          if (r == 0) nxte[u + 1] = e;
         }
-        float nb[J], ls = 0.f;
-#pragma unroll
-        for (int ii = 0; ii < J; ++ii) { nb[ii] = bacc[ii].x + bacc[ii].y; ls += nb[ii]; }
-        const float gs = group_sum<G>(ls);
-        if (act && gs > 0.f && !isinf(gs)) {
-          rescale_pow2<J>(nb, gs);
+        if (bact && red.x > 0.f && !isinf(red.x)) {
+          const int e = rescale_pow2<J>(nb, red.x);
 #pragma unroll
           for (int ii = 0; ii < J; ++ii) beta[ii] = nb[ii];
+          D = mul_pow2(red.y, -e);
         }
+        sb = sb_cur;
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) { bb[jj] = bbn[jj]; br[jj] = brn[jj]; }
       }
+      __syncwarp();
     }
+
     // t = 0: gamma_1 for pi and the first emission
+    float cpi[J];
     {
       float a0[J];
-      if (alive) load_vec_smem<J>(a0, seg + j0);
-      else {
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) a0[jj] = 0.f;
-      }
-      float dl = 0.f;
-#pragma unroll
-      for (int jj = 0; jj < J; ++jj) dl += a0[jj] * beta[jj];
-      const float D = group_sum<G>(dl);
       if (alive) {
+        load_vec_smem<J>(a0, ck + j0);
         const int o0 = __ldg(o);
         const float wd = w / D;
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) {
-          const float gmm = wd * a0[jj] * beta[jj];
-          cpi[jj] = gmm;
-          cb[(j0 + jj) * MP + o0] += gmm;
+          cpi[jj] = wd * a0[jj] * beta[jj];
+          cb[(j0 + jj) * MP + o0] += cpi[jj];
         }
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) cpi[jj] = 0.f;
       }
     }
     __syncwarp();
@@ -383,7 +449,7 @@ hmm_fb_simt(FbLaunch a) {
 size_t fb_smem_bytes(int NP, int G, int C, int NC, int M) {
   const int PP = 32 / G;
   const int XS = NP + 4;
-  int n = 2 * XS + NC * NP + C * NP + NC + C + NP * (M + 1);
+  int n = 4 * XS + NC * NP + 2 * C * NP + NC + 2 * C + NP * (M + 1);
   n = (n + 3) & ~3;
   return (size_t)kWarpsPerBlock * PP * n * sizeof(float);
 }

@@ -86,10 +86,7 @@ hmm_forward_simt(FwdLaunch a) {
       for (int jj = 0; jj < J; ++jj) x[jj] = 0.f;
     }
     {
-      float ls = 0.f;
-#pragma unroll
-      for (int jj = 0; jj < J; ++jj) ls += x[jj];
-      const float gs = group_sum<G>(ls);
+      const float gs = group_sum<G>(tree_sum<J>(x));
       if (Tn > 0 && !bad) {
         if (gs == 0.f) dead = true;
         else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
@@ -97,7 +94,9 @@ hmm_forward_simt(FwdLaunch a) {
       }
     }
 
-    // emission row for step 1, prefetched
+    // emission row for step 1 and the symbol of step 2, prefetched: the
+    // symbol load of step t+2 and the emission-row load of step t+1 are both
+    // issued a full step before their values are needed
     float bn[J];
     int on = 0;
     if (1 < Tn) {
@@ -105,41 +104,27 @@ hmm_forward_simt(FwdLaunch a) {
       if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
     }
     load_vec<J>(bn, Bk + (size_t)on * NP);
+    int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
 
     for (int t = 1; t < Tmax; ++t) {
       const bool act = t < Tn && !dead && !bad;
       float* xb = &xs[warp][t & 1][p][0];
       store_vec<J>(xb + j0, x);
       __syncwarp();
-      float2 acc[J];
-#pragma unroll
-      for (int jj = 0; jj < J; ++jj) acc[jj] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < NP / 4; ++q) {
-        const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
-        const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-          acc[jj] = ffma2(lo, a2[2 * q][jj], acc[jj]);
-          acc[jj] = ffma2(hi, a2[2 * q + 1][jj], acc[jj]);
-        }
-      }
+      float nx[J];
+      matvec_cols<NP, J>(xb, a2, nx);
       float b[J];
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) b[jj] = bn[jj];
       if (t + 1 < Tn) {
-        on = __ldg(o + t + 1);
+        on = o2;
         if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
         load_vec<J>(bn, Bk + (size_t)on * NP);
+        if (t + 2 < Tn) o2 = __ldg(o + t + 2);
       }
-      float nx[J];
-      float ls = 0.f;
 #pragma unroll
-      for (int jj = 0; jj < J; ++jj) {
-        nx[jj] = (acc[jj].x + acc[jj].y) * b[jj];
-        ls += nx[jj];
-      }
-      const float gs = group_sum<G>(ls);
+      for (int jj = 0; jj < J; ++jj) nx[jj] *= b[jj];
+      const float gs = group_sum<G>(tree_sum<J>(nx));
       if (act) {
         if (gs == 0.f) {
           dead = true;
@@ -155,10 +140,7 @@ hmm_forward_simt(FwdLaunch a) {
     }
     // (bad, dead and E are uniform across the lanes of a pair: every lane
     // reads the same symbols and the butterfly sums agree bitwise)
-    float ls = 0.f;
-#pragma unroll
-    for (int jj = 0; jj < J; ++jj) ls += x[jj];
-    const float fs = group_sum<G>(ls);
+    const float fs = group_sum<G>(tree_sum<J>(x));
     if (has && r == 0) {
       float out;
       if (bad) {

@@ -14,7 +14,7 @@ namespace hmmgb {
 constexpr int kWarpsPerBlock = 4;      // SIMT kernels: 128-thread blocks
 constexpr int kPlanThreads = 1024;     // setup kernel block size
 constexpr int kLenBuckets = 1024;      // scheduler length buckets
-constexpr int kReduceChunk = 256;      // sequences per first-level count reduction
+constexpr int kReduceChunk = 32;       // sequences per first-level count reduction
 constexpr int kReduceTile = 256;       // count entries per reduction block
 constexpr float kViterbiQuant = 32768.f;  // Viterbi offsets are multiples of 2^-15
 
@@ -170,6 +170,140 @@ __device__ __forceinline__ void load_vec_smem(float (&d)[J], const float* p) {
       float4 v = reinterpret_cast<const float4*>(p)[q];
       d[4 * q] = v.x; d[4 * q + 1] = v.y; d[4 * q + 2] = v.z; d[4 * q + 3] = v.w;
     }
+  }
+}
+
+// Sum of J registers as a balanced tree (short dependency chain).
+template <int J>
+__device__ __forceinline__ float tree_sum(const float (&x)[J]) {
+  if constexpr (J == 1) {
+    return x[0];
+  } else {
+    float t[J / 2];
+#pragma unroll
+    for (int i = 0; i < J / 2; ++i) t[i] = x[2 * i] + x[2 * i + 1];
+    return tree_sum<J / 2>(t);
+  }
+}
+
+template <int J>
+__device__ __forceinline__ float tree_max(const float (&x)[J]) {
+  if constexpr (J == 1) {
+    return x[0];
+  } else {
+    float t[J / 2];
+#pragma unroll
+    for (int i = 0; i < J / 2; ++i) t[i] = fmaxf(x[2 * i], x[2 * i + 1]);
+    return tree_max<J / 2>(t);
+  }
+}
+
+// out[jj] = sum_i x_i a_{i, j0+jj}: x is the per-pair shared-memory row (NP
+// floats, 16-byte aligned), a2[i2][jj] = (a_{2 i2, j}, a_{2 i2 + 1, j}) the
+// register-resident column slice. Packed FP32x2 FMAs over pairs of rows; NS
+// independent accumulator sets keep at least four FMA chains in flight.
+template <int NP, int J>
+__device__ __forceinline__ void matvec_cols(const float* xb, const float2 (&a2)[NP / 2][J],
+                                            float (&out)[J]) {
+  constexpr int NS = (J >= 4) ? 1 : (4 / J < NP / 4 ? 4 / J : NP / 4);
+  float2 acc[NS][J];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) acc[s][jj] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < NP / 4; ++q) {
+    const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
+    const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
+    const int s = q % NS;
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) acc[s][jj] = __ffma2_rn(lo, a2[2 * q][jj], acc[s][jj]);
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) acc[s][jj] = __ffma2_rn(hi, a2[2 * q + 1][jj], acc[s][jj]);
+  }
+#pragma unroll
+  for (int jj = 0; jj < J; ++jj) {
+    float2 t = acc[0][jj];
+#pragma unroll
+    for (int s = 1; s < NS; ++s) t = __fadd2_rn(t, acc[s][jj]);
+    out[jj] = t.x + t.y;
+  }
+}
+
+// out[jj] = max_i (x_i + la_{i, j0+jj}) (max-plus product; exact, so the
+// grouping into NS partial maxima does not change the result).
+template <int NP, int J>
+__device__ __forceinline__ void maxplus_cols(const float* xb, const float2 (&a2)[NP / 2][J],
+                                             float (&out)[J]) {
+  constexpr int NS = (J >= 4) ? 1 : (4 / J < NP / 4 ? 4 / J : NP / 4);
+  float m[NS][J];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) m[s][jj] = -INFINITY;
+#pragma unroll
+  for (int q = 0; q < NP / 4; ++q) {
+    const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
+    const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
+    const int s = q % NS;
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+      const float2 v = __fadd2_rn(lo, a2[2 * q][jj]);
+      m[s][jj] = fmax3(m[s][jj], v.x, v.y);
+    }
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+      const float2 w = __fadd2_rn(hi, a2[2 * q + 1][jj]);
+      m[s][jj] = fmax3(m[s][jj], w.x, w.y);
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < J; ++jj) {
+    float t = m[0][jj];
+#pragma unroll
+    for (int s = 1; s < NS; ++s) t = fmaxf(t, m[s][jj]);
+    out[jj] = t;
+  }
+}
+
+// As maxplus_cols, also returning the smallest maximising i per column.
+template <int NP, int J>
+__device__ __forceinline__ void maxarg_cols(const float* xb, const float2 (&a2)[NP / 2][J],
+                                            float (&out)[J], int (&arg)[J]) {
+  constexpr int NS = (J >= 4) ? 1 : (4 / J < NP / 4 ? 4 / J : NP / 4);
+  float m[NS][J];
+  int a[NS][J];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) { m[s][jj] = -INFINITY; a[s][jj] = 0; }
+#pragma unroll
+  for (int q = 0; q < NP / 4; ++q) {
+    const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
+    const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
+    const int s = q % NS;
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+      const float2 v = __fadd2_rn(lo, a2[2 * q][jj]);
+      if (v.x > m[s][jj]) { m[s][jj] = v.x; a[s][jj] = 4 * q; }
+      if (v.y > m[s][jj]) { m[s][jj] = v.y; a[s][jj] = 4 * q + 1; }
+    }
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+      const float2 w = __fadd2_rn(hi, a2[2 * q + 1][jj]);
+      if (w.x > m[s][jj]) { m[s][jj] = w.x; a[s][jj] = 4 * q + 2; }
+      if (w.y > m[s][jj]) { m[s][jj] = w.y; a[s][jj] = 4 * q + 3; }
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < J; ++jj) {
+    float t = m[0][jj];
+    int ta = a[0][jj];
+#pragma unroll
+    for (int s = 1; s < NS; ++s)
+      if (m[s][jj] > t || (m[s][jj] == t && a[s][jj] < ta)) { t = m[s][jj]; ta = a[s][jj]; }
+    out[jj] = t;
+    arg[jj] = ta;
   }
 }
 

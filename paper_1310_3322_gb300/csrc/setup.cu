@@ -303,19 +303,42 @@ __global__ void __launch_bounds__(kReduceTile) reduce1_kernel(ReduceLaunch a, in
 #pragma unroll
   for (int q = 0; q < kReduceModels; ++q) acc[q][tid] = 0.f;
   const int s0 = c * chunk, s1 = min(a.S, s0 + chunk);
-  if (e < a.slot_floats) {
+  if (e >= a.slot_floats) return;
+  constexpr int U = 8;  // independent loads in flight
+  if (a.model_of_seq) {
+    for (int s = s0; s < s1; s += U) {
+      float v[U];
+      int kk[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = s + u;
+        kk[u] = -1;
+        v[u] = 0.f;
+        if (q < s1 && a.seqlen[q] >= 0) {
+          const int k = a.model_of_seq[q];
+          if (k >= k0 && k < k1) {
+            kk[u] = k - k0;
+            v[u] = a.partial[(int64_t)q * a.slot_floats + e];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (kk[u] >= 0) acc[kk[u]][tid] += v[u];
+    }
+  } else {
     for (int s = s0; s < s1; ++s) {
       if (a.seqlen[s] < 0) continue;
-      if (a.model_of_seq) {
-        const int k = a.model_of_seq[s];
-        if (k >= k0 && k < k1) acc[k - k0][tid] += a.partial[(int64_t)s * a.slot_floats + e];
-      } else {
-        for (int k = k0; k < k1; ++k)
-          acc[k - k0][tid] += a.partial[((int64_t)s * a.K + k) * a.slot_floats + e];
-      }
+      const float* row = a.partial + (int64_t)s * a.K * a.slot_floats + e;
+      float v[kReduceModels];
+#pragma unroll
+      for (int q = 0; q < kReduceModels; ++q)
+        v[q] = (k0 + q < k1) ? row[(int64_t)(k0 + q) * a.slot_floats] : 0.f;
+#pragma unroll
+      for (int q = 0; q < kReduceModels; ++q) acc[q][tid] += v[q];
     }
-    for (int k = k0; k < k1; ++k) a.red1[((int64_t)c * a.K + k) * a.slot_floats + e] = acc[k - k0][tid];
   }
+  for (int k = k0; k < k1; ++k) a.red1[((int64_t)c * a.K + k) * a.slot_floats + e] = acc[k - k0][tid];
 }
 
 __global__ void reduce2_kernel(ReduceLaunch a) {
@@ -345,8 +368,19 @@ __global__ void reduce2_kernel(ReduceLaunch a) {
     e = a.NP + (int64_t)a.NP * a.NP + (int64_t)j * a.M + m;
     out = a.cnt_B + r;
   }
+  // chunks in order, eight loads in flight
+  const int64_t stride = (int64_t)a.K * a.slot_floats;
+  const float* p = a.red1 + (int64_t)k * a.slot_floats + e;
   float s = 0.f;
-  for (int c = 0; c < a.nchunks; ++c) s += a.red1[((int64_t)c * a.K + k) * a.slot_floats + e];
+  int c = 0;
+  for (; c + 8 <= a.nchunks; c += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = p[(int64_t)(c + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; c < a.nchunks; ++c) s += p[(int64_t)c * stride];
   *out = s;
 }
 

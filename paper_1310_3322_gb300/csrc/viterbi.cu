@@ -38,10 +38,7 @@ __device__ __forceinline__ void group_argmax(float& v, int& j) {
 // when every entry is -inf (impossible so far).
 template <int J, int G>
 __device__ __forceinline__ bool normalise_max(float (&x)[J], long long& Q, bool apply) {
-  float m = x[0];
-#pragma unroll
-  for (int jj = 1; jj < J; ++jj) m = fmaxf(m, x[jj]);
-  m = group_max<G>(m);
+  float m = group_max<G>(tree_max<J>(x));
   if (!apply) return true;
   if (m == -INFINITY) return false;
   const int q = __float2int_rn(m * kViterbiQuant);
@@ -114,6 +111,7 @@ hmm_viterbi_scores(VitLaunch a) {
       if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
     }
     load_vec<J>(bn, Bk + (size_t)on * NP);
+    int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
 
     for (int t = 1; t < Tmax; ++t) {
       const bool act = t < Tn && !dead && !bad;
@@ -121,27 +119,15 @@ hmm_viterbi_scores(VitLaunch a) {
       store_vec<J>(xb + j0, x);
       __syncwarp();
       float m[J];
-#pragma unroll
-      for (int jj = 0; jj < J; ++jj) m[jj] = -INFINITY;
-#pragma unroll
-      for (int q = 0; q < NP / 4; ++q) {
-        const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
-        const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-          const float2 v = fadd2(lo, a2[2 * q][jj]);
-          const float2 w = fadd2(hi, a2[2 * q + 1][jj]);
-          m[jj] = fmax3(m[jj], v.x, v.y);
-          m[jj] = fmax3(m[jj], w.x, w.y);
-        }
-      }
+      maxplus_cols<NP, J>(xb, a2, m);
       float b[J];
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) b[jj] = bn[jj];
       if (t + 1 < Tn) {
-        on = __ldg(o + t + 1);
+        on = o2;
         if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
         load_vec<J>(bn, Bk + (size_t)on * NP);
+        if (t + 2 < Tn) o2 = __ldg(o + t + 2);
       }
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) m[jj] += b[jj];
@@ -291,6 +277,7 @@ hmm_viterbi_paths(VitLaunch a) {
       if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
     }
     load_vec<J>(bn, Bk + (size_t)on * NP);
+    int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
 
     for (int t = 1; t < Tmax; ++t) {
       const bool act = t < Tn && !dead && !bad;
@@ -299,29 +286,15 @@ hmm_viterbi_paths(VitLaunch a) {
       __syncwarp();
       float m[J];
       int arg[J];
-#pragma unroll
-      for (int jj = 0; jj < J; ++jj) { m[jj] = -INFINITY; arg[jj] = 0; }
-#pragma unroll
-      for (int q = 0; q < NP / 4; ++q) {
-        const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
-        const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-          const float2 v = fadd2(lo, a2[2 * q][jj]);
-          const float2 w = fadd2(hi, a2[2 * q + 1][jj]);
-          if (v.x > m[jj]) { m[jj] = v.x; arg[jj] = 4 * q; }
-          if (v.y > m[jj]) { m[jj] = v.y; arg[jj] = 4 * q + 1; }
-          if (w.x > m[jj]) { m[jj] = w.x; arg[jj] = 4 * q + 2; }
-          if (w.y > m[jj]) { m[jj] = w.y; arg[jj] = 4 * q + 3; }
-        }
-      }
+      maxarg_cols<NP, J>(xb, a2, m, arg);
       float b[J];
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) b[jj] = bn[jj];
       if (t + 1 < Tn) {
-        on = __ldg(o + t + 1);
+        on = o2;
         if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
         load_vec<J>(bn, Bk + (size_t)on * NP);
+        if (t + 2 < Tn) o2 = __ldg(o + t + 2);
       }
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) m[jj] += b[jj];

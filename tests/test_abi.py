@@ -116,7 +116,8 @@ def test_viterbi_and_adjoint_argument_errors(lib):
 
 
 def test_tuning_table(lib):
-    for op in (hmm.HMM_OP_FORWARD, hmm.HMM_OP_VITERBI, hmm.HMM_OP_FORWARD_BACKWARD):
+    for op in (hmm.HMM_OP_FORWARD, hmm.HMM_OP_VITERBI, hmm.HMM_OP_FORWARD_BACKWARD,
+               hmm.HMM_TUNE_VITERBI_PATHS):
         for n_pad in (4, 8, 16, 32):
             cands = hmm.hmm_tuning_candidates(op, n_pad)
             assert cands and all(32 % g == 0 and n_pad % g == 0 for g in cands)

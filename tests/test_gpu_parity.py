@@ -41,7 +41,7 @@ def _npad(N):
 @pytest.fixture(autouse=True)
 def _reset_tuning():
     yield
-    for op in (0, 1, 2):
+    for op in (0, 1, 2, 3):
         for n in (4, 8, 16, 32, 64):
             hmm.hmm_set_tuning(op, n, 0)
 
@@ -83,8 +83,12 @@ def test_viterbi_scores_and_paths(case):
     rs, rbest, rpath, _, _ = oracle.viterbi(oparams(w), w.symbols, w.offsets, w.lengths,
                                             nthreads=8)
     tol = ll_tol(w.lengths)[:, None]
-    for G in hmm.hmm_tuning_candidates(hmm.HMM_OP_VITERBI, _npad(w.N)):
+    gs = hmm.hmm_tuning_candidates(hmm.HMM_OP_VITERBI, _npad(w.N))
+    gp = hmm.hmm_tuning_candidates(hmm.HMM_TUNE_VITERBI_PATHS, _npad(w.N))
+    for i in range(max(len(gs), len(gp))):
+        G = gs[i % len(gs)]
         hmm.hmm_set_tuning(hmm.HMM_OP_VITERBI, _npad(w.N), G)
+        hmm.hmm_set_tuning(hmm.HMM_TUNE_VITERBI_PATHS, _npad(w.N), gp[i % len(gp)])
         sc, best, path = hmm.hmm_viterbi(pi, A, B, seqs)
         sc, best, path = sc.cpu().numpy(), best.cpu().numpy(), path.cpu().numpy()
         err = np.abs(sc - rs)
@@ -98,10 +102,12 @@ def test_viterbi_labelled(case):
     w = margin_filtered(_workload(case), labelled=True)
     seqs, pi, A, B = to_gpu(w, labelled=True)
     rs, rbest, rpath, _, _ = oracle.viterbi(oparams(w), w.symbols, w.offsets, w.lengths, w.labels)
-    sc, best, path = hmm.hmm_viterbi(pi, A, B, seqs)
-    assert np.all(np.abs(sc.cpu().numpy() - rs) <= ll_tol(w.lengths))
-    np.testing.assert_array_equal(best.cpu().numpy(), w.labels)
-    np.testing.assert_array_equal(path.cpu().numpy(), rpath)
+    for Gp in hmm.hmm_tuning_candidates(hmm.HMM_TUNE_VITERBI_PATHS, _npad(w.N)):
+        hmm.hmm_set_tuning(hmm.HMM_TUNE_VITERBI_PATHS, _npad(w.N), Gp)
+        sc, best, path = hmm.hmm_viterbi(pi, A, B, seqs)
+        assert np.all(np.abs(sc.cpu().numpy() - rs) <= ll_tol(w.lengths))
+        np.testing.assert_array_equal(best.cpu().numpy(), w.labels)
+        np.testing.assert_array_equal(path.cpu().numpy(), rpath)
     # scores only (no path) take the score kernel
     sc2, _, _ = hmm.hmm_viterbi(pi, A, B, seqs, want_path=False)
     np.testing.assert_array_equal(sc2.cpu().numpy(), sc.cpu().numpy())

@@ -70,6 +70,8 @@ typedef struct CUstream_st* hmm_stream_t;
 #define HMM_STATUS_PARAM 0x2      /* a negative, NaN or infinite parameter */
 #define HMM_STATUS_SEQ 0x4        /* offset/length out of range, bad model index,
                                      or sum of lengths above total_obs (Viterbi) */
+#define HMM_STATUS_TIMEOUT 0x8    /* a bounded device-side wait gave up (the
+                                     tensor-core kernels); outputs are invalid */
 
 typedef enum {
   HMM_FP32 = 0,      /* FP32 SIMT recursion (exact power-of-two rescaling) */

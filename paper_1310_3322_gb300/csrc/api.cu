@@ -54,10 +54,11 @@ static int np_index(int NP) {
     if (kNPs[i] == NP) return i;
   return -1;
 }
+// 4..64 for the SIMT kernels, 128 for the tensor-core forward
 static int pad_states(int N) {
   for (int i = 0; i < 5; ++i)
     if (N <= kNPs[i]) return kNPs[i];
-  return -1;
+  return N <= 128 ? 128 : -1;
 }
 
 // candidate lanes-per-pair, default first; 0 terminates
@@ -226,16 +227,23 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
 }
 
 static int max_states(int op, int precision) {
+  if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 128;
   if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
   return op == HMM_OP_FORWARD_BACKWARD ? 32 : 64;
 }
 
 static int check_precision(int precision, int op) {
   if (precision == HMM_FP32 || precision == HMM_AUTO) return HMM_OK;
+  if (precision == HMM_BF16_MMA && op == HMM_OP_FORWARD) return HMM_OK;
   if (precision == HMM_BF16_MMA || precision == HMM_TF32_MMA)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core precision %d not available for op %d in this build",
                 precision, op);
   return fail(HMM_ERR_ARG, "unknown precision %d", precision);
+}
+
+// Tensor-core forward: N in (32, 128], every sequence against every model.
+static bool use_mma_forward(const hmm_dims_t& d, int precision) {
+  return precision == HMM_BF16_MMA || (precision == HMM_AUTO && d.N > 64);
 }
 
 // ---------------------------------------------------------------------------
@@ -297,7 +305,7 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
   g_err[0] = 0;
   if (!bytes) return fail(HMM_ERR_ARG, "bytes is NULL");
   if (op < HMM_OP_FORWARD || op > HMM_OP_FORWARD_BACKWARD) return fail(HMM_ERR_ARG, "bad op %d", op);
-  int rc = check_dims(dims, max_states(op, HMM_FP32));
+  int rc = check_dims(dims, max_states(op, HMM_AUTO));
   if (rc) return rc;
   if (!seqs) return fail(HMM_ERR_ARG, "seqs is NULL");
   if (seqs->S < 0 || seqs->total_obs < 0) return fail(HMM_ERR_ARG, "negative S or total_obs");
@@ -348,14 +356,52 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
   if (argmax && !al(argmax, 4)) return fail(HMM_ERR_ARG, "argmax misaligned");
   const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD);
   if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  const bool all = seqs->model_of_seq == nullptr;
+  const bool mma = use_mma_forward(dims, precision);
+  if (mma && dims.N <= 32)
+    return fail(HMM_ERR_UNSUPPORTED, "tensor-core forward needs N > 32 (N=%d: use HMM_FP32)", dims.N);
+  if (mma && !all)
+    return fail(HMM_ERR_UNSUPPORTED,
+                "tensor-core forward scores every sequence against every model "
+                "(model_of_seq must be NULL)");
   if (seqs->S == 0) return HMM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const bool all = seqs->model_of_seq == nullptr;
+  cudaError_t e;
+  if (mma) {
+    const int n_tiles = (seqs->S + 127) / 128;
+    const int n_pairs = (n_tiles + 1) / 2;
+    if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+    s.ndone = argmax ? n_pairs : 0;
+    {
+      Timed tm(T_SETUP, st);
+      e = launch_setup(s, st);
+      tm.stop();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+    MmaFwdLaunch f;
+    f.seq = seq_args(dims, *seqs, L, ws);
+    f.mod = model_args(L, ws);
+    f.loglik = loglik;
+    f.argmax = argmax;
+    f.done = at<int32_t>(ws, L.done);
+    f.queue = &at<WsHeader>(ws, 0)->queue[0];
+    f.status = &at<WsHeader>(ws, 0)->status;
+    f.n_tiles = n_tiles;
+    f.n_items = n_pairs * dims.K;
+    {
+      Timed tm(T_FORWARD, st);
+      e = launch_forward_mma(L.NP, f, st);
+      tm.stop();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");
+    return HMM_OK;
+  }
   const int G = lanes_for(HMM_OP_FORWARD, L.NP);
   const int PP = 32 / G;
   const int ngroups = (seqs->S + PP - 1) / PP;
 
-  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
+  e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
   s.ndone = (all && argmax) ? ngroups : 0;

@@ -389,6 +389,19 @@ struct FbLaunch {
 cudaError_t launch_fb(int NP, int G, const FbLaunch& a, cudaStream_t st);
 size_t fb_smem_bytes(int NP, int G, int C, int NC, int M);
 
+struct MmaFwdLaunch {
+  SeqArgs seq;
+  ModelArgs mod;      // probability tables padded to NP (64 or 128)
+  float* loglik;      // [S][K]
+  int32_t* argmax;    // [S] or NULL
+  int32_t* done;      // per tile pair
+  int32_t* queue;
+  int32_t* status;
+  int n_items;        // ceil(n_tiles / 2) * K
+  int n_tiles;        // ceil(S / 128)
+};
+cudaError_t launch_forward_mma(int NP, const MmaFwdLaunch& a, cudaStream_t st);
+
 struct ReduceLaunch {
   const float* partial;
   float* red1;

@@ -1,0 +1,325 @@
+// mma_forward.cu -- scaled forward algorithm on the tensor cores for N = 64 or
+// 128 states (Sec. 2.7 "Forward"; Rabiner 1989 eqs. 19-21, per-step scaling).
+//
+// At these state counts the step  abar_t = alpha_{t-1} A  is a real dense
+// contraction when 128 (sequence, model) pairs of one model are stacked:
+//   D[128 x N] = X[128 x N] . A[N x N]
+// with X the BF16 rescaled alpha rows in shared memory (A operand, K-major),
+// A^T in BF16 in shared memory (B operand, K-major), and D in FP32 in tensor
+// memory (tcgen05.mma, cta_group::1, M = 128, N = NP, K = 16 per instruction).
+// The epilogue (one thread per row: TMEM lane = pair) streams D through
+// registers 32 columns at a time: it multiplies by the emission row b(o_t) in
+// FP32, scales by an exact power of two, accumulates the row sum and writes
+// the next BF16 X row.
+//
+// Scaling is one step late so the epilogue needs a single pass: step t scales
+// by 2^-f_t with f_t the exponent of the previous row sum sigma_{t-1}; sums
+// then stay near the per-step likelihood ratio (never drift), and
+//   log P = ln sigma_{T-1} + (sum_t f_t) ln 2
+// with the exponents summed exactly in an integer.
+//
+// A CTA has two warpgroups, each owning one 128-row tile of the same model:
+// while one warpgroup's MMA runs, the other runs its epilogue. Work items are
+// (pair of tiles, model), taken longest-first from an atomic queue over the
+// length-sorted sequence order. Every wait on the MMA-completion mbarrier is
+// bounded; on timeout the kernel records HMM_STATUS_TIMEOUT and leaves.
+#include "hmm_internal.cuh"
+#include "tc.cuh"
+
+namespace hmmgb {
+
+template <int NP>
+struct MmaFwdSmem {
+  static constexpr int kB = NP * NP * 2;        // A^T, BF16
+  static constexpr int kX = 128 * NP * 2;       // one tile of alpha rows, BF16
+  static constexpr int OFF_B = 0;
+  static constexpr int OFF_X0 = kB;
+  static constexpr int OFF_X1 = kB + kX;
+  static constexpr int OFF_BAR = kB + 2 * kX;   // two mbarriers
+  static constexpr int OFF_MISC = OFF_BAR + 16; // tmem base, item, abort flag, last flag, per-warp max
+  static constexpr int TOTAL = OFF_MISC + 16 * 4;
+};
+
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+// x * 2^-f for f in [-252, 252] (exact).
+__device__ __forceinline__ float scale_pow2(float x, int f) {
+  if (f >= -126 && f <= 126) return x * exp2i(-f);
+  const int f1 = f / 2;
+  return x * exp2i(-f1) * exp2i(-(f - f1));
+}
+
+// Exponent e with s * 2^-e in [1, 2) for finite s > 0 (subnormals included).
+__device__ __forceinline__ int exponent_of(float s) {
+  if (s < 0x1p-120f) return frexp2(s * 0x1p64f) - 64;
+  return frexp2(s);
+}
+
+// Per-row state of the recursion.
+struct RowState {
+  int F;        // sum of the scale exponents applied so far
+  int f;        // exponent applied at the next step
+  bool dead, bad, written;
+  int err;
+  float ll;
+};
+
+// Scales 32 values, accumulates their sum and stores them as four 16-byte
+// BF16 groups of the row's K-major core-matrix layout.
+__device__ __forceinline__ float store_chunk(float (&y)[32], int f, bool live, uint8_t* rowp,
+                                             int c) {
+  float part[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float t8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float x = live ? scale_pow2(y[8 * q + u], f) : 0.f;
+      y[8 * q + u] = x;
+      t8[u] = x;
+    }
+    part[q] = tree_sum<8>(t8);
+    uint4 w;
+    w.x = tc::pack_bf16(y[8 * q + 0], y[8 * q + 1]);
+    w.y = tc::pack_bf16(y[8 * q + 2], y[8 * q + 3]);
+    w.z = tc::pack_bf16(y[8 * q + 4], y[8 * q + 5]);
+    w.w = tc::pack_bf16(y[8 * q + 6], y[8 * q + 7]);
+    *reinterpret_cast<uint4*>(rowp + (4 * c + q) * 128) = w;
+  }
+  return (part[0] + part[1]) + (part[2] + part[3]);
+}
+
+// After a step's row sum sigma: liveness checks, the log-likelihood at the
+// row's last step, and the exponent for the next step.
+__device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int Tn) {
+  if (t >= Tn || st.dead || st.bad) return;
+  if (sigma == 0.f) {
+    st.dead = true;
+    return;
+  }
+  if (!(sigma > 0.f) || isinf(sigma)) {
+    st.bad = true;
+    st.err |= HMM_STATUS_PARAM;
+    return;
+  }
+  if (t == Tn - 1) {
+    st.ll = (float)(log((double)sigma) + (double)st.F * 0.69314718055994530942);
+    st.written = true;
+  }
+  st.f = exponent_of(sigma);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
+  using L = MmaFwdSmem<NP>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sB = smem + L::OFF_B;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+  volatile int32_t* misc = reinterpret_cast<volatile int32_t*>(smem + L::OFF_MISC);
+
+  const int tid = threadIdx.x, wg = tid >> 7, row = tid & 127;
+  const int warp = tid >> 5, wq = warp & 3, lane = tid & 31;
+  uint8_t* sX = smem + (wg ? L::OFF_X1 : L::OFF_X0);
+  uint8_t* rowp = sX + (row / 8) * (NP * 16) + (row % 8) * 16;
+  const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
+
+  if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), 2 * NP);
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+    misc[2] = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = (uint32_t)misc[0];
+  const uint32_t d_tmem = tmem + (uint32_t)(wg * NP);
+  const uint32_t ld_addr = d_tmem + ((uint32_t)(wq * 32) << 16);
+  constexpr uint32_t idesc = tc::instr_desc(1, 128, NP);
+  const uint32_t x_base = tc::smem_u32(sX), b_base = tc::smem_u32(sB);
+  constexpr uint32_t SBO = NP * 16;
+  uint32_t phase = 0;
+  int cur_model = -1;
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) misc[1] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int item = misc[1];
+    if (item >= a.n_items || misc[2]) break;
+    const int tp = item / K, k = item % K;
+
+    if (k != cur_model) {
+      // B operand: element (n = j, k = i) = a_ij in BF16
+      const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
+      for (int idx = tid; idx < NP * NP / 2; idx += 256) {
+        const int j = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
+        const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + (i + 1) * NP + j));
+        const uint32_t off = (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 + (i % 8) * 2;
+        *reinterpret_cast<uint32_t*>(sB + off) = w;
+      }
+      cur_model = k;
+      tc::fence_proxy_async();
+      __syncthreads();
+    }
+
+    const int tile = 2 * tp + wg;
+    const int pos = tile * 128 + row;
+    const bool has = tile < a.n_tiles && pos < S;
+    const int s = has ? a.seq.order[pos] : 0;
+    const int T = has ? a.seq.seqlen[s] : 0;
+    const bool bad_seq = T < 0;
+    const int Tn = bad_seq ? 0 : T;
+    {
+      const int wm = __reduce_max_sync(HMM_FULL_MASK, Tn);
+      if (lane == 0) misc[4 + warp] = wm;
+    }
+    tc::bar_sync(1 + wg, 128);
+    const int Tmax = max(max(misc[4 + 4 * wg], misc[5 + 4 * wg]),
+                         max(misc[6 + 4 * wg], misc[7 + 4 * wg]));
+
+    const float* Bk = a.mod.Btp + (size_t)k * M * NP;
+    const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
+    RowState st;
+    st.F = 0; st.f = 0; st.dead = false; st.bad = bad_seq; st.written = (Tn == 0);
+    st.err = 0; st.ll = 0.f;
+
+    // t = 0: x_0 = pi . b(o_0), no scaling
+    {
+      int o0 = Tn > 0 ? __ldg(o) : 0;
+      if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
+      const bool live = Tn > 0 && !st.bad;
+      const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)o0 * NP);
+      const float4* p4 = reinterpret_cast<const float4*>(a.mod.pip + (size_t)k * NP);
+      float sigma = 0.f;
+#pragma unroll
+      for (int c = 0; c < NP / 32; ++c) {
+        float y[32];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 bb = __ldg(b4 + 8 * c + q), pp = __ldg(p4 + 8 * c + q);
+          y[4 * q] = pp.x * bb.x; y[4 * q + 1] = pp.y * bb.y;
+          y[4 * q + 2] = pp.z * bb.z; y[4 * q + 3] = pp.w * bb.w;
+        }
+        sigma += store_chunk(y, 0, live, rowp, c);
+      }
+      close_step(st, sigma, 0, Tn);
+    }
+    int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
+
+    bool aborted = false;
+    for (int t = 1; t < Tmax; ++t) {
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      tc::bar_sync(1 + wg, 128);
+      if (row == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int ks = 0; ks < NP / 16; ++ks)
+          tc::mma_bf16(d_tmem, tc::smem_desc(x_base + ks * 256, 128, SBO),
+                       tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
+        tc::mma_commit(&bars[wg]);
+      }
+      int ot = o_next;
+      if (t + 1 < Tn) o_next = __ldg(o + t + 1);
+      if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
+      if ((unsigned)ot >= (unsigned)M) ot = 0;
+      const bool live = t < Tn && !st.dead && !st.bad;
+      if (live) st.F += st.f;
+      const bool ok = tc::mbar_wait_bounded(&bars[wg], phase, kWaitLimit);
+      phase ^= 1;
+      // the whole warpgroup agrees before anyone leaves the loop
+      if (!tc::bar_and(1 + wg, 128, ok)) {
+        aborted = true;
+        break;
+      }
+      tc::fence_after_sync();
+      const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)ot * NP);
+      float sigma = 0.f;
+#pragma unroll
+      for (int c = 0; c < NP / 32; ++c) {
+        float y[32];
+        tc::tmem_ld32(ld_addr + (uint32_t)(c * 32), y);
+        float4 bb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) bb[q] = __ldg(b4 + 8 * c + q);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          y[4 * q] *= bb[q].x; y[4 * q + 1] *= bb[q].y;
+          y[4 * q + 2] *= bb[q].z; y[4 * q + 3] *= bb[q].w;
+        }
+        sigma += store_chunk(y, st.f, live, rowp, c);
+      }
+      close_step(st, sigma, t, Tn);
+    }
+    if (aborted && lane == 0) {
+      misc[2] = 1;
+      set_status(a.status, HMM_STATUS_TIMEOUT);
+    }
+    if (has) {
+      float out = st.ll;
+      if (st.bad || aborted) out = __int_as_float(0x7fc00000);
+      else if (st.dead) out = -INFINITY;
+      else if (!st.written) out = __int_as_float(0x7fc00000);
+      if (st.bad && st.err) set_status(a.status, st.err);
+      a.loglik[(size_t)s * K + k] = out;
+    }
+
+    // recognition: the last item of a tile pair takes the argmax over models
+    if (a.argmax) {
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        misc[3] = (atomicAdd(a.done + tp, 1) == K - 1) ? 1 : 0;
+      }
+      __syncthreads();
+      if (misc[3]) {
+        __threadfence();
+        if (has) {
+          const float* rp = a.loglik + (size_t)s * K;
+          float best = __ldcg(rp);
+          int arg = isnan(best) ? -1 : 0;
+          for (int kk = 1; kk < K; ++kk) {
+            const float vv = __ldcg(rp + kk);
+            if (isnan(vv)) arg = -1;
+            else if (arg >= 0 && vv > best) { best = vv; arg = kk; }
+          }
+          a.argmax[s] = arg;
+        }
+      }
+    }
+  }
+
+  // teardown: no MMA of ours may still be in flight when TMEM is released
+  tc::fence_before_sync();
+  __syncthreads();
+  if (misc[2] && row == 0) tc::mbar_wait_bounded(&bars[wg], phase, kWaitLimit);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * NP);
+}
+
+template <int NP>
+static cudaError_t launch_mma_t(const MmaFwdLaunch& a, cudaStream_t st) {
+  auto kern = hmm_forward_mma<NP>;
+  const int smem = MmaFwdSmem<NP>::TOTAL;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int blocks = num_sms() * per_sm;
+  if (blocks > a.n_items) blocks = a.n_items > 0 ? a.n_items : 1;
+  kern<<<blocks, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_mma(int NP, const MmaFwdLaunch& a, cudaStream_t st) {
+  if (NP == 64) return launch_mma_t<64>(a, st);
+  if (NP == 128) return launch_mma_t<128>(a, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hmmgb

@@ -59,6 +59,15 @@ def test_workspace_size_is_host_only_and_monotone(lib):
     q = _seqs(S=100)
     out = ctypes.c_size_t()
     assert lib.hmm_workspace_size(d, ctypes.byref(q), 7, ctypes.byref(out)) == hmm.HMM_ERR_ARG
+    # N up to 128 for the (tensor-core) forward, 64 for Viterbi, 32 for the adjoint
+    big = hmm.hmm_dims_t(4, 128, 256)
+    assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_FORWARD, ctypes.byref(out)) == 0
+    assert out.value >= 4 * 128 * 128 * 4
+    assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_VITERBI,
+                                  ctypes.byref(out)) == hmm.HMM_ERR_UNSUPPORTED
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 33, 8), ctypes.byref(q),
+                                  hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
+        == hmm.HMM_ERR_UNSUPPORTED
 
 
 def _forward(lib, dims, seqs, pi=_fake(5), loglik=_fake(8), ws=_fake(9), ws_bytes=1 << 30,

@@ -1,0 +1,96 @@
+"""Tensor-core (BF16 tcgen05) forward vs the FP64 oracle.
+
+The tensor-core path rounds the transition matrix A and the rescaled forward
+variable to BF16 (unit roundoff u = 2^-8) and accumulates in FP32. Two checks:
+
+* against the oracle run on the same model with A rounded to BF16 (the
+  systematic part of the error removed), the remaining difference comes from
+  rounding alpha each step and must stay within the FP32 bound
+  1e-4 * max(T, 1) nats;
+* against the oracle on the exact model, every term of every step is a sum of
+  non-negative products whose factors carry relative errors <= u, so
+  |delta log P| <= 2 u T is a hard bound; the mean per-step error is reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import ll_tol, to_gpu
+from paper_1310_3322_gb300 import hmm, synth
+
+pytestmark = pytest.mark.gpu
+
+U_BF16 = 2.0 ** -8
+
+
+def bf16_round(x):
+    """Round-to-nearest-even of float32 values to bfloat16, returned as float32."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+CASES = [
+    ("large", 48, ("uniform", 20, 400), {"K": 2}),           # N=128, M=256
+    ("training", 96, ("uniform", 1, 300), {"K": 3}),         # N=64, M=128
+    ("large", 40, ("uniform", 0, 200), {"K": 2, "N": 100}),  # padded to 128
+    ("gradient", 60, ("uniform", 1, 150), {"K": 3, "N": 40}),  # padded to 64
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[3]}")
+def test_bf16_forward_matches_oracle(case):
+    name, S, lengths, over = case
+    w = synth.make_workload(name, n_seqs=S, lengths=lengths, **over)
+    seqs, pi, A, B = to_gpu(w)
+    ll, am = hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_BF16_MMA)
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    ll = ll.cpu().numpy()
+    T = np.maximum(w.lengths, 1).astype(np.float64)[:, None]
+    # systematic rounding of A removed: only the per-step rounding of alpha
+    # (relative <= u per term, all terms non-negative) remains
+    Pr = oracle.params(w.pi, bf16_round(w.A), w.B)
+    ref_r, _, _ = oracle.forward(Pr, w.symbols, w.offsets, w.lengths, nthreads=8)
+    err_r = np.abs(ll - ref_r)
+    assert np.all(err_r <= U_BF16 * T + ll_tol(w.lengths)[:, None]), (err_r / T).max()
+    # ... and it is a random-signed error far below that bound on average
+    assert np.mean(err_r / T) <= U_BF16 / 8, np.mean(err_r / T)
+    # exact model: hard bound 2 u T
+    ref, ref_am, _ = oracle.forward(oracle.params(w.pi, w.A, w.B), w.symbols, w.offsets,
+                                    w.lengths, nthreads=8)
+    err = np.abs(ll - ref)
+    assert np.all(err <= 2 * U_BF16 * T + ll_tol(w.lengths)[:, None]), (err / T).max()
+    print(f"{name} N={w.N}: max|d|/T vs exact {np.max(err / T):.2e}, mean {np.mean(err / T):.2e}; "
+          f"vs bf16-A {np.max(err_r / T):.2e}")
+    # recognition: argmax agrees where the top two models are well separated
+    srt = np.sort(ref, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 4 * U_BF16 * T[:, 0]
+    np.testing.assert_array_equal(am.cpu().numpy()[clear], ref_am[clear])
+
+
+def test_bf16_forward_degenerate_and_errors():
+    import torch
+    rng = np.random.default_rng(4)
+    pi, A, B = synth.random_model(rng, 2, 70, 5)
+    seqs_l = [rng.integers(0, 5, size=T).tolist() for T in (0, 1, 2, 129, 3)]
+    seqs_l[2] = [0, 7]          # bad symbol
+    lengths = np.array([len(x) for x in seqs_l], np.int32)
+    offsets = np.zeros(len(seqs_l), np.int64)
+    offsets[1:] = np.cumsum(lengths)[:-1]
+    sym = np.array([x for q in seqs_l for x in q], np.int32)
+    seqs = hmm.Sequences.from_numpy(sym, offsets, lengths)
+    t = [torch.from_numpy(x).cuda() for x in (pi, A, B)]
+    ll, am = hmm.hmm_forward(*t, seqs, precision=hmm.HMM_BF16_MMA)
+    ll = ll.cpu().numpy()
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) & hmm.HMM_STATUS_SYMBOL
+    assert np.all(ll[0] == 0.0) and np.all(np.isnan(ll[2])) and am.cpu().numpy()[2] == -1
+    ref, _, _ = oracle.forward(oracle.params(pi, A, B), sym, offsets, lengths)
+    ok = np.array([True, True, False, True, True])
+    assert np.all(np.abs(ll[ok] - ref[ok]) <= 2 * U_BF16 * np.maximum(lengths[ok], 1)[:, None])
+    # labelled mode and small N are not served by the tensor-core path
+    with pytest.raises(hmm.HmmError):
+        hmm.hmm_forward(*t, seqs.labelled(torch.zeros(5, dtype=torch.int32, device="cuda")),
+                        precision=hmm.HMM_BF16_MMA)
+    small = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 2, 16, 5)]
+    with pytest.raises(hmm.HmmError):
+        hmm.hmm_forward(*small, seqs, precision=hmm.HMM_BF16_MMA)

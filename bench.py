@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--n-seqs", type=int, default=None, help="smaller batch (profiling only)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "large", "training"],
+                    help="batched: the full step (default); large/training: tensor-core forward")
     return ap.parse_args()
 
 
@@ -430,6 +433,83 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def measured_peak_bf16():
+    """Dense BF16 TFLOP/s measured on this machine (burst), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
+
+
+def run_forward_only(args):
+    """Forward (all K models + argmax) on the large-state configurations, the
+    only op this build runs on the tensor cores; one JSON line."""
+    import torch
+    from paper_1310_3322_gb300 import hmm, synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.make_workload(args.workload, n_seqs=args.n_seqs,
+                            seed=synth.SEEDS[args.workload] + rank)
+    K, N = w.K, w.N
+    sumT = int(w.lengths.astype(np.int64).sum())
+    units = sumT * K
+    seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
+    pi, A, B = (torch.from_numpy(x).to(dev) for x in (w.pi, w.A, w.B))
+    ll = torch.empty((w.S, K), device=dev)
+    am = torch.empty(w.S, dtype=torch.int32, device=dev)
+    ws = hmm.Workspace(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    variants = [("bf16_mma", hmm.HMM_BF16_MMA)]
+    if N <= hmm.hmm_max_states(hmm.HMM_OP_FORWARD, hmm.HMM_FP32):
+        variants.append(("fp32_simt", hmm.HMM_FP32))
+    for name, prec in variants:
+        def step():
+            hmm.hmm_forward(pi, A, B, seqs, precision=prec, loglik=ll, argmax=am, workspace=ws)
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        assert hmm.hmm_get_device_status(ws) == 0
+        hmm.hmm_timing_reset()
+        hmm.hmm_timing_enable(True)
+        evs = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step()
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        kt = hmm.hmm_timing_read()
+        hmm.hmm_timing_enable(False)
+        ms = float(np.mean([x.elapsed_time(y) for x, y in evs]))
+        kms = kt["forward"][1] / max(kt["forward"][0], 1)
+        out[name] = {"ms_per_step": ms, "kernel_ms": kms, "value": units / (ms / 1e3),
+                     "tflops": 2.0 * N * N * units / (kms / 1e3) / 1e12}
+    peak, basis = measured_peak_bf16()
+    main_v = out["bf16_mma"]
+    line = {
+        "metric": METRIC, "value": main_v["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_v["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} K={K} N={N} M={w.M} S={w.S} (forward, all "
+                               "K models + argmax, tensor cores)", "units_per_step": units,
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "timing": "eager step, CUDA events"},
+        "roofline": {"bound": "tensor", "kernel": "forward_mma", "achieved": main_v["tflops"],
+                     "peak": peak, "unit": "TFLOP/s", "frac": main_v["tflops"] / peak,
+                     "peak_basis": f"dense BF16, {basis} (burst)", "traffic": None},
+        "variants": out,
+        "gpu_launches": 2 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -437,6 +517,9 @@ def main():
         return
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload != WORKLOAD:
+        run_forward_only(args)
+        return
     run_gpu(args)
 
 

@@ -4,25 +4,35 @@
 // At these state counts the step  abar_t = alpha_{t-1} A  is a real dense
 // contraction when 128 (sequence, model) pairs of one model are stacked:
 //   D[128 x N] = X[128 x N] . A[N x N]
-// with X the BF16 rescaled alpha rows in shared memory (A operand, K-major),
-// A^T in BF16 in shared memory (B operand, K-major), and D in FP32 in tensor
-// memory (tcgen05.mma, cta_group::1, M = 128, N = NP, K = 16 per instruction).
-// The epilogue (one thread per row: TMEM lane = pair) streams D through
-// registers 32 columns at a time: it multiplies by the emission row b(o_t) in
-// FP32, scales by an exact power of two, accumulates the row sum and writes
-// the next BF16 X row.
+// tcgen05.mma (cta_group::1, kind::f16, M = 128, N = NP, K = 16 per
+// instruction) with
+//   * X, the BF16 rescaled alpha rows, in tensor memory (A operand: lane =
+//     row, two BF16 per 32-bit column), written by the epilogue with
+//     tcgen05.st -- no shared-memory traffic for X at all;
+//   * A^T in BF16 in shared memory (B operand, K-major, no swizzle);
+//   * D in FP32 in tensor memory.
+// The epilogue (one thread per row) streams D through registers 32 columns at
+// a time: multiply by the emission row b(o_t) in FP32, scale by an exact power
+// of two, accumulate the row sum, pack to BF16 and store the next X row.
+//
+// Emission rows: each row's b(o_{t+1}) (NP FP32 values) is brought into that
+// row's slot of a shared-memory staging tile by one bulk (TMA-engine) copy,
+// issued as soon as the row has read b(o_t) and completing on an mbarrier
+// while the next MMA runs. Slots are padded by 16 bytes so that the eight rows
+// of one shared-memory wavefront fall in distinct banks.
 //
 // Scaling is one step late so the epilogue needs a single pass: step t scales
-// by 2^-f_t with f_t the exponent of the previous row sum sigma_{t-1}; sums
-// then stay near the per-step likelihood ratio (never drift), and
+// by 2^-f_t with f_t the exponent of the previous row sum sigma_{t-1} (clamped
+// to the float range; a clamped step is caught up by the next one); sums stay
+// near the per-step likelihood ratio, and
 //   log P = ln sigma_{T-1} + (sum_t f_t) ln 2
 // with the exponents summed exactly in an integer.
 //
 // A CTA has two warpgroups, each owning one 128-row tile of the same model:
 // while one warpgroup's MMA runs, the other runs its epilogue. Work items are
 // (pair of tiles, model), taken longest-first from an atomic queue over the
-// length-sorted sequence order. Every wait on the MMA-completion mbarrier is
-// bounded; on timeout the kernel records HMM_STATUS_TIMEOUT and leaves.
+// length-sorted sequence order. Every mbarrier wait is bounded; on timeout the
+// kernel records HMM_STATUS_TIMEOUT and leaves.
 #include "hmm_internal.cuh"
 #include "tc.cuh"
 
@@ -30,24 +40,20 @@ namespace hmmgb {
 
 template <int NP>
 struct MmaFwdSmem {
-  static constexpr int kB = NP * NP * 2;        // A^T, BF16
-  static constexpr int kX = 128 * NP * 2;       // one tile of alpha rows, BF16
+  static constexpr int kB = NP * NP * 2;          // A^T, BF16
+  static constexpr int kES = NP * 4 + 16;         // padded emission row, FP32
+  static constexpr int kE = 128 * kES;            // one tile of emission rows
   static constexpr int OFF_B = 0;
-  static constexpr int OFF_X0 = kB;
-  static constexpr int OFF_X1 = kB + kX;
-  static constexpr int OFF_BAR = kB + 2 * kX;   // two mbarriers
-  static constexpr int OFF_MISC = OFF_BAR + 16; // tmem base, item, abort flag, last flag, per-warp max
+  static constexpr int OFF_E0 = kB;
+  static constexpr int OFF_E1 = kB + kE;
+  static constexpr int OFF_BAR = kB + 2 * kE;     // mma[2], emission[2]
+  static constexpr int OFF_MISC = OFF_BAR + 32;   // tmem base, item, abort, last, per-warp max
   static constexpr int TOTAL = OFF_MISC + 16 * 4;
 };
+static_assert(MmaFwdSmem<128>::TOTAL <= 227 * 1024, "shared memory budget");
 
 constexpr uint32_t kWaitLimit = 1u << 24;
-
-// x * 2^-f for f in [-252, 252] (exact).
-__device__ __forceinline__ float scale_pow2(float x, int f) {
-  if (f >= -126 && f <= 126) return x * exp2i(-f);
-  const int f1 = f / 2;
-  return x * exp2i(-f1) * exp2i(-(f - f1));
-}
+constexpr uint32_t kTmemCols = 512;  // per warpgroup: D (NP cols) then X (NP/2 cols) at 256 * wg
 
 // Exponent e with s * 2^-e in [1, 2) for finite s > 0 (subnormals included).
 __device__ __forceinline__ int exponent_of(float s) {
@@ -58,35 +64,25 @@ __device__ __forceinline__ int exponent_of(float s) {
 // Per-row state of the recursion.
 struct RowState {
   int F;        // sum of the scale exponents applied so far
-  int f;        // exponent applied at the next step
+  int f;        // exponent applied at the next step, within [-126, 126]
   bool dead, bad, written;
   int err;
   float ll;
 };
 
-// Scales 32 values, accumulates their sum and stores them as four 16-byte
-// BF16 groups of the row's K-major core-matrix layout.
-__device__ __forceinline__ float store_chunk(float (&y)[32], int f, bool live, uint8_t* rowp,
-                                             int c) {
-  float part[4];
+// Starts the bulk copy of emission row `sym` into this row's slot.
+template <int NP>
+__device__ __forceinline__ void stage_emission(uint32_t slot, const float* Bk, int sym,
+                                               uint64_t* ebar) {
+  tc::fence_proxy_async();  // this thread's reads of the slot precede the copy
+  tc::mbar_arrive_expect_tx(ebar, NP * 4);
+  tc::bulk_g2s(slot, Bk + (size_t)sym * NP, NP * 4, ebar);
+}
+
+// 32 values -> 16 packed BF16 pairs (even k in the low half).
+__device__ __forceinline__ void pack32(const float (&y)[32], uint32_t (&w)[16]) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float t8[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const float x = live ? scale_pow2(y[8 * q + u], f) : 0.f;
-      y[8 * q + u] = x;
-      t8[u] = x;
-    }
-    part[q] = tree_sum<8>(t8);
-    uint4 w;
-    w.x = tc::pack_bf16(y[8 * q + 0], y[8 * q + 1]);
-    w.y = tc::pack_bf16(y[8 * q + 2], y[8 * q + 3]);
-    w.z = tc::pack_bf16(y[8 * q + 4], y[8 * q + 5]);
-    w.w = tc::pack_bf16(y[8 * q + 6], y[8 * q + 7]);
-    *reinterpret_cast<uint4*>(rowp + (4 * c + q) * 128) = w;
-  }
-  return (part[0] + part[1]) + (part[2] + part[3]);
+  for (int i = 0; i < 16; ++i) w[i] = tc::pack_bf16(y[2 * i], y[2 * i + 1]);
 }
 
 // After a step's row sum sigma: liveness checks, the log-likelihood at the
@@ -106,7 +102,7 @@ __device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int
     st.ll = (float)(log((double)sigma) + (double)st.F * 0.69314718055994530942);
     st.written = true;
   }
-  st.f = exponent_of(sigma);
+  st.f = min(126, max(-126, exponent_of(sigma)));
 }
 
 template <int NP>
@@ -119,26 +115,31 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
 
   const int tid = threadIdx.x, wg = tid >> 7, row = tid & 127;
   const int warp = tid >> 5, wq = warp & 3, lane = tid & 31;
-  uint8_t* sX = smem + (wg ? L::OFF_X1 : L::OFF_X0);
-  uint8_t* rowp = sX + (row / 8) * (NP * 16) + (row % 8) * 16;
+  const uint8_t* erow = smem + (wg ? L::OFF_E1 : L::OFF_E0) + row * L::kES;
+  const uint32_t eslot = tc::smem_u32(erow);
+  uint64_t* mbar = &bars[wg];
+  uint64_t* ebar = &bars[2 + wg];
   const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
 
-  if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), 2 * NP);
+  if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), kTmemCols);
   if (tid == 0) {
     tc::mbar_init(&bars[0], 1);
     tc::mbar_init(&bars[1], 1);
+    tc::mbar_init(&bars[2], 128);
+    tc::mbar_init(&bars[3], 128);
     misc[2] = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = (uint32_t)misc[0];
-  const uint32_t d_tmem = tmem + (uint32_t)(wg * NP);
-  const uint32_t ld_addr = d_tmem + ((uint32_t)(wq * 32) << 16);
+  const uint32_t d_tmem = tmem + (uint32_t)(wg * 256);          // D: NP FP32 columns
+  const uint32_t x_tmem = d_tmem + (uint32_t)NP;                // X: NP/2 packed columns
+  const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
   constexpr uint32_t idesc = tc::instr_desc(1, 128, NP);
-  const uint32_t x_base = tc::smem_u32(sX), b_base = tc::smem_u32(sB);
+  const uint32_t b_base = tc::smem_u32(sB);
   constexpr uint32_t SBO = NP * 16;
-  uint32_t phase = 0;
+  uint32_t mphase = 0, ephase = 0;
   int cur_model = -1;
 
   for (;;) {
@@ -195,63 +196,83 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
 #pragma unroll
       for (int c = 0; c < NP / 32; ++c) {
         float y[32];
+        float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const float4 bb = __ldg(b4 + 8 * c + q), pp = __ldg(p4 + 8 * c + q);
-          y[4 * q] = pp.x * bb.x; y[4 * q + 1] = pp.y * bb.y;
-          y[4 * q + 2] = pp.z * bb.z; y[4 * q + 3] = pp.w * bb.w;
+          y[4 * q] = live ? pp.x * bb.x : 0.f; y[4 * q + 1] = live ? pp.y * bb.y : 0.f;
+          y[4 * q + 2] = live ? pp.z * bb.z : 0.f; y[4 * q + 3] = live ? pp.w * bb.w : 0.f;
+          part[q & 3] += (y[4 * q] + y[4 * q + 1]) + (y[4 * q + 2] + y[4 * q + 3]);
         }
-        sigma += store_chunk(y, 0, live, rowp, c);
+        sigma += (part[0] + part[1]) + (part[2] + part[3]);
+        uint32_t w[16];
+        pack32(y, w);
+        tc::tmem_st16(x_tmem + lane_off + (uint32_t)(16 * c), w);
       }
+      tc::tmem_st_wait();
       close_step(st, sigma, 0, Tn);
     }
     int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
+    if (Tmax > 1)
+      stage_emission<NP>(eslot, Bk, (1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0, ebar);
 
     bool aborted = false;
     for (int t = 1; t < Tmax; ++t) {
-      tc::fence_proxy_async();
       tc::fence_before_sync();
       tc::bar_sync(1 + wg, 128);
       if (row == 0) {
         tc::fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < NP / 16; ++ks)
-          tc::mma_bf16(d_tmem, tc::smem_desc(x_base + ks * 256, 128, SBO),
-                       tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
-        tc::mma_commit(&bars[wg]);
+          tc::mma_bf16_ts(d_tmem, x_tmem + (uint32_t)(ks * 8),
+                          tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
+        tc::mma_commit(mbar);
       }
-      int ot = o_next;
+      const int ot = o_next;
       if (t + 1 < Tn) o_next = __ldg(o + t + 1);
       if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
-      if ((unsigned)ot >= (unsigned)M) ot = 0;
       const bool live = t < Tn && !st.dead && !st.bad;
       if (live) st.F += st.f;
-      const bool ok = tc::mbar_wait_bounded(&bars[wg], phase, kWaitLimit);
-      phase ^= 1;
+      const float2 fac2 = make_float2(exp2i(-st.f), exp2i(-st.f));
+      const bool ok_e = tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
+      const bool ok_m = tc::mbar_wait_bounded(mbar, mphase, kWaitLimit);
+      ephase ^= 1;
+      mphase ^= 1;
       // the whole warpgroup agrees before anyone leaves the loop
-      if (!tc::bar_and(1 + wg, 128, ok)) {
+      if (!tc::bar_and(1 + wg, 128, ok_e && ok_m)) {
         aborted = true;
         break;
       }
       tc::fence_after_sync();
-      const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)ot * NP);
       float sigma = 0.f;
 #pragma unroll
       for (int c = 0; c < NP / 32; ++c) {
         float y[32];
-        tc::tmem_ld32(ld_addr + (uint32_t)(c * 32), y);
-        float4 bb[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) bb[q] = __ldg(b4 + 8 * c + q);
+        tc::tmem_ld32(d_tmem + lane_off + (uint32_t)(c * 32), y);
         tc::tmem_ld_wait();
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          y[4 * q] *= bb[q].x; y[4 * q + 1] *= bb[q].y;
-          y[4 * q + 2] *= bb[q].z; y[4 * q + 3] *= bb[q].w;
+          const float4 b = *reinterpret_cast<const float4*>(erow + (8 * c + q) * 16);
+          float2 lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
+                                            make_float2(b.x, b.y)), fac2);
+          float2 hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
+                                            make_float2(b.z, b.w)), fac2);
+          if (!live) { lo = make_float2(0.f, 0.f); hi = lo; }
+          acc = __fadd2_rn(acc, __fadd2_rn(lo, hi));
+          y[4 * q] = lo.x; y[4 * q + 1] = lo.y; y[4 * q + 2] = hi.x; y[4 * q + 3] = hi.y;
         }
-        sigma += store_chunk(y, st.f, live, rowp, c);
+        sigma += acc.x + acc.y;
+        uint32_t w[16];
+        pack32(y, w);
+        tc::tmem_st16(x_tmem + lane_off + (uint32_t)(16 * c), w);
       }
+      tc::tmem_st_wait();
       close_step(st, sigma, t, Tn);
+      if (t + 1 < Tmax) {
+        const int on = (t + 1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0;
+        stage_emission<NP>(eslot, Bk, on, ebar);
+      }
     }
     if (aborted && lane == 0) {
       misc[2] = 1;
@@ -291,26 +312,27 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
     }
   }
 
-  // teardown: no MMA of ours may still be in flight when TMEM is released
+  // teardown: no MMA or copy of ours may still be in flight
   tc::fence_before_sync();
   __syncthreads();
-  if (misc[2] && row == 0) tc::mbar_wait_bounded(&bars[wg], phase, kWaitLimit);
+  if (misc[2] && row == 0) {
+    tc::mbar_wait_bounded(mbar, mphase, kWaitLimit);
+    tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
+  }
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, 2 * NP);
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 template <int NP>
 static cudaError_t launch_mma_t(const MmaFwdLaunch& a, cudaStream_t st) {
   auto kern = hmm_forward_mma<NP>;
-  const int smem = MmaFwdSmem<NP>::TOTAL;
+  // one CTA per SM (it holds all 512 tensor-memory columns): ask for more
+  // than half of the shared memory even when the tiles need less
+  const int smem = MmaFwdSmem<NP>::TOTAL > 120 * 1024 ? MmaFwdSmem<NP>::TOTAL : 120 * 1024;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-  if (err != cudaSuccess) return err;
-  if (per_sm < 1) per_sm = 1;
-  int blocks = num_sms() * per_sm;
+  int blocks = num_sms();
   if (blocks > a.n_items) blocks = a.n_items > 0 ? a.n_items : 1;
   kern<<<blocks, 256, smem, st>>>(a);
   return cudaGetLastError();

@@ -369,7 +369,8 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
   cudaError_t e;
   if (mma) {
     const int n_tiles = (seqs->S + 127) / 128;
-    const int n_pairs = (n_tiles + 1) / 2;
+    const int nt = mma_tiles_per_cta(L.NP);
+    const int n_pairs = (n_tiles + nt - 1) / nt;  // tile groups of one CTA
     if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
     SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
     s.ndone = argmax ? n_pairs : 0;

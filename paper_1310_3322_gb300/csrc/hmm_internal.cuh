@@ -397,10 +397,11 @@ struct MmaFwdLaunch {
   int32_t* done;      // per tile pair
   int32_t* queue;
   int32_t* status;
-  int n_items;        // ceil(n_tiles / 2) * K
+  int n_items;        // ceil(n_tiles / tiles per CTA) * K
   int n_tiles;        // ceil(S / 128)
 };
 cudaError_t launch_forward_mma(int NP, const MmaFwdLaunch& a, cudaStream_t st);
+int mma_tiles_per_cta(int NP);  // 128-row tiles one CTA of the tensor-core forward holds
 
 struct ReduceLaunch {
   const float* partial;

@@ -11,9 +11,11 @@
 //     tcgen05.st -- no shared-memory traffic for X at all;
 //   * A^T in BF16 in shared memory (B operand, K-major, no swizzle);
 //   * D in FP32 in tensor memory.
-// The epilogue (one thread per row) streams D through registers 32 columns at
-// a time: multiply by the emission row b(o_t) in FP32, scale by an exact power
-// of two, accumulate the row sum, pack to BF16 and store the next X row.
+// The epilogue gives every row TPR threads (warps w, w+4, ... of a tile's
+// group see the same 32 tensor-memory lanes); each streams its share of the
+// row's D columns through registers 32 at a time: multiply by the emission
+// row b(o_t) in FP32, scale by an exact power of two, accumulate a partial row
+// sum, pack to BF16 and store its share of the next X row.
 //
 // Emission rows: each row's b(o_{t+1}) (NP FP32 values) is brought into that
 // row's slot of a shared-memory staging tile by one bulk (TMA-engine) copy,
@@ -21,39 +23,45 @@
 // while the next MMA runs. Slots are padded by 16 bytes so that the eight rows
 // of one shared-memory wavefront fall in distinct banks.
 //
-// Scaling is one step late so the epilogue needs a single pass: step t scales
-// by 2^-f_t with f_t the exponent of the previous row sum sigma_{t-1} (clamped
-// to the float range; a clamped step is caught up by the next one); sums stay
-// near the per-step likelihood ratio, and
+// Scaling is one step late so no thread waits for a full row sum inside a
+// step: step t scales by 2^-f_t with f_t the exponent of the previous row sum
+// sigma_{t-1} (clamped to the float range; a clamped step is caught up by the
+// next one), the two partial sums meet in shared memory behind the barrier
+// that precedes the next MMA, sums stay near the per-step likelihood ratio,
+// and
 //   log P = ln sigma_{T-1} + (sum_t f_t) ln 2
 // with the exponents summed exactly in an integer.
 //
-// A CTA has two warpgroups, each owning one 128-row tile of the same model:
-// while one warpgroup's MMA runs, the other runs its epilogue. Work items are
-// (pair of tiles, model), taken longest-first from an atomic queue over the
-// length-sorted sequence order. Every mbarrier wait is bounded; on timeout the
-// kernel records HMM_STATUS_TIMEOUT and leaves.
+// A CTA of 512 threads owns NT 128-row tiles of the same model (NT = 2 with two
+// threads per row at N = 128, where tensor memory holds two tiles; NT = 4 with
+// one thread per row at N = 64): while one tile's MMA runs, the others run
+// their epilogues. Work items are (group of NT tiles, model), taken
+// longest-first from an atomic queue over the length-sorted sequence order.
+// Every mbarrier wait is bounded; on timeout the kernel records
+// HMM_STATUS_TIMEOUT and leaves.
 #include "hmm_internal.cuh"
 #include "tc.cuh"
 
 namespace hmmgb {
 
-template <int NP>
+template <int NP, int NT, int TPR>
 struct MmaFwdSmem {
   static constexpr int kB = NP * NP * 2;          // A^T, BF16
   static constexpr int kES = NP * 4 + 16;         // padded emission row, FP32
   static constexpr int kE = 128 * kES;            // one tile of emission rows
   static constexpr int OFF_B = 0;
-  static constexpr int OFF_E0 = kB;
-  static constexpr int OFF_E1 = kB + kE;
-  static constexpr int OFF_BAR = kB + 2 * kE;     // mma[2], emission[2]
-  static constexpr int OFF_MISC = OFF_BAR + 32;   // tmem base, item, abort, last, per-warp max
-  static constexpr int TOTAL = OFF_MISC + 16 * 4;
+  static constexpr int OFF_E = kB;                // [NT] tiles of emission rows
+  static constexpr int OFF_PS = kB + NT * kE;     // partial row sums [NT][TPR][128]
+  static constexpr int OFF_BAR = OFF_PS + NT * TPR * 128 * 4;  // mma[NT], emission[NT]
+  static constexpr int OFF_MISC = OFF_BAR + 2 * NT * 8;        // tmem, item, abort, last, warp max
+  static constexpr int TOTAL = OFF_MISC + 24 * 4;
 };
-static_assert(MmaFwdSmem<128>::TOTAL <= 227 * 1024, "shared memory budget");
+static_assert(MmaFwdSmem<128, 2, 2>::TOTAL <= 227 * 1024, "shared memory budget");
+static_assert(MmaFwdSmem<64, 4, 1>::TOTAL <= 227 * 1024, "shared memory budget");
 
 constexpr uint32_t kWaitLimit = 1u << 24;
-constexpr uint32_t kTmemCols = 512;  // per warpgroup: D (NP cols) then X (NP/2 cols) at 256 * wg
+constexpr uint32_t kTmemCols = 512;  // per tile: D (NP cols) then X (NP/2 cols) at (512/NT) * tile
+constexpr int kMmaThreads = 512;
 
 // Exponent e with s * 2^-e in [1, 2) for finite s > 0 (subnormals included).
 __device__ __forceinline__ int exponent_of(float s) {
@@ -61,7 +69,7 @@ __device__ __forceinline__ int exponent_of(float s) {
   return frexp2(s);
 }
 
-// Per-row state of the recursion.
+// Per-row state of the recursion (kept identically by both threads of a row).
 struct RowState {
   int F;        // sum of the scale exponents applied so far
   int f;        // exponent applied at the next step, within [-126, 126]
@@ -74,7 +82,7 @@ struct RowState {
 template <int NP>
 __device__ __forceinline__ void stage_emission(uint32_t slot, const float* Bk, int sym,
                                                uint64_t* ebar) {
-  tc::fence_proxy_async();  // this thread's reads of the slot precede the copy
+  tc::fence_proxy_async();  // this row's reads of the slot precede the copy
   tc::mbar_arrive_expect_tx(ebar, NP * 4);
   tc::bulk_g2s(slot, Bk + (size_t)sym * NP, NP * 4, ebar);
 }
@@ -85,7 +93,7 @@ __device__ __forceinline__ void pack32(const float (&y)[32], uint32_t (&w)[16]) 
   for (int i = 0; i < 16; ++i) w[i] = tc::pack_bf16(y[2 * i], y[2 * i + 1]);
 }
 
-// After a step's row sum sigma: liveness checks, the log-likelihood at the
+// After step t's row sum sigma: liveness checks, the log-likelihood at the
 // row's last step, and the exponent for the next step.
 __device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int Tn) {
   if (t >= Tn || st.dead || st.bad) return;
@@ -105,37 +113,48 @@ __device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int
   st.f = min(126, max(-126, exponent_of(sigma)));
 }
 
-template <int NP>
-__global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
-  using L = MmaFwdSmem<NP>;
+template <int NP, int NT, int TPR>
+__global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a) {
+  using L = MmaFwdSmem<NP, NT, TPR>;
+  constexpr int WGT = 128 * TPR;     // threads per tile
+  static_assert(NT * WGT == kMmaThreads, "512 threads per CTA");
+  constexpr int HALF = NP / TPR;     // columns per thread
+  constexpr int CH = HALF / 32;      // 32-column chunks per thread
+  constexpr int TS = 512 / NT;       // tensor-memory columns per tile
+  static_assert(NP + NP / 2 <= TS, "tile does not fit its tensor-memory share");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem + L::OFF_B;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   volatile int32_t* misc = reinterpret_cast<volatile int32_t*>(smem + L::OFF_MISC);
 
-  const int tid = threadIdx.x, wg = tid >> 7, row = tid & 127;
-  const int warp = tid >> 5, wq = warp & 3, lane = tid & 31;
-  const uint8_t* erow = smem + (wg ? L::OFF_E1 : L::OFF_E0) + row * L::kES;
+  const int tid = threadIdx.x, wg = tid / WGT, wtid = tid % WGT;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wq = warp & 3, h = (wtid >> 7);   // lane quarter, column share
+  const int row = wq * 32 + lane;
+  const uint8_t* erow = smem + L::OFF_E + wg * L::kE + row * L::kES;
   const uint32_t eslot = tc::smem_u32(erow);
+  float* psum = reinterpret_cast<float*>(smem + L::OFF_PS) + wg * TPR * 128;  // [TPR][128]
   uint64_t* mbar = &bars[wg];
-  uint64_t* ebar = &bars[2 + wg];
+  uint64_t* ebar = &bars[NT + wg];
   const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
 
   if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), kTmemCols);
   if (tid == 0) {
-    tc::mbar_init(&bars[0], 1);
-    tc::mbar_init(&bars[1], 1);
-    tc::mbar_init(&bars[2], 128);
-    tc::mbar_init(&bars[3], 128);
+    for (int i = 0; i < NT; ++i) {
+      tc::mbar_init(&bars[i], 1);
+      tc::mbar_init(&bars[NT + i], 128);
+    }
     misc[2] = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = (uint32_t)misc[0];
-  const uint32_t d_tmem = tmem + (uint32_t)(wg * 256);          // D: NP FP32 columns
+  const uint32_t d_tmem = tmem + (uint32_t)(wg * TS);           // D: NP FP32 columns
   const uint32_t x_tmem = d_tmem + (uint32_t)NP;                // X: NP/2 packed columns
   const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+  const uint32_t d_mine = d_tmem + lane_off + (uint32_t)(h * HALF);
+  const uint32_t x_mine = x_tmem + lane_off + (uint32_t)(h * HALF / 2);
   constexpr uint32_t idesc = tc::instr_desc(1, 128, NP);
   const uint32_t b_base = tc::smem_u32(sB);
   constexpr uint32_t SBO = NP * 16;
@@ -153,7 +172,7 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
     if (k != cur_model) {
       // B operand: element (n = j, k = i) = a_ij in BF16
       const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
-      for (int idx = tid; idx < NP * NP / 2; idx += 256) {
+      for (int idx = tid; idx < NP * NP / 2; idx += kMmaThreads) {
         const int j = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
         const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + (i + 1) * NP + j));
         const uint32_t off = (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 + (i % 8) * 2;
@@ -164,7 +183,7 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
       __syncthreads();
     }
 
-    const int tile = 2 * tp + wg;
+    const int tile = NT * tp + wg;
     const int pos = tile * 128 + row;
     const bool has = tile < a.n_tiles && pos < S;
     const int s = has ? a.seq.order[pos] : 0;
@@ -175,9 +194,10 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
       const int wm = __reduce_max_sync(HMM_FULL_MASK, Tn);
       if (lane == 0) misc[4 + warp] = wm;
     }
-    tc::bar_sync(1 + wg, 128);
-    const int Tmax = max(max(misc[4 + 4 * wg], misc[5 + 4 * wg]),
-                         max(misc[6 + 4 * wg], misc[7 + 4 * wg]));
+    tc::bar_sync(1 + wg, WGT);
+    int Tmax = 0;
+#pragma unroll
+    for (int w8 = 0; w8 < WGT / 32; ++w8) Tmax = max(Tmax, (int)misc[4 + (WGT / 32) * wg + w8]);
 
     const float* Bk = a.mod.Btp + (size_t)k * M * NP;
     const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
@@ -190,37 +210,35 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
       int o0 = Tn > 0 ? __ldg(o) : 0;
       if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
       const bool live = Tn > 0 && !st.bad;
-      const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)o0 * NP);
-      const float4* p4 = reinterpret_cast<const float4*>(a.mod.pip + (size_t)k * NP);
-      float sigma = 0.f;
+      const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)o0 * NP + h * HALF);
+      const float4* p4 = reinterpret_cast<const float4*>(a.mod.pip + (size_t)k * NP + h * HALF);
+      float part = 0.f;
 #pragma unroll
-      for (int c = 0; c < NP / 32; ++c) {
+      for (int c = 0; c < CH; ++c) {
         float y[32];
-        float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const float4 bb = __ldg(b4 + 8 * c + q), pp = __ldg(p4 + 8 * c + q);
           y[4 * q] = live ? pp.x * bb.x : 0.f; y[4 * q + 1] = live ? pp.y * bb.y : 0.f;
           y[4 * q + 2] = live ? pp.z * bb.z : 0.f; y[4 * q + 3] = live ? pp.w * bb.w : 0.f;
-          part[q & 3] += (y[4 * q] + y[4 * q + 1]) + (y[4 * q + 2] + y[4 * q + 3]);
         }
-        sigma += (part[0] + part[1]) + (part[2] + part[3]);
+        part += tree_sum<32>(y);
         uint32_t w[16];
         pack32(y, w);
-        tc::tmem_st16(x_tmem + lane_off + (uint32_t)(16 * c), w);
+        tc::tmem_st16(x_mine + (uint32_t)(16 * c), w);
       }
       tc::tmem_st_wait();
-      close_step(st, sigma, 0, Tn);
+      psum[h * 128 + row] = part;
     }
     int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
-    if (Tmax > 1)
+    if (Tmax > 1 && h == 0)
       stage_emission<NP>(eslot, Bk, (1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0, ebar);
 
     bool aborted = false;
     for (int t = 1; t < Tmax; ++t) {
       tc::fence_before_sync();
-      tc::bar_sync(1 + wg, 128);
-      if (row == 0) {
+      tc::bar_sync(1 + wg, WGT);
+      if (wtid == 0) {
         tc::fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < NP / 16; ++ks)
@@ -228,32 +246,39 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
                           tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
         tc::mma_commit(mbar);
       }
+      close_step(st, TPR == 2 ? psum[row] + psum[128 + row] : psum[row], t - 1, Tn);
       const int ot = o_next;
       if (t + 1 < Tn) o_next = __ldg(o + t + 1);
       if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
       const bool live = t < Tn && !st.dead && !st.bad;
       if (live) st.F += st.f;
       const float2 fac2 = make_float2(exp2i(-st.f), exp2i(-st.f));
-      const bool ok_e = tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
-      const bool ok_m = tc::mbar_wait_bounded(mbar, mphase, kWaitLimit);
+      // one warp polls both mbarriers; the rest of the warpgroup waits in the
+      // hardware barrier (no issue slots spent spinning)
+      bool ok = true;
+      if (wtid < 32) {
+        ok = tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
+        ok = tc::mbar_wait_bounded(mbar, mphase, kWaitLimit) && ok;
+      }
       ephase ^= 1;
       mphase ^= 1;
-      // the whole warpgroup agrees before anyone leaves the loop
-      if (!tc::bar_and(1 + wg, 128, ok_e && ok_m)) {
+      // the whole warpgroup agrees before anyone leaves the loop (and every
+      // thread has read the partial sums before they are overwritten)
+      if (!tc::bar_and(1 + wg, WGT, ok)) {
         aborted = true;
         break;
       }
       tc::fence_after_sync();
-      float sigma = 0.f;
+      float part = 0.f;
 #pragma unroll
-      for (int c = 0; c < NP / 32; ++c) {
+      for (int c = 0; c < CH; ++c) {
         float y[32];
-        tc::tmem_ld32(d_tmem + lane_off + (uint32_t)(c * 32), y);
+        tc::tmem_ld32(d_mine + (uint32_t)(c * 32), y);
         tc::tmem_ld_wait();
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float4 b = *reinterpret_cast<const float4*>(erow + (8 * c + q) * 16);
+          const float4 b = *reinterpret_cast<const float4*>(erow + (h * HALF + 32 * c + 4 * q) * 4);
           float2 lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
                                             make_float2(b.x, b.y)), fac2);
           float2 hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
@@ -262,23 +287,26 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
           acc = __fadd2_rn(acc, __fadd2_rn(lo, hi));
           y[4 * q] = lo.x; y[4 * q + 1] = lo.y; y[4 * q + 2] = hi.x; y[4 * q + 3] = hi.y;
         }
-        sigma += acc.x + acc.y;
+        part += acc.x + acc.y;
         uint32_t w[16];
         pack32(y, w);
-        tc::tmem_st16(x_tmem + lane_off + (uint32_t)(16 * c), w);
+        tc::tmem_st16(x_mine + (uint32_t)(16 * c), w);
       }
       tc::tmem_st_wait();
-      close_step(st, sigma, t, Tn);
-      if (t + 1 < Tmax) {
+      psum[h * 128 + row] = part;
+      if (t + 1 < Tmax && h == 0) {
         const int on = (t + 1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0;
         stage_emission<NP>(eslot, Bk, on, ebar);
       }
     }
-    if (aborted && lane == 0) {
+    tc::bar_sync(1 + wg, WGT);
+    if (!aborted && Tmax > 0)
+      close_step(st, TPR == 2 ? psum[row] + psum[128 + row] : psum[row], Tmax - 1, Tn);
+    if (aborted && lane == 0 && h == 0) {
       misc[2] = 1;
       set_status(a.status, HMM_STATUS_TIMEOUT);
     }
-    if (has) {
+    if (has && h == 0) {
       float out = st.ll;
       if (st.bad || aborted) out = __int_as_float(0x7fc00000);
       else if (st.dead) out = -INFINITY;
@@ -297,7 +325,7 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
       __syncthreads();
       if (misc[3]) {
         __threadfence();
-        if (has) {
+        if (has && h == 0) {
           const float* rp = a.loglik + (size_t)s * K;
           float best = __ldcg(rp);
           int arg = isnan(best) ? -1 : 0;
@@ -315,7 +343,7 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
   // teardown: no MMA or copy of ours may still be in flight
   tc::fence_before_sync();
   __syncthreads();
-  if (misc[2] && row == 0) {
+  if (misc[2] && wtid == 0) {
     tc::mbar_wait_bounded(mbar, mphase, kWaitLimit);
     tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
   }
@@ -324,23 +352,26 @@ __global__ void __launch_bounds__(256, 1) hmm_forward_mma(MmaFwdLaunch a) {
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int NP>
+template <int NP, int NT, int TPR>
 static cudaError_t launch_mma_t(const MmaFwdLaunch& a, cudaStream_t st) {
-  auto kern = hmm_forward_mma<NP>;
+  auto kern = hmm_forward_mma<NP, NT, TPR>;
+  using L = MmaFwdSmem<NP, NT, TPR>;
   // one CTA per SM (it holds all 512 tensor-memory columns): ask for more
   // than half of the shared memory even when the tiles need less
-  const int smem = MmaFwdSmem<NP>::TOTAL > 120 * 1024 ? MmaFwdSmem<NP>::TOTAL : 120 * 1024;
+  const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   int blocks = num_sms();
   if (blocks > a.n_items) blocks = a.n_items > 0 ? a.n_items : 1;
-  kern<<<blocks, 256, smem, st>>>(a);
+  kern<<<blocks, kMmaThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+int mma_tiles_per_cta(int NP) { return NP == 64 ? 4 : 2; }
+
 cudaError_t launch_forward_mma(int NP, const MmaFwdLaunch& a, cudaStream_t st) {
-  if (NP == 64) return launch_mma_t<64>(a, st);
-  if (NP == 128) return launch_mma_t<128>(a, st);
+  if (NP == 64) return launch_mma_t<64, 4, 1>(a, st);
+  if (NP == 128) return launch_mma_t<128, 2, 2>(a, st);
   return cudaErrorInvalidValue;
 }
 

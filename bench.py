@@ -57,9 +57,12 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--n-seqs", type=int, default=None, help="smaller batch (profiling only)")
+    ap.add_argument("--lanes", default=None,
+                    help="fixed lanes per pair 'fwd,viterbi,paths,adjoint' instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "large", "training"],
-                    help="batched: the full step (default); large/training: tensor-core forward")
+                    choices=[WORKLOAD, "large", "gradient", "training"],
+                    help="batched: the full step (default); large: tensor-core forward; "
+                         "gradient/training: the learning step")
     return ap.parse_args()
 
 
@@ -264,7 +267,16 @@ def run_gpu(args):
     step()
     torch.cuda.synchronize()
     from paper_1310_3322_gb300 import tune
-    tuning = tune.autotune(*probs, seqs, lab, repeats=3, cache=None)
+    if args.lanes:
+        # fixed lanes per pair (forward, viterbi scores, viterbi paths, adjoint)
+        npad = tune.n_pad(N)
+        tuning = {}
+        for op, g in zip((hmm.HMM_OP_FORWARD, hmm.HMM_OP_VITERBI, hmm.HMM_TUNE_VITERBI_PATHS,
+                          hmm.HMM_OP_FORWARD_BACKWARD), (int(x) for x in args.lanes.split(","))):
+            hmm.hmm_set_tuning(op, npad, g)
+            tuning[tune.KERNEL_OF[op]] = {"lanes": g, "ms": {}}
+    else:
+        tuning = tune.autotune(*probs, seqs, lab, repeats=3, cache=None)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -510,6 +522,132 @@ def run_forward_only(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_steps(torch, step, steps, flush):
+    """Mean ms of `steps` calls of step() with an L2 flush before each."""
+    evs = []
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([x.elapsed_time(y) for x, y in evs]))
+
+
+def run_learning(args):
+    """One learning step on the gradient / training configurations: softmax
+    rows -> forward + adjoint of every sequence against its labelled model ->
+    logit gradient -> Adam, captured in a CUDA graph; units = sum_s T_s. The
+    plain all-models forward kernels on the same data are reported beside it."""
+    import torch
+    from paper_1310_3322_gb300 import hmm, synth, tune
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.make_workload(args.workload, n_seqs=args.n_seqs,
+                            seed=synth.SEEDS[args.workload] + rank)
+    K, N, M = w.K, w.N, w.M
+    sumT = int(w.lengths.astype(np.int64).sum())
+    seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
+    lab = seqs.labelled(torch.from_numpy(w.labels).to(dev))
+    sizes = [K * N, K * N * N, K * N * M]
+    shapes = [(K, N), (K, N, N), (K, N, M)]
+    logits = torch.from_numpy(np.concatenate([x.ravel() for x in w.logits]).astype(np.float32)).to(dev)
+    grads = torch.zeros_like(logits)
+    m_, v_ = torch.zeros_like(logits), torch.zeros_like(logits)
+    counter = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def views(flat):
+        out, o = [], 0
+        for n, sh in zip(sizes, shapes):
+            out.append(flat[o:o + n].view(*sh))
+            o += n
+        return out
+
+    lg, gr = views(logits), views(grads)
+    probs = [torch.empty(sh, device=dev) for sh in shapes]
+    fll = torch.empty(w.S, device=dev)
+    cnts = [torch.empty(sh, device=dev) for sh in shapes]
+    ws = hmm.Workspace(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        hmm.hmm_softmax_rows(*lg, out=probs)
+        hmm.hmm_forward_backward(*probs, lab, loglik=fll, counts=cnts, workspace=ws)
+        hmm.hmm_softmax_grad(*probs, *cnts, out=gr)
+        hmm.hmm_adam_step(logits, grads, m_, v_, 1e-3, grad_scale=-1.0 / sumT,
+                          step_counter=counter)
+
+    step()
+    torch.cuda.synchronize()
+    tuning = tune.autotune(*probs, seqs, lab, ops=[hmm.HMM_OP_FORWARD_BACKWARD], cache=None)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(ws) == 0
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = _time_steps(torch, graph.replay, args.steps, flush)
+    clk = clocks.stop()
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, step, args.steps, flush)
+    kt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    adj_ms = kt["adjoint"][1] / max(kt["adjoint"][0], 1)
+    flops = (8 * N * N + 10 * N) * sumT
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (adj_ms / 1e3) / 1e12
+
+    # the plain per-sequence forward kernels on the same data (all K models)
+    fwd = {}
+    ll = torch.empty((w.S, K), device=dev)
+    am = torch.empty(w.S, dtype=torch.int32, device=dev)
+    for name, prec in (("fp32_simt", hmm.HMM_FP32), ("bf16_mma", hmm.HMM_BF16_MMA)):
+        if N > hmm.hmm_max_states(hmm.HMM_OP_FORWARD, prec) or (prec == hmm.HMM_BF16_MMA and N <= 32):
+            continue
+        def fstep(prec=prec):
+            hmm.hmm_forward(*probs, seqs, precision=prec, loglik=ll, argmax=am, workspace=ws)
+        fstep()
+        fms = _time_steps(torch, fstep, args.steps, flush)
+        fwd[name] = {"ms": fms, "obs_models_per_s": sumT * K / (fms / 1e3),
+                     "tflops": 2.0 * N * N * sumT * K / (fms / 1e3) / 1e12}
+    line = {
+        "metric": METRIC, "value": sumT / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} K={K} N={N} M={M} S={w.S} (softmax rows, "
+                               "forward+adjoint against the labelled model, logit gradient, "
+                               "Adam; CUDA graph)", "units_per_step": sumT,
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "lanes_per_pair": {k: v["lanes"] for k, v in tuning.items()}},
+        "roofline": {"bound": "alu", "kernel": "adjoint", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "launch_ms": adj_ms,
+                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
+                     "traffic": None},
+        "clocks": clk,
+        "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]},
+        "forward_all_models": fwd,
+        "gpu_launches": 8 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -517,8 +655,11 @@ def main():
         return
     import __graft_entry__
     __graft_entry__.build()
-    if args.workload != WORKLOAD:
+    if args.workload == "large":
         run_forward_only(args)
+        return
+    if args.workload in ("gradient", "training"):
+        run_learning(args)
         return
     run_gpu(args)
 

@@ -65,7 +65,7 @@ static int pad_states(int N) {
 static const int kCand[4][5][5] = {
     /* forward */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
     /* viterbi scores */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
-    /* fb      */ {{4, 2, 0}, {8, 4, 0}, {8, 16, 0}, {32, 0}, {0}},
+    /* fb      */ {{4, 2, 0}, {8, 4, 0}, {8, 16, 0}, {32, 0}, {32, 0}},
     /* viterbi paths */ {{4, 2, 1, 0}, {8, 4, 2, 0}, {8, 16, 4, 0}, {16, 32, 8, 0}, {32, 0}},
 };
 static int g_tuning[4][5] = {{0}};
@@ -229,7 +229,7 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
 static int max_states(int op, int precision) {
   if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 128;
   if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
-  return op == HMM_OP_FORWARD_BACKWARD ? 32 : 64;
+  return 64;
 }
 
 static int check_precision(int precision, int op) {
@@ -531,7 +531,7 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
   const int G = lanes_for(HMM_OP_FORWARD_BACKWARD, L.NP);
   const int C = ckpt_stride(seqs->max_len);
   const int NC = (seqs->max_len > 0 ? (seqs->max_len - 1) / C : 0) + 1;
-  const size_t smem = fb_smem_bytes(L.NP, G, C, NC, dims.M);
+  const size_t smem = fb_smem_bytes(L.NP, G, C, NC, dims.M, 1);  // one warp per block at least
   if (smem > 227 * 1024)
     return fail(HMM_ERR_UNSUPPORTED,
                 "adjoint shared memory %zu bytes above 227 KB (N=%d M=%d max_len=%d)", smem,

@@ -446,28 +446,32 @@ hmm_fb_simt(FbLaunch a) {
 // --------------------------------------------------------------------------
 // dispatch
 // --------------------------------------------------------------------------
-size_t fb_smem_bytes(int NP, int G, int C, int NC, int M) {
+// Shared memory of a block of `warps` warps (the per-pair regions of FbLayout).
+size_t fb_smem_bytes(int NP, int G, int C, int NC, int M, int warps) {
   const int PP = 32 / G;
   const int XS = NP + 4;
   int n = 4 * XS + NC * NP + 2 * C * NP + NC + 2 * C + NP * (M + 1);
   n = (n + 3) & ~3;
-  return (size_t)kWarpsPerBlock * PP * n * sizeof(float);
+  return (size_t)warps * PP * n * sizeof(float);
 }
 
 template <int NP, int G>
 static cudaError_t launch_fb_t(const FbLaunch& a, cudaStream_t st) {
   auto kern = hmm_fb_simt<NP, G>;
-  const size_t smem = fb_smem_bytes(NP, G, a.ckpt, a.nck, a.seq.M);
+  // as many warps per block (up to 4) as the per-pair buffers allow
+  int warps = kWarpsPerBlock;
+  while (warps > 1 && fb_smem_bytes(NP, G, a.ckpt, a.nck, a.seq.M, warps) > 227 * 1024) warps >>= 1;
+  const size_t smem = fb_smem_bytes(NP, G, a.ckpt, a.nck, a.seq.M, warps);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int blocks = num_sms() * per_sm;
-  const int need = (a.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int need = (a.n_items + warps - 1) / warps;
   if (blocks > need) blocks = need > 0 ? need : 1;
-  kern<<<blocks, kWarpsPerBlock * 32, smem, st>>>(a);
+  kern<<<blocks, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -479,6 +483,7 @@ cudaError_t launch_fb(int NP, int G, const FbLaunch& a, cudaStream_t st) {
   HMM_FB_CASE(8, 4) HMM_FB_CASE(8, 8)
   HMM_FB_CASE(16, 8) HMM_FB_CASE(16, 16)
   HMM_FB_CASE(32, 32)
+  HMM_FB_CASE(64, 32)
   return cudaErrorInvalidValue;
 }
 

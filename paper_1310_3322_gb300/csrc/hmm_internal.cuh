@@ -387,7 +387,7 @@ struct FbLaunch {
   int nck;           // checkpoints per pair (ceil(max_len / C))
 };
 cudaError_t launch_fb(int NP, int G, const FbLaunch& a, cudaStream_t st);
-size_t fb_smem_bytes(int NP, int G, int C, int NC, int M);
+size_t fb_smem_bytes(int NP, int G, int C, int NC, int M, int warps);
 
 struct MmaFwdLaunch {
   SeqArgs seq;

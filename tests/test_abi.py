@@ -65,7 +65,7 @@ def test_workspace_size_is_host_only_and_monotone(lib):
     assert out.value >= 4 * 128 * 128 * 4
     assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_VITERBI,
                                   ctypes.byref(out)) == hmm.HMM_ERR_UNSUPPORTED
-    assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 33, 8), ctypes.byref(q),
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 65, 8), ctypes.byref(q),
                                   hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
         == hmm.HMM_ERR_UNSUPPORTED
 
@@ -106,7 +106,7 @@ def test_viterbi_and_adjoint_argument_errors(lib):
     assert lib.hmm_forward_backward(d, _fake(5), _fake(6), _fake(7), ctypes.byref(q), None,
                                     hmm.HMM_FP32, _fake(8), None, _fake(11), _fake(12),
                                     _fake(9), 1 << 30, None) == hmm.HMM_ERR_ARG
-    big = hmm.hmm_dims_t(2, 33, 8)
+    big = hmm.hmm_dims_t(2, 65, 8)
     assert lib.hmm_forward_backward(big, _fake(5), _fake(6), _fake(7), ctypes.byref(q), None,
                                     hmm.HMM_FP32, _fake(8), _fake(10), _fake(11), _fake(12),
                                     _fake(9), 1 << 30, None) == hmm.HMM_ERR_UNSUPPORTED
@@ -138,7 +138,7 @@ def test_tuning_table(lib):
     hmm.hmm_set_tuning(hmm.HMM_OP_FORWARD, 16, 0)
     assert hmm.hmm_get_tuning(hmm.HMM_OP_FORWARD, 16) == 2
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD) == 64
-    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD) == 32
+    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD) == 64
 
 
 def test_last_error_is_thread_local(lib):

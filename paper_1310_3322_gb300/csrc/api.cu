@@ -105,7 +105,26 @@ static int ckpt_stride(int max_len) {
   return C < 1 ? 1 : C;
 }
 
-static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op) {
+// Checkpoint images per CTA of the tensor-core adjoint for tiles up to max_len.
+static int fb_mma_nsmax(int max_len) {
+  const int l1 = max_len < 8192 ? max_len : 8192;
+  int ns = l1 > 0 ? (l1 + fb_mma_segment(l1) - 1) / fb_mma_segment(l1) : 1;
+  const int big = (int)ceil(sqrt((double)(max_len > 0 ? max_len : 1))) + 1;
+  if (max_len > 8192 && big > ns) ns = big;
+  return ns < 1 ? 1 : ns;
+}
+
+static int fb_mma_tile_cap(const hmm_dims_t& d, const hmm_seqs_t& q) {
+  const int64_t chunks = ((int64_t)(q.S > 0 ? q.S : 0) + 127) / 128;
+  const int64_t cap = q.model_of_seq ? chunks + d.K : chunks * d.K;
+  return (int)(cap < 1 ? 1 : cap);
+}
+
+static int fb_mma_grid(const hmm_dims_t& d, int NP) {
+  return num_sms() * fb_mma_ctas_per_sm(NP, d.M);
+}
+
+static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma = false) {
   WsLayout L;
   memset(&L, 0, sizeof(L));
   const int NP = pad_states(d.N);
@@ -126,12 +145,36 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op) {
     L.bp_cap = (q.total_obs > 0 ? q.total_obs : 0) * (int64_t)NP;
     L.bp = off; off = align256(off + (size_t)L.bp_cap);
   }
-  if (op == HMM_OP_FORWARD_BACKWARD) {
+  if (op == HMM_OP_FORWARD_BACKWARD && !mma) {
     L.slot_floats = (int64_t)NP + (int64_t)NP * NP + (int64_t)NP * d.M;
     L.slots = q.model_of_seq ? (int64_t)S : (int64_t)S * d.K;
     L.nchunks = first_chunks((int)S);
     L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
     L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
+  }
+  if (op == HMM_OP_FORWARD_BACKWARD && mma) {
+    // tensor-core adjoint: tile plan, per-tile count slots, per-CTA buffers
+    const int cap = fb_mma_tile_cap(d, q);
+    const size_t img = (size_t)128 * NP * 2;
+    L.slot_floats = (int64_t)NP + (int64_t)NP * NP + (int64_t)NP * d.M;
+    L.slots = cap;
+    L.nchunks = first_chunks(cap);
+    L.m_sorted = off; off = align256(off + S * 4);
+    L.m_tmp = off; off = align256(off + S * 4);
+    L.m_tiles = off; off = align256(off + (size_t)cap * 6 * 4);
+    L.m_ntiles = off; off = align256(off + 4);
+    L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
+    L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
+    const int grid = fb_mma_grid(d, NP);
+    const int max_len = q.max_len > 0 ? q.max_len : 1;
+    L.m_grid = grid;
+    L.m_ckpt_bytes = (int64_t)fb_mma_nsmax(max_len) * img;
+    L.m_scr_bytes = (int64_t)fb_mma_segment(max_len) * img;
+    L.m_gexp_bytes = (int64_t)align256((size_t)max_len * 128);
+    L.m_ckpt = off; off = align256(off + (size_t)grid * L.m_ckpt_bytes);
+    L.m_scr = off; off = align256(off + (size_t)grid * L.m_scr_bytes);
+    L.m_gexp = off; off = align256(off + (size_t)grid * L.m_gexp_bytes);
+    L.m_gbuf = off; off = align256(off + (size_t)grid * 128 * NP * 4);
   }
   L.total = off;
   return L;
@@ -227,14 +270,17 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
 }
 
 static int max_states(int op, int precision) {
-  if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 128;
+  if ((op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD) &&
+      (precision == HMM_BF16_MMA || precision == HMM_AUTO))
+    return 128;
   if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
   return 64;
 }
 
 static int check_precision(int precision, int op) {
   if (precision == HMM_FP32 || precision == HMM_AUTO) return HMM_OK;
-  if (precision == HMM_BF16_MMA && op == HMM_OP_FORWARD) return HMM_OK;
+  if (precision == HMM_BF16_MMA && (op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD))
+    return HMM_OK;
   if (precision == HMM_BF16_MMA || precision == HMM_TF32_MMA)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core precision %d not available for op %d in this build",
                 precision, op);
@@ -244,6 +290,13 @@ static int check_precision(int precision, int op) {
 // Tensor-core forward: N in (32, 128], every sequence against every model.
 static bool use_mma_forward(const hmm_dims_t& d, int precision) {
   return precision == HMM_BF16_MMA || (precision == HMM_AUTO && d.N > 64);
+}
+
+// Tensor-core adjoint: N in (32, 128]; the library's choice above N = 32
+// (the FP32 SIMT adjoint holds a whole N = 64 pair in one warp's registers
+// and spills there).
+static bool use_mma_fb(const hmm_dims_t& d, int precision) {
+  return precision == HMM_BF16_MMA || (precision == HMM_AUTO && d.N > 32);
 }
 
 // ---------------------------------------------------------------------------
@@ -288,6 +341,104 @@ struct Timed {
   }
 };
 
+static int zero_counts(const hmm_dims_t& d, float* cnt_pi, float* cnt_A, float* cnt_B,
+                       cudaStream_t st) {
+  const size_t n = (size_t)d.K * d.N;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(cnt_pi, 0, n * 4, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(cnt_A, 0, n * d.N * 4, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(cnt_B, 0, n * d.M * 4, st)) != cudaSuccess)
+    return cuda_fail(e, "memset");
+  return HMM_OK;
+}
+
+// hmm_forward_backward on the tensor cores (arguments already checked except
+// the workspace): setup, tile plan, adjoint, fixed-order reduction.
+static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* weight,
+                  float* loglik, float* cnt_pi, float* cnt_A, float* cnt_B, void* ws,
+                  size_t ws_bytes, hmm_stream_t stream, const float* pi, const float* A,
+                  const float* B) {
+  const int NP = pad_states(dims.N);
+  if (!fb_mma_supported(NP, dims.M))
+    return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports M <= 256 (M=%d)", dims.M);
+  if (seqs->model_of_seq && dims.K > 65536)
+    return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports K <= 65536 labelled models");
+  const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD, true);
+  int rc;
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (seqs->S == 0) return zero_counts(dims, cnt_pi, cnt_A, cnt_B, st);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  const bool labelled = seqs->model_of_seq != nullptr;
+  const int cap = (int)L.slots;
+  int32_t* tiles = at<int32_t>(ws, L.m_tiles);
+  MmaPlanArgs p;
+  p.S = seqs->S; p.K = dims.K; p.labelled = labelled ? 1 : 0;
+  p.seqlen = at<int32_t>(ws, L.seqlen);
+  p.model_of_seq = seqs->model_of_seq;
+  p.loglik = loglik;
+  p.sorted = at<int32_t>(ws, L.m_sorted);
+  p.tmp = at<int32_t>(ws, L.m_tmp);
+  p.tile_start = tiles; p.tile_rows = tiles + cap; p.tile_model = tiles + 2 * cap;
+  p.tile_len = tiles + 3 * cap; p.tile_order = tiles + 4 * cap; p.tile_tmp = tiles + 5 * cap;
+  p.n_tiles_cap = cap;
+  p.n_tiles = at<int32_t>(ws, L.m_ntiles);
+  {
+    Timed tm(T_SETUP, st);
+    e = launch_setup(s, st);
+    if (e == cudaSuccess) e = launch_mma_plan(p, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+
+  MmaFbLaunch f;
+  f.seq = seq_args(dims, *seqs, L, ws);
+  f.mod = model_args(L, ws);
+  f.weight = weight;
+  f.loglik = loglik;
+  f.sorted = p.sorted;
+  f.tile_start = p.tile_start; f.tile_rows = p.tile_rows; f.tile_model = p.tile_model;
+  f.tile_len = p.tile_len; f.tile_order = p.tile_order; f.n_tiles = p.n_tiles;
+  f.labelled = p.labelled;
+  f.slots = at<float>(ws, L.partial);
+  f.slot_floats = L.slot_floats;
+  f.ckpt = at<uint8_t>(ws, L.m_ckpt);
+  f.scr = at<uint8_t>(ws, L.m_scr);
+  f.gexp = at<int8_t>(ws, L.m_gexp);
+  f.gbuf = at<float>(ws, L.m_gbuf);
+  f.ckpt_bytes = L.m_ckpt_bytes;
+  f.scr_bytes = L.m_scr_bytes;
+  f.gexp_bytes = L.m_gexp_bytes;
+  f.queue = &at<WsHeader>(ws, 0)->queue[3];
+  f.status = &at<WsHeader>(ws, 0)->status;
+  const int grid = cap < L.m_grid ? cap : L.m_grid;
+  {
+    Timed tm(T_FB, st);
+    e = launch_fb_mma(NP, dims.M, grid, f, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint launch");
+
+  ReduceLaunch r;
+  r.partial = f.slots;
+  r.red1 = at<float>(ws, L.red1);
+  r.model_of_seq = p.tile_model;  // every slot is one tile of one model
+  r.seqlen = p.tile_len;          // -1 marks unused slots
+  r.S = cap; r.K = dims.K; r.N = dims.N; r.M = dims.M; r.NP = NP;
+  r.slot_floats = L.slot_floats;
+  r.nchunks = L.nchunks;
+  r.cnt_pi = cnt_pi; r.cnt_A = cnt_A; r.cnt_B = cnt_B;
+  {
+    Timed tm(T_REDUCE, st);
+    e = launch_reduce(r, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+  return HMM_OK;
+}
+
 }  // namespace hmmgb
 
 using namespace hmmgb;
@@ -309,7 +460,15 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
   if (rc) return rc;
   if (!seqs) return fail(HMM_ERR_ARG, "seqs is NULL");
   if (seqs->S < 0 || seqs->total_obs < 0) return fail(HMM_ERR_ARG, "negative S or total_obs");
-  *bytes = make_layout(dims, *seqs, op).total;
+  size_t need = 0;
+  if (op != HMM_OP_FORWARD_BACKWARD || dims.N <= 64) need = make_layout(dims, *seqs, op).total;
+  if (op == HMM_OP_FORWARD_BACKWARD && dims.N > 32) {
+    if (!fb_mma_supported(pad_states(dims.N), dims.M))
+      return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports M <= 256 (M=%d)", dims.M);
+    const size_t m = make_layout(dims, *seqs, op, true).total;
+    if (m > need) need = m;
+  }
+  *bytes = need;
   return HMM_OK;
 }
 
@@ -526,6 +685,11 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
     return fail(HMM_ERR_ARG, "count outputs NULL or misaligned");
   if (seqs->S > 0 && (!loglik || !al(loglik, 4))) return fail(HMM_ERR_ARG, "loglik NULL or misaligned");
   if (weight && !al(weight, 4)) return fail(HMM_ERR_ARG, "weight misaligned");
+  if (use_mma_fb(dims, precision)) {
+    if (dims.N <= 32)
+      return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint needs N > 32 (N=%d: use HMM_FP32)", dims.N);
+    return fb_mma(dims, seqs, weight, loglik, cnt_pi, cnt_A, cnt_B, ws, ws_bytes, stream, pi, A, B);
+  }
   const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD);
   if ((rc = check_ws(ws, ws_bytes, L))) return rc;
   const int G = lanes_for(HMM_OP_FORWARD_BACKWARD, L.NP);

@@ -35,6 +35,10 @@ struct WsLayout {
   int64_t slots;       // adjoint partial slots
   int64_t slot_floats; // floats per slot (NP + NP*NP + NP*M)
   int nchunks;         // first-level reduction chunks
+  // tensor-core adjoint
+  size_t m_sorted, m_tmp, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf;
+  int64_t m_ckpt_bytes, m_scr_bytes, m_gexp_bytes;
+  int m_grid;
 };
 
 // ---------------------------------------------------------------------------
@@ -402,6 +406,65 @@ struct MmaFwdLaunch {
 };
 cudaError_t launch_forward_mma(int NP, const MmaFwdLaunch& a, cudaStream_t st);
 int mma_tiles_per_cta(int NP);  // 128-row tiles one CTA of the tensor-core forward holds
+
+// Plan of the tensor-core adjoint: the rows of every 128-row tile share one
+// model, and the tile composition is a deterministic function of the input
+// (stable sort by model, then decreasing length, then sequence index), so the
+// per-tile count sums are bitwise reproducible.
+struct MmaPlanArgs {
+  int S, K, labelled;
+  const int32_t* seqlen;        // validated lengths (-1 = invalid)
+  const int32_t* model_of_seq;  // labelled mode
+  float* loglik;                // rows in no tile: 0 (T = 0) or NaN (invalid)
+  int32_t* sorted;              // [S] tile rows, in tile order
+  int32_t* tmp;                 // [S] scratch
+  int32_t* tile_start;          // [cap] first row (index into sorted)
+  int32_t* tile_rows;           // [cap] rows in the tile (1..128)
+  int32_t* tile_model;          // [cap]
+  int32_t* tile_len;            // [cap] longest row (-1 for unused entries)
+  int32_t* tile_order;          // [cap] tiles by decreasing length
+  int32_t* tile_tmp;            // [cap] scratch
+  int n_tiles_cap;
+  int32_t* n_tiles;             // device count
+};
+cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st);
+
+struct MmaFbLaunch {
+  SeqArgs seq;
+  ModelArgs mod;                // probability tables padded to NP
+  const float* weight;          // [S] or [S][K], NULL = 1
+  float* loglik;                // [S] or [S][K]
+  const int32_t* sorted;
+  const int32_t* tile_start;
+  const int32_t* tile_rows;
+  const int32_t* tile_model;
+  const int32_t* tile_len;
+  const int32_t* tile_order;
+  const int32_t* n_tiles;
+  int labelled;
+  float* slots;                 // [tile][slot_floats] per-tile counts
+  int64_t slot_floats;
+  uint8_t* ckpt;                // per CTA: checkpoint images
+  uint8_t* scr;                 // per CTA: recomputed segment images
+  int8_t* gexp;                 // per CTA: [max_len][128] forward scale exponents
+  float* gbuf;                  // per CTA: [128][NP] gamma_1 rows
+  int64_t ckpt_bytes, scr_bytes, gexp_bytes;  // per-CTA strides
+  int32_t* queue;
+  int32_t* status;
+};
+cudaError_t launch_fb_mma(int NP, int M, int grid, const MmaFbLaunch& a, cudaStream_t st);
+// Checkpoint stride of a tile whose longest row has L steps, and the per-CTA
+// buffer sizes of the tensor-core adjoint for sequences up to max_len.
+__host__ __device__ inline int fb_mma_segment(int L) {
+  long long c = (long long)sqrtf((float)(L > 1 ? L : 1));
+  if (c < 1) c = 1;
+  while (c * c < L) ++c;                       // ceil(sqrt(L))
+  while (c > 1 && (c - 1) * (c - 1) >= L) --c;
+  if (L <= 8192 && c > 16) c = 16;             // recompute buffer sized for L2
+  return (int)c;
+}
+int fb_mma_ctas_per_sm(int NP, int M);
+bool fb_mma_supported(int NP, int M);
 
 struct ReduceLaunch {
   const float* partial;

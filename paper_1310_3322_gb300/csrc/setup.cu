@@ -152,6 +152,192 @@ cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
+// plan of the tensor-core adjoint (one 1024-thread block)
+// ---------------------------------------------------------------------------
+// One stable counting-sort pass: `out` receives `in` ordered by digit(item) in
+// [0, 256), items with equal digits keeping their input order. Chunks of 1024
+// items are ranked with warp match masks and per-warp digit counts.
+template <typename DigitFn>
+__device__ void stable_pass(const int32_t* in, int32_t* out, int n, DigitFn digit, int* base,
+                            int* wh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < 256) base[tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += kPlanThreads) atomicAdd(&base[digit(in[i])], 1);
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the 256 digit counts
+    int v[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { v[q] = base[lane * 8 + q]; sum += v[q]; }
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(HMM_FULL_MASK, x, o);
+      if (lane >= o) x += y;
+    }
+    int run = x - sum;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { base[lane * 8 + q] = run; run += v[q]; }
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
+    const int i = c0 + tid;
+    const bool valid = i < n;
+    const int item = valid ? in[i] : 0;
+    const int d = valid ? digit(item) : 256;
+    for (int q = tid; q < 32 * 256; q += kPlanThreads) wh[q] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(HMM_FULL_MASK, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wh[warp * 256 + d] = __popc(peers);
+    __syncthreads();
+    if (tid < 256) {
+      int run = base[tid];
+      for (int w = 0; w < 32; ++w) {
+        const int c = wh[w * 256 + tid];
+        wh[w * 256 + tid] = run;
+        run += c;
+      }
+      base[tid] = run;
+    }
+    __syncthreads();
+    if (valid) out[wh[warp * 256 + d] + rank] = item;
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int len_key(int T) { return kLenBuckets - 1 - length_bucket(T); }
+
+// Longest row of a tile: the length buckets above 255 are wider than one
+// length, so the first row of a tile is not always the longest.
+__device__ int tile_max_len(const int32_t* seqlen, const int32_t* sorted, int p, int rows) {
+  int mx = 0;
+  for (int q = p; q < p + rows; ++q) mx = max(mx, seqlen[sorted[q]]);
+  return mx;
+}
+
+// First position p in [0, n) with key(p) >= k (keys non-decreasing).
+template <typename KeyFn>
+__device__ int lower_bound_pos(int n, int k, KeyFn key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (key(mid) < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
+  __shared__ int base[256];
+  __shared__ int wh[32 * 256];
+  __shared__ int itmp[32];
+  __shared__ int total;
+  const int tid = threadIdx.x;
+
+  // rows with T >= 1, in index order; the others get their log-likelihood here
+  int n = 0;
+  for (int c0 = 0; c0 < a.S; c0 += kPlanThreads) {
+    const int s = c0 + tid;
+    const int T = s < a.S ? a.seqlen[s] : 0;
+    const int keep = (s < a.S && T >= 1) ? 1 : 0;
+    if (s < a.S && !keep) {
+      const float v = T == 0 ? 0.f : __int_as_float(0x7fc00000);
+      if (a.labelled) a.loglik[s] = v;
+      else
+        for (int k = 0; k < a.K; ++k) a.loglik[(size_t)s * a.K + k] = v;
+    }
+    const int pos = block_exclusive_scan<int>(keep, itmp, &total);
+    if (keep) a.tmp[n + pos] = s;
+    n += total;
+    __syncthreads();
+  }
+
+  // stable sort: by decreasing length (two 8-bit digits of the length key),
+  // then (labelled) by model
+  const int32_t* seqlen = a.seqlen;
+  const int32_t* mos = a.model_of_seq;
+  auto lo8 = [seqlen](int s) { return len_key(seqlen[s]) & 255; };
+  auto hi8 = [seqlen](int s) { return len_key(seqlen[s]) >> 8; };
+  stable_pass(a.tmp, a.sorted, n, lo8, base, wh);
+  stable_pass(a.sorted, a.tmp, n, hi8, base, wh);
+  const int32_t* res = a.tmp;
+  if (a.labelled) {
+    auto m0 = [mos](int s) { return mos[s] & 255; };
+    stable_pass(a.tmp, a.sorted, n, m0, base, wh);
+    res = a.sorted;
+    if (a.K > 256) {
+      auto m1 = [mos](int s) { return (mos[s] >> 8) & 255; };
+      stable_pass(a.sorted, a.tmp, n, m1, base, wh);
+      res = a.tmp;
+    }
+  }
+  if (res != a.sorted) {
+    for (int i = tid; i < n; i += kPlanThreads) a.sorted[i] = res[i];
+    __syncthreads();
+  }
+
+  // tiles of at most 128 rows of one model
+  int n_tiles = 0;
+  if (a.labelled) {
+    const int32_t* sorted = a.sorted;
+    auto model_at = [sorted, mos](int p) { return mos[sorted[p]]; };
+    for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
+      const int p = c0 + tid;
+      int flag = 0, k = 0, gs = 0, ge = 0;
+      if (p < n) {
+        k = model_at(p);
+        gs = lower_bound_pos(n, k, model_at);
+        ge = lower_bound_pos(n, k + 1, model_at);
+        flag = ((p - gs) % 128) == 0 ? 1 : 0;
+      }
+      const int id = n_tiles + block_exclusive_scan<int>(flag, itmp, &total);
+      if (flag && id < a.n_tiles_cap) {
+        const int rows = min(128, ge - p);
+        a.tile_start[id] = p;
+        a.tile_rows[id] = rows;
+        a.tile_model[id] = k;
+        a.tile_len[id] = tile_max_len(seqlen, sorted, p, rows);
+        a.tile_order[id] = id;
+      }
+      n_tiles += total;
+      __syncthreads();
+    }
+    n_tiles = min(n_tiles, a.n_tiles_cap);
+    // longest tiles first (stable in tile index)
+    const int32_t* tl = a.tile_len;
+    auto t0 = [tl](int t) { return len_key(tl[t]) & 255; };
+    auto t1 = [tl](int t) { return len_key(tl[t]) >> 8; };
+    stable_pass(a.tile_order, a.tile_tmp, n_tiles, t0, base, wh);
+    stable_pass(a.tile_tmp, a.tile_order, n_tiles, t1, base, wh);
+  } else {
+    // every length-sorted chunk of 128 rows against every model, chunk-major
+    // (already longest first)
+    const int n_chunks = (n + 127) / 128;
+    n_tiles = min(n_chunks * a.K, a.n_tiles_cap);
+    for (int id = tid; id < n_tiles; id += kPlanThreads) {
+      const int c = id / a.K, k = id % a.K;
+      const int rows = min(128, n - 128 * c);
+      a.tile_start[id] = 128 * c;
+      a.tile_rows[id] = rows;
+      a.tile_model[id] = k;
+      a.tile_len[id] = tile_max_len(seqlen, a.sorted, 128 * c, rows);
+      a.tile_order[id] = id;
+    }
+  }
+  for (int id = n_tiles + tid; id < a.n_tiles_cap; id += kPlanThreads) {
+    a.tile_len[id] = -1;
+    a.tile_model[id] = 0;
+  }
+  if (tid == 0) *a.n_tiles = n_tiles;
+}
+
+cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st) {
+  mma_plan_kernel<<<1, kPlanThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // row softmax and its chain rule (one warp per row)
 // ---------------------------------------------------------------------------
 struct RowMap {

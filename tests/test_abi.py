@@ -59,13 +59,21 @@ def test_workspace_size_is_host_only_and_monotone(lib):
     q = _seqs(S=100)
     out = ctypes.c_size_t()
     assert lib.hmm_workspace_size(d, ctypes.byref(q), 7, ctypes.byref(out)) == hmm.HMM_ERR_ARG
-    # N up to 128 for the (tensor-core) forward, 64 for Viterbi, 32 for the adjoint
+    # N up to 128 for the forward and the adjoint (tensor cores above 64), 64
+    # for Viterbi; the tensor-core adjoint takes M <= 256
     big = hmm.hmm_dims_t(4, 128, 256)
     assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_FORWARD, ctypes.byref(out)) == 0
     assert out.value >= 4 * 128 * 128 * 4
     assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_VITERBI,
                                   ctypes.byref(out)) == hmm.HMM_ERR_UNSUPPORTED
-    assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 65, 8), ctypes.byref(q),
+    assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_FORWARD_BACKWARD,
+                                  ctypes.byref(out)) == 0
+    # per-tile count slots and per-CTA checkpoint buffers
+    assert out.value >= (100 // 128 + 1 + 4) * 128 * (1 + 128 + 256) * 4
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 129, 8), ctypes.byref(q),
+                                  hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
+        == hmm.HMM_ERR_UNSUPPORTED
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 65, 300), ctypes.byref(q),
                                   hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
         == hmm.HMM_ERR_UNSUPPORTED
 
@@ -139,6 +147,8 @@ def test_tuning_table(lib):
     assert hmm.hmm_get_tuning(hmm.HMM_OP_FORWARD, 16) == 2
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD) == 64
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD) == 64
+    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD, hmm.HMM_BF16_MMA) == 128
+    assert hmm.hmm_max_states(hmm.HMM_OP_VITERBI, hmm.HMM_BF16_MMA) == 0
 
 
 def test_last_error_is_thread_local(lib):

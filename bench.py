@@ -61,8 +61,8 @@ def parse():
                     help="fixed lanes per pair 'fwd,viterbi,paths,adjoint' instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "large", "gradient", "training"],
-                    help="batched: the full step (default); large: tensor-core forward; "
-                         "gradient/training: the learning step")
+                    help="batched: the full step (default); large: tensor-core forward "
+                         "and adjoint; gradient/training: the learning step")
     return ap.parse_args()
 
 
@@ -454,9 +454,12 @@ def measured_peak_bf16():
         return 1900.0, "fallback"
 
 
-def run_forward_only(args):
-    """Forward (all K models + argmax) on the large-state configurations, the
-    only op this build runs on the tensor cores; one JSON line."""
+def run_large(args):
+    """The large-state configuration on the tensor cores: one step = the
+    forward of every sequence against all K models with the argmax
+    (recognition) plus the forward-backward adjoint of every sequence against
+    its labelled model; units = sum_s T_s (K + 1). One JSON line; the
+    forward-only and adjoint-only kernels are reported beside it."""
     import torch
     from paper_1310_3322_gb300 import hmm, synth
 
@@ -465,59 +468,72 @@ def run_forward_only(args):
     dev = torch.device("cuda", local)
     w = synth.make_workload(args.workload, n_seqs=args.n_seqs,
                             seed=synth.SEEDS[args.workload] + rank)
-    K, N = w.K, w.N
+    K, N, M = w.K, w.N, w.M
     sumT = int(w.lengths.astype(np.int64).sum())
-    units = sumT * K
+    units = sumT * (K + 1)
     seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
+    lab = seqs.labelled(torch.from_numpy(w.labels).to(dev))
     pi, A, B = (torch.from_numpy(x).to(dev) for x in (w.pi, w.A, w.B))
     ll = torch.empty((w.S, K), device=dev)
     am = torch.empty(w.S, dtype=torch.int32, device=dev)
-    ws = hmm.Workspace(dev)
+    fll = torch.empty(w.S, device=dev)
+    cnts = [torch.empty(sh, device=dev) for sh in ((K, N), (K, N, N), (K, N, M))]
+    ws = [hmm.Workspace(dev), hmm.Workspace(dev)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    out = {}
-    variants = [("bf16_mma", hmm.HMM_BF16_MMA)]
-    if N <= hmm.hmm_max_states(hmm.HMM_OP_FORWARD, hmm.HMM_FP32):
-        variants.append(("fp32_simt", hmm.HMM_FP32))
-    for name, prec in variants:
-        def step():
-            hmm.hmm_forward(pi, A, B, seqs, precision=prec, loglik=ll, argmax=am, workspace=ws)
-        for _ in range(max(args.warmup, 3)):
-            step()
-        torch.cuda.synchronize()
-        assert hmm.hmm_get_device_status(ws) == 0
-        hmm.hmm_timing_reset()
-        hmm.hmm_timing_enable(True)
-        evs = []
-        for i in range(args.steps):
-            flush.fill_(i & 0xff)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            step()
-            b.record()
-            evs.append((a, b))
-        torch.cuda.synchronize()
-        kt = hmm.hmm_timing_read()
-        hmm.hmm_timing_enable(False)
-        ms = float(np.mean([x.elapsed_time(y) for x, y in evs]))
-        kms = kt["forward"][1] / max(kt["forward"][0], 1)
-        out[name] = {"ms_per_step": ms, "kernel_ms": kms, "value": units / (ms / 1e3),
-                     "tflops": 2.0 * N * N * units / (kms / 1e3) / 1e12}
+    prec = hmm.HMM_BF16_MMA
+
+    def fwd():
+        hmm.hmm_forward(pi, A, B, seqs, precision=prec, loglik=ll, argmax=am, workspace=ws[0])
+
+    def adj():
+        hmm.hmm_forward_backward(pi, A, B, lab, precision=prec, loglik=fll, counts=cnts,
+                                 workspace=ws[1])
+
+    def step():
+        fwd()
+        adj()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(ws[0]) == 0 and hmm.hmm_get_device_status(ws[1]) == 0
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = _time_steps(torch, step, args.steps, flush)
+    clk = clocks.stop()
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, step, args.steps, flush)
+    kt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    kms = {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]}
+    f_tf = 2.0 * N * N * sumT * K / (kms["forward"] / 1e3) / 1e12
+    a_tf = (8.0 * N * N + 10 * N) * sumT / (kms["adjoint"] / 1e3) / 1e12
+    dom = "adjoint" if kms["adjoint"] >= kms["forward"] else "forward"
+    achieved = a_tf if dom == "adjoint" else f_tf
     peak, basis = measured_peak_bf16()
-    main_v = out["bf16_mma"]
     line = {
-        "metric": METRIC, "value": main_v["value"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_v["ms_per_step"],
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} K={K} N={N} M={w.M} S={w.S} (forward, all "
-                               "K models + argmax, tensor cores)", "units_per_step": units,
+        "config": {"workload": f"{args.workload} K={K} N={N} M={M} S={w.S} (forward of all "
+                               "K models + argmax, and the adjoint against the labelled "
+                               "model; tcgen05 BF16)", "units_per_step": units,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "timing": "eager step, CUDA events"},
-        "roofline": {"bound": "tensor", "kernel": "forward_mma", "achieved": main_v["tflops"],
-                     "peak": peak, "unit": "TFLOP/s", "frac": main_v["tflops"] / peak,
-                     "peak_basis": f"dense BF16, {basis} (burst)", "traffic": None},
-        "variants": out,
-        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "tensor", "kernel": dom + "_mma", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "launch_ms": kms[dom], "peak_basis": f"dense BF16, {basis} (burst)",
+                     "traffic": None},
+        "phases": {"forward": {"ms": kms["forward"], "tflops": f_tf,
+                               "obs_models_per_s": sumT * K / (kms["forward"] / 1e3)},
+                   "adjoint": {"ms": kms["adjoint"], "tflops": a_tf,
+                               "obs_per_s": sumT / (kms["adjoint"] / 1e3)},
+                   **{k: {"ms": v} for k, v in kms.items() if k not in ("forward", "adjoint")}},
+        "clocks": clk,
+        "gpu_launches": 7 * args.steps,  # forward: setup, kernel; adjoint: setup, plan, kernel, reduce x2
     }
     print(json.dumps(line), flush=True)
 
@@ -550,6 +566,9 @@ def run_learning(args):
     w = synth.make_workload(args.workload, n_seqs=args.n_seqs,
                             seed=synth.SEEDS[args.workload] + rank)
     K, N, M = w.K, w.N, w.M
+    # the library's choice: FP32 SIMT adjoint up to N = 32, tensor cores above
+    mma = N > 32
+    prec = hmm.HMM_AUTO
     sumT = int(w.lengths.astype(np.int64).sum())
     seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
     lab = seqs.labelled(torch.from_numpy(w.labels).to(dev))
@@ -576,14 +595,16 @@ def run_learning(args):
 
     def step():
         hmm.hmm_softmax_rows(*lg, out=probs)
-        hmm.hmm_forward_backward(*probs, lab, loglik=fll, counts=cnts, workspace=ws)
+        hmm.hmm_forward_backward(*probs, lab, precision=prec, loglik=fll, counts=cnts,
+                                 workspace=ws)
         hmm.hmm_softmax_grad(*probs, *cnts, out=gr)
         hmm.hmm_adam_step(logits, grads, m_, v_, 1e-3, grad_scale=-1.0 / sumT,
                           step_counter=counter)
 
     step()
     torch.cuda.synchronize()
-    tuning = tune.autotune(*probs, seqs, lab, ops=[hmm.HMM_OP_FORWARD_BACKWARD], cache=None)
+    tuning = {} if mma else tune.autotune(*probs, seqs, lab, ops=[hmm.HMM_OP_FORWARD_BACKWARD],
+                                          cache=None)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -610,7 +631,12 @@ def run_learning(args):
     adj_ms = kt["adjoint"][1] / max(kt["adjoint"][0], 1)
     flops = (8 * N * N + 10 * N) * sumT
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if mma:
+        peak, basis = measured_peak_bf16()
+        peak_basis = f"dense BF16, {basis} (burst)"
+    else:
+        peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak_basis = f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
     achieved = flops / (adj_ms / 1e3) / 1e12
 
     # the plain per-sequence forward kernels on the same data (all K models)
@@ -629,17 +655,19 @@ def run_learning(args):
     line = {
         "metric": METRIC, "value": sumT / (ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if mma else "f32",
         "data": "synthetic",
         "config": {"workload": f"{args.workload} K={K} N={N} M={M} S={w.S} (softmax rows, "
                                "forward+adjoint against the labelled model, logit gradient, "
                                "Adam; CUDA graph)", "units_per_step": sumT,
+                   "adjoint": "tcgen05 BF16" if mma else "FP32 SIMT",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "lanes_per_pair": {k: v["lanes"] for k, v in tuning.items()}},
-        "roofline": {"bound": "alu", "kernel": "adjoint", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "launch_ms": adj_ms,
-                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
-                     "traffic": None},
+        "roofline": {"bound": "tensor" if mma else "alu", "kernel": "adjoint",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "launch_ms": adj_ms,
+                     "peak_basis": peak_basis, "traffic": None},
         "clocks": clk,
         "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]},
         "forward_all_models": fwd,
@@ -656,7 +684,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     if args.workload == "large":
-        run_forward_only(args)
+        run_large(args)
         return
     if args.workload in ("gradient", "training"):
         run_learning(args)

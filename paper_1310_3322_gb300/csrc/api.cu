@@ -161,7 +161,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.nchunks = first_chunks(cap);
     L.m_sorted = off; off = align256(off + S * 4);
     L.m_tmp = off; off = align256(off + S * 4);
-    L.m_tiles = off; off = align256(off + (size_t)cap * 6 * 4);
+    L.m_tiles = off; off = align256(off + ((size_t)cap * 6 + (size_t)d.K * 2) * 4);
     L.m_ntiles = off; off = align256(off + 4);
     L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
     L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
@@ -383,6 +383,7 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   p.tmp = at<int32_t>(ws, L.m_tmp);
   p.tile_start = tiles; p.tile_rows = tiles + cap; p.tile_model = tiles + 2 * cap;
   p.tile_len = tiles + 3 * cap; p.tile_order = tiles + 4 * cap; p.tile_tmp = tiles + 5 * cap;
+  p.group_start = tiles + 6 * cap; p.group_end = p.group_start + dims.K;
   p.n_tiles_cap = cap;
   p.n_tiles = at<int32_t>(ws, L.m_ntiles);
   {

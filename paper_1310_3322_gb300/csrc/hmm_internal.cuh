@@ -424,6 +424,8 @@ struct MmaPlanArgs {
   int32_t* tile_len;            // [cap] longest row (-1 for unused entries)
   int32_t* tile_order;          // [cap] tiles by decreasing length
   int32_t* tile_tmp;            // [cap] scratch
+  int32_t* group_start;         // [K] labelled: first sorted position of each model
+  int32_t* group_end;           // [K] ... and one past its last
   int n_tiles_cap;
   int32_t* n_tiles;             // device count
 };

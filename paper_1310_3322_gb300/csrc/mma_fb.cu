@@ -52,27 +52,33 @@ namespace hmmgb {
 
 template <int NP, int MB>
 struct MmaFbCfg {
-  static constexpr int TPR = NP / 32;            // threads per row, 32 columns each
+  static constexpr int TPR = 4;                  // threads per row
   static constexpr int NTH = 128 * TPR;
+  static constexpr int COLS = NP / TPR;          // columns per thread (16 or 32)
+  static constexpr int CH = COLS / 8;            // 16-byte image chunks per thread
   static constexpr int IMG = 128 * NP * 2;       // one 128-row BF16 image
-  static constexpr int MAT = NP * NP * 2;        // one BF16 transition image
-  static constexpr int OFF_AT = 0;               // forward B operand: (n=j, k=i) = a_ij
-  static constexpr int OFF_AM = MAT;             // backward B operand: (n=i, k=j) = a_ij
-  static constexpr int OFF_XI = 2 * MAT;         // X_t (xi A operand)
-  static constexpr int OFF_Y = OFF_XI + IMG;     // Y_t
-  static constexpr int OFF_G = OFF_Y + IMG;      // gamma_t; forward X operand in phase 1 / recompute
+  static constexpr int MAT = NP * NP * 2;        // the BF16 transition image
+  static constexpr bool EMIS = (NP == 64 && MB == 1);   // emission table in shared memory
+  static constexpr int XIB = (NP == 64 || MB == 1) ? 2 : 1;  // X_t buffers
+  static constexpr int ES = NP * 4 + 16;         // padded emission row (bytes)
+  static constexpr int OFF_AT = 0;               // (n=j, k=i) = a_ij: forward K-major, backward MN-major
+  static constexpr int OFF_XI = MAT;             // X_t images (xi A operand; epilogue rows)
+  static constexpr int OFF_Y = OFF_XI + XIB * IMG;   // Y_t
+  static constexpr int OFF_G = OFF_Y + IMG;      // gamma_t; the forward X operand in phase 1 / recompute
   static constexpr int OFF_OH = OFF_G + IMG;     // one-hot [k][m], MB blocks of 128 x 128
-  static constexpr int OFF_PS = OFF_OH + MB * 32768;    // row partial sums [TPR][128]
-  static constexpr int OFF_BAR = OFF_PS + TPR * 128 * 4;  // mma, xi copy
-  static constexpr int OFF_MISC = OFF_BAR + 16;
+  static constexpr int OFF_B = OFF_OH + MB * 32768;  // emission rows b(k), k < 128 (EMIS)
+  static constexpr int OFF_PS = OFF_B + (EMIS ? 128 * ES : 0);  // row partial sums [2][TPR][128]
+  static constexpr int OFF_BAR = OFF_PS + 2 * TPR * 128 * 4;    // mma, gload, xi[2]
+  static constexpr int OFF_MISC = OFF_BAR + 64;
   static constexpr int TOTAL = OFF_MISC + 64;
   static constexpr int TMEM_USED = (2 + MB) * NP;  // D, XI, CB blocks
   static constexpr int TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
-  static constexpr int CTAS = (TOTAL <= 113 * 1024 && TMEM_COLS <= 256) ? 2 : 1;
 };
 static_assert(MmaFbCfg<128, 2>::TOTAL <= 227 * 1024, "shared memory budget");
+static_assert(MmaFbCfg<128, 1>::TOTAL <= 227 * 1024, "shared memory budget");
+static_assert(MmaFbCfg<64, 1>::TOTAL <= 227 * 1024, "shared memory budget");
+static_assert(MmaFbCfg<64, 2>::TOTAL <= 227 * 1024, "shared memory budget");
 static_assert(MmaFbCfg<128, 2>::TMEM_USED <= 512, "tensor memory budget");
-static_assert(MmaFbCfg<64, 1>::CTAS == 2, "two CTAs per SM at N = 64, M <= 128");
 
 constexpr uint32_t kFbWaitLimit = 1u << 24;
 
@@ -82,48 +88,16 @@ __device__ __forceinline__ uint32_t img_off(int m, int c8) {
   return (uint32_t)((m & 7) * 16 + c8 * 128 + (m >> 3) * NP * 16);
 }
 
-// Row m, columns [32h, 32h + 32) of an image, as 16 packed BF16 pairs.
-template <int NP>
-__device__ __forceinline__ void img_put(uint8_t* img, int m, int h, const uint32_t (&w)[16]) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    *reinterpret_cast<uint4*>(img + img_off<NP>(m, 4 * h + q)) =
-        make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-}
-template <int NP>
-__device__ __forceinline__ void img_put_global(uint8_t* img, int m, int h, const uint32_t (&w)[16]) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    __stcg(reinterpret_cast<uint4*>(img + img_off<NP>(m, 4 * h + q)),
-           make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]));
-}
-template <int NP>
-__device__ __forceinline__ void img_get_global(const uint8_t* img, int m, int h, uint32_t (&w)[16]) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(img + img_off<NP>(m, 4 * h + q)));
-    w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
-  }
-}
-
-// 32 emission probabilities b_j(sym), j in [32h, 32h + 32).
-template <int NP>
-__device__ __forceinline__ void load_emis(float (&b)[32], const float* Bk, int sym, int h) {
-  const float4* p = reinterpret_cast<const float4*>(Bk + (size_t)sym * NP + 32 * h);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float4 v = __ldg(p + q);
-    b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
-  }
+// COLS consecutive FP32 values from tensor memory (one row = one lane).
+template <int COLS>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[COLS]) {
+  if constexpr (COLS == 32) tc::tmem_ld32(taddr, v);
+  else tc::tmem_ld16(taddr, v);
+  tc::tmem_ld_wait();
 }
 
 __device__ __forceinline__ float2 unpack_bf16(uint32_t w) {
   return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
-
-__device__ __forceinline__ void pack32w(const float (&y)[32], uint32_t (&w)[16]) {
-#pragma unroll
-  for (int i = 0; i < 16; ++i) w[i] = tc::pack_bf16(y[2 * i], y[2 * i + 1]);
 }
 
 __device__ __forceinline__ int exponent_of_fb(float s) {
@@ -153,46 +127,120 @@ __device__ __forceinline__ void fb_close(FbRow& st, float sigma, int t, int T) {
   st.f = min(126, max(-126, exponent_of_fb(sigma)));
 }
 
+// Per-thread view of one tile row: the row, its column range and where its
+// emission rows come from.
 template <int NP, int MB>
-__global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
-    hmm_fb_mma(MmaFbLaunch a) {
+struct FbThread {
   using L = MmaFbCfg<NP, MB>;
-  constexpr int TPR = L::TPR, NTH = L::NTH, IMG = L::IMG;
+  int row, col0;
+  const uint8_t* sB;   // shared emission table (EMIS)
+  const float* Bk;     // global emission table of the model [M][NP]
+
+  // b_j(sym) for this thread's columns
+  __device__ __forceinline__ void emis(float (&b)[L::COLS], int sym) const {
+    if constexpr (L::EMIS) {
+      const float4* p = reinterpret_cast<const float4*>(sB + sym * L::ES + col0 * 4);
+#pragma unroll
+      for (int q = 0; q < L::COLS / 4; ++q) {
+        const float4 v = p[q];
+        b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+      }
+    } else {
+      const float4* p = reinterpret_cast<const float4*>(Bk + (size_t)sym * NP + col0);
+#pragma unroll
+      for (int q = 0; q < L::COLS / 4; ++q) {
+        const float4 v = __ldg(p + q);
+        b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+      }
+    }
+  }
+  // this thread's columns of the row image: write (BF16 pairs) / read
+  __device__ __forceinline__ void put(uint8_t* img, const uint32_t (&w)[L::COLS / 2]) const {
+#pragma unroll
+    for (int c = 0; c < L::CH; ++c)
+      *reinterpret_cast<uint4*>(img + img_off<NP>(row, col0 / 8 + c)) =
+          make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+  }
+  __device__ __forceinline__ void get(const uint8_t* img, uint32_t (&w)[L::COLS / 2]) const {
+#pragma unroll
+    for (int c = 0; c < L::CH; ++c) {
+      const uint4 v = *reinterpret_cast<const uint4*>(img + img_off<NP>(row, col0 / 8 + c));
+      w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+    }
+  }
+  __device__ __forceinline__ void get_global(const uint8_t* img, uint32_t (&w)[L::COLS / 2]) const {
+#pragma unroll
+    for (int c = 0; c < L::CH; ++c) {
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(img + img_off<NP>(row, col0 / 8 + c)));
+      w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+    }
+  }
+};
+
+// Forward step epilogue: y = D . b . 2^-f (zero when not live), packed into
+// the operand image; returns the partial row sum.
+template <int COLS>
+__device__ __forceinline__ float fwd_epilogue(float (&y)[COLS], const float (&b)[COLS], int f,
+                                              bool live, uint32_t (&w)[COLS / 2]) {
+  const float fac = exp2i(-f);
+  const float2 f2 = make_float2(fac, fac);
+#pragma unroll
+  for (int i = 0; i < COLS / 2; ++i) {
+    float2 v = __fmul2_rn(__fmul2_rn(make_float2(y[2 * i], y[2 * i + 1]),
+                                     make_float2(b[2 * i], b[2 * i + 1])), f2);
+    if (!live) v = make_float2(0.f, 0.f);
+    y[2 * i] = v.x; y[2 * i + 1] = v.y;
+    w[i] = tc::pack_bf16(v.x, v.y);
+  }
+  return tree_sum<COLS>(y);
+}
+
+template <int NP, int MB>
+__global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaunch a) {
+  using L = MmaFbCfg<NP, MB>;
+  constexpr int TPR = L::TPR, NTH = L::NTH, IMG = L::IMG, COLS = L::COLS, XIB = L::XIB;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAT = smem + L::OFF_AT;
-  uint8_t* sAM = smem + L::OFF_AM;
   uint8_t* sXI = smem + L::OFF_XI;
   uint8_t* sY = smem + L::OFF_Y;
   uint8_t* sG = smem + L::OFF_G;
   uint8_t* sOH = smem + L::OFF_OH;
-  float* psum = reinterpret_cast<float*>(smem + L::OFF_PS);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
-  uint64_t* xbar = mbar + 1;
+  float* psum = reinterpret_cast<float*>(smem + L::OFF_PS);  // [2][TPR][128]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+  uint64_t* mbar = bars;       // MMA commits
+  uint64_t* gbar = bars + 1;   // checkpoint -> forward operand loads
+  uint64_t* xbar = bars + 2;   // [XIB] X_t image loads
   volatile int32_t* misc = reinterpret_cast<volatile int32_t*>(smem + L::OFF_MISC);
+  enum { M_TMEM = 0, M_ITEM = 1, M_ABORT = 2 };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wq = warp & 3, h = warp >> 2, row = wq * 32 + lane;
+  const int wq = warp & 3, h = warp >> 2;
   const int K = a.seq.K, M = a.seq.M;
+  FbThread<NP, MB> me;
+  me.row = wq * 32 + lane;
+  me.col0 = h * COLS;
+  me.sB = smem + L::OFF_B;
+  const int row = me.row;
 
   for (int i = tid; i < MB * 32768 / 16; i += NTH)
     reinterpret_cast<uint4*>(sOH)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), L::TMEM_COLS);
   if (tid == 0) {
-    tc::mbar_init(mbar, 1);
-    tc::mbar_init(xbar, 1);
-    misc[2] = 0;
+    for (int i = 0; i < 2 + XIB; ++i) tc::mbar_init(&bars[i], 1);
+    misc[M_ABORT] = 0;
   }
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = (uint32_t)misc[0];
+  const uint32_t tmem = (uint32_t)misc[M_TMEM];
   const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
   const uint32_t d_tm = tmem, xi_tm = tmem + NP, cb_tm = tmem + 2 * NP;
+  const uint32_t my_cols = lane_off + (uint32_t)me.col0;
   constexpr uint32_t id_kk = tc::instr_desc(1, 128, NP);               // A, B K-major
   constexpr uint32_t id_mm = id_kk | (1u << 15) | (1u << 16);          // A, B MN-major
   constexpr uint32_t id_km = id_kk | (1u << 16);                       // B MN-major
-  const uint32_t aAT = tc::smem_u32(sAT), aAM = tc::smem_u32(sAM), aXI = tc::smem_u32(sXI);
+  const uint32_t aAT = tc::smem_u32(sAT), aXI = tc::smem_u32(sXI);
   const uint32_t aY = tc::smem_u32(sY), aG = tc::smem_u32(sG), aOH = tc::smem_u32(sOH);
   constexpr uint32_t SBO = NP * 16;
 
@@ -201,34 +249,35 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
   int8_t* gexp = a.gexp + (size_t)blockIdx.x * a.gexp_bytes;
   float* gbuf = a.gbuf + (size_t)blockIdx.x * 128 * NP;
 
-  uint32_t mph = 0, xph = 0;
-  bool x_inflight = false;  // thread 0: a copy into sXI not yet waited for
-  uint32_t x_par = 0;       // ... and the parity its completion flips
-  bool mma_pending = false; // thread 0: MMAs committed but not waited for
-  uint32_t m_par = 0;       // ... and the parity their commit completes
-  bool aborted = false;
+  // barrier phases (every thread tracks them; thread 0 also remembers what
+  // it has in flight for the teardown)
+  uint32_t mph = 0, gph = 0, xph[2] = {0, 0};
+  bool m_pend = false, g_pend = false, x_pend[2] = {false, false};
+  uint32_t m_par = 0, g_par = 0, x_par[2] = {0, 0};
   int cur_model = -1;
 
-  // thread 0 issues; warp 0 polls; everyone agrees on the outcome
+  auto fail = [&]() { misc[M_ABORT] = 1; };
   auto commit = [&]() {  // thread 0
     tc::mma_commit(mbar);
-    mma_pending = true;
+    m_pend = true;
     m_par = mph;
   };
-  auto wait_mma = [&]() -> bool {
-    bool ok = true;
-    if (warp == 0) ok = tc::mbar_wait_bounded(mbar, mph, kFbWaitLimit);
+  auto wait_mma = [&]() {  // every thread; a timeout is acted on at the next barrier
+    if (!tc::mbar_wait_bounded(mbar, mph, kFbWaitLimit)) fail();
+    else if (tid == 0) m_pend = false;
     mph ^= 1;
-    if (tid == 0) mma_pending = !ok;
-    ok = tc::bar_and(1, NTH, ok);
     tc::fence_after_sync();
-    return ok;
   };
-  auto copy_x = [&](const uint8_t* src) {  // thread 0: sXI <- one row image
-    tc::mbar_arrive_expect_tx(xbar, IMG);
-    tc::bulk_g2s(aXI, src, IMG, xbar);
-    x_inflight = true;
-    x_par = xph;
+  auto load_x = [&](int b, const uint8_t* src) {  // thread 0: sXI[b] <- one row image
+    tc::mbar_arrive_expect_tx(&xbar[b], IMG);
+    tc::bulk_g2s(aXI + b * IMG, src, IMG, &xbar[b]);
+    x_pend[b] = true;
+    x_par[b] = xph[b];
+  };
+  auto wait_x = [&](int b) {  // every thread
+    if (!tc::mbar_wait_bounded(&xbar[b], xph[b], kFbWaitLimit)) fail();
+    else if (tid == 0) x_pend[b] = false;
+    xph[b] ^= 1;
   };
   auto issue_fwd = [&]() {  // D = X_op . A   (X_op in sG)
 #pragma unroll
@@ -236,13 +285,23 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
       tc::mma_bf16(d_tm, tc::smem_desc(aG + ks * 256, 128, SBO),
                    tc::smem_desc(aAT + ks * 256, 128, SBO), id_kk, ks > 0 ? 1u : 0u);
   };
+  auto store_img = [&](uint8_t* dst) {  // thread 0: sG -> global image
+    tc::bulk_s2g(dst, aG, IMG);
+    tc::bulk_commit();
+  };
+  auto row_sum = [&](int par) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < TPR; ++q) s += psum[(par * TPR + q) * 128 + row];
+    return s;
+  };
 
   for (;;) {
     __syncthreads();
-    if (tid == 0) misc[1] = atomicAdd(a.queue, 1);
+    if (tid == 0) misc[M_ITEM] = atomicAdd(a.queue, 1);
     __syncthreads();
-    const int item = misc[1];
-    if (item >= __ldcg(a.n_tiles) || misc[2]) break;
+    const int item = misc[M_ITEM];
+    if (item >= __ldcg(a.n_tiles) || misc[M_ABORT]) break;
     const int tile = a.tile_order[item];
     const int k = a.tile_model[tile];
     const int start = a.tile_start[tile];
@@ -250,21 +309,20 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
     const int Lt = a.tile_len[tile];
 
     const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
+    me.Bk = a.mod.Btp + (size_t)k * M * NP;
     if (k != cur_model) {
+      // transition image: (n = j, k = i) = a_ij, pairs along i
       for (int idx = tid; idx < NP * NP / 2; idx += NTH) {
-        // forward image: (n = j, k = i), pairs along i
-        {
-          const int j = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
-          const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + (i + 1) * NP + j));
-          *reinterpret_cast<uint32_t*>(sAT + (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 +
-                                       (i % 8) * 2) = w;
-        }
-        // backward image: (n = i, k = j), pairs along j
-        {
-          const int i = idx / (NP / 2), j = (idx % (NP / 2)) * 2;
-          const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + i * NP + j + 1));
-          *reinterpret_cast<uint32_t*>(sAM + (i / 8) * SBO + (j / 8) * 128 + (i % 8) * 16 +
-                                       (j % 8) * 2) = w;
+        const int j = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
+        const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + (i + 1) * NP + j));
+        *reinterpret_cast<uint32_t*>(sAT + (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 +
+                                     (i % 8) * 2) = w;
+      }
+      if constexpr (L::EMIS) {  // emission rows of the model, padded
+        for (int idx = tid; idx < M * (NP / 4); idx += NTH) {
+          const int sym = idx / (NP / 4), q = idx % (NP / 4);
+          *reinterpret_cast<float4*>(smem + L::OFF_B + sym * L::ES + q * 16) =
+              __ldg(reinterpret_cast<const float4*>(me.Bk + (size_t)sym * NP) + q);
         }
       }
       cur_model = k;
@@ -278,9 +336,13 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
     const size_t oidx = a.labelled ? (size_t)s : (size_t)s * K + k;
     const float w = has ? (a.weight ? a.weight[oidx] : 1.f) : 0.f;
     const int32_t* o = a.seq.symbols + (has ? a.seq.offsets[s] : 0);
-    const float* Bk = a.mod.Btp + (size_t)k * M * NP;
     const int C = fb_mma_segment(Lt);
     const int NS = (Lt + C - 1) / C;
+    auto sym_at = [&](int t) -> int {  // symbol at step t (0 past the row's end)
+      if (t >= T) return 0;
+      const int v = __ldg(o + t);
+      return (unsigned)v < (unsigned)M ? v : 0;
+    };
 
     // ---------------- phase 1: forward, checkpoints every C steps ----------------
     FbRow st;
@@ -290,44 +352,37 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
       int o0 = T > 0 ? __ldg(o) : 0;
       if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
       const bool live = T > 0 && !st.bad;
-      float b[32], y[32];
-      load_emis<NP>(b, Bk, o0, h);
-      const float4* p4 = reinterpret_cast<const float4*>(a.mod.pip + (size_t)k * NP + 32 * h);
+      float b[COLS], y[COLS];
+      me.emis(b, o0);
+      const float* pik = a.mod.pip + (size_t)k * NP + me.col0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 pp = __ldg(p4 + q);
-        y[4 * q] = live ? pp.x * b[4 * q] : 0.f;
-        y[4 * q + 1] = live ? pp.y * b[4 * q + 1] : 0.f;
-        y[4 * q + 2] = live ? pp.z * b[4 * q + 2] : 0.f;
-        y[4 * q + 3] = live ? pp.w * b[4 * q + 3] : 0.f;
-      }
-      uint32_t wv[16];
-      pack32w(y, wv);
-      img_put<NP>(sG, row, h, wv);
-      img_put_global<NP>(ckpt, row, h, wv);
-      psum[h * 128 + row] = tree_sum<32>(y);
+      for (int i = 0; i < COLS; ++i) y[i] = __ldg(pik + i);
+      uint32_t wv[COLS / 2];
+      const float sum = fwd_epilogue<COLS>(y, b, 0, live, wv);
+      me.put(sG, wv);
+      psum[(0 * TPR + h) * 128 + row] = sum;
       if (h == 0) __stcg(gexp + row, (int8_t)0);
     }
     int o_n1 = (1 < T) ? __ldg(o + 1) : 0;  // symbol of the next step
     int o_n2 = (2 < T) ? __ldg(o + 2) : 0;  // and the one after
-    float bcur[32];
-    load_emis<NP>(bcur, Bk, (unsigned)o_n1 < (unsigned)M ? o_n1 : 0, h);
+    float bcur[COLS];
+    if constexpr (!L::EMIS) me.emis(bcur, (unsigned)o_n1 < (unsigned)M ? o_n1 : 0);
     tc::fence_proxy_async();
 
-    for (int t = 1; t < Lt && !aborted; ++t) {
+    for (int t = 1; t < Lt; ++t) {
       tc::fence_before_sync();
       __syncthreads();
+      if (misc[M_ABORT]) break;
       if (tid == 0) {
         tc::fence_after_sync();
         issue_fwd();
+        if ((t - 1) % C == 0) {  // checkpoint X_{t-1} while the MMA reads it too
+          store_img(ckpt + (size_t)((t - 1) / C) * IMG);
+          tc::bulk_wait_read();
+        }
         commit();
       }
-      {
-        float sig = 0.f;
-#pragma unroll
-        for (int q = 0; q < TPR; ++q) sig += psum[q * 128 + row];
-        fb_close(st, sig, t - 1, T);
-      }
+      fb_close(st, row_sum((t - 1) & 1), t - 1, T);
       const int ot = o_n1;
       o_n1 = o_n2;
       o_n2 = (t + 2 < T) ? __ldg(o + t + 2) : 0;
@@ -335,40 +390,35 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
       const bool live = t < T && !st.dead && !st.bad;
       if (live) st.F += st.f;
       if (h == 0) __stcg(gexp + (size_t)t * 128 + row, (int8_t)st.f);
-      if (!wait_mma()) { aborted = true; break; }
-      float y[32];
-      tc::tmem_ld32(d_tm + lane_off + (uint32_t)(32 * h), y);
-      tc::tmem_ld_wait();
-      const float fac = exp2i(-st.f);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) y[i] = live ? y[i] * bcur[i] * fac : 0.f;
-      uint32_t wv[16];
-      pack32w(y, wv);
-      img_put<NP>(sG, row, h, wv);
-      if (t % C == 0) img_put_global<NP>(ckpt + (size_t)(t / C) * IMG, row, h, wv);
-      psum[h * 128 + row] = tree_sum<32>(y);
-      load_emis<NP>(bcur, Bk, (t + 1 < T && (unsigned)o_n1 < (unsigned)M) ? o_n1 : 0, h);
+      if constexpr (L::EMIS) me.emis(bcur, live ? ot : 0);
+      wait_mma();
+      float y[COLS];
+      tmem_ld_cols<COLS>(d_tm + my_cols, y);
+      uint32_t wv[COLS / 2];
+      const float sum = fwd_epilogue<COLS>(y, bcur, st.f, live, wv);
+      me.put(sG, wv);
+      psum[((t & 1) * TPR + h) * 128 + row] = sum;
+      if constexpr (!L::EMIS)
+        me.emis(bcur, (t + 1 < T && (unsigned)o_n1 < (unsigned)M) ? o_n1 : 0);
       tc::fence_proxy_async();
     }
-    // checkpoints (generic-proxy stores) may be read by bulk copies
-    asm volatile("fence.proxy.async;" ::: "memory");
+    tc::fence_before_sync();
     __syncthreads();
-    if (!aborted && Lt > 0) {
-      float sig = 0.f;
-#pragma unroll
-      for (int q = 0; q < TPR; ++q) sig += psum[q * 128 + row];
-      fb_close(st, sig, Lt - 1, T);
+    if (misc[M_ABORT]) break;
+    if (tid == 0) {
+      if ((Lt - 1) % C == 0) store_img(ckpt + (size_t)((Lt - 1) / C) * IMG);
+      tc::bulk_wait_all();  // every checkpoint written before phase 2 reads them
     }
-    __syncthreads();  // every row has read its sums before phase 2 rewrites them
+    if (Lt > 0) fb_close(st, row_sum((Lt - 1) & 1), Lt - 1, T);
     if (has && h == 0) {
       float out = st.ll;
-      if (st.bad || aborted) out = __int_as_float(0x7fc00000);
+      if (st.bad) out = __int_as_float(0x7fc00000);
       else if (st.dead) out = -INFINITY;
       else if (!st.written) out = __int_as_float(0x7fc00000);
       if (st.bad && st.err) set_status(a.status, st.err);
       a.loglik[oidx] = out;
     }
-    if (aborted) break;
+    __syncthreads();  // every row has read its sums (and thread 0 waited for the checkpoints)
 
     // ---------------- phase 2: segments backwards ----------------
     const bool act = has && st.written && !st.dead && !st.bad && w != 0.f;
@@ -377,7 +427,8 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
     bool xi_on = false;   // thread 0: an xi MMA has been issued for this tile
     bool cb_on = false;   // thread 0: an emission MMA has been issued for this tile
     bool cb_pending = false;
-    for (int seg = NS - 1; seg >= 0 && !aborted; --seg) {
+    bool stop = false;
+    for (int seg = NS - 1; seg >= 0 && !stop; --seg) {
       const int t0 = seg * C, t1 = min(t0 + C, Lt);
       const uint8_t* ck = ckpt + (size_t)seg * IMG;
       auto img_of = [&](int t) -> const uint8_t* {
@@ -385,156 +436,154 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
       };
       // (R) recompute X over the segment from its checkpoint
       if (t1 - t0 > 1) {
-        {
-          uint32_t wv[16];
-          img_get_global<NP>(ck, row, h, wv);
-          img_put<NP>(sG, row, h, wv);
+        if (tid == 0) {
+          tc::mbar_arrive_expect_tx(gbar, IMG);
+          tc::bulk_g2s(aG, ck, IMG, gbar);
+          g_pend = true;
+          g_par = gph;
         }
         int fn = (int)__ldcg(gexp + (size_t)(t0 + 1) * 128 + row);
-        int on = (t0 + 1 < T) ? __ldg(o + t0 + 1) : 0;
-        load_emis<NP>(bcur, Bk, (unsigned)on < (unsigned)M ? on : 0, h);
-        on = (t0 + 2 < T && t0 + 2 < t1) ? __ldg(o + t0 + 2) : 0;
-        tc::fence_proxy_async();
+        int on = sym_at(t0 + 1);
+        if constexpr (!L::EMIS) me.emis(bcur, on);
         for (int t = t0 + 1; t < t1; ++t) {
           tc::fence_before_sync();
           __syncthreads();
+          if (misc[M_ABORT]) { stop = true; break; }
           if (tid == 0) {
+            if (t == t0 + 1) {
+              if (!tc::mbar_wait_bounded(gbar, gph, kFbWaitLimit)) fail();
+              else g_pend = false;
+            }
             tc::fence_after_sync();
             issue_fwd();
+            if (t - 1 > t0) {
+              store_img(scr + (size_t)(t - 1 - t0) * IMG);
+              tc::bulk_wait_read();
+            }
             commit();
           }
+          if (t == t0 + 1) gph ^= 1;
           const int f = fn;
-          if (!wait_mma()) { aborted = true; break; }
-          const bool live = act && t < T;
-          float y[32];
-          tc::tmem_ld32(d_tm + lane_off + (uint32_t)(32 * h), y);
-          tc::tmem_ld_wait();
-          const float fac = exp2i(-f);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) y[i] = live ? y[i] * bcur[i] * fac : 0.f;
-          uint32_t wv[16];
-          pack32w(y, wv);
-          img_put<NP>(sG, row, h, wv);
-          img_put_global<NP>(scr + (size_t)(t - t0) * IMG, row, h, wv);
+          const int ot = on;
           if (t + 1 < t1) {
             fn = (int)__ldcg(gexp + (size_t)(t + 1) * 128 + row);
-            load_emis<NP>(bcur, Bk, (unsigned)on < (unsigned)M ? on : 0, h);
-            on = (t + 2 < T && t + 2 < t1) ? __ldg(o + t + 2) : 0;
+            on = sym_at(t + 1);
           }
+          if constexpr (L::EMIS) me.emis(bcur, ot);
+          wait_mma();
+          float y[COLS];
+          tmem_ld_cols<COLS>(d_tm + my_cols, y);
+          uint32_t wv[COLS / 2];
+          fwd_epilogue<COLS>(y, bcur, f, act && t < T, wv);
+          me.put(sG, wv);
+          if constexpr (!L::EMIS)
+            if (t + 1 < t1) me.emis(bcur, on);
           tc::fence_proxy_async();
         }
-        if (aborted) break;
-        // the recomputed images (generic-proxy stores) are read by bulk copies
-        asm volatile("fence.proxy.async;" ::: "memory");
+        if (stop) break;
+        tc::fence_before_sync();
+        __syncthreads();
+        if (misc[M_ABORT]) break;
+        if (tid == 0) {
+          store_img(scr + (size_t)(t1 - 1 - t0) * IMG);
+          tc::bulk_wait_all();  // the segment's images are in memory (and sG is free)
+        }
       }
-      __syncthreads();
 
       // (B) backward over the segment
-      uint32_t xcur[16];
-      float bb[32];
-      int ocur, gcur;
-      {
-        const int t = t1 - 1;
-        img_get_global<NP>(img_of(t), row, h, xcur);
-        ocur = (t < T) ? __ldg(o + t) : 0;
-        if ((unsigned)ocur >= (unsigned)M) ocur = 0;
-        load_emis<NP>(bb, Bk, ocur, h);
-        gcur = (int)__ldcg(gexp + (size_t)t * 128 + row);
-        if (tid == 0 && t < Lt - 1) copy_x(img_of(t));
-      }
+      uint32_t xcur[COLS / 2];   // X_t of this row (XIB == 1: from memory)
+      float bb[COLS];
+      int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
+      if constexpr (XIB == 1) me.get_global(img_of(t1 - 1), xcur);
+      if constexpr (!L::EMIS) me.emis(bb, ocur);
+      if (tid == 0 && (XIB == 2 || t1 - 1 < Lt - 1)) load_x((t1 - 1) % XIB, img_of(t1 - 1));
       for (int t = t1 - 1; t >= t0; --t) {
         const bool has_mma = t < Lt - 1;
-        float rho_prev = 0.f;
-        if (has_mma) {
-          tc::fence_before_sync();
-          __syncthreads();
-          bool ok0 = true;
-          if (tid == 0) {
-            ok0 = tc::mbar_wait_bounded(xbar, xph, kFbWaitLimit);
-            xph ^= 1;
-            x_inflight = !ok0;
-            if (ok0) {
-              tc::fence_after_sync();
-              if (cb_pending) {
-#pragma unroll
-                for (int b = 0; b < MB; ++b)
-#pragma unroll
-                  for (int ks = 0; ks < 8; ++ks)
-                    tc::mma_bf16(cb_tm + (uint32_t)(b * NP),
-                                 tc::smem_desc(aOH + b * 32768 + ks * 256, 128, 2048),
-                                 tc::smem_desc(aG + ks * 32 * NP, NP * 16, 128), id_km,
-                                 (ks > 0 || cb_on) ? 1u : 0u);
-                cb_on = true;
-              }
-#pragma unroll
-              for (int ks = 0; ks < 8; ++ks)
-                tc::mma_bf16(xi_tm, tc::smem_desc(aXI + ks * 32 * NP, NP * 16, 128),
-                             tc::smem_desc(aY + ks * 32 * NP, NP * 16, 128), id_mm,
-                             (ks > 0 || xi_on) ? 1u : 0u);
-              xi_on = true;
-#pragma unroll
-              for (int ks = 0; ks < NP / 16; ++ks)
-                tc::mma_bf16(d_tm, tc::smem_desc(aY + ks * 256, 128, SBO),
-                             tc::smem_desc(aAM + ks * 256, 128, SBO), id_kk, ks > 0 ? 1u : 0u);
-            }
-            commit();  // also when skipped: the phase still completes
-          }
-#pragma unroll
-          for (int q = 0; q < TPR; ++q) rho_prev += psum[q * 128 + row];
-          bool ok = true;
-          if (warp == 0) ok = tc::mbar_wait_bounded(mbar, mph, kFbWaitLimit);
-          mph ^= 1;
-          if (tid == 0) mma_pending = !ok;
-          ok = tc::bar_and(1, NTH, ok && ok0);
+        const int xb = t % XIB;
+        tc::fence_before_sync();
+        __syncthreads();
+        if (misc[M_ABORT]) { stop = true; break; }
+        if (tid == 0) {
           tc::fence_after_sync();
-          if (!ok) { aborted = true; break; }
+          if (has_mma) {
+            if (XIB == 1) wait_x(0);
+            else if (tc::mbar_wait_bounded(&xbar[xb], xph[xb], kFbWaitLimit)) x_pend[xb] = false;
+            else fail();
+            tc::fence_after_sync();
+            if (cb_pending) {
+#pragma unroll
+              for (int b = 0; b < MB; ++b)
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)
+                  tc::mma_bf16(cb_tm + (uint32_t)(b * NP),
+                               tc::smem_desc(aOH + b * 32768 + ks * 256, 128, 2048),
+                               tc::smem_desc(aG + ks * 32 * NP, NP * 16, 128), id_km,
+                               (ks > 0 || cb_on) ? 1u : 0u);
+              cb_on = true;
+            }
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks)
+              tc::mma_bf16(xi_tm, tc::smem_desc(aXI + xb * IMG + ks * 32 * NP, NP * 16, 128),
+                           tc::smem_desc(aY + ks * 32 * NP, NP * 16, 128), id_mm,
+                           (ks > 0 || xi_on) ? 1u : 0u);
+            xi_on = true;
+            // beta: D = Y . A^T, the transition image read MN-major
+#pragma unroll
+            for (int ks = 0; ks < NP / 16; ++ks)
+              tc::mma_bf16(d_tm, tc::smem_desc(aY + ks * 256, 128, SBO),
+                           tc::smem_desc(aAT + ks * 32 * NP, NP * 16, 128), id_km,
+                           ks > 0 ? 1u : 0u);
+            commit();
+          }
+          // the next step's X image (its buffer was last read before this
+          // step's barrier; with one buffer, after this step's xi product)
+          if (XIB == 2 && t > t0) load_x((t - 1) % 2, img_of(t - 1));
         }
-        cb_pending = false;
-        // copy X_{t-1} for the next step's xi product (sXI is free now)
-        if (tid == 0 && t > t0) copy_x(img_of(t - 1));
-        float bt[32];
+        if (XIB == 1 && has_mma && tid != 0) xph[0] ^= 1;  // thread 0 flipped it in wait_x
+        const float rho_prev = row_sum((t + 1) & 1);
+        if constexpr (XIB == 2) {
+          if (tid != 0 || !has_mma) wait_x(xb);
+          else xph[xb] ^= 1;
+        }
+        if (has_mma) wait_mma();
+        if (XIB == 1 && tid == 0 && t > t0) load_x(0, img_of(t - 1));
+        float bt[COLS];
         if (has_mma) {
-          tc::tmem_ld32(d_tm + lane_off + (uint32_t)(32 * h), bt);
-          tc::tmem_ld_wait();
+          tmem_ld_cols<COLS>(d_tm + my_cols, bt);
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) bt[i] = 0.f;
+          for (int i = 0; i < COLS; ++i) bt[i] = 0.f;
         }
+        if constexpr (XIB == 2) me.get(sXI + xb * IMG, xcur);
+        if constexpr (L::EMIS) me.emis(bb, ocur);
         const bool is_init = act && t == T - 1;
         const bool on = act && t < T - 1;
         if (is_init) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) bt[i] = 1.f;
+          for (int i = 0; i < COLS; ++i) bt[i] = 1.f;
           c = w / st.S_last;
         } else if (on) {
           c = w / (c * rho_prev);
         }
         const bool live = (is_init || on) && isfinite(c);
         const float fc = exp2i(-gcur) * c;  // exact: c times a power of two
-        float part = 0.f;
+        const float2 c2 = make_float2(c, c), fc2 = make_float2(fc, fc);
+        float2 part2 = make_float2(0.f, 0.f);
+        uint32_t gp[COLS / 2], yp[COLS / 2];
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {  // 8 columns = one 16-byte image chunk
-          uint32_t gp[4], yp[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int q = 4 * g8 + u;
-            const float2 xv = unpack_bf16(xcur[q]);
-            const float g0 = xv.x * bt[2 * q], g1 = xv.y * bt[2 * q + 1];
-            part += g0 + g1;
-            float ga = g0 * c, gb = g1 * c;
-            float ya = bb[2 * q] * bt[2 * q] * fc, yb = bb[2 * q + 1] * bt[2 * q + 1] * fc;
-            if (!live) { ga = 0.f; gb = 0.f; ya = 0.f; yb = 0.f; }
-            if (t == 0)
-              __stcg(reinterpret_cast<float2*>(gbuf + (size_t)row * NP + 32 * h + 2 * q),
-                     make_float2(ga, gb));
-            gp[u] = tc::pack_bf16(ga, gb);
-            yp[u] = tc::pack_bf16(ya, yb);
-          }
-          *reinterpret_cast<uint4*>(sY + img_off<NP>(row, 4 * h + g8)) =
-              make_uint4(yp[0], yp[1], yp[2], yp[3]);
-          *reinterpret_cast<uint4*>(sG + img_off<NP>(row, 4 * h + g8)) =
-              make_uint4(gp[0], gp[1], gp[2], gp[3]);
+        for (int q = 0; q < COLS / 2; ++q) {
+          const float2 bt2 = make_float2(bt[2 * q], bt[2 * q + 1]);
+          const float2 g = __fmul2_rn(unpack_bf16(xcur[q]), bt2);
+          part2 = __fadd2_rn(part2, g);
+          float2 ga = __fmul2_rn(g, c2);
+          float2 ya = __fmul2_rn(__fmul2_rn(make_float2(bb[2 * q], bb[2 * q + 1]), bt2), fc2);
+          if (!live) { ga = make_float2(0.f, 0.f); ya = ga; }
+          if (t == 0) __stcg(reinterpret_cast<float2*>(gbuf + (size_t)row * NP + me.col0 + 2 * q), ga);
+          gp[q] = tc::pack_bf16(ga.x, ga.y);
+          yp[q] = tc::pack_bf16(ya.x, ya.y);
         }
+        me.put(sY, yp);
+        me.put(sG, gp);
         if (h == 0) {
           if (kprev >= 0)
             *reinterpret_cast<uint16_t*>(sOH + (kprev >> 7) * 32768 + img_off<128>(kprev & 127, row >> 3) +
@@ -546,23 +595,23 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
             kprev = ocur;
           }
         }
-        psum[h * 128 + row] = live ? part : 0.f;
+        psum[((t & 1) * TPR + h) * 128 + row] = live ? part2.x + part2.y : 0.f;
         if (!live) c = 0.f;
-        // prefetch step t - 1
+        // next step's inputs
         if (t > t0) {
-          img_get_global<NP>(img_of(t - 1), row, h, xcur);
-          ocur = (t - 1 < T) ? __ldg(o + t - 1) : 0;
-          if ((unsigned)ocur >= (unsigned)M) ocur = 0;
-          load_emis<NP>(bb, Bk, ocur, h);
+          ocur = sym_at(t - 1);
           gcur = (int)__ldcg(gexp + (size_t)(t - 1) * 128 + row);
+          if constexpr (XIB == 1) me.get_global(img_of(t - 1), xcur);
+          if constexpr (!L::EMIS) me.emis(bb, ocur);
         }
         tc::fence_proxy_async();
         cb_pending = true;
       }
-      if (aborted) break;
+      if (stop) break;
       // the segment's last emission product, before gamma's buffer is reused
       tc::fence_before_sync();
       __syncthreads();
+      if (misc[M_ABORT]) { stop = true; break; }
       if (tid == 0) {
         tc::fence_after_sync();
 #pragma unroll
@@ -577,25 +626,28 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
         commit();
       }
       cb_pending = false;
-      if (!wait_mma()) { aborted = true; break; }
+      wait_mma();
     }
-    if (aborted) break;
+    if (stop) break;
+    tc::fence_before_sync();
+    __syncthreads();
+    if (misc[M_ABORT]) break;
+    tc::fence_after_sync();
 
     // ---------------- tile counts -> slot ----------------
     float* slot = a.slots + (size_t)tile * a.slot_floats;
     if (wq * 32 < NP) {  // xi rows i = row (warp-uniform)
-      float v[32];
+      float v[COLS];
       if (Lt >= 2) {
-        tc::tmem_ld32(xi_tm + lane_off + (uint32_t)(32 * h), v);
-        tc::tmem_ld_wait();
+        tmem_ld_cols<COLS>(xi_tm + my_cols, v);
       } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        for (int i = 0; i < COLS; ++i) v[i] = 0.f;
       }
-      const float4* a4 = reinterpret_cast<const float4*>(Ak + (size_t)row * NP + 32 * h);
-      float4* d4 = reinterpret_cast<float4*>(slot + NP + (size_t)row * NP + 32 * h);
+      const float4* a4 = reinterpret_cast<const float4*>(Ak + (size_t)row * NP + me.col0);
+      float4* d4 = reinterpret_cast<float4*>(slot + NP + (size_t)row * NP + me.col0);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < COLS / 4; ++q) {
         const float4 av = __ldg(a4 + q);
         d4[q] = make_float4(v[4 * q] * av.x, v[4 * q + 1] * av.y, v[4 * q + 2] * av.z,
                             v[4 * q + 3] * av.w);
@@ -603,14 +655,13 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
     }
 #pragma unroll
     for (int b = 0; b < MB; ++b) {
-      float v[32];
-      tc::tmem_ld32(cb_tm + (uint32_t)(b * NP) + lane_off + (uint32_t)(32 * h), v);
-      tc::tmem_ld_wait();
+      float v[COLS];
+      tmem_ld_cols<COLS>(cb_tm + (uint32_t)(b * NP) + my_cols, v);
       const int sym = b * 128 + row;
       if (sym < M) {
         float* dst = slot + NP + (size_t)NP * NP + sym;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) dst[(size_t)(32 * h + jj) * M] = v[jj];
+        for (int jj = 0; jj < COLS; ++jj) dst[(size_t)(me.col0 + jj) * M] = v[jj];
       }
     }
     __syncthreads();
@@ -627,16 +678,14 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, MmaFbCfg<NP, MB>::CTAS)
   }
 
   // teardown: nothing of ours may still be in flight
-  if (aborted) {
-    if (lane == 0 && h == 0) {
-      misc[2] = 1;
-      set_status(a.status, HMM_STATUS_TIMEOUT);
-    }
-  }
   __syncthreads();
   if (tid == 0) {
-    if (mma_pending) tc::mbar_wait_bounded(mbar, m_par, kFbWaitLimit);
-    if (x_inflight) tc::mbar_wait_bounded(xbar, x_par, kFbWaitLimit);
+    if (misc[M_ABORT]) set_status(a.status, HMM_STATUS_TIMEOUT);
+    if (m_pend) tc::mbar_wait_bounded(mbar, m_par, kFbWaitLimit);
+    if (g_pend) tc::mbar_wait_bounded(gbar, g_par, kFbWaitLimit);
+    for (int b = 0; b < XIB; ++b)
+      if (x_pend[b]) tc::mbar_wait_bounded(&xbar[b], x_par[b], kFbWaitLimit);
+    tc::bulk_wait_all();
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -657,16 +706,10 @@ static cudaError_t launch_fb_mma_t(int grid, const MmaFbLaunch& a, cudaStream_t 
 static int fb_mma_blocks(int M) { return (M + 127) / 128; }
 
 bool fb_mma_supported(int NP, int M) {
-  if (NP == 64) return fb_mma_blocks(M) <= 2;
-  if (NP == 128) return fb_mma_blocks(M) <= 2;
-  return false;
+  return (NP == 64 || NP == 128) && fb_mma_blocks(M) <= 2;
 }
 
-int fb_mma_ctas_per_sm(int NP, int M) {
-  const int mb = fb_mma_blocks(M);
-  if (NP == 64) return mb == 1 ? MmaFbCfg<64, 1>::CTAS : MmaFbCfg<64, 2>::CTAS;
-  return mb == 1 ? MmaFbCfg<128, 1>::CTAS : MmaFbCfg<128, 2>::CTAS;
-}
+int fb_mma_ctas_per_sm(int, int) { return 1; }
 
 cudaError_t launch_fb_mma(int NP, int M, int grid, const MmaFbLaunch& a, cudaStream_t st) {
   const int mb = fb_mma_blocks(M);

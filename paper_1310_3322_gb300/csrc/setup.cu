@@ -163,7 +163,12 @@ __device__ void stable_pass(const int32_t* in, int32_t* out, int n, DigitFn digi
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < 256) base[tid] = 0;
   __syncthreads();
-  for (int i = tid; i < n; i += kPlanThreads) atomicAdd(&base[digit(in[i])], 1);
+  for (int c0 = 0; c0 < n; c0 += kPlanThreads) {  // one atomic per distinct digit per warp
+    const int i = c0 + tid;
+    const int d = i < n ? digit(in[i]) : 256;
+    const unsigned peers = __match_any_sync(HMM_FULL_MASK, d);
+    if (d < 256 && lane == __ffs(peers) - 1) atomicAdd(&base[d], __popc(peers));
+  }
   __syncthreads();
   if (warp == 0) {  // exclusive scan of the 256 digit counts
     int v[8], sum = 0;
@@ -208,24 +213,20 @@ __device__ void stable_pass(const int32_t* in, int32_t* out, int n, DigitFn digi
 
 __device__ __forceinline__ int len_key(int T) { return kLenBuckets - 1 - length_bucket(T); }
 
-// Longest row of a tile: the length buckets above 255 are wider than one
-// length, so the first row of a tile is not always the longest.
-__device__ int tile_max_len(const int32_t* seqlen, const int32_t* sorted, int p, int rows) {
-  int mx = 0;
-  for (int q = p; q < p + rows; ++q) mx = max(mx, seqlen[sorted[q]]);
-  return mx;
-}
-
-// First position p in [0, n) with key(p) >= k (keys non-decreasing).
-template <typename KeyFn>
-__device__ int lower_bound_pos(int n, int k, KeyFn key) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (key(mid) < k) lo = mid + 1;
-    else hi = mid;
+// Length of every tile = its longest row (the length buckets above 255 are
+// wider than one length, so the first row is not always the longest); one
+// warp per tile.
+__device__ void tile_lengths(const MmaPlanArgs& a, int n_tiles) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int id = warp; id < n_tiles; id += kPlanThreads / 32) {
+    const int p = a.tile_start[id], rows = a.tile_rows[id];
+    int mx = 0;
+    for (int q = lane; q < rows; q += 32) mx = max(mx, a.seqlen[a.sorted[p + q]]);
+    mx = __reduce_max_sync(HMM_FULL_MASK, mx);
+    if (lane == 0) a.tile_len[id] = mx;
   }
-  return lo;
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
@@ -282,28 +283,33 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
   if (a.labelled) {
     const int32_t* sorted = a.sorted;
     auto model_at = [sorted, mos](int p) { return mos[sorted[p]]; };
+    // first and one-past-last position of every model's group
+    for (int p = tid; p < n; p += kPlanThreads) {
+      const int k = model_at(p);
+      if (p == 0 || model_at(p - 1) != k) a.group_start[k] = p;
+      if (p == n - 1 || model_at(p + 1) != k) a.group_end[k] = p + 1;
+    }
+    __syncthreads();
     for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
       const int p = c0 + tid;
-      int flag = 0, k = 0, gs = 0, ge = 0;
+      int flag = 0, k = 0, ge = 0;
       if (p < n) {
         k = model_at(p);
-        gs = lower_bound_pos(n, k, model_at);
-        ge = lower_bound_pos(n, k + 1, model_at);
-        flag = ((p - gs) % 128) == 0 ? 1 : 0;
+        ge = a.group_end[k];
+        flag = ((p - a.group_start[k]) % 128) == 0 ? 1 : 0;
       }
       const int id = n_tiles + block_exclusive_scan<int>(flag, itmp, &total);
       if (flag && id < a.n_tiles_cap) {
-        const int rows = min(128, ge - p);
         a.tile_start[id] = p;
-        a.tile_rows[id] = rows;
+        a.tile_rows[id] = min(128, ge - p);
         a.tile_model[id] = k;
-        a.tile_len[id] = tile_max_len(seqlen, sorted, p, rows);
         a.tile_order[id] = id;
       }
       n_tiles += total;
       __syncthreads();
     }
     n_tiles = min(n_tiles, a.n_tiles_cap);
+    tile_lengths(a, n_tiles);
     // longest tiles first (stable in tile index)
     const int32_t* tl = a.tile_len;
     auto t0 = [tl](int t) { return len_key(tl[t]) & 255; };
@@ -317,13 +323,13 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
     n_tiles = min(n_chunks * a.K, a.n_tiles_cap);
     for (int id = tid; id < n_tiles; id += kPlanThreads) {
       const int c = id / a.K, k = id % a.K;
-      const int rows = min(128, n - 128 * c);
       a.tile_start[id] = 128 * c;
-      a.tile_rows[id] = rows;
+      a.tile_rows[id] = min(128, n - 128 * c);
       a.tile_model[id] = k;
-      a.tile_len[id] = tile_max_len(seqlen, a.sorted, 128 * c, rows);
       a.tile_order[id] = id;
     }
+    __syncthreads();
+    tile_lengths(a, n_tiles);
   }
   for (int id = n_tiles + tid; id < a.n_tiles_cap; id += kPlanThreads) {
     a.tile_len[id] = -1;

@@ -52,25 +52,35 @@ namespace hmmgb {
 
 template <int NP, int MB>
 struct MmaFbCfg {
-  static constexpr int TPR = 4;                  // threads per row
-  static constexpr int NTH = 128 * TPR;
-  static constexpr int COLS = NP / TPR;          // columns per thread (16 or 32)
-  static constexpr int CH = COLS / 8;            // 16-byte image chunks per thread
+  // epilogue threads per row: 4 at N = 64 (17 warps: at most 96 registers a
+  // thread), 2 at N = 128 (9 warps, room for 64 prefetched emission values)
+  static constexpr int TPR = NP == 64 ? 4 : 2;
+  static constexpr int NEP = 128 * TPR;          // epilogue threads
+  static constexpr int NTH = NEP + 32;           // + the control warp (MMAs and copies)
+  static constexpr int COLS = NP / TPR;          // columns per epilogue thread (16 or 64)
+  static constexpr int SUB = COLS < 32 ? COLS : 32;  // columns per tensor-memory load
+  static constexpr int NSUB = COLS / SUB;
   static constexpr int IMG = 128 * NP * 2;       // one 128-row BF16 image
   static constexpr int MAT = NP * NP * 2;        // the BF16 transition image
-  static constexpr bool EMIS = (NP == 64 && MB == 1);   // emission table in shared memory
-  static constexpr int XIB = (NP == 64 || MB == 1) ? 2 : 1;  // X_t buffers
+  static constexpr bool EMIS = (NP == 64 && MB == 1);  // emission table in shared memory
+  static constexpr bool DB = (NP == 64 && MB == 1);    // two operand sets: beta issued first
+  static constexpr int NB = DB ? 2 : 1;                // Y / gamma / one-hot sets
+  static constexpr int XIB = 2;                  // X_t buffers
   static constexpr int ES = NP * 4 + 16;         // padded emission row (bytes)
   static constexpr int OFF_AT = 0;               // (n=j, k=i) = a_ij: forward K-major, backward MN-major
   static constexpr int OFF_XI = MAT;             // X_t images (xi A operand; epilogue rows)
-  static constexpr int OFF_Y = OFF_XI + XIB * IMG;   // Y_t
-  static constexpr int OFF_G = OFF_Y + IMG;      // gamma_t; the forward X operand in phase 1 / recompute
-  static constexpr int OFF_OH = OFF_G + IMG;     // one-hot [k][m], MB blocks of 128 x 128
-  static constexpr int OFF_B = OFF_OH + MB * 32768;  // emission rows b(k), k < 128 (EMIS)
+  static constexpr int OFF_Y = OFF_XI + XIB * IMG;     // Y_t sets
+  static constexpr int OFF_G = OFF_Y + NB * IMG;       // gamma_t sets
+  static constexpr int OFF_OH = OFF_G + NB * IMG;      // one-hot [k][m] sets, MB blocks of 128 x 128
+  static constexpr int OFF_XOP = OFF_OH + NB * MB * 32768;  // forward X operand (else aliases gamma)
+  static constexpr int OFF_B = OFF_XOP + (DB ? IMG : 0);    // emission rows b(k), k < 128 (EMIS)
   static constexpr int OFF_PS = OFF_B + (EMIS ? 128 * ES : 0);  // row partial sums [2][TPR][128]
-  static constexpr int OFF_BAR = OFF_PS + 2 * TPR * 128 * 4;    // mma, gload, xi[2]
-  static constexpr int OFF_MISC = OFF_BAR + 64;
+  static constexpr int NBAR = 10;                // mbarriers (see the kernel)
+  static constexpr int OFF_BAR = OFF_PS + 2 * TPR * 128 * 4;
+  static constexpr int OFF_MISC = OFF_BAR + 128;
+  static_assert(NBAR * 8 <= OFF_MISC - OFF_BAR, "mbarrier area");
   static constexpr int TOTAL = OFF_MISC + 64;
+  static constexpr int XOP = DB ? OFF_XOP : OFF_G;
   static constexpr int TMEM_USED = (2 + MB) * NP;  // D, XI, CB blocks
   static constexpr int TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
 };
@@ -127,51 +137,54 @@ __device__ __forceinline__ void fb_close(FbRow& st, float sigma, int t, int T) {
   st.f = min(126, max(-126, exponent_of_fb(sigma)));
 }
 
-// Per-thread view of one tile row: the row, its column range and where its
-// emission rows come from.
+// Per-thread view of one tile row: the row, its column range (in sub-chunks
+// of SUB columns) and where its emission rows come from.
 template <int NP, int MB>
 struct FbThread {
   using L = MmaFbCfg<NP, MB>;
+  static constexpr int SUB = L::SUB;
   int row, col0;
   const uint8_t* sB;   // shared emission table (EMIS)
   const float* Bk;     // global emission table of the model [M][NP]
 
-  // b_j(sym) for this thread's columns
-  __device__ __forceinline__ void emis(float (&b)[L::COLS], int sym) const {
-    if constexpr (L::EMIS) {
-      const float4* p = reinterpret_cast<const float4*>(sB + sym * L::ES + col0 * 4);
+  // b_j(sym) for this thread's columns: sub-chunk `sub` from the shared
+  // table, or all of them from memory (prefetched a step ahead)
+  __device__ __forceinline__ void emis_sub(float (&b)[SUB], int sym, int sub) const {
+    const float4* p = reinterpret_cast<const float4*>(sB + sym * L::ES + (col0 + sub * SUB) * 4);
 #pragma unroll
-      for (int q = 0; q < L::COLS / 4; ++q) {
-        const float4 v = p[q];
-        b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
-      }
-    } else {
-      const float4* p = reinterpret_cast<const float4*>(Bk + (size_t)sym * NP + col0);
-#pragma unroll
-      for (int q = 0; q < L::COLS / 4; ++q) {
-        const float4 v = __ldg(p + q);
-        b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
-      }
+    for (int q = 0; q < SUB / 4; ++q) {
+      const float4 v = p[q];
+      b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
     }
   }
-  // this thread's columns of the row image: write (BF16 pairs) / read
-  __device__ __forceinline__ void put(uint8_t* img, const uint32_t (&w)[L::COLS / 2]) const {
+  __device__ __forceinline__ void emis_all(float (&b)[L::COLS], int sym) const {
+    const float4* p = reinterpret_cast<const float4*>(Bk + (size_t)sym * NP + col0);
 #pragma unroll
-    for (int c = 0; c < L::CH; ++c)
-      *reinterpret_cast<uint4*>(img + img_off<NP>(row, col0 / 8 + c)) =
+    for (int q = 0; q < L::COLS / 4; ++q) {
+      const float4 v = __ldg(p + q);
+      b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+    }
+  }
+  // sub-chunk `sub` of this thread's columns of a row image (BF16 pairs)
+  __device__ __forceinline__ uint32_t off(int sub, int c) const {
+    return img_off<NP>(row, (col0 + sub * SUB) / 8 + c);
+  }
+  __device__ __forceinline__ void put(uint8_t* img, int sub, const uint32_t (&w)[SUB / 2]) const {
+#pragma unroll
+    for (int c = 0; c < SUB / 8; ++c)
+      *reinterpret_cast<uint4*>(img + off(sub, c)) =
           make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
   }
-  __device__ __forceinline__ void get(const uint8_t* img, uint32_t (&w)[L::COLS / 2]) const {
+  __device__ __forceinline__ void put_global(uint8_t* img, int sub, const uint32_t (&w)[SUB / 2]) const {
 #pragma unroll
-    for (int c = 0; c < L::CH; ++c) {
-      const uint4 v = *reinterpret_cast<const uint4*>(img + img_off<NP>(row, col0 / 8 + c));
-      w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
-    }
+    for (int c = 0; c < SUB / 8; ++c)
+      __stcg(reinterpret_cast<uint4*>(img + off(sub, c)),
+             make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]));
   }
-  __device__ __forceinline__ void get_global(const uint8_t* img, uint32_t (&w)[L::COLS / 2]) const {
+  __device__ __forceinline__ void get(const uint8_t* img, int sub, uint32_t (&w)[SUB / 2]) const {
 #pragma unroll
-    for (int c = 0; c < L::CH; ++c) {
-      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(img + img_off<NP>(row, col0 / 8 + c)));
+    for (int c = 0; c < SUB / 8; ++c) {
+      const uint4 v = *reinterpret_cast<const uint4*>(img + off(sub, c));
       w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
     }
   }
@@ -180,8 +193,8 @@ struct FbThread {
 // Forward step epilogue: y = D . b . 2^-f (zero when not live), packed into
 // the operand image; returns the partial row sum.
 template <int COLS>
-__device__ __forceinline__ float fwd_epilogue(float (&y)[COLS], const float (&b)[COLS], int f,
-                                              bool live, uint32_t (&w)[COLS / 2]) {
+__device__ __forceinline__ float fwd_epilogue(float (&y)[COLS], const float* b, int f, bool live,
+                                              uint32_t (&w)[COLS / 2]) {
   const float fac = exp2i(-f);
   const float2 f2 = make_float2(fac, fac);
 #pragma unroll
@@ -195,26 +208,52 @@ __device__ __forceinline__ float fwd_epilogue(float (&y)[COLS], const float (&b)
   return tree_sum<COLS>(y);
 }
 
+// Bounded mbarrier wait that also gives up once another thread has recorded
+// an abort; a timeout records one.
+__device__ __forceinline__ bool fb_wait(uint64_t* bar, uint32_t parity,
+                                        volatile int32_t* abort_flag) {
+  for (uint32_t i = 0; i < kFbWaitLimit; ++i) {
+    if (tc::mbar_test(bar, parity)) return true;
+    if ((i & 31) == 31 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// One-hot entry (symbol k, row m) of a 128-column block set.
+__device__ __forceinline__ uint16_t* onehot_at(uint8_t* set, int k, int m) {
+  return reinterpret_cast<uint16_t*>(set + (k >> 7) * 32768 + img_off<128>(k & 127, m >> 3) +
+                                     (m & 7) * 2);
+}
+
 template <int NP, int MB>
 __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaunch a) {
   using L = MmaFbCfg<NP, MB>;
-  constexpr int TPR = L::TPR, NTH = L::NTH, IMG = L::IMG, COLS = L::COLS, XIB = L::XIB;
+  constexpr int TPR = L::TPR, NEP = L::NEP, IMG = L::IMG, COLS = L::COLS, XIB = L::XIB;
+  constexpr int NB = L::NB;
+  constexpr bool DB = L::DB;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAT = smem + L::OFF_AT;
   uint8_t* sXI = smem + L::OFF_XI;
   uint8_t* sY = smem + L::OFF_Y;
   uint8_t* sG = smem + L::OFF_G;
   uint8_t* sOH = smem + L::OFF_OH;
+  uint8_t* sXO = smem + L::XOP;
   float* psum = reinterpret_cast<float*>(smem + L::OFF_PS);  // [2][TPR][128]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
-  uint64_t* mbar = bars;       // MMA commits
-  uint64_t* gbar = bars + 1;   // checkpoint -> forward operand loads
-  uint64_t* xbar = bars + 2;   // [XIB] X_t image loads
+  uint64_t* b_rdy = bars + 0;    // epilogue -> control: operands written
+  uint64_t* b_done = bars + 1;   // the products the epilogue waits for
+  uint64_t* b_aux = bars + 2;    // [2] xi (+ emission) products of even / odd steps: control only
+  uint64_t* b_seg = bars + 4;    // segment-end emission product: control only
+  uint64_t* b_g = bars + 5;      // checkpoint -> forward operand
+  uint64_t* b_x = bars + 6;      // [2] X_t images
+  uint64_t* b_fin = bars + 8;    // teardown after an abort (bars + 9 unused)
   volatile int32_t* misc = reinterpret_cast<volatile int32_t*>(smem + L::OFF_MISC);
   enum { M_TMEM = 0, M_ITEM = 1, M_ABORT = 2 };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wq = warp & 3, h = warp >> 2;
+  const bool ctrl = warp == NEP / 32;
+  const int wq = warp & 3, h = (warp >> 2) & 3;
   const int K = a.seq.K, M = a.seq.M;
   FbThread<NP, MB> me;
   me.row = wq * 32 + lane;
@@ -222,11 +261,11 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
   me.sB = smem + L::OFF_B;
   const int row = me.row;
 
-  for (int i = tid; i < MB * 32768 / 16; i += NTH)
+  for (int i = tid; i < NB * MB * 32768 / 16; i += L::NTH)
     reinterpret_cast<uint4*>(sOH)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), L::TMEM_COLS);
   if (tid == 0) {
-    for (int i = 0; i < 2 + XIB; ++i) tc::mbar_init(&bars[i], 1);
+    for (int i = 0; i < L::NBAR; ++i) tc::mbar_init(&bars[i], 1);
     misc[M_ABORT] = 0;
   }
   tc::fence_proxy_async();
@@ -240,7 +279,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
   constexpr uint32_t id_kk = tc::instr_desc(1, 128, NP);               // A, B K-major
   constexpr uint32_t id_mm = id_kk | (1u << 15) | (1u << 16);          // A, B MN-major
   constexpr uint32_t id_km = id_kk | (1u << 16);                       // B MN-major
-  const uint32_t aAT = tc::smem_u32(sAT), aXI = tc::smem_u32(sXI);
+  const uint32_t aAT = tc::smem_u32(sAT), aXI = tc::smem_u32(sXI), aXO = tc::smem_u32(sXO);
   const uint32_t aY = tc::smem_u32(sY), aG = tc::smem_u32(sG), aOH = tc::smem_u32(sOH);
   constexpr uint32_t SBO = NP * 16;
 
@@ -249,52 +288,16 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
   int8_t* gexp = a.gexp + (size_t)blockIdx.x * a.gexp_bytes;
   float* gbuf = a.gbuf + (size_t)blockIdx.x * 128 * NP;
 
-  // barrier phases (every thread tracks them; thread 0 also remembers what
-  // it has in flight for the teardown)
-  uint32_t mph = 0, gph = 0, xph[2] = {0, 0};
-  bool m_pend = false, g_pend = false, x_pend[2] = {false, false};
-  uint32_t m_par = 0, g_par = 0, x_par[2] = {0, 0};
+  // barrier phases: the epilogue threads track b_done and b_x, the control
+  // lane every barrier it waits on (each waiter waits every phase, in order)
+  uint32_t ph_done = 0, ph_x[2] = {0, 0};
+  uint32_t c_rdy = 0, c_aux[2] = {0, 0}, c_seg = 0, c_g = 0;
+  uint32_t c_x[2] = {0, 0};      // parity the next load into each X buffer completes
+  uint32_t c_xpar[2] = {0, 0};   // ... and that of the last one issued
+  bool c_xpend[2] = {false, false}, c_gpend = false;
+  uint32_t c_gpar = 0;
   int cur_model = -1;
-
-  auto fail = [&]() { misc[M_ABORT] = 1; };
-  auto commit = [&]() {  // thread 0
-    tc::mma_commit(mbar);
-    m_pend = true;
-    m_par = mph;
-  };
-  auto wait_mma = [&]() {  // every thread; a timeout is acted on at the next barrier
-    if (!tc::mbar_wait_bounded(mbar, mph, kFbWaitLimit)) fail();
-    else if (tid == 0) m_pend = false;
-    mph ^= 1;
-    tc::fence_after_sync();
-  };
-  auto load_x = [&](int b, const uint8_t* src) {  // thread 0: sXI[b] <- one row image
-    tc::mbar_arrive_expect_tx(&xbar[b], IMG);
-    tc::bulk_g2s(aXI + b * IMG, src, IMG, &xbar[b]);
-    x_pend[b] = true;
-    x_par[b] = xph[b];
-  };
-  auto wait_x = [&](int b) {  // every thread
-    if (!tc::mbar_wait_bounded(&xbar[b], xph[b], kFbWaitLimit)) fail();
-    else if (tid == 0) x_pend[b] = false;
-    xph[b] ^= 1;
-  };
-  auto issue_fwd = [&]() {  // D = X_op . A   (X_op in sG)
-#pragma unroll
-    for (int ks = 0; ks < NP / 16; ++ks)
-      tc::mma_bf16(d_tm, tc::smem_desc(aG + ks * 256, 128, SBO),
-                   tc::smem_desc(aAT + ks * 256, 128, SBO), id_kk, ks > 0 ? 1u : 0u);
-  };
-  auto store_img = [&](uint8_t* dst) {  // thread 0: sG -> global image
-    tc::bulk_s2g(dst, aG, IMG);
-    tc::bulk_commit();
-  };
-  auto row_sum = [&](int par) {
-    float s = 0.f;
-#pragma unroll
-    for (int q = 0; q < TPR; ++q) s += psum[(par * TPR + q) * 128 + row];
-    return s;
-  };
+  volatile int32_t* abortp = misc + M_ABORT;
 
   for (;;) {
     __syncthreads();
@@ -307,19 +310,18 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
     const int start = a.tile_start[tile];
     const int nrows = a.tile_rows[tile];
     const int Lt = a.tile_len[tile];
-
     const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
     me.Bk = a.mod.Btp + (size_t)k * M * NP;
     if (k != cur_model) {
       // transition image: (n = j, k = i) = a_ij, pairs along i
-      for (int idx = tid; idx < NP * NP / 2; idx += NTH) {
+      for (int idx = tid; idx < NP * NP / 2; idx += L::NTH) {
         const int j = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
         const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + (i + 1) * NP + j));
         *reinterpret_cast<uint32_t*>(sAT + (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 +
                                      (i % 8) * 2) = w;
       }
       if constexpr (L::EMIS) {  // emission rows of the model, padded
-        for (int idx = tid; idx < M * (NP / 4); idx += NTH) {
+        for (int idx = tid; idx < M * (NP / 4); idx += L::NTH) {
           const int sym = idx / (NP / 4), q = idx % (NP / 4);
           *reinterpret_cast<float4*>(smem + L::OFF_B + sym * L::ES + q * 16) =
               __ldg(reinterpret_cast<const float4*>(me.Bk + (size_t)sym * NP) + q);
@@ -329,364 +331,438 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
       tc::fence_proxy_async();
       __syncthreads();
     }
-
-    const bool has = row < nrows;
-    const int s = has ? a.sorted[start + row] : 0;
-    const int T = has ? a.seq.seqlen[s] : 0;
-    const size_t oidx = a.labelled ? (size_t)s : (size_t)s * K + k;
-    const float w = has ? (a.weight ? a.weight[oidx] : 1.f) : 0.f;
-    const int32_t* o = a.seq.symbols + (has ? a.seq.offsets[s] : 0);
     const int C = fb_mma_segment(Lt);
     const int NS = (Lt + C - 1) / C;
-    auto sym_at = [&](int t) -> int {  // symbol at step t (0 past the row's end)
-      if (t >= T) return 0;
-      const int v = __ldg(o + t);
-      return (unsigned)v < (unsigned)M ? v : 0;
-    };
 
-    // ---------------- phase 1: forward, checkpoints every C steps ----------------
-    FbRow st;
-    st.F = 0; st.f = 0; st.dead = false; st.bad = false; st.written = false;
-    st.err = 0; st.ll = 0.f; st.S_last = 0.f;
-    {
-      int o0 = T > 0 ? __ldg(o) : 0;
-      if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
-      const bool live = T > 0 && !st.bad;
-      float b[COLS], y[COLS];
-      me.emis(b, o0);
-      const float* pik = a.mod.pip + (size_t)k * NP + me.col0;
+    if (ctrl) {
+      // ======================= control lane: every MMA and copy =======================
+      if (lane == 0) {
+        bool ok = true;
+        auto wait_c = [&](uint64_t* bar, uint32_t& ph) {
+          ok = ok && fb_wait(bar, ph, abortp);
+          ph ^= 1;
+          return ok;
+        };
+        auto issue_fwd = [&]() {  // D = X_op . A
+          tc::fence_after_sync();
 #pragma unroll
-      for (int i = 0; i < COLS; ++i) y[i] = __ldg(pik + i);
-      uint32_t wv[COLS / 2];
-      const float sum = fwd_epilogue<COLS>(y, b, 0, live, wv);
-      me.put(sG, wv);
-      psum[(0 * TPR + h) * 128 + row] = sum;
-      if (h == 0) __stcg(gexp + row, (int8_t)0);
-    }
-    int o_n1 = (1 < T) ? __ldg(o + 1) : 0;  // symbol of the next step
-    int o_n2 = (2 < T) ? __ldg(o + 2) : 0;  // and the one after
-    float bcur[COLS];
-    if constexpr (!L::EMIS) me.emis(bcur, (unsigned)o_n1 < (unsigned)M ? o_n1 : 0);
-    tc::fence_proxy_async();
-
-    for (int t = 1; t < Lt; ++t) {
-      tc::fence_before_sync();
-      __syncthreads();
-      if (misc[M_ABORT]) break;
-      if (tid == 0) {
-        tc::fence_after_sync();
-        issue_fwd();
-        if ((t - 1) % C == 0) {  // checkpoint X_{t-1} while the MMA reads it too
-          store_img(ckpt + (size_t)((t - 1) / C) * IMG);
-          tc::bulk_wait_read();
+          for (int ks = 0; ks < NP / 16; ++ks)
+            tc::mma_bf16(d_tm, tc::smem_desc(aXO + ks * 256, 128, SBO),
+                         tc::smem_desc(aAT + ks * 256, 128, SBO), id_kk, ks > 0 ? 1u : 0u);
+          tc::mma_commit(b_done);
+        };
+        auto load_x = [&](int t, const uint8_t* src) {
+          const int b = t % XIB;
+          tc::mbar_arrive_expect_tx(&b_x[b], IMG);
+          tc::bulk_g2s(aXI + b * IMG, src, IMG, &b_x[b]);
+          c_xpend[b] = true;   // the epilogue waits for it too; the last step's
+          c_xpar[b] = c_x[b];  // load is waited for by the epilogue alone
+          c_x[b] ^= 1;
+        };
+        bool xi_on = false, cb_on = false;
+        // the xi / emission products of step t are committed to b_aux[t % 2]:
+        // one outstanding phase per barrier at most
+        bool aux_pend[2] = {false, false};
+        auto wait_aux = [&](int b) {
+          if (aux_pend[b] && ok) { wait_c(&b_aux[b], c_aux[b]); aux_pend[b] = false; }
+        };
+        // phase 1
+        for (int t = 1; t < Lt && ok; ++t) {
+          if (!wait_c(b_rdy, c_rdy)) break;
+          issue_fwd();
         }
-        commit();
+        if (ok) wait_c(b_rdy, c_rdy);  // phase 1 finished, checkpoints in memory
+        // phase 2
+        for (int seg = NS - 1; seg >= 0 && ok; --seg) {
+          const int t0 = seg * C, t1 = min(t0 + C, Lt);
+          const uint8_t* ck = ckpt + (size_t)seg * IMG;
+          auto img_of = [&](int t) -> const uint8_t* {
+            return t == t0 ? ck : scr + (size_t)(t - t0) * IMG;
+          };
+          if (t1 - t0 > 1) {  // recompute from the checkpoint
+            tc::mbar_arrive_expect_tx(b_g, IMG);
+            tc::bulk_g2s(aXO, ck, IMG, b_g);
+            c_gpend = true;
+            c_gpar = c_g;
+            if (!wait_c(b_g, c_g)) break;
+            c_gpend = false;
+            for (int t = t0 + 1; t < t1 && ok; ++t) {
+              if (t > t0 + 1 && !wait_c(b_rdy, c_rdy)) break;
+              issue_fwd();
+            }
+            if (!ok || !wait_c(b_rdy, c_rdy)) break;  // images of the segment in memory
+          }
+          // backward
+          if (XIB == 2 || t1 - 1 < Lt - 1) load_x(t1 - 1, img_of(t1 - 1));
+          bool cb_pending = false;
+          for (int t = t1 - 1; t >= t0 && ok; --t) {
+            const int S1 = (t + 1) % NB;  // operand set written by the previous step
+            if (t < Lt - 1) {
+              if (t < t1 - 1 && !wait_c(b_rdy, c_rdy)) break;
+              tc::fence_after_sync();
+              auto issue_beta = [&]() {  // D = Y_{t+1} . A^T (transition image MN-major)
+#pragma unroll
+                for (int ks = 0; ks < NP / 16; ++ks)
+                  tc::mma_bf16(d_tm, tc::smem_desc(aY + S1 * IMG + ks * 256, 128, SBO),
+                               tc::smem_desc(aAT + ks * 32 * NP, NP * 16, 128), id_km,
+                               ks > 0 ? 1u : 0u);
+              };
+              auto issue_xi_cb = [&]() {
+                uint32_t par = c_xpar[t % XIB];
+                if (!wait_c(&b_x[t % XIB], par)) return;
+                c_xpend[t % XIB] = false;
+                tc::fence_after_sync();
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)
+                  tc::mma_bf16(xi_tm,
+                               tc::smem_desc(aXI + (t % XIB) * IMG + ks * 32 * NP, NP * 16, 128),
+                               tc::smem_desc(aY + S1 * IMG + ks * 32 * NP, NP * 16, 128), id_mm,
+                               (ks > 0 || xi_on) ? 1u : 0u);
+                xi_on = true;
+                if (cb_pending) {
+#pragma unroll
+                  for (int b = 0; b < MB; ++b)
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks)
+                      tc::mma_bf16(cb_tm + (uint32_t)(b * NP),
+                                   tc::smem_desc(aOH + (S1 * MB + b) * 32768 + ks * 256, 128, 2048),
+                                   tc::smem_desc(aG + S1 * IMG + ks * 32 * NP, NP * 16, 128),
+                                   id_km, (ks > 0 || cb_on) ? 1u : 0u);
+                  cb_on = true;
+                }
+                tc::mma_commit(&b_aux[t & 1]);
+                aux_pend[t & 1] = true;
+              };
+              if (DB) {  // beta first: the epilogue waits for it alone
+                issue_beta();
+                tc::mma_commit(b_done);
+                issue_xi_cb();
+              } else {
+                issue_xi_cb();
+                issue_beta();
+                tc::mma_commit(b_done);
+              }
+              if (!ok) break;
+            }
+            // the next step's X image: its buffer was last read by the xi
+            // product of step t+1
+            if (t > t0) {
+              wait_aux((t + 1) & 1);
+              if (!ok) break;
+              load_x(t - 1, img_of(t - 1));
+            }
+            cb_pending = true;
+          }
+          if (!ok) break;
+          // the segment's last emission product, before its buffers are reused
+          if (!wait_c(b_rdy, c_rdy)) break;
+          tc::fence_after_sync();
+          const int S0 = t0 % NB;
+#pragma unroll
+          for (int b = 0; b < MB; ++b)
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks)
+              tc::mma_bf16(cb_tm + (uint32_t)(b * NP),
+                           tc::smem_desc(aOH + (S0 * MB + b) * 32768 + ks * 256, 128, 2048),
+                           tc::smem_desc(aG + S0 * IMG + ks * 32 * NP, NP * 16, 128), id_km,
+                           (ks > 0 || cb_on) ? 1u : 0u);
+          cb_on = true;
+          tc::mma_commit(b_seg);
+          tc::mma_commit(b_done);
+          wait_aux(0);
+          wait_aux(1);
+          wait_c(b_seg, c_seg);
+          // the epilogue has consumed that phase too: a waiter on an mbarrier
+          // must never fall two phases behind
+          wait_c(b_rdy, c_rdy);
+        }
+        if (!ok) {  // nothing of ours may stay in flight
+          tc::mma_commit(b_fin);  // arrives once every MMA issued so far is done
+          tc::mbar_wait_bounded(b_fin, 0, kFbWaitLimit);
+          if (c_gpend) tc::mbar_wait_bounded(b_g, c_gpar, kFbWaitLimit);
+          for (int b = 0; b < XIB; ++b)
+            if (c_xpend[b]) tc::mbar_wait_bounded(&b_x[b], c_xpar[b], kFbWaitLimit);
+        }
       }
-      fb_close(st, row_sum((t - 1) & 1), t - 1, T);
-      const int ot = o_n1;
-      o_n1 = o_n2;
-      o_n2 = (t + 2 < T) ? __ldg(o + t + 2) : 0;
-      if (t < T && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
-      const bool live = t < T && !st.dead && !st.bad;
-      if (live) st.F += st.f;
-      if (h == 0) __stcg(gexp + (size_t)t * 128 + row, (int8_t)st.f);
-      if constexpr (L::EMIS) me.emis(bcur, live ? ot : 0);
-      wait_mma();
-      float y[COLS];
-      tmem_ld_cols<COLS>(d_tm + my_cols, y);
-      uint32_t wv[COLS / 2];
-      const float sum = fwd_epilogue<COLS>(y, bcur, st.f, live, wv);
-      me.put(sG, wv);
-      psum[((t & 1) * TPR + h) * 128 + row] = sum;
-      if constexpr (!L::EMIS)
-        me.emis(bcur, (t + 1 < T && (unsigned)o_n1 < (unsigned)M) ? o_n1 : 0);
+      __syncwarp();
+    } else {
+      // ======================= epilogue warps =======================
+      constexpr int SUB = L::SUB, NSUB = L::NSUB;
+      const bool has = row < nrows;
+      const int s = has ? a.sorted[start + row] : 0;
+      const int T = has ? a.seq.seqlen[s] : 0;
+      const size_t oidx = a.labelled ? (size_t)s : (size_t)s * K + k;
+      const float w = has ? (a.weight ? a.weight[oidx] : 1.f) : 0.f;
+      const int32_t* o = a.seq.symbols + (has ? a.seq.offsets[s] : 0);
+      auto sym_at = [&](int t) -> int {  // symbol at step t (0 past the row's end)
+        if (t >= T) return 0;
+        const int v = __ldg(o + t);
+        return (unsigned)v < (unsigned)M ? v : 0;
+      };
+      auto wait_e = [&](uint64_t* bar, uint32_t& ph) {
+        fb_wait(bar, ph, abortp);
+        ph ^= 1;
+        tc::fence_after_sync();
+      };
+      // all epilogue threads: operands written -> tell the control lane;
+      // returns false (in every thread) once anyone has recorded an abort
+      auto handoff = [&]() -> bool {
+        tc::fence_before_sync();
+        const bool go = tc::bar_and(1, NEP, *abortp == 0);
+        if (go && tid == 0) tc::mbar_arrive(b_rdy);
+        return go;
+      };
+      auto row_sum = [&](int par) {
+        float sum = 0.f;
+#pragma unroll
+        for (int q = 0; q < TPR; ++q) sum += psum[(par * TPR + q) * 128 + row];
+        return sum;
+      };
+      // one forward step's epilogue over this thread's columns: D (tensor
+      // memory) -> X_t (operand image, and `gimg` in memory when not null)
+      float pf[L::EMIS ? 1 : COLS];  // emission values prefetched from memory
+      float bsm[SUB];                // emission values from the shared table (EMIS)
+      auto fwd_step = [&](int f, bool live, uint8_t* gimg) -> float {
+        float sum = 0.f;
+#pragma unroll
+        for (int sub = 0; sub < NSUB; ++sub) {
+          float y[SUB];
+          tmem_ld_cols<SUB>(d_tm + my_cols + (uint32_t)(sub * SUB), y);
+          uint32_t wv[SUB / 2];
+          sum += fwd_epilogue<SUB>(y, L::EMIS ? bsm : pf + sub * SUB, f, live, wv);
+          me.put(sXO, sub, wv);
+          if (gimg) me.put_global(gimg, sub, wv);
+        }
+        return sum;
+      };
+      bool run = true;
+
+      // ---------------- phase 1: forward, checkpoints every C steps ----------------
+      FbRow st;
+      st.F = 0; st.f = 0; st.dead = false; st.bad = false; st.written = false;
+      st.err = 0; st.ll = 0.f; st.S_last = 0.f;
+      {
+        int o0 = T > 0 ? __ldg(o) : 0;
+        if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
+        const bool live = T > 0 && !st.bad;
+        if constexpr (!L::EMIS) me.emis_all(pf, o0);
+        const float* pik = a.mod.pip + (size_t)k * NP + me.col0;
+        float sum = 0.f;
+#pragma unroll
+        for (int sub = 0; sub < NSUB; ++sub) {
+          float y[SUB];
+#pragma unroll
+          for (int i = 0; i < SUB; ++i) y[i] = __ldg(pik + sub * SUB + i);
+          if constexpr (L::EMIS) me.emis_sub(bsm, o0, sub);
+          uint32_t wv[SUB / 2];
+          sum += fwd_epilogue<SUB>(y, L::EMIS ? bsm : pf + sub * SUB, 0, live, wv);
+          me.put(sXO, sub, wv);
+          me.put_global(ckpt, sub, wv);
+        }
+        psum[(0 * TPR + h) * 128 + row] = sum;
+        if (h == 0) __stcg(gexp + row, (int8_t)0);
+      }
+      int o_n1 = (1 < T) ? __ldg(o + 1) : 0;  // symbol of the next step
+      int o_n2 = (2 < T) ? __ldg(o + 2) : 0;  // and the one after
+      if constexpr (!L::EMIS) me.emis_all(pf, (unsigned)o_n1 < (unsigned)M ? o_n1 : 0);
+      tc::fence_proxy_async();
+      if (Lt == 1) tc::fence_proxy_async_all();
+      run = handoff();
+      for (int t = 1; t < Lt && run; ++t) {
+        fb_close(st, row_sum((t - 1) & 1), t - 1, T);
+        const int ot = o_n1;
+        o_n1 = o_n2;
+        o_n2 = (t + 2 < T) ? __ldg(o + t + 2) : 0;
+        if (t < T && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
+        const bool live = t < T && !st.dead && !st.bad;
+        if (live) st.F += st.f;
+        if (h == 0) __stcg(gexp + (size_t)t * 128 + row, (int8_t)st.f);
+        if constexpr (L::EMIS) me.emis_sub(bsm, live ? ot : 0, 0);
+        wait_e(b_done, ph_done);
+        const float sum = fwd_step(st.f, live, t % C == 0 ? ckpt + (size_t)(t / C) * IMG : nullptr);
+        psum[((t & 1) * TPR + h) * 128 + row] = sum;
+        if constexpr (!L::EMIS)
+          me.emis_all(pf, (t + 1 < T && (unsigned)o_n1 < (unsigned)M) ? o_n1 : 0);
+        tc::fence_proxy_async();
+        if (t == Lt - 1) tc::fence_proxy_async_all();  // checkpoints, read by bulk copies
+        run = handoff();
+      }
+      if (run && Lt > 0) fb_close(st, row_sum((Lt - 1) & 1), Lt - 1, T);
+      if (has && h == 0) {
+        float out = st.ll;
+        if (st.bad) out = __int_as_float(0x7fc00000);
+        else if (st.dead) out = -INFINITY;
+        else if (!st.written) out = __int_as_float(0x7fc00000);
+        if (st.bad && st.err) set_status(a.status, st.err);
+        a.loglik[oidx] = out;
+      }
+      if (run) run = tc::bar_and(1, NEP, *abortp == 0);  // sums read before phase 2 writes them
+
+      // ---------------- phase 2: segments backwards ----------------
+      const bool act = has && st.written && !st.dead && !st.bad && w != 0.f;
+      float c = 0.f;               // this row's current normaliser
+      int kprev[2] = {-1, -1};     // one-hot entries set in each operand set
+      for (int seg = NS - 1; seg >= 0 && run; --seg) {
+        const int t0 = seg * C, t1 = min(t0 + C, Lt);
+        // (R) recompute X over the segment from its checkpoint
+        if (t1 - t0 > 1) {
+          int fn = (int)__ldcg(gexp + (size_t)(t0 + 1) * 128 + row);
+          int on = sym_at(t0 + 1);
+          if constexpr (!L::EMIS) me.emis_all(pf, on);
+          for (int t = t0 + 1; t < t1 && run; ++t) {
+            const int f = fn;
+            const int ot = on;
+            if (t + 1 < t1) {
+              fn = (int)__ldcg(gexp + (size_t)(t + 1) * 128 + row);
+              on = sym_at(t + 1);
+            }
+            if constexpr (L::EMIS) me.emis_sub(bsm, ot, 0);
+            wait_e(b_done, ph_done);
+            fwd_step(f, act && t < T, scr + (size_t)(t - t0) * IMG);
+            if constexpr (!L::EMIS)
+              if (t + 1 < t1) me.emis_all(pf, on);
+            tc::fence_proxy_async();
+            if (t == t1 - 1) tc::fence_proxy_async_all();  // images read by bulk copies
+            run = handoff();
+          }
+          if (!run) break;
+        }
+
+        // (B) backward over the segment
+        int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
+        if constexpr (!L::EMIS) me.emis_all(pf, ocur);
+        for (int t = t1 - 1; t >= t0 && run; --t) {
+          const bool has_mma = t < Lt - 1;
+          const int S = t % NB;
+          const float rho_prev = row_sum((t + 1) & 1);
+          if constexpr (L::EMIS) me.emis_sub(bsm, ocur, 0);
+          wait_e(&b_x[t % 2], ph_x[t % 2]);
+          if (has_mma) wait_e(b_done, ph_done);
+          const bool is_init = act && t == T - 1;
+          const bool on = act && t < T - 1;
+          if (is_init) c = w / st.S_last;
+          else if (on) c = w / (c * rho_prev);
+          const bool live = (is_init || on) && isfinite(c);
+          const float fc = exp2i(-gcur) * c;  // exact: c times a power of two
+          const float2 c2 = make_float2(c, c), fc2 = make_float2(fc, fc);
+          float2 part2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int sub = 0; sub < NSUB; ++sub) {
+            float bt[SUB];
+            if (has_mma) {
+              tmem_ld_cols<SUB>(d_tm + my_cols + (uint32_t)(sub * SUB), bt);
+            } else {
+#pragma unroll
+              for (int i = 0; i < SUB; ++i) bt[i] = 0.f;
+            }
+            if (is_init) {
+#pragma unroll
+              for (int i = 0; i < SUB; ++i) bt[i] = 1.f;
+            }
+            uint32_t xw[SUB / 2];
+            me.get(sXI + (t % 2) * IMG, sub, xw);
+            const float* bb = L::EMIS ? bsm : pf + sub * SUB;
+            uint32_t gp[SUB / 2], yp[SUB / 2];
+#pragma unroll
+            for (int q = 0; q < SUB / 2; ++q) {
+              const float2 bt2 = make_float2(bt[2 * q], bt[2 * q + 1]);
+              const float2 g = __fmul2_rn(unpack_bf16(xw[q]), bt2);
+              part2 = __fadd2_rn(part2, g);
+              float2 ga = __fmul2_rn(g, c2);
+              float2 ya = __fmul2_rn(__fmul2_rn(make_float2(bb[2 * q], bb[2 * q + 1]), bt2), fc2);
+              if (!live) { ga = make_float2(0.f, 0.f); ya = ga; }
+              if (t == 0)
+                __stcg(reinterpret_cast<float2*>(gbuf + (size_t)row * NP + me.col0 + sub * SUB +
+                                                 2 * q), ga);
+              gp[q] = tc::pack_bf16(ga.x, ga.y);
+              yp[q] = tc::pack_bf16(ya.x, ya.y);
+            }
+            me.put(sY + S * IMG, sub, yp);
+            me.put(sG + S * IMG, sub, gp);
+          }
+          if (h == 0) {
+            uint8_t* oh = sOH + S * MB * 32768;
+            if (kprev[S] >= 0) *onehot_at(oh, kprev[S], row) = 0;
+            kprev[S] = -1;
+            if (live) {
+              *onehot_at(oh, ocur, row) = 0x3F80;  // BF16 1.0
+              kprev[S] = ocur;
+            }
+          }
+          psum[((t & 1) * TPR + h) * 128 + row] = live ? part2.x + part2.y : 0.f;
+          if (!live) c = 0.f;
+          // next step's inputs
+          if (t > t0) {
+            ocur = sym_at(t - 1);
+            gcur = (int)__ldcg(gexp + (size_t)(t - 1) * 128 + row);
+            if constexpr (!L::EMIS) me.emis_all(pf, ocur);
+          }
+          tc::fence_proxy_async();
+          run = handoff();
+        }
+        if (!run) break;
+        wait_e(b_done, ph_done);  // the segment's last emission product
+        run = handoff();
+      }
+      if (run) {
+        // ---------------- tile counts -> slot ----------------
+        float* slot = a.slots + (size_t)tile * a.slot_floats;
+        if (wq * 32 < NP) {  // xi rows i = row (warp-uniform)
+#pragma unroll
+          for (int sub = 0; sub < NSUB; ++sub) {
+            float v[SUB];
+            if (Lt >= 2) {
+              tmem_ld_cols<SUB>(xi_tm + my_cols + (uint32_t)(sub * SUB), v);
+            } else {
+#pragma unroll
+              for (int i = 0; i < SUB; ++i) v[i] = 0.f;
+            }
+            const int j0 = me.col0 + sub * SUB;
+            const float4* a4 = reinterpret_cast<const float4*>(Ak + (size_t)row * NP + j0);
+            float4* d4 = reinterpret_cast<float4*>(slot + NP + (size_t)row * NP + j0);
+#pragma unroll
+            for (int q = 0; q < SUB / 4; ++q) {
+              const float4 av = __ldg(a4 + q);
+              d4[q] = make_float4(v[4 * q] * av.x, v[4 * q + 1] * av.y, v[4 * q + 2] * av.z,
+                                  v[4 * q + 3] * av.w);
+            }
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < MB; ++b) {
+#pragma unroll
+          for (int sub = 0; sub < NSUB; ++sub) {
+            float v[SUB];
+            tmem_ld_cols<SUB>(cb_tm + (uint32_t)(b * NP + sub * SUB) + my_cols, v);
+            const int sym = b * 128 + row;
+            if (sym < M) {
+              float* dst = slot + NP + (size_t)NP * NP + sym;
+#pragma unroll
+              for (int jj = 0; jj < SUB; ++jj) dst[(size_t)(me.col0 + sub * SUB + jj) * M] = v[jj];
+            }
+          }
+        }
+        tc::bar_sync(1, NEP);
+        if (tid < NP) {
+          float sum = 0.f;
+          for (int m = 0; m < 128; ++m) sum += __ldcg(gbuf + (size_t)m * NP + tid);
+          slot[tid] = sum;
+        }
+      }
+      if (h == 0)
+        for (int q = 0; q < NB; ++q)
+          if (kprev[q] >= 0) *onehot_at(sOH + q * MB * 32768, kprev[q], row) = 0;
       tc::fence_proxy_async();
     }
     tc::fence_before_sync();
     __syncthreads();
     if (misc[M_ABORT]) break;
-    if (tid == 0) {
-      if ((Lt - 1) % C == 0) store_img(ckpt + (size_t)((Lt - 1) / C) * IMG);
-      tc::bulk_wait_all();  // every checkpoint written before phase 2 reads them
-    }
-    if (Lt > 0) fb_close(st, row_sum((Lt - 1) & 1), Lt - 1, T);
-    if (has && h == 0) {
-      float out = st.ll;
-      if (st.bad) out = __int_as_float(0x7fc00000);
-      else if (st.dead) out = -INFINITY;
-      else if (!st.written) out = __int_as_float(0x7fc00000);
-      if (st.bad && st.err) set_status(a.status, st.err);
-      a.loglik[oidx] = out;
-    }
-    __syncthreads();  // every row has read its sums (and thread 0 waited for the checkpoints)
-
-    // ---------------- phase 2: segments backwards ----------------
-    const bool act = has && st.written && !st.dead && !st.bad && w != 0.f;
-    float c = 0.f;        // this row's current normaliser
-    int kprev = -1;       // one-hot entry set by the previous step
-    bool xi_on = false;   // thread 0: an xi MMA has been issued for this tile
-    bool cb_on = false;   // thread 0: an emission MMA has been issued for this tile
-    bool cb_pending = false;
-    bool stop = false;
-    for (int seg = NS - 1; seg >= 0 && !stop; --seg) {
-      const int t0 = seg * C, t1 = min(t0 + C, Lt);
-      const uint8_t* ck = ckpt + (size_t)seg * IMG;
-      auto img_of = [&](int t) -> const uint8_t* {
-        return t == t0 ? ck : scr + (size_t)(t - t0) * IMG;
-      };
-      // (R) recompute X over the segment from its checkpoint
-      if (t1 - t0 > 1) {
-        if (tid == 0) {
-          tc::mbar_arrive_expect_tx(gbar, IMG);
-          tc::bulk_g2s(aG, ck, IMG, gbar);
-          g_pend = true;
-          g_par = gph;
-        }
-        int fn = (int)__ldcg(gexp + (size_t)(t0 + 1) * 128 + row);
-        int on = sym_at(t0 + 1);
-        if constexpr (!L::EMIS) me.emis(bcur, on);
-        for (int t = t0 + 1; t < t1; ++t) {
-          tc::fence_before_sync();
-          __syncthreads();
-          if (misc[M_ABORT]) { stop = true; break; }
-          if (tid == 0) {
-            if (t == t0 + 1) {
-              if (!tc::mbar_wait_bounded(gbar, gph, kFbWaitLimit)) fail();
-              else g_pend = false;
-            }
-            tc::fence_after_sync();
-            issue_fwd();
-            if (t - 1 > t0) {
-              store_img(scr + (size_t)(t - 1 - t0) * IMG);
-              tc::bulk_wait_read();
-            }
-            commit();
-          }
-          if (t == t0 + 1) gph ^= 1;
-          const int f = fn;
-          const int ot = on;
-          if (t + 1 < t1) {
-            fn = (int)__ldcg(gexp + (size_t)(t + 1) * 128 + row);
-            on = sym_at(t + 1);
-          }
-          if constexpr (L::EMIS) me.emis(bcur, ot);
-          wait_mma();
-          float y[COLS];
-          tmem_ld_cols<COLS>(d_tm + my_cols, y);
-          uint32_t wv[COLS / 2];
-          fwd_epilogue<COLS>(y, bcur, f, act && t < T, wv);
-          me.put(sG, wv);
-          if constexpr (!L::EMIS)
-            if (t + 1 < t1) me.emis(bcur, on);
-          tc::fence_proxy_async();
-        }
-        if (stop) break;
-        tc::fence_before_sync();
-        __syncthreads();
-        if (misc[M_ABORT]) break;
-        if (tid == 0) {
-          store_img(scr + (size_t)(t1 - 1 - t0) * IMG);
-          tc::bulk_wait_all();  // the segment's images are in memory (and sG is free)
-        }
-      }
-
-      // (B) backward over the segment
-      uint32_t xcur[COLS / 2];   // X_t of this row (XIB == 1: from memory)
-      float bb[COLS];
-      int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
-      if constexpr (XIB == 1) me.get_global(img_of(t1 - 1), xcur);
-      if constexpr (!L::EMIS) me.emis(bb, ocur);
-      if (tid == 0 && (XIB == 2 || t1 - 1 < Lt - 1)) load_x((t1 - 1) % XIB, img_of(t1 - 1));
-      for (int t = t1 - 1; t >= t0; --t) {
-        const bool has_mma = t < Lt - 1;
-        const int xb = t % XIB;
-        tc::fence_before_sync();
-        __syncthreads();
-        if (misc[M_ABORT]) { stop = true; break; }
-        if (tid == 0) {
-          tc::fence_after_sync();
-          if (has_mma) {
-            if (XIB == 1) wait_x(0);
-            else if (tc::mbar_wait_bounded(&xbar[xb], xph[xb], kFbWaitLimit)) x_pend[xb] = false;
-            else fail();
-            tc::fence_after_sync();
-            if (cb_pending) {
-#pragma unroll
-              for (int b = 0; b < MB; ++b)
-#pragma unroll
-                for (int ks = 0; ks < 8; ++ks)
-                  tc::mma_bf16(cb_tm + (uint32_t)(b * NP),
-                               tc::smem_desc(aOH + b * 32768 + ks * 256, 128, 2048),
-                               tc::smem_desc(aG + ks * 32 * NP, NP * 16, 128), id_km,
-                               (ks > 0 || cb_on) ? 1u : 0u);
-              cb_on = true;
-            }
-#pragma unroll
-            for (int ks = 0; ks < 8; ++ks)
-              tc::mma_bf16(xi_tm, tc::smem_desc(aXI + xb * IMG + ks * 32 * NP, NP * 16, 128),
-                           tc::smem_desc(aY + ks * 32 * NP, NP * 16, 128), id_mm,
-                           (ks > 0 || xi_on) ? 1u : 0u);
-            xi_on = true;
-            // beta: D = Y . A^T, the transition image read MN-major
-#pragma unroll
-            for (int ks = 0; ks < NP / 16; ++ks)
-              tc::mma_bf16(d_tm, tc::smem_desc(aY + ks * 256, 128, SBO),
-                           tc::smem_desc(aAT + ks * 32 * NP, NP * 16, 128), id_km,
-                           ks > 0 ? 1u : 0u);
-            commit();
-          }
-          // the next step's X image (its buffer was last read before this
-          // step's barrier; with one buffer, after this step's xi product)
-          if (XIB == 2 && t > t0) load_x((t - 1) % 2, img_of(t - 1));
-        }
-        if (XIB == 1 && has_mma && tid != 0) xph[0] ^= 1;  // thread 0 flipped it in wait_x
-        const float rho_prev = row_sum((t + 1) & 1);
-        if constexpr (XIB == 2) {
-          if (tid != 0 || !has_mma) wait_x(xb);
-          else xph[xb] ^= 1;
-        }
-        if (has_mma) wait_mma();
-        if (XIB == 1 && tid == 0 && t > t0) load_x(0, img_of(t - 1));
-        float bt[COLS];
-        if (has_mma) {
-          tmem_ld_cols<COLS>(d_tm + my_cols, bt);
-        } else {
-#pragma unroll
-          for (int i = 0; i < COLS; ++i) bt[i] = 0.f;
-        }
-        if constexpr (XIB == 2) me.get(sXI + xb * IMG, xcur);
-        if constexpr (L::EMIS) me.emis(bb, ocur);
-        const bool is_init = act && t == T - 1;
-        const bool on = act && t < T - 1;
-        if (is_init) {
-#pragma unroll
-          for (int i = 0; i < COLS; ++i) bt[i] = 1.f;
-          c = w / st.S_last;
-        } else if (on) {
-          c = w / (c * rho_prev);
-        }
-        const bool live = (is_init || on) && isfinite(c);
-        const float fc = exp2i(-gcur) * c;  // exact: c times a power of two
-        const float2 c2 = make_float2(c, c), fc2 = make_float2(fc, fc);
-        float2 part2 = make_float2(0.f, 0.f);
-        uint32_t gp[COLS / 2], yp[COLS / 2];
-#pragma unroll
-        for (int q = 0; q < COLS / 2; ++q) {
-          const float2 bt2 = make_float2(bt[2 * q], bt[2 * q + 1]);
-          const float2 g = __fmul2_rn(unpack_bf16(xcur[q]), bt2);
-          part2 = __fadd2_rn(part2, g);
-          float2 ga = __fmul2_rn(g, c2);
-          float2 ya = __fmul2_rn(__fmul2_rn(make_float2(bb[2 * q], bb[2 * q + 1]), bt2), fc2);
-          if (!live) { ga = make_float2(0.f, 0.f); ya = ga; }
-          if (t == 0) __stcg(reinterpret_cast<float2*>(gbuf + (size_t)row * NP + me.col0 + 2 * q), ga);
-          gp[q] = tc::pack_bf16(ga.x, ga.y);
-          yp[q] = tc::pack_bf16(ya.x, ya.y);
-        }
-        me.put(sY, yp);
-        me.put(sG, gp);
-        if (h == 0) {
-          if (kprev >= 0)
-            *reinterpret_cast<uint16_t*>(sOH + (kprev >> 7) * 32768 + img_off<128>(kprev & 127, row >> 3) +
-                                         (row & 7) * 2) = 0;
-          kprev = -1;
-          if (live) {
-            *reinterpret_cast<uint16_t*>(sOH + (ocur >> 7) * 32768 + img_off<128>(ocur & 127, row >> 3) +
-                                         (row & 7) * 2) = 0x3F80;  // BF16 1.0
-            kprev = ocur;
-          }
-        }
-        psum[((t & 1) * TPR + h) * 128 + row] = live ? part2.x + part2.y : 0.f;
-        if (!live) c = 0.f;
-        // next step's inputs
-        if (t > t0) {
-          ocur = sym_at(t - 1);
-          gcur = (int)__ldcg(gexp + (size_t)(t - 1) * 128 + row);
-          if constexpr (XIB == 1) me.get_global(img_of(t - 1), xcur);
-          if constexpr (!L::EMIS) me.emis(bb, ocur);
-        }
-        tc::fence_proxy_async();
-        cb_pending = true;
-      }
-      if (stop) break;
-      // the segment's last emission product, before gamma's buffer is reused
-      tc::fence_before_sync();
-      __syncthreads();
-      if (misc[M_ABORT]) { stop = true; break; }
-      if (tid == 0) {
-        tc::fence_after_sync();
-#pragma unroll
-        for (int b = 0; b < MB; ++b)
-#pragma unroll
-          for (int ks = 0; ks < 8; ++ks)
-            tc::mma_bf16(cb_tm + (uint32_t)(b * NP),
-                         tc::smem_desc(aOH + b * 32768 + ks * 256, 128, 2048),
-                         tc::smem_desc(aG + ks * 32 * NP, NP * 16, 128), id_km,
-                         (ks > 0 || cb_on) ? 1u : 0u);
-        cb_on = true;
-        commit();
-      }
-      cb_pending = false;
-      wait_mma();
-    }
-    if (stop) break;
-    tc::fence_before_sync();
-    __syncthreads();
-    if (misc[M_ABORT]) break;
     tc::fence_after_sync();
-
-    // ---------------- tile counts -> slot ----------------
-    float* slot = a.slots + (size_t)tile * a.slot_floats;
-    if (wq * 32 < NP) {  // xi rows i = row (warp-uniform)
-      float v[COLS];
-      if (Lt >= 2) {
-        tmem_ld_cols<COLS>(xi_tm + my_cols, v);
-      } else {
-#pragma unroll
-        for (int i = 0; i < COLS; ++i) v[i] = 0.f;
-      }
-      const float4* a4 = reinterpret_cast<const float4*>(Ak + (size_t)row * NP + me.col0);
-      float4* d4 = reinterpret_cast<float4*>(slot + NP + (size_t)row * NP + me.col0);
-#pragma unroll
-      for (int q = 0; q < COLS / 4; ++q) {
-        const float4 av = __ldg(a4 + q);
-        d4[q] = make_float4(v[4 * q] * av.x, v[4 * q + 1] * av.y, v[4 * q + 2] * av.z,
-                            v[4 * q + 3] * av.w);
-      }
-    }
-#pragma unroll
-    for (int b = 0; b < MB; ++b) {
-      float v[COLS];
-      tmem_ld_cols<COLS>(cb_tm + (uint32_t)(b * NP) + my_cols, v);
-      const int sym = b * 128 + row;
-      if (sym < M) {
-        float* dst = slot + NP + (size_t)NP * NP + sym;
-#pragma unroll
-        for (int jj = 0; jj < COLS; ++jj) dst[(size_t)(me.col0 + jj) * M] = v[jj];
-      }
-    }
-    __syncthreads();
-    if (tid < NP) {
-      float sum = 0.f;
-      for (int m = 0; m < 128; ++m) sum += __ldcg(gbuf + (size_t)m * NP + tid);
-      slot[tid] = sum;
-    }
-    if (h == 0 && kprev >= 0)
-      *reinterpret_cast<uint16_t*>(sOH + (kprev >> 7) * 32768 + img_off<128>(kprev & 127, row >> 3) +
-                                   (row & 7) * 2) = 0;
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
   }
 
-  // teardown: nothing of ours may still be in flight
+  // teardown
   __syncthreads();
-  if (tid == 0) {
-    if (misc[M_ABORT]) set_status(a.status, HMM_STATUS_TIMEOUT);
-    if (m_pend) tc::mbar_wait_bounded(mbar, m_par, kFbWaitLimit);
-    if (g_pend) tc::mbar_wait_bounded(gbar, g_par, kFbWaitLimit);
-    for (int b = 0; b < XIB; ++b)
-      if (x_pend[b]) tc::mbar_wait_bounded(&xbar[b], x_par[b], kFbWaitLimit);
-    tc::bulk_wait_all();
-  }
+  if (tid == 0 && misc[M_ABORT]) set_status(a.status, HMM_STATUS_TIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();

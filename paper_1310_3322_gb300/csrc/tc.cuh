@@ -47,6 +47,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Arrives once on the mbarrier (release semantics for this thread's prior
+// memory operations).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // ---------------------------------------------------------------- TMEM
 // One full warp allocates `ncols` columns (power of two >= 32) and writes the
 // base address to shared memory.
@@ -72,6 +78,11 @@ __device__ __forceinline__ void fence_after_sync() {
 // Generic-proxy shared-memory writes become visible to the tensor core.
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// ... and generic-proxy writes to any state space (global memory included)
+// become visible to later bulk copies.
+__device__ __forceinline__ void fence_proxy_async_all() {
+  asm volatile("fence.proxy.async;" ::: "memory");
 }
 
 // 32 lanes x 32 consecutive 32-bit columns: thread t of the warp receives

@@ -371,6 +371,7 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
   SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  s.skip_order = 1;  // the tile plan orders the sequences itself
   const bool labelled = seqs->model_of_seq != nullptr;
   const int cap = (int)L.slots;
   int32_t* tiles = at<int32_t>(ws, L.m_tiles);

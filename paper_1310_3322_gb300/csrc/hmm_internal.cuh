@@ -67,6 +67,7 @@ struct SetupArgs {
   int max_len;         // sequences longer than this are rejected
   int log_mode;        // 1: tables hold natural logs (Viterbi), 0: probabilities
   int want_bpoff;      // 1: compute backpointer offsets (Viterbi)
+  int skip_order;      // 1: validate only (the caller builds its own schedule)
   int ndone;           // entries of `done` to clear
   const float* pi;
   const float* A;

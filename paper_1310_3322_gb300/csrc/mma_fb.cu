@@ -436,6 +436,13 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               if (DB) {  // beta first: the epilogue waits for it alone
                 issue_beta();
                 tc::mma_commit(b_done);
+                // the next step's X image (its buffer was last read by the xi
+                // product of step t+1), then this step's xi / emission batch
+                if (t > t0) {
+                  wait_aux((t + 1) & 1);
+                  if (!ok) break;
+                  load_x(t - 1, img_of(t - 1));
+                }
                 issue_xi_cb();
               } else {
                 issue_xi_cb();
@@ -446,7 +453,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             }
             // the next step's X image: its buffer was last read by the xi
             // product of step t+1
-            if (t > t0) {
+            if (t > t0 && !(DB && t < Lt - 1)) {
               wait_aux((t + 1) & 1);
               if (!ok) break;
               load_x(t - 1, img_of(t - 1));
@@ -606,15 +613,20 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         const int t0 = seg * C, t1 = min(t0 + C, Lt);
         // (R) recompute X over the segment from its checkpoint
         if (t1 - t0 > 1) {
+          // symbol and exponent of steps t + 1 and t + 2 in flight
           int fn = (int)__ldcg(gexp + (size_t)(t0 + 1) * 128 + row);
           int on = sym_at(t0 + 1);
+          int fn2 = t0 + 2 < t1 ? (int)__ldcg(gexp + (size_t)(t0 + 2) * 128 + row) : 0;
+          int on2 = t0 + 2 < t1 ? sym_at(t0 + 2) : 0;
           if constexpr (!L::EMIS) me.emis_all(pf, on);
           for (int t = t0 + 1; t < t1 && run; ++t) {
             const int f = fn;
             const int ot = on;
-            if (t + 1 < t1) {
-              fn = (int)__ldcg(gexp + (size_t)(t + 1) * 128 + row);
-              on = sym_at(t + 1);
+            fn = fn2;
+            on = on2;
+            if (t + 2 < t1) {
+              fn2 = (int)__ldcg(gexp + (size_t)(t + 2) * 128 + row);
+              on2 = sym_at(t + 2);
             }
             if constexpr (L::EMIS) me.emis_sub(bsm, ot, 0);
             wait_e(b_done, ph_done);
@@ -630,6 +642,8 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
 
         // (B) backward over the segment
         int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
+        int onx = t1 - 2 >= t0 ? sym_at(t1 - 2) : 0;  // step t - 1, in flight
+        int gnx = t1 - 2 >= t0 ? (int)__ldcg(gexp + (size_t)(t1 - 2) * 128 + row) : 0;
         if constexpr (!L::EMIS) me.emis_all(pf, ocur);
         for (int t = t1 - 1; t >= t0 && run; --t) {
           const bool has_mma = t < Lt - 1;
@@ -693,8 +707,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           if (!live) c = 0.f;
           // next step's inputs
           if (t > t0) {
-            ocur = sym_at(t - 1);
-            gcur = (int)__ldcg(gexp + (size_t)(t - 1) * 128 + row);
+            ocur = onx;
+            gcur = gnx;
+            if (t - 2 >= t0) {
+              onx = sym_at(t - 2);
+              gnx = (int)__ldcg(gexp + (size_t)(t - 2) * 128 + row);
+            }
             if constexpr (!L::EMIS) me.emis_all(pf, ocur);
           }
           tc::fence_proxy_async();

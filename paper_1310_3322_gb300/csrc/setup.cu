@@ -63,8 +63,9 @@ __device__ void plan_block(const SetupArgs& a) {
     }
     if (!ok) set_status(a.status, HMM_STATUS_SEQ);
     a.seqlen[s] = ok ? T : -1;
-    atomicAdd(&hist[kLenBuckets - 1 - length_bucket(ok ? T : 0)], 1);
+    if (!a.skip_order) atomicAdd(&hist[kLenBuckets - 1 - length_bucket(ok ? T : 0)], 1);
   }
+  if (a.skip_order) return;
   __syncthreads();
 
   // one bucket per thread (kLenBuckets == kPlanThreads)
@@ -156,7 +157,8 @@ cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // One stable counting-sort pass: `out` receives `in` ordered by digit(item) in
 // [0, 256), items with equal digits keeping their input order. Chunks of 1024
-// items are ranked with warp match masks and per-warp digit counts.
+// items are ranked with warp match masks and per-(digit, warp) counts `wh`
+// (digit-major, all zero on entry and on return).
 template <typename DigitFn>
 __device__ void stable_pass(const int32_t* in, int32_t* out, int n, DigitFn digit, int* base,
                             int* wh) {
@@ -190,25 +192,33 @@ __device__ void stable_pass(const int32_t* in, int32_t* out, int n, DigitFn digi
     const bool valid = i < n;
     const int item = valid ? in[i] : 0;
     const int d = valid ? digit(item) : 256;
-    for (int q = tid; q < 32 * 256; q += kPlanThreads) wh[q] = 0;
-    __syncthreads();
     const unsigned peers = __match_any_sync(HMM_FULL_MASK, d);
     const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && rank == 0) wh[warp * 256 + d] = __popc(peers);
+    if (valid && rank == 0) wh[d * 32 + warp] = __popc(peers);
     __syncthreads();
-    if (tid < 256) {
-      int run = base[tid];
-      for (int w = 0; w < 32; ++w) {
-        const int c = wh[w * 256 + tid];
-        wh[w * 256 + tid] = run;
-        run += c;
+    // per digit, exclusive scan over the 32 warps (warp w owns digits 8w..8w+7)
+#pragma unroll
+    for (int dd = 0; dd < 8; ++dd) {
+      const int d2 = warp * 8 + dd;
+      const int v = wh[d2 * 32 + lane];
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(HMM_FULL_MASK, x, o);
+        if (lane >= o) x += y;
       }
-      base[tid] = run;
+      const int b0 = base[d2];
+      __syncwarp();
+      wh[d2 * 32 + lane] = b0 + x - v;
+      if (lane == 31) base[d2] = b0 + x;
     }
     __syncthreads();
-    if (valid) out[wh[warp * 256 + d] + rank] = item;
+    if (valid) out[wh[d * 32 + warp] + rank] = item;
     __syncthreads();
+#pragma unroll
+    for (int dd = 0; dd < 8; ++dd) wh[(warp * 8 + dd) * 32 + lane] = 0;  // the entries this warp scanned
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ int len_key(int T) { return kLenBuckets - 1 - length_bucket(T); }
@@ -235,21 +245,30 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
   __shared__ int itmp[32];
   __shared__ int total;
   const int tid = threadIdx.x;
+  for (int i = tid; i < 32 * 256; i += kPlanThreads) wh[i] = 0;
 
-  // rows with T >= 1, in index order; the others get their log-likelihood here
+  // rows with T >= 1, in index order (4 consecutive sequences per thread);
+  // the others get their log-likelihood here
   int n = 0;
-  for (int c0 = 0; c0 < a.S; c0 += kPlanThreads) {
-    const int s = c0 + tid;
-    const int T = s < a.S ? a.seqlen[s] : 0;
-    const int keep = (s < a.S && T >= 1) ? 1 : 0;
-    if (s < a.S && !keep) {
-      const float v = T == 0 ? 0.f : __int_as_float(0x7fc00000);
-      if (a.labelled) a.loglik[s] = v;
-      else
-        for (int k = 0; k < a.K; ++k) a.loglik[(size_t)s * a.K + k] = v;
+  for (int c0 = 0; c0 < a.S; c0 += 4 * kPlanThreads) {
+    int keep[4], cnt = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = c0 + 4 * tid + u;
+      const int T = s < a.S ? a.seqlen[s] : 0;
+      keep[u] = (s < a.S && T >= 1) ? 1 : 0;
+      cnt += keep[u];
+      if (s < a.S && !keep[u]) {
+        const float v = T == 0 ? 0.f : __int_as_float(0x7fc00000);
+        if (a.labelled) a.loglik[s] = v;
+        else
+          for (int k = 0; k < a.K; ++k) a.loglik[(size_t)s * a.K + k] = v;
+      }
     }
-    const int pos = block_exclusive_scan<int>(keep, itmp, &total);
-    if (keep) a.tmp[n + pos] = s;
+    int pos = n + block_exclusive_scan<int>(cnt, itmp, &total);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (keep[u]) a.tmp[pos++] = c0 + 4 * tid + u;
     n += total;
     __syncthreads();
   }
@@ -290,20 +309,32 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
       if (p == n - 1 || model_at(p + 1) != k) a.group_end[k] = p + 1;
     }
     __syncthreads();
-    for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
-      const int p = c0 + tid;
-      int flag = 0, k = 0, ge = 0;
-      if (p < n) {
-        k = model_at(p);
-        ge = a.group_end[k];
-        flag = ((p - a.group_start[k]) % 128) == 0 ? 1 : 0;
+    for (int c0 = 0; c0 < n; c0 += 4 * kPlanThreads) {
+      int flag[4], kk[4], ge[4], cnt = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = c0 + 4 * tid + u;
+        flag[u] = 0; kk[u] = 0; ge[u] = 0;
+        if (p < n) {
+          kk[u] = model_at(p);
+          ge[u] = a.group_end[kk[u]];
+          flag[u] = ((p - a.group_start[kk[u]]) % 128) == 0 ? 1 : 0;
+        }
+        cnt += flag[u];
       }
-      const int id = n_tiles + block_exclusive_scan<int>(flag, itmp, &total);
-      if (flag && id < a.n_tiles_cap) {
-        a.tile_start[id] = p;
-        a.tile_rows[id] = min(128, ge - p);
-        a.tile_model[id] = k;
-        a.tile_order[id] = id;
+      int id = n_tiles + block_exclusive_scan<int>(cnt, itmp, &total);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = c0 + 4 * tid + u;
+        if (flag[u]) {
+          if (id < a.n_tiles_cap) {
+            a.tile_start[id] = p;
+            a.tile_rows[id] = min(128, ge[u] - p);
+            a.tile_model[id] = kk[u];
+            a.tile_order[id] = id;
+          }
+          ++id;
+        }
       }
       n_tiles += total;
       __syncthreads();

@@ -168,10 +168,16 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
  *   cnt_B[k][j][m] = sum_s w_s sum_{t: o_t = m} gamma_t(j)
  * over the pairs scored against model k, which are exactly the gradient of
  * sum_s w_s log P with respect to log pi, log A, log B. Alpha is checkpointed
- * every ceil(sqrt(max_len)) steps and recomputed segment by segment.
+ * every ceil(sqrt(T)) steps and recomputed segment by segment.
  *   weight  [S] or [S][K] (the layout of loglik), NULL = all 1
  *   loglik  [S] or [S][K]
  *   counts  overwritten; summed in a fixed order (bitwise reproducible).
+ * precision: HMM_FP32 runs the FP32 SIMT adjoint (N <= 64); HMM_BF16_MMA the
+ * tensor-core adjoint (32 < N <= 128, M <= 256: BF16 operands, FP32
+ * accumulation, per-row messages renormalised every step, checkpoint stride
+ * capped at 16 while T <= 8192); HMM_AUTO chooses the tensor cores above
+ * N = 32. Its errors against FP64 are of order the BF16 unit roundoff 2^-8
+ * relative per count (|delta log P| <= 2^-7 T).
  * Impossible or invalid pairs contribute no counts. */
 int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                          const hmm_seqs_t* seqs, const float* weight,

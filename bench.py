@@ -508,6 +508,17 @@ def run_large(args):
     kt = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     kms = {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]}
+    # the TF32 forward on the same data, beside the BF16 one
+    def fwd_tf32():
+        hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_TF32_MMA, loglik=ll, argmax=am,
+                        workspace=ws[0])
+    fwd_tf32()
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, fwd_tf32, args.steps, flush)
+    kt32 = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    tf32_ms = kt32["forward"][1] / max(kt32["forward"][0], 1)
     f_tf = 2.0 * N * N * sumT * K / (kms["forward"] / 1e3) / 1e12
     a_tf = (8.0 * N * N + 10 * N) * sumT / (kms["adjoint"] / 1e3) / 1e12
     dom = "adjoint" if kms["adjoint"] >= kms["forward"] else "forward"
@@ -531,9 +542,12 @@ def run_large(args):
                                "obs_models_per_s": sumT * K / (kms["forward"] / 1e3)},
                    "adjoint": {"ms": kms["adjoint"], "tflops": a_tf,
                                "obs_per_s": sumT / (kms["adjoint"] / 1e3)},
+                   "forward_tf32": {"ms": tf32_ms,
+                                    "tflops": 2.0 * N * N * sumT * K / (tf32_ms / 1e3) / 1e12},
                    **{k: {"ms": v} for k, v in kms.items() if k not in ("forward", "adjoint")}},
         "clocks": clk,
         "gpu_launches": 7 * args.steps,  # forward: setup, kernel; adjoint: setup, plan, kernel, reduce x2
+        "note": "forward_tf32 is timed separately (TF32 operands, 2N^2 flop per obs*model)",
     }
     print(json.dumps(line), flush=True)
 

@@ -273,6 +273,7 @@ static int max_states(int op, int precision) {
   if ((op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD) &&
       (precision == HMM_BF16_MMA || precision == HMM_AUTO))
     return 128;
+  if (op == HMM_OP_FORWARD && precision == HMM_TF32_MMA) return 128;
   if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
   return 64;
 }
@@ -281,6 +282,7 @@ static int check_precision(int precision, int op) {
   if (precision == HMM_FP32 || precision == HMM_AUTO) return HMM_OK;
   if (precision == HMM_BF16_MMA && (op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD))
     return HMM_OK;
+  if (precision == HMM_TF32_MMA && op == HMM_OP_FORWARD) return HMM_OK;
   if (precision == HMM_BF16_MMA || precision == HMM_TF32_MMA)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core precision %d not available for op %d in this build",
                 precision, op);
@@ -289,7 +291,8 @@ static int check_precision(int precision, int op) {
 
 // Tensor-core forward: N in (32, 128], every sequence against every model.
 static bool use_mma_forward(const hmm_dims_t& d, int precision) {
-  return precision == HMM_BF16_MMA || (precision == HMM_AUTO && d.N > 64);
+  return precision == HMM_BF16_MMA || precision == HMM_TF32_MMA ||
+         (precision == HMM_AUTO && d.N > 64);
 }
 
 // Tensor-core adjoint: N in (32, 128]; the library's choice above N = 32
@@ -553,7 +556,7 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     f.n_items = n_pairs * dims.K;
     {
       Timed tm(T_FORWARD, st);
-      e = launch_forward_mma(L.NP, f, st);
+      e = launch_forward_mma(L.NP, precision == HMM_TF32_MMA, f, st);
       tm.stop();
     }
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");

@@ -405,7 +405,7 @@ struct MmaFwdLaunch {
   int n_items;        // ceil(n_tiles / tiles per CTA) * K
   int n_tiles;        // ceil(S / 128)
 };
-cudaError_t launch_forward_mma(int NP, const MmaFwdLaunch& a, cudaStream_t st);
+cudaError_t launch_forward_mma(int NP, bool tf32, const MmaFwdLaunch& a, cudaStream_t st);
 int mma_tiles_per_cta(int NP);  // 128-row tiles one CTA of the tensor-core forward holds
 
 // Plan of the tensor-core adjoint: the rows of every 128-row tile share one

@@ -44,9 +44,11 @@
 
 namespace hmmgb {
 
-template <int NP, int NT, int TPR>
+// AB: operand type, 1 = BF16 (kind::f16, two values per 32-bit column of
+// tensor memory), 2 = TF32 (kind::tf32, one value per column).
+template <int NP, int NT, int TPR, int AB = 1>
 struct MmaFwdSmem {
-  static constexpr int kB = NP * NP * 2;          // A^T, BF16
+  static constexpr int kB = NP * NP * (AB == 1 ? 2 : 4);  // A^T
   static constexpr int kES = NP * 4 + 16;         // padded emission row, FP32
   static constexpr int kE = 128 * kES;            // one tile of emission rows
   static constexpr int OFF_B = 0;
@@ -56,8 +58,8 @@ struct MmaFwdSmem {
   static constexpr int OFF_MISC = OFF_BAR + 2 * NT * 8;        // tmem, item, abort, last, warp max
   static constexpr int TOTAL = OFF_MISC + 24 * 4;
 };
-static_assert(MmaFwdSmem<128, 2, 2>::TOTAL <= 227 * 1024, "shared memory budget");
-static_assert(MmaFwdSmem<64, 4, 1>::TOTAL <= 227 * 1024, "shared memory budget");
+static_assert(MmaFwdSmem<128, 2, 2, 2>::TOTAL <= 227 * 1024, "shared memory budget");
+static_assert(MmaFwdSmem<64, 4, 1, 2>::TOTAL <= 227 * 1024, "shared memory budget");
 
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kTmemCols = 512;  // per tile: D (NP cols) then X (NP/2 cols) at (512/NT) * tile
@@ -93,6 +95,25 @@ __device__ __forceinline__ void pack32(const float (&y)[32], uint32_t (&w)[16]) 
   for (int i = 0; i < 16; ++i) w[i] = tc::pack_bf16(y[2 * i], y[2 * i + 1]);
 }
 
+// Chunk c (32 values) of this thread's share of the next X row into tensor
+// memory: BF16 pairs (16 columns) or TF32 values (32 columns).
+template <int AB>
+__device__ __forceinline__ void store_x(uint32_t x_mine, int c, const float (&y)[32]) {
+  if constexpr (AB == 1) {
+    uint32_t w[16];
+    pack32(y, w);
+    tc::tmem_st16(x_mine + (uint32_t)(16 * c), w);
+  } else {
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = tc::to_tf32(y[i]);
+    tc::tmem_st16(x_mine + (uint32_t)(32 * c), w);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = tc::to_tf32(y[16 + i]);
+    tc::tmem_st16(x_mine + (uint32_t)(32 * c + 16), w);
+  }
+}
+
 // After step t's row sum sigma: liveness checks, the log-likelihood at the
 // row's last step, and the exponent for the next step.
 __device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int Tn) {
@@ -113,15 +134,17 @@ __device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int
   st.f = min(126, max(-126, exponent_of(sigma)));
 }
 
-template <int NP, int NT, int TPR>
+template <int NP, int NT, int TPR, int AB>
 __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a) {
-  using L = MmaFwdSmem<NP, NT, TPR>;
+  using L = MmaFwdSmem<NP, NT, TPR, AB>;
+  constexpr int XC = AB == 1 ? NP / 2 : NP;   // tensor-memory columns of X
+  constexpr int KI = AB == 1 ? 16 : 8;        // K per instruction
   constexpr int WGT = 128 * TPR;     // threads per tile
   static_assert(NT * WGT == kMmaThreads, "512 threads per CTA");
   constexpr int HALF = NP / TPR;     // columns per thread
   constexpr int CH = HALF / 32;      // 32-column chunks per thread
   constexpr int TS = 512 / NT;       // tensor-memory columns per tile
-  static_assert(NP + NP / 2 <= TS, "tile does not fit its tensor-memory share");
+  static_assert(NP + XC <= TS, "tile does not fit its tensor-memory share");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem + L::OFF_B;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
@@ -151,13 +174,13 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
   tc::fence_after_sync();
   const uint32_t tmem = (uint32_t)misc[0];
   const uint32_t d_tmem = tmem + (uint32_t)(wg * TS);           // D: NP FP32 columns
-  const uint32_t x_tmem = d_tmem + (uint32_t)NP;                // X: NP/2 packed columns
+  const uint32_t x_tmem = d_tmem + (uint32_t)NP;                // X: XC columns
   const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
   const uint32_t d_mine = d_tmem + lane_off + (uint32_t)(h * HALF);
-  const uint32_t x_mine = x_tmem + lane_off + (uint32_t)(h * HALF / 2);
-  constexpr uint32_t idesc = tc::instr_desc(1, 128, NP);
+  const uint32_t x_mine = x_tmem + lane_off + (uint32_t)(h * HALF * XC / NP);
+  constexpr uint32_t idesc = tc::instr_desc(AB, 128, NP);
   const uint32_t b_base = tc::smem_u32(sB);
-  constexpr uint32_t SBO = NP * 16;
+  constexpr uint32_t SBO = AB == 1 ? NP * 16 : NP * 32;  // next 8 rows of the B image
   uint32_t mphase = 0, ephase = 0;
   int cur_model = -1;
 
@@ -170,13 +193,22 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
     const int tp = item / K, k = item % K;
 
     if (k != cur_model) {
-      // B operand: element (n = j, k = i) = a_ij in BF16
+      // B operand: element (n = j, k = i) = a_ij, K-major core matrices of 8
+      // rows x 16 bytes (8 BF16 or 4 TF32 values of i)
       const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
-      for (int idx = tid; idx < NP * NP / 2; idx += kMmaThreads) {
-        const int j = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
-        const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + (i + 1) * NP + j));
-        const uint32_t off = (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 + (i % 8) * 2;
-        *reinterpret_cast<uint32_t*>(sB + off) = w;
+      if constexpr (AB == 1) {
+        for (int idx = tid; idx < NP * NP / 2; idx += kMmaThreads) {
+          const int j = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
+          const uint32_t w = tc::pack_bf16(__ldg(Ak + i * NP + j), __ldg(Ak + (i + 1) * NP + j));
+          const uint32_t off = (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 + (i % 8) * 2;
+          *reinterpret_cast<uint32_t*>(sB + off) = w;
+        }
+      } else {
+        for (int idx = tid; idx < NP * NP; idx += kMmaThreads) {
+          const int j = idx / NP, i = idx % NP;
+          const uint32_t off = (j / 8) * SBO + (i / 4) * 128 + (j % 8) * 16 + (i % 4) * 4;
+          *reinterpret_cast<uint32_t*>(sB + off) = tc::to_tf32(__ldg(Ak + i * NP + j));
+        }
       }
       cur_model = k;
       tc::fence_proxy_async();
@@ -223,9 +255,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
           y[4 * q + 2] = live ? pp.z * bb.z : 0.f; y[4 * q + 3] = live ? pp.w * bb.w : 0.f;
         }
         part += tree_sum<32>(y);
-        uint32_t w[16];
-        pack32(y, w);
-        tc::tmem_st16(x_mine + (uint32_t)(16 * c), w);
+        store_x<AB>(x_mine, c, y);
       }
       tc::tmem_st_wait();
       psum[h * 128 + row] = part;
@@ -241,9 +271,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
       if (wtid == 0) {
         tc::fence_after_sync();
 #pragma unroll
-        for (int ks = 0; ks < NP / 16; ++ks)
-          tc::mma_bf16_ts(d_tmem, x_tmem + (uint32_t)(ks * 8),
-                          tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
+        for (int ks = 0; ks < NP / KI; ++ks) {  // 8 tensor-memory columns of X per instruction
+          if constexpr (AB == 1)
+            tc::mma_bf16_ts(d_tmem, x_tmem + (uint32_t)(ks * 8),
+                            tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
+          else
+            tc::mma_tf32_ts(d_tmem, x_tmem + (uint32_t)(ks * 8),
+                            tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
+        }
         tc::mma_commit(mbar);
       }
       close_step(st, TPR == 2 ? psum[row] + psum[128 + row] : psum[row], t - 1, Tn);
@@ -288,9 +323,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
           y[4 * q] = lo.x; y[4 * q + 1] = lo.y; y[4 * q + 2] = hi.x; y[4 * q + 3] = hi.y;
         }
         part += acc.x + acc.y;
-        uint32_t w[16];
-        pack32(y, w);
-        tc::tmem_st16(x_mine + (uint32_t)(16 * c), w);
+        store_x<AB>(x_mine, c, y);
       }
       tc::tmem_st_wait();
       psum[h * 128 + row] = part;
@@ -352,10 +385,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int NP, int NT, int TPR>
+template <int NP, int NT, int TPR, int AB>
 static cudaError_t launch_mma_t(const MmaFwdLaunch& a, cudaStream_t st) {
-  auto kern = hmm_forward_mma<NP, NT, TPR>;
-  using L = MmaFwdSmem<NP, NT, TPR>;
+  auto kern = hmm_forward_mma<NP, NT, TPR, AB>;
+  using L = MmaFwdSmem<NP, NT, TPR, AB>;
   // one CTA per SM (it holds all 512 tensor-memory columns): ask for more
   // than half of the shared memory even when the tiles need less
   const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;
@@ -369,9 +402,9 @@ static cudaError_t launch_mma_t(const MmaFwdLaunch& a, cudaStream_t st) {
 
 int mma_tiles_per_cta(int NP) { return NP == 64 ? 4 : 2; }
 
-cudaError_t launch_forward_mma(int NP, const MmaFwdLaunch& a, cudaStream_t st) {
-  if (NP == 64) return launch_mma_t<64, 4, 1>(a, st);
-  if (NP == 128) return launch_mma_t<128, 2, 2>(a, st);
+cudaError_t launch_forward_mma(int NP, bool tf32, const MmaFwdLaunch& a, cudaStream_t st) {
+  if (NP == 64) return tf32 ? launch_mma_t<64, 4, 1, 2>(a, st) : launch_mma_t<64, 4, 1, 1>(a, st);
+  if (NP == 128) return tf32 ? launch_mma_t<128, 2, 2, 2>(a, st) : launch_mma_t<128, 2, 2, 1>(a, st);
   return cudaErrorInvalidValue;
 }
 

@@ -1,12 +1,13 @@
-"""Tensor-core (BF16 tcgen05) forward vs the FP64 oracle.
+"""Tensor-core (tcgen05) forward vs the FP64 oracle, BF16 and TF32 operands.
 
 The tensor-core path rounds the transition matrix A and the rescaled forward
-variable to BF16 (unit roundoff u = 2^-8) and accumulates in FP32. Two checks:
+variable to BF16 (unit roundoff u = 2^-8) or TF32 (u = 2^-11, round to nearest)
+and accumulates in FP32. Two checks:
 
 * against the oracle run on the same model with A rounded to BF16 (the
   systematic part of the error removed), the remaining difference comes from
   rounding alpha each step and must stay within the FP32 bound
-  1e-4 * max(T, 1) nats;
+  FP32 bound 1e-4 * max(T, 1) nats plus u T;
 * against the oracle on the exact model, every term of every step is a sum of
   non-negative products whose factors carry relative errors <= u, so
   |delta log P| <= 2 u T is a hard bound; the mean per-step error is reported.
@@ -21,6 +22,7 @@ from paper_1310_3322_gb300 import hmm, synth
 pytestmark = pytest.mark.gpu
 
 U_BF16 = 2.0 ** -8
+U_TF32 = 2.0 ** -11
 
 
 def bf16_round(x):
@@ -28,6 +30,18 @@ def bf16_round(x):
     b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
     b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
     return b.astype(np.uint32).view(np.float32)
+
+
+def tf32_round(x):
+    """Round to nearest (ties away from zero) of non-negative float32 values to
+    a 10-bit mantissa, returned as float32."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x1000) >> 13) << 13
+    return b.astype(np.uint32).view(np.float32)
+
+
+PRECISIONS = {"bf16": (hmm.HMM_BF16_MMA, U_BF16, bf16_round),
+              "tf32": (hmm.HMM_TF32_MMA, U_TF32, tf32_round)}
 
 
 CASES = [
@@ -38,33 +52,35 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[3]}")
-def test_bf16_forward_matches_oracle(case):
+def test_tensor_core_forward_matches_oracle(case, prec):
+    precision, u, rnd = PRECISIONS[prec]
     name, S, lengths, over = case
     w = synth.make_workload(name, n_seqs=S, lengths=lengths, **over)
     seqs, pi, A, B = to_gpu(w)
-    ll, am = hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_BF16_MMA)
+    ll, am = hmm.hmm_forward(pi, A, B, seqs, precision=precision)
     assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
     ll = ll.cpu().numpy()
     T = np.maximum(w.lengths, 1).astype(np.float64)[:, None]
     # systematic rounding of A removed: only the per-step rounding of alpha
     # (relative <= u per term, all terms non-negative) remains
-    Pr = oracle.params(w.pi, bf16_round(w.A), w.B)
+    Pr = oracle.params(w.pi, rnd(w.A), w.B)
     ref_r, _, _ = oracle.forward(Pr, w.symbols, w.offsets, w.lengths, nthreads=8)
     err_r = np.abs(ll - ref_r)
-    assert np.all(err_r <= U_BF16 * T + ll_tol(w.lengths)[:, None]), (err_r / T).max()
+    assert np.all(err_r <= u * T + ll_tol(w.lengths)[:, None]), (err_r / T).max()
     # ... and it is a random-signed error far below that bound on average
-    assert np.mean(err_r / T) <= U_BF16 / 8, np.mean(err_r / T)
+    assert np.mean(err_r / T) <= u / 8 + 1e-5, np.mean(err_r / T)
     # exact model: hard bound 2 u T
     ref, ref_am, _ = oracle.forward(oracle.params(w.pi, w.A, w.B), w.symbols, w.offsets,
                                     w.lengths, nthreads=8)
     err = np.abs(ll - ref)
-    assert np.all(err <= 2 * U_BF16 * T + ll_tol(w.lengths)[:, None]), (err / T).max()
-    print(f"{name} N={w.N}: max|d|/T vs exact {np.max(err / T):.2e}, mean {np.mean(err / T):.2e}; "
-          f"vs bf16-A {np.max(err_r / T):.2e}")
+    assert np.all(err <= 2 * u * T + ll_tol(w.lengths)[:, None]), (err / T).max()
+    print(f"{prec} {name} N={w.N}: max|d|/T vs exact {np.max(err / T):.2e}, "
+          f"mean {np.mean(err / T):.2e}; vs rounded-A {np.max(err_r / T):.2e}")
     # recognition: argmax agrees where the top two models are well separated
     srt = np.sort(ref, axis=1)
-    clear = srt[:, -1] - srt[:, -2] > 4 * U_BF16 * T[:, 0]
+    clear = srt[:, -1] - srt[:, -2] > 4 * u * T[:, 0] + 2 * ll_tol(w.lengths)
     np.testing.assert_array_equal(am.cpu().numpy()[clear], ref_am[clear])
 
 

@@ -204,6 +204,19 @@ int hmm_softmax_grad(hmm_dims_t dims, const float* pi, const float* A, const flo
                      const float* cnt_pi, const float* cnt_A, const float* cnt_B, float* g_pi,
                      float* g_A, float* g_B, hmm_stream_t stream);
 
+/* Baum-Welch re-estimation, the M-step (Sec. 2.7 "Baum-Welch"; Rabiner
+ * eq. 40): from the expected counts of hmm_forward_backward (unit weights),
+ *   pi_out[k][i]   = cnt_pi[k][i] / sum_i cnt_pi[k][i]
+ *   A_out[k][i][j] = cnt_A[k][i][j] / sum_j cnt_A[k][i][j]
+ *   B_out[k][j][m] = cnt_B[k][j][m] / sum_m cnt_B[k][j][m]
+ * A row whose counts sum to zero keeps the old row of pi / A / B. Outputs may
+ * alias pi, A, B (in-place re-estimation); all pointers are device pointers.
+ * Alternating hmm_forward_backward and hmm_mstep never lowers sum_s log P
+ * (up to rounding): the paper's learning loop. */
+int hmm_mstep(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+              const float* cnt_pi, const float* cnt_A, const float* cnt_B, float* pi_out,
+              float* A_out, float* B_out, hmm_stream_t stream);
+
 /* One Adam step (Kingma & Ba 2015) on n parameters, in place:
  *   t = *step_counter + 1;  g = grad_scale * grad;
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
@@ -241,9 +254,9 @@ int hmm_tuning_candidates(int32_t op, int32_t n_pad, int32_t* out, int32_t cap);
  * hmm_timing_read() synchronises those events and reports, per kernel kind,
  * the number of launches and their summed duration since the last reset.
  * Kinds: 0 setup, 1 forward, 2 viterbi-scores, 3 viterbi-paths, 4 adjoint,
- * 5 count-reduce, 6 softmax-rows, 7 softmax-grad, 8 adam. Not for use inside
- * CUDA-graph capture; not thread-safe against concurrent launches. */
-#define HMM_TIMING_KINDS 9
+ * 5 count-reduce, 6 softmax-rows, 7 softmax-grad, 8 adam, 9 mstep. Not for
+ * use inside CUDA-graph capture; not thread-safe against concurrent launches. */
+#define HMM_TIMING_KINDS 10
 int hmm_timing_enable(int on);
 int hmm_timing_reset(void);
 int hmm_timing_read(int32_t kind, int64_t* launches, double* total_ms);

@@ -305,7 +305,7 @@ static bool use_mma_fb(const hmm_dims_t& d, int precision) {
 // ---------------------------------------------------------------------------
 // kernel timing (host-side tracing with CUDA events)
 // ---------------------------------------------------------------------------
-enum { T_SETUP = 0, T_FORWARD, T_VSCORES, T_VPATHS, T_FB, T_REDUCE, T_SOFTMAX, T_SGRAD, T_ADAM };
+enum { T_SETUP = 0, T_FORWARD, T_VSCORES, T_VPATHS, T_FB, T_REDUCE, T_SOFTMAX, T_SGRAD, T_ADAM, T_MSTEP };
 
 struct EventPair {
   cudaEvent_t a, b;
@@ -788,6 +788,20 @@ int hmm_softmax_grad(hmm_dims_t dims, const float* pi, const float* A, const flo
                                       reinterpret_cast<cudaStream_t>(stream));
   tm.stop();
   return e == cudaSuccess ? HMM_OK : cuda_fail(e, "softmax grad launch");
+}
+
+int hmm_mstep(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+              const float* cnt_pi, const float* cnt_A, const float* cnt_B, float* pi_out,
+              float* A_out, float* B_out, hmm_stream_t stream) {
+  g_err[0] = 0;
+  if (dims.K < 1 || dims.N < 1 || dims.M < 1) return fail(HMM_ERR_ARG, "dims must be positive");
+  if (!pi || !A || !B || !cnt_pi || !cnt_A || !cnt_B || !pi_out || !A_out || !B_out)
+    return fail(HMM_ERR_ARG, "NULL table");
+  Timed tm(T_MSTEP, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_mstep(dims.K, dims.N, dims.M, pi, A, B, cnt_pi, cnt_A, cnt_B, pi_out,
+                               A_out, B_out, reinterpret_cast<cudaStream_t>(stream));
+  tm.stop();
+  return e == cudaSuccess ? HMM_OK : cuda_fail(e, "mstep launch");
 }
 
 int hmm_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,

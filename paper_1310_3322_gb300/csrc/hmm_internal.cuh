@@ -346,6 +346,9 @@ cudaError_t launch_softmax_grad(int K, int N, int M, const float* pi, const floa
                                 const float* B, const float* cpi, const float* cA,
                                 const float* cB, float* gpi, float* gA, float* gB,
                                 cudaStream_t st);
+cudaError_t launch_mstep(int K, int N, int M, const float* pi, const float* A, const float* B,
+                         const float* cpi, const float* cA, const float* cB, float* opi,
+                         float* oA, float* oB, cudaStream_t st);
 cudaError_t launch_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, float gs, int32_t* step, cudaStream_t st);
 

@@ -445,7 +445,43 @@ __global__ void softmax_grad_kernel(RowMap map, Tables p, Tables c, MTables g, l
   for (int q = lane; q < width; q += 32) gg[q] = cc[q] - pp[q] * tot;
 }
 
+// Baum-Welch re-estimation (Rabiner eq. 40): every row of pi, A and B becomes
+// its expected counts normalised to sum 1; a row whose counts sum to zero keeps
+// its old values. Outputs may alias the old parameters (each element depends
+// on its own row only).
+__global__ void mstep_kernel(RowMap map, Tables p, Tables c, MTables out, long long nrows) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  long long base; int width;
+  map.row(r, base, width);
+  const float* pp = p.at(base);
+  const float* cc = c.at(base);
+  float* oo = out.at(base);
+  float tot = 0.f;
+  for (int q = lane; q < width; q += 32) tot += cc[q];
+  tot = group_sum<32>(tot);
+  const float inv = tot > 0.f ? 1.f / tot : 0.f;
+  __syncwarp();
+  for (int q = lane; q < width; q += 32) oo[q] = tot > 0.f ? cc[q] * inv : pp[q];
+}
+
 static long long n_rows(int K, int N) { return (long long)K + 2LL * K * N; }
+
+cudaError_t launch_mstep(int K, int N, int M, const float* pi, const float* A, const float* B,
+                         const float* cpi, const float* cA, const float* cB, float* opi,
+                         float* oA, float* oB, cudaStream_t st) {
+  RowMap map{K, N, M};
+  const long long nA0 = (long long)K * N, nB0 = nA0 + (long long)K * N * N;
+  Tables p{pi, A, B, nA0, nB0};
+  Tables c{cpi, cA, cB, nA0, nB0};
+  MTables o{opi, oA, oB, nA0, nB0};
+  const long long rows = n_rows(K, N);
+  const int threads = 256;
+  const long long blocks = (rows * 32 + threads - 1) / threads;
+  mstep_kernel<<<(unsigned)blocks, threads, 0, st>>>(map, p, c, o, rows);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_softmax_rows(int K, int N, int M, const float* lpi, const float* lA,
                                 const float* lB, float* pi, float* A, float* B, cudaStream_t st) {

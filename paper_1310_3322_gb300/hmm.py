@@ -71,6 +71,7 @@ _SIG = {
                                     _I32, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "hmm_softmax_rows": (_I32, [hmm_dims_t, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "hmm_softmax_grad": (_I32, [hmm_dims_t, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "hmm_mstep": (_I32, [hmm_dims_t, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "hmm_adam_step": (_I32, [ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_float, ctypes.c_float,
                              ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP, _VP]),
     "hmm_get_device_status": (_I32, [_VP, _VP, ctypes.POINTER(_I32)]),
@@ -85,7 +86,7 @@ _SIG = {
 }
 
 TIMING_KINDS = ("setup", "forward", "viterbi_scores", "viterbi_paths", "adjoint",
-                "count_reduce", "softmax_rows", "softmax_grad", "adam")
+                "count_reduce", "softmax_rows", "softmax_grad", "adam", "mstep")
 
 
 def lib():
@@ -339,6 +340,17 @@ def hmm_softmax_grad(pi, A, B, cpi, cA, cB, out=None, stream=None):
     _check(lib().hmm_softmax_grad(_dims(pi, B), _ptr(pi), _ptr(A), _ptr(B), _ptr(cpi), _ptr(cA),
                                   _ptr(cB), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
                                   _stream(stream)))
+    return out
+
+
+def hmm_mstep(pi, A, B, cpi, cA, cB, out=None, stream=None):
+    """Baum-Welch re-estimation from expected counts; ``out=(pi, A, B)`` updates
+    the parameters in place."""
+    torch = _torch()
+    if out is None:
+        out = (torch.empty_like(pi), torch.empty_like(A), torch.empty_like(B))
+    _check(lib().hmm_mstep(_dims(pi, B), _ptr(pi), _ptr(A), _ptr(B), _ptr(cpi), _ptr(cA),
+                           _ptr(cB), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream)))
     return out
 
 

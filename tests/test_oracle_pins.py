@@ -325,6 +325,53 @@ def test_baum_welch_step_never_lowers_likelihood(orc):
             np.testing.assert_allclose(arr.sum(-1), 1.0, rtol=1e-12)
 
 
+def test_mstep_closed_form_when_the_state_path_is_observable(orc):
+    """State i emits only symbols 2i and 2i+1, so each observation fixes its
+    state and the posteriors are one-hot: re-estimation (Rabiner eq. 40) is
+    then plain frequency counting along the observed state path, and a state
+    that is never left (or never entered) keeps its old row."""
+    N, M = 4, 8
+    pi, A, B = _rand_model(31, 1, N, M)
+    B = np.zeros((1, N, M))
+    for i in range(N):
+        B[0, i, 2 * i], B[0, i, 2 * i + 1] = 0.3, 0.7
+    # state 3 is never visited; state 2 only ends sequences
+    seqs = [[0, 3, 1, 2, 5], [2, 2, 3, 0, 1], [1, 4], [3, 0, 5]]
+    sym, off, ln = _pack(seqs)
+    P = orc.params(pi, A, B)
+    _, cpi, cA, cB, _ = orc.forward_backward(P, sym, off, ln, np.zeros(len(seqs), np.int32))
+    Q = orc.mstep(P, cpi, cA, cB)
+    npi = np.zeros(N); nA = np.zeros((N, N)); nB = np.zeros((N, M))
+    for o in seqs:
+        s = [x // 2 for x in o]
+        npi[s[0]] += 1
+        for a, b in zip(s, s[1:]):
+            nA[a, b] += 1
+        for x, st in zip(o, s):
+            nB[st, x] += 1
+    np.testing.assert_allclose(Q.pi[0], npi / npi.sum(), atol=1e-12)
+    for i in range(N):
+        ra = nA[i] / nA[i].sum() if nA[i].sum() else A[0, i]
+        rb = nB[i] / nB[i].sum() if nB[i].sum() else B[0, i]
+        np.testing.assert_allclose(Q.A[0, i], ra, atol=1e-12)
+        np.testing.assert_allclose(Q.B[0, i], rb, atol=1e-12)
+    assert nA[2].sum() == 0 and nB[3].sum() == 0   # the keep-old-row cases are exercised
+
+
+def test_mstep_single_state_gives_symbol_frequencies(orc):
+    """N = 1: the only free parameter is B, whose maximum-likelihood value is
+    the empirical symbol frequency, reached in one step from any start."""
+    pi, A, B = _rand_model(32, 1, 1, 5)
+    seqs = [[0, 4, 4, 1], [4, 2], [1, 1, 4, 0, 3]]
+    sym, off, ln = _pack(seqs)
+    P = orc.params(pi, A, B)
+    _, cpi, cA, cB, _ = orc.forward_backward(P, sym, off, ln, np.zeros(3, np.int32))
+    Q = orc.mstep(P, cpi, cA, cB)
+    freq = np.bincount(sym, minlength=5) / sym.size
+    np.testing.assert_allclose(Q.B[0, 0], freq, atol=1e-12)
+    assert Q.pi[0, 0] == 1.0 and Q.A[0, 0, 0] == 1.0
+
+
 # --------------------------------------------------------------------------
 # sensitivity: the pins catch planted mistakes (made on the oracle's inputs)
 # --------------------------------------------------------------------------

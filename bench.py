@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--lanes", default=None,
                     help="fixed lanes per pair 'fwd,viterbi,paths,adjoint' instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "large", "gradient", "training"],
+                    choices=[WORKLOAD, "large", "gradient", "training", "teamwork"],
                     help="batched: the full step (default); large: tensor-core forward "
-                         "and adjoint; gradient/training: the learning step")
+                         "and adjoint; gradient/training: the learning step (and a "
+                         "Baum-Welch iteration); teamwork: per-role recognition, N=5")
     return ap.parse_args()
 
 
@@ -666,6 +667,33 @@ def run_learning(args):
         fms = _time_steps(torch, fstep, args.steps, flush)
         fwd[name] = {"ms": fms, "obs_models_per_s": sumT * K / (fms / 1e3),
                      "tflops": 2.0 * N * N * sumT * K / (fms / 1e3) / 1e12}
+    # Baum-Welch re-estimation (E-step + M-step) on the same data: one
+    # iteration captured in a CUDA graph and timed like the learning step, and
+    # the library's graph-replayed loop run for a few iterations from the
+    # current parameters (the log-likelihood it reports must not fall)
+    from paper_1310_3322_gb300 import baum_welch
+    bw_p = [x.clone() for x in probs]
+    bw_ll = torch.empty(w.S, device=dev)
+
+    def bw_iter():
+        hmm.hmm_forward_backward(*bw_p, lab, precision=hmm.HMM_AUTO, loglik=bw_ll, counts=cnts,
+                                 workspace=ws)
+        hmm.hmm_mstep(*bw_p, *cnts, out=bw_p)
+
+    bw_iter()
+    torch.cuda.synchronize()
+    bw_graph = torch.cuda.CUDAGraph()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(bw_graph, stream=side):
+            bw_iter()
+    torch.cuda.current_stream().wait_stream(side)
+    bw_ms = _time_steps(torch, bw_graph.replay, args.steps, flush)
+    bw_hist = baum_welch.baum_welch(*bw_p, lab, max_iters=6, tol=0.0, chunk=3, workspace=ws)
+    assert hmm.hmm_get_device_status(ws) == 0
+    bw = {"ms_per_iter": bw_ms, "obs_per_s": sumT / (bw_ms / 1e3),
+          "loglik_per_obs_first_last": [bw_hist[0] / sumT, bw_hist[-1] / sumT],
+          "timing": "CUDA-graph replay of forward-backward + M-step, L2 flushed"}
     line = {
         "metric": METRIC, "value": sumT / (ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -685,7 +713,113 @@ def run_learning(args):
         "clocks": clk,
         "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]},
         "forward_all_models": fwd,
+        "baum_welch": bw,
         "gpu_launches": 8 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_teamwork(args):
+    """Paper-shaped recognition (Sec. 5.7): four roles with one set of six
+    action HMMs each (N = 5, M = 64), many short sequences; one step = for
+    every role, the forward of its sequences against its six models with the
+    argmax and the Viterbi scores, decoded action and best path, the four
+    roles on four streams of one CUDA graph. Units = sum_s T_s * 6."""
+    import torch
+    from paper_1310_3322_gb300 import hmm, synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.make_workload("teamwork", n_seqs=args.n_seqs, seed=synth.SEEDS["teamwork"] + rank)
+    R = w.meta["roles"]
+    Kr, N, M = w.K // R, w.N, w.M
+    sumT = int(w.lengths.astype(np.int64).sum())
+    units = sumT * Kr
+    sym = torch.from_numpy(w.symbols).to(dev)
+    pi, A, B = (torch.from_numpy(x).to(dev) for x in (w.pi, w.A, w.B))
+    path = torch.empty(max(w.total_obs, 1), dtype=torch.int32, device=dev)
+    roles = []
+    for r in range(R):
+        idx = np.nonzero(w.labels // Kr == r)[0]
+        sq = hmm.Sequences(symbols=sym, offsets=torch.from_numpy(w.offsets[idx]).to(dev),
+                           lengths=torch.from_numpy(w.lengths[idx]).to(dev),
+                           max_len=int(w.lengths[idx].max()))
+        sl = slice(r * Kr, (r + 1) * Kr)
+        roles.append(dict(seqs=sq, p=(pi[sl], A[sl], B[sl]),
+                          ll=torch.empty((idx.size, Kr), device=dev),
+                          am=torch.empty(idx.size, dtype=torch.int32, device=dev),
+                          vs=torch.empty((idx.size, Kr), device=dev),
+                          vb=torch.empty(idx.size, dtype=torch.int32, device=dev),
+                          ws=(hmm.Workspace(dev), hmm.Workspace(dev)),
+                          stream=torch.cuda.Stream(device=dev)))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def role_step(x):
+        hmm.hmm_forward(*x["p"], x["seqs"], loglik=x["ll"], argmax=x["am"], workspace=x["ws"][0])
+        hmm.hmm_viterbi(*x["p"], x["seqs"], score=x["vs"], best_model=x["vb"], path=path,
+                        workspace=x["ws"][1])
+
+    def step():
+        cur = torch.cuda.current_stream()
+        for x in roles:
+            x["stream"].wait_stream(cur)
+            with torch.cuda.stream(x["stream"]):
+                role_step(x)
+        for x in roles:
+            cur.wait_stream(x["stream"])
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    for x in roles:
+        st = hmm.hmm_get_device_status(x["ws"][0]) | hmm.hmm_get_device_status(x["ws"][1])
+        if st:
+            raise RuntimeError(f"device status {st:#x}")
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = _time_steps(torch, graph.replay, args.steps, flush)
+    clk = clocks.stop()
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, step, args.steps, flush)
+    kt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    per_launch = {k: v[1] / v[0] for k, v in kt.items() if v[0]}
+    # algorithmic work per launch (one role): 2N^2 + N flop per obs*model
+    # (forward: alpha A, emission; Viterbi scores: the same count in max-plus)
+    flop_launch = (2.0 * N * N + N) * units / R
+    dom = max(("forward", "viterbi_scores"), key=lambda k: per_launch.get(k, 0.0))
+    achieved = flop_launch / (per_launch[dom] / 1e3) / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"teamwork {R} roles x {Kr} actions, N={N} M={M} S={w.S} "
+                               "T~U{20..120} (per role: forward of its models + argmax, "
+                               "Viterbi scores + decoded action + path; 4 streams, CUDA graph)",
+                   "units_per_step": units,
+                   "l2": "flushed between steps (256 MB write outside the timed events)"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "launch_ms": per_launch[dom],
+                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x "
+                                   f"{SM_MAX_MHZ:.0f} MHz", "traffic": None},
+        "clocks": clk,
+        "kernel_ms_per_launch": per_launch,
+        "gpu_launches": sum(v[0] for v in kt.values()),
     }
     print(json.dumps(line), flush=True)
 
@@ -702,6 +836,9 @@ def main():
         return
     if args.workload in ("gradient", "training"):
         run_learning(args)
+        return
+    if args.workload == "teamwork":
+        run_teamwork(args)
         return
     run_gpu(args)
 

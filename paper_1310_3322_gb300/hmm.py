@@ -132,6 +132,8 @@ def _ptr(t) -> Optional[int]:
         return None
     if isinstance(t, int):
         return t
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous (dense, row-major)")
     return t.data_ptr()
 
 

@@ -20,6 +20,11 @@ configurations:
                                  T ~ U{100..2000}
   training   K=20, N=64,  M=128  logits ~ N(0,0.5^2); 65536 sequences,
                                  P(T) ~ T^-1.5 on [50,1000] (inverse CDF, floor)
+  teamwork   4 roles x 6 actions = 24 models, N=5, M=64 (six binary features
+                                 as one mixed-radix symbol); parameters as
+                                 "batched"; 16384 sequences, T ~ U{20..120};
+                                 label = role * 6 + action, role and action
+                                 uniform (the application shape of Sec. 5.7)
 
 Every sequence is sampled from the model of its label. Parameters are stored
 as float32 (what the GPU computes with); the oracle reads the same float32
@@ -33,7 +38,7 @@ from typing import Optional
 import numpy as np
 
 SEEDS = {"plain": 1310001, "batched": 1310002, "gradient": 1310003, "large": 1310004,
-         "training": 1310005}
+         "training": 1310005, "teamwork": 1310006}
 
 SPECS = {
     "plain": dict(K=1, N=4, M=8, S=64, lengths=("fixed", 50), params=("dirichlet", 1.0)),
@@ -45,6 +50,8 @@ SPECS = {
                   params=("dirichlet", 0.3)),
     "training": dict(K=20, N=64, M=128, S=65536, lengths=("powerlaw", 1.5, 50, 1000),
                      params=("logits", 0.5)),
+    "teamwork": dict(K=24, N=5, M=64, S=16384, lengths=("uniform", 20, 120),
+                     params=("sticky", 0.5, 0.6, 0.9), roles=4),
 }
 
 
@@ -208,7 +215,8 @@ def make_workload(name: str, n_seqs: Optional[int] = None, seed: Optional[int] =
         offsets[1:] = np.cumsum(T.astype(np.int64))[:-1]
     return Workload(name=name, K=Kk, N=spec["N"], M=spec["M"], pi=pi, A=A, B=B,
                     symbols=symbols, offsets=offsets, lengths=T, labels=labels, seed=seed,
-                    logits=logits, meta={"S": S, "lengths": lengths or spec["lengths"]})
+                    logits=logits, meta={"S": S, "lengths": lengths or spec["lengths"],
+                                         "roles": spec.get("roles", 1)})
 
 
 def resample(w: Workload, idx, round_: int) -> Workload:
@@ -246,3 +254,27 @@ def random_sequences(rng: np.random.Generator, S: int, M: int, lo: int, hi: int)
         offsets[1:] = np.cumsum(T.astype(np.int64))[:-1]
     symbols = rng.integers(0, M, size=int(T.astype(np.int64).sum())).astype(np.int32)
     return symbols, offsets, T
+
+
+def role_split(w: Workload, roles: int):
+    """Splits a workload whose K models are ``roles`` consecutive sets (one HMM
+    set per role, Sec. 5.7) into one workload per role: that role's models,
+    its sequences (own packed buffer) and labels relative to the set."""
+    if w.K % roles:
+        raise ValueError("K is not a multiple of the number of roles")
+    Kr = w.K // roles
+    out = []
+    for r in range(roles):
+        idx = np.nonzero(w.labels // Kr == r)[0]
+        T = w.lengths[idx]
+        off = np.zeros(idx.size, np.int64)
+        if idx.size:
+            off[1:] = np.cumsum(T.astype(np.int64))[:-1]
+        sym = (np.concatenate([w.symbols[w.offsets[i]:w.offsets[i] + w.lengths[i]] for i in idx])
+               if idx.size else np.zeros(0, np.int32)).astype(np.int32)
+        sl = slice(r * Kr, (r + 1) * Kr)
+        out.append(replace(w, name=f"{w.name}/role{r}", K=Kr, pi=w.pi[sl].copy(),
+                           A=w.A[sl].copy(), B=w.B[sl].copy(), symbols=sym, offsets=off,
+                           lengths=T.copy(), labels=(w.labels[idx] % Kr).astype(np.int32),
+                           logits=None, meta={**w.meta, "role": r, "index": idx}))
+    return out

@@ -6,7 +6,7 @@ import pytest
 from paper_1310_3322_gb300 import synth
 
 
-@pytest.mark.parametrize("name", ["plain", "batched", "gradient"])
+@pytest.mark.parametrize("name", ["plain", "batched", "gradient", "teamwork"])
 def test_workload_shapes_and_determinism(name):
     a = synth.make_workload(name)
     b = synth.make_workload(name)
@@ -55,3 +55,20 @@ def test_resample_changes_only_selected():
         b = v.symbols[v.offsets[s]: v.offsets[s] + v.lengths[s]]
         if s not in (3, 7):
             np.testing.assert_array_equal(a, b)
+
+
+def test_role_split_partitions_sequences_and_models():
+    w = synth.make_workload("teamwork", n_seqs=300)
+    parts = synth.role_split(w, w.meta["roles"])
+    assert len(parts) == 4 and sum(p.S for p in parts) == w.S
+    seen = np.concatenate([p.meta["index"] for p in parts])
+    np.testing.assert_array_equal(np.sort(seen), np.arange(w.S))
+    for r, p in enumerate(parts):
+        assert p.K == 6 and p.labels.min() >= 0 and p.labels.max() < 6
+        np.testing.assert_array_equal(p.A, w.A[6 * r: 6 * r + 6])
+        np.testing.assert_array_equal(p.offsets[1:], np.cumsum(p.lengths)[:-1])
+        for j, s in enumerate(p.meta["index"]):
+            assert w.labels[s] // 6 == r and w.labels[s] % 6 == p.labels[j]
+            np.testing.assert_array_equal(
+                p.symbols[p.offsets[j]: p.offsets[j] + p.lengths[j]],
+                w.symbols[w.offsets[s]: w.offsets[s] + w.lengths[s]])

@@ -17,11 +17,14 @@
 // row b(o_t) in FP32, scale by an exact power of two, accumulate a partial row
 // sum, pack to BF16 and store its share of the next X row.
 //
-// Emission rows: each row's b(o_{t+1}) (NP FP32 values) is brought into that
-// row's slot of a shared-memory staging tile by one bulk (TMA-engine) copy,
-// issued as soon as the row has read b(o_t) and completing on an mbarrier
-// while the next MMA runs. Slots are padded by 16 bytes so that the eight rows
-// of one shared-memory wavefront fall in distinct banks.
+// Emission rows: when the model's whole emission table (M rows of NP FP32
+// values, rows padded by 16 bytes) fits in shared memory next to A^T, it is
+// loaded there once per model and each row reads b(o_t) straight from it, with
+// the symbols themselves loaded two steps ahead -- no global-memory round trip
+// remains on a step's critical path. Otherwise each row's b(o_{t+1}) is
+// brought into that row's slot of a shared-memory staging tile by one bulk
+// (TMA-engine) copy, issued as soon as the row has read b(o_t) and completing
+// on an mbarrier while the next MMA runs.
 //
 // Scaling is one step late so no thread waits for a full row sum inside a
 // step: step t scales by 2^-f_t with f_t the exponent of the previous row sum
@@ -46,20 +49,25 @@ namespace hmmgb {
 
 // AB: operand type, 1 = BF16 (kind::f16, two values per 32-bit column of
 // tensor memory), 2 = TF32 (kind::tf32, one value per column).
-template <int NP, int NT, int TPR, int AB = 1>
+// EMIS: the model's emission table lives in shared memory (M padded rows,
+// after the fixed part); otherwise NT tiles of per-row staging slots.
+template <int NP, int NT, int TPR, int AB = 1, bool EMIS = false>
 struct MmaFwdSmem {
   static constexpr int kB = NP * NP * (AB == 1 ? 2 : 4);  // A^T
   static constexpr int kES = NP * 4 + 16;         // padded emission row, FP32
   static constexpr int kE = 128 * kES;            // one tile of emission rows
   static constexpr int OFF_B = 0;
-  static constexpr int OFF_E = kB;                // [NT] tiles of emission rows
-  static constexpr int OFF_PS = kB + NT * kE;     // partial row sums [NT][TPR][128]
+  static constexpr int OFF_PS = kB;               // partial row sums [NT][TPR][128]
   static constexpr int OFF_BAR = OFF_PS + NT * TPR * 128 * 4;  // mma[NT], emission[NT]
   static constexpr int OFF_MISC = OFF_BAR + 2 * NT * 8;        // tmem, item, abort, last, warp max
-  static constexpr int TOTAL = OFF_MISC + 24 * 4;
+  static constexpr int OFF_E = (OFF_MISC + 24 * 4 + 127) / 128 * 128;  // staging or table
+  static constexpr int FIXED = OFF_E + (EMIS ? 0 : NT * kE);
+  // total bytes for M symbols
+  static constexpr int total(int M) { return FIXED + (EMIS ? M * kES : 0); }
 };
-static_assert(MmaFwdSmem<128, 2, 2, 2>::TOTAL <= 227 * 1024, "shared memory budget");
-static_assert(MmaFwdSmem<64, 4, 1, 2>::TOTAL <= 227 * 1024, "shared memory budget");
+constexpr int kFwdSmemMax = 227 * 1024;
+static_assert(MmaFwdSmem<128, 2, 2, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
+static_assert(MmaFwdSmem<64, 4, 1, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
 
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kTmemCols = 512;  // per tile: D (NP cols) then X (NP/2 cols) at (512/NT) * tile
@@ -134,9 +142,9 @@ __device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int
   st.f = min(126, max(-126, exponent_of(sigma)));
 }
 
-template <int NP, int NT, int TPR, int AB>
+template <int NP, int NT, int TPR, int AB, bool EMIS>
 __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a) {
-  using L = MmaFwdSmem<NP, NT, TPR, AB>;
+  using L = MmaFwdSmem<NP, NT, TPR, AB, EMIS>;
   constexpr int XC = AB == 1 ? NP / 2 : NP;   // tensor-memory columns of X
   constexpr int KI = AB == 1 ? 16 : 8;        // K per instruction
   constexpr int WGT = 128 * TPR;     // threads per tile
@@ -154,7 +162,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
   const int warp = tid >> 5, lane = tid & 31;
   const int wq = warp & 3, h = (wtid >> 7);   // lane quarter, column share
   const int row = wq * 32 + lane;
-  const uint8_t* erow = smem + L::OFF_E + wg * L::kE + row * L::kES;
+  // staging slot of this row (EMIS: the table's base)
+  const uint8_t* erow = smem + L::OFF_E + (EMIS ? 0 : wg * L::kE + row * L::kES);
   const uint32_t eslot = tc::smem_u32(erow);
   float* psum = reinterpret_cast<float*>(smem + L::OFF_PS) + wg * TPR * 128;  // [TPR][128]
   uint64_t* mbar = &bars[wg];
@@ -210,6 +219,13 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
           *reinterpret_cast<uint32_t*>(sB + off) = tc::to_tf32(__ldg(Ak + i * NP + j));
         }
       }
+      if constexpr (EMIS) {  // the model's emission table, rows padded to kES bytes
+        const float4* src = reinterpret_cast<const float4*>(a.mod.Btp + (size_t)k * M * NP);
+        for (int idx = tid; idx < M * NP / 4; idx += kMmaThreads) {
+          const int m = idx / (NP / 4), c = idx % (NP / 4);
+          *reinterpret_cast<float4*>(smem + L::OFF_E + m * L::kES + c * 16) = __ldg(src + idx);
+        }
+      }
       cur_model = k;
       tc::fence_proxy_async();
       __syncthreads();
@@ -261,8 +277,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
       psum[h * 128 + row] = part;
     }
     int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
-    if (Tmax > 1 && h == 0)
-      stage_emission<NP>(eslot, Bk, (1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0, ebar);
+    int o_next2 = (EMIS && 2 < Tn) ? __ldg(o + 2) : 0;  // EMIS: symbols two steps ahead
+    if constexpr (!EMIS) {
+      if (Tmax > 1 && h == 0)
+        stage_emission<NP>(eslot, Bk, (1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0, ebar);
+    }
 
     bool aborted = false;
     for (int t = 1; t < Tmax; ++t) {
@@ -283,8 +302,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
       }
       close_step(st, TPR == 2 ? psum[row] + psum[128 + row] : psum[row], t - 1, Tn);
       const int ot = o_next;
-      if (t + 1 < Tn) o_next = __ldg(o + t + 1);
+      if constexpr (EMIS) {
+        o_next = o_next2;
+        if (t + 2 < Tn) o_next2 = __ldg(o + t + 2);
+      } else {
+        if (t + 1 < Tn) o_next = __ldg(o + t + 1);
+      }
       if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
+      const uint8_t* eb = EMIS ? erow + ((unsigned)ot < (unsigned)M ? ot : 0) * L::kES : erow;
       const bool live = t < Tn && !st.dead && !st.bad;
       if (live) st.F += st.f;
       const float2 fac2 = make_float2(exp2i(-st.f), exp2i(-st.f));
@@ -292,10 +317,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
       // hardware barrier (no issue slots spent spinning)
       bool ok = true;
       if (wtid < 32) {
-        ok = tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
+        if constexpr (!EMIS) ok = tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
         ok = tc::mbar_wait_bounded(mbar, mphase, kWaitLimit) && ok;
       }
-      ephase ^= 1;
+      if constexpr (!EMIS) ephase ^= 1;
       mphase ^= 1;
       // the whole warpgroup agrees before anyone leaves the loop (and every
       // thread has read the partial sums before they are overwritten)
@@ -313,7 +338,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float4 b = *reinterpret_cast<const float4*>(erow + (h * HALF + 32 * c + 4 * q) * 4);
+          const float4 b = *reinterpret_cast<const float4*>(eb + (h * HALF + 32 * c + 4 * q) * 4);
           float2 lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
                                             make_float2(b.x, b.y)), fac2);
           float2 hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
@@ -327,9 +352,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
       }
       tc::tmem_st_wait();
       psum[h * 128 + row] = part;
-      if (t + 1 < Tmax && h == 0) {
-        const int on = (t + 1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0;
-        stage_emission<NP>(eslot, Bk, on, ebar);
+      if constexpr (!EMIS) {
+        if (t + 1 < Tmax && h == 0) {
+          const int on = (t + 1 < Tn && (unsigned)o_next < (unsigned)M) ? o_next : 0;
+          stage_emission<NP>(eslot, Bk, on, ebar);
+        }
       }
     }
     tc::bar_sync(1 + wg, WGT);
@@ -378,20 +405,21 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
   __syncthreads();
   if (misc[2] && wtid == 0) {
     tc::mbar_wait_bounded(mbar, mphase, kWaitLimit);
-    tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
+    if constexpr (!EMIS) tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
   }
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int NP, int NT, int TPR, int AB>
+template <int NP, int NT, int TPR, int AB, bool EMIS>
 static cudaError_t launch_mma_t(const MmaFwdLaunch& a, cudaStream_t st) {
-  auto kern = hmm_forward_mma<NP, NT, TPR, AB>;
-  using L = MmaFwdSmem<NP, NT, TPR, AB>;
+  auto kern = hmm_forward_mma<NP, NT, TPR, AB, EMIS>;
+  using L = MmaFwdSmem<NP, NT, TPR, AB, EMIS>;
   // one CTA per SM (it holds all 512 tensor-memory columns): ask for more
   // than half of the shared memory even when the tiles need less
-  const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;
+  const int need = L::total(a.seq.M);
+  const int smem = need > 120 * 1024 ? need : 120 * 1024;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   int blocks = num_sms();
@@ -402,9 +430,17 @@ static cudaError_t launch_mma_t(const MmaFwdLaunch& a, cudaStream_t st) {
 
 int mma_tiles_per_cta(int NP) { return NP == 64 ? 4 : 2; }
 
+// The emission table goes to shared memory when it fits next to A^T.
+template <int NP, int NT, int TPR, int AB>
+static cudaError_t launch_mma_e(const MmaFwdLaunch& a, cudaStream_t st) {
+  if (MmaFwdSmem<NP, NT, TPR, AB, true>::total(a.seq.M) <= kFwdSmemMax)
+    return launch_mma_t<NP, NT, TPR, AB, true>(a, st);
+  return launch_mma_t<NP, NT, TPR, AB, false>(a, st);
+}
+
 cudaError_t launch_forward_mma(int NP, bool tf32, const MmaFwdLaunch& a, cudaStream_t st) {
-  if (NP == 64) return tf32 ? launch_mma_t<64, 4, 1, 2>(a, st) : launch_mma_t<64, 4, 1, 1>(a, st);
-  if (NP == 128) return tf32 ? launch_mma_t<128, 2, 2, 2>(a, st) : launch_mma_t<128, 2, 2, 1>(a, st);
+  if (NP == 64) return tf32 ? launch_mma_e<64, 4, 1, 2>(a, st) : launch_mma_e<64, 4, 1, 1>(a, st);
+  if (NP == 128) return tf32 ? launch_mma_e<128, 2, 2, 2>(a, st) : launch_mma_e<128, 2, 2, 1>(a, st);
   return cudaErrorInvalidValue;
 }
 

@@ -49,6 +49,9 @@ CASES = [
     ("training", 96, ("uniform", 1, 300), {"K": 3}),         # N=64, M=128
     ("large", 40, ("uniform", 0, 200), {"K": 2, "N": 100}),  # padded to 128
     ("gradient", 60, ("uniform", 1, 150), {"K": 3, "N": 40}),  # padded to 64
+    # emission tables too large for shared memory: per-row staging copies
+    ("large", 40, ("uniform", 1, 150), {"K": 2, "M": 400}),
+    ("training", 60, ("uniform", 1, 150), {"K": 2, "M": 900}),
 ]
 
 

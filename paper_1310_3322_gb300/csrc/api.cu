@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -161,6 +162,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.nchunks = first_chunks(cap);
     L.m_sorted = off; off = align256(off + S * 4);
     L.m_tmp = off; off = align256(off + S * 4);
+    L.m_keys = off; off = align256(off + 2 * (size_t)std::max<int64_t>(S, cap) * 4);
     L.m_tiles = off; off = align256(off + ((size_t)cap * 6 + (size_t)d.K * 2) * 4);
     L.m_ntiles = off; off = align256(off + 4);
     L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
@@ -385,6 +387,8 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   p.loglik = loglik;
   p.sorted = at<int32_t>(ws, L.m_sorted);
   p.tmp = at<int32_t>(ws, L.m_tmp);
+  p.key = at<uint32_t>(ws, L.m_keys);
+  p.key_tmp = p.key + std::max<int64_t>(seqs->S, (int64_t)cap);
   p.tile_start = tiles; p.tile_rows = tiles + cap; p.tile_model = tiles + 2 * cap;
   p.tile_len = tiles + 3 * cap; p.tile_order = tiles + 4 * cap; p.tile_tmp = tiles + 5 * cap;
   p.group_start = tiles + 6 * cap; p.group_end = p.group_start + dims.K;

@@ -36,7 +36,7 @@ struct WsLayout {
   int64_t slot_floats; // floats per slot (NP + NP*NP + NP*M)
   int nchunks;         // first-level reduction chunks
   // tensor-core adjoint
-  size_t m_sorted, m_tmp, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf;
+  size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf;
   int64_t m_ckpt_bytes, m_scr_bytes, m_gexp_bytes;
   int m_grid;
 };
@@ -422,6 +422,8 @@ struct MmaPlanArgs {
   float* loglik;                // rows in no tile: 0 (T = 0) or NaN (invalid)
   int32_t* sorted;              // [S] tile rows, in tile order
   int32_t* tmp;                 // [S] scratch
+  uint32_t* key;                // [max(S, cap)] sort keys of `sorted` (model << 10 | length key)
+  uint32_t* key_tmp;            // [max(S, cap)] scratch
   int32_t* tile_start;          // [cap] first row (index into sorted)
   int32_t* tile_rows;           // [cap] rows in the tile (1..128)
   int32_t* tile_model;          // [cap]

@@ -155,73 +155,178 @@ cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // plan of the tensor-core adjoint (one 1024-thread block)
 // ---------------------------------------------------------------------------
-// One stable counting-sort pass: `out` receives `in` ordered by digit(item) in
-// [0, 256), items with equal digits keeping their input order. Chunks of 1024
-// items are ranked with warp match masks and per-(digit, warp) counts `wh`
-// (digit-major, all zero on entry and on return).
-template <typename DigitFn>
-__device__ void stable_pass(const int32_t* in, int32_t* out, int n, DigitFn digit, int* base,
-                            int* wh) {
+// One stable counting-sort pass over (key, item) pairs: the outputs receive
+// the inputs ordered by the digit (key >> shift) & 255, pairs with equal
+// digits keeping their input order. A chunk is 4096 pairs, 128 consecutive
+// ones per warp. Within a warp, equal digits are found with eight ballots
+// (one per digit bit) and ranked in index order; per-(digit, warp) counts in
+// `wh` ([256][32], digit-major, zero on entry and on return) become offsets
+// by a scan over the warps of each digit (four threads per digit). Each chunk
+// is first placed in digit order in shared memory and then written out in
+// runs, so the global stores are coalesced; the next chunk's pairs are loaded
+// while the current one is ranked.
+constexpr int kSortIpt = 4;                          // pairs per thread and chunk
+constexpr int kSortChunk = kSortIpt * kPlanThreads;  // 4096
+
+struct SortSmem {
+  int base[256];    // output start of each digit (running over chunks)
+  int lstart[256];  // start of each digit within the chunk
+  int tot[256];     // the chunk's count per digit
+  int wh[256 * 32];
+  int st_item[kSortChunk];
+  uint32_t st_key[kSortChunk];
+};
+
+__device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
+  unsigned peers = __ballot_sync(HMM_FULL_MASK, valid);
+  if (!valid) peers = ~peers;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1;
+    const unsigned bal = __ballot_sync(HMM_FULL_MASK, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+// wh[d][w] (counts) -> sum over warps w' < w of wh[d][w'], tot[d] = the
+// digit's total. Thread t owns digit t / 4, warps 8(t % 4)..+7.
+__device__ __forceinline__ void scan_warp_counts(SortSmem& m) {
+  const int tid = threadIdx.x, d = tid >> 2, q = tid & 3;
+  int4* p = reinterpret_cast<int4*>(m.wh + d * 32 + q * 8);
+  const int4 a = p[0], b = p[1];
+  const int s = a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w;
+  int x = s;  // inclusive scan over the digit's four threads (consecutive lanes)
+  int y = __shfl_up_sync(HMM_FULL_MASK, x, 1);
+  if (q >= 1) x += y;
+  y = __shfl_up_sync(HMM_FULL_MASK, x, 2);
+  if (q >= 2) x += y;
+  int run = x - s;
+  int4 oa, ob;
+  oa.x = run; run += a.x; oa.y = run; run += a.y; oa.z = run; run += a.z; oa.w = run; run += a.w;
+  ob.x = run; run += b.x; ob.y = run; run += b.y; ob.z = run; run += b.z; ob.w = run; run += b.w;
+  p[0] = oa;
+  p[1] = ob;
+  if (q == 3) m.tot[d] = x;
+}
+
+// dst[d] = exclusive prefix of src[0..256) (one warp).
+__device__ __forceinline__ void warp_scan256(const int* src, int* dst) {
+  const int lane = threadIdx.x & 31;
+  int v[8], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { v[q] = src[lane * 8 + q]; sum += v[q]; }
+  int x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(HMM_FULL_MASK, x, o);
+    if (lane >= o) x += y;
+  }
+  int run = x - sum;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { dst[lane * 8 + q] = run; run += v[q]; }
+}
+
+__device__ __forceinline__ void zero_wh(SortSmem& m) {
+  int4* p = reinterpret_cast<int4*>(m.wh + (threadIdx.x >> 2) * 32 + (threadIdx.x & 3) * 8);
+  p[0] = make_int4(0, 0, 0, 0);
+  p[1] = make_int4(0, 0, 0, 0);
+}
+
+__device__ void stable_pass(const int32_t* in_i, const uint32_t* in_k, int32_t* out_i,
+                            uint32_t* out_k, int n, int shift, SortSmem& m) {
+  static_assert(kPlanThreads == 1024, "one thread per (digit, quarter of the warps)");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid < 256) base[tid] = 0;
-  __syncthreads();
-  for (int c0 = 0; c0 < n; c0 += kPlanThreads) {  // one atomic per distinct digit per warp
-    const int i = c0 + tid;
-    const int d = i < n ? digit(in[i]) : 256;
-    const unsigned peers = __match_any_sync(HMM_FULL_MASK, d);
-    if (d < 256 && lane == __ffs(peers) - 1) atomicAdd(&base[d], __popc(peers));
-  }
-  __syncthreads();
-  if (warp == 0) {  // exclusive scan of the 256 digit counts
-    int v[8], sum = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  // digit histogram: per-warp counts (each warp owns its column of wh)
+  for (int c0 = 0; c0 < n; c0 += kSortChunk) {
+    int dv[kSortIpt];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) { v[q] = base[lane * 8 + q]; sum += v[q]; }
-    int x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(HMM_FULL_MASK, x, o);
-      if (lane >= o) x += y;
+    for (int u = 0; u < kSortIpt; ++u) {
+      const int i = c0 + warp * (32 * kSortIpt) + u * 32 + lane;
+      dv[u] = i < n ? (int)((__ldcg(in_k + i) >> shift) & 255u) : 256;
     }
-    int run = x - sum;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) { base[lane * 8 + q] = run; run += v[q]; }
-  }
-  __syncthreads();
-  for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
-    const int i = c0 + tid;
-    const bool valid = i < n;
-    const int item = valid ? in[i] : 0;
-    const int d = valid ? digit(item) : 256;
-    const unsigned peers = __match_any_sync(HMM_FULL_MASK, d);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && rank == 0) wh[d * 32 + warp] = __popc(peers);
-    __syncthreads();
-    // per digit, exclusive scan over the 32 warps (warp w owns digits 8w..8w+7)
-#pragma unroll
-    for (int dd = 0; dd < 8; ++dd) {
-      const int d2 = warp * 8 + dd;
-      const int v = wh[d2 * 32 + lane];
-      int x = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(HMM_FULL_MASK, x, o);
-        if (lane >= o) x += y;
-      }
-      const int b0 = base[d2];
+    for (int u = 0; u < kSortIpt; ++u) {
+      const bool valid = dv[u] < 256;
+      const unsigned peers = digit_peers(dv[u] & 255, valid);
+      if (valid && (peers & lt) == 0) m.wh[dv[u] * 32 + warp] += __popc(peers);
       __syncwarp();
-      wh[d2 * 32 + lane] = b0 + x - v;
-      if (lane == 31) base[d2] = b0 + x;
     }
-    __syncthreads();
-    if (valid) out[wh[d * 32 + warp] + rank] = item;
-    __syncthreads();
-#pragma unroll
-    for (int dd = 0; dd < 8; ++dd) wh[(warp * 8 + dd) * 32 + lane] = 0;  // the entries this warp scanned
   }
   __syncthreads();
+  scan_warp_counts(m);  // tot[d] = the digit's total
+  __syncthreads();
+  if (warp == 0) warp_scan256(m.tot, m.base);
+  zero_wh(m);
+  __syncthreads();
+  // scatter, chunk by chunk
+  uint32_t kn[kSortIpt];
+  int in_[kSortIpt];
+#pragma unroll
+  for (int u = 0; u < kSortIpt; ++u) {
+    const int i = warp * (32 * kSortIpt) + u * 32 + lane;
+    kn[u] = i < n ? __ldcg(in_k + i) : 0u;
+    in_[u] = i < n ? __ldcg(in_i + i) : 0;
+  }
+  for (int c0 = 0; c0 < n; c0 += kSortChunk) {
+    const int cn = min(kSortChunk, n - c0);
+    uint32_t key[kSortIpt];
+    int item[kSortIpt], dv[kSortIpt], off[kSortIpt];
+#pragma unroll
+    for (int u = 0; u < kSortIpt; ++u) {
+      key[u] = kn[u];
+      item[u] = in_[u];
+      const int i = c0 + warp * (32 * kSortIpt) + u * 32 + lane;
+      dv[u] = i < n ? (int)((key[u] >> shift) & 255u) : 256;
+      const int inext = i + kSortChunk;  // the next chunk, in flight
+      if (inext < n) {
+        kn[u] = __ldcg(in_k + inext);
+        in_[u] = __ldcg(in_i + inext);
+      }
+    }
+    // ranks within the warp, in index order (slot by slot)
+#pragma unroll
+    for (int u = 0; u < kSortIpt; ++u) {
+      const bool valid = dv[u] < 256;
+      const unsigned peers = digit_peers(dv[u] & 255, valid);
+      const int cur = valid ? m.wh[dv[u] * 32 + warp] : 0;
+      off[u] = cur + __popc(peers & lt);
+      __syncwarp();
+      if (valid && (peers & lt) == 0) m.wh[dv[u] * 32 + warp] = cur + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    scan_warp_counts(m);
+    __syncthreads();
+    if (warp == 0) warp_scan256(m.tot, m.lstart);
+    __syncthreads();
+    // the chunk in digit order in shared memory
+#pragma unroll
+    for (int u = 0; u < kSortIpt; ++u)
+      if (dv[u] < 256) {
+        const int lp = m.lstart[dv[u]] + m.wh[dv[u] * 32 + warp] + off[u];
+        m.st_item[lp] = item[u];
+        m.st_key[lp] = key[u];
+      }
+    __syncthreads();
+    // ... and out in runs: local position j of digit d goes to base[d] + j - lstart[d]
+    for (int j = tid; j < cn; j += kPlanThreads) {
+      const uint32_t k = m.st_key[j];
+      const int d = (int)((k >> shift) & 255u);
+      const int pos = m.base[d] + j - m.lstart[d];
+      out_i[pos] = m.st_item[j];
+      out_k[pos] = k;
+    }
+    __syncthreads();
+    if (tid < 256) m.base[tid] += m.tot[tid];
+    zero_wh(m);
+    __syncthreads();
+  }
 }
 
 __device__ __forceinline__ int len_key(int T) { return kLenBuckets - 1 - length_bucket(T); }
+static_assert(kLenBuckets == 1024, "sort keys hold the length key in 10 bits");
 
 // Length of every tile = its longest row (the length buckets above 255 are
 // wider than one length, so the first row is not always the longest); one
@@ -240,23 +345,28 @@ __device__ void tile_lengths(const MmaPlanArgs& a, int n_tiles) {
 }
 
 __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
-  __shared__ int base[256];
-  __shared__ int wh[32 * 256];
+  extern __shared__ __align__(16) uint8_t plan_smem[];
+  SortSmem& m = *reinterpret_cast<SortSmem*>(plan_smem);
   __shared__ int itmp[32];
   __shared__ int total;
   const int tid = threadIdx.x;
-  for (int i = tid; i < 32 * 256; i += kPlanThreads) wh[i] = 0;
+  for (int i = tid; i < 32 * 256; i += kPlanThreads) m.wh[i] = 0;
 
-  // rows with T >= 1, in index order (4 consecutive sequences per thread);
-  // the others get their log-likelihood here
+  // rows with T >= 1, in index order (4 consecutive sequences per thread),
+  // with their sort keys (model << 10 | length key); the other rows get their
+  // log-likelihood here
   int n = 0;
   for (int c0 = 0; c0 < a.S; c0 += 4 * kPlanThreads) {
     int keep[4], cnt = 0;
+    uint32_t key[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int s = c0 + 4 * tid + u;
       const int T = s < a.S ? a.seqlen[s] : 0;
       keep[u] = (s < a.S && T >= 1) ? 1 : 0;
+      key[u] = 0;
+      if (keep[u])
+        key[u] = ((a.labelled ? (uint32_t)a.model_of_seq[s] : 0u) << 10) | (uint32_t)len_key(T);
       cnt += keep[u];
       if (s < a.S && !keep[u]) {
         const float v = T == 0 ? 0.f : __int_as_float(0x7fc00000);
@@ -268,40 +378,42 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
     int pos = n + block_exclusive_scan<int>(cnt, itmp, &total);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (keep[u]) a.tmp[pos++] = c0 + 4 * tid + u;
+      if (keep[u]) {
+        a.sorted[pos] = c0 + 4 * tid + u;
+        a.key[pos] = key[u];
+        ++pos;
+      }
     n += total;
     __syncthreads();
   }
 
-  // stable sort: by decreasing length (two 8-bit digits of the length key),
-  // then (labelled) by model
-  const int32_t* seqlen = a.seqlen;
-  const int32_t* mos = a.model_of_seq;
-  auto lo8 = [seqlen](int s) { return len_key(seqlen[s]) & 255; };
-  auto hi8 = [seqlen](int s) { return len_key(seqlen[s]) >> 8; };
-  stable_pass(a.tmp, a.sorted, n, lo8, base, wh);
-  stable_pass(a.sorted, a.tmp, n, hi8, base, wh);
-  const int32_t* res = a.tmp;
-  if (a.labelled) {
-    auto m0 = [mos](int s) { return mos[s] & 255; };
-    stable_pass(a.tmp, a.sorted, n, m0, base, wh);
-    res = a.sorted;
-    if (a.K > 256) {
-      auto m1 = [mos](int s) { return (mos[s] >> 8) & 255; };
-      stable_pass(a.sorted, a.tmp, n, m1, base, wh);
-      res = a.tmp;
-    }
+  // stable LSD sort on the key: decreasing length within each model, models
+  // in increasing order, input order among equal keys
+  int bits = 10;
+  if (a.labelled)
+    while (bits < 32 && ((a.K - 1) >> (bits - 10)) != 0) ++bits;
+  int32_t* ci = a.sorted;
+  uint32_t* ck = a.key;
+  int32_t* oi = a.tmp;
+  uint32_t* ok = a.key_tmp;
+  for (int shift = 0; shift < bits; shift += 8) {
+    stable_pass(ci, ck, oi, ok, n, shift, m);
+    int32_t* ti = ci; ci = oi; oi = ti;
+    uint32_t* tk = ck; ck = ok; ok = tk;
   }
-  if (res != a.sorted) {
-    for (int i = tid; i < n; i += kPlanThreads) a.sorted[i] = res[i];
+  if (ci != a.sorted) {
+    for (int i = tid; i < n; i += kPlanThreads) {
+      a.sorted[i] = ci[i];
+      a.key[i] = ck[i];
+    }
     __syncthreads();
   }
 
   // tiles of at most 128 rows of one model
   int n_tiles = 0;
   if (a.labelled) {
-    const int32_t* sorted = a.sorted;
-    auto model_at = [sorted, mos](int p) { return mos[sorted[p]]; };
+    const uint32_t* keys = a.key;
+    auto model_at = [keys](int p) { return (int)(__ldcg(keys + p) >> 10); };
     // first and one-past-last position of every model's group
     for (int p = tid; p < n; p += kPlanThreads) {
       const int k = model_at(p);
@@ -341,12 +453,17 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
     }
     n_tiles = min(n_tiles, a.n_tiles_cap);
     tile_lengths(a, n_tiles);
-    // longest tiles first (stable in tile index)
-    const int32_t* tl = a.tile_len;
-    auto t0 = [tl](int t) { return len_key(tl[t]) & 255; };
-    auto t1 = [tl](int t) { return len_key(tl[t]) >> 8; };
-    stable_pass(a.tile_order, a.tile_tmp, n_tiles, t0, base, wh);
-    stable_pass(a.tile_tmp, a.tile_order, n_tiles, t1, base, wh);
+    // longest tiles first (stable in tile index): keys = length keys; the
+    // row keys are no longer needed, their buffers hold the tile keys
+    for (int id = tid; id < n_tiles; id += kPlanThreads) {
+      a.tile_tmp[id] = id;
+      a.key_tmp[id] = (uint32_t)len_key(a.tile_len[id]);
+    }
+    __syncthreads();
+    stable_pass(a.tile_tmp, a.key_tmp, a.tile_order, a.key, n_tiles, 0, m);
+    stable_pass(a.tile_order, a.key, a.tile_tmp, a.key_tmp, n_tiles, 8, m);
+    for (int id = tid; id < n_tiles; id += kPlanThreads) a.tile_order[id] = a.tile_tmp[id];
+    __syncthreads();
   } else {
     // every length-sorted chunk of 128 rows against every model, chunk-major
     // (already longest first)
@@ -370,7 +487,11 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
 }
 
 cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st) {
-  mma_plan_kernel<<<1, kPlanThreads, 0, st>>>(a);
+  const int smem = (int)sizeof(SortSmem);
+  cudaError_t e = cudaFuncSetAttribute(mma_plan_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  mma_plan_kernel<<<1, kPlanThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -60,10 +60,11 @@ def parse():
     ap.add_argument("--lanes", default=None,
                     help="fixed lanes per pair 'fwd,viterbi,paths,adjoint' instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "large", "gradient", "training", "teamwork"],
+                    choices=[WORKLOAD, "large", "gradient", "training", "teamwork", "cuhmm"],
                     help="batched: the full step (default); large: tensor-core forward "
                          "and adjoint; gradient/training: the learning step (and a "
-                         "Baum-Welch iteration); teamwork: per-role recognition, N=5")
+                         "Baum-Welch iteration); teamwork: per-role recognition, N=5; "
+                         "cuhmm: the 512-state forward")
     return ap.parse_args()
 
 
@@ -840,6 +841,72 @@ def run_teamwork(args):
     print(json.dumps(line), flush=True)
 
 
+def run_wide(args):
+    """The 512-state x 512-sequence shape Sec. 5.6 quotes for the cited forward
+    kernel: the forward of every sequence on the tensor cores (one 128-row tile
+    per CTA, A^T streamed from a BF16 image); units = sum_s T_s * K."""
+    import torch
+    from paper_1310_3322_gb300 import hmm, synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.make_workload("cuhmm", n_seqs=args.n_seqs, seed=synth.SEEDS["cuhmm"] + rank)
+    K, N, M = w.K, w.N, w.M
+    sumT = int(w.lengths.astype(np.int64).sum())
+    units = sumT * K
+    seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
+    pi, A, B = (torch.from_numpy(x).to(dev) for x in (w.pi, w.A, w.B))
+    ll = torch.empty((w.S, K), device=dev)
+    am = torch.empty(w.S, dtype=torch.int32, device=dev)
+    ws = hmm.Workspace(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_BF16_MMA, loglik=ll, argmax=am,
+                        workspace=ws)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(ws) == 0
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = _time_steps(torch, step, args.steps, flush)
+    clk = clocks.stop()
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, step, args.steps, flush)
+    kt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    kms = {k: v[1] / v[0] for k, v in kt.items() if v[0]}
+    achieved = 2.0 * N * N * units / (kms["forward"] / 1e3) / 1e12
+    peak, basis = measured_peak_bf16()
+    n_tiles = (w.S + 127) // 128
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    line = {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"cuhmm K={K} N={N} M={M} S={w.S} T~U{{100..500}} (forward of "
+                               "every sequence, tcgen05 BF16, A^T streamed)",
+                   "units_per_step": units, "tiles": n_tiles * K,
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "timing": "eager step, CUDA events"},
+        "roofline": {"bound": "tensor", "kernel": "forward_wide", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "launch_ms": kms["forward"], "peak_basis": f"dense BF16, {basis} (burst)",
+                     "frac_of_busy_sms": achieved / (peak * min(n_tiles * K, sm_count) / sm_count),
+                     "traffic": None},
+        "kernel_ms": kms,
+        "clocks": clk,
+        "gpu_launches": 3 * args.steps,  # setup, A^T image, forward
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -855,6 +922,9 @@ def main():
         return
     if args.workload == "teamwork":
         run_teamwork(args)
+        return
+    if args.workload == "cuhmm":
+        run_wide(args)
         return
     run_gpu(args)
 

@@ -118,11 +118,13 @@ int hmm_max_states(hmm_op_t op, hmm_precision_t precision);
  *           written when model_of_seq is NULL.
  * HMM_FP32 (N <= 64): the alpha recursion runs in FP32 with exact
  * power-of-two rescaling every step; the exponent sum is an integer and the
- * final log is taken in FP64. HMM_BF16_MMA / HMM_TF32_MMA (32 < N <= 128,
- * every sequence against every model): alpha*A on the tensor cores with BF16
- * (u = 2^-8) or TF32 (u = 2^-11, round to nearest) operands and FP32
- * accumulation, |delta log P| <= 2 u T against FP64. HMM_AUTO: tensor cores
- * (BF16) above N = 64. */
+ * final log is taken in FP64. HMM_BF16_MMA (32 < N <= 512) / HMM_TF32_MMA
+ * (32 < N <= 128), every sequence against every model: alpha*A on the tensor
+ * cores with BF16 (u = 2^-8) or TF32 (u = 2^-11, round to nearest) operands
+ * and FP32 accumulation, |delta log P| <= 2 u T against FP64. Above 128
+ * states (the cited cuHMM kernel's 512-state workload, Sec. 5.6) one CTA
+ * holds one 128-sequence tile and streams A^T from a BF16 image the call
+ * builds in the workspace. HMM_AUTO: tensor cores (BF16) above N = 64. */
 int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                 const hmm_seqs_t* seqs, hmm_precision_t precision, float* loglik,
                 int32_t* argmax, void* workspace, size_t workspace_bytes, hmm_stream_t stream);

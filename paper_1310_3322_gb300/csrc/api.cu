@@ -55,11 +55,14 @@ static int np_index(int NP) {
     if (kNPs[i] == NP) return i;
   return -1;
 }
-// 4..64 for the SIMT kernels, 128 for the tensor-core forward
+// 4..64 for the SIMT kernels, 128 for the tensor-core forward and adjoint,
+// 256 and 512 for the wide tensor-core forward
 static int pad_states(int N) {
   for (int i = 0; i < 5; ++i)
     if (N <= kNPs[i]) return kNPs[i];
-  return N <= 128 ? 128 : -1;
+  if (N <= 128) return 128;
+  if (N <= 256) return 256;
+  return N <= 512 ? 512 : -1;
 }
 
 // candidate lanes-per-pair, default first; 0 terminates
@@ -145,6 +148,9 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
   if (op == HMM_OP_VITERBI) {
     L.bp_cap = (q.total_obs > 0 ? q.total_obs : 0) * (int64_t)NP;
     L.bp = off; off = align256(off + (size_t)L.bp_cap);
+  }
+  if (op == HMM_OP_FORWARD && NP >= 256) {
+    L.wimg = off; off = align256(off + (size_t)d.K * NP * NP * 2);
   }
   if (op == HMM_OP_FORWARD_BACKWARD && !mma) {
     L.slot_floats = (int64_t)NP + (int64_t)NP * NP + (int64_t)NP * d.M;
@@ -272,8 +278,8 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
 }
 
 static int max_states(int op, int precision) {
-  if ((op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD) &&
-      (precision == HMM_BF16_MMA || precision == HMM_AUTO))
+  if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 512;
+  if (op == HMM_OP_FORWARD_BACKWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO))
     return 128;
   if (op == HMM_OP_FORWARD && precision == HMM_TF32_MMA) return 128;
   if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
@@ -535,6 +541,36 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
   if (seqs->S == 0) return HMM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e;
+  if (mma && L.NP >= 256) {  // wide state counts: one tile per CTA, A^T streamed
+    const int n_tiles = (seqs->S + 127) / 128;
+    if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+    s.ndone = argmax ? n_tiles : 0;
+    {
+      Timed tm(T_SETUP, st);
+      e = launch_setup(s, st);
+      tm.stop();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+    MmaWideLaunch f;
+    f.seq = seq_args(dims, *seqs, L, ws);
+    f.mod = model_args(L, ws);
+    f.img = at<uint8_t>(ws, L.wimg);
+    f.loglik = loglik;
+    f.argmax = argmax;
+    f.done = at<int32_t>(ws, L.done);
+    f.queue = &at<WsHeader>(ws, 0)->queue[0];
+    f.status = &at<WsHeader>(ws, 0)->status;
+    f.n_tiles = n_tiles;
+    f.n_items = n_tiles * dims.K;
+    {
+      Timed tm(T_FORWARD, st);
+      e = launch_forward_wide(L.NP, f, st);
+      tm.stop();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");
+    return HMM_OK;
+  }
   if (mma) {
     const int n_tiles = (seqs->S + 127) / 128;
     const int nt = mma_tiles_per_cta(L.NP);

@@ -37,6 +37,7 @@ struct WsLayout {
   int nchunks;         // first-level reduction chunks
   // tensor-core adjoint
   size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf;
+  size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
   int64_t m_ckpt_bytes, m_scr_bytes, m_gexp_bytes;
   int m_grid;
 };
@@ -410,6 +411,22 @@ struct MmaFwdLaunch {
 };
 cudaError_t launch_forward_mma(int NP, bool tf32, const MmaFwdLaunch& a, cudaStream_t st);
 int mma_tiles_per_cta(int NP);  // 128-row tiles one CTA of the tensor-core forward holds
+
+// Tensor-core forward for 128 < N <= 512 (mma_wide.cu): one 128-row tile per
+// CTA, A^T streamed from a BF16 image built per call.
+struct MmaWideLaunch {
+  SeqArgs seq;
+  ModelArgs mod;      // probability tables padded to NP (256 or 512)
+  uint8_t* img;       // [K][NP * NP] BF16 image of A^T, chunk-major
+  float* loglik;      // [S][K]
+  int32_t* argmax;    // [S] or NULL
+  int32_t* done;      // per tile
+  int32_t* queue;
+  int32_t* status;
+  int n_items;        // n_tiles * K
+  int n_tiles;        // ceil(S / 128)
+};
+cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st);
 
 // Plan of the tensor-core adjoint: the rows of every 128-row tile share one
 // model, and the tile composition is a deterministic function of the input

@@ -20,6 +20,9 @@ configurations:
                                  T ~ U{100..2000}
   training   K=20, N=64,  M=128  logits ~ N(0,0.5^2); 65536 sequences,
                                  P(T) ~ T^-1.5 on [50,1000] (inverse CDF, floor)
+  cuhmm      K=1,  N=512, M=64   Dirichlet(0.3) rows; 512 sequences,
+                                 T ~ U{100..500} (the 512-state x 512-sequence
+                                 shape Sec. 5.6 quotes; M and T not stated)
   teamwork   4 roles x 6 actions = 24 models, N=5, M=64 (six binary features
                                  as one mixed-radix symbol); parameters as
                                  "batched"; 16384 sequences, T ~ U{20..120};
@@ -38,7 +41,7 @@ from typing import Optional
 import numpy as np
 
 SEEDS = {"plain": 1310001, "batched": 1310002, "gradient": 1310003, "large": 1310004,
-         "training": 1310005, "teamwork": 1310006}
+         "training": 1310005, "teamwork": 1310006, "cuhmm": 1310007}
 
 SPECS = {
     "plain": dict(K=1, N=4, M=8, S=64, lengths=("fixed", 50), params=("dirichlet", 1.0)),
@@ -50,6 +53,8 @@ SPECS = {
                   params=("dirichlet", 0.3)),
     "training": dict(K=20, N=64, M=128, S=65536, lengths=("powerlaw", 1.5, 50, 1000),
                      params=("logits", 0.5)),
+    "cuhmm": dict(K=1, N=512, M=64, S=512, lengths=("uniform", 100, 500),
+                  params=("dirichlet", 0.3)),
     "teamwork": dict(K=24, N=5, M=64, S=16384, lengths=("uniform", 20, 120),
                      params=("sticky", 0.5, 0.6, 0.9), roles=4),
 }

@@ -76,6 +76,12 @@ def test_workspace_size_is_host_only_and_monotone(lib):
     assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 65, 300), ctypes.byref(q),
                                   hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
         == hmm.HMM_ERR_UNSUPPORTED
+    # the forward goes to 512 states (BF16 A^T images of every model included)
+    wide = hmm.hmm_dims_t(3, 512, 64)
+    assert lib.hmm_workspace_size(wide, ctypes.byref(q), hmm.HMM_OP_FORWARD, ctypes.byref(out)) == 0
+    assert out.value >= 3 * 512 * 512 * (4 + 2)
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(3, 513, 64), ctypes.byref(q), hmm.HMM_OP_FORWARD,
+                                  ctypes.byref(out)) == hmm.HMM_ERR_UNSUPPORTED
 
 
 def _forward(lib, dims, seqs, pi=_fake(5), loglik=_fake(8), ws=_fake(9), ws_bytes=1 << 30,
@@ -148,6 +154,8 @@ def test_tuning_table(lib):
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD) == 64
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD) == 64
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD, hmm.HMM_BF16_MMA) == 128
+    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD, hmm.HMM_BF16_MMA) == 512
+    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD, hmm.HMM_TF32_MMA) == 128
     assert hmm.hmm_max_states(hmm.HMM_OP_VITERBI, hmm.HMM_BF16_MMA) == 0
 
 

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import ll_tol, to_gpu
+from helpers import ll_tol, oparams, to_gpu
 from paper_1310_3322_gb300 import hmm, synth
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +55,21 @@ CASES = [
 ]
 
 
+# above 128 states: one tile per CTA with A^T streamed (BF16 only); padded
+# and exact N, ragged tiles, an emission table of more than 256 symbols
+WIDE_CASES = [
+    ("large", 150, ("uniform", 1, 90), {"K": 2, "N": 200, "M": 64}),    # padded to 256
+    ("large", 130, ("uniform", 20, 60), {"K": 2, "N": 256, "M": 300}),
+    ("large", 140, ("uniform", 1, 40), {"K": 2, "N": 333, "M": 64}),    # padded to 512
+    ("large", 129, ("uniform", 10, 40), {"K": 1, "N": 512, "M": 32}),
+]
+
+
+@pytest.mark.parametrize("case", WIDE_CASES, ids=lambda c: f"{c[0]}-{c[3]}")
+def test_wide_tensor_core_forward_matches_oracle(case):
+    test_tensor_core_forward_matches_oracle(case, "bf16")
+
+
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[3]}")
 def test_tensor_core_forward_matches_oracle(case, prec):
@@ -82,6 +97,9 @@ def test_tensor_core_forward_matches_oracle(case, prec):
     print(f"{prec} {name} N={w.N}: max|d|/T vs exact {np.max(err / T):.2e}, "
           f"mean {np.mean(err / T):.2e}; vs rounded-A {np.max(err_r / T):.2e}")
     # recognition: argmax agrees where the top two models are well separated
+    if w.K == 1:
+        np.testing.assert_array_equal(am.cpu().numpy(), np.where(np.isnan(ll[:, 0]), -1, 0))
+        return
     srt = np.sort(ref, axis=1)
     clear = srt[:, -1] - srt[:, -2] > 4 * u * T[:, 0] + 2 * ll_tol(w.lengths)
     np.testing.assert_array_equal(am.cpu().numpy()[clear], ref_am[clear])
@@ -113,3 +131,19 @@ def test_bf16_forward_degenerate_and_errors():
     small = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 2, 16, 5)]
     with pytest.raises(hmm.HmmError):
         hmm.hmm_forward(*small, seqs, precision=hmm.HMM_BF16_MMA)
+
+
+def test_wide_forward_full_cuhmm_shape_sampled():
+    """The 512-state x 512-sequence workload the bench times: sampled
+    sequences against the oracle (exact model, 2uT bound)."""
+    w = synth.make_workload("cuhmm")
+    seqs, pi, A, B = to_gpu(w)
+    ll, am = hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_BF16_MMA)
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    ll = ll.cpu().numpy()
+    assert np.all(np.isfinite(ll))
+    idx = np.random.default_rng(10).choice(w.S, size=6, replace=False)
+    ref, _, _ = oracle.forward(oparams(w), w.symbols, w.offsets[idx], w.lengths[idx],
+                               nthreads=8)
+    T = w.lengths[idx].astype(np.float64)[:, None]
+    assert np.all(np.abs(ll[idx] - ref) <= 2 * U_BF16 * T + ll_tol(w.lengths[idx])[:, None])

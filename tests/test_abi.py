@@ -136,6 +136,16 @@ def test_viterbi_and_adjoint_argument_errors(lib):
                              None) == hmm.HMM_OK
     st = ctypes.c_int32()
     assert lib.hmm_get_device_status(None, None, ctypes.byref(st)) == hmm.HMM_ERR_ARG
+    # Baum-Welch M-step: host-side checks only (nothing is launched)
+    f = [_fake(i) for i in range(1, 10)]
+    assert lib.hmm_mstep(d, None, *f[1:], None) == hmm.HMM_ERR_ARG
+    assert lib.hmm_mstep(d, *f[:5], None, *f[6:], None) == hmm.HMM_ERR_ARG
+    assert lib.hmm_mstep(hmm.hmm_dims_t(2, 0, 8), *f, None) == hmm.HMM_ERR_ARG
+    # the tensor-core forward goes to 512 states, TF32 to 128
+    assert _forward(lib, hmm.hmm_dims_t(2, 513, 8), q, precision=hmm.HMM_BF16_MMA) \
+        == hmm.HMM_ERR_UNSUPPORTED
+    assert _forward(lib, hmm.hmm_dims_t(2, 200, 8), q, precision=hmm.HMM_TF32_MMA) \
+        == hmm.HMM_ERR_UNSUPPORTED
 
 
 def test_tuning_table(lib):

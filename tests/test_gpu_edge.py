@@ -199,6 +199,74 @@ def test_cuda_graph_replay_matches_eager():
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("case", [("training", None), ("large", None), ("large", 300)],
+                         ids=["bf16-64", "bf16-128", "bf16-512"])
+def test_tensor_core_graph_replay_matches_eager(case):
+    """The tensor-core forward (N = 64, 128 and the 512-state kernel) and
+    adjoint (N = 64, 128) captured in one CUDA graph: replays are bitwise the
+    eager results (fixed tile plan, fixed reduction order)."""
+    import torch
+    name, n_big = case
+    over = {"K": 2} if n_big is None else {"K": 2, "N": n_big, "M": 40}
+    w = synth.make_workload(name, n_seqs=300, lengths=("uniform", 1, 90), **over)
+    seqs, pi, A, B = to_gpu(w)
+    lab = seqs.labelled(torch.from_numpy(w.labels).cuda())
+    ws1, ws2 = hmm.Workspace(), hmm.Workspace()
+    prec = hmm.HMM_BF16_MMA
+    with_fb = w.N <= 128
+    eager = list(hmm.hmm_forward(pi, A, B, seqs, precision=prec, workspace=ws1))
+    if with_fb:
+        eager += list(hmm.hmm_forward_backward(pi, A, B, lab, precision=prec, workspace=ws2))
+    outs = [torch.empty_like(x) for x in eager]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            hmm.hmm_forward(pi, A, B, seqs, precision=prec, loglik=outs[0], argmax=outs[1],
+                            workspace=ws1)
+            if with_fb:
+                hmm.hmm_forward_backward(pi, A, B, lab, precision=prec, loglik=outs[2],
+                                         counts=tuple(outs[3:]), workspace=ws2)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(ws1) == 0
+    for a, b in zip(outs, eager):
+        assert torch.equal(a, b)
+
+
+def test_concurrent_streams_match_serial():
+    """Recognition and the adjoint on three streams with their own workspaces
+    (as the batched bench step runs them) give the serial results bitwise."""
+    import torch
+    w = synth.make_workload("batched", n_seqs=700)
+    seqs, pi, A, B = to_gpu(w)
+    lab = seqs.labelled(torch.from_numpy(w.labels).cuda())
+    ws = [hmm.Workspace() for _ in range(3)]
+    ser = [hmm.hmm_forward(pi, A, B, seqs, workspace=ws[0]),
+           hmm.hmm_viterbi(pi, A, B, seqs, workspace=ws[1]),
+           hmm.hmm_forward_backward(pi, A, B, lab, workspace=ws[2])]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    cur = torch.cuda.current_stream()
+    for st in streams:
+        st.wait_stream(cur)
+    with torch.cuda.stream(streams[0]):
+        c0 = hmm.hmm_forward_backward(pi, A, B, lab, workspace=ws[2])
+    with torch.cuda.stream(streams[1]):
+        c1 = hmm.hmm_viterbi(pi, A, B, seqs, workspace=ws[1])
+    with torch.cuda.stream(streams[2]):
+        c2 = hmm.hmm_forward(pi, A, B, seqs, workspace=ws[0])
+    for st in streams:
+        cur.wait_stream(st)
+    torch.cuda.synchronize()
+    for got, ref in ((c2, ser[0]), (c1, ser[1]), (c0, ser[2])):
+        for a, b in zip(got, ref):
+            if a is not None:
+                assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("name", ["batched", "gradient"])
 def test_full_size_sampled_and_invariants(name):
     """The full configuration in the launch shape the bench uses; the oracle

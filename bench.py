@@ -448,7 +448,7 @@ def run_gpu(args):
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "timing": "CUDA-graph replay of the whole step" if graph is not None
                        else "eager step", "parallelism": f"replicas x{world}",
-                       "lanes_per_pair": {k: v["lanes"] for k, v in tuning.items()}},
+                       "tuning": {k: v["lanes"] for k, v in tuning.items()}},
             "autotune_ms": {k: v["ms"] for k, v in tuning.items()},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -635,7 +635,8 @@ def run_learning(args):
 
     step()
     torch.cuda.synchronize()
-    tuning = {} if mma else tune.autotune(*probs, seqs, lab, ops=[hmm.HMM_OP_FORWARD_BACKWARD],
+    tuning = {} if mma else tune.autotune(*probs, seqs, lab,
+                                          ops=[hmm.HMM_OP_FORWARD_BACKWARD, hmm.HMM_TUNE_FB_RANGES],
                                           cache=None)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -722,7 +723,7 @@ def run_learning(args):
                                "Adam; CUDA graph)", "units_per_step": sumT,
                    "adjoint": "tcgen05 BF16" if mma else "FP32 SIMT",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
-                   "lanes_per_pair": {k: v["lanes"] for k, v in tuning.items()}},
+                   "tuning": {k: v["lanes"] for k, v in tuning.items()}},
         "roofline": {"bound": "tensor" if mma else "alu", "kernel": "adjoint",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "launch_ms": adj_ms,

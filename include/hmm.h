@@ -239,12 +239,20 @@ int hmm_get_device_status(const void* workspace, hmm_stream_t stream, int32_t* s
 /* Autotuner hook: lanes of a warp that cooperate on one (sequence, model)
  * pair, per tunable kernel and padded state count n_pad (4, 8, 16, 32, 64).
  * `op` is HMM_OP_FORWARD, HMM_OP_VITERBI (the score kernel),
- * HMM_OP_FORWARD_BACKWARD or HMM_TUNE_VITERBI_PATHS (the path kernel). The
- * value must be one this build instantiates (hmm_tuning_candidates, whose
- * first entry is the default); 0 restores the default. Process-wide; not
- * thread-safe against concurrent launches. The choice changes only the speed:
- * every candidate computes the same recursion. */
+ * HMM_OP_FORWARD_BACKWARD or HMM_TUNE_VITERBI_PATHS (the path kernel); or
+ * HMM_TUNE_FB_RANGES, whose value is the number of ranges the segments of one
+ * pair are split into by the FP32 SIMT adjoint (1, the default: forward,
+ * recompute and backward in one kernel; more: forward and backward recursions
+ * as independent chains keeping checkpoints of both, then each range of
+ * segments a separate work item with its own count slot -- shorter chains,
+ * for batches of few long sequences that leave the GPU idle; the workspace
+ * grows with the value). The value must be
+ * one this build instantiates (hmm_tuning_candidates, whose first entry is
+ * the default); 0 restores the default. Process-wide; not thread-safe against
+ * concurrent launches. The choice changes only the speed and the rounding
+ * order of the counts: every candidate computes the same recursion. */
 #define HMM_TUNE_VITERBI_PATHS 3
+#define HMM_TUNE_FB_RANGES 4
 int hmm_set_tuning(int32_t op, int32_t n_pad, int32_t lanes_per_pair);
 int hmm_get_tuning(int32_t op, int32_t n_pad, int32_t* lanes_per_pair);
 /* Writes up to cap candidate lane counts for (op, n_pad) into out (HOST

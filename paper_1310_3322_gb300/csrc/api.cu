@@ -65,19 +65,23 @@ static int pad_states(int N) {
   return N <= 512 ? 512 : -1;
 }
 
-// candidate lanes-per-pair, default first; 0 terminates
-static const int kCand[4][5][5] = {
+// candidate lanes-per-pair (ops 0-3) or segment ranges per pair of the SIMT
+// adjoint (op 4, 1 = the single-kernel adjoint), default first; 0 terminates
+constexpr int kTuneOps = 5;
+static const int kCand[kTuneOps][5][5] = {
     /* forward */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
     /* viterbi scores */ {{1, 2, 4, 0}, {1, 2, 4, 8, 0}, {2, 4, 8, 16, 0}, {8, 16, 32, 0}, {32, 0}},
     /* fb      */ {{4, 2, 0}, {8, 4, 0}, {8, 16, 0}, {32, 0}, {32, 0}},
     /* viterbi paths */ {{4, 2, 1, 0}, {8, 4, 2, 0}, {8, 16, 4, 0}, {16, 32, 8, 0}, {32, 0}},
+    /* fb ranges */ {{1, 2, 4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16},
+                     {1, 2, 4, 8, 16}},
 };
-static int g_tuning[4][5] = {{0}};
+static int g_tuning[kTuneOps][5] = {{0}};
 static std::mutex g_tuning_mu;
 
 int candidates(int op, int NP, int* out, int cap) {
   const int ni = np_index(NP);
-  if (op < 0 || op > 3 || ni < 0) return -1;
+  if (op < 0 || op >= kTuneOps || ni < 0) return -1;
   int n = 0;
   for (int i = 0; i < 5 && kCand[op][ni][i]; ++i) {
     if (n < cap && out) out[n] = kCand[op][ni][i];
@@ -88,6 +92,7 @@ int candidates(int op, int NP, int* out, int cap) {
 
 static int lanes_for(int op, int NP) {
   const int ni = np_index(NP);
+  if (ni < 0) return 1;  // no SIMT kernel at this state count
   std::lock_guard<std::mutex> lk(g_tuning_mu);
   const int v = g_tuning[op][ni];
   return v ? v : kCand[op][ni][0];
@@ -155,8 +160,18 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
   if (op == HMM_OP_FORWARD_BACKWARD && !mma) {
     L.slot_floats = (int64_t)NP + (int64_t)NP * NP + (int64_t)NP * d.M;
     L.slots = q.model_of_seq ? (int64_t)S : (int64_t)S * d.K;
-    L.nchunks = first_chunks((int)S);
-    L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
+    // segment ranges: checkpoints of alpha and beta, one slot per range
+    const int C = ckpt_stride(q.max_len);
+    const int NC = (q.max_len > 0 ? (q.max_len - 1) / C : 0) + 1;
+    const int want = lanes_for(HMM_TUNE_FB_RANGES, NP);  // the current tuning
+    L.s_planes = NC < want ? NC : want;
+    L.nchunks = first_chunks((int)(S * L.s_planes));
+    L.s_ckA = off; off = align256(off + (size_t)L.slots * NC * NP * 4);
+    L.s_ckB = off; off = align256(off + (size_t)L.slots * NC * NP * 4);
+    L.s_ckE = off; off = align256(off + (size_t)L.slots * NC * 4);
+    L.s_sig = off; off = align256(off + (size_t)L.slots * 4);
+    L.s_skip = off; off = align256(off + (size_t)L.slots * 4);
+    L.partial = off; off = align256(off + (size_t)(L.slots * L.s_planes * L.slot_floats * 4));
     L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
   }
   if (op == HMM_OP_FORWARD_BACKWARD && mma) {
@@ -442,6 +457,7 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   r.model_of_seq = p.tile_model;  // every slot is one tile of one model
   r.seqlen = p.tile_len;          // -1 marks unused slots
   r.S = cap; r.K = dims.K; r.N = dims.N; r.M = dims.M; r.NP = NP;
+  r.planes = 1;
   r.slot_floats = L.slot_floats;
   r.nchunks = L.nchunks;
   r.cnt_pi = cnt_pi; r.cnt_A = cnt_A; r.cnt_B = cnt_B;
@@ -490,7 +506,7 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
 int hmm_set_tuning(int32_t op, int32_t n_pad, int32_t lanes) {
   g_err[0] = 0;
   const int ni = np_index(n_pad);
-  if (op < 0 || op > 3 || ni < 0) return fail(HMM_ERR_ARG, "bad op %d or n_pad %d", op, n_pad);
+  if (op < 0 || op >= kTuneOps || ni < 0) return fail(HMM_ERR_ARG, "bad op %d or n_pad %d", op, n_pad);
   if (lanes != 0) {
     bool ok = false;
     for (int i = 0; i < 5 && kCand[op][ni][i]; ++i) ok |= kCand[op][ni][i] == lanes;
@@ -504,7 +520,7 @@ int hmm_set_tuning(int32_t op, int32_t n_pad, int32_t lanes) {
 int hmm_get_tuning(int32_t op, int32_t n_pad, int32_t* lanes) {
   g_err[0] = 0;
   const int ni = np_index(n_pad);
-  if (op < 0 || op > 3 || ni < 0 || !lanes) return fail(HMM_ERR_ARG, "bad op, n_pad or pointer");
+  if (op < 0 || op >= kTuneOps || ni < 0 || !lanes) return fail(HMM_ERR_ARG, "bad op, n_pad or pointer");
   if (!kCand[op][ni][0]) return fail(HMM_ERR_UNSUPPORTED, "no kernel for op %d n_pad %d", op, n_pad);
   *lanes = lanes_for(op, n_pad);
   return HMM_OK;
@@ -740,7 +756,13 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
   const int G = lanes_for(HMM_OP_FORWARD_BACKWARD, L.NP);
   const int C = ckpt_stride(seqs->max_len);
   const int NC = (seqs->max_len > 0 ? (seqs->max_len - 1) / C : 0) + 1;
-  const size_t smem = fb_smem_bytes(L.NP, G, C, NC, dims.M, 1);  // one warp per block at least
+  // segment ranges per pair (1 = the single-kernel adjoint)
+  int spar = lanes_for(HMM_TUNE_FB_RANGES, L.NP);
+  if (spar > L.s_planes) spar = L.s_planes;
+  const int spg = (NC + (spar > 0 ? spar : 1) - 1) / (spar > 0 ? spar : 1);
+  if (spar > 1) spar = (NC + spg - 1) / spg;  // no empty ranges
+  const size_t smem = spar > 1 ? fb_seg_smem_bytes(L.NP, G, C, dims.M, 1)
+                               : fb_smem_bytes(L.NP, G, C, NC, dims.M, 1);  // one warp per block
   if (smem > 227 * 1024)
     return fail(HMM_ERR_UNSUPPORTED,
                 "adjoint shared memory %zu bytes above 227 KB (N=%d M=%d max_len=%d)", smem,
@@ -768,19 +790,45 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
   }
   if (e != cudaSuccess) return cuda_fail(e, "setup launch");
 
-  FbLaunch f;
-  f.seq = seq_args(dims, *seqs, L, ws);
-  f.mod = model_args(L, ws);
-  f.weight = weight;
-  f.loglik = loglik;
-  f.partial = at<float>(ws, L.partial);
-  f.slot_floats = L.slot_floats;
-  f.queue = &at<WsHeader>(ws, 0)->queue[2];
-  f.status = &at<WsHeader>(ws, 0)->status;
-  f.n_items = labelled ? ngroups : ngroups * dims.K;
-  f.ckpt = C;
-  f.nck = NC;
-  {
+  const int items = labelled ? ngroups : ngroups * dims.K;
+  if (spar > 1) {
+    FbSegLaunch f;
+    f.seq = seq_args(dims, *seqs, L, ws);
+    f.mod = model_args(L, ws);
+    f.weight = weight;
+    f.loglik = loglik;
+    f.partial = at<float>(ws, L.partial);
+    f.slot_floats = L.slot_floats;
+    f.ckA = at<float>(ws, L.s_ckA);
+    f.ckB = at<float>(ws, L.s_ckB);
+    f.ckE = at<int32_t>(ws, L.s_ckE);
+    f.sig = at<float>(ws, L.s_sig);
+    f.skip = at<int32_t>(ws, L.s_skip);
+    f.queue = &at<WsHeader>(ws, 0)->queue[4];
+    f.status = &at<WsHeader>(ws, 0)->status;
+    f.npairs = (int)L.slots;
+    f.n_items_pass = 2 * items;
+    f.n_items_seg = items * spar;
+    f.ckpt = C;
+    f.nck = NC;
+    f.spar = spar;
+    f.spg = spg;
+    Timed tm(T_FB, st);
+    e = launch_fb_seg(L.NP, G, f, st);
+    tm.stop();
+  } else {
+    FbLaunch f;
+    f.seq = seq_args(dims, *seqs, L, ws);
+    f.mod = model_args(L, ws);
+    f.weight = weight;
+    f.loglik = loglik;
+    f.partial = at<float>(ws, L.partial);
+    f.slot_floats = L.slot_floats;
+    f.queue = &at<WsHeader>(ws, 0)->queue[2];
+    f.status = &at<WsHeader>(ws, 0)->status;
+    f.n_items = items;
+    f.ckpt = C;
+    f.nck = NC;
     Timed tm(T_FB, st);
     e = launch_fb(L.NP, G, f, st);
     tm.stop();
@@ -788,13 +836,14 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
 
   ReduceLaunch r;
-  r.partial = f.partial;
+  r.partial = at<float>(ws, L.partial);
   r.red1 = at<float>(ws, L.red1);
   r.model_of_seq = seqs->model_of_seq;
   r.seqlen = at<int32_t>(ws, L.seqlen);
   r.S = seqs->S; r.K = dims.K; r.N = dims.N; r.M = dims.M; r.NP = L.NP;
+  r.planes = spar > 1 ? spar : 1;
   r.slot_floats = L.slot_floats;
-  r.nchunks = L.nchunks;
+  r.nchunks = first_chunks(seqs->S * r.planes);
   r.cnt_pi = cnt_pi; r.cnt_A = cnt_A; r.cnt_B = cnt_B;
   {
     Timed tm(T_REDUCE, st);

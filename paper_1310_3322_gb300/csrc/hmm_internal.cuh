@@ -38,6 +38,8 @@ struct WsLayout {
   // tensor-core adjoint
   size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf;
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
+  size_t s_ckA, s_ckB, s_ckE, s_sig, s_skip;  // SIMT adjoint with segment ranges
+  int s_planes;        // largest number of ranges per pair the workspace holds
   int64_t m_ckpt_bytes, m_scr_bytes, m_gexp_bytes;
   int m_grid;
 };
@@ -398,6 +400,32 @@ struct FbLaunch {
 cudaError_t launch_fb(int NP, int G, const FbLaunch& a, cudaStream_t st);
 size_t fb_smem_bytes(int NP, int G, int C, int NC, int M, int warps);
 
+// FP32 SIMT adjoint with segment-parallel counts (fb_seg.cu): a pass kernel
+// (forward and backward recursions as independent chains, checkpoints of
+// both) and a segment kernel (one work item per range of segments of a pair).
+struct FbSegLaunch {
+  SeqArgs seq;
+  ModelArgs mod;
+  const float* weight;
+  float* loglik;
+  float* partial;      // [spar][npairs][slot_floats]
+  int64_t slot_floats;
+  float* ckA;          // [npairs][nck][NP] alpha at t = c C (power-of-two scaled)
+  float* ckB;          // [npairs][nck][NP] beta at t = c C (power-of-two scaled)
+  int32_t* ckE;        // [npairs][nck] exponent removed from alpha at t = c C
+  float* sig;          // [npairs] sum of alpha_{T-1}
+  int32_t* skip;       // [npairs] 1: no counts (empty, impossible or invalid, zero weight)
+  int32_t* queue;      // [2] work counters of the two kernels
+  int32_t* status;
+  int npairs;          // S (labelled) or S * K
+  int n_items_pass;    // 2 * pair-group items (forward and backward)
+  int n_items_seg;     // pair-group items * spar
+  int ckpt, nck;       // segment length C, segments of the longest sequence
+  int spar, spg;       // ranges per pair, segments per range
+};
+cudaError_t launch_fb_seg(int NP, int G, const FbSegLaunch& a, cudaStream_t st);
+size_t fb_seg_smem_bytes(int NP, int G, int C, int M, int warps);
+
 struct MmaFwdLaunch {
   SeqArgs seq;
   ModelArgs mod;      // probability tables padded to NP (64 or 128)
@@ -492,11 +520,12 @@ int fb_mma_ctas_per_sm(int NP, int M);
 bool fb_mma_supported(int NP, int M);
 
 struct ReduceLaunch {
-  const float* partial;
+  const float* partial;  // [planes][S (or S * K)][slot_floats]
   float* red1;
   const int32_t* model_of_seq;
   const int32_t* seqlen;
   int S, K, N, M, NP;
+  int planes;
   int64_t slot_floats;
   int nchunks;
   float* cnt_pi;

@@ -682,7 +682,8 @@ __global__ void __launch_bounds__(kReduceTile) reduce1_kernel(ReduceLaunch a, in
   const int k1 = min(a.K, k0 + kReduceModels);
 #pragma unroll
   for (int q = 0; q < kReduceModels; ++q) acc[q][tid] = 0.f;
-  const int s0 = c * chunk, s1 = min(a.S, s0 + chunk);
+  const int Stot = a.S * a.planes;  // slot rows: plane-major, sequence index q % S
+  const int s0 = c * chunk, s1 = min(Stot, s0 + chunk);
   if (e >= a.slot_floats) return;
   constexpr int U = 8;  // independent loads in flight
   if (a.model_of_seq) {
@@ -694,8 +695,8 @@ __global__ void __launch_bounds__(kReduceTile) reduce1_kernel(ReduceLaunch a, in
         const int q = s + u;
         kk[u] = -1;
         v[u] = 0.f;
-        if (q < s1 && a.seqlen[q] >= 0) {
-          const int k = a.model_of_seq[q];
+        if (q < s1 && a.seqlen[q % a.S] >= 0) {
+          const int k = a.model_of_seq[q % a.S];
           if (k >= k0 && k < k1) {
             kk[u] = k - k0;
             v[u] = a.partial[(int64_t)q * a.slot_floats + e];
@@ -708,7 +709,7 @@ __global__ void __launch_bounds__(kReduceTile) reduce1_kernel(ReduceLaunch a, in
     }
   } else {
     for (int s = s0; s < s1; ++s) {
-      if (a.seqlen[s] < 0) continue;
+      if (a.seqlen[s % a.S] < 0) continue;
       const float* row = a.partial + (int64_t)s * a.K * a.slot_floats + e;
       float v[kReduceModels];
 #pragma unroll
@@ -765,7 +766,7 @@ __global__ void reduce2_kernel(ReduceLaunch a) {
 }
 
 cudaError_t launch_reduce(const ReduceLaunch& a, cudaStream_t st) {
-  const int chunk = (a.S + a.nchunks - 1) / a.nchunks;
+  const int chunk = (a.S * a.planes + a.nchunks - 1) / a.nchunks;
   dim3 g1((unsigned)((a.slot_floats + kReduceTile - 1) / kReduceTile), (unsigned)a.nchunks,
           (unsigned)((a.K + kReduceModels - 1) / kReduceModels));
   reduce1_kernel<<<g1, kReduceTile, 0, st>>>(a, chunk);

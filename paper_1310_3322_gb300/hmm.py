@@ -35,6 +35,7 @@ HMM_STATUS_SEQ = 0x4
 HMM_FP32, HMM_BF16_MMA, HMM_TF32_MMA, HMM_AUTO = 0, 1, 2, 3
 HMM_OP_FORWARD, HMM_OP_VITERBI, HMM_OP_FORWARD_BACKWARD = 0, 1, 2
 HMM_TUNE_VITERBI_PATHS = 3
+HMM_TUNE_FB_RANGES = 4
 
 
 class HmmError(RuntimeError):

@@ -1,12 +1,14 @@
-"""Autotuner for the lanes-per-pair choice of each kernel.
+"""Autotuner for the lanes-per-pair choice of each kernel and the number of
+segment ranges per pair of the SIMT adjoint.
 
 For a given batch and model shape it times every instantiated candidate of
-the forward, Viterbi-score, Viterbi-path and adjoint kernels with the
-library's CUDA-event timing, keeps the fastest, installs it with
-hmm_set_tuning, and caches the choice in a JSON file keyed by the GPU name,
-kernel, padded state count, number of models and coarse buckets of the batch
-size and maximum length. Every candidate computes the same recursion, so the
-choice affects only speed.
+the forward, Viterbi-score, Viterbi-path and adjoint kernels (and, for the
+adjoint, every number of segment ranges, timed together with the count
+reduction, whose input grows with it) with the library's CUDA-event timing,
+keeps the fastest, installs it with hmm_set_tuning, and caches the choice in a
+JSON file keyed by the GPU name, kernel, padded state count, number of models
+and coarse buckets of the batch size and maximum length. Every candidate
+computes the same recursion, so the choice affects only speed.
 """
 from __future__ import annotations
 
@@ -19,7 +21,10 @@ from . import hmm
 
 KERNEL_OF = {hmm.HMM_OP_FORWARD: "forward", hmm.HMM_OP_VITERBI: "viterbi_scores",
              hmm.HMM_TUNE_VITERBI_PATHS: "viterbi_paths",
-             hmm.HMM_OP_FORWARD_BACKWARD: "adjoint"}
+             hmm.HMM_OP_FORWARD_BACKWARD: "adjoint",
+             hmm.HMM_TUNE_FB_RANGES: "adjoint_ranges"}
+# timing kinds summed for each tuned op
+TIMED = {hmm.HMM_TUNE_FB_RANGES: ("adjoint", "count_reduce")}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hmmgb_tuning.json")
 
 
@@ -51,7 +56,7 @@ def _run(op, pi, A, B, seqs, labelled, ws):
         hmm.hmm_forward(pi, A, B, seqs, workspace=ws)
     elif op in (hmm.HMM_OP_VITERBI, hmm.HMM_TUNE_VITERBI_PATHS):
         hmm.hmm_viterbi(pi, A, B, seqs, workspace=ws)
-    else:
+    else:  # the adjoint: lanes per pair or segment ranges
         hmm.hmm_forward_backward(pi, A, B, labelled, workspace=ws)
 
 
@@ -63,12 +68,13 @@ def autotune(pi, A, B, seqs, labelled=None, ops=None, repeats: int = 3,
     K, N = int(pi.shape[0]), int(pi.shape[1])
     gpu = torch.cuda.get_device_name(pi.device)
     ops = ops or [hmm.HMM_OP_FORWARD, hmm.HMM_OP_VITERBI, hmm.HMM_TUNE_VITERBI_PATHS,
-                  hmm.HMM_OP_FORWARD_BACKWARD]
+                  hmm.HMM_OP_FORWARD_BACKWARD, hmm.HMM_TUNE_FB_RANGES]
     table = _load(cache) if cache else {}
     ws = hmm.Workspace(pi.device)
     out = {}
     for op in ops:
-        if op == hmm.HMM_OP_FORWARD_BACKWARD and (labelled is None or N > hmm.hmm_max_states(op)):
+        if op in (hmm.HMM_OP_FORWARD_BACKWARD, hmm.HMM_TUNE_FB_RANGES) and (
+                labelled is None or N > hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD)):
             continue
         np_ = n_pad(N)
         cands = hmm.hmm_tuning_candidates(op, np_)
@@ -89,9 +95,9 @@ def autotune(pi, A, B, seqs, labelled=None, ops=None, repeats: int = 3,
             for _ in range(repeats):
                 _run(op, pi, A, B, seqs, labelled, ws)
             torch.cuda.synchronize()
-            t = hmm.hmm_timing_read()[KERNEL_OF[op]]
+            tr = hmm.hmm_timing_read()
             hmm.hmm_timing_enable(False)
-            times[g] = t[1] / max(t[0], 1)
+            times[g] = sum(tr[kd][1] / max(tr[kd][0], 1) for kd in TIMED.get(op, (KERNEL_OF[op],)))
         best = min(times, key=times.get)
         hmm.hmm_set_tuning(op, np_, best)
         table[k] = {"lanes": best, "ms": {str(g): v for g, v in times.items()}}

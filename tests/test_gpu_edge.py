@@ -309,3 +309,29 @@ def test_full_size_sampled_and_invariants(name):
         assert cA[k].sum() == pytest.approx((w.lengths[sel] - 1).sum(), rel=1e-4)
         assert cB[k].sum() == pytest.approx(w.lengths[sel].sum(), rel=1e-4)
     np.testing.assert_allclose(fll.cpu().numpy(), ll[np.arange(w.S), w.labels], rtol=1e-6)
+
+
+def test_autotuner_installs_candidates_and_keeps_results():
+    """The autotuner times every candidate (lanes per pair of each kernel and
+    the adjoint's segment ranges) on a batch, installs valid choices, and
+    the outputs under its choices match those under the defaults."""
+    import torch
+    from paper_1310_3322_gb300 import tune
+    w = synth.make_workload("batched", n_seqs=256, lengths=("uniform", 10, 200))
+    seqs, pi, A, B = to_gpu(w)
+    lab = seqs.labelled(torch.from_numpy(w.labels).cuda())
+    ref_ll = hmm.hmm_forward(pi, A, B, seqs)[0]
+    ref_fb = hmm.hmm_forward_backward(pi, A, B, lab)
+    try:
+        out = tune.autotune(pi, A, B, seqs, lab, repeats=1, cache=None)
+        assert set(out) == {"forward", "viterbi_scores", "viterbi_paths", "adjoint",
+                            "adjoint_ranges"}
+        for op, name in tune.KERNEL_OF.items():
+            assert out[name]["lanes"] in hmm.hmm_tuning_candidates(op, 16)
+            assert hmm.hmm_get_tuning(op, 16) == out[name]["lanes"]
+        torch.testing.assert_close(hmm.hmm_forward(pi, A, B, seqs)[0], ref_ll, rtol=0, atol=1e-4)
+        for a, b in zip(hmm.hmm_forward_backward(pi, A, B, lab), ref_fb):
+            torch.testing.assert_close(a, b, rtol=1e-4, atol=1e-4)
+    finally:
+        for op in tune.KERNEL_OF:
+            hmm.hmm_set_tuning(op, 16, 0)

@@ -41,7 +41,7 @@ def _npad(N):
 @pytest.fixture(autouse=True)
 def _reset_tuning():
     yield
-    for op in (0, 1, 2, 3):
+    for op in (0, 1, 2, 3, hmm.HMM_TUNE_FB_RANGES):
         for n in (4, 8, 16, 32, 64):
             hmm.hmm_set_tuning(op, n, 0)
 
@@ -132,10 +132,15 @@ def test_forward_backward_labelled(case):
     wt = torch.from_numpy(wts).cuda()
     rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
                                                   w.labels, wts.astype(np.float64), nthreads=8)
-    for G in hmm.hmm_tuning_candidates(hmm.HMM_OP_FORWARD_BACKWARD, _npad(w.N)):
+    gs = hmm.hmm_tuning_candidates(hmm.HMM_OP_FORWARD_BACKWARD, _npad(w.N))
+    rs = hmm.hmm_tuning_candidates(hmm.HMM_TUNE_FB_RANGES, _npad(w.N))
+    # every lanes-per-pair choice, and every number of segment ranges per pair
+    # (1: the single-kernel adjoint)
+    for G, R in [(g, rs[0]) for g in gs] + [(gs[0], r) for r in rs[1:]]:
         hmm.hmm_set_tuning(hmm.HMM_OP_FORWARD_BACKWARD, _npad(w.N), G)
+        hmm.hmm_set_tuning(hmm.HMM_TUNE_FB_RANGES, _npad(w.N), R)
         ll, cpi, cA, cB = hmm.hmm_forward_backward(pi, A, B, seqs, weight=wt)
-        assert np.all(np.abs(ll.cpu().numpy() - rll) <= ll_tol(w.lengths)), f"G={G}"
+        assert np.all(np.abs(ll.cpu().numpy() - rll) <= ll_tol(w.lengths)), f"G={G} R={R}"
         _check_counts((cpi, cA, cB), (rpi, rA, rB))
         # the logit gradient built from the counts
         g = hmm.hmm_softmax_grad(pi, A, B, cpi, cA, cB)
@@ -152,12 +157,15 @@ def test_forward_backward_all_models_weighted(case):
     wts = np.random.default_rng(4).uniform(-1.0, 1.0, size=(w.S, w.K)).astype(np.float32)
     rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
                                                   None, wts.astype(np.float64), nthreads=8)
-    ll, cpi, cA, cB = hmm.hmm_forward_backward(pi, A, B, seqs, weight=torch.from_numpy(wts).cuda())
-    assert np.all(np.abs(ll.cpu().numpy() - rll) <= ll_tol(w.lengths)[:, None])
-    # signed weights: compare against the scale of the unsigned totals
-    for g, r in zip((cpi, cA, cB), (rpi, rA, rB)):
-        g = g.cpu().numpy()
-        assert np.abs(g - r).max() <= COUNT_RTOL * max(1.0, np.abs(r).max()) * 10
+    for R in hmm.hmm_tuning_candidates(hmm.HMM_TUNE_FB_RANGES, _npad(w.N)):
+        hmm.hmm_set_tuning(hmm.HMM_TUNE_FB_RANGES, _npad(w.N), R)
+        ll, cpi, cA, cB = hmm.hmm_forward_backward(pi, A, B, seqs,
+                                                   weight=torch.from_numpy(wts).cuda())
+        assert np.all(np.abs(ll.cpu().numpy() - rll) <= ll_tol(w.lengths)[:, None])
+        # signed weights: compare against the scale of the unsigned totals
+        for g, r in zip((cpi, cA, cB), (rpi, rA, rB)):
+            g = g.cpu().numpy()
+            assert np.abs(g - r).max() <= COUNT_RTOL * max(1.0, np.abs(r).max()) * 10, R
 
 
 def test_deterministic_repeat():

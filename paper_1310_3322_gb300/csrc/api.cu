@@ -186,6 +186,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.m_keys = off; off = align256(off + 2 * (size_t)std::max<int64_t>(S, cap) * 4);
     L.m_tiles = off; off = align256(off + ((size_t)cap * 6 + (size_t)d.K * 2) * 4);
     L.m_ntiles = off; off = align256(off + 4);
+    L.m_pscr = off; off = align256(off + mma_plan_scratch_bytes((int64_t)S));
     L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
     L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
     const int grid = fb_mma_grid(d, NP);
@@ -415,6 +416,12 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   p.group_start = tiles + 6 * cap; p.group_end = p.group_start + dims.K;
   p.n_tiles_cap = cap;
   p.n_tiles = at<int32_t>(ws, L.m_ntiles);
+  {
+    const int nb = (int)((seqs->S + 4095) / 4096 > 0 ? (seqs->S + 4095) / 4096 : 1);
+    p.bcnt = at<int32_t>(ws, L.m_pscr);
+    p.hist = p.bcnt + nb;
+    p.n_valid = p.hist + 256 * nb;
+  }
   {
     Timed tm(T_SETUP, st);
     e = launch_setup(s, st);

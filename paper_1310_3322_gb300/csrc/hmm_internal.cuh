@@ -36,7 +36,7 @@ struct WsLayout {
   int64_t slot_floats; // floats per slot (NP + NP*NP + NP*M)
   int nchunks;         // first-level reduction chunks
   // tensor-core adjoint
-  size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf;
+  size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf, m_pscr;
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
   size_t s_ckA, s_ckB, s_ckE, s_sig, s_skip;  // SIMT adjoint with segment ranges
   int s_planes;        // largest number of ranges per pair the workspace holds
@@ -479,7 +479,15 @@ struct MmaPlanArgs {
   int32_t* group_end;           // [K] ... and one past its last
   int n_tiles_cap;
   int32_t* n_tiles;             // device count
+  int32_t* bcnt;                // [ceil(S / 4096)] valid rows per block, then offsets
+  int32_t* hist;                // [256][ceil(S / 4096)] digit counts, then offsets
+  int32_t* n_valid;             // device count of rows with T >= 1
 };
+// Plan scratch bytes for S sequences (bcnt, hist, n_valid).
+inline size_t mma_plan_scratch_bytes(int64_t S) {
+  const int64_t nb = (S + 4095) / 4096 > 0 ? (S + 4095) / 4096 : 1;
+  return (size_t)(nb + 256 * nb + 8) * 4;
+}
 cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st);
 
 struct MmaFbLaunch {

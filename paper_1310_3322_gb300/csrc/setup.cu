@@ -233,94 +233,106 @@ __device__ __forceinline__ void zero_wh(SortSmem& m) {
   p[1] = make_int4(0, 0, 0, 0);
 }
 
+// Ranks the chunk of 4096 pairs starting at c0 (digit = (key >> shift) & 255)
+// and writes it out stably: digit d's pairs go to m.base[d] onwards, in input
+// order. m.wh must be zero on entry; it is zero again on return.
+__device__ void scatter_chunk(const int32_t* in_i, const uint32_t* in_k, int32_t* out_i,
+                              uint32_t* out_k, int n, int c0, int shift, SortSmem& m) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int cn = min(kSortChunk, n - c0);
+  uint32_t key[kSortIpt];
+  int item[kSortIpt], dv[kSortIpt], off[kSortIpt];
+#pragma unroll
+  for (int u = 0; u < kSortIpt; ++u) {
+    const int i = c0 + warp * (32 * kSortIpt) + u * 32 + lane;
+    key[u] = i < n ? __ldcg(in_k + i) : 0u;
+    item[u] = i < n ? __ldcg(in_i + i) : 0;
+    dv[u] = i < n ? (int)((key[u] >> shift) & 255u) : 256;
+  }
+  // ranks within the warp, in index order (slot by slot)
+#pragma unroll
+  for (int u = 0; u < kSortIpt; ++u) {
+    const bool valid = dv[u] < 256;
+    const unsigned peers = digit_peers(dv[u] & 255, valid);
+    const int cur = valid ? m.wh[dv[u] * 32 + warp] : 0;
+    off[u] = cur + __popc(peers & lt);
+    __syncwarp();
+    if (valid && (peers & lt) == 0) m.wh[dv[u] * 32 + warp] = cur + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  scan_warp_counts(m);
+  __syncthreads();
+  if (warp == 0) warp_scan256(m.tot, m.lstart);
+  __syncthreads();
+  // the chunk in digit order in shared memory
+#pragma unroll
+  for (int u = 0; u < kSortIpt; ++u)
+    if (dv[u] < 256) {
+      const int lp = m.lstart[dv[u]] + m.wh[dv[u] * 32 + warp] + off[u];
+      m.st_item[lp] = item[u];
+      m.st_key[lp] = key[u];
+    }
+  __syncthreads();
+  // ... and out in runs: local position j of digit d goes to base[d] + j - lstart[d]
+  for (int j = tid; j < cn; j += kPlanThreads) {
+    const uint32_t k = m.st_key[j];
+    const int d = (int)((k >> shift) & 255u);
+    const int pos = m.base[d] + j - m.lstart[d];
+    out_i[pos] = m.st_item[j];
+    out_k[pos] = k;
+  }
+  __syncthreads();
+  zero_wh(m);
+  __syncthreads();
+}
+
+// The digit counts of the chunk at c0 into m.tot (m.wh zero on entry and return).
+__device__ void chunk_histogram(const uint32_t* in_k, int n, int c0, int shift, SortSmem& m) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int dv[kSortIpt];
+#pragma unroll
+  for (int u = 0; u < kSortIpt; ++u) {
+    const int i = c0 + warp * (32 * kSortIpt) + u * 32 + lane;
+    dv[u] = i < n ? (int)((__ldcg(in_k + i) >> shift) & 255u) : 256;
+  }
+#pragma unroll
+  for (int u = 0; u < kSortIpt; ++u) {
+    const bool valid = dv[u] < 256;
+    const unsigned peers = digit_peers(dv[u] & 255, valid);
+    if (valid && (peers & lt) == 0) m.wh[dv[u] * 32 + warp] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  scan_warp_counts(m);  // tot[d] = the chunk's count of digit d
+  __syncthreads();
+  zero_wh(m);
+  __syncthreads();
+}
+
+// One stable counting-sort pass in one block (the tile order of the plan).
 __device__ void stable_pass(const int32_t* in_i, const uint32_t* in_k, int32_t* out_i,
                             uint32_t* out_k, int n, int shift, SortSmem& m) {
   static_assert(kPlanThreads == 1024, "one thread per (digit, quarter of the warps)");
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  // digit histogram: per-warp counts (each warp owns its column of wh)
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid < 256) m.base[tid] = 0;
+  __syncthreads();
   for (int c0 = 0; c0 < n; c0 += kSortChunk) {
-    int dv[kSortIpt];
-#pragma unroll
-    for (int u = 0; u < kSortIpt; ++u) {
-      const int i = c0 + warp * (32 * kSortIpt) + u * 32 + lane;
-      dv[u] = i < n ? (int)((__ldcg(in_k + i) >> shift) & 255u) : 256;
-    }
-#pragma unroll
-    for (int u = 0; u < kSortIpt; ++u) {
-      const bool valid = dv[u] < 256;
-      const unsigned peers = digit_peers(dv[u] & 255, valid);
-      if (valid && (peers & lt) == 0) m.wh[dv[u] * 32 + warp] += __popc(peers);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  scan_warp_counts(m);  // tot[d] = the digit's total
-  __syncthreads();
-  if (warp == 0) warp_scan256(m.tot, m.base);
-  zero_wh(m);
-  __syncthreads();
-  // scatter, chunk by chunk
-  uint32_t kn[kSortIpt];
-  int in_[kSortIpt];
-#pragma unroll
-  for (int u = 0; u < kSortIpt; ++u) {
-    const int i = warp * (32 * kSortIpt) + u * 32 + lane;
-    kn[u] = i < n ? __ldcg(in_k + i) : 0u;
-    in_[u] = i < n ? __ldcg(in_i + i) : 0;
-  }
-  for (int c0 = 0; c0 < n; c0 += kSortChunk) {
-    const int cn = min(kSortChunk, n - c0);
-    uint32_t key[kSortIpt];
-    int item[kSortIpt], dv[kSortIpt], off[kSortIpt];
-#pragma unroll
-    for (int u = 0; u < kSortIpt; ++u) {
-      key[u] = kn[u];
-      item[u] = in_[u];
-      const int i = c0 + warp * (32 * kSortIpt) + u * 32 + lane;
-      dv[u] = i < n ? (int)((key[u] >> shift) & 255u) : 256;
-      const int inext = i + kSortChunk;  // the next chunk, in flight
-      if (inext < n) {
-        kn[u] = __ldcg(in_k + inext);
-        in_[u] = __ldcg(in_i + inext);
-      }
-    }
-    // ranks within the warp, in index order (slot by slot)
-#pragma unroll
-    for (int u = 0; u < kSortIpt; ++u) {
-      const bool valid = dv[u] < 256;
-      const unsigned peers = digit_peers(dv[u] & 255, valid);
-      const int cur = valid ? m.wh[dv[u] * 32 + warp] : 0;
-      off[u] = cur + __popc(peers & lt);
-      __syncwarp();
-      if (valid && (peers & lt) == 0) m.wh[dv[u] * 32 + warp] = cur + __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    scan_warp_counts(m);
-    __syncthreads();
-    if (warp == 0) warp_scan256(m.tot, m.lstart);
-    __syncthreads();
-    // the chunk in digit order in shared memory
-#pragma unroll
-    for (int u = 0; u < kSortIpt; ++u)
-      if (dv[u] < 256) {
-        const int lp = m.lstart[dv[u]] + m.wh[dv[u] * 32 + warp] + off[u];
-        m.st_item[lp] = item[u];
-        m.st_key[lp] = key[u];
-      }
-    __syncthreads();
-    // ... and out in runs: local position j of digit d goes to base[d] + j - lstart[d]
-    for (int j = tid; j < cn; j += kPlanThreads) {
-      const uint32_t k = m.st_key[j];
-      const int d = (int)((k >> shift) & 255u);
-      const int pos = m.base[d] + j - m.lstart[d];
-      out_i[pos] = m.st_item[j];
-      out_k[pos] = k;
-    }
-    __syncthreads();
+    chunk_histogram(in_k, n, c0, shift, m);
     if (tid < 256) m.base[tid] += m.tot[tid];
-    zero_wh(m);
+    __syncthreads();
+  }
+  if (warp == 0) {  // digit totals -> exclusive digit starts
+    warp_scan256(m.base, m.lstart);
+    __syncwarp();
+    for (int d = threadIdx.x; d < 256; d += 32) m.base[d] = m.lstart[d];
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += kSortChunk) {
+    scatter_chunk(in_i, in_k, out_i, out_k, n, c0, shift, m);
+    if (tid < 256) m.base[tid] += m.tot[tid];
     __syncthreads();
   }
 }
@@ -344,70 +356,120 @@ __device__ void tile_lengths(const MmaPlanArgs& a, int n_tiles) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
+// Plan stage 1 (one block per 4 * kPlanThreads rows): rows with T >= 1 are
+// counted per block; the other rows get their log-likelihood here.
+__global__ void __launch_bounds__(kPlanThreads) plan_count_kernel(MmaPlanArgs a) {
+  __shared__ int itmp[32];
+  __shared__ int total;
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * 4 * kPlanThreads;
+  int cnt = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int s = c0 + 4 * tid + u;
+    const int T = s < a.S ? a.seqlen[s] : 0;
+    const bool keep = s < a.S && T >= 1;
+    cnt += keep ? 1 : 0;
+    if (s < a.S && !keep) {
+      const float v = T == 0 ? 0.f : __int_as_float(0x7fc00000);
+      if (a.labelled) a.loglik[s] = v;
+      else
+        for (int k = 0; k < a.K; ++k) a.loglik[(size_t)s * a.K + k] = v;
+    }
+  }
+  block_exclusive_scan<int>(cnt, itmp, &total);
+  if (tid == 0) a.bcnt[blockIdx.x] = total;
+}
+
+// Exclusive prefix of `n` counts in place (one block); the total to *sum.
+__global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(int32_t* v, int n, int32_t* sum) {
+  __shared__ int itmp[32];
+  __shared__ int total;
+  int carry = 0;
+  for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
+    const int i = c0 + threadIdx.x;
+    const int x = i < n ? v[i] : 0;
+    const int ex = block_exclusive_scan<int>(x, itmp, &total);
+    if (i < n) v[i] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sum) *sum = carry;
+}
+
+// Plan stage 2: every block writes its valid rows, in index order, with their
+// sort keys (model << 10 | length key) at its offset.
+__global__ void __launch_bounds__(kPlanThreads) plan_rows_kernel(MmaPlanArgs a) {
+  __shared__ int itmp[32];
+  __shared__ int total;
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * 4 * kPlanThreads;
+  int keep[4], cnt = 0;
+  uint32_t key[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int s = c0 + 4 * tid + u;
+    const int T = s < a.S ? a.seqlen[s] : 0;
+    keep[u] = (s < a.S && T >= 1) ? 1 : 0;
+    key[u] = keep[u] ? (((a.labelled ? (uint32_t)a.model_of_seq[s] : 0u) << 10) |
+                        (uint32_t)len_key(T))
+                     : 0u;
+    cnt += keep[u];
+  }
+  int pos = a.bcnt[blockIdx.x] + block_exclusive_scan<int>(cnt, itmp, &total);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (keep[u]) {
+      a.sorted[pos] = c0 + 4 * tid + u;
+      a.key[pos] = key[u];
+      ++pos;
+    }
+}
+
+// One pass of the stable LSD sort over many blocks, a 4096-pair chunk each:
+// per-chunk digit counts (digit-major [256][chunks]) ...
+__global__ void __launch_bounds__(kPlanThreads) plan_hist_kernel(const uint32_t* in_k,
+                                                                 const int32_t* n_valid,
+                                                                 int shift, int32_t* hist,
+                                                                 int nchunks) {
+  extern __shared__ __align__(16) uint8_t plan_smem[];
+  SortSmem& m = *reinterpret_cast<SortSmem*>(plan_smem);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 32 * 256; i += kPlanThreads) m.wh[i] = 0;
+  __syncthreads();
+  const int n = *n_valid;
+  const int c0 = blockIdx.x * kSortChunk;
+  if (c0 < n) chunk_histogram(in_k, n, c0, shift, m);
+  if (tid < 256) hist[(size_t)tid * nchunks + blockIdx.x] = c0 < n ? m.tot[tid] : 0;
+}
+
+// ... and, after their exclusive prefix, every chunk written out stably.
+__global__ void __launch_bounds__(kPlanThreads) plan_scatter_kernel(
+    const int32_t* in_i, const uint32_t* in_k, int32_t* out_i, uint32_t* out_k,
+    const int32_t* n_valid, int shift, const int32_t* off, int nchunks) {
+  extern __shared__ __align__(16) uint8_t plan_smem[];
+  SortSmem& m = *reinterpret_cast<SortSmem*>(plan_smem);
+  const int tid = threadIdx.x;
+  const int n = *n_valid;
+  const int c0 = blockIdx.x * kSortChunk;
+  if (c0 >= n) return;
+  for (int i = tid; i < 32 * 256; i += kPlanThreads) m.wh[i] = 0;
+  if (tid < 256) m.base[tid] = off[(size_t)tid * nchunks + blockIdx.x];
+  __syncthreads();
+  scatter_chunk(in_i, in_k, out_i, out_k, n, c0, shift, m);
+}
+
+// Plan stage 3 (one block): tiles of at most 128 rows of one model, their
+// lengths, and the longest-first tile order.
+__global__ void __launch_bounds__(kPlanThreads) plan_tiles_kernel(MmaPlanArgs a) {
   extern __shared__ __align__(16) uint8_t plan_smem[];
   SortSmem& m = *reinterpret_cast<SortSmem*>(plan_smem);
   __shared__ int itmp[32];
   __shared__ int total;
   const int tid = threadIdx.x;
   for (int i = tid; i < 32 * 256; i += kPlanThreads) m.wh[i] = 0;
-
-  // rows with T >= 1, in index order (4 consecutive sequences per thread),
-  // with their sort keys (model << 10 | length key); the other rows get their
-  // log-likelihood here
-  int n = 0;
-  for (int c0 = 0; c0 < a.S; c0 += 4 * kPlanThreads) {
-    int keep[4], cnt = 0;
-    uint32_t key[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int s = c0 + 4 * tid + u;
-      const int T = s < a.S ? a.seqlen[s] : 0;
-      keep[u] = (s < a.S && T >= 1) ? 1 : 0;
-      key[u] = 0;
-      if (keep[u])
-        key[u] = ((a.labelled ? (uint32_t)a.model_of_seq[s] : 0u) << 10) | (uint32_t)len_key(T);
-      cnt += keep[u];
-      if (s < a.S && !keep[u]) {
-        const float v = T == 0 ? 0.f : __int_as_float(0x7fc00000);
-        if (a.labelled) a.loglik[s] = v;
-        else
-          for (int k = 0; k < a.K; ++k) a.loglik[(size_t)s * a.K + k] = v;
-      }
-    }
-    int pos = n + block_exclusive_scan<int>(cnt, itmp, &total);
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (keep[u]) {
-        a.sorted[pos] = c0 + 4 * tid + u;
-        a.key[pos] = key[u];
-        ++pos;
-      }
-    n += total;
-    __syncthreads();
-  }
-
-  // stable LSD sort on the key: decreasing length within each model, models
-  // in increasing order, input order among equal keys
-  int bits = 10;
-  if (a.labelled)
-    while (bits < 32 && ((a.K - 1) >> (bits - 10)) != 0) ++bits;
-  int32_t* ci = a.sorted;
-  uint32_t* ck = a.key;
-  int32_t* oi = a.tmp;
-  uint32_t* ok = a.key_tmp;
-  for (int shift = 0; shift < bits; shift += 8) {
-    stable_pass(ci, ck, oi, ok, n, shift, m);
-    int32_t* ti = ci; ci = oi; oi = ti;
-    uint32_t* tk = ck; ck = ok; ok = tk;
-  }
-  if (ci != a.sorted) {
-    for (int i = tid; i < n; i += kPlanThreads) {
-      a.sorted[i] = ci[i];
-      a.key[i] = ck[i];
-    }
-    __syncthreads();
-  }
+  __syncthreads();
+  const int n = *a.n_valid;
 
   // tiles of at most 128 rows of one model
   int n_tiles = 0;
@@ -488,10 +550,43 @@ __global__ void __launch_bounds__(kPlanThreads) mma_plan_kernel(MmaPlanArgs a) {
 
 cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st) {
   const int smem = (int)sizeof(SortSmem);
-  cudaError_t e = cudaFuncSetAttribute(mma_plan_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  mma_plan_kernel<<<1, kPlanThreads, smem, st>>>(a);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(plan_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(plan_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(plan_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem)))
+    return e;
+  const int nrb = (a.S + 4 * kPlanThreads - 1) / (4 * kPlanThreads);  // row blocks
+  const int nch = (a.S + kSortChunk - 1) / kSortChunk;                // sort chunks
+  if (nrb < 1 || nch < 1) return cudaErrorInvalidValue;
+  plan_count_kernel<<<nrb, kPlanThreads, 0, st>>>(a);
+  plan_scan_kernel<<<1, kPlanThreads, 0, st>>>(a.bcnt, nrb, a.n_valid);
+  plan_rows_kernel<<<nrb, kPlanThreads, 0, st>>>(a);
+  // key bits: 10 of length, then the model; an even number of 8-bit passes
+  // so the result lands back in (sorted, key)
+  int bits = 10;
+  if (a.labelled)
+    while (bits < 32 && ((a.K - 1) >> (bits - 10)) != 0) ++bits;
+  int passes = (bits + 7) / 8;
+  passes += passes & 1;
+  int32_t* ci = a.sorted;
+  uint32_t* ck = a.key;
+  int32_t* oi = a.tmp;
+  uint32_t* ok = a.key_tmp;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    plan_hist_kernel<<<nch, kPlanThreads, smem, st>>>(ck, a.n_valid, shift, a.hist, nch);
+    plan_scan_kernel<<<1, kPlanThreads, 0, st>>>(a.hist, 256 * nch, nullptr);
+    plan_scatter_kernel<<<nch, kPlanThreads, smem, st>>>(ci, ck, oi, ok, a.n_valid, shift,
+                                                         a.hist, nch);
+    int32_t* ti = ci; ci = oi; oi = ti;
+    uint32_t* tk = ck; ck = ok; ok = tk;
+  }
+  plan_tiles_kernel<<<1, kPlanThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

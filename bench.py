@@ -43,7 +43,9 @@ UNIT = "obs*models/s"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-KERNELS_PER_STEP = 13  # setup x3, softmax, forward, v-scores, v-paths, adjoint, reduce x2, grad, adam x2
+# setup x3, softmax, forward, v-scores, v-paths, adjoint, reduce x2, grad, adam x2
+# (the adjoint is two kernels when its segments are split into ranges)
+KERNELS_PER_STEP = 13
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -254,7 +256,7 @@ def run_gpu(args):
     # run on three streams (fork after the softmax, join before the step ends)
     rec_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
 
-    def step(sq=seqs, lb=lab, concurrent=True):
+    def step(sq=seqs, lb=lab, concurrent=True, copy_out=None):
         cur = torch.cuda.current_stream()
         hmm.hmm_softmax_rows(*lg, out=probs)
         if concurrent:
@@ -262,10 +264,16 @@ def run_gpu(args):
                 x.wait_stream(cur)
         # the longest chain (the adjoint) is launched first
         hmm.hmm_forward_backward(*probs, lb, loglik=fll, counts=cnts, workspace=ws[2])
+        # recognition results go to the host from their own streams, beside the
+        # adjoint (copy_out = pinned host (argmax, path))
         with torch.cuda.stream(rec_streams[0] if concurrent else cur):
             hmm.hmm_viterbi(*probs, sq, score=vs, best_model=vbest, path=vpath, workspace=ws[1])
+            if copy_out is not None:
+                copy_out[1].copy_(vpath, non_blocking=True)
         with torch.cuda.stream(rec_streams[1] if concurrent else cur):
             hmm.hmm_forward(*probs, sq, loglik=ll, argmax=am, workspace=ws[0])
+            if copy_out is not None:
+                copy_out[0].copy_(am, non_blocking=True)
         hmm.hmm_softmax_grad(*probs, *cnts, out=gr)
         if concurrent:  # the next softmax overwrites probs: recognition must be done
             for x in rec_streams:
@@ -406,9 +414,7 @@ def run_gpu(args):
             d_off.copy_(h_off, non_blocking=True)
             d_len.copy_(h_len, non_blocking=True)
             d_lab.copy_(h_lab, non_blocking=True)
-            step(sq2, lb2)
-            o_am.copy_(am, non_blocking=True)
-            o_path.copy_(vpath, non_blocking=True)
+            step(sq2, lb2, copy_out=(o_am, o_path))
             o_nll.copy_(fll.sum().neg().view(1), non_blocking=True)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
@@ -453,7 +459,8 @@ def run_gpu(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "gpu_launches": (KERNELS_PER_STEP + (1 if hmm.hmm_get_tuning(
+                hmm.HMM_TUNE_FB_RANGES, tune.n_pad(N)) > 1 else 0)) * args.steps,
             "clocks": clk,
             "phases": phases,
             "kernel_ms_per_step": step_kernel_ms,

@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of replays")
+    ap.add_argument("--teamwork-calls", default="sets", choices=["sets", "roles"],
+                    help="teamwork recognition as one call per op over per-role model sets, "
+                         "or one call per role on its own stream")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--n-seqs", type=int, default=None, help="smaller batch (profiling only)")
@@ -762,8 +765,10 @@ def run_teamwork(args):
     """Paper-shaped recognition (Sec. 5.7): four roles with one set of six
     action HMMs each (N = 5, M = 64), many short sequences; one step = for
     every role, the forward of its sequences against its six models with the
-    argmax and the Viterbi scores, decoded action and best path, the four
-    roles on four streams of one CUDA graph. Units = sum_s T_s * 6."""
+    argmax and the Viterbi scores, decoded action and best path, in one CUDA
+    graph. ``sets``: one forward and one Viterbi call over all sequences, each
+    scored against its role's model set; ``roles``: one call pair per role, the
+    four roles on four streams. Units = sum_s T_s * 6."""
     import torch
     from paper_1310_3322_gb300 import hmm, synth
 
@@ -779,7 +784,7 @@ def run_teamwork(args):
     pi, A, B = (torch.from_numpy(x).to(dev) for x in (w.pi, w.A, w.B))
     path = torch.empty(max(w.total_obs, 1), dtype=torch.int32, device=dev)
     roles = []
-    for r in range(R):
+    for r in (range(R) if args.teamwork_calls == "roles" else []):
         idx = np.nonzero(w.labels // Kr == r)[0]
         sq = hmm.Sequences(symbols=sym, offsets=torch.from_numpy(w.offsets[idx]).to(dev),
                            lengths=torch.from_numpy(w.lengths[idx]).to(dev),
@@ -791,22 +796,38 @@ def run_teamwork(args):
                           vs=torch.empty((idx.size, Kr), device=dev),
                           vb=torch.empty(idx.size, dtype=torch.int32, device=dev),
                           ws=(hmm.Workspace(dev), hmm.Workspace(dev)),
-                          stream=torch.cuda.Stream(device=dev)))
+                          streams=(torch.cuda.Stream(device=dev),)))
+    if args.teamwork_calls == "sets":
+        sq = hmm.Sequences(symbols=sym, offsets=torch.from_numpy(w.offsets).to(dev),
+                           lengths=torch.from_numpy(w.lengths).to(dev), max_len=w.max_len)
+        base = torch.from_numpy((w.labels // Kr * Kr).astype(np.int32)).to(dev)
+        roles.append(dict(seqs=sq.model_sets(base, Kr), p=(pi, A, B),
+                          ll=torch.empty((w.S, Kr), device=dev),
+                          am=torch.empty(w.S, dtype=torch.int32, device=dev),
+                          vs=torch.empty((w.S, Kr), device=dev),
+                          vb=torch.empty(w.S, dtype=torch.int32, device=dev),
+                          ws=(hmm.Workspace(dev), hmm.Workspace(dev)),
+                          streams=(torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev))))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def role_step(x):
-        hmm.hmm_forward(*x["p"], x["seqs"], loglik=x["ll"], argmax=x["am"], workspace=x["ws"][0])
-        hmm.hmm_viterbi(*x["p"], x["seqs"], score=x["vs"], best_model=x["vb"], path=path,
-                        workspace=x["ws"][1])
-
-    def step():
+    def step(serial=False):
+        # forward and Viterbi of a role (or of the model-set call) on the
+        # role's stream(s): with two, the two ops run side by side; serial =
+        # everything on the current stream (per-kernel timing)
         cur = torch.cuda.current_stream()
         for x in roles:
-            x["stream"].wait_stream(cur)
-            with torch.cuda.stream(x["stream"]):
-                role_step(x)
+            sf, sv = (cur, cur) if serial else (x["streams"][0], x["streams"][-1])
+            for st in x["streams"]:
+                st.wait_stream(cur)
+            with torch.cuda.stream(sf):
+                hmm.hmm_forward(*x["p"], x["seqs"], loglik=x["ll"], argmax=x["am"],
+                                workspace=x["ws"][0])
+            with torch.cuda.stream(sv):
+                hmm.hmm_viterbi(*x["p"], x["seqs"], score=x["vs"], best_model=x["vb"],
+                                path=path, workspace=x["ws"][1])
         for x in roles:
-            cur.wait_stream(x["stream"])
+            for st in x["streams"]:
+                cur.wait_stream(st)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -831,13 +852,14 @@ def run_teamwork(args):
     clk = clocks.stop()
     hmm.hmm_timing_reset()
     hmm.hmm_timing_enable(True)
-    _time_steps(torch, step, args.steps, flush)
+    _time_steps(torch, lambda: step(serial=True), args.steps, flush)
     kt = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     per_launch = {k: v[1] / v[0] for k, v in kt.items() if v[0]}
-    # algorithmic work per launch (one role): 2N^2 + N flop per obs*model
-    # (forward: alpha A, emission; Viterbi scores: the same count in max-plus)
-    flop_launch = (2.0 * N * N + N) * units / R
+    # algorithmic work per launch (one role, or all of them with model sets):
+    # 2N^2 + N flop per obs*model (forward: alpha A, emission; Viterbi scores:
+    # the same count in max-plus)
+    flop_launch = (2.0 * N * N + N) * units / len(roles)
     dom = max(("forward", "viterbi_scores"), key=lambda k: per_launch.get(k, 0.0))
     achieved = flop_launch / (per_launch[dom] / 1e3) / 1e12
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -849,7 +871,11 @@ def run_teamwork(args):
         "data": "synthetic",
         "config": {"workload": f"teamwork {R} roles x {Kr} actions, N={N} M={M} S={w.S} "
                                "T~U{20..120} (per role: forward of its models + argmax, "
-                               "Viterbi scores + decoded action + path; 4 streams, CUDA graph)",
+                               "Viterbi scores + decoded action + path; "
+                               + ("one call per op over per-role model sets, forward and "
+                                  "Viterbi on two streams"
+                                  if args.teamwork_calls == "sets" else "one call per role, "
+                                  "4 streams") + ", CUDA graph)",
                    "units_per_step": units,
                    "l2": "flushed between steps (256 MB write outside the timed events)"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,

@@ -101,6 +101,14 @@ typedef struct {
   int32_t max_len;             /* host: upper bound on every lengths[s]; sizes
                                   the adjoint's checkpoint buffers */
   int64_t total_obs;           /* host: number of elements of symbols */
+  /* Model sets (one HMM set per role, Sec. 5.7), used when model_of_seq is
+   * NULL and model_base is not: sequence s is scored against models
+   * [model_base[s], model_base[s] + model_span) only, and every per-model
+   * output ([S][K] above) becomes [S][model_span] with indices relative to
+   * the set. FP32 forward and Viterbi only; zero-initialised fields (NULL, 0)
+   * mean "every model". */
+  const int32_t* model_base;   /* device [S], model_base[s] + model_span <= K */
+  int32_t model_span;          /* host: models per set, 1 .. K */
 } hmm_seqs_t;
 
 /* Workspace bytes that `op` needs for these dimensions and sequences (host

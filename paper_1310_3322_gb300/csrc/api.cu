@@ -233,7 +233,18 @@ static int check_seqs(const hmm_seqs_t* q, const hmm_dims_t& d) {
     if (q->total_obs > 0 && (!q->symbols || !al(q->symbols, 4)))
       return fail(HMM_ERR_ARG, "symbols NULL or misaligned");
   }
+  if (q->model_base) {
+    if (q->model_of_seq) return fail(HMM_ERR_ARG, "model_of_seq and model_base both set");
+    if (q->model_span < 1 || q->model_span > d.K)
+      return fail(HMM_ERR_ARG, "model_span %d outside [1, K=%d]", q->model_span, d.K);
+    if (!al(q->model_base, 4)) return fail(HMM_ERR_ARG, "misaligned model_base");
+  }
   return HMM_OK;
+}
+
+// Models each sequence is scored against in all-models mode.
+static int span_of(const hmm_seqs_t& q, const hmm_dims_t& d) {
+  return q.model_base ? q.model_span : d.K;
 }
 
 static int check_params(const float* pi, const float* A, const float* B) {
@@ -266,6 +277,7 @@ static SetupArgs setup_args(const hmm_dims_t& d, const hmm_seqs_t& q, const WsLa
   s.log_mode = log_mode;
   s.pi = pi; s.A = A; s.B = B;
   s.lengths = q.lengths; s.offsets = q.offsets; s.model_of_seq = q.model_of_seq;
+  s.model_base = q.model_base; s.span = span_of(q, d);
   s.pip = at<float>(ws, L.pip); s.Ap = at<float>(ws, L.Ap); s.Btp = at<float>(ws, L.Btp);
   s.seqlen = at<int32_t>(ws, L.seqlen);
   s.order = at<int32_t>(ws, L.order);
@@ -279,6 +291,8 @@ static SeqArgs seq_args(const hmm_dims_t& d, const hmm_seqs_t& q, const WsLayout
   a.symbols = q.symbols;
   a.offsets = q.offsets;
   a.model_of_seq = q.model_of_seq;
+  a.model_base = q.model_base;
+  a.span = span_of(q, d);
   a.seqlen = at<int32_t>(ws, L.seqlen);
   a.order = at<int32_t>(ws, L.order);
   a.S = q.S; a.K = d.K; a.M = d.M;
@@ -557,10 +571,10 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
   const bool mma = use_mma_forward(dims, precision);
   if (mma && dims.N <= 32)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core forward needs N > 32 (N=%d: use HMM_FP32)", dims.N);
-  if (mma && !all)
+  if (mma && (!all || seqs->model_base))
     return fail(HMM_ERR_UNSUPPORTED,
                 "tensor-core forward scores every sequence against every model "
-                "(model_of_seq must be NULL)");
+                "(model_of_seq and model_base must be NULL)");
   if (seqs->S == 0) return HMM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e;
@@ -648,7 +662,7 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
   f.done = at<int32_t>(ws, L.done);
   f.queue = &at<WsHeader>(ws, 0)->queue[0];
   f.status = &at<WsHeader>(ws, 0)->status;
-  f.n_items = all ? ngroups * dims.K : ngroups;
+  f.n_items = all ? ngroups * span_of(*seqs, dims) : ngroups;
   {
     Timed tm(T_FORWARD, st);
     e = launch_forward(L.NP, G, f, st);
@@ -707,7 +721,7 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
   v.status = &at<WsHeader>(ws, 0)->status;
   v.bpoff = at<int64_t>(ws, L.bpoff);
   v.bp = at<uint8_t>(ws, L.bp);
-  v.n_items_score = all ? ngroups * dims.K : ngroups;
+  v.n_items_score = all ? ngroups * span_of(*seqs, dims) : ngroups;
   v.n_items_path = (seqs->S + PPp - 1) / PPp;
   auto scores = [&]() {
     Timed tm(T_VSCORES, st);
@@ -753,6 +767,8 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
     return fail(HMM_ERR_ARG, "count outputs NULL or misaligned");
   if (seqs->S > 0 && (!loglik || !al(loglik, 4))) return fail(HMM_ERR_ARG, "loglik NULL or misaligned");
   if (weight && !al(weight, 4)) return fail(HMM_ERR_ARG, "weight misaligned");
+  if (seqs->model_base)
+    return fail(HMM_ERR_UNSUPPORTED, "model sets apply to recognition; the adjoint takes model_of_seq");
   if (use_mma_fb(dims, precision)) {
     if (dims.N <= 32)
       return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint needs N > 32 (N=%d: use HMM_FP32)", dims.N);

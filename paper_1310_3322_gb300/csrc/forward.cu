@@ -38,20 +38,23 @@ hmm_forward_simt(FwdLaunch a) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = lane / G, r = lane % G, j0 = r * J;
-  const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
+  const int M = a.seq.M, S = a.seq.S;
+  const int span = a.seq.span;  // models per sequence in all-models mode
 
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(a.queue, 1);
     item = __shfl_sync(HMM_FULL_MASK, item, 0);
     if (item >= a.n_items) break;
-    const int g = ALL ? item / K : item;
-    int k = ALL ? item % K : 0;
+    const int g = ALL ? item / span : item;
+    const int kr = ALL ? item % span : 0;  // model index within the sequence's set
+    int k = kr;
     const int pos = g * PP + p;
     const bool has = pos < S;
     const int s = has ? a.seq.order[pos] : 0;
     int T = has ? a.seq.seqlen[s] : 0;
     if (!ALL && has && T >= 0) k = a.seq.model_of_seq[s];
+    if (ALL && has && T >= 0 && a.seq.model_base) k += a.seq.model_base[s];
     const bool bad_seq = T < 0;
     const int Tn = bad_seq ? 0 : T;
     const int Tmax = __reduce_max_sync(HMM_FULL_MASK, Tn);
@@ -153,7 +156,7 @@ hmm_forward_simt(FwdLaunch a) {
       } else {
         out = (float)(log((double)fs) + (double)E * 0.69314718055994530942);
       }
-      a.loglik[ALL ? (size_t)s * K + k : (size_t)s] = out;
+      a.loglik[ALL ? (size_t)s * span + kr : (size_t)s] = out;
     }
 
     if (ALL && a.argmax) {
@@ -161,16 +164,16 @@ hmm_forward_simt(FwdLaunch a) {
       int last = 0;
       if (lane == 0) {
         __threadfence();
-        last = atomicAdd(a.done + g, 1) == K - 1;
+        last = atomicAdd(a.done + g, 1) == span - 1;
       }
       last = __shfl_sync(HMM_FULL_MASK, last, 0);
       if (last) {
         __threadfence();
         if (has && r == 0) {
-          const float* row = a.loglik + (size_t)s * K;
+          const float* row = a.loglik + (size_t)s * span;
           float best = __ldcg(row);
           int arg = isnan(best) ? -1 : 0;
-          for (int kk = 1; kk < K; ++kk) {
+          for (int kk = 1; kk < span; ++kk) {
             const float v = __ldcg(row + kk);
             if (isnan(v)) arg = -1;
             else if (arg >= 0 && v > best) { best = v; arg = kk; }

@@ -51,6 +51,8 @@ struct SeqArgs {
   const int32_t* symbols;
   const int64_t* offsets;
   const int32_t* model_of_seq;  // NULL = all models
+  const int32_t* model_base;    // all-models mode with model sets: first model of s's set
+  int span;                     // models scored per sequence in all-models mode (K or the set size)
   const int32_t* seqlen;        // validated lengths (-1 = invalid pair)
   const int32_t* order;         // sequences sorted by decreasing length
   int S;
@@ -78,6 +80,8 @@ struct SetupArgs {
   const int32_t* lengths;
   const int64_t* offsets;
   const int32_t* model_of_seq;
+  const int32_t* model_base;  // model sets: model_base[s] + span <= K
+  int span;
   float* pip;
   float* Ap;
   float* Btp;

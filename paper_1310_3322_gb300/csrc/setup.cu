@@ -44,6 +44,96 @@ __device__ T block_exclusive_scan(T v, T* tmp, T* total) {
   return r;
 }
 
+__device__ __forceinline__ bool seq_ok(const SetupArgs& a, int s, int T, long long off) {
+  bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
+  if (ok && a.model_of_seq) {
+    const int k = a.model_of_seq[s];
+    ok = k >= 0 && k < a.K;
+  }
+  if (ok && a.model_base) {
+    const int b = a.model_base[s];
+    ok = b >= 0 && b <= a.K - a.span;
+  }
+  return ok;
+}
+
+// The same plan for S <= kPlanRegs * kPlanThreads with every sequence's
+// length held in registers: thread t owns sequences t + i * kPlanThreads, all
+// of its loads are issued together and nothing written is read back. The
+// backpointer offsets (an exclusive prefix of the lengths in index order) are
+// one block scan per row i of kPlanThreads sequences.
+constexpr int kPlanRegs = 16;
+
+__device__ void plan_block_cached(const SetupArgs& a) {
+  __shared__ int hist[kLenBuckets];
+  __shared__ int itmp[32];
+  __shared__ long long ltmp[32];
+  __shared__ long long row_total;
+  const int tid = threadIdx.x;
+  hist[tid] = 0;  // kLenBuckets == kPlanThreads
+  for (int i = tid; i < a.ndone; i += kPlanThreads) a.done[i] = 0;
+  // loads and checks only (no stores in between), so the unrolled loads can
+  // all be in flight together
+  int Ts[kPlanRegs];
+  int bad = 0;
+#pragma unroll
+  for (int i = 0; i < kPlanRegs; ++i) {
+    const int s = tid + i * kPlanThreads;
+    Ts[i] = 0;
+    if (s < a.S) {
+      Ts[i] = a.lengths[s];
+      if (!seq_ok(a, s, Ts[i], a.offsets[s])) { Ts[i] = -1; bad = 1; }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kPlanRegs; ++i) {
+    const int s = tid + i * kPlanThreads;
+    if (s < a.S) {
+      a.seqlen[s] = Ts[i];
+      if (!a.skip_order) atomicAdd(&hist[kLenBuckets - 1 - length_bucket(max(Ts[i], 0))], 1);
+    }
+  }
+  if (bad) set_status(a.status, HMM_STATUS_SEQ);
+  if (!a.skip_order) {
+    __syncthreads();
+    const int start = block_exclusive_scan<int>(hist[tid], itmp, nullptr);
+    hist[tid] = start;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPlanRegs; ++i) {
+      const int s = tid + i * kPlanThreads;
+      if (s < a.S) {
+        const int pos = atomicAdd(&hist[kLenBuckets - 1 - length_bucket(max(Ts[i], 0))], 1);
+        a.order[pos] = s;
+      }
+    }
+  }
+  if (a.want_bpoff) {
+    long long run = 0;  // lengths of every earlier row
+    bool over = false;
+    for (int i = 0; i * kPlanThreads < a.S; ++i) {
+      const int s = tid + i * kPlanThreads;
+      int T = 0;
+#pragma unroll
+      for (int ii = 0; ii < kPlanRegs; ++ii)
+        if (ii == i) T = Ts[ii];
+      const long long v = s < a.S ? max(T, 0) : 0;
+      const long long x = run + block_exclusive_scan<long long>(v, ltmp, &row_total);
+      if (s < a.S) {
+        a.bpoff[s] = x;
+        if (T > 0 && x + T > a.bp_cap_rows) {  // sum of lengths above total_obs
+          a.seqlen[s] = -1;
+          over = true;
+        }
+      }
+      run += row_total;
+      __syncthreads();  // row_total is rewritten by the next scan
+    }
+    if (over) set_status(a.status, HMM_STATUS_SEQ);
+  }
+}
+
 __device__ void plan_block(const SetupArgs& a) {
   __shared__ int hist[kLenBuckets];
   __shared__ int itmp[32];
@@ -55,12 +145,7 @@ __device__ void plan_block(const SetupArgs& a) {
 
   for (int s = tid; s < a.S; s += kPlanThreads) {
     const int T = a.lengths[s];
-    const long long off = a.offsets[s];
-    bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
-    if (ok && a.model_of_seq) {
-      const int k = a.model_of_seq[s];
-      ok = k >= 0 && k < a.K;
-    }
+    const bool ok = seq_ok(a, s, T, a.offsets[s]);
     if (!ok) set_status(a.status, HMM_STATUS_SEQ);
     a.seqlen[s] = ok ? T : -1;
     if (!a.skip_order) atomicAdd(&hist[kLenBuckets - 1 - length_bucket(ok ? T : 0)], 1);
@@ -138,8 +223,12 @@ __device__ void prep_blocks(const SetupArgs& a, int blk, int nblk) {
 }
 
 __global__ void __launch_bounds__(kPlanThreads) setup_kernel(SetupArgs a) {
-  if (blockIdx.x == 0)
-    plan_block(a);
+  if (blockIdx.x == 0) {
+    if (a.S <= kPlanRegs * kPlanThreads)
+      plan_block_cached(a);
+    else
+      plan_block(a);
+  }
   else
     prep_blocks(a, blockIdx.x - 1, gridDim.x - 1);
 }

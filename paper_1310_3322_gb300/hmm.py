@@ -52,7 +52,8 @@ class hmm_seqs_t(ctypes.Structure):
     _fields_ = [("symbols", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
                 ("lengths", ctypes.c_void_p), ("model_of_seq", ctypes.c_void_p),
                 ("S", ctypes.c_int32), ("max_len", ctypes.c_int32),
-                ("total_obs", ctypes.c_int64)]
+                ("total_obs", ctypes.c_int64), ("model_base", ctypes.c_void_p),
+                ("model_span", ctypes.c_int32)]
 
 
 _lib = None
@@ -149,13 +150,17 @@ def _stream(stream=None) -> Optional[int]:
 class Sequences:
     """Ragged batch on the device: ``symbols`` int32 [total_obs], ``offsets``
     int64 [S], ``lengths`` int32 [S], optional ``model_of_seq`` int32 [S];
-    ``max_len`` bounds every length (host value)."""
+    ``max_len`` bounds every length (host value). ``model_base`` int32 [S] with
+    ``model_span`` scores sequence s against models [base[s], base[s] + span)
+    only (one HMM set per role)."""
 
     symbols: object
     offsets: object
     lengths: object
     max_len: int
     model_of_seq: object = None
+    model_base: object = None
+    model_span: int = 0
 
     @property
     def S(self) -> int:
@@ -169,11 +174,22 @@ class Sequences:
         return replace(self, model_of_seq=model_of_seq)
 
     def all_models(self) -> "Sequences":
-        return replace(self, model_of_seq=None)
+        return replace(self, model_of_seq=None, model_base=None, model_span=0)
+
+    def model_sets(self, model_base, span: int) -> "Sequences":
+        """Every sequence against its own set of ``span`` consecutive models."""
+        return replace(self, model_of_seq=None, model_base=model_base, model_span=int(span))
+
+    @property
+    def span(self) -> Optional[int]:
+        """Models each sequence is scored against in all-models mode (None:
+        all K)."""
+        return self.model_span if self.model_base is not None else None
 
     def c(self) -> hmm_seqs_t:
         return hmm_seqs_t(_ptr(self.symbols), _ptr(self.offsets), _ptr(self.lengths),
-                          _ptr(self.model_of_seq), self.S, int(self.max_len), self.total_obs)
+                          _ptr(self.model_of_seq), self.S, int(self.max_len), self.total_obs,
+                          _ptr(self.model_base), int(self.model_span))
 
     @staticmethod
     def from_numpy(symbols, offsets, lengths, model_of_seq=None, device="cuda",
@@ -244,7 +260,7 @@ def hmm_forward(pi, A, B, seqs: Sequences, precision: int = HMM_FP32, want_argma
     """log P(O_s | lambda_k): [S,K] (+ argmax [S]) or [S] when labelled."""
     torch = _torch()
     dims = _dims(pi, B)
-    S, K = seqs.S, dims.K
+    S, K = seqs.S, (seqs.span or dims.K)
     all_models = seqs.model_of_seq is None
     if loglik is None:
         loglik = torch.empty((S, K) if all_models else (S,), dtype=torch.float32, device=pi.device)
@@ -266,7 +282,7 @@ def hmm_forward_static(pi, A, B, seqs: Sequences, precision: int = HMM_FP32, wan
     used instead (see include/hmm.h). Outputs as in hmm_forward."""
     torch = _torch()
     dims = _dims(pi, B)
-    S, K = seqs.S, dims.K
+    S, K = seqs.S, (seqs.span or dims.K)
     all_models = seqs.model_of_seq is None
     if loglik is None:
         loglik = torch.empty((S, K) if all_models else (S,), dtype=torch.float32, device=pi.device)
@@ -284,7 +300,7 @@ def hmm_viterbi(pi, A, B, seqs: Sequences, want_path=True, want_best=True, score
     """(score [S,K] or [S], best_model [S], path [total_obs])."""
     torch = _torch()
     dims = _dims(pi, B)
-    S, K = seqs.S, dims.K
+    S, K = seqs.S, (seqs.span or dims.K)
     all_models = seqs.model_of_seq is None
     if score is None:
         score = torch.empty((S, K) if all_models else (S,), dtype=torch.float32, device=pi.device)

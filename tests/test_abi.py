@@ -182,3 +182,27 @@ def test_last_error_is_thread_local(lib):
     t.start()
     t.join()
     assert seen["msg"] == "" and "pi/A/B" in hmm.hmm_last_error()
+
+
+def test_model_set_argument_errors(lib):
+    d = hmm.hmm_dims_t(6, 4, 8)
+
+    def sets(base=_fake(4), span=3, mos=None):
+        return hmm.hmm_seqs_t(_fake(1), _fake(2), _fake(3), mos, 4, 10, 40, base, span)
+
+    assert _forward(lib, d, sets(span=0)) == hmm.HMM_ERR_ARG
+    assert "model_span" in hmm.hmm_last_error()
+    assert _forward(lib, d, sets(span=7)) == hmm.HMM_ERR_ARG
+    assert _forward(lib, d, sets(base=_fake(4) + 2)) == hmm.HMM_ERR_ARG
+    assert _forward(lib, d, sets(mos=_fake(10))) == hmm.HMM_ERR_ARG
+    assert "both" in hmm.hmm_last_error()
+    # sets are for recognition: the tensor-core forward and the adjoint refuse them
+    wide = hmm.hmm_dims_t(6, 128, 8)
+    assert _forward(lib, wide, sets(), precision=hmm.HMM_BF16_MMA) == hmm.HMM_ERR_UNSUPPORTED
+    assert lib.hmm_forward_backward(d, _fake(5), _fake(6), _fake(7), ctypes.byref(sets()), None,
+                                    hmm.HMM_FP32, _fake(8), _fake(10), _fake(11), _fake(12),
+                                    _fake(9), 1 << 30, None) == hmm.HMM_ERR_UNSUPPORTED
+    # S == 0 with a valid set returns before any CUDA call
+    q0 = sets()
+    q0.S = 0
+    assert _forward(lib, d, q0) == hmm.HMM_OK

@@ -83,7 +83,8 @@ typedef enum {
 typedef enum {
   HMM_OP_FORWARD = 0,
   HMM_OP_VITERBI = 1,
-  HMM_OP_FORWARD_BACKWARD = 2
+  HMM_OP_FORWARD_BACKWARD = 2,
+  HMM_OP_FORWARD_SCAN = 3  /* hmm_forward_scan with the automatic chunk length */
 } hmm_op_t;
 
 typedef struct {
@@ -164,6 +165,32 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
 int hmm_forward_static(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                        const hmm_seqs_t* seqs, hmm_precision_t precision, float* loglik,
                        int32_t* argmax, hmm_stream_t stream);
+
+/* Parallel-in-time forward for few, very long sequences (not in the paper:
+ * an associative-scan reformulation of the same Forward, Sec. 2.7 / Rabiner
+ * eqs. 19-21). alpha_{T-1} = alpha_0 M_1 ... M_{T-1} with the step matrices
+ * M_t = A diag(b(o_t)); the steps 1 .. T-1 of every sequence are cut into
+ * chunks of `chunk` steps whose products are computed independently (row i
+ * of a chunk product is the recursion started from state i, each row with its
+ * own power-of-two exponent), then every pair combines its chunks in order.
+ * Outputs, argmax, model_of_seq / model sets and the device status bits are
+ * those of hmm_forward with HMM_FP32 (N <= 32 here); only the rounding order
+ * differs. It does N times the arithmetic of hmm_forward, in exchange for a
+ * dependency chain of chunk + T / chunk steps instead of T: worth it when a
+ * batch has too few (sequence, model) pairs to fill the GPU.
+ *   chunk  steps per chunk, 1 .. 65536, or 0 = ceil(sqrt(2 max_len)) rounded
+ *          up to a multiple of 16 (the chain-length balance point).
+ * The workspace holds N_pad^2 + N_pad floats per (chunk, model) pair:
+ * hmm_forward_scan_workspace_size() (host only) gives the bytes for a chunk
+ * length; hmm_workspace_size(HMM_OP_FORWARD_SCAN) those of the automatic one.
+ * A batch whose chunks exceed that storage (overlapping sequences whose
+ * lengths sum past total_obs) has the excess sequences marked bad
+ * (HMM_STATUS_SEQ, NaN). */
+int hmm_forward_scan(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                     const hmm_seqs_t* seqs, int32_t chunk, float* loglik, int32_t* argmax,
+                     void* workspace, size_t workspace_bytes, hmm_stream_t stream);
+int hmm_forward_scan_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, int32_t chunk,
+                                    size_t* bytes);
 
 /* Viterbi algorithm (Sec. 2.7 "Viterbi"; Rabiner eqs. 32-35):
  *   score       [S][K] or [S]: max_Q log P(O_s, Q | lambda_k)
@@ -272,9 +299,10 @@ int hmm_tuning_candidates(int32_t op, int32_t n_pad, int32_t* out, int32_t cap);
  * hmm_timing_read() synchronises those events and reports, per kernel kind,
  * the number of launches and their summed duration since the last reset.
  * Kinds: 0 setup, 1 forward, 2 viterbi-scores, 3 viterbi-paths, 4 adjoint,
- * 5 count-reduce, 6 softmax-rows, 7 softmax-grad, 8 adam, 9 mstep. Not for
- * use inside CUDA-graph capture; not thread-safe against concurrent launches. */
-#define HMM_TIMING_KINDS 10
+ * 5 count-reduce, 6 softmax-rows, 7 softmax-grad, 8 adam, 9 mstep,
+ * 10 scan-chunks, 11 scan-combine. Not for use inside CUDA-graph capture; not
+ * thread-safe against concurrent launches. */
+#define HMM_TIMING_KINDS 12
 int hmm_timing_enable(int on);
 int hmm_timing_reset(void);
 int hmm_timing_read(int32_t kind, int64_t* launches, double* total_ms);

@@ -133,7 +133,27 @@ static int fb_mma_grid(const hmm_dims_t& d, int NP) {
   return num_sms() * fb_mma_ctas_per_sm(NP, d.M);
 }
 
-static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma = false) {
+// Steps per chunk of the parallel-in-time forward (0 = automatic).
+static int scan_chunk_len(int chunk, int max_len) {
+  if (chunk > 0) return chunk;
+  int L = (int)ceil(sqrt(2.0 * (max_len > 1 ? max_len : 1)));
+  L = (L + 15) / 16 * 16;
+  return L < kScanMaxChunk ? L : kScanMaxChunk;
+}
+
+// Chunk slots per model slot: enough for every sequence at max_len and for
+// non-overlapping sequences within total_obs, whichever is fewer.
+static int64_t scan_cap(const hmm_seqs_t& q, int L) {
+  const int64_t S = q.S > 0 ? q.S : 0;
+  const int64_t per = q.max_len > 1 ? ((int64_t)q.max_len - 1 + L - 1) / L : 0;
+  const int64_t a1 = S * per;
+  const int64_t a2 = (q.total_obs > 0 ? q.total_obs : 0) / L + S;
+  const int64_t c = a1 < a2 ? a1 : a2;
+  return c > 1 ? c : 1;
+}
+
+static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma = false,
+                            int scan_L = 0) {
   WsLayout L;
   memset(&L, 0, sizeof(L));
   const int NP = pad_states(d.N);
@@ -156,6 +176,13 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
   }
   if (op == HMM_OP_FORWARD && NP >= 256) {
     L.wimg = off; off = align256(off + (size_t)d.K * NP * NP * 2);
+  }
+  if (op == HMM_OP_FORWARD_SCAN) {
+    const int64_t slots = (q.model_of_seq ? 1 : (q.model_base ? q.model_span : d.K));
+    L.sc_cap = scan_cap(q, scan_L);
+    L.sc_coff = off; off = align256(off + (S + 1) * 8);
+    L.sc_P = off; off = align256(off + (size_t)(slots * L.sc_cap) * NP * NP * 4);
+    L.sc_E = off; off = align256(off + (size_t)(slots * L.sc_cap) * NP * 4);
   }
   if (op == HMM_OP_FORWARD_BACKWARD && !mma) {
     L.slot_floats = (int64_t)NP + (int64_t)NP * NP + (int64_t)NP * d.M;
@@ -308,6 +335,7 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
 }
 
 static int max_states(int op, int precision) {
+  if (op == HMM_OP_FORWARD_SCAN) return (precision == HMM_FP32 || precision == HMM_AUTO) ? 32 : 0;
   if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 512;
   if (op == HMM_OP_FORWARD_BACKWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO))
     return 128;
@@ -343,7 +371,10 @@ static bool use_mma_fb(const hmm_dims_t& d, int precision) {
 // ---------------------------------------------------------------------------
 // kernel timing (host-side tracing with CUDA events)
 // ---------------------------------------------------------------------------
-enum { T_SETUP = 0, T_FORWARD, T_VSCORES, T_VPATHS, T_FB, T_REDUCE, T_SOFTMAX, T_SGRAD, T_ADAM, T_MSTEP };
+enum {
+  T_SETUP = 0, T_FORWARD, T_VSCORES, T_VPATHS, T_FB, T_REDUCE, T_SOFTMAX, T_SGRAD, T_ADAM, T_MSTEP,
+  T_SCAN_CHUNKS, T_SCAN_COMBINE
+};
 
 struct EventPair {
   cudaEvent_t a, b;
@@ -500,14 +531,15 @@ extern "C" {
 const char* hmm_last_error(void) { return g_err; }
 
 int hmm_max_states(hmm_op_t op, hmm_precision_t precision) {
-  if (op < HMM_OP_FORWARD || op > HMM_OP_FORWARD_BACKWARD) return fail(HMM_ERR_ARG, "bad op");
+  if (op < HMM_OP_FORWARD || op > HMM_OP_FORWARD_SCAN) return fail(HMM_ERR_ARG, "bad op");
   return max_states(op, precision);
 }
 
 int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, size_t* bytes) {
   g_err[0] = 0;
   if (!bytes) return fail(HMM_ERR_ARG, "bytes is NULL");
-  if (op < HMM_OP_FORWARD || op > HMM_OP_FORWARD_BACKWARD) return fail(HMM_ERR_ARG, "bad op %d", op);
+  if (op < HMM_OP_FORWARD || op > HMM_OP_FORWARD_SCAN) return fail(HMM_ERR_ARG, "bad op %d", op);
+  if (op == HMM_OP_FORWARD_SCAN) return hmm_forward_scan_workspace_size(dims, seqs, 0, bytes);
   int rc = check_dims(dims, max_states(op, HMM_AUTO));
   if (rc) return rc;
   if (!seqs) return fail(HMM_ERR_ARG, "seqs is NULL");
@@ -669,6 +701,84 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     tm.stop();
   }
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return HMM_OK;
+}
+
+int hmm_forward_scan_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, int32_t chunk,
+                                    size_t* bytes) {
+  g_err[0] = 0;
+  if (!bytes) return fail(HMM_ERR_ARG, "bytes is NULL");
+  int rc = check_dims(dims, max_states(HMM_OP_FORWARD_SCAN, HMM_FP32));
+  if (rc) return rc;
+  if (!seqs) return fail(HMM_ERR_ARG, "seqs is NULL");
+  if (seqs->S < 0 || seqs->total_obs < 0 || seqs->max_len < 0)
+    return fail(HMM_ERR_ARG, "negative S, max_len or total_obs");
+  if (chunk < 0 || chunk > kScanMaxChunk)
+    return fail(HMM_ERR_ARG, "chunk %d outside [0, %d]", chunk, kScanMaxChunk);
+  *bytes = make_layout(dims, *seqs, HMM_OP_FORWARD_SCAN, false,
+                       scan_chunk_len(chunk, seqs->max_len)).total;
+  return HMM_OK;
+}
+
+int hmm_forward_scan(hmm_dims_t dims, const float* pi, const float* A, const float* B,
+                     const hmm_seqs_t* seqs, int32_t chunk, float* loglik, int32_t* argmax,
+                     void* ws, size_t ws_bytes, hmm_stream_t stream) {
+  g_err[0] = 0;
+  int rc;
+  if ((rc = check_dims(dims, max_states(HMM_OP_FORWARD_SCAN, HMM_FP32)))) return rc;
+  if ((rc = check_seqs(seqs, dims))) return rc;
+  if ((rc = check_params(pi, A, B))) return rc;
+  if (chunk < 0 || chunk > kScanMaxChunk)
+    return fail(HMM_ERR_ARG, "chunk %d outside [0, %d]", chunk, kScanMaxChunk);
+  if (seqs->S > 0 && (!loglik || !al(loglik, 4))) return fail(HMM_ERR_ARG, "loglik NULL or misaligned");
+  if (argmax && !al(argmax, 4)) return fail(HMM_ERR_ARG, "argmax misaligned");
+  const int Lc = scan_chunk_len(chunk, seqs->max_len);
+  const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_SCAN, false, Lc);
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  if (seqs->S == 0) return HMM_OK;
+  const bool all = seqs->model_of_seq == nullptr;
+  const int span = all ? span_of(*seqs, dims) : 1;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  s.ndone = (all && argmax) ? seqs->S : 0;
+  s.scan_chunk = Lc;
+  s.coff = at<int64_t>(ws, L.sc_coff);
+  s.coff_cap = L.sc_cap;
+  {
+    Timed tm(T_SETUP, st);
+    e = launch_setup(s, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+  ScanLaunch a;
+  a.seq = seq_args(dims, *seqs, L, ws);
+  a.mod = model_args(L, ws);
+  a.coff = at<int64_t>(ws, L.sc_coff);
+  a.P = at<float>(ws, L.sc_P);
+  a.E = at<int32_t>(ws, L.sc_E);
+  a.cap = L.sc_cap;
+  a.L = Lc;
+  a.loglik = loglik;
+  a.argmax = all ? argmax : nullptr;
+  a.done = at<int32_t>(ws, L.done);
+  a.queue = &at<WsHeader>(ws, 0)->queue[0];
+  a.status = &at<WsHeader>(ws, 0)->status;
+  const int rpw = 32 / L.NP;
+  a.n_pair_items = (int)(((int64_t)seqs->S * span + rpw - 1) / rpw);
+  {
+    Timed tm(T_SCAN_CHUNKS, st);
+    e = launch_scan(L.NP, a, L.sc_cap * span, 0, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "scan chunk launch");
+  {
+    Timed tm(T_SCAN_COMBINE, st);
+    e = launch_scan(L.NP, a, L.sc_cap * span, 1, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "scan combine launch");
   return HMM_OK;
 }
 

@@ -38,6 +38,8 @@ struct WsLayout {
   // tensor-core adjoint
   size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf, m_pscr;
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
+  size_t sc_coff, sc_P, sc_E;  // parallel-in-time forward: chunk offsets, products
+  int64_t sc_cap;              // chunk slots per model slot
   size_t s_ckA, s_ckB, s_ckE, s_sig, s_skip;  // SIMT adjoint with segment ranges
   int s_planes;        // largest number of ranges per pair the workspace holds
   int64_t m_ckpt_bytes, m_scr_bytes, m_gexp_bytes;
@@ -90,6 +92,9 @@ struct SetupArgs {
   int32_t* done;
   int64_t* bpoff;
   int64_t bp_cap_rows;   // rows of NP bytes available for backpointers
+  int scan_chunk;        // > 0: chunk offsets of the parallel-in-time forward
+  int64_t* coff;         // [S + 1] exclusive prefix of ceil((T_s - 1) / scan_chunk)
+  int64_t coff_cap;      // chunk slots available (sequences past it are rejected)
   int32_t* status;
 };
 
@@ -428,6 +433,31 @@ struct FbSegLaunch {
   int spar, spg;       // ranges per pair, segments per range
 };
 cudaError_t launch_fb_seg(int NP, int G, const FbSegLaunch& a, cudaStream_t st);
+
+// Parallel-in-time forward (scan.cu): per-chunk products of the step
+// matrices A diag(b(o_t)), then one ordered combine per pair.
+constexpr int kScanDead = -(1 << 30);      // row exponent: the row is all zero
+constexpr int kScanBad = -(1 << 30) - 1;   // row exponent: invalid symbol / overflow
+constexpr int kScanMaxChunk = 1 << 16;     // largest steps per chunk
+struct ScanLaunch {
+  SeqArgs seq;
+  ModelArgs mod;
+  const int64_t* coff;  // [S + 1] first chunk of each sequence, coff[S] = all chunks
+  float* P;             // [span][cap][NP][NP] chunk products, row-normalised
+  int32_t* E;           // [span][cap][NP] base-2 exponent of each row
+  int64_t cap;          // chunk slots per model slot
+  int L;                // steps per chunk
+  float* loglik;
+  int32_t* argmax;
+  int32_t* done;
+  int32_t* queue;       // [0] chunk items, [1] pair items
+  int32_t* status;
+  int n_pair_items;     // warps' worth of pairs in the combine
+};
+// phase 0: chunk products (max_chunks bounds the device's chunk count);
+// phase 1: combine
+cudaError_t launch_scan(int NP, const ScanLaunch& a, int64_t max_chunks, int phase,
+                        cudaStream_t st);
 size_t fb_seg_smem_bytes(int NP, int G, int C, int M, int warps);
 
 struct MmaFwdLaunch {

@@ -44,6 +44,15 @@ __device__ T block_exclusive_scan(T v, T* tmp, T* total) {
   return r;
 }
 
+// Prefix units of a validated length: backpointer rows (kind 0, Viterbi) or
+// chunks of the parallel-in-time forward (kind 1: steps 1 .. T-1 in chunks of
+// scan_chunk).
+__device__ __forceinline__ long long prefix_units(const SetupArgs& a, int T, int kind) {
+  if (T <= 0) return 0;
+  if (kind == 0) return T;
+  return (T - 1 + (long long)a.scan_chunk - 1) / a.scan_chunk;
+}
+
 __device__ __forceinline__ bool seq_ok(const SetupArgs& a, int s, int T, long long off) {
   bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
   if (ok && a.model_of_seq) {
@@ -109,8 +118,11 @@ __device__ void plan_block_cached(const SetupArgs& a) {
       }
     }
   }
-  if (a.want_bpoff) {
-    long long run = 0;  // lengths of every earlier row
+  for (int kind = 0; kind < 2; ++kind) {
+    if (kind == 0 ? !a.want_bpoff : a.scan_chunk <= 0) continue;
+    int64_t* out = kind == 0 ? a.bpoff : a.coff;
+    const long long cap = kind == 0 ? a.bp_cap_rows : a.coff_cap;
+    long long run = 0;  // units of every earlier row
     bool over = false;
     for (int i = 0; i * kPlanThreads < a.S; ++i) {
       const int s = tid + i * kPlanThreads;
@@ -118,11 +130,11 @@ __device__ void plan_block_cached(const SetupArgs& a) {
 #pragma unroll
       for (int ii = 0; ii < kPlanRegs; ++ii)
         if (ii == i) T = Ts[ii];
-      const long long v = s < a.S ? max(T, 0) : 0;
+      const long long v = s < a.S ? prefix_units(a, T, kind) : 0;
       const long long x = run + block_exclusive_scan<long long>(v, ltmp, &row_total);
       if (s < a.S) {
-        a.bpoff[s] = x;
-        if (T > 0 && x + T > a.bp_cap_rows) {  // sum of lengths above total_obs
+        out[s] = x;
+        if (v > 0 && x + v > cap) {  // storage exhausted
           a.seqlen[s] = -1;
           over = true;
         }
@@ -131,6 +143,7 @@ __device__ void plan_block_cached(const SetupArgs& a) {
       __syncthreads();  // row_total is rewritten by the next scan
     }
     if (over) set_status(a.status, HMM_STATUS_SEQ);
+    if (kind == 1 && tid == 0) a.coff[a.S] = run < cap ? run : cap;
   }
 }
 
@@ -165,24 +178,29 @@ __device__ void plan_block(const SetupArgs& a) {
     a.order[pos] = s;
   }
 
-  if (a.want_bpoff) {
+  __shared__ long long total;
+  for (int kind = 0; kind < 2; ++kind) {
+    if (kind == 0 ? !a.want_bpoff : a.scan_chunk <= 0) continue;
+    int64_t* out = kind == 0 ? a.bpoff : a.coff;
+    const long long cap = kind == 0 ? a.bp_cap_rows : a.coff_cap;
     __syncthreads();
     const int chunk = (a.S + kPlanThreads - 1) / kPlanThreads;
     const int b0 = min(a.S, tid * chunk), b1 = min(a.S, b0 + chunk);
     long long local = 0;
-    for (int s = b0; s < b1; ++s) local += max(a.seqlen[s], 0);
-    long long run = block_exclusive_scan<long long>(local, ltmp, nullptr);
+    for (int s = b0; s < b1; ++s) local += prefix_units(a, a.seqlen[s], kind);
+    long long run = block_exclusive_scan<long long>(local, ltmp, &total);
     for (int s = b0; s < b1; ++s) {
-      const int T = a.seqlen[s];
-      a.bpoff[s] = run;
-      if (T > 0) {
-        if (run + T > a.bp_cap_rows) {  // sum of lengths above total_obs
+      const long long v = prefix_units(a, a.seqlen[s], kind);
+      out[s] = run;
+      if (v > 0) {
+        if (run + v > cap) {  // storage exhausted
           a.seqlen[s] = -1;
           set_status(a.status, HMM_STATUS_SEQ);
         }
-        run += T;
+        run += v;
       }
     }
+    if (kind == 1 && tid == 0) a.coff[a.S] = total < cap ? total : cap;
   }
 }
 

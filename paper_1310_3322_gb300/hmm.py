@@ -33,7 +33,7 @@ HMM_STATUS_PARAM = 0x2
 HMM_STATUS_SEQ = 0x4
 
 HMM_FP32, HMM_BF16_MMA, HMM_TF32_MMA, HMM_AUTO = 0, 1, 2, 3
-HMM_OP_FORWARD, HMM_OP_VITERBI, HMM_OP_FORWARD_BACKWARD = 0, 1, 2
+HMM_OP_FORWARD, HMM_OP_VITERBI, HMM_OP_FORWARD_BACKWARD, HMM_OP_FORWARD_SCAN = 0, 1, 2, 3
 HMM_TUNE_VITERBI_PATHS = 3
 HMM_TUNE_FB_RANGES = 4
 
@@ -67,6 +67,10 @@ _SIG = {
                            _VP, _VP, ctypes.c_size_t, _VP]),
     "hmm_forward_static": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _I32,
                                   _VP, _VP, _VP]),
+    "hmm_forward_scan": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _I32, _VP,
+                                _VP, _VP, ctypes.c_size_t, _VP]),
+    "hmm_forward_scan_workspace_size": (_I32, [hmm_dims_t, ctypes.POINTER(hmm_seqs_t), _I32,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
     "hmm_viterbi": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _VP, _VP, _VP,
                            _VP, ctypes.c_size_t, _VP]),
     "hmm_forward_backward": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _VP,
@@ -88,7 +92,8 @@ _SIG = {
 }
 
 TIMING_KINDS = ("setup", "forward", "viterbi_scores", "viterbi_paths", "adjoint",
-                "count_reduce", "softmax_rows", "softmax_grad", "adam", "mstep")
+                "count_reduce", "softmax_rows", "softmax_grad", "adam", "mstep", "scan_chunks",
+                "scan_combine")
 
 
 def lib():
@@ -273,6 +278,36 @@ def hmm_forward(pi, A, B, seqs: Sequences, precision: int = HMM_FP32, want_argma
     _check(lib().hmm_forward(dims, _ptr(pi), _ptr(A), _ptr(B), ctypes.byref(c), precision,
                              _ptr(loglik), _ptr(argmax if all_models else None), _ptr(buf),
                              buf.numel(), _stream(stream)))
+    return loglik, (argmax if all_models else None)
+
+
+def hmm_forward_scan_workspace_size(dims: hmm_dims_t, seqs: Sequences, chunk: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    c = seqs.c()
+    _check(lib().hmm_forward_scan_workspace_size(dims, ctypes.byref(c), int(chunk),
+                                                 ctypes.byref(out)))
+    return int(out.value)
+
+
+def hmm_forward_scan(pi, A, B, seqs: Sequences, chunk: int = 0, want_argmax=True, loglik=None,
+                     argmax=None, workspace: Optional[Workspace] = None, stream=None):
+    """Parallel-in-time forward (chunk products + ordered combine): the
+    outputs of hmm_forward with HMM_FP32, for batches of few long sequences.
+    ``chunk`` = steps per chunk (0: automatic)."""
+    torch = _torch()
+    dims = _dims(pi, B)
+    S, K = seqs.S, (seqs.span or dims.K)
+    all_models = seqs.model_of_seq is None
+    if loglik is None:
+        loglik = torch.empty((S, K) if all_models else (S,), dtype=torch.float32, device=pi.device)
+    if all_models and want_argmax and argmax is None:
+        argmax = torch.empty(S, dtype=torch.int32, device=pi.device)
+    ws = _ws(workspace, pi.device)
+    buf = ws.get(hmm_forward_scan_workspace_size(dims, seqs, chunk))
+    c = seqs.c()
+    _check(lib().hmm_forward_scan(dims, _ptr(pi), _ptr(A), _ptr(B), ctypes.byref(c), int(chunk),
+                                  _ptr(loglik), _ptr(argmax if all_models else None), _ptr(buf),
+                                  buf.numel(), _stream(stream)))
     return loglik, (argmax if all_models else None)
 
 

@@ -28,6 +28,8 @@ configurations:
                                  "batched"; 16384 sequences, T ~ U{20..120};
                                  label = role * 6 + action, role and action
                                  uniform (the application shape of Sec. 5.7)
+  longseq    K=4,  N=32,  M=64   parameters as "batched"; 8 sequences,
+                                 T ~ U{2^19..2^20} (few very long recordings)
 
 Every sequence is sampled from the model of its label. Parameters are stored
 as float32 (what the GPU computes with); the oracle reads the same float32
@@ -41,7 +43,7 @@ from typing import Optional
 import numpy as np
 
 SEEDS = {"plain": 1310001, "batched": 1310002, "gradient": 1310003, "large": 1310004,
-         "training": 1310005, "teamwork": 1310006, "cuhmm": 1310007}
+         "training": 1310005, "teamwork": 1310006, "cuhmm": 1310007, "longseq": 1310008}
 
 SPECS = {
     "plain": dict(K=1, N=4, M=8, S=64, lengths=("fixed", 50), params=("dirichlet", 1.0)),
@@ -57,6 +59,10 @@ SPECS = {
                   params=("dirichlet", 0.3)),
     "teamwork": dict(K=24, N=5, M=64, S=16384, lengths=("uniform", 20, 120),
                      params=("sticky", 0.5, 0.6, 0.9), roles=4),
+    # few very long recordings: too few (sequence, model) pairs to fill the
+    # GPU, the regime of the parallel-in-time forward
+    "longseq": dict(K=4, N=32, M=64, S=8, lengths=("uniform", 1 << 19, 1 << 20),
+                    params=("sticky", 0.5, 0.6, 0.9)),
 }
 
 

@@ -206,3 +206,39 @@ def test_model_set_argument_errors(lib):
     q0 = sets()
     q0.S = 0
     assert _forward(lib, d, q0) == hmm.HMM_OK
+
+
+def test_scan_host_checks(lib):
+    d = hmm.hmm_dims_t(2, 16, 8)
+    q = _seqs(S=4, max_len=10000, total=40000)
+    out = ctypes.c_size_t()
+    sizes = []
+    for chunk in (0, 16, 64, 1024):
+        assert lib.hmm_forward_scan_workspace_size(d, ctypes.byref(q), chunk,
+                                                   ctypes.byref(out)) == 0
+        sizes.append(out.value)
+    # smaller chunks need more chunk-product storage (N_pad^2 + N_pad floats each)
+    assert sizes[1] > sizes[2] > sizes[3]
+    assert sizes[1] >= 2 * (40000 // 16) * (16 * 16 + 16) * 4
+    # the op code takes the automatic chunk
+    assert lib.hmm_workspace_size(d, ctypes.byref(q), hmm.HMM_OP_FORWARD_SCAN,
+                                  ctypes.byref(out)) == 0
+    assert out.value == sizes[0]
+    assert lib.hmm_max_states(hmm.HMM_OP_FORWARD_SCAN, hmm.HMM_FP32) == 32
+    assert lib.hmm_forward_scan_workspace_size(d, ctypes.byref(q), -1,
+                                               ctypes.byref(out)) == hmm.HMM_ERR_ARG
+    assert lib.hmm_forward_scan_workspace_size(d, ctypes.byref(q), 65537,
+                                               ctypes.byref(out)) == hmm.HMM_ERR_ARG
+    assert lib.hmm_forward_scan_workspace_size(hmm.hmm_dims_t(2, 33, 8), ctypes.byref(q), 0,
+                                               ctypes.byref(out)) == hmm.HMM_ERR_UNSUPPORTED
+
+    def scan(dims, seqs, chunk=0, loglik=_fake(8), ws=_fake(9), ws_bytes=1 << 40):
+        return lib.hmm_forward_scan(dims, _fake(5), _fake(6), _fake(7), ctypes.byref(seqs),
+                                    chunk, loglik, None, ws, ws_bytes, None)
+
+    assert scan(d, q, chunk=-3) == hmm.HMM_ERR_ARG
+    assert scan(d, q, loglik=None) == hmm.HMM_ERR_ARG
+    assert scan(hmm.hmm_dims_t(2, 33, 8), q) == hmm.HMM_ERR_UNSUPPORTED
+    assert scan(d, q, ws_bytes=1024) == hmm.HMM_ERR_WORKSPACE
+    assert "need" in hmm.hmm_last_error()
+    assert scan(d, _seqs(S=0)) == hmm.HMM_OK

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of replays")
+    ap.add_argument("--scan-chunk", type=int, default=0,
+                    help="longseq: steps per chunk of the parallel-in-time forward (0 = auto)")
     ap.add_argument("--teamwork-calls", default="sets", choices=["sets", "roles"],
                     help="teamwork recognition as one call per op over per-role model sets, "
                          "or one call per role on its own stream")
@@ -65,7 +67,8 @@ def parse():
     ap.add_argument("--lanes", default=None,
                     help="fixed lanes per pair 'fwd,viterbi,paths,adjoint' instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "large", "gradient", "training", "teamwork", "cuhmm"],
+                    choices=[WORKLOAD, "large", "gradient", "training", "teamwork", "cuhmm",
+                             "longseq"],
                     help="batched: the full step (default); large: tensor-core forward "
                          "and adjoint; gradient/training: the learning step (and a "
                          "Baum-Welch iteration); teamwork: per-role recognition, N=5; "
@@ -955,6 +958,87 @@ def run_wide(args):
     print(json.dumps(line), flush=True)
 
 
+def run_longseq(args):
+    """Few very long sequences (8 x T ~ U{2^19..2^20}, K=4, N=32): every
+    sequence against every model by the parallel-in-time forward (chunk
+    products, then the ordered per-pair combine), with the sequential FP32
+    forward on the same batch timed beside it. Units = sum_s T_s * K."""
+    import torch
+    from paper_1310_3322_gb300 import hmm, synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.make_workload("longseq", n_seqs=args.n_seqs, seed=synth.SEEDS["longseq"] + rank)
+    K, N, M = w.K, w.N, w.M
+    NP = 1 << max(2, (N - 1).bit_length())
+    sumT = int(w.lengths.astype(np.int64).sum())
+    units = sumT * K
+    seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
+    pi, A, B = (torch.from_numpy(x).to(dev) for x in (w.pi, w.A, w.B))
+    ll = torch.empty((w.S, K), device=dev)
+    am = torch.empty(w.S, dtype=torch.int32, device=dev)
+    ws = hmm.Workspace(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        hmm.hmm_forward_scan(pi, A, B, seqs, chunk=args.scan_chunk, loglik=ll, argmax=am,
+                             workspace=ws)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(ws) == 0
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = _time_steps(torch, step, args.steps, flush)
+    clk = clocks.stop()
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, step, args.steps, flush)
+    kt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    kms = {k: v[1] / v[0] for k, v in kt.items() if v[0]}
+    # the sequential recursion on the same batch (one chain of T steps per pair)
+    sl = torch.empty_like(ll)
+    hmm.hmm_forward(pi, A, B, seqs, loglik=sl, argmax=am, workspace=ws)
+    torch.cuda.synchronize()
+    seq_ms = _time_steps(torch, lambda: hmm.hmm_forward(pi, A, B, seqs, loglik=sl, argmax=am,
+                                                        workspace=ws), 2, flush)
+    diff = float((ll - sl).abs().max())
+    # chunk products: 2 NP^3 flop per step and pair (row i of a product is the
+    # recursion started from state i); the sequential recursion does 2 N^2
+    steps = int((np.maximum(w.lengths.astype(np.int64), 1) - 1).sum()) * K
+    achieved = 2.0 * NP ** 3 * steps / (kms["scan_chunks"] / 1e3) / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    L = args.scan_chunk or min(65536, -(-int(np.ceil(np.sqrt(2.0 * w.max_len))) // 16) * 16)
+    line = {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"longseq K={K} N={N} M={M} S={w.S} T~U{{2^19..2^20}} "
+                               f"(parallel-in-time forward, {L} steps per chunk, every "
+                               "sequence against every model + argmax)",
+                   "units_per_step": units, "chunk": L,
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "timing": "eager step, CUDA events"},
+        "roofline": {"bound": "alu", "kernel": "scan_chunks", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "launch_ms": kms["scan_chunks"],
+                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x "
+                                   f"{SM_MAX_MHZ:.0f} MHz", "traffic": None},
+        "kernel_ms": kms,
+        "sequential_forward": {"ms": seq_ms, "value": units / (seq_ms / 1e3),
+                               "max_abs_diff_nats": diff},
+        "clocks": clk,
+        "gpu_launches": 3 * args.steps,  # setup, chunk products, combine
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -973,6 +1057,9 @@ def main():
         return
     if args.workload == "cuhmm":
         run_wide(args)
+        return
+    if args.workload == "longseq":
+        run_longseq(args)
         return
     run_gpu(args)
 

@@ -82,15 +82,19 @@ __device__ __forceinline__ int seq_of_chunk(const int64_t* coff, int S, int64_t 
 // --------------------------------------------------------------------------
 // chunk products
 // --------------------------------------------------------------------------
-template <int NP>
+// R rows of one chunk item per lane (lanes li and rows li, li + NP / R, ...):
+// every A value read from shared memory feeds R * 4 FMAs, and the warp's
+// 32 / (NP / R) items read distinct, bank-disjoint copies of A.
+template <int NP, int R>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 hmm_scan_chunks(ScanLaunch a) {
-  constexpr int RPW = 32 / NP;       // chunk items per warp
+  constexpr int LPI = NP / R;        // lanes per chunk item
+  constexpr int RPW = 32 / LPI;      // chunk items per warp
   constexpr int AS = NP * NP + 4;    // per-item A stride (floats): items on different banks
   __shared__ __align__(16) float As[kWarpsPerBlock][RPW][AS];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane / NP, i = lane % NP;
+  const int sub = lane / LPI, li = lane % LPI;
   const int S = a.seq.S, M = a.seq.M;
   const bool all = a.seq.model_of_seq == nullptr;
   const int64_t CT = __ldcg(a.coff + S);  // chunks of all sequences (written by setup)
@@ -123,9 +127,11 @@ hmm_scan_chunks(ScanLaunch a) {
     const int nT = t1 - t0;  // >= 1 for every real chunk
     const int nTmax = __reduce_max_sync(HMM_FULL_MASK, nT);
 
-    // A of this item's model, row i loaded by lane i
+    // A of this item's model, rows li + r LPI loaded by lane li
     __syncwarp();
-    {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = li + r * LPI;
       float row[NP];
       load_vec<NP>(row, a.mod.Ap + ((size_t)k * NP + i) * NP);
 #pragma unroll
@@ -137,11 +143,16 @@ hmm_scan_chunks(ScanLaunch a) {
 
     const float* Bk = a.mod.Btp + (size_t)k * M * NP;
     const int32_t* o = a.seq.symbols + (has ? a.seq.offsets[s] : 0);
-    float x[NP];
+    float x[R][NP];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) x[j] = (j == i) ? 1.f : 0.f;
-    int E = 0;
-    bool bad = false, dead = false, perr = false;
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) x[r][j] = (j == li + r * LPI) ? 1.f : 0.f;
+    int E[R];
+    bool dead[R], perr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { E[r] = 0; dead[r] = false; perr[r] = false; }
+    bool bad = false;  // an invalid symbol (the same for every row of the item)
 
     // emission row of the first step, symbol of the second
     int on = nT > 0 ? __ldg(o + t0) : 0;
@@ -152,7 +163,7 @@ hmm_scan_chunks(ScanLaunch a) {
     int o2 = nT > 1 ? __ldg(o + t0 + 1) : 0;
 
     for (int u = 0; u < nTmax; ++u) {
-      const bool act = u < nT;
+      const bool act = u < nT && !bad;
       float b[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) b[j] = bn[j];
@@ -162,52 +173,63 @@ hmm_scan_chunks(ScanLaunch a) {
         load_vec<NP>(bn, Bk + (size_t)on * NP);
         if (u + 2 < nT) o2 = __ldg(o + t0 + u + 2);
       }
-      // y = x A: packed FMAs over pairs of columns, A rows broadcast from shared
-      float2 acc[NP / 2];
+      // y = x A: packed FMAs over pairs of columns, each A row of shared
+      // memory applied to the R rows
+      float2 acc[R][NP / 2];
 #pragma unroll
-      for (int q = 0; q < NP / 2; ++q) acc[q] = make_float2(0.f, 0.f);
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < NP / 2; ++q) acc[r][q] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int l = 0; l < NP; ++l) {
-        const float2 xl = make_float2(x[l], x[l]);
 #pragma unroll
         for (int q = 0; q < NP / 4; ++q) {
           const float4 av = *reinterpret_cast<const float4*>(Asub + l * NP + 4 * q);
-          acc[2 * q] = ffma2(xl, make_float2(av.x, av.y), acc[2 * q]);
-          acc[2 * q + 1] = ffma2(xl, make_float2(av.z, av.w), acc[2 * q + 1]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float2 xl = make_float2(x[r][l], x[r][l]);
+            acc[r][2 * q] = ffma2(xl, make_float2(av.x, av.y), acc[r][2 * q]);
+            acc[r][2 * q + 1] = ffma2(xl, make_float2(av.z, av.w), acc[r][2 * q + 1]);
+          }
         }
       }
-      float y[NP];
 #pragma unroll
-      for (int q = 0; q < NP / 2; ++q) {
-        y[2 * q] = acc[q].x * b[2 * q];
-        y[2 * q + 1] = acc[q].y * b[2 * q + 1];
-      }
-      const float m = tree_max<NP>(y);
-      if (act && !dead && !bad) {
-        if (!(m < INFINITY)) {  // finite parameters whose product overflows
-          bad = true;
-          perr = true;
-        } else if (m > 0.f) {
-          int e;
-          split_pow2(m, e);
+      for (int r = 0; r < R; ++r) {
+        float y[NP];
 #pragma unroll
-          for (int j = 0; j < NP; ++j) x[j] = pow2_scale(y[j], e);
-          E += e;
-        } else {
-          dead = true;  // this start state cannot produce the chunk
+        for (int q = 0; q < NP / 2; ++q) {
+          y[2 * q] = acc[r][q].x * b[2 * q];
+          y[2 * q + 1] = acc[r][q].y * b[2 * q + 1];
+        }
+        const float m = tree_max<NP>(y);
+        if (act && !dead[r] && !perr[r]) {
+          if (!(m < INFINITY)) {  // finite parameters whose product overflows
+            perr[r] = true;
+          } else if (m > 0.f) {
+            int e;
+            split_pow2(m, e);
 #pragma unroll
-          for (int j = 0; j < NP; ++j) x[j] = 0.f;
+            for (int j = 0; j < NP; ++j) x[r][j] = pow2_scale(y[j], e);
+            E[r] += e;
+          } else {
+            dead[r] = true;  // this start state cannot produce the chunk
+#pragma unroll
+            for (int j = 0; j < NP; ++j) x[r][j] = 0.f;
+          }
         }
       }
     }
 
     if (has) {
       const int64_t slot = (int64_t)kk * a.cap + g;
-      float* P = a.P + (slot * NP + i) * NP;
-      store_vec<NP>(P, x);
-      a.E[slot * NP + i] = bad ? kScanBad : (dead ? kScanDead : E);
-      if (serr && i == 0) set_status(a.status, HMM_STATUS_SYMBOL);
-      if (perr) set_status(a.status, HMM_STATUS_PARAM);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = li + r * LPI;
+        store_vec<NP>(a.P + (slot * NP + i) * NP, x[r]);
+        a.E[slot * NP + i] = (bad || perr[r]) ? kScanBad : (dead[r] ? kScanDead : E[r]);
+        if (perr[r]) set_status(a.status, HMM_STATUS_PARAM);
+      }
+      if (serr && li == 0) set_status(a.status, HMM_STATUS_SYMBOL);
     }
   }
 }
@@ -370,12 +392,18 @@ static cudaError_t launch_fill(Kern kern, int64_t need_warps, cudaStream_t st, c
   return cudaGetLastError();
 }
 
+// rows per lane of the chunk products: two from 8 states up (fewer shared
+// loads per FMA; at 4 states eight items already share each warp)
+template <int NP>
+constexpr int scan_rows() { return NP >= 8 ? 2 : 1; }
+
 template <int NP>
 static cudaError_t launch_scan_t(const ScanLaunch& a, int64_t max_chunks, cudaStream_t st,
                                  int phase) {
-  constexpr int RPW = 32 / NP;
+  constexpr int R = scan_rows<NP>();
+  constexpr int RPW = 32 / (NP / R);
   if (phase == 0)
-    return launch_fill(hmm_scan_chunks<NP>, (max_chunks + RPW - 1) / RPW, st, a);
+    return launch_fill(hmm_scan_chunks<NP, R>, (max_chunks + RPW - 1) / RPW, st, a);
   if (a.seq.model_of_seq == nullptr)
     return launch_fill(hmm_scan_combine<NP, true>, a.n_pair_items, st, a);
   return launch_fill(hmm_scan_combine<NP, false>, a.n_pair_items, st, a);

@@ -220,6 +220,14 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
  * capped at 16 while T <= 8192); HMM_AUTO chooses the tensor cores above
  * N = 32. Its errors against FP64 are of order the BF16 unit roundoff 2^-8
  * relative per count (|delta log P| <= 2^-7 T).
+ * Above 128 states (N <= 512, the cited cuHMM shape of Sec. 5.6) the
+ * tensor-core forward and backward passes keep every step's rescaled alpha
+ * and beta rows in the workspace (4 K total_obs N_pad floats), and the counts
+ * are formed from them: xi as one fixed-order contraction over all steps.
+ * This path scores every sequence against every model (model_of_seq only
+ * with K = 1) and needs N_pad (M + 1) * 4 bytes <= 227 KB (M <= 112 at 512
+ * padded states); other requests return HMM_ERR_UNSUPPORTED. Same error
+ * bounds.
  * Impossible or invalid pairs contribute no counts. */
 int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                          const hmm_seqs_t* seqs, const float* weight,

@@ -201,7 +201,29 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.partial = off; off = align256(off + (size_t)(L.slots * L.s_planes * L.slot_floats * 4));
     L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
   }
-  if (op == HMM_OP_FORWARD_BACKWARD && mma) {
+  if (op == HMM_OP_FORWARD_BACKWARD && mma && NP >= 256) {
+    // adjoint above 128 states: per-step rows of both passes, count partials
+    const int64_t rtot = q.total_obs > 0 ? q.total_obs : 1;
+    const int64_t slots = d.K;
+    L.w_rtot = rtot;
+    L.bpoff = off; off = align256(off + S * 8);
+    L.wimg = off; off = align256(off + (size_t)d.K * NP * NP * 2);
+    const size_t rowb = (size_t)(slots * rtot) * NP * 4;
+    L.w_X = off; off = align256(off + rowb);
+    L.w_Bh = off; off = align256(off + rowb);
+    L.w_V = off; off = align256(off + rowb);
+    L.w_G = off; off = align256(off + rowb);
+    L.w_xe = off; off = align256(off + (size_t)(slots * rtot) * 4);
+    L.w_sym = off; off = align256(off + (size_t)(slots * rtot) * 4);
+    const int tiles = (NP / 128) * (NP / 128);
+    int ns = (2 * num_sms() + tiles * d.K - 1) / (tiles * d.K);
+    L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
+    int nc = (2 * num_sms() + d.K - 1) / d.K;
+    L.w_nchunks = nc < 1 ? 1 : (nc > 512 ? 512 : nc);
+    L.w_Cp = off; off = align256(off + (size_t)slots * L.w_nsplit * NP * NP * 4);
+    L.w_Ep = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * d.M * 4);
+    L.w_Pp = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * 4);
+  } else if (op == HMM_OP_FORWARD_BACKWARD && mma) {
     // tensor-core adjoint: tile plan, per-tile count slots, per-CTA buffers
     const int cap = fb_mma_tile_cap(d, q);
     const size_t img = (size_t)128 * NP * 2;
@@ -335,6 +357,8 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
 }
 
 static int max_states(int op, int precision) {
+  if (op == HMM_OP_FORWARD_BACKWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO))
+    return 512;
   if (op == HMM_OP_FORWARD_SCAN) return (precision == HMM_FP32 || precision == HMM_AUTO) ? 32 : 0;
   if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 512;
   if (op == HMM_OP_FORWARD_BACKWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO))
@@ -421,6 +445,105 @@ static int zero_counts(const hmm_dims_t& d, float* cnt_pi, float* cnt_A, float* 
       (e = cudaMemsetAsync(cnt_A, 0, n * d.N * 4, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(cnt_B, 0, n * d.M * 4, st)) != cudaSuccess)
     return cuda_fail(e, "memset");
+  return HMM_OK;
+}
+
+// hmm_forward_backward above 128 states (arguments already checked except the
+// workspace): setup, the tensor-core forward and backward passes keeping their
+// per-step rows, then the count kernels of fb_wide.cu.
+static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* weight,
+                   float* loglik, float* cnt_pi, float* cnt_A, float* cnt_B, void* ws,
+                   size_t ws_bytes, hmm_stream_t stream, const float* pi, const float* A,
+                   const float* B) {
+  const bool labelled = seqs->model_of_seq != nullptr;
+  if (labelled && dims.K != 1)
+    return fail(HMM_ERR_UNSUPPORTED,
+                "above 128 states the adjoint scores every sequence against every model "
+                "(model_of_seq only with K = 1)");
+  const int NP = pad_states(dims.N);
+  if (fbw_emis_smem(NP, dims.M) > 227 * 1024)
+    return fail(HMM_ERR_UNSUPPORTED, "adjoint above 128 states: M=%d too large", dims.M);
+  const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD, true);
+  int rc = check_ws(ws, ws_bytes, L);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (seqs->S == 0) return zero_counts(dims, cnt_pi, cnt_A, cnt_B, st);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  s.want_bpoff = 1;
+  s.bpoff = at<int64_t>(ws, L.bpoff);
+  s.bp_cap_rows = L.w_rtot;
+  {
+    Timed tm(T_SETUP, st);
+    e = launch_setup(s, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+  const int n_tiles = (seqs->S + 127) / 128;
+  MmaWideLaunch f;
+  memset(&f, 0, sizeof(f));
+  f.seq = seq_args(dims, *seqs, L, ws);
+  f.mod = model_args(L, ws);
+  f.img = at<uint8_t>(ws, L.wimg);
+  f.loglik = loglik;
+  f.done = at<int32_t>(ws, L.done);
+  f.queue = &at<WsHeader>(ws, 0)->queue[0];
+  f.status = &at<WsHeader>(ws, 0)->status;
+  f.n_tiles = n_tiles;
+  f.n_items = n_tiles * dims.K;
+  f.xs = at<float>(ws, L.w_X);
+  f.roff = at<int64_t>(ws, L.bpoff);
+  f.rtot = L.w_rtot;
+  {
+    Timed tm(T_FORWARD, st);
+    e = launch_forward_wide(NP, f, st, 0);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");
+  f.queue = &at<WsHeader>(ws, 0)->queue[1];
+  f.xs = at<float>(ws, L.w_Bh);
+  f.xe = at<int32_t>(ws, L.w_xe);
+  {
+    Timed tm(T_FB, st);
+    e = launch_forward_wide(NP, f, st, 1);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core backward launch");
+  FbWideArgs c;
+  memset(&c, 0, sizeof(c));
+  c.K = dims.K; c.N = dims.N; c.M = dims.M; c.NP = NP; c.S = seqs->S;
+  c.labelled = labelled ? 1 : 0;
+  c.rtot = L.w_rtot;
+  c.X = at<float>(ws, L.w_X);
+  c.Bh = at<float>(ws, L.w_Bh);
+  c.V = at<float>(ws, L.w_V);
+  c.G = at<float>(ws, L.w_G);
+  c.xe = at<int32_t>(ws, L.w_xe);
+  c.sym = at<int32_t>(ws, L.w_sym);
+  c.roff = at<int64_t>(ws, L.bpoff);
+  c.seqlen = at<int32_t>(ws, L.seqlen);
+  c.offsets = seqs->offsets;
+  c.symbols = seqs->symbols;
+  c.Btp = at<float>(ws, L.Btp);
+  c.weight = weight;
+  c.A = A;
+  c.Cp = at<float>(ws, L.w_Cp);
+  c.nsplit = L.w_nsplit;
+  c.rows_per_split = ((L.w_rtot + L.w_nsplit - 1) / L.w_nsplit + 7) / 8 * 8;
+  c.Ep = at<float>(ws, L.w_Ep);
+  c.Pp = at<float>(ws, L.w_Pp);
+  c.nchunks = L.w_nchunks;
+  c.rows_per_chunk = (L.w_rtot + L.w_nchunks - 1) / L.w_nchunks;
+  c.cnt_pi = cnt_pi;
+  c.cnt_A = cnt_A;
+  c.cnt_B = cnt_B;
+  {
+    Timed tm(T_REDUCE, st);
+    e = launch_fbw_counts(c, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint count launch");
   return HMM_OK;
 }
 
@@ -547,7 +670,10 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
   size_t need = 0;
   if (op != HMM_OP_FORWARD_BACKWARD || dims.N <= 64) need = make_layout(dims, *seqs, op).total;
   if (op == HMM_OP_FORWARD_BACKWARD && dims.N > 32) {
-    if (!fb_mma_supported(pad_states(dims.N), dims.M))
+    if (pad_states(dims.N) >= 256) {
+      if (fbw_emis_smem(pad_states(dims.N), dims.M) > 227 * 1024)
+        return fail(HMM_ERR_UNSUPPORTED, "adjoint above 128 states: M=%d too large", dims.M);
+    } else if (!fb_mma_supported(pad_states(dims.N), dims.M))
       return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports M <= 256 (M=%d)", dims.M);
     const size_t m = make_layout(dims, *seqs, op, true).total;
     if (m > need) need = m;
@@ -622,6 +748,7 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     }
     if (e != cudaSuccess) return cuda_fail(e, "setup launch");
     MmaWideLaunch f;
+    memset(&f, 0, sizeof(f));
     f.seq = seq_args(dims, *seqs, L, ws);
     f.mod = model_args(L, ws);
     f.img = at<uint8_t>(ws, L.wimg);
@@ -882,6 +1009,8 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
   if (use_mma_fb(dims, precision)) {
     if (dims.N <= 32)
       return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint needs N > 32 (N=%d: use HMM_FP32)", dims.N);
+    if (pad_states(dims.N) >= 256)
+      return fb_wide(dims, seqs, weight, loglik, cnt_pi, cnt_A, cnt_B, ws, ws_bytes, stream, pi, A, B);
     return fb_mma(dims, seqs, weight, loglik, cnt_pi, cnt_A, cnt_B, ws, ws_bytes, stream, pi, A, B);
   }
   const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD);

@@ -39,6 +39,9 @@ struct WsLayout {
   size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf, m_pscr;
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
   size_t sc_coff, sc_P, sc_E;  // parallel-in-time forward: chunk offsets, products
+  size_t w_X, w_Bh, w_V, w_G, w_xe, w_sym, w_Cp, w_Ep, w_Pp;  // adjoint above 128 states
+  int w_nsplit, w_nchunks;
+  int64_t w_rtot;
   int64_t sc_cap;              // chunk slots per model slot
   size_t s_ckA, s_ckB, s_ckE, s_sig, s_skip;  // SIMT adjoint with segment ranges
   int s_planes;        // largest number of ranges per pair the workspace holds
@@ -487,8 +490,48 @@ struct MmaWideLaunch {
   int32_t* status;
   int n_items;        // n_tiles * K
   int n_tiles;        // ceil(S / 128)
+  // per-step rows for the adjoint above 128 states (xs NULL: recognition only)
+  float* xs;             // [K][rtot][NP] forward: scaled alpha_t; backward: scaled beta_t
+  int32_t* xe;           // backward: [K][rtot] power of two removed at each step
+  const int64_t* roff;   // [S] first row of each sequence (exclusive prefix of lengths)
+  int64_t rtot;          // rows per model
 };
-cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st);
+// Counts of the adjoint above 128 states from the two passes' rows (fb_wide.cu).
+struct FbWideArgs {
+  int K, N, M, NP, S;
+  int labelled;          // model_of_seq given (K == 1)
+  int64_t rtot;          // rows per model
+  float* X;              // [K][rtot][NP] forward rows, overwritten by U
+  const float* Bh;       // [K][rtot][NP] backward rows
+  float* V;              // [K][rtot][NP]
+  float* G;              // [K][rtot][NP] gamma rows (weighted)
+  const int32_t* xe;     // [K][rtot] backward exponents
+  int32_t* sym;          // [K][rtot] symbol code of each row
+  const int64_t* roff;   // [S]
+  const int32_t* seqlen; // [S] validated lengths
+  const int64_t* offsets;
+  const int32_t* symbols;
+  const float* Btp;      // [K][M][NP] padded emission table
+  const float* weight;   // [S] or [S][K], or NULL
+  const float* A;        // caller's [K][N][N]
+  float* Cp;             // [K][nsplit][NP][NP]
+  int nsplit;
+  int64_t rows_per_split;
+  float* Ep;             // [K][nchunks][NP][M]
+  float* Pp;             // [K][nchunks][NP]
+  int nchunks;
+  int64_t rows_per_chunk;
+  float* cnt_pi;
+  float* cnt_A;
+  float* cnt_B;
+};
+cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st);
+size_t fbw_emis_smem(int NP, int M);
+
+// dir 0: the forward recursion (loglik, argmax); dir 1: the backward
+// recursion in Y_t = b(o_t) o beta_t, i.e. the forward recursion with A^T for
+// A run from t = T-1 down to 0 from Y_{T-1} = b(o_{T-1}) (needs xs).
+cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st, int dir = 0);
 
 // Plan of the tensor-core adjoint: the rows of every 128-row tile share one
 // model, and the tile composition is a deterministic function of the input

@@ -55,8 +55,10 @@ constexpr uint32_t kWideWait = 1u << 24;
 // [32 kc, 32 kc + 32) for every j, element (n = j, k = i) = a_ij at
 //   (j / 8) * 512 + (il / 8) * 128 + (j % 8) * 16 + (il % 8) * 2,  il = i - 32 kc
 // (K-major core matrices of 8 rows x 16 bytes; 512 = 32 K values x 16 bytes).
+// `transpose` builds the image of A instead (element (n = j, k = i) = a_ji),
+// the operand of the backward recursion.
 template <int NP>
-__global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K) {
+__global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K, int transpose) {
   const long long n = (long long)K * NP * NP / 2;  // pairs along i
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -67,12 +69,13 @@ __global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K) {
     const int kc = i / 32, il = i % 32;
     const size_t off = (size_t)k * NP * NP * 2 + (size_t)kc * WideCfg<NP>::CHUNK +
                        (size_t)(j / 8) * 512 + (il / 8) * 128 + (j % 8) * 16 + (il % 8) * 2;
-    *reinterpret_cast<uint32_t*>(img + off) = tc::pack_bf16(Ak[(size_t)i * NP + j],
-                                                            Ak[(size_t)(i + 1) * NP + j]);
+    const float v0 = transpose ? Ak[(size_t)j * NP + i] : Ak[(size_t)i * NP + j];
+    const float v1 = transpose ? Ak[(size_t)j * NP + i + 1] : Ak[(size_t)(i + 1) * NP + j];
+    *reinterpret_cast<uint32_t*>(img + off) = tc::pack_bf16(v0, v1);
   }
 }
 
-template <int NP>
+template <int NP, int DIR>
 __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
   using L = WideCfg<NP>;
   constexpr int COLS = L::COLS, CH = L::CH, NKC = L::NKC, RING = L::RING;
@@ -137,6 +140,11 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
     const float* Bk = a.mod.Btp + (size_t)k * M * NP;
     const uint8_t* img = a.img + (size_t)k * NP * NP * 2;
     const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
+    // step t reads symbol o_t (forward) or o_{T-1-t} (backward)
+    auto tix = [&](int t) { return DIR ? Tn - 1 - t : t; };
+    // this row's per-step output rows (adjoint above 128 states)
+    float* xrow = (a.xs && has && !bad_seq)
+                      ? a.xs + ((size_t)k * a.rtot + (size_t)a.roff[s]) * NP + col0 : nullptr;
     RowState st;
     st.F = 0; st.f = 0; st.dead = false; st.bad = bad_seq; st.written = (Tn == 0);
     st.err = 0; st.ll = 0.f;
@@ -151,9 +159,9 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
       }
     }
 
-    // t = 0: x_0 = pi . b(o_0), no scaling
+    // t = 0: x_0 = pi . b(o_0) (backward: Y_{T-1} = b(o_{T-1}), beta = 1), no scaling
     {
-      int o0 = Tn > 0 ? __ldg(o) : 0;
+      int o0 = Tn > 0 ? __ldg(o + tix(0)) : 0;
       if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
       const bool live = Tn > 0 && !st.bad;
       const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)o0 * NP + col0);
@@ -164,9 +172,16 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
         float y[32];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float4 bb = __ldg(b4 + 8 * c + q), pp = __ldg(p4 + 8 * c + q);
+          const float4 bb = __ldg(b4 + 8 * c + q);
+          const float4 pp = DIR ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(p4 + 8 * c + q);
           y[4 * q] = live ? pp.x * bb.x : 0.f; y[4 * q + 1] = live ? pp.y * bb.y : 0.f;
           y[4 * q + 2] = live ? pp.z * bb.z : 0.f; y[4 * q + 3] = live ? pp.w * bb.w : 0.f;
+          if (xrow && Tn > 0) {
+            const float4 sv = DIR ? make_float4(live ? 1.f : 0.f, live ? 1.f : 0.f,
+                                                live ? 1.f : 0.f, live ? 1.f : 0.f)
+                                  : make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+            *reinterpret_cast<float4*>(xrow + (size_t)tix(0) * NP + 32 * c + 4 * q) = sv;
+          }
         }
         part += tree_sum<32>(y);
         uint32_t w[16];
@@ -177,9 +192,10 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
               make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
       }
       psum[h * 128 + row] = part;
+      if (DIR && xrow && Tn > 0 && h == 0) a.xe[(size_t)k * a.rtot + a.roff[s] + tix(0)] = 0;
     }
-    int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
-    int o_next2 = (2 < Tn) ? __ldg(o + 2) : 0;
+    int o_next = (1 < Tn) ? __ldg(o + tix(1)) : 0;
+    int o_next2 = (2 < Tn) ? __ldg(o + tix(2)) : 0;
 
     bool aborted = false;
     int g = 0;  // chunk counter of this item
@@ -225,7 +241,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
       close_step(st, psum[row] + psum[128 + row] + psum[256 + row] + psum[384 + row], t - 1, Tn);
       const int ot = o_next;
       o_next = o_next2;
-      if (t + 2 < Tn) o_next2 = __ldg(o + t + 2);
+      if (t + 2 < Tn) o_next2 = __ldg(o + tix(t + 2));
       if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
       const bool live = t < Tn && !st.dead && !st.bad;
       if (live) st.F += st.f;
@@ -255,13 +271,25 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
         tc::tmem_ld32(d_mine + (uint32_t)(c * 32), y);
         tc::tmem_ld_wait();
         float2 acc = make_float2(0.f, 0.f);
+        float* xdst = (xrow && t < Tn) ? xrow + (size_t)tix(t) * NP + 32 * c : nullptr;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          float2 lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
-                                            make_float2(bq[q].x, bq[q].y)), fac2);
-          float2 hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
-                                            make_float2(bq[q].z, bq[q].w)), fac2);
-          if (!live) { lo = make_float2(0.f, 0.f); hi = lo; }
+          float2 lo, hi;
+          if constexpr (DIR == 0) {
+            lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
+                                       make_float2(bq[q].x, bq[q].y)), fac2);
+            hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
+                                       make_float2(bq[q].z, bq[q].w)), fac2);
+            if (!live) { lo = make_float2(0.f, 0.f); hi = lo; }
+            if (xdst) *reinterpret_cast<float4*>(xdst + 4 * q) = make_float4(lo.x, lo.y, hi.x, hi.y);
+          } else {  // beta_t = D 2^-f kept, Y_t = beta_t o b(o_t) is the next operand
+            float2 plo = __fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]), fac2);
+            float2 phi = __fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]), fac2);
+            if (!live) { plo = make_float2(0.f, 0.f); phi = plo; }
+            if (xdst) *reinterpret_cast<float4*>(xdst + 4 * q) = make_float4(plo.x, plo.y, phi.x, phi.y);
+            lo = __fmul2_rn(plo, make_float2(bq[q].x, bq[q].y));
+            hi = __fmul2_rn(phi, make_float2(bq[q].z, bq[q].w));
+          }
           acc = __fadd2_rn(acc, __fadd2_rn(lo, hi));
           y[4 * q] = lo.x; y[4 * q + 1] = lo.y; y[4 * q + 2] = hi.x; y[4 * q + 3] = hi.y;
         }
@@ -277,6 +305,8 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
           for (int q = 0; q < 8; ++q) bq[q] = bn[q];
       }
       psum[h * 128 + row] = part;
+      if (DIR && xrow && t < Tn && h == 0)
+        a.xe[(size_t)k * a.rtot + a.roff[s] + tix(t)] = live ? st.f : 0;
     }
     if (tid == 0 && !abort_issue) {  // the last chunk's commit (its MMAs are done by now)
       for (int i = 0; i < RING; ++i)
@@ -294,7 +324,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
       misc[2] = 1;
       set_status(a.status, HMM_STATUS_TIMEOUT);
     }
-    if (has && h == 0) {
+    if (DIR == 0 && has && h == 0) {
       float out = st.ll;
       if (st.bad || aborted) out = __int_as_float(0x7fc00000);
       else if (st.dead) out = -INFINITY;
@@ -303,7 +333,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
       a.loglik[(size_t)s * K + k] = out;
     }
     // recognition: the last model of a tile takes the argmax over models
-    if (a.argmax) {
+    if (DIR == 0 && a.argmax) {
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -343,16 +373,16 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
 }
 
 template <int NP>
-static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st) {
+static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st, int dir) {
   using L = WideCfg<NP>;
   {
     const long long n = (long long)a.seq.K * NP * NP / 2;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    wide_image_kernel<NP><<<blocks, 256, 0, st>>>(a.mod.Ap, a.img, a.seq.K);
+    wide_image_kernel<NP><<<blocks, 256, 0, st>>>(a.mod.Ap, a.img, a.seq.K, dir);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  auto kern = hmm_forward_wide<NP>;
+  auto kern = dir ? hmm_forward_wide<NP, 1> : hmm_forward_wide<NP, 0>;
   const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;  // one CTA per SM
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
@@ -362,9 +392,10 @@ static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st) {
-  if (NP == 256) return launch_wide_t<256>(a, st);
-  if (NP == 512) return launch_wide_t<512>(a, st);
+cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st, int dir) {
+  if (dir && !a.xs) return cudaErrorInvalidValue;
+  if (NP == 256) return launch_wide_t<256>(a, st, dir);
+  if (NP == 512) return launch_wide_t<512>(a, st, dir);
   return cudaErrorInvalidValue;
 }
 

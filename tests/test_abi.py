@@ -70,7 +70,14 @@ def test_workspace_size_is_host_only_and_monotone(lib):
                                   ctypes.byref(out)) == 0
     # per-tile count slots and per-CTA checkpoint buffers
     assert out.value >= (100 // 128 + 1 + 4) * 128 * (1 + 128 + 256) * 4
+    # above 128 states: per-step rows of both passes (4 buffers of K * total_obs * N_pad)
     assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 129, 8), ctypes.byref(q),
+                                  hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) == 0
+    assert out.value >= 4 * 4 * q.total_obs * 256 * 4
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(1, 300, 200), ctypes.byref(q),
+                                  hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
+        == hmm.HMM_ERR_UNSUPPORTED
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(1, 513, 8), ctypes.byref(q),
                                   hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
         == hmm.HMM_ERR_UNSUPPORTED
     assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 65, 300), ctypes.byref(q),
@@ -163,7 +170,7 @@ def test_tuning_table(lib):
     assert hmm.hmm_get_tuning(hmm.HMM_OP_FORWARD, 16) == 2
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD) == 64
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD) == 64
-    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD, hmm.HMM_BF16_MMA) == 128
+    assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD_BACKWARD, hmm.HMM_BF16_MMA) == 512
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD, hmm.HMM_BF16_MMA) == 512
     assert hmm.hmm_max_states(hmm.HMM_OP_FORWARD, hmm.HMM_TF32_MMA) == 128
     assert hmm.hmm_max_states(hmm.HMM_OP_VITERBI, hmm.HMM_BF16_MMA) == 0

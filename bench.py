@@ -936,6 +936,31 @@ def run_wide(args):
     peak, basis = measured_peak_bf16()
     n_tiles = (w.S + 127) // 128
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    # one Baum-Welch iteration of the same shape (Sec. 5.6 quotes forward and
+    # Baum-Welch): tensor-core forward + backward passes keeping their rows,
+    # count contraction, M-step (in place on copies of the parameters)
+    bw_pi, bw_A, bw_B = pi.clone(), A.clone(), B.clone()
+    cnt = (torch.empty_like(pi), torch.empty_like(A), torch.empty_like(B))
+    bll = torch.empty((w.S, K), device=dev)
+    wsb = hmm.Workspace(dev)
+
+    def bw_step():
+        hmm.hmm_forward_backward(bw_pi, bw_A, bw_B, seqs, precision=hmm.HMM_BF16_MMA, loglik=bll,
+                                 counts=cnt, workspace=wsb)
+        hmm.hmm_mstep(bw_pi, bw_A, bw_B, *cnt, out=(bw_pi, bw_A, bw_B))
+
+    bw_step()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(wsb) == 0
+    ll0 = float(bll.sum())
+    bw_ms = _time_steps(torch, bw_step, max(2, args.steps // 2), flush)
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, bw_step, 2, flush)
+    bkt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    bkms = {k2: v[1] / v[0] for k2, v in bkt.items() if v[0]}
+    ll1 = float(bll.sum())
     line = {
         "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -952,6 +977,10 @@ def run_wide(args):
                      "frac_of_busy_sms": achieved / (peak * min(n_tiles * K, sm_count) / sm_count),
                      "traffic": None},
         "kernel_ms": kms,
+        "baum_welch": {"ms_per_iteration": bw_ms, "value": units / (bw_ms / 1e3), "unit": UNIT,
+                       "kernel_ms": bkms, "loglik_sum_first_last": [ll0, ll1],
+                       "note": "forward + backward passes (BF16 tcgen05) keeping per-step "
+                               "rows, count contraction, M-step"},
         "clocks": clk,
         "gpu_launches": 3 * args.steps,  # setup, A^T image, forward
     }

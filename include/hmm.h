@@ -133,7 +133,11 @@ int hmm_max_states(hmm_op_t op, hmm_precision_t precision);
  * and FP32 accumulation, |delta log P| <= 2 u T against FP64. Above 128
  * states (the cited cuHMM kernel's 512-state workload, Sec. 5.6) one CTA
  * holds one 128-sequence tile and streams A^T from a BF16 image the call
- * builds in the workspace. HMM_AUTO: tensor cores (BF16) above N = 64. */
+ * builds in the workspace. HMM_AUTO: tensor cores (BF16) above N = 64; for
+ * N <= 32 and a batch of few long sequences (max_len >= 4096, pairs * N_pad^3
+ * <= 2^21) the parallel-in-time forward of hmm_forward_scan, when the
+ * workspace holds its chunk products (hmm_workspace_size(HMM_OP_FORWARD)
+ * counts them for such batches); FP32 SIMT otherwise. */
 int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                 const hmm_seqs_t* seqs, hmm_precision_t precision, float* loglik,
                 int32_t* argmax, void* workspace, size_t workspace_bytes, hmm_stream_t stream);

@@ -25,6 +25,15 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma,
+                            int scan_L);
+// Workspace of hmm_forward without HMM_AUTO's parallel-in-time variant (the
+// static entry point's scratch is sized for this; hmm_forward falls back to
+// the sequential recursion when the scan's storage does not fit).
+size_t forward_ws_sequential(const hmm_dims_t& d, const hmm_seqs_t& q) {
+  return make_layout(d, q, HMM_OP_FORWARD, false, 0).total;
+}
+
 // Records an error message for hmm_last_error() (used by entry points that
 // live in other translation units).
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -150,6 +159,18 @@ static int64_t scan_cap(const hmm_seqs_t& q, int L) {
   const int64_t a2 = (q.total_obs > 0 ? q.total_obs : 0) / L + S;
   const int64_t c = a1 < a2 ? a1 : a2;
   return c > 1 ? c : 1;
+}
+
+// HMM_AUTO's choice of the parallel-in-time forward: a batch whose pairs
+// leave the GPU mostly idle, long enough that the T-step chain dominates, and
+// small enough that the scan's N_pad^3 work per step stays below the chain's
+// time (pairs * N_pad^3 <= 2^21: e.g. 64 pairs at 32 states, 512 at 16).
+static bool scan_preferred(const hmm_dims_t& d, const hmm_seqs_t& q) {
+  if (d.N > 32 || q.max_len < 4096 || q.S <= 0) return false;
+  const int64_t span = q.model_of_seq ? 1 : (q.model_base ? q.model_span : d.K);
+  const int64_t pairs = (int64_t)q.S * span;
+  const int64_t NP = pad_states(d.N);
+  return pairs * NP * NP * NP <= ((int64_t)1 << 21) && pairs <= (int64_t)num_sms() * 32;
 }
 
 static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma = false,
@@ -669,6 +690,11 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
   if (seqs->S < 0 || seqs->total_obs < 0) return fail(HMM_ERR_ARG, "negative S or total_obs");
   size_t need = 0;
   if (op != HMM_OP_FORWARD_BACKWARD || dims.N <= 64) need = make_layout(dims, *seqs, op).total;
+  if (op == HMM_OP_FORWARD && scan_preferred(dims, *seqs)) {  // room for HMM_AUTO's scan
+    const size_t sc = make_layout(dims, *seqs, HMM_OP_FORWARD_SCAN, false,
+                                  scan_chunk_len(0, seqs->max_len)).total;
+    if (sc > need) need = sc;
+  }
   if (op == HMM_OP_FORWARD_BACKWARD && dims.N > 32) {
     if (pad_states(dims.N) >= 256) {
       if (fbw_emis_smem(pad_states(dims.N), dims.M) > 227 * 1024)
@@ -723,10 +749,16 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
   if ((rc = check_params(pi, A, B))) return rc;
   if (seqs->S > 0 && (!loglik || !al(loglik, 4))) return fail(HMM_ERR_ARG, "loglik NULL or misaligned");
   if (argmax && !al(argmax, 4)) return fail(HMM_ERR_ARG, "argmax misaligned");
+  const bool mma = use_mma_forward(dims, precision);
+  // HMM_AUTO takes the parallel-in-time forward for batches of few long
+  // sequences, when the workspace holds its chunk products
+  if (precision == HMM_AUTO && !mma && scan_preferred(dims, *seqs) && ws && al(ws, 256) &&
+      ws_bytes >= make_layout(dims, *seqs, HMM_OP_FORWARD_SCAN, false,
+                              scan_chunk_len(0, seqs->max_len)).total)
+    return hmm_forward_scan(dims, pi, A, B, seqs, 0, loglik, argmax, ws, ws_bytes, stream);
   const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD);
   if ((rc = check_ws(ws, ws_bytes, L))) return rc;
   const bool all = seqs->model_of_seq == nullptr;
-  const bool mma = use_mma_forward(dims, precision);
   if (mma && dims.N <= 32)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core forward needs N > 32 (N=%d: use HMM_FP32)", dims.N);
   if (mma && (!all || seqs->model_base))

@@ -621,6 +621,7 @@ cudaError_t launch_reduce(const ReduceLaunch& a, cudaStream_t st);
 
 // Instantiated lane counts per (op, NP); the first entry is the default.
 int candidates(int op, int NP, int* out, int cap);
+size_t forward_ws_sequential(const hmm_dims_t& d, const hmm_seqs_t& q);
 int num_sms();
 
 }  // namespace hmmgb

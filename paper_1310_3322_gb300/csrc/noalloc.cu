@@ -63,6 +63,9 @@ extern "C" int hmm_forward_static(hmm_dims_t dims, const float* pi, const float*
   size_t need = 0;
   int rc = hmm_workspace_size(dims, seqs, HMM_OP_FORWARD, &need);
   if (rc != HMM_OK) return rc;
+  // the sequential recursion's need (HMM_AUTO's parallel-in-time variant is
+  // only taken when its storage fits the scratch)
+  need = hmmgb::forward_ws_sequential(dims, *seqs);
   if (need > (size_t)HMM_STATIC_SCRATCH_BYTES) {
     char msg[160];
     snprintf(msg, sizeof(msg),

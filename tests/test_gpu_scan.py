@@ -169,3 +169,44 @@ def test_scan_graph_replay_is_bitwise_identical():
         g.replay()
     torch.cuda.synchronize()
     assert torch.equal(ll, ll0) and torch.equal(am, am0)
+
+
+def _scan_launches(fn):
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    out = fn()
+    kt = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    return out, kt["scan_chunks"][0]
+
+
+def test_auto_precision_takes_the_scan_for_few_long_sequences():
+    """HMM_AUTO picks the parallel-in-time forward for a batch of few long
+    sequences (the workspace query leaves room for it; the static-scratch
+    entry point too, its chunk products fitting the scratch) and the
+    sequential recursion for many short ones."""
+    import torch
+    w = synth.make_workload("longseq", n_seqs=2, K=2, N=16, lengths=("uniform", 9000, 12000))
+    pi, A, B = _params(w)
+    seqs = _gpu(w)
+    ws = hmm.Workspace(torch.device("cuda"))
+    (auto_ll, auto_am), n = _scan_launches(
+        lambda: hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_AUTO, workspace=ws))
+    assert n == 1
+    scan_ll, scan_am = hmm.hmm_forward_scan(pi, A, B, seqs, workspace=ws)
+    (seq_ll, seq_am), n = _scan_launches(
+        lambda: hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_FP32, workspace=ws))
+    assert n == 0
+    assert torch.equal(auto_ll, scan_ll) and torch.equal(auto_am, scan_am)
+    assert torch.equal(auto_am, seq_am)
+    assert np.all(np.abs(auto_ll.cpu().numpy() - seq_ll.cpu().numpy())
+                  <= 1e-5 * w.lengths[:, None])
+    st_ll, _ = hmm.hmm_forward_static(pi, A, B, seqs, precision=hmm.HMM_AUTO)
+    assert torch.equal(st_ll, scan_ll)
+    # many short sequences: AUTO is the sequential recursion
+    w2 = synth.make_workload("batched", n_seqs=64, lengths=("uniform", 30, 300))
+    p2 = _params(w2)
+    (a2, _), n = _scan_launches(lambda: hmm.hmm_forward(*p2, _gpu(w2), precision=hmm.HMM_AUTO))
+    assert n == 0
+    f2, _ = hmm.hmm_forward(*p2, _gpu(w2), precision=hmm.HMM_FP32)
+    assert torch.equal(a2, f2)

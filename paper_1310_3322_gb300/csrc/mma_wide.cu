@@ -51,6 +51,13 @@ struct WideCfg {
 
 constexpr uint32_t kWideWait = 1u << 24;
 
+// One 32-byte store (256-bit vector store, sm_100+): a full sector per lane.
+__device__ __forceinline__ void st_v8(float* p, float4 a, float4 b) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               :: "l"(p), "f"(a.x), "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z),
+                  "f"(b.w) : "memory");
+}
+
 // BF16 image of A^T per model, chunk-major: chunk kc holds states i in
 // [32 kc, 32 kc + 32) for every j, element (n = j, k = i) = a_ij at
 //   (j / 8) * 512 + (il / 8) * 128 + (j % 8) * 16 + (il % 8) * 2,  il = i - 32 kc
@@ -271,24 +278,32 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
         tc::tmem_ld32(d_mine + (uint32_t)(c * 32), y);
         tc::tmem_ld_wait();
         float2 acc = make_float2(0.f, 0.f);
+        // (32-byte aligned: rows of NP floats, 32-column chunks)
         float* xdst = (xrow && t < Tn) ? xrow + (size_t)tix(t) * NP + 32 * c : nullptr;
+        float4 held = make_float4(0.f, 0.f, 0.f, 0.f);  // the even group, stored with the odd
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           float2 lo, hi;
+          float4 sv;
           if constexpr (DIR == 0) {
             lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
                                        make_float2(bq[q].x, bq[q].y)), fac2);
             hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
                                        make_float2(bq[q].z, bq[q].w)), fac2);
             if (!live) { lo = make_float2(0.f, 0.f); hi = lo; }
-            if (xdst) *reinterpret_cast<float4*>(xdst + 4 * q) = make_float4(lo.x, lo.y, hi.x, hi.y);
+            sv = make_float4(lo.x, lo.y, hi.x, hi.y);
           } else {  // beta_t = D 2^-f kept, Y_t = beta_t o b(o_t) is the next operand
             float2 plo = __fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]), fac2);
             float2 phi = __fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]), fac2);
             if (!live) { plo = make_float2(0.f, 0.f); phi = plo; }
-            if (xdst) *reinterpret_cast<float4*>(xdst + 4 * q) = make_float4(plo.x, plo.y, phi.x, phi.y);
+            sv = make_float4(plo.x, plo.y, phi.x, phi.y);
             lo = __fmul2_rn(plo, make_float2(bq[q].x, bq[q].y));
             hi = __fmul2_rn(phi, make_float2(bq[q].z, bq[q].w));
+          }
+          if (q & 1) {
+            if (xdst) st_v8(xdst + 4 * (q - 1), held, sv);
+          } else {
+            held = sv;
           }
           acc = __fadd2_rn(acc, __fadd2_rn(lo, hi));
           y[4 * q] = lo.x; y[4 * q + 1] = lo.y; y[4 * q + 2] = hi.x; y[4 * q + 3] = hi.y;

@@ -53,55 +53,50 @@ __device__ __forceinline__ long long prefix_units(const SetupArgs& a, int T, int
   return (T - 1 + (long long)a.scan_chunk - 1) / a.scan_chunk;
 }
 
-__device__ __forceinline__ bool seq_ok(const SetupArgs& a, int s, int T, long long off) {
-  bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
-  if (ok && a.model_of_seq) {
-    const int k = a.model_of_seq[s];
-    ok = k >= 0 && k < a.K;
-  }
-  if (ok && a.model_base) {
-    const int b = a.model_base[s];
-    ok = b >= 0 && b <= a.K - a.span;
-  }
-  return ok;
-}
-
-// The same plan for S <= kPlanRegs * kPlanThreads with every sequence's
-// length held in registers: thread t owns sequences t + i * kPlanThreads, all
-// of its loads are issued together and nothing written is read back. The
-// backpointer offsets (an exclusive prefix of the lengths in index order) are
-// one block scan per row i of kPlanThreads sequences.
+// The plan for S <= kPlanRegs * kPlanThreads with every sequence's length
+// held in registers: thread t validates sequences t + i * kPlanThreads (all
+// of its loads in flight together) and sorts them by length bucket; the
+// prefix sums in sequence order (backpointer rows, scan chunks) take
+// contiguous runs of kPlanRegs per thread and one block scan.
 constexpr int kPlanRegs = 16;
 
 __device__ void plan_block_cached(const SetupArgs& a) {
   __shared__ int hist[kLenBuckets];
   __shared__ int itmp[32];
   __shared__ long long ltmp[32];
-  __shared__ long long row_total;
+  __shared__ long long total;
   const int tid = threadIdx.x;
   hist[tid] = 0;  // kLenBuckets == kPlanThreads
   for (int i = tid; i < a.ndone; i += kPlanThreads) a.done[i] = 0;
-  // loads and checks only (no stores in between), so the unrolled loads can
-  // all be in flight together
+  // every load first, none behind a test, so all of them are in flight
+  // together (a load under a data-dependent branch waits for the branch)
   int Ts[kPlanRegs];
   int bad = 0;
 #pragma unroll
   for (int i = 0; i < kPlanRegs; ++i) {
     const int s = tid + i * kPlanThreads;
-    Ts[i] = 0;
-    if (s < a.S) {
-      Ts[i] = a.lengths[s];
-      if (!seq_ok(a, s, Ts[i], a.offsets[s])) { Ts[i] = -1; bad = 1; }
-    }
+    const bool in = s < a.S;
+    const int T = in ? __ldg(a.lengths + s) : 0;
+    const long long off = in ? __ldg(a.offsets + s) : 0;
+    const int mk = (in && a.model_of_seq) ? __ldg(a.model_of_seq + s) : 0;
+    const int mb = (in && a.model_base) ? __ldg(a.model_base + s) : 0;
+    bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
+    if (a.model_of_seq) ok = ok && mk >= 0 && mk < a.K;
+    if (a.model_base) ok = ok && mb >= 0 && mb <= a.K - a.span;
+    Ts[i] = in ? (ok ? T : -1) : 0;
+    if (in && !ok) bad = 1;
   }
-  __syncthreads();
 #pragma unroll
   for (int i = 0; i < kPlanRegs; ++i) {
     const int s = tid + i * kPlanThreads;
-    if (s < a.S) {
-      a.seqlen[s] = Ts[i];
-      if (!a.skip_order) atomicAdd(&hist[kLenBuckets - 1 - length_bucket(max(Ts[i], 0))], 1);
-    }
+    if (s < a.S) a.seqlen[s] = Ts[i];
+  }
+  __syncthreads();  // hist cleared; seqlen visible to the whole block
+#pragma unroll
+  for (int i = 0; i < kPlanRegs; ++i) {
+    const int s = tid + i * kPlanThreads;
+    if (s < a.S && !a.skip_order)
+      atomicAdd(&hist[kLenBuckets - 1 - length_bucket(max(Ts[i], 0))], 1);
   }
   if (bad) set_status(a.status, HMM_STATUS_SEQ);
   if (!a.skip_order) {
@@ -118,32 +113,39 @@ __device__ void plan_block_cached(const SetupArgs& a) {
       }
     }
   }
+  // prefix sums in sequence order: thread t owns the contiguous run
+  // [t R, t R + R) of the validated lengths (read back from seqlen), so one
+  // block scan of the per-thread totals serves all of them
   for (int kind = 0; kind < 2; ++kind) {
     if (kind == 0 ? !a.want_bpoff : a.scan_chunk <= 0) continue;
     int64_t* out = kind == 0 ? a.bpoff : a.coff;
     const long long cap = kind == 0 ? a.bp_cap_rows : a.coff_cap;
-    long long run = 0;  // units of every earlier row
-    bool over = false;
-    for (int i = 0; i * kPlanThreads < a.S; ++i) {
-      const int s = tid + i * kPlanThreads;
-      int T = 0;
+    const int b0 = tid * kPlanRegs;
+    long long u[kPlanRegs];
+    long long local = 0;
 #pragma unroll
-      for (int ii = 0; ii < kPlanRegs; ++ii)
-        if (ii == i) T = Ts[ii];
-      const long long v = s < a.S ? prefix_units(a, T, kind) : 0;
-      const long long x = run + block_exclusive_scan<long long>(v, ltmp, &row_total);
+    for (int i = 0; i < kPlanRegs; ++i) {
+      const int s = b0 + i;
+      u[i] = s < a.S ? prefix_units(a, a.seqlen[s], kind) : 0;
+      local += u[i];
+    }
+    long long run = block_exclusive_scan<long long>(local, ltmp, &total);
+    bool over = false;
+#pragma unroll
+    for (int i = 0; i < kPlanRegs; ++i) {
+      const int s = b0 + i;
       if (s < a.S) {
-        out[s] = x;
-        if (v > 0 && x + v > cap) {  // storage exhausted
+        out[s] = run;
+        if (u[i] > 0 && run + u[i] > cap) {  // storage exhausted
           a.seqlen[s] = -1;
           over = true;
         }
+        run += u[i];
       }
-      run += row_total;
-      __syncthreads();  // row_total is rewritten by the next scan
     }
     if (over) set_status(a.status, HMM_STATUS_SEQ);
-    if (kind == 1 && tid == 0) a.coff[a.S] = run < cap ? run : cap;
+    if (kind == 1 && tid == 0) a.coff[a.S] = total < cap ? total : cap;
+    __syncthreads();  // seqlen rewrites and `total` settle before the next kind
   }
 }
 
@@ -156,9 +158,16 @@ __device__ void plan_block(const SetupArgs& a) {
   for (int i = tid; i < a.ndone; i += kPlanThreads) a.done[i] = 0;
   __syncthreads();
 
+#pragma unroll 4
   for (int s = tid; s < a.S; s += kPlanThreads) {
-    const int T = a.lengths[s];
-    const bool ok = seq_ok(a, s, T, a.offsets[s]);
+    // loads first, none behind a test (see plan_block_cached)
+    const int T = __ldg(a.lengths + s);
+    const long long off = __ldg(a.offsets + s);
+    const int mk = a.model_of_seq ? __ldg(a.model_of_seq + s) : 0;
+    const int mb = a.model_base ? __ldg(a.model_base + s) : 0;
+    bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
+    if (a.model_of_seq) ok = ok && mk >= 0 && mk < a.K;
+    if (a.model_base) ok = ok && mb >= 0 && mb <= a.K - a.span;
     if (!ok) set_status(a.status, HMM_STATUS_SEQ);
     a.seqlen[s] = ok ? T : -1;
     if (!a.skip_order) atomicAdd(&hist[kLenBuckets - 1 - length_bucket(ok ? T : 0)], 1);

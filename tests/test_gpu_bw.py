@@ -86,3 +86,32 @@ def test_baum_welch_graph_replay_matches_eager():
     assert results[0][0] == results[1][0]
     for a, b in zip(results[0][1], results[1][1]):
         np.testing.assert_array_equal(a, b)
+
+
+def test_baum_welch_above_128_states_follows_the_oracle_and_replays():
+    """The re-estimation loop on the 512-state recipe at 300 states (the
+    adjoint above 128 states: wide forward and backward passes, the count
+    contraction, the M-step), eager and graph-replayed: the total rises and
+    follows the FP64 iteration within the BF16 bound, and the replayed loop
+    equals the eager one bit for bit."""
+    w = synth.make_workload("cuhmm", n_seqs=20, lengths=("uniform", 20, 70), N=300, M=32)
+    rng = np.random.default_rng(13)
+    start = [x * rng.uniform(0.5, 1.5, size=x.shape).astype(np.float32) for x in (w.pi, w.A, w.B)]
+    start = [x / x.sum(axis=-1, keepdims=True) for x in start]
+    w0 = dataclasses.replace(w, pi=start[0], A=start[1], B=start[2])
+    iters, tol = 4, 2 ** -7
+    results = []
+    for graph in (True, False):
+        seqs, pi, A, B = to_gpu(w0, labelled=True)
+        h = baum_welch.baum_welch(pi, A, B, seqs, max_iters=iters, tol=0.0, chunk=2, graph=graph,
+                                  precision=hmm.HMM_BF16_MMA)
+        assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+        results.append((h, [t.cpu().numpy() for t in (pi, A, B)]))
+    assert results[0][0] == results[1][0]
+    for a, b in zip(results[0][1], results[1][1]):
+        np.testing.assert_array_equal(a, b)
+    hist = results[0][0]
+    _, rhist = _oracle_bw(w0, iters)
+    sumT = float(w.lengths.sum())
+    assert hist[-1] > hist[0]
+    np.testing.assert_allclose(hist, rhist, rtol=0, atol=tol * sumT)

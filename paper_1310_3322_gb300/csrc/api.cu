@@ -378,6 +378,7 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
 }
 
 static int max_states(int op, int precision) {
+  if (op == HMM_OP_VITERBI) return (precision == HMM_FP32 || precision == HMM_AUTO) ? 128 : 0;
   if (op == HMM_OP_FORWARD_BACKWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO))
     return 512;
   if (op == HMM_OP_FORWARD_SCAN) return (precision == HMM_FP32 || precision == HMM_AUTO) ? 32 : 0;
@@ -958,10 +959,13 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
   if (seqs->S == 0) return HMM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const bool all = seqs->model_of_seq == nullptr;
-  const int G = lanes_for(HMM_OP_VITERBI, L.NP);
-  const int PP = 32 / G;
+  // above 64 states: one warp per pair, the log matrix in shared memory; an
+  // all-models item is a group of 4 sequences sharing the block's matrix
+  const bool wide = L.NP > 64;
+  const int G = wide ? 32 : lanes_for(HMM_OP_VITERBI, L.NP);
+  const int PP = wide ? ((all && !seqs->model_base) ? 4 : 1) : 32 / G;
   const int ngroups = (seqs->S + PP - 1) / PP;
-  const int Gp = lanes_for(HMM_TUNE_VITERBI_PATHS, L.NP);
+  const int Gp = wide ? 32 : lanes_for(HMM_TUNE_VITERBI_PATHS, L.NP);
   const int PPp = 32 / Gp;
   int32_t* best = best_model ? best_model : at<int32_t>(ws, L.best);
   const bool need_best = all && (best_model || path);
@@ -994,13 +998,13 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
   v.n_items_path = (seqs->S + PPp - 1) / PPp;
   auto scores = [&]() {
     Timed tm(T_VSCORES, st);
-    cudaError_t r = launch_viterbi_scores(L.NP, G, v, st);
+    cudaError_t r = wide ? launch_viterbi_scores_wide(v, st) : launch_viterbi_scores(L.NP, G, v, st);
     tm.stop();
     return r;
   };
   auto paths = [&]() {
     Timed tm(T_VPATHS, st);
-    cudaError_t r = launch_viterbi_paths(L.NP, Gp, v, st);
+    cudaError_t r = wide ? launch_viterbi_paths_wide(v, st) : launch_viterbi_paths(L.NP, Gp, v, st);
     tm.stop();
     return r;
   };

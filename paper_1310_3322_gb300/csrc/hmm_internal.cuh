@@ -395,6 +395,9 @@ struct VitLaunch {
 };
 cudaError_t launch_viterbi_scores(int NP, int G, const VitLaunch& a, cudaStream_t st);
 cudaError_t launch_viterbi_paths(int NP, int G, const VitLaunch& a, cudaStream_t st);
+// 64 < N <= 128 (viterbi_wide.cu): one warp per pair, log A in shared memory
+cudaError_t launch_viterbi_scores_wide(const VitLaunch& a, cudaStream_t st);
+cudaError_t launch_viterbi_paths_wide(const VitLaunch& a, cudaStream_t st);
 
 struct FbLaunch {
   SeqArgs seq;

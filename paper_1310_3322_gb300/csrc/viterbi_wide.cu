@@ -1,0 +1,388 @@
+// viterbi_wide.cu -- Viterbi decoding above 64 states (up to 128), FP32 SIMT
+// (Sec. 2.7 "Viterbi"; Rabiner 1989 eqs. 32-35).
+//
+// The same recursion, shifts and tie-breaks as viterbi.cu, with one warp per
+// (sequence, model) pair and four consecutive states j per lane. The log
+// transition matrix (128 x 128 FP32, 64 KB) no longer fits a lane's
+// registers, so it is staged in shared memory per work item and every step
+// reads it row by row: lane l takes log a_{i, 4l .. 4l+3} as one 16-byte load
+// (conflict-free across the warp) and delta_{t-1}(i) as a broadcast, four
+// rows at a time.
+//
+//  * scores: all-models items are (group of W sequences, model), the W warps
+//    of a block sharing the model's matrix; labelled pairs and model sets use
+//    one-warp blocks (one pair, one matrix).
+//  * paths: one-warp blocks (the decoded model differs per sequence); the
+//    smallest maximising predecessor of each state is stored as one byte per
+//    (t, j), 128 bytes per step written by the warp as one line, and the
+//    backtrack walks 32 rows at a time from registers with one shuffle per
+//    step, as in viterbi.cu.
+#include "hmm_internal.cuh"
+
+namespace hmmgb {
+
+namespace {
+
+constexpr int kVW = 128;  // padded states served here
+
+__device__ __forceinline__ float nan_w() { return __int_as_float(0x7fc00000); }
+
+// Shift the warp's 128-state vector (4 per lane) by its maximum rounded to a
+// multiple of 2^-15; false when every entry is -inf.
+__device__ __forceinline__ bool shift_max(float (&x)[4], long long& Q, bool apply) {
+  float m = group_max<32>(fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])));
+  if (!apply) return true;
+  if (m == -INFINITY) return false;
+  const int q = __float2int_rn(m * kViterbiQuant);
+  const float qf = (float)q * (1.f / kViterbiQuant);
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) x[jj] -= qf;
+  Q += q;
+  return true;
+}
+
+// Stages the log transition matrix of model k (padded rows) in shared memory.
+__device__ __forceinline__ void stage_la(float* lA, const float* Ap, int k, int nthreads) {
+  const float4* src = reinterpret_cast<const float4*>(Ap + (size_t)k * kVW * kVW);
+  float4* dst = reinterpret_cast<float4*>(lA);
+  for (int i = threadIdx.x; i < kVW * kVW / 4; i += nthreads) dst[i] = __ldg(src + i);
+}
+
+// m[jj] = max_i (x_i + la_{i, j0+jj}); with ARG also the smallest maximising i.
+template <bool ARG>
+__device__ __forceinline__ void maxplus_smem(const float* xb, const float* lA, int j0,
+                                             float (&m)[4], int (&arg)[4]) {
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) { m[jj] = -INFINITY; arg[jj] = 0; }
+#pragma unroll 4
+  for (int i4 = 0; i4 < kVW / 4; ++i4) {
+    const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * i4);
+    const float xi[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * i4 + u;
+      const float4 la = *reinterpret_cast<const float4*>(lA + i * kVW + j0);
+      const float v[4] = {xi[u] + la.x, xi[u] + la.y, xi[u] + la.z, xi[u] + la.w};
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        if constexpr (ARG) {
+          if (v[jj] > m[jj]) { m[jj] = v[jj]; arg[jj] = i; }
+        } else {
+          m[jj] = fmaxf(m[jj], v[jj]);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// W warps per block; ALLW: all-models items over groups of W sequences.
+template <int W, bool ALL>
+__global__ void __launch_bounds__(W * 32) hmm_viterbi_scores_wide(VitLaunch a) {
+  extern __shared__ __align__(16) float vsm[];
+  float* lA = vsm;                                  // [128][128]
+  float* xs = vsm + kVW * kVW;                      // [W][2][128]
+  __shared__ int item_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j0 = 4 * lane;
+  const int M = a.seq.M, S = a.seq.S;
+  const int span = a.seq.span;
+  const bool param_bad = (__ldcg(a.status) & HMM_STATUS_PARAM) != 0;
+  // W > 1 only for all-models items without model sets (one model per block)
+
+  for (;;) {
+    __syncthreads();  // the previous item's readers of lA are done
+    if (threadIdx.x == 0) item_s = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int item = item_s;
+    if (item >= a.n_items_score) break;
+    const int g = ALL ? item / span : item;
+    const int kr = ALL ? item % span : 0;
+    const int pos = g * W + warp;
+    const bool has = pos < S;
+    const int s = has ? a.seq.order[pos] : 0;
+    const int T = has ? a.seq.seqlen[s] : 0;
+    int k = kr;
+    if (!ALL && has && T >= 0) k = a.seq.model_of_seq[s];
+    if (ALL && has && T >= 0 && a.seq.model_base) k += a.seq.model_base[s];
+    stage_la(lA, a.mod.Ap, k, W * 32);  // (W > 1: every warp of the block has model kr)
+    __syncthreads();
+
+    const bool bad_seq = T < 0;
+    const int Tn = bad_seq ? 0 : T;
+    const float* Bk = a.mod.Btp + (size_t)k * M * kVW + j0;
+    const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
+    float x[4];
+    long long Q = 0;
+    bool dead = false, bad = bad_seq || param_bad;
+    int err = 0;
+    {
+      int o0 = Tn > 0 ? __ldg(o) : 0;
+      if ((unsigned)o0 >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; o0 = 0; }
+      const float4 b = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)o0 * kVW));
+      const float4 pv = __ldg(reinterpret_cast<const float4*>(a.mod.pip + (size_t)k * kVW + j0));
+      x[0] = pv.x + b.x; x[1] = pv.y + b.y; x[2] = pv.z + b.z; x[3] = pv.w + b.w;
+      if (!shift_max(x, Q, Tn > 0 && !bad)) dead = true;
+    }
+    int on = 0;
+    if (1 < Tn) {
+      on = __ldg(o + 1);
+      if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
+    }
+    float4 bn = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on * kVW));
+    int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
+
+    for (int t = 1; t < Tn; ++t) {  // warp-uniform: one pair per warp
+      const bool act = !dead && !bad;
+      float* xb = xs + (warp * 2 + (t & 1)) * kVW;
+      *reinterpret_cast<float4*>(xb + j0) = make_float4(x[0], x[1], x[2], x[3]);
+      __syncwarp();
+      float m[4];
+      int arg[4];
+      maxplus_smem<false>(xb, lA, j0, m, arg);
+      const float4 b = bn;
+      if (t + 1 < Tn) {
+        on = o2;
+        if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
+        bn = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on * kVW));
+        if (t + 2 < Tn) o2 = __ldg(o + t + 2);
+      }
+      m[0] += b.x; m[1] += b.y; m[2] += b.z; m[3] += b.w;
+      const long long Qold = Q;
+      if (!shift_max(m, Q, act)) dead = true;
+      if (act && !dead) {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) x[jj] = m[jj];
+      } else {
+        Q = Qold;
+      }
+    }
+    const float fm = group_max<32>(fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])));
+    if (has && lane == 0) {
+      float out;
+      if (bad) {
+        out = nan_w();
+        if (err) set_status(a.status, err);
+      } else if (Tn == 0) {
+        out = 0.f;
+      } else if (dead) {
+        out = -INFINITY;
+      } else {
+        out = (float)((double)fm + (double)Q * (1.0 / kViterbiQuant));
+      }
+      a.score[ALL ? (size_t)s * span + kr : (size_t)s] = out;
+      if (!ALL && a.best) a.best[s] = bad ? -1 : k;
+    }
+
+    if (ALL && a.best) {
+      __syncthreads();
+      __shared__ int last_s;
+      if (threadIdx.x == 0) {
+        __threadfence();
+        last_s = atomicAdd(a.done + g, 1) == span - 1;
+      }
+      __syncthreads();
+      if (last_s) {
+        __threadfence();
+        if (has && lane == 0) {
+          const float* row = a.score + (size_t)s * span;
+          float best = __ldcg(row);
+          int barg = isnan(best) ? -1 : 0;
+          for (int kk = 1; kk < span; ++kk) {
+            const float v = __ldcg(row + kk);
+            if (isnan(v)) barg = -1;
+            else if (barg >= 0 && v > best) { best = v; barg = kk; }
+          }
+          a.best[s] = barg;
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32) hmm_viterbi_paths_wide(VitLaunch a) {
+  constexpr int CH = 32;  // backtrack rows fetched per chunk
+  extern __shared__ __align__(16) float vsm[];
+  float* lA = vsm;
+  float* xs = vsm + kVW * kVW;  // [2][128]
+  const int lane = threadIdx.x, j0 = 4 * lane;
+  const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
+  const int span = a.seq.span;
+  const bool labelled = a.seq.model_of_seq != nullptr;
+  const bool param_bad = (__ldcg(a.status) & HMM_STATUS_PARAM) != 0;
+
+  for (;;) {
+    __syncwarp();
+    int item = 0;
+    if (lane == 0) item = atomicAdd(a.queue + 1, 1);
+    item = __shfl_sync(HMM_FULL_MASK, item, 0);
+    if (item >= a.n_items_path) break;
+    const int pos = item;
+    const bool has = pos < S;
+    const int s = has ? a.seq.order[pos] : 0;
+    const int T = has ? a.seq.seqlen[s] : 0;
+    int k = 0;
+    bool bad = T < 0 || param_bad;
+    if (has && T >= 0) {
+      if (labelled) {
+        k = a.seq.model_of_seq[s];
+        if (k < 0 || k >= K) { bad = true; k = 0; }
+      } else {
+        k = __ldcg(a.best + s);
+        if (k < 0 || k >= span) { bad = true; k = 0; }
+        else if (a.seq.model_base) k += a.seq.model_base[s];
+      }
+    }
+    const int Tn = (T < 0) ? 0 : T;
+    stage_la(lA, a.mod.Ap, k, 32);
+    __syncwarp();
+
+    const float* Bk = a.mod.Btp + (size_t)k * M * kVW + j0;
+    const long long off = (has && T >= 0) ? a.seq.offsets[s] : 0;
+    const int32_t* o = a.seq.symbols + off;
+    uint8_t* bp = a.bp + ((has && T >= 0) ? a.bpoff[s] : 0) * (long long)kVW + j0;
+
+    float x[4];
+    long long Q = 0;
+    bool dead = false;
+    int err = 0;
+    {
+      int o0 = Tn > 0 ? __ldg(o) : 0;
+      if ((unsigned)o0 >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; o0 = 0; }
+      const float4 b = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)o0 * kVW));
+      const float4 pv = __ldg(reinterpret_cast<const float4*>(a.mod.pip + (size_t)k * kVW + j0));
+      x[0] = pv.x + b.x; x[1] = pv.y + b.y; x[2] = pv.z + b.z; x[3] = pv.w + b.w;
+      if (!shift_max(x, Q, Tn > 0 && !bad)) dead = true;
+    }
+    int on = 0;
+    if (1 < Tn) {
+      on = __ldg(o + 1);
+      if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
+    }
+    float4 bn = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on * kVW));
+    int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
+
+    for (int t = 1; t < Tn; ++t) {
+      const bool act = !dead && !bad;
+      float* xb = xs + (t & 1) * kVW;
+      *reinterpret_cast<float4*>(xb + j0) = make_float4(x[0], x[1], x[2], x[3]);
+      __syncwarp();
+      float m[4];
+      int arg[4];
+      maxplus_smem<true>(xb, lA, j0, m, arg);
+      const float4 b = bn;
+      if (t + 1 < Tn) {
+        on = o2;
+        if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
+        bn = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on * kVW));
+        if (t + 2 < Tn) o2 = __ldg(o + t + 2);
+      }
+      m[0] += b.x; m[1] += b.y; m[2] += b.z; m[3] += b.w;
+      const long long Qold = Q;
+      if (!shift_max(m, Q, act)) dead = true;
+      if (act && !dead) {
+        const uint32_t w = (uint32_t)(arg[0] & 0xff) | ((uint32_t)(arg[1] & 0xff) << 8) |
+                           ((uint32_t)(arg[2] & 0xff) << 16) | ((uint32_t)(arg[3] & 0xff) << 24);
+        *reinterpret_cast<uint32_t*>(bp + (long long)t * kVW) = w;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) x[jj] = m[jj];
+      } else {
+        Q = Qold;
+      }
+    }
+
+    // final state: smallest argmax of delta_T
+    float fv = x[0];
+    int fj = j0;
+#pragma unroll
+    for (int jj = 1; jj < 4; ++jj)
+      if (x[jj] > fv) { fv = x[jj]; fj = j0 + jj; }
+#pragma unroll
+    for (int o5 = 16; o5 > 0; o5 >>= 1) {
+      const float v2 = __shfl_xor_sync(HMM_FULL_MASK, fv, o5);
+      const int j2 = __shfl_xor_sync(HMM_FULL_MASK, fj, o5);
+      if (v2 > fv || (v2 == fv && j2 < fj)) { fv = v2; fj = j2; }
+    }
+    if (has && lane == 0) {
+      float out;
+      if (bad) {
+        out = nan_w();
+        if (err) set_status(a.status, err);
+      } else if (Tn == 0) {
+        out = 0.f;
+      } else if (dead) {
+        out = -INFINITY;
+      } else {
+        out = (float)((double)fv + (double)Q * (1.0 / kViterbiQuant));
+      }
+      if (labelled) {
+        a.score[s] = out;
+        if (a.best) a.best[s] = bad ? -1 : k;
+      }
+    }
+    if (!a.path) continue;
+
+    // backtrack: 32 rows of this lane's four bytes at a time
+    const bool walk = has && !bad && !dead && Tn > 0;
+    int q = walk ? fj : 0;
+    if (has && Tn > 0 && lane == 0) a.path[off + Tn - 1] = bad ? -1 : q;
+    for (int tc = Tn - 1; tc >= 1; tc -= CH) {
+      uint32_t rows[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int t = tc - u;
+        rows[u] = (walk && t >= 1) ? __ldcg(reinterpret_cast<const unsigned int*>(
+                                         bp + (long long)t * kVW)) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int t = tc - u;
+        const int owner = q >> 2;
+        const uint32_t byte = (rows[u] >> (8 * (q & 3))) & 0xffu;
+        const int nq = __shfl_sync(HMM_FULL_MASK, (int)byte, owner);
+        if (has && t >= 1) {
+          if (walk) q = nq;
+          if (lane == (t - 1) % 32) a.path[off + t - 1] = bad ? -1 : (dead ? 0 : q);
+        }
+      }
+    }
+  }
+}
+
+size_t viterbi_wide_smem(int warps) { return ((size_t)kVW * kVW + (size_t)warps * 2 * kVW) * 4; }
+
+template <typename Kern>
+static cudaError_t launch_vw(Kern kern, int warps, int n_items, const VitLaunch& a,
+                             cudaStream_t st) {
+  const size_t smem = viterbi_wide_smem(warps);
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int blocks = num_sms() * per_sm;
+  if (blocks > n_items) blocks = n_items > 0 ? n_items : 1;
+  kern<<<blocks, warps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Groups of sequences per all-models item (one model per block): 4 warps.
+int viterbi_wide_group(const VitLaunch& a) {
+  return (a.seq.model_of_seq == nullptr && a.seq.model_base == nullptr) ? 4 : 1;
+}
+
+cudaError_t launch_viterbi_scores_wide(const VitLaunch& a, cudaStream_t st) {
+  if (a.seq.model_of_seq != nullptr)
+    return launch_vw(hmm_viterbi_scores_wide<1, false>, 1, a.n_items_score, a, st);
+  if (viterbi_wide_group(a) == 4)
+    return launch_vw(hmm_viterbi_scores_wide<4, true>, 4, a.n_items_score, a, st);
+  return launch_vw(hmm_viterbi_scores_wide<1, true>, 1, a.n_items_score, a, st);
+}
+
+cudaError_t launch_viterbi_paths_wide(const VitLaunch& a, cudaStream_t st) {
+  return launch_vw(hmm_viterbi_paths_wide, 1, a.n_items_path, a, st);
+}
+
+}  // namespace hmmgb

@@ -59,13 +59,18 @@ def test_workspace_size_is_host_only_and_monotone(lib):
     q = _seqs(S=100)
     out = ctypes.c_size_t()
     assert lib.hmm_workspace_size(d, ctypes.byref(q), 7, ctypes.byref(out)) == hmm.HMM_ERR_ARG
-    # N up to 128 for the forward and the adjoint (tensor cores above 64), 64
-    # for Viterbi; the tensor-core adjoint takes M <= 256
+    # N up to 128 for the forward, the adjoint (tensor cores above 64) and
+    # Viterbi; the tensor-core adjoint takes M <= 256
     big = hmm.hmm_dims_t(4, 128, 256)
     assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_FORWARD, ctypes.byref(out)) == 0
     assert out.value >= 4 * 128 * 128 * 4
+    # Viterbi to 128 states (one warp per pair above 64), uint8 backpointers
     assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_VITERBI,
+                                  ctypes.byref(out)) == 0
+    assert out.value >= q.total_obs * 128
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(4, 129, 8), ctypes.byref(q), hmm.HMM_OP_VITERBI,
                                   ctypes.byref(out)) == hmm.HMM_ERR_UNSUPPORTED
+    assert lib.hmm_max_states(hmm.HMM_OP_VITERBI, hmm.HMM_FP32) == 128
     assert lib.hmm_workspace_size(big, ctypes.byref(q), hmm.HMM_OP_FORWARD_BACKWARD,
                                   ctypes.byref(out)) == 0
     # per-tile count slots and per-CTA checkpoint buffers

@@ -563,6 +563,27 @@ def run_large(args):
     kt32 = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     tf32_ms = kt32["forward"][1] / max(kt32["forward"][0], 1)
+    # Viterbi of every sequence against all K models (FP32 SIMT, one warp per
+    # pair above 64 states): scores, decoded model, best path
+    vsc = torch.empty((w.S, K), device=dev)
+    vbest = torch.empty(w.S, dtype=torch.int32, device=dev)
+    vpath = torch.empty(max(w.total_obs, 1), dtype=torch.int32, device=dev)
+
+    def vit():
+        hmm.hmm_viterbi(pi, A, B, seqs, score=vsc, best_model=vbest, path=vpath,
+                        workspace=ws[0])
+    vit()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(ws[0]) == 0
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    vit_ms = _time_steps(torch, vit, 2, flush)
+    ktv = hmm.hmm_timing_read()
+    hmm.hmm_timing_enable(False)
+    vkms = {k2: v[1] / v[0] for k2, v in ktv.items() if v[0]}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    vs_tf = 2.0 * N * N * sumT * K / (vkms["viterbi_scores"] / 1e3) / 1e12
     f_tf = 2.0 * N * N * sumT * K / (kms["forward"] / 1e3) / 1e12
     a_tf = (8.0 * N * N + 10 * N) * sumT / (kms["adjoint"] / 1e3) / 1e12
     dom = "adjoint" if kms["adjoint"] >= kms["forward"] else "forward"
@@ -589,6 +610,11 @@ def run_large(args):
                                "obs_per_s": sumT / (kms["adjoint"] / 1e3)},
                    "forward_tf32": {"ms": tf32_ms,
                                     "tflops": 2.0 * N * N * sumT * K / (tf32_ms / 1e3) / 1e12},
+                   "viterbi": {"ms": vit_ms, "kernel_ms": vkms,
+                               "obs_models_per_s": sumT * K / (vit_ms / 1e3),
+                               "scores_tflops": vs_tf, "scores_frac_fp32": vs_tf / fp32_peak,
+                               "note": "FP32 SIMT max-plus (2N^2 ops per obs*model), all K "
+                                       "models + decoded model + best path"},
                    **{k: {"ms": v} for k, v in kms.items() if k not in ("forward", "adjoint")}},
         "clocks": clk,
         "gpu_launches": 7 * args.steps,  # forward: setup, kernel; adjoint: setup, plan, kernel, reduce x2

@@ -202,7 +202,9 @@ int hmm_forward_scan_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, int
  *               k on ties, -1 if a score is NaN), or model_of_seq[s]
  *   path        [total_obs] or NULL: the best state path of the decoded model,
  *               path[offsets[s] + t] = q_t (sequences must not overlap)
- * Requires sum_s lengths[s] <= total_obs (backpointer storage). */
+ * Requires sum_s lengths[s] <= total_obs (backpointer storage: one byte per
+ * padded state and step). FP32 SIMT max-plus for N <= 128 (above 64 states
+ * one warp per pair with log A staged in shared memory). */
 int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                 const hmm_seqs_t* seqs, float* score, int32_t* best_model, int32_t* path,
                 void* workspace, size_t workspace_bytes, hmm_stream_t stream);

@@ -49,6 +49,9 @@ __device__ __forceinline__ void stage_la(float* lA, const float* Ap, int k, int 
 }
 
 // m[jj] = max_i (x_i + la_{i, j0+jj}); with ARG also the smallest maximising i.
+// The sums are packed FP32x2 adds (rounded like scalar adds) and, without
+// ARG, two rows fold into one three-input max: the maximum is exact in any
+// grouping, so both variants return the same values.
 template <bool ARG>
 __device__ __forceinline__ void maxplus_smem(const float* xb, const float* lA, int j0,
                                              float (&m)[4], int (&arg)[4]) {
@@ -58,18 +61,30 @@ __device__ __forceinline__ void maxplus_smem(const float* xb, const float* lA, i
   for (int i4 = 0; i4 < kVW / 4; ++i4) {
     const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * i4);
     const float xi[4] = {xv.x, xv.y, xv.z, xv.w};
+    float2 v01[4], v23[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int i = 4 * i4 + u;
-      const float4 la = *reinterpret_cast<const float4*>(lA + i * kVW + j0);
-      const float v[4] = {xi[u] + la.x, xi[u] + la.y, xi[u] + la.z, xi[u] + la.w};
+      const float4 la = *reinterpret_cast<const float4*>(lA + (4 * i4 + u) * kVW + j0);
+      const float2 xx = make_float2(xi[u], xi[u]);
+      v01[u] = fadd2(xx, make_float2(la.x, la.y));
+      v23[u] = fadd2(xx, make_float2(la.z, la.w));
+    }
+    if constexpr (ARG) {
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        if constexpr (ARG) {
+      for (int u = 0; u < 4; ++u) {
+        const int i = 4 * i4 + u;
+        const float v[4] = {v01[u].x, v01[u].y, v23[u].x, v23[u].y};
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
           if (v[jj] > m[jj]) { m[jj] = v[jj]; arg[jj] = i; }
-        } else {
-          m[jj] = fmaxf(m[jj], v[jj]);
-        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; u += 2) {
+        m[0] = fmax3(m[0], v01[u].x, v01[u + 1].x);
+        m[1] = fmax3(m[1], v01[u].y, v01[u + 1].y);
+        m[2] = fmax3(m[2], v23[u].x, v23[u + 1].x);
+        m[3] = fmax3(m[3], v23[u].y, v23[u + 1].y);
       }
     }
   }

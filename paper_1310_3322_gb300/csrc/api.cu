@@ -959,11 +959,12 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
   if (seqs->S == 0) return HMM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const bool all = seqs->model_of_seq == nullptr;
-  // above 64 states: one warp per pair, the log matrix in shared memory; an
-  // all-models item is a group of 4 sequences sharing the block's matrix
+  // above 64 states: one warp per pair (four in all-models score blocks),
+  // the log matrix in shared memory; an all-models score item is a group of
+  // 16 sequences sharing the block's matrix
   const bool wide = L.NP > 64;
   const int G = wide ? 32 : lanes_for(HMM_OP_VITERBI, L.NP);
-  const int PP = wide ? ((all && !seqs->model_base) ? 4 : 1) : 32 / G;
+  const int PP = wide ? ((all && !seqs->model_base) ? 16 : 1) : 32 / G;
   const int ngroups = (seqs->S + PP - 1) / PP;
   const int Gp = wide ? 32 : lanes_for(HMM_TUNE_VITERBI_PATHS, L.NP);
   const int PPp = 32 / Gp;

@@ -9,9 +9,10 @@
 // (conflict-free across the warp) and delta_{t-1}(i) as a broadcast, four
 // rows at a time.
 //
-//  * scores: all-models items are (group of W sequences, model), the W warps
-//    of a block sharing the model's matrix; labelled pairs and model sets use
-//    one-warp blocks (one pair, one matrix).
+//  * scores: all-models items are (group of 16 sequences, model): four warps
+//    of four pairs each share the model's matrix, every row read from shared
+//    memory serving four pairs; labelled pairs and model sets use one-warp
+//    blocks (one pair, one matrix).
 //  * paths: one-warp blocks (the decoded model differs per sequence); the
 //    smallest maximising predecessor of each state is stored as one byte per
 //    (t, j), 128 bytes per step written by the warp as one line, and the
@@ -92,18 +93,58 @@ __device__ __forceinline__ void maxplus_smem(const float* xb, const float* lA, i
 
 }  // namespace
 
-// W warps per block; ALLW: all-models items over groups of W sequences.
-template <int W, bool ALL>
+// m[p][jj] = max_i (x_p(i) + la_{i, j0+jj}) for P pairs of one model: every
+// row of log A read from shared memory serves all P pairs. Same values as
+// maxplus_smem (exact maxima, identically rounded sums).
+template <int P>
+__device__ __forceinline__ void maxplus_smem_multi(const float* xb, const float* lA, int j0,
+                                                   float (&m)[P][4]) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) m[p][jj] = -INFINITY;
+#pragma unroll 2
+  for (int i4 = 0; i4 < kVW / 4; ++i4) {
+    float4 xv[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) xv[p] = *reinterpret_cast<const float4*>(xb + p * 2 * kVW + 4 * i4);
+#pragma unroll
+    for (int uu = 0; uu < 4; uu += 2) {
+      const float4 l0 = *reinterpret_cast<const float4*>(lA + (4 * i4 + uu) * kVW + j0);
+      const float4 l1 = *reinterpret_cast<const float4*>(lA + (4 * i4 + uu + 1) * kVW + j0);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float x0 = uu == 0 ? xv[p].x : xv[p].z;
+        const float x1 = uu == 0 ? xv[p].y : xv[p].w;
+        const float2 a01 = fadd2(make_float2(x0, x0), make_float2(l0.x, l0.y));
+        const float2 a23 = fadd2(make_float2(x0, x0), make_float2(l0.z, l0.w));
+        const float2 b01 = fadd2(make_float2(x1, x1), make_float2(l1.x, l1.y));
+        const float2 b23 = fadd2(make_float2(x1, x1), make_float2(l1.z, l1.w));
+        m[p][0] = fmax3(m[p][0], a01.x, b01.x);
+        m[p][1] = fmax3(m[p][1], a01.y, b01.y);
+        m[p][2] = fmax3(m[p][2], a23.x, b23.x);
+        m[p][3] = fmax3(m[p][3], a23.y, b23.y);
+      }
+    }
+  }
+}
+
+// W warps per block, P pairs per warp. All-models items without model sets
+// are (group of W * P sequences, model): every pair of the block has the
+// model whose matrix the block staged. Labelled pairs and model sets: one
+// pair per block (W = P = 1).
+template <int W, int P, bool ALL>
 __global__ void __launch_bounds__(W * 32) hmm_viterbi_scores_wide(VitLaunch a) {
   extern __shared__ __align__(16) float vsm[];
   float* lA = vsm;                                  // [128][128]
-  float* xs = vsm + kVW * kVW;                      // [W][2][128]
+  float* xs = vsm + kVW * kVW;                      // [W][P][2][128]
   __shared__ int item_s;
+  __shared__ int last_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j0 = 4 * lane;
   const int M = a.seq.M, S = a.seq.S;
   const int span = a.seq.span;
   const bool param_bad = (__ldcg(a.status) & HMM_STATUS_PARAM) != 0;
-  // W > 1 only for all-models items without model sets (one model per block)
+  float* xw = xs + warp * P * 2 * kVW;
 
   for (;;) {
     __syncthreads();  // the previous item's readers of lA are done
@@ -113,85 +154,105 @@ __global__ void __launch_bounds__(W * 32) hmm_viterbi_scores_wide(VitLaunch a) {
     if (item >= a.n_items_score) break;
     const int g = ALL ? item / span : item;
     const int kr = ALL ? item % span : 0;
-    const int pos = g * W + warp;
-    const bool has = pos < S;
-    const int s = has ? a.seq.order[pos] : 0;
-    const int T = has ? a.seq.seqlen[s] : 0;
+    int s[P], Tn[P];
+    bool has[P], bad[P], dead[P];
+    long long Q[P];
+    float x[P][4];
+    float4 bn[P];
+    int on[P], o2[P], err[P];
+    const int32_t* o[P];
     int k = kr;
-    if (!ALL && has && T >= 0) k = a.seq.model_of_seq[s];
-    if (ALL && has && T >= 0 && a.seq.model_base) k += a.seq.model_base[s];
-    stage_la(lA, a.mod.Ap, k, W * 32);  // (W > 1: every warp of the block has model kr)
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int pos = (g * W + warp) * P + p;
+      has[p] = pos < S;
+      s[p] = has[p] ? a.seq.order[pos] : 0;
+      const int T = has[p] ? a.seq.seqlen[s[p]] : 0;
+      if (P == 1) {  // one pair: its own model
+        if (!ALL && has[p] && T >= 0) k = a.seq.model_of_seq[s[p]];
+        if (ALL && has[p] && T >= 0 && a.seq.model_base) k += a.seq.model_base[s[p]];
+      }
+      bad[p] = T < 0 || param_bad;
+      Tn[p] = T < 0 ? 0 : T;
+      dead[p] = false;
+      Q[p] = 0;
+      err[p] = 0;
+    }
+    stage_la(lA, a.mod.Ap, k, W * 32);
     __syncthreads();
 
-    const bool bad_seq = T < 0;
-    const int Tn = bad_seq ? 0 : T;
     const float* Bk = a.mod.Btp + (size_t)k * M * kVW + j0;
-    const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
-    float x[4];
-    long long Q = 0;
-    bool dead = false, bad = bad_seq || param_bad;
-    int err = 0;
-    {
-      int o0 = Tn > 0 ? __ldg(o) : 0;
-      if ((unsigned)o0 >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; o0 = 0; }
+    int Tmax = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      Tmax = max(Tmax, Tn[p]);
+      o[p] = a.seq.symbols + (has[p] && Tn[p] > 0 ? a.seq.offsets[s[p]] : 0);
+      int o0 = Tn[p] > 0 ? __ldg(o[p]) : 0;
+      if ((unsigned)o0 >= (unsigned)M) { bad[p] = true; err[p] |= HMM_STATUS_SYMBOL; o0 = 0; }
       const float4 b = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)o0 * kVW));
       const float4 pv = __ldg(reinterpret_cast<const float4*>(a.mod.pip + (size_t)k * kVW + j0));
-      x[0] = pv.x + b.x; x[1] = pv.y + b.y; x[2] = pv.z + b.z; x[3] = pv.w + b.w;
-      if (!shift_max(x, Q, Tn > 0 && !bad)) dead = true;
+      x[p][0] = pv.x + b.x; x[p][1] = pv.y + b.y; x[p][2] = pv.z + b.z; x[p][3] = pv.w + b.w;
+      if (!shift_max(x[p], Q[p], Tn[p] > 0 && !bad[p])) dead[p] = true;
+      on[p] = 0;
+      if (1 < Tn[p]) {
+        on[p] = __ldg(o[p] + 1);
+        if ((unsigned)on[p] >= (unsigned)M) { bad[p] = true; err[p] |= HMM_STATUS_SYMBOL; on[p] = 0; }
+      }
+      bn[p] = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on[p] * kVW));
+      o2[p] = (2 < Tn[p]) ? __ldg(o[p] + 2) : 0;
     }
-    int on = 0;
-    if (1 < Tn) {
-      on = __ldg(o + 1);
-      if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
-    }
-    float4 bn = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on * kVW));
-    int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
 
-    for (int t = 1; t < Tn; ++t) {  // warp-uniform: one pair per warp
-      const bool act = !dead && !bad;
-      float* xb = xs + (warp * 2 + (t & 1)) * kVW;
-      *reinterpret_cast<float4*>(xb + j0) = make_float4(x[0], x[1], x[2], x[3]);
-      __syncwarp();
-      float m[4];
-      int arg[4];
-      maxplus_smem<false>(xb, lA, j0, m, arg);
-      const float4 b = bn;
-      if (t + 1 < Tn) {
-        on = o2;
-        if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
-        bn = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on * kVW));
-        if (t + 2 < Tn) o2 = __ldg(o + t + 2);
-      }
-      m[0] += b.x; m[1] += b.y; m[2] += b.z; m[3] += b.w;
-      const long long Qold = Q;
-      if (!shift_max(m, Q, act)) dead = true;
-      if (act && !dead) {
+    for (int t = 1; t < Tmax; ++t) {  // warp-uniform: the longest of the warp's pairs
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) x[jj] = m[jj];
-      } else {
-        Q = Qold;
+      for (int p = 0; p < P; ++p)
+        *reinterpret_cast<float4*>(xw + (p * 2 + (t & 1)) * kVW + j0) =
+            make_float4(x[p][0], x[p][1], x[p][2], x[p][3]);
+      __syncwarp();
+      float m[P][4];
+      maxplus_smem_multi<P>(xw + (t & 1) * kVW, lA, j0, m);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const bool act = t < Tn[p] && !dead[p] && !bad[p];
+        const float4 b = bn[p];
+        if (t + 1 < Tn[p]) {
+          on[p] = o2[p];
+          if ((unsigned)on[p] >= (unsigned)M) { bad[p] = true; err[p] |= HMM_STATUS_SYMBOL; on[p] = 0; }
+          bn[p] = __ldg(reinterpret_cast<const float4*>(Bk + (size_t)on[p] * kVW));
+          if (t + 2 < Tn[p]) o2[p] = __ldg(o[p] + t + 2);
+        }
+        m[p][0] += b.x; m[p][1] += b.y; m[p][2] += b.z; m[p][3] += b.w;
+        const long long Qold = Q[p];
+        if (!shift_max(m[p], Q[p], act)) dead[p] = true;
+        if (act && !dead[p]) {
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) x[p][jj] = m[p][jj];
+        } else {
+          Q[p] = Qold;
+        }
       }
     }
-    const float fm = group_max<32>(fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])));
-    if (has && lane == 0) {
-      float out;
-      if (bad) {
-        out = nan_w();
-        if (err) set_status(a.status, err);
-      } else if (Tn == 0) {
-        out = 0.f;
-      } else if (dead) {
-        out = -INFINITY;
-      } else {
-        out = (float)((double)fm + (double)Q * (1.0 / kViterbiQuant));
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const float fm = group_max<32>(fmaxf(fmaxf(x[p][0], x[p][1]), fmaxf(x[p][2], x[p][3])));
+      if (has[p] && lane == 0) {
+        float out;
+        if (bad[p]) {
+          out = nan_w();
+          if (err[p]) set_status(a.status, err[p]);
+        } else if (Tn[p] == 0) {
+          out = 0.f;
+        } else if (dead[p]) {
+          out = -INFINITY;
+        } else {
+          out = (float)((double)fm + (double)Q[p] * (1.0 / kViterbiQuant));
+        }
+        a.score[ALL ? (size_t)s[p] * span + kr : (size_t)s[p]] = out;
+        if (!ALL && a.best) a.best[s[p]] = bad[p] ? -1 : k;
       }
-      a.score[ALL ? (size_t)s * span + kr : (size_t)s] = out;
-      if (!ALL && a.best) a.best[s] = bad ? -1 : k;
     }
 
     if (ALL && a.best) {
       __syncthreads();
-      __shared__ int last_s;
       if (threadIdx.x == 0) {
         __threadfence();
         last_s = atomicAdd(a.done + g, 1) == span - 1;
@@ -199,16 +260,19 @@ __global__ void __launch_bounds__(W * 32) hmm_viterbi_scores_wide(VitLaunch a) {
       __syncthreads();
       if (last_s) {
         __threadfence();
-        if (has && lane == 0) {
-          const float* row = a.score + (size_t)s * span;
-          float best = __ldcg(row);
-          int barg = isnan(best) ? -1 : 0;
-          for (int kk = 1; kk < span; ++kk) {
-            const float v = __ldcg(row + kk);
-            if (isnan(v)) barg = -1;
-            else if (barg >= 0 && v > best) { best = v; barg = kk; }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          if (has[p] && lane == 0) {
+            const float* row = a.score + (size_t)s[p] * span;
+            float best = __ldcg(row);
+            int barg = isnan(best) ? -1 : 0;
+            for (int kk = 1; kk < span; ++kk) {
+              const float v = __ldcg(row + kk);
+              if (isnan(v)) barg = -1;
+              else if (barg >= 0 && v > best) { best = v; barg = kk; }
+            }
+            a.best[s[p]] = barg;
           }
-          a.best[s] = barg;
         }
       }
     }
@@ -364,12 +428,14 @@ __global__ void __launch_bounds__(32) hmm_viterbi_paths_wide(VitLaunch a) {
   }
 }
 
-size_t viterbi_wide_smem(int warps) { return ((size_t)kVW * kVW + (size_t)warps * 2 * kVW) * 4; }
+size_t viterbi_wide_smem(int warps, int pairs) {
+  return ((size_t)kVW * kVW + (size_t)warps * pairs * 2 * kVW) * 4;
+}
 
 template <typename Kern>
-static cudaError_t launch_vw(Kern kern, int warps, int n_items, const VitLaunch& a,
+static cudaError_t launch_vw(Kern kern, int warps, int pairs, int n_items, const VitLaunch& a,
                              cudaStream_t st) {
-  const size_t smem = viterbi_wide_smem(warps);
+  const size_t smem = viterbi_wide_smem(warps, pairs);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
@@ -383,21 +449,20 @@ static cudaError_t launch_vw(Kern kern, int warps, int n_items, const VitLaunch&
   return cudaGetLastError();
 }
 
-// Groups of sequences per all-models item (one model per block): 4 warps.
-int viterbi_wide_group(const VitLaunch& a) {
-  return (a.seq.model_of_seq == nullptr && a.seq.model_base == nullptr) ? 4 : 1;
-}
+// Sequences per all-models score item (4 warps x 4 pairs sharing one model's
+// matrix); 1 for labelled pairs and model sets.
+int viterbi_wide_group(bool all, bool sets) { return (all && !sets) ? 16 : 1; }
 
 cudaError_t launch_viterbi_scores_wide(const VitLaunch& a, cudaStream_t st) {
   if (a.seq.model_of_seq != nullptr)
-    return launch_vw(hmm_viterbi_scores_wide<1, false>, 1, a.n_items_score, a, st);
-  if (viterbi_wide_group(a) == 4)
-    return launch_vw(hmm_viterbi_scores_wide<4, true>, 4, a.n_items_score, a, st);
-  return launch_vw(hmm_viterbi_scores_wide<1, true>, 1, a.n_items_score, a, st);
+    return launch_vw(hmm_viterbi_scores_wide<1, 1, false>, 1, 1, a.n_items_score, a, st);
+  if (a.seq.model_base == nullptr)
+    return launch_vw(hmm_viterbi_scores_wide<4, 4, true>, 4, 4, a.n_items_score, a, st);
+  return launch_vw(hmm_viterbi_scores_wide<1, 1, true>, 1, 1, a.n_items_score, a, st);
 }
 
 cudaError_t launch_viterbi_paths_wide(const VitLaunch& a, cudaStream_t st) {
-  return launch_vw(hmm_viterbi_paths_wide, 1, a.n_items_path, a, st);
+  return launch_vw(hmm_viterbi_paths_wide, 1, 1, a.n_items_path, a, st);
 }
 
 }  // namespace hmmgb

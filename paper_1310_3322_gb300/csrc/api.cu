@@ -365,7 +365,7 @@ static SeqArgs seq_args(const hmm_dims_t& d, const hmm_seqs_t& q, const WsLayout
   a.span = span_of(q, d);
   a.seqlen = at<int32_t>(ws, L.seqlen);
   a.order = at<int32_t>(ws, L.order);
-  a.S = q.S; a.K = d.K; a.M = d.M;
+  a.S = q.S; a.K = d.K; a.M = d.M; a.N = d.N;
   return a;
 }
 

@@ -28,7 +28,7 @@
 
 namespace hmmgb {
 
-template <int NP, int G, bool ALL>
+template <int NP, int G, bool ALL, int NV = NP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 hmm_forward_simt(FwdLaunch a) {
   constexpr int J = NP / G;
@@ -115,7 +115,7 @@ hmm_forward_simt(FwdLaunch a) {
       store_vec<J>(xb + j0, x);
       __syncwarp();
       float nx[J];
-      matvec_cols<NP, J>(xb, a2, nx);
+      matvec_cols<NP, J, NV>(xb, a2, nx);
       float b[J];
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) b[jj] = bn[jj];
@@ -188,10 +188,10 @@ hmm_forward_simt(FwdLaunch a) {
 // --------------------------------------------------------------------------
 // dispatch
 // --------------------------------------------------------------------------
-template <int NP, int G>
+template <int NP, int G, int NV = NP>
 static cudaError_t launch_fwd_t(const FwdLaunch& a, cudaStream_t st) {
   const bool all = a.seq.model_of_seq == nullptr;
-  auto kern = all ? hmm_forward_simt<NP, G, true> : hmm_forward_simt<NP, G, false>;
+  auto kern = all ? hmm_forward_simt<NP, G, true, NV> : hmm_forward_simt<NP, G, false, NV>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, 0);
   if (err != cudaSuccess) return err;

@@ -63,6 +63,7 @@ struct SeqArgs {
   int S;
   int K;
   int M;
+  int N;                        // states (the padded count is the kernel's NP)
 };
 
 struct ModelArgs {
@@ -222,10 +223,15 @@ __device__ __forceinline__ float tree_max(const float (&x)[J]) {
 // floats, 16-byte aligned), a2[i2][jj] = (a_{2 i2, j}, a_{2 i2 + 1, j}) the
 // register-resident column slice. Packed FP32x2 FMAs over pairs of rows; NS
 // independent accumulator sets keep at least four FMA chains in flight.
-template <int NP, int J>
+// NV < NP (states NV .. NP-1 are padding: x and a are exactly 0 there) skips
+// the padded row pairs and, when one lane owns every column (J == NP), the
+// padded columns: the skipped terms are exact zeros, so the sums are bitwise
+// those of the full product.
+template <int NP, int J, int NV = NP>
 __device__ __forceinline__ void matvec_cols(const float* xb, const float2 (&a2)[NP / 2][J],
                                             float (&out)[J]) {
   constexpr int NS = (J >= 4) ? 1 : (4 / J < NP / 4 ? 4 / J : NP / 4);
+  constexpr int JC = (J == NP) ? NV : J;  // columns computed
   float2 acc[NS][J];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -233,13 +239,16 @@ __device__ __forceinline__ void matvec_cols(const float* xb, const float2 (&a2)[
     for (int jj = 0; jj < J; ++jj) acc[s][jj] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < NP / 4; ++q) {
+    if (4 * q >= NV) continue;
     const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
     const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
     const int s = q % NS;
 #pragma unroll
-    for (int jj = 0; jj < J; ++jj) acc[s][jj] = __ffma2_rn(lo, a2[2 * q][jj], acc[s][jj]);
+    for (int jj = 0; jj < JC; ++jj) acc[s][jj] = __ffma2_rn(lo, a2[2 * q][jj], acc[s][jj]);
+    if (4 * q + 2 < NV) {
 #pragma unroll
-    for (int jj = 0; jj < J; ++jj) acc[s][jj] = __ffma2_rn(hi, a2[2 * q + 1][jj], acc[s][jj]);
+      for (int jj = 0; jj < JC; ++jj) acc[s][jj] = __ffma2_rn(hi, a2[2 * q + 1][jj], acc[s][jj]);
+    }
   }
 #pragma unroll
   for (int jj = 0; jj < J; ++jj) {
@@ -251,11 +260,13 @@ __device__ __forceinline__ void matvec_cols(const float* xb, const float2 (&a2)[
 }
 
 // out[jj] = max_i (x_i + la_{i, j0+jj}) (max-plus product; exact, so the
-// grouping into NS partial maxima does not change the result).
-template <int NP, int J>
+// grouping into NS partial maxima does not change the result). NV as in
+// matvec_cols (padded entries are -inf and never win).
+template <int NP, int J, int NV = NP>
 __device__ __forceinline__ void maxplus_cols(const float* xb, const float2 (&a2)[NP / 2][J],
                                              float (&out)[J]) {
   constexpr int NS = (J >= 4) ? 1 : (4 / J < NP / 4 ? 4 / J : NP / 4);
+  constexpr int JC = (J == NP) ? NV : J;
   float m[NS][J];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -263,18 +274,21 @@ __device__ __forceinline__ void maxplus_cols(const float* xb, const float2 (&a2)
     for (int jj = 0; jj < J; ++jj) m[s][jj] = -INFINITY;
 #pragma unroll
   for (int q = 0; q < NP / 4; ++q) {
+    if (4 * q >= NV) continue;
     const float4 xv = *reinterpret_cast<const float4*>(xb + 4 * q);
     const float2 lo = make_float2(xv.x, xv.y), hi = make_float2(xv.z, xv.w);
     const int s = q % NS;
 #pragma unroll
-    for (int jj = 0; jj < J; ++jj) {
+    for (int jj = 0; jj < JC; ++jj) {
       const float2 v = __fadd2_rn(lo, a2[2 * q][jj]);
       m[s][jj] = fmax3(m[s][jj], v.x, v.y);
     }
+    if (4 * q + 2 < NV) {
 #pragma unroll
-    for (int jj = 0; jj < J; ++jj) {
-      const float2 w = __fadd2_rn(hi, a2[2 * q + 1][jj]);
-      m[s][jj] = fmax3(m[s][jj], w.x, w.y);
+      for (int jj = 0; jj < JC; ++jj) {
+        const float2 w = __fadd2_rn(hi, a2[2 * q + 1][jj]);
+        m[s][jj] = fmax3(m[s][jj], w.x, w.y);
+      }
     }
   }
 #pragma unroll

@@ -124,3 +124,33 @@ def test_model_set_out_of_range_is_flagged():
     P = oracle.params(w.pi[:6], w.A[:6], w.B[:6])
     rll, _, _ = oracle.forward(P, w.symbols, w.offsets, w.lengths, nthreads=8)
     assert np.all(np.abs(ll[ok] - rll[ok]) <= ll_tol(w.lengths[ok])[:, None])
+
+
+def test_padded_state_skipping_is_bitwise_exact():
+    """At 8 padded states with one lane per pair the Viterbi score kernel
+    skips the padded rows and columns for N = 5..7 (their terms are -inf): an
+    N = 5 model and the same model zero-padded to N = 8 (which runs the full
+    kernel) give bit-identical scores; the forward likewise."""
+    import torch
+    w = synth.make_workload("teamwork", n_seqs=700, lengths=("uniform", 0, 120))
+    pad = lambda x, shape: np.pad(x, [(0, s - d) for s, d in zip(shape, x.shape)])
+    K, M = w.K, w.M
+    p5 = [torch.from_numpy(x).cuda() for x in (w.pi, w.A, w.B)]
+    p8 = [torch.from_numpy(np.ascontiguousarray(pad(x, sh))).cuda()
+          for x, sh in ((w.pi, (K, 8)), (w.A, (K, 8, 8)), (w.B, (K, 8, M)))]
+    seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device="cuda")
+    for op in (hmm.HMM_OP_FORWARD, hmm.HMM_OP_VITERBI):
+        hmm.hmm_set_tuning(op, 8, 1)
+    try:
+        l5, a5 = hmm.hmm_forward(*p5, seqs)
+        l8, a8 = hmm.hmm_forward(*p8, seqs)
+        s5, b5, _ = hmm.hmm_viterbi(*p5, seqs, want_path=False)
+        s8, b8, _ = hmm.hmm_viterbi(*p8, seqs, want_path=False)
+    finally:
+        for op in (hmm.HMM_OP_FORWARD, hmm.HMM_OP_VITERBI):
+            hmm.hmm_set_tuning(op, 8, 0)
+    assert torch.equal(l5, l8) and torch.equal(a5, a8)
+    assert torch.equal(s5, s8) and torch.equal(b5, b8)
+    P = oracle.params(w.pi, w.A, w.B)
+    rll, _, _ = oracle.forward(P, w.symbols, w.offsets, w.lengths, nthreads=8)
+    assert np.all(np.abs(l5.cpu().numpy() - rll) <= ll_tol(w.lengths)[:, None])

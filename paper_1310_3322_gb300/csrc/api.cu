@@ -184,6 +184,11 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
   L.order = off; off = align256(off + S * 4);
   L.seqlen = off; off = align256(off + S * 4);
   L.done = off; off = align256(off + S * 4);
+  {
+    const size_t nb = (size_t)plan_blocks((int)S);
+    L.phist = off; off = align256(off + nb * kLenBuckets * 4);
+    L.punits = off; off = align256(off + 2 * nb * 8);
+  }
   if (op == HMM_OP_VITERBI) {
     L.bpoff = off; off = align256(off + S * 8);
     L.best = off; off = align256(off + S * 4);
@@ -341,6 +346,8 @@ static SetupArgs setup_args(const hmm_dims_t& d, const hmm_seqs_t& q, const WsLa
                             int log_mode) {
   SetupArgs s;
   memset(&s, 0, sizeof(s));
+  s.phist = at<int32_t>(ws, L.phist);
+  s.punits = at<int64_t>(ws, L.punits);
   s.K = d.K; s.N = d.N; s.M = d.M; s.NP = L.NP; s.S = q.S;
   s.total_obs = q.total_obs;
   s.max_len = q.max_len;

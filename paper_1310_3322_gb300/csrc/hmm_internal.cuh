@@ -30,6 +30,7 @@ static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
 struct WsLayout {
   size_t order, seqlen, done, bpoff, best, pip, Ap, Btp, bp, partial, red1, total;
+  size_t phist, punits;  // setup plan over many blocks
   int NP;
   int64_t bp_cap;      // bytes of backpointer storage
   int64_t slots;       // adjoint partial slots
@@ -96,6 +97,8 @@ struct SetupArgs {
   int32_t* done;
   int64_t* bpoff;
   int64_t bp_cap_rows;   // rows of NP bytes available for backpointers
+  int32_t* phist;        // S > 4096: per-plan-block length-bucket counts [nb][1024]
+  int64_t* punits;       // S > 4096: per-plan-block prefix units [2][nb]
   int scan_chunk;        // > 0: chunk offsets of the parallel-in-time forward
   int64_t* coff;         // [S + 1] exclusive prefix of ceil((T_s - 1) / scan_chunk)
   int64_t coff_cap;      // chunk slots available (sequences past it are rejected)
@@ -638,6 +641,7 @@ cudaError_t launch_reduce(const ReduceLaunch& a, cudaStream_t st);
 
 // Instantiated lane counts per (op, NP); the first entry is the default.
 int candidates(int op, int NP, int* out, int cap);
+int plan_blocks(int S);  // plan blocks of the setup for S sequences
 size_t forward_ws_sequential(const hmm_dims_t& d, const hmm_seqs_t& q);
 int num_sms();
 

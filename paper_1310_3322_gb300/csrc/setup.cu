@@ -260,11 +260,175 @@ __global__ void __launch_bounds__(kPlanThreads) setup_kernel(SetupArgs a) {
     prep_blocks(a, blockIdx.x - 1, gridDim.x - 1);
 }
 
+// ---------------------------------------------------------------------------
+// the same plan over many blocks (S > kPlanSingleMax): one block per
+// kPlanBlockSeqs consecutive sequences validates them and counts their
+// length buckets and prefix units (kernel A, beside the table blocks); one
+// block turns the per-block counts into per-block starting offsets (kernel B);
+// every plan block then places its sequences and writes its prefix sums
+// (kernel C). Same outputs as the single block (within a length bucket the
+// order of sequences is the atomics' order in both).
+// ---------------------------------------------------------------------------
+constexpr int kPlanPer = 4;                                   // sequences per thread
+constexpr int kPlanBlockSeqs = kPlanPer * kPlanThreads;      // 4096 per block
+constexpr int kPlanSingleMax = 4096;
+
+int plan_blocks(int S) { return (S + kPlanBlockSeqs - 1) / kPlanBlockSeqs; }
+
+__global__ void __launch_bounds__(kPlanThreads) plan_mb_a_kernel(SetupArgs a, int nb) {
+  if ((int)blockIdx.x >= nb) {
+    prep_blocks(a, blockIdx.x - nb, gridDim.x - nb);
+    return;
+  }
+  __shared__ int hist[kLenBuckets];
+  __shared__ long long red[2][32];
+  const int tid = threadIdx.x, b = blockIdx.x;
+  hist[tid] = 0;
+  for (int i = b * kPlanThreads + tid; i < a.ndone; i += nb * kPlanThreads) a.done[i] = 0;
+  int Ts[kPlanPer];
+  int bad = 0;
+#pragma unroll
+  for (int i = 0; i < kPlanPer; ++i) {  // loads first, none behind a test
+    const int s = b * kPlanBlockSeqs + tid + i * kPlanThreads;
+    const bool in = s < a.S;
+    const int T = in ? __ldg(a.lengths + s) : 0;
+    const long long off = in ? __ldg(a.offsets + s) : 0;
+    const int mk = (in && a.model_of_seq) ? __ldg(a.model_of_seq + s) : 0;
+    const int mb = (in && a.model_base) ? __ldg(a.model_base + s) : 0;
+    bool ok = T >= 0 && T <= a.max_len && off >= 0 && off <= a.total_obs - (long long)T;
+    if (a.model_of_seq) ok = ok && mk >= 0 && mk < a.K;
+    if (a.model_base) ok = ok && mb >= 0 && mb <= a.K - a.span;
+    Ts[i] = in ? (ok ? T : -1) : 0;
+    if (in && !ok) bad = 1;
+  }
+  long long u0 = 0, u1 = 0;
+#pragma unroll
+  for (int i = 0; i < kPlanPer; ++i) {
+    const int s = b * kPlanBlockSeqs + tid + i * kPlanThreads;
+    if (s < a.S) {
+      a.seqlen[s] = Ts[i];
+      if (a.want_bpoff) u0 += prefix_units(a, Ts[i], 0);
+      if (a.scan_chunk > 0) u1 += prefix_units(a, Ts[i], 1);
+    }
+  }
+  if (bad) set_status(a.status, HMM_STATUS_SEQ);
+  __syncthreads();  // hist cleared
+  if (!a.skip_order) {
+#pragma unroll
+    for (int i = 0; i < kPlanPer; ++i) {
+      const int s = b * kPlanBlockSeqs + tid + i * kPlanThreads;
+      if (s < a.S) atomicAdd(&hist[kLenBuckets - 1 - length_bucket(max(Ts[i], 0))], 1);
+    }
+  }
+  // block sums of the prefix units
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    u0 += __shfl_xor_sync(HMM_FULL_MASK, u0, o);
+    u1 += __shfl_xor_sync(HMM_FULL_MASK, u1, o);
+  }
+  if ((tid & 31) == 0) { red[0][tid >> 5] = u0; red[1][tid >> 5] = u1; }
+  __syncthreads();
+  if (tid < 2) {
+    long long t = 0;
+    for (int w = 0; w < kPlanThreads / 32; ++w) t += red[tid][w];
+    a.punits[(size_t)tid * nb + b] = t;
+  }
+  if (!a.skip_order) a.phist[(size_t)b * kLenBuckets + tid] = hist[tid];
+}
+
+__global__ void __launch_bounds__(kPlanThreads) plan_mb_b_kernel(SetupArgs a, int nb) {
+  __shared__ int itmp[32];
+  const int tid = threadIdx.x;
+  if (!a.skip_order) {  // thread = bucket: per-block starting offsets, in place
+    int tot = 0;
+    for (int b = 0; b < nb; ++b) tot += a.phist[(size_t)b * kLenBuckets + tid];
+    int base = block_exclusive_scan<int>(tot, itmp, nullptr);
+    for (int b = 0; b < nb; ++b) {
+      int* h = a.phist + (size_t)b * kLenBuckets + tid;
+      const int v = *h;
+      *h = base;
+      base += v;
+    }
+  }
+  if (tid < 2) {  // per-block offsets of the prefix units (blocks in sequence order)
+    const int kind = tid;
+    if (kind == 0 ? !a.want_bpoff : a.scan_chunk <= 0) return;
+    long long run = 0;
+    for (int b = 0; b < nb; ++b) {
+      int64_t* u = a.punits + (size_t)kind * nb + b;
+      const long long v = *u;
+      *u = run;
+      run += v;
+    }
+    if (kind == 1) a.coff[a.S] = run < a.coff_cap ? run : a.coff_cap;
+  }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) plan_mb_c_kernel(SetupArgs a, int nb) {
+  __shared__ int hist[kLenBuckets];
+  __shared__ long long ltmp[32];
+  const int tid = threadIdx.x, b = blockIdx.x;
+  if (!a.skip_order) {
+    hist[tid] = a.phist[(size_t)b * kLenBuckets + tid];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPlanPer; ++i) {
+      const int s = b * kPlanBlockSeqs + tid + i * kPlanThreads;
+      if (s < a.S) {
+        const int T = a.seqlen[s];
+        const int pos = atomicAdd(&hist[kLenBuckets - 1 - length_bucket(max(T, 0))], 1);
+        a.order[pos] = s;
+      }
+    }
+  }
+  for (int kind = 0; kind < 2; ++kind) {
+    if (kind == 0 ? !a.want_bpoff : a.scan_chunk <= 0) continue;
+    int64_t* out = kind == 0 ? a.bpoff : a.coff;
+    const long long cap = kind == 0 ? a.bp_cap_rows : a.coff_cap;
+    const int s0 = b * kPlanBlockSeqs + tid * kPlanPer;  // a contiguous run per thread
+    long long u[kPlanPer];
+    long long local = 0;
+#pragma unroll
+    for (int i = 0; i < kPlanPer; ++i) {
+      u[i] = s0 + i < a.S ? prefix_units(a, a.seqlen[s0 + i], kind) : 0;
+      local += u[i];
+    }
+    long long run = a.punits[(size_t)kind * nb + b] +
+                    block_exclusive_scan<long long>(local, ltmp, nullptr);
+    bool over = false;
+#pragma unroll
+    for (int i = 0; i < kPlanPer; ++i) {
+      const int s = s0 + i;
+      if (s < a.S) {
+        out[s] = run;
+        if (u[i] > 0 && run + u[i] > cap) {  // storage exhausted
+          a.seqlen[s] = -1;
+          over = true;
+        }
+        run += u[i];
+      }
+    }
+    if (over) set_status(a.status, HMM_STATUS_SEQ);
+    __syncthreads();  // seqlen rewrites settle before the next kind reads them
+  }
+}
+
 cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st) {
   const long long work = (long long)a.K * a.NP * (1 + a.NP + a.M);
   int nprep = (int)((work + kPlanThreads * 4 - 1) / (kPlanThreads * 4));
   nprep = max(1, min(nprep, 2 * num_sms()));
-  setup_kernel<<<1 + nprep, kPlanThreads, 0, st>>>(a);
+  if (a.S <= kPlanSingleMax || !a.phist || !a.punits) {
+    setup_kernel<<<1 + nprep, kPlanThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  const int nb = plan_blocks(a.S);
+  plan_mb_a_kernel<<<nb + nprep, kPlanThreads, 0, st>>>(a, nb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.skip_order && !a.want_bpoff && a.scan_chunk <= 0) return cudaSuccess;
+  plan_mb_b_kernel<<<1, kPlanThreads, 0, st>>>(a, nb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  plan_mb_c_kernel<<<nb, kPlanThreads, 0, st>>>(a, nb);
   return cudaGetLastError();
 }
 

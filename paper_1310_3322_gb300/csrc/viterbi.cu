@@ -390,15 +390,6 @@ static cudaError_t launch_persistent(Kern kern, int n_items, const VitLaunch& a,
 
 template <int NP, int G, int NV = NP>
 static cudaError_t launch_vs_t(const VitLaunch& a, cudaStream_t st) {
-  // one lane per pair at 8 padded states: padded rows and columns skipped
-  // (measured on 16 384 sequences x 24 models at N = 5: 192 -> 173 us; the
-  // same skipping in the forward kernel measured slower, 181 -> 192 us, and
-  // is not dispatched there)
-  if constexpr (NP == 8 && G == 1 && NV == NP) {
-    if (a.seq.N == 5) return launch_vs_t<8, 1, 5>(a, st);
-    if (a.seq.N == 6) return launch_vs_t<8, 1, 6>(a, st);
-    if (a.seq.N == 7) return launch_vs_t<8, 1, 7>(a, st);
-  }
   const bool all = a.seq.model_of_seq == nullptr;
   if (all) return launch_persistent(hmm_viterbi_scores<NP, G, true, NV>, a.n_items_score, a, st);
   return launch_persistent(hmm_viterbi_scores<NP, G, false, NV>, a.n_items_score, a, st);

@@ -126,11 +126,11 @@ def test_model_set_out_of_range_is_flagged():
     assert np.all(np.abs(ll[ok] - rll[ok]) <= ll_tol(w.lengths[ok])[:, None])
 
 
-def test_padded_state_skipping_is_bitwise_exact():
-    """At 8 padded states with one lane per pair the Viterbi score kernel
-    skips the padded rows and columns for N = 5..7 (their terms are -inf): an
-    N = 5 model and the same model zero-padded to N = 8 (which runs the full
-    kernel) give bit-identical scores; the forward likewise."""
+def test_padding_is_invisible():
+    """An N = 5 model and the same model zero-padded to N = 8 (explicit zero
+    rows and columns, which the library's own padding to 8 states also
+    produces) give bit-identical forward and Viterbi outputs at one lane per
+    pair: padded states contribute exact zeros (forward) and -inf (Viterbi)."""
     import torch
     w = synth.make_workload("teamwork", n_seqs=700, lengths=("uniform", 0, 120))
     pad = lambda x, shape: np.pad(x, [(0, s - d) for s, d in zip(shape, x.shape)])

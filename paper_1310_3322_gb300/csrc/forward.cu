@@ -188,10 +188,10 @@ hmm_forward_simt(FwdLaunch a) {
 // --------------------------------------------------------------------------
 // dispatch
 // --------------------------------------------------------------------------
-template <int NP, int G, int NV = NP>
+template <int NP, int G>
 static cudaError_t launch_fwd_t(const FwdLaunch& a, cudaStream_t st) {
   const bool all = a.seq.model_of_seq == nullptr;
-  auto kern = all ? hmm_forward_simt<NP, G, true, NV> : hmm_forward_simt<NP, G, false, NV>;
+  auto kern = all ? hmm_forward_simt<NP, G, true> : hmm_forward_simt<NP, G, false>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, 0);
   if (err != cudaSuccess) return err;

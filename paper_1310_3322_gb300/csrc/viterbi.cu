@@ -388,11 +388,11 @@ static cudaError_t launch_persistent(Kern kern, int n_items, const VitLaunch& a,
   return cudaGetLastError();
 }
 
-template <int NP, int G, int NV = NP>
+template <int NP, int G>
 static cudaError_t launch_vs_t(const VitLaunch& a, cudaStream_t st) {
   const bool all = a.seq.model_of_seq == nullptr;
-  if (all) return launch_persistent(hmm_viterbi_scores<NP, G, true, NV>, a.n_items_score, a, st);
-  return launch_persistent(hmm_viterbi_scores<NP, G, false, NV>, a.n_items_score, a, st);
+  if (all) return launch_persistent(hmm_viterbi_scores<NP, G, true>, a.n_items_score, a, st);
+  return launch_persistent(hmm_viterbi_scores<NP, G, false>, a.n_items_score, a, st);
 }
 
 template <int NP, int G>

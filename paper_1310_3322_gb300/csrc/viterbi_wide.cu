@@ -449,10 +449,6 @@ static cudaError_t launch_vw(Kern kern, int warps, int pairs, int n_items, const
   return cudaGetLastError();
 }
 
-// Sequences per all-models score item (4 warps x 4 pairs sharing one model's
-// matrix); 1 for labelled pairs and model sets.
-int viterbi_wide_group(bool all, bool sets) { return (all && !sets) ? 16 : 1; }
-
 cudaError_t launch_viterbi_scores_wide(const VitLaunch& a, cudaStream_t st) {
   if (a.seq.model_of_seq != nullptr)
     return launch_vw(hmm_viterbi_scores_wide<1, 1, false>, 1, 1, a.n_items_score, a, st);

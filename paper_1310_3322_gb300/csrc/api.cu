@@ -234,6 +234,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.w_rtot = rtot;
     L.bpoff = off; off = align256(off + S * 8);
     L.wimg = off; off = align256(off + (size_t)d.K * NP * NP * 2);
+    L.w_img2 = off; off = align256(off + (size_t)d.K * NP * NP * 2);
     const size_t rowb = (size_t)(slots * rtot) * NP * 4;
     L.w_X = off; off = align256(off + rowb);
     L.w_Bh = off; off = align256(off + rowb);
@@ -524,21 +525,19 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   f.xs = at<float>(ws, L.w_X);
   f.roff = at<int64_t>(ws, L.bpoff);
   f.rtot = L.w_rtot;
-  {
-    Timed tm(T_FORWARD, st);
-    e = launch_forward_wide(NP, f, st, 0);
-    tm.stop();
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");
-  f.queue = &at<WsHeader>(ws, 0)->queue[1];
-  f.xs = at<float>(ws, L.w_Bh);
-  f.xe = at<int32_t>(ws, L.w_xe);
+  // the backward pass: own queue, A image and row buffers
+  MmaWideLaunch b = f;
+  b.queue = &at<WsHeader>(ws, 0)->queue[1];
+  b.img = at<uint8_t>(ws, L.w_img2);
+  b.xs = at<float>(ws, L.w_Bh);
+  b.xe = at<int32_t>(ws, L.w_xe);
+  b.loglik = nullptr;
   {
     Timed tm(T_FB, st);
-    e = launch_forward_wide(NP, f, st, 1);
+    e = launch_wide_passes(NP, f, b, st);
     tm.stop();
   }
-  if (e != cudaSuccess) return cuda_fail(e, "tensor-core backward launch");
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward/backward launch");
   FbWideArgs c;
   memset(&c, 0, sizeof(c));
   c.K = dims.K; c.N = dims.N; c.M = dims.M; c.NP = NP; c.S = seqs->S;

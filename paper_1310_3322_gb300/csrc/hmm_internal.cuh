@@ -41,6 +41,7 @@ struct WsLayout {
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
   size_t sc_coff, sc_P, sc_E;  // parallel-in-time forward: chunk offsets, products
   size_t w_X, w_Bh, w_V, w_G, w_xe, w_sym, w_Cp, w_Ep, w_Pp;  // adjoint above 128 states
+  size_t w_img2;                                              // its backward pass's A image
   int w_nsplit, w_nchunks;
   int64_t w_rtot;
   int64_t sc_cap;              // chunk slots per model slot
@@ -552,6 +553,10 @@ size_t fbw_emis_smem(int NP, int M);
 // recursion in Y_t = b(o_t) o beta_t, i.e. the forward recursion with A^T for
 // A run from t = T-1 down to 0 from Y_{T-1} = b(o_{T-1}) (needs xs).
 cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st, int dir = 0);
+// the forward (f) and backward (b) passes of the adjoint in one launch, on
+// disjoint halves of the SMs (separate queues, images and row buffers)
+cudaError_t launch_wide_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
+                               cudaStream_t st);
 
 // Plan of the tensor-core adjoint: the rows of every 128-row tile share one
 // model, and the tile composition is a deterministic function of the input

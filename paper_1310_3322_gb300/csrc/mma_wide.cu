@@ -82,8 +82,9 @@ __global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K, int tran
   }
 }
 
+// The work of one CTA (all of it: items come from a.queue until it runs dry).
 template <int NP, int DIR>
-__global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
+__device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
   using L = WideCfg<NP>;
   constexpr int COLS = L::COLS, CH = L::CH, NKC = L::NKC, RING = L::RING;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -385,6 +386,57 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_wide(MmaWideLaunch a) {
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+template <int NP, int DIR>
+__global__ void __launch_bounds__(512, 1) hmm_forward_wide(const __grid_constant__ MmaWideLaunch a) {
+  wide_body<NP, DIR>(a);
+}
+
+// Both passes of the adjoint in one launch (they are independent): CTAs
+// [0, nf) take the forward items of f, the others the backward items of b,
+// each side with its own queue, A image and row buffers.
+template <int NP>
+__global__ void __launch_bounds__(512, 1)
+hmm_wide_passes(const __grid_constant__ MmaWideLaunch f, const __grid_constant__ MmaWideLaunch b,
+                int nf) {
+  if ((int)blockIdx.x < nf) wide_body<NP, 0>(f);
+  else wide_body<NP, 1>(b);
+}
+
+template <int NP>
+static cudaError_t build_wide_image(const MmaWideLaunch& a, int dir, cudaStream_t st) {
+  const long long n = (long long)a.seq.K * NP * NP / 2;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  wide_image_kernel<NP><<<blocks, 256, 0, st>>>(a.mod.Ap, a.img, a.seq.K, dir);
+  return cudaGetLastError();
+}
+
+template <int NP>
+static cudaError_t launch_passes_t(const MmaWideLaunch& f, const MmaWideLaunch& b,
+                                   cudaStream_t st) {
+  using L = WideCfg<NP>;
+  cudaError_t e;
+  if ((e = build_wide_image<NP>(f, 0, st)) != cudaSuccess) return e;
+  if ((e = build_wide_image<NP>(b, 1, st)) != cudaSuccess) return e;
+  auto kern = hmm_wide_passes<NP>;
+  const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;  // one CTA per SM
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+      cudaSuccess)
+    return e;
+  const int half = num_sms() / 2 > 0 ? num_sms() / 2 : 1;
+  const int nf = f.n_items < half ? (f.n_items > 0 ? f.n_items : 1) : half;
+  const int nb = b.n_items < half ? (b.n_items > 0 ? b.n_items : 1) : half;
+  kern<<<nf + nb, L::NTH, smem, st>>>(f, b, nf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
+                               cudaStream_t st) {
+  if (!f.xs || !b.xs || !b.xe || f.img == b.img || f.queue == b.queue) return cudaErrorInvalidValue;
+  if (NP == 256) return launch_passes_t<256>(f, b, st);
+  if (NP == 512) return launch_passes_t<512>(f, b, st);
+  return cudaErrorInvalidValue;
 }
 
 template <int NP>

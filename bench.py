@@ -192,6 +192,13 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def setup_launches(S: int, ordered: bool = True) -> int:
+    """Kernel launches of one call's setup: one block up to 4096 sequences;
+    above, validation blocks plus (when the call needs the length order or
+    prefix sums) the offsets block and the placement blocks."""
+    return 1 if (S <= 4096 or not ordered) else 3
+
+
 def traffic_for(kernel: str):
     """Per-launch DRAM bytes of `kernel` from a committed ncu capture, or None
     when the kernel's source changed since that capture."""
@@ -617,7 +624,8 @@ def run_large(args):
                                        "models + decoded model + best path"},
                    **{k: {"ms": v} for k, v in kms.items() if k not in ("forward", "adjoint")}},
         "clocks": clk,
-        "gpu_launches": 7 * args.steps,  # forward: setup, kernel; adjoint: setup, plan, kernel, reduce x2
+        # forward: setup, kernel; adjoint: setup (validation only), plan, kernel, reduce x2
+        "gpu_launches": (setup_launches(w.S) + 6) * args.steps,
         "note": "forward_tf32 is timed separately (TF32 operands, 2N^2 flop per obs*model)",
     }
     print(json.dumps(line), flush=True)
@@ -913,7 +921,9 @@ def run_teamwork(args):
                                    f"{SM_MAX_MHZ:.0f} MHz", "traffic": None},
         "clocks": clk,
         "kernel_ms_per_launch": per_launch,
-        "gpu_launches": sum(v[0] for v in kt.values()),
+        "gpu_launches": sum(v[0] for v in kt.values())
+                        + (setup_launches(w.S if args.teamwork_calls == "sets" else w.S // R) - 1)
+                        * kt["setup"][0],
     }
     print(json.dumps(line), flush=True)
 

@@ -192,6 +192,10 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
   if (op == HMM_OP_VITERBI) {
     L.bpoff = off; off = align256(off + S * 8);
     L.best = off; off = align256(off + S * 4);
+    if (NP > 64) {  // paths grouped by decoded model, segments padded to 4
+      L.vgorder = off; off = align256(off + (S + 4 * ((size_t)d.K + 1)) * 4);
+      L.vgcount = off; off = align256(off + 4);
+    }
   }
   L.pip = off; off = align256(off + (size_t)d.K * NP * 4);
   L.Ap = off; off = align256(off + (size_t)d.K * NP * NP * 4);
@@ -1001,6 +1005,8 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
   v.status = &at<WsHeader>(ws, 0)->status;
   v.bpoff = at<int64_t>(ws, L.bpoff);
   v.bp = at<uint8_t>(ws, L.bp);
+  v.gorder = wide ? at<int32_t>(ws, L.vgorder) : nullptr;
+  v.gcount = wide ? at<int32_t>(ws, L.vgcount) : nullptr;
   v.n_items_score = all ? ngroups * span_of(*seqs, dims) : ngroups;
   v.n_items_path = (seqs->S + PPp - 1) / PPp;
   auto scores = [&]() {

@@ -31,6 +31,7 @@ static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 struct WsLayout {
   size_t order, seqlen, done, bpoff, best, pip, Ap, Btp, bp, partial, red1, total;
   size_t phist, punits;  // setup plan over many blocks
+  size_t vgorder, vgcount;  // Viterbi paths above 64 states: grouping by model
   int NP;
   int64_t bp_cap;      // bytes of backpointer storage
   int64_t slots;       // adjoint partial slots
@@ -410,6 +411,8 @@ struct VitLaunch {
   uint8_t* bp;
   int n_items_score;
   int n_items_path;
+  int32_t* gorder;   // above 64 states: sequences grouped by decoded model (or NULL)
+  int32_t* gcount;   // above 64 states: items of gorder
 };
 cudaError_t launch_viterbi_scores(int NP, int G, const VitLaunch& a, cudaStream_t st);
 cudaError_t launch_viterbi_paths(int NP, int G, const VitLaunch& a, cudaStream_t st);

@@ -279,26 +279,99 @@ __global__ void __launch_bounds__(W * 32) hmm_viterbi_scores_wide(VitLaunch a) {
   }
 }
 
-__global__ void __launch_bounds__(32) hmm_viterbi_paths_wide(VitLaunch a) {
+// Groups the sequences by decoded (or labelled) model for the path kernel:
+// gorder holds each model's sequences (visited in length order) in a segment
+// padded with -1 to a multiple of kPathGroup, segments in model order, and
+// the rejected or undecoded ones in a last segment; gcount = the number of
+// kPathGroup-entry items. One block; nk = K + 1 buckets in shared memory.
+constexpr int kPathGroup = 4;
+
+__device__ __forceinline__ int path_bucket(const VitLaunch& a, int s, int nk) {
+  const int T = a.seq.seqlen[s];
+  if (T < 0) return nk - 1;
+  if (a.seq.model_of_seq) return a.seq.model_of_seq[s];  // validated by the setup
+  const int b = __ldcg(a.best + s);
+  if (b < 0 || b >= a.seq.span) return nk - 1;
+  return b + (a.seq.model_base ? a.seq.model_base[s] : 0);
+}
+
+__global__ void __launch_bounds__(1024) vw_group_kernel(VitLaunch a, int nk) {
+  extern __shared__ int gsm[];
+  int* hist = gsm;       // [nk]
+  int* cur = gsm + nk;   // [nk]
+  __shared__ int wsum[32];
+  const int tid = threadIdx.x, S = a.seq.S;
+  for (int k = tid; k < nk; k += 1024) hist[k] = 0;
+  __syncthreads();
+  for (int pos = tid; pos < S; pos += 1024) atomicAdd(&hist[path_bucket(a, a.seq.order[pos], nk)], 1);
+  __syncthreads();
+  // exclusive prefix of the padded segment sizes: thread t owns buckets
+  // [t per, t per + per)
+  const int per = (nk + 1023) / 1024;
+  const int k0 = tid * per, k1 = min(nk, k0 + per);
+  int local = 0;
+  for (int k = k0; k < k1; ++k) local += (hist[k] + kPathGroup - 1) / kPathGroup * kPathGroup;
+  int x = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(HMM_FULL_MASK, x, o);
+    if ((tid & 31) >= o) x += y;
+  }
+  if ((tid & 31) == 31) wsum[tid >> 5] = x;
+  __syncthreads();
+  int wbase = 0;
+  for (int w = 0; w < (tid >> 5); ++w) wbase += wsum[w];
+  int run = wbase + x - local;
+  for (int k = k0; k < k1; ++k) {
+    const int padded = (hist[k] + kPathGroup - 1) / kPathGroup * kPathGroup;
+    cur[k] = run;
+    for (int j = run + hist[k]; j < run + padded; ++j) a.gorder[j] = -1;
+    run += padded;
+  }
+  if (tid == 1023) *a.gcount = run / kPathGroup;  // the last thread's run is the total
+  __syncthreads();
+  for (int pos = tid; pos < S; pos += 1024) {
+    const int s = a.seq.order[pos];
+    a.gorder[atomicAdd(&cur[path_bucket(a, s, nk)], 1)] = s;
+  }
+}
+
+// W = 1: one pair per block, items in length order. W = kPathGroup: the
+// items of vw_group_kernel, whose W sequences share one decoded model, so the
+// block stages one matrix for W warps (one pair each).
+template <int W>
+__global__ void __launch_bounds__(W * 32) hmm_viterbi_paths_wide(VitLaunch a) {
   constexpr int CH = 32;  // backtrack rows fetched per chunk
   extern __shared__ __align__(16) float vsm[];
+  __shared__ int item_s, kblk_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j0 = 4 * lane;
   float* lA = vsm;
-  float* xs = vsm + kVW * kVW;  // [2][128]
-  const int lane = threadIdx.x, j0 = 4 * lane;
+  float* xs = vsm + kVW * kVW + warp * 2 * kVW;  // [2][128] per warp
   const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
   const int span = a.seq.span;
   const bool labelled = a.seq.model_of_seq != nullptr;
   const bool param_bad = (__ldcg(a.status) & HMM_STATUS_PARAM) != 0;
+  const int n_items = W == 1 ? a.n_items_path : __ldcg(a.gcount);
 
   for (;;) {
-    __syncwarp();
-    int item = 0;
-    if (lane == 0) item = atomicAdd(a.queue + 1, 1);
-    item = __shfl_sync(HMM_FULL_MASK, item, 0);
-    if (item >= a.n_items_path) break;
-    const int pos = item;
-    const bool has = pos < S;
-    const int s = has ? a.seq.order[pos] : 0;
+    __syncthreads();  // the previous item's readers of lA are done
+    if (threadIdx.x == 0) {
+      item_s = atomicAdd(a.queue + 1, 1);
+      kblk_s = INT_MAX;
+    }
+    __syncthreads();
+    const int item = item_s;
+    if (item >= n_items) break;
+    bool has;
+    int s;
+    if (W == 1) {
+      has = item < S;
+      s = has ? a.seq.order[item] : 0;
+    } else {
+      const int e = __ldcg(a.gorder + item * W + warp);
+      has = e >= 0;
+      s = has ? e : 0;
+    }
     const int T = has ? a.seq.seqlen[s] : 0;
     int k = 0;
     bool bad = T < 0 || param_bad;
@@ -312,9 +385,17 @@ __global__ void __launch_bounds__(32) hmm_viterbi_paths_wide(VitLaunch a) {
         else if (a.seq.model_base) k += a.seq.model_base[s];
       }
     }
+    int kb = k;
+    if (W > 1) {  // the block's model (one per item by construction)
+      if (lane == 0 && has && !bad) atomicMin(&kblk_s, k);
+      __syncthreads();
+      kb = kblk_s == INT_MAX ? 0 : kblk_s;
+      if (has && !bad && k != kb) bad = true;
+      k = kb;
+    }
     const int Tn = (T < 0) ? 0 : T;
-    stage_la(lA, a.mod.Ap, k, 32);
-    __syncwarp();
+    stage_la(lA, a.mod.Ap, kb, W * 32);
+    __syncthreads();
 
     const float* Bk = a.mod.Btp + (size_t)k * M * kVW + j0;
     const long long off = (has && T >= 0) ? a.seq.offsets[s] : 0;
@@ -428,6 +509,8 @@ __global__ void __launch_bounds__(32) hmm_viterbi_paths_wide(VitLaunch a) {
   }
 }
 
+size_t viterbi_group_smem(int nk) { return (size_t)2 * nk * 4; }
+
 size_t viterbi_wide_smem(int warps, int pairs) {
   return ((size_t)kVW * kVW + (size_t)warps * pairs * 2 * kVW) * 4;
 }
@@ -458,7 +541,18 @@ cudaError_t launch_viterbi_scores_wide(const VitLaunch& a, cudaStream_t st) {
 }
 
 cudaError_t launch_viterbi_paths_wide(const VitLaunch& a, cudaStream_t st) {
-  return launch_vw(hmm_viterbi_paths_wide, 1, 1, a.n_items_path, a, st);
+  const int nk = a.seq.K + 1;
+  if (!a.gorder || !a.gcount || viterbi_group_smem(nk) > 200 * 1024)
+    return launch_vw(hmm_viterbi_paths_wide<1>, 1, 1, a.n_items_path, a, st);
+  const size_t gs = viterbi_group_smem(nk);
+  cudaError_t e = cudaFuncSetAttribute(vw_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gs);
+  if (e != cudaSuccess) return e;
+  vw_group_kernel<<<1, 1024, gs, st>>>(a, nk);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // at most (S + nk (kPathGroup - 1)) / kPathGroup items; the kernel reads the count
+  const int max_items = (a.seq.S + nk * (kPathGroup - 1) + kPathGroup - 1) / kPathGroup;
+  return launch_vw(hmm_viterbi_paths_wide<kPathGroup>, kPathGroup, 1, max_items, a, st);
 }
 
 }  // namespace hmmgb

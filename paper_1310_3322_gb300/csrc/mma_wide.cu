@@ -21,6 +21,17 @@
 // each); thread 0 issues the MMAs and copies, warp 1 polls the step's commit.
 // Every mbarrier wait is bounded; on timeout the kernel records
 // HMM_STATUS_TIMEOUT, waits (bounded) for its own copies and MMAs and leaves.
+//
+// The adjoint above 128 states (Baum-Welch E-step, Rabiner eqs. 24-25) uses
+// the same recursion twice: with Y_t = b(o_t) o beta_t the backward recursion
+// reads Y_t = (Y_{t+1} A^T) o b(o_t), i.e. the forward recursion with A^T in
+// place of A (the image built from A, `transpose`), run from t = T-1 down to
+// 0 from Y_{T-1} = b(o_{T-1}). DIR = 1 selects that direction, and both
+// directions store every step's rescaled row (forward: alpha_t; backward:
+// beta_t before the emission product, with its exponent) for the count
+// kernels of fb_wide.cu. `hmm_wide_passes` runs the two directions side by
+// side in one launch, half of the CTAs each, with separate queues, images and
+// row buffers.
 #include "hmm_internal.cuh"
 #include "mma_rows.cuh"
 #include "tc.cuh"

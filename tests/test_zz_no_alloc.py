@@ -33,10 +33,11 @@ def _call_static(lib, pi, A, B, seqs, loglik, argmax):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("labelled", [False, True])
-def test_static_scratch_matches_workspace_entry_point(labelled):
+@pytest.mark.parametrize("n_seqs", [300, 6000])  # 6000: the setup plan over many blocks
+def test_static_scratch_matches_workspace_entry_point(labelled, n_seqs):
     import torch
     lib = hmm.lib()
-    w = synth.make_workload("batched", n_seqs=300, lengths=("uniform", 0, 300))
+    w = synth.make_workload("batched", n_seqs=n_seqs, lengths=("uniform", 0, 300))
     seqs, pi, A, B = to_gpu(w, labelled=labelled)
     ref_ll, ref_am = hmm.hmm_forward(pi, A, B, seqs)
     tol = torch.from_numpy(ll_tol(w.lengths)).float().cuda()

@@ -72,3 +72,22 @@ def test_role_split_partitions_sequences_and_models():
             np.testing.assert_array_equal(
                 p.symbols[p.offsets[j]: p.offsets[j] + p.lengths[j]],
                 w.symbols[w.offsets[s]: w.offsets[s] + w.lengths[s]])
+
+
+def test_wide_and_long_sequence_recipes():
+    """The 512-state recipe (Dirichlet(0.3) rows, T ~ U{100..500}) and the
+    few-long-sequences recipe (T ~ U{2^19..2^20}): shapes, determinism and
+    length laws (the long one checked on its length draw alone)."""
+    w = synth.make_workload("cuhmm", n_seqs=64)
+    assert (w.K, w.N, w.M, w.S) == (1, 512, 64, 64)
+    assert w.lengths.min() >= 100 and w.lengths.max() <= 500
+    np.testing.assert_array_equal(w.symbols, synth.make_workload("cuhmm", n_seqs=64).symbols)
+    np.testing.assert_allclose(w.A.sum(-1), 1.0, rtol=1e-5)
+    spec = synth.SPECS["longseq"]
+    T = synth.draw_lengths(spec, spec["S"], synth.SEEDS["longseq"])
+    assert T.size == 8 and T.min() >= 1 << 19 and T.max() <= 1 << 20
+    w = synth.make_workload("longseq", n_seqs=3, lengths=("uniform", 50, 60))
+    assert (w.K, w.N, w.M) == (4, 32, 64) and w.symbols.max() < w.M
+    # the "batched" parameter recipe: self-transitions in [0.6, 0.9]
+    d = np.diagonal(w.A, axis1=1, axis2=2)
+    assert d.min() >= 0.6 - 1e-6 and d.max() <= 0.9 + 1e-6

@@ -552,9 +552,7 @@ struct FbWideArgs {
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st);
 size_t fbw_emis_smem(int NP, int M);
 
-// dir 0: the forward recursion (loglik, argmax); dir 1: the backward
-// recursion in Y_t = b(o_t) o beta_t, i.e. the forward recursion with A^T for
-// A run from t = T-1 down to 0 from Y_{T-1} = b(o_{T-1}) (needs xs).
+// The recognition forward (loglik, argmax; dir must be 0 and xs NULL).
 cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st, int dir = 0);
 // the forward (f) and backward (b) passes of the adjoint in one launch, on
 // disjoint halves of the SMs (separate queues, images and row buffers)

@@ -94,7 +94,9 @@ __global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K, int tran
 }
 
 // The work of one CTA (all of it: items come from a.queue until it runs dry).
-template <int NP, int DIR>
+// STORE: keep every step's row in a.xs (the adjoint); recognition compiles
+// without the store path.
+template <int NP, int DIR, bool STORE>
 __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
   using L = WideCfg<NP>;
   constexpr int COLS = L::COLS, CH = L::CH, NKC = L::NKC, RING = L::RING;
@@ -162,7 +164,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
     // step t reads symbol o_t (forward) or o_{T-1-t} (backward)
     auto tix = [&](int t) { return DIR ? Tn - 1 - t : t; };
     // this row's per-step output rows (adjoint above 128 states)
-    float* xrow = (a.xs && has && !bad_seq)
+    float* xrow = (STORE && has && !bad_seq)
                       ? a.xs + ((size_t)k * a.rtot + (size_t)a.roff[s]) * NP + col0 : nullptr;
     RowState st;
     st.F = 0; st.f = 0; st.dead = false; st.bad = bad_seq; st.written = (Tn == 0);
@@ -195,7 +197,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
           const float4 pp = DIR ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(p4 + 8 * c + q);
           y[4 * q] = live ? pp.x * bb.x : 0.f; y[4 * q + 1] = live ? pp.y * bb.y : 0.f;
           y[4 * q + 2] = live ? pp.z * bb.z : 0.f; y[4 * q + 3] = live ? pp.w * bb.w : 0.f;
-          if (xrow && Tn > 0) {
+          if (STORE && xrow && Tn > 0) {
             const float4 sv = DIR ? make_float4(live ? 1.f : 0.f, live ? 1.f : 0.f,
                                                 live ? 1.f : 0.f, live ? 1.f : 0.f)
                                   : make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
@@ -211,7 +213,8 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
               make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
       }
       psum[h * 128 + row] = part;
-      if (DIR && xrow && Tn > 0 && h == 0) a.xe[(size_t)k * a.rtot + a.roff[s] + tix(0)] = 0;
+      if (STORE && DIR && xrow && Tn > 0 && h == 0)
+        a.xe[(size_t)k * a.rtot + a.roff[s] + tix(0)] = 0;
     }
     int o_next = (1 < Tn) ? __ldg(o + tix(1)) : 0;
     int o_next2 = (2 < Tn) ? __ldg(o + tix(2)) : 0;
@@ -291,7 +294,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
         tc::tmem_ld_wait();
         float2 acc = make_float2(0.f, 0.f);
         // (32-byte aligned: rows of NP floats, 32-column chunks)
-        float* xdst = (xrow && t < Tn) ? xrow + (size_t)tix(t) * NP + 32 * c : nullptr;
+        float* xdst = (STORE && xrow && t < Tn) ? xrow + (size_t)tix(t) * NP + 32 * c : nullptr;
         float4 held = make_float4(0.f, 0.f, 0.f, 0.f);  // the even group, stored with the odd
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -312,10 +315,12 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
             lo = __fmul2_rn(plo, make_float2(bq[q].x, bq[q].y));
             hi = __fmul2_rn(phi, make_float2(bq[q].z, bq[q].w));
           }
-          if (q & 1) {
-            if (xdst) st_v8(xdst + 4 * (q - 1), held, sv);
-          } else {
-            held = sv;
+          if constexpr (STORE) {
+            if (q & 1) {
+              if (xdst) st_v8(xdst + 4 * (q - 1), held, sv);
+            } else {
+              held = sv;
+            }
           }
           acc = __fadd2_rn(acc, __fadd2_rn(lo, hi));
           y[4 * q] = lo.x; y[4 * q + 1] = lo.y; y[4 * q + 2] = hi.x; y[4 * q + 3] = hi.y;
@@ -332,7 +337,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
           for (int q = 0; q < 8; ++q) bq[q] = bn[q];
       }
       psum[h * 128 + row] = part;
-      if (DIR && xrow && t < Tn && h == 0)
+      if (STORE && DIR && xrow && t < Tn && h == 0)
         a.xe[(size_t)k * a.rtot + a.roff[s] + tix(t)] = live ? st.f : 0;
     }
     if (tid == 0 && !abort_issue) {  // the last chunk's commit (its MMAs are done by now)
@@ -399,9 +404,10 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-template <int NP, int DIR>
+// Recognition: the forward recursion alone (no row stores).
+template <int NP>
 __global__ void __launch_bounds__(512, 1) hmm_forward_wide(const __grid_constant__ MmaWideLaunch a) {
-  wide_body<NP, DIR>(a);
+  wide_body<NP, 0, false>(a);
 }
 
 // Both passes of the adjoint in one launch (they are independent): CTAs
@@ -411,8 +417,8 @@ template <int NP>
 __global__ void __launch_bounds__(512, 1)
 hmm_wide_passes(const __grid_constant__ MmaWideLaunch f, const __grid_constant__ MmaWideLaunch b,
                 int nf) {
-  if ((int)blockIdx.x < nf) wide_body<NP, 0>(f);
-  else wide_body<NP, 1>(b);
+  if ((int)blockIdx.x < nf) wide_body<NP, 0, true>(f);
+  else wide_body<NP, 1, true>(b);
 }
 
 template <int NP>
@@ -451,18 +457,13 @@ cudaError_t launch_wide_passes(int NP, const MmaWideLaunch& f, const MmaWideLaun
 }
 
 template <int NP>
-static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st, int dir) {
+static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st) {
   using L = WideCfg<NP>;
-  {
-    const long long n = (long long)a.seq.K * NP * NP / 2;
-    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    wide_image_kernel<NP><<<blocks, 256, 0, st>>>(a.mod.Ap, a.img, a.seq.K, dir);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  auto kern = dir ? hmm_forward_wide<NP, 1> : hmm_forward_wide<NP, 0>;
+  cudaError_t err = build_wide_image<NP>(a, 0, st);
+  if (err != cudaSuccess) return err;
+  auto kern = hmm_forward_wide<NP>;
   const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;  // one CTA per SM
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   int blocks = num_sms();
   if (blocks > a.n_items) blocks = a.n_items > 0 ? a.n_items : 1;
@@ -471,9 +472,9 @@ static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st, int di
 }
 
 cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st, int dir) {
-  if (dir && !a.xs) return cudaErrorInvalidValue;
-  if (NP == 256) return launch_wide_t<256>(a, st, dir);
-  if (NP == 512) return launch_wide_t<512>(a, st, dir);
+  if (dir != 0 || a.xs) return cudaErrorInvalidValue;  // the adjoint's passes: launch_wide_passes
+  if (NP == 256) return launch_wide_t<256>(a, st);
+  if (NP == 512) return launch_wide_t<512>(a, st);
   return cudaErrorInvalidValue;
 }
 

@@ -254,3 +254,30 @@ def test_scan_host_checks(lib):
     assert scan(d, q, ws_bytes=1024) == hmm.HMM_ERR_WORKSPACE
     assert "need" in hmm.hmm_last_error()
     assert scan(d, _seqs(S=0)) == hmm.HMM_OK
+
+
+def test_python_binding_marshals_model_sets_and_scan_sizes(lib):
+    """Host side of the binding (CPU tensors stand in for device buffers; no
+    kernel is launched): model sets reach the C struct, output widths follow
+    the set size, and the scan workspace query goes through the binding."""
+    import torch
+    S = 6
+    seqs = hmm.Sequences(symbols=torch.zeros(60, dtype=torch.int32),
+                         offsets=torch.arange(S, dtype=torch.int64) * 10,
+                         lengths=torch.full((S,), 10, dtype=torch.int32), max_len=10)
+    assert seqs.span is None and seqs.c().model_base is None
+    base = torch.tensor([0, 3, 0, 3, 0, 3], dtype=torch.int32)
+    sets = seqs.model_sets(base, 3)
+    c = sets.c()
+    assert c.model_base == base.data_ptr() and c.model_span == 3 and c.model_of_seq is None
+    assert sets.span == 3 and sets.all_models().span is None
+    dims = hmm.hmm_dims_t(6, 16, 8)
+    auto = hmm.hmm_forward_scan_workspace_size(dims, seqs, 0)
+    assert auto == hmm.hmm_workspace_size(dims, seqs, hmm.HMM_OP_FORWARD_SCAN)
+    assert hmm.hmm_forward_scan_workspace_size(dims, seqs, 1) > auto
+    # model sets shrink the chunk-product storage to the set size
+    assert hmm.hmm_forward_scan_workspace_size(dims, sets, 1) < \
+        hmm.hmm_forward_scan_workspace_size(dims, seqs, 1)
+    with pytest.raises(ValueError):  # non-contiguous tensors are refused
+        hmm.Sequences(symbols=torch.zeros(60, dtype=torch.int32)[::2], offsets=seqs.offsets,
+                      lengths=seqs.lengths, max_len=10).c()

@@ -153,12 +153,18 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
  * that loads the library, held until the process exits) and is otherwise
  * hmm_forward: same arguments except the workspace, same outputs, same device
  * status bits. It allocates nothing and calls no allocating routine.
- *   - Calls whose scratch need (hmm_workspace_size for HMM_OP_FORWARD) is
- *     above HMM_STATIC_SCRATCH_BYTES return HMM_ERR_WORKSPACE and enqueue
+ *   - What must fit is the scratch of the sequential recursion: the value of
+ *     hmm_workspace_size(HMM_OP_FORWARD) for every batch except the few-long-
+ *     sequence batches that HMM_AUTO sends to the parallel-in-time forward,
+ *     for which that query also counts the chunk products (this call takes
+ *     that variant only when the products fit too, else the sequential
+ *     recursion). Larger requests return HMM_ERR_WORKSPACE and enqueue
  *     nothing; about 8 MiB covers e.g. 65536 sequences with K=10, N=32, M=256.
  *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture on the device.
+ *     per device, with that device current) and keeps it for the life of the
+ *     process; make that first call before any stream capture on the device.
+ *     A device reset (cudaDeviceReset) invalidates the kept address: do not
+ *     call this entry point on a device after resetting it.
  *   - Every call on a device shares the one array, and the next call
  *     overwrites what the last one left there: calls that may overlap on the
  *     GPU (different streams, or threads without ordering) race and give wrong
@@ -307,6 +313,21 @@ int hmm_get_tuning(int32_t op, int32_t n_pad, int32_t* lanes_per_pair);
 /* Writes up to cap candidate lane counts for (op, n_pad) into out (HOST
  * pointer); returns how many there are, or a negative error code. */
 int hmm_tuning_candidates(int32_t op, int32_t n_pad, int32_t* out, int32_t cap);
+
+/* Failure detection of the tensor-core kernels (HMM_BF16_MMA / HMM_TF32_MMA
+ * forward and adjoint). Their threads hand each time step to one another
+ * through shared-memory mbarriers; every such wait polls at most `polls`
+ * times (0 = the default, 2^24, seconds of polling) and then gives up: the
+ * kernel sets HMM_STATUS_TIMEOUT in the workspace's status word, first waits
+ * (with the default limit) for the matrix products and copies it has already
+ * started, frees its tensor memory and returns; the outputs of that call are
+ * invalid (log-likelihoods of unfinished rows NaN). No wait ever traps or
+ * spins forever. A small limit makes the waits give up on purpose, which is
+ * how the give-up path is tested. Process-wide, read at each launch (not
+ * inside a captured graph's replays); returns HMM_OK. hmm_get_wait_limit
+ * returns the limit in force. */
+int hmm_set_wait_limit(uint32_t polls);
+uint32_t hmm_get_wait_limit(void);
 
 /* Kernel timing (host-side tracing). While enabled, every kernel launch of
  * the library is bracketed by two CUDA events recorded on the launch stream;

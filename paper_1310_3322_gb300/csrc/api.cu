@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -40,6 +41,13 @@ int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 static int cuda_fail(cudaError_t e, const char* what) {
   return fail(HMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static std::atomic<uint32_t> g_wait_limit{0};  // 0 = kDrainPolls
+
+uint32_t wait_limit_polls() {
+  const uint32_t v = g_wait_limit.load(std::memory_order_relaxed);
+  return v ? v : kDrainPolls;
 }
 
 int num_sms() {
@@ -395,8 +403,6 @@ static int max_states(int op, int precision) {
     return 512;
   if (op == HMM_OP_FORWARD_SCAN) return (precision == HMM_FP32 || precision == HMM_AUTO) ? 32 : 0;
   if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 512;
-  if (op == HMM_OP_FORWARD_BACKWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO))
-    return 128;
   if (op == HMM_OP_FORWARD && precision == HMM_TF32_MMA) return 128;
   if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
   return 64;
@@ -529,6 +535,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   f.xs = at<float>(ws, L.w_X);
   f.roff = at<int64_t>(ws, L.bpoff);
   f.rtot = L.w_rtot;
+  f.wait_limit = wait_limit_polls();
   // the backward pass: own queue, A image and row buffers
   MmaWideLaunch b = f;
   b.queue = &at<WsHeader>(ws, 0)->queue[1];
@@ -650,6 +657,7 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   f.gexp_bytes = L.m_gexp_bytes;
   f.queue = &at<WsHeader>(ws, 0)->queue[3];
   f.status = &at<WsHeader>(ws, 0)->status;
+  f.wait_limit = wait_limit_polls();
   const int grid = cap < L.m_grid ? cap : L.m_grid;
   {
     Timed tm(T_FB, st);
@@ -802,6 +810,7 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     f.status = &at<WsHeader>(ws, 0)->status;
     f.n_tiles = n_tiles;
     f.n_items = n_tiles * dims.K;
+    f.wait_limit = wait_limit_polls();
     {
       Timed tm(T_FORWARD, st);
       e = launch_forward_wide(L.NP, f, st);
@@ -833,6 +842,7 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     f.status = &at<WsHeader>(ws, 0)->status;
     f.n_tiles = n_tiles;
     f.n_items = n_pairs * dims.K;
+    f.wait_limit = wait_limit_polls();
     {
       Timed tm(T_FORWARD, st);
       e = launch_forward_mma(L.NP, precision == HMM_TF32_MMA, f, st);
@@ -1235,6 +1245,14 @@ int hmm_get_device_status(const void* ws, hmm_stream_t stream, int32_t* status) 
                      (h & HMM_STATUS_SEQ) ? " bad-sequence" : "");
   return HMM_OK;
 }
+
+int hmm_set_wait_limit(uint32_t polls) {
+  g_err[0] = 0;
+  g_wait_limit.store(polls, std::memory_order_relaxed);
+  return HMM_OK;
+}
+
+uint32_t hmm_get_wait_limit(void) { return wait_limit_polls(); }
 
 int hmm_timing_enable(int on) {
   g_err[0] = 0;

@@ -497,6 +497,7 @@ struct MmaFwdLaunch {
   int32_t* status;
   int n_items;        // ceil(n_tiles / tiles per CTA) * K
   int n_tiles;        // ceil(S / 128)
+  uint32_t wait_limit;  // polls before a step's mbarrier wait gives up
 };
 cudaError_t launch_forward_mma(int NP, bool tf32, const MmaFwdLaunch& a, cudaStream_t st);
 int mma_tiles_per_cta(int NP);  // 128-row tiles one CTA of the tensor-core forward holds
@@ -519,6 +520,7 @@ struct MmaWideLaunch {
   int32_t* xe;           // backward: [K][rtot] power of two removed at each step
   const int64_t* roff;   // [S] first row of each sequence (exclusive prefix of lengths)
   int64_t rtot;          // rows per model
+  uint32_t wait_limit;   // polls before a step's mbarrier wait gives up
 };
 // Counts of the adjoint above 128 states from the two passes' rows (fb_wide.cu).
 struct FbWideArgs {
@@ -615,6 +617,7 @@ struct MmaFbLaunch {
   int64_t ckpt_bytes, scr_bytes, gexp_bytes;  // per-CTA strides
   int32_t* queue;
   int32_t* status;
+  uint32_t wait_limit;          // polls before a step's mbarrier wait gives up
 };
 cudaError_t launch_fb_mma(int NP, int M, int grid, const MmaFbLaunch& a, cudaStream_t st);
 // Checkpoint stride of a tile whose longest row has L steps, and the per-CTA
@@ -650,5 +653,9 @@ int candidates(int op, int NP, int* out, int cap);
 int plan_blocks(int S);  // plan blocks of the setup for S sequences
 size_t forward_ws_sequential(const hmm_dims_t& d, const hmm_seqs_t& q);
 int num_sms();
+// Polls a tensor-core kernel's per-step mbarrier wait makes before it gives
+// up (hmm_set_wait_limit; the drain waits after a give-up keep kDrainPolls).
+uint32_t wait_limit_polls();
+constexpr uint32_t kDrainPolls = 1u << 24;
 
 }  // namespace hmmgb

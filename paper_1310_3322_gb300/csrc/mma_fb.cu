@@ -90,7 +90,7 @@ static_assert(MmaFbCfg<64, 1>::TOTAL <= 227 * 1024, "shared memory budget");
 static_assert(MmaFbCfg<64, 2>::TOTAL <= 227 * 1024, "shared memory budget");
 static_assert(MmaFbCfg<128, 2>::TMEM_USED <= 512, "tensor memory budget");
 
-constexpr uint32_t kFbWaitLimit = 1u << 24;
+constexpr uint32_t kFbWaitLimit = 1u << 24;  // polls of the drain waits after an abort
 
 // Byte offset of 8-column group c8 of row m in a 128 x NP row image.
 template <int NP>
@@ -208,11 +208,12 @@ __device__ __forceinline__ float fwd_epilogue(float (&y)[COLS], const float* b, 
   return tree_sum<COLS>(y);
 }
 
-// Bounded mbarrier wait that also gives up once another thread has recorded
-// an abort; a timeout records one.
+// Bounded mbarrier wait (`limit` polls) that also gives up once another
+// thread has recorded an abort; a timeout records one.
 __device__ __forceinline__ bool fb_wait(uint64_t* bar, uint32_t parity,
-                                        volatile int32_t* abort_flag) {
-  for (uint32_t i = 0; i < kFbWaitLimit; ++i) {
+                                        volatile int32_t* abort_flag, uint32_t limit) {
+  if (tc::mbar_probe(bar, parity)) return true;  // first poll: never suspends
+  for (uint32_t i = 1; i < limit; ++i) {
     if (tc::mbar_test(bar, parity)) return true;
     if ((i & 31) == 31 && *abort_flag) return false;
   }
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
       if (lane == 0) {
         bool ok = true;
         auto wait_c = [&](uint64_t* bar, uint32_t& ph) {
-          ok = ok && fb_wait(bar, ph, abortp);
+          ok = ok && fb_wait(bar, ph, abortp, a.wait_limit);
           ph ^= 1;
           return ok;
         };
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         return (unsigned)v < (unsigned)M ? v : 0;
       };
       auto wait_e = [&](uint64_t* bar, uint32_t& ph) {
-        fb_wait(bar, ph, abortp);
+        fb_wait(bar, ph, abortp, a.wait_limit);
         ph ^= 1;
         tc::fence_after_sync();
       };

@@ -59,8 +59,8 @@ struct MmaFwdSmem {
   static constexpr int kE = 128 * kES;            // one tile of emission rows
   static constexpr int OFF_B = 0;
   static constexpr int OFF_PS = kB;               // partial row sums [NT][TPR][128]
-  static constexpr int OFF_BAR = OFF_PS + NT * TPR * 128 * 4;  // mma[NT], emission[NT]
-  static constexpr int OFF_MISC = OFF_BAR + 2 * NT * 8;        // tmem, item, abort, last, warp max
+  static constexpr int OFF_BAR = OFF_PS + NT * TPR * 128 * 4;  // mma[NT], emission[NT], fin[NT]
+  static constexpr int OFF_MISC = OFF_BAR + 3 * NT * 8;        // tmem, item, abort, last, warp max
   static constexpr int OFF_E = (OFF_MISC + 24 * 4 + 127) / 128 * 128;  // staging or table
   static constexpr int FIXED = OFF_E + (EMIS ? 0 : NT * kE);
   // total bytes for M symbols
@@ -70,7 +70,7 @@ constexpr int kFwdSmemMax = 227 * 1024;
 static_assert(MmaFwdSmem<128, 2, 2, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
 static_assert(MmaFwdSmem<64, 4, 1, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
 
-constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kWaitLimit = 1u << 24;  // polls of the teardown's drain waits
 constexpr uint32_t kTmemCols = 512;  // per tile: D (NP cols) then X (NP/2 cols) at (512/NT) * tile
 constexpr int kMmaThreads = 512;
 
@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
   float* psum = reinterpret_cast<float*>(smem + L::OFF_PS) + wg * TPR * 128;  // [TPR][128]
   uint64_t* mbar = &bars[wg];
   uint64_t* ebar = &bars[NT + wg];
+  uint64_t* fbar = &bars[2 * NT + wg];  // teardown: every MMA of this warpgroup done
   const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
 
   if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), kTmemCols);
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
     for (int i = 0; i < NT; ++i) {
       tc::mbar_init(&bars[i], 1);
       tc::mbar_init(&bars[NT + i], 128);
+      tc::mbar_init(&bars[2 * NT + i], 1);
     }
     misc[2] = 0;
   }
@@ -249,8 +251,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
       // hardware barrier (no issue slots spent spinning)
       bool ok = true;
       if (wtid < 32) {
-        if constexpr (!EMIS) ok = tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
-        ok = tc::mbar_wait_bounded(mbar, mphase, kWaitLimit) && ok;
+        if constexpr (!EMIS) ok = tc::mbar_wait_bounded(ebar, ephase, a.wait_limit);
+        ok = tc::mbar_wait_bounded(mbar, mphase, a.wait_limit) && ok;
       }
       if constexpr (!EMIS) ephase ^= 1;
       mphase ^= 1;
@@ -332,12 +334,17 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
     }
   }
 
-  // teardown: no MMA or copy of ours may still be in flight
+  // teardown: no MMA or copy of ours may still be in flight. After a wait
+  // gave up, the MMAs this warpgroup's issuing thread started are awaited
+  // through a fresh commit, and the emission copies through the phase that
+  // was being waited for (its parity is the flipped one's complement: a
+  // completed phase returns at once).
   tc::fence_before_sync();
   __syncthreads();
   if (misc[2] && wtid == 0) {
-    tc::mbar_wait_bounded(mbar, mphase, kWaitLimit);
-    if constexpr (!EMIS) tc::mbar_wait_bounded(ebar, ephase, kWaitLimit);
+    tc::mma_commit(fbar);
+    tc::mbar_wait_bounded(fbar, 0, kWaitLimit);
+    if constexpr (!EMIS) tc::mbar_wait_bounded(ebar, ephase ^ 1u, kWaitLimit);
   }
   __syncthreads();
   tc::fence_after_sync();

@@ -60,7 +60,7 @@ struct WideCfg {
   static_assert(TOTAL <= 227 * 1024, "shared memory budget");
 };
 
-constexpr uint32_t kWideWait = 1u << 24;
+constexpr uint32_t kWideWait = 1u << 24;  // polls of the teardown's drain waits
 
 // One 32-byte store (256-bit vector store, sm_100+): a full sector per lane.
 __device__ __forceinline__ void st_v8(float* p, float4 a, float4 b) {
@@ -229,7 +229,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
         tc::fence_after_sync();
         for (int kc = 0; kc < NKC; ++kc, ++g) {
           const int sl = g % RING;
-          if (!tc::mbar_wait_bounded(&full[sl], ph_full[sl], kWideWait)) { abort_issue = true; break; }
+          if (!tc::mbar_wait_bounded(&full[sl], ph_full[sl], a.wait_limit)) { abort_issue = true; break; }
           ph_full[sl] ^= 1;
           pend_full[sl] = false;
 #pragma unroll
@@ -245,7 +245,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
           // the previous chunk's buffer refills with the chunk RING - 1 ahead
           if (g >= 1) {
             const int pg = g - 1, ps = pg % RING;
-            if (!tc::mbar_wait_bounded(&empty[ps], ph_empty[ps], kWideWait)) { abort_issue = true; break; }
+            if (!tc::mbar_wait_bounded(&empty[ps], ph_empty[ps], a.wait_limit)) { abort_issue = true; break; }
             ph_empty[ps] ^= 1;
             pend_empty[ps] = false;
             const int ng = pg + RING;
@@ -274,7 +274,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) bq[q] = __ldg(eb + q);
       bool ok = true;
-      if (warp == 1) ok = tc::mbar_wait_bounded(done, ph_done, kWideWait);
+      if (warp == 1) ok = tc::mbar_wait_bounded(done, ph_done, a.wait_limit);
       ph_done ^= 1;
       // everyone agrees (and has read the partial sums) before they are rewritten
       if (!tc::bar_and(1, 512, ok && misc[2] == 0)) {
@@ -343,7 +343,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
     if (tid == 0 && !abort_issue) {  // the last chunk's commit (its MMAs are done by now)
       for (int i = 0; i < RING; ++i)
         if (pend_empty[i]) {
-          if (!tc::mbar_wait_bounded(&empty[i], ph_empty[i], kWideWait)) { abort_issue = true; break; }
+          if (!tc::mbar_wait_bounded(&empty[i], ph_empty[i], a.wait_limit)) { abort_issue = true; break; }
           ph_empty[i] ^= 1;
           pend_empty[i] = false;
         }

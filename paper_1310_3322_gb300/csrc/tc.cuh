@@ -39,10 +39,26 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking check that the phase with the given parity has completed.
+__device__ __forceinline__ bool mbar_probe(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the phase with the given parity to complete; gives up after
-// `limit` polls and returns false (the caller reports a timeout).
+// `limit` polls and returns false (the caller reports a timeout). The first
+// poll never suspends the thread (a limit of 1 is one instantaneous check);
+// the others may, for a hardware-defined time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i)
+  if (mbar_probe(bar, parity)) return true;
+  for (uint32_t i = 1; i < limit; ++i)
     if (mbar_test(bar, parity)) return true;
   return false;
 }

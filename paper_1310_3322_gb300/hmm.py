@@ -31,6 +31,7 @@ HMM_ERR_DEVICE = -5
 HMM_STATUS_SYMBOL = 0x1
 HMM_STATUS_PARAM = 0x2
 HMM_STATUS_SEQ = 0x4
+HMM_STATUS_TIMEOUT = 0x8
 
 HMM_FP32, HMM_BF16_MMA, HMM_TF32_MMA, HMM_AUTO = 0, 1, 2, 3
 HMM_OP_FORWARD, HMM_OP_VITERBI, HMM_OP_FORWARD_BACKWARD, HMM_OP_FORWARD_SCAN = 0, 1, 2, 3
@@ -85,6 +86,8 @@ _SIG = {
     "hmm_get_tuning": (_I32, [_I32, _I32, ctypes.POINTER(_I32)]),
     "hmm_tuning_candidates": (_I32, [_I32, _I32, ctypes.POINTER(_I32), _I32]),
     "hmm_last_error": (ctypes.c_char_p, []),
+    "hmm_set_wait_limit": (_I32, [ctypes.c_uint32]),
+    "hmm_get_wait_limit": (ctypes.c_uint32, []),
     "hmm_timing_enable": (_I32, [_I32]),
     "hmm_timing_reset": (_I32, []),
     "hmm_timing_read": (_I32, [_I32, ctypes.POINTER(ctypes.c_int64),
@@ -448,6 +451,15 @@ def hmm_tuning_candidates(op: int, n_pad: int) -> list:
     buf = (ctypes.c_int32 * 16)()
     n = _check(lib().hmm_tuning_candidates(op, n_pad, buf, 16))
     return [int(buf[i]) for i in range(min(n, 16))]
+
+
+def hmm_set_wait_limit(polls: int = 0):
+    """Polls before a tensor-core kernel's step wait gives up (0 = default)."""
+    _check(lib().hmm_set_wait_limit(int(polls)))
+
+
+def hmm_get_wait_limit() -> int:
+    return int(lib().hmm_get_wait_limit())
 
 
 def hmm_timing_enable(on: bool = True):

@@ -1,26 +1,38 @@
 #!/usr/bin/env python3
 """Throughput of the HMM recognition hot path on GB300 (one JSON line).
 
-Workload: the batched-recognition configuration -- K=10 activity HMMs, N=16
-states, M=32 symbols, 4096 ragged sequences with T ~ U{30..300} -- synthetic
-and seeded (the paper's UCF teamwork recordings are not available).
+Default workload: the large-state configuration -- K=4 activity HMMs, N=128
+states, M=256 symbols, Dirichlet(0.3) rows, 16384 ragged sequences with
+T ~ U{100..2000} -- synthetic and seeded (the paper's UCF teamwork
+recordings are not available). It is the largest configuration that fits
+one GPU.
 
-One step = one pass of the whole hot path over the batch:
-  softmax rows (logits -> pi, A, B), forward log-likelihood of every
-  (sequence, model) pair with the argmax over models, Viterbi scores of every
-  pair plus the best path of the decoded model, the forward-backward adjoint
-  of every sequence against its labelled model, the logit gradient, and one
-  Adam update of the logits.
-Throughput unit: observations x models scored per second (sum_s T_s * K per
-step). `value` comes from CUDA-graph replays of the step on device-resident
-inputs, with an L2 flush (a 256 MB write) between steps outside the timed
-events; `e2e` repeats the step through the public API with the inputs copied
-from pinned host memory and the results copied back inside the timed region.
+One step = the BF16 tensor-core forward of every (sequence, model) pair with
+the argmax over models (recognition) and the BF16 tensor-core
+forward-backward adjoint of every sequence against its labelled model (the
+Baum-Welch E-step's expected counts, which are the log-likelihood gradient),
+the two on two streams. Throughput unit: observations x models per second
+(sum_s T_s * (K + 1) per step). `value` is timed with CUDA events around
+eager steps on device-resident inputs, with an L2 flush (a 256 MB write)
+between steps outside the timed events; `e2e` repeats the step through the
+public API with the inputs copied from pinned host memory and every result
+copied back inside the timed region. The line also carries the TF32 forward
+and the Viterbi decoding of the same batch, the error of each precision
+against the FP64 oracle on a sample, the measured peaks (BF16 from the pool's
+file, FP32 from the library's FMA probe, TF32 from a GEMM), the oracle's
+CPU throughput (all host threads and one), and short summaries of the
+batched-recognition and training configurations.
+
+Other workloads (--workload): batched (K=10, N=16: forward, Viterbi, adjoint,
+gradient and Adam in one CUDA graph), gradient / training (the learning step),
+teamwork (per-role recognition, N=5), cuhmm (512 states), longseq (few very
+long sequences).
 
 Multi-GPU: every rank runs its own shard (its own batch, seed + rank) with no
 collective on the data path ("weak" scaling); the barrier and the max over
 ranks use torch.distributed. `--impl reference` times the FP64 CPU oracle on
-the host cores instead (rank 0 only).
+the host cores instead (rank 0 only), on a bounded sample of the same
+configuration per step.
 """
 from __future__ import annotations
 
@@ -37,7 +49,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "batched"
+WORKLOAD = "large"
 METRIC = "HMM obs·models/s (forward, Viterbi, fwd+adjoint)"
 UNIT = "obs*models/s"
 SM_COUNT_NOMINAL = 152
@@ -67,12 +79,14 @@ def parse():
     ap.add_argument("--lanes", default=None,
                     help="fixed lanes per pair 'fwd,viterbi,paths,adjoint' instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "large", "gradient", "training", "teamwork", "cuhmm",
+                    choices=["large", "batched", "gradient", "training", "teamwork", "cuhmm",
                              "longseq"],
-                    help="batched: the full step (default); large: tensor-core forward "
-                         "and adjoint; gradient/training: the learning step (and a "
+                    help="large: tensor-core forward and adjoint (default); batched: the "
+                         "full N=16 step; gradient/training: the learning step (and a "
                          "Baum-Welch iteration); teamwork: per-role recognition, N=5; "
                          "cuhmm: the 512-state forward")
+    ap.add_argument("--skip-others", action="store_true",
+                    help="large: skip the batched and training summaries")
     return ap.parse_args()
 
 
@@ -108,29 +122,45 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1310_3322_gb300 import synth
-    w = synth.make_workload(WORKLOAD)
     cores = os.cpu_count() or 1
-    idx = cpu_sample(w, 512)
-    units = int(w.lengths[idx].astype(np.int64).sum()) * w.K
-    for _ in range(args.warmup):
-        oracle_step(w, idx, cores)
-    times = []
-    for _ in range(args.steps):
+    if args.workload == "large":
+        w = synth.make_workload("large")
+        # 8 sequences per step (a fresh seeded draw each step): a few seconds
+        # of FP64 work on the host cores, so the whole run ends in minutes
+        draws = [large_sample(w, 8, 0, 100 + i) for i in range(args.warmup + args.steps)]
+        per_unit = w.K + 1
+        work = oracle_large_step
+        cfg = (f"large K={w.K} N={w.N} M={w.M} S={w.S} T~U{{100..2000}} (forward of all K "
+               "models + argmax, forward-backward adjoint against the labelled model)")
+        what = ("forward over all K models + labelled forward-backward counts, FP64 "
+                "log-space, a fresh seeded draw of 8 sequences per step")
+    else:
+        w = synth.make_workload("batched")
+        draws = [cpu_sample(w, 512)] * (args.warmup + args.steps)
+        per_unit = w.K
+        work = oracle_step
+        cfg = "batched-recognition K=10 N=16 M=32 S=4096 T~U{30..300}"
+        what = ("forward+Viterbi over all K models, labelled adjoint + logit gradient, FP64, "
+                "512 sequences per step")
+    for i in range(args.warmup):
+        work(w, draws[i], cores)
+    times, units = [], []
+    for i in range(args.steps):
+        idx = draws[args.warmup + i]
         t0 = time.perf_counter()
-        oracle_step(w, idx, cores)
+        work(w, idx, cores)
         times.append(time.perf_counter() - t0)
+        units.append(int(w.lengths[idx].astype(np.int64).sum()) * per_unit)
     ms = 1e3 * float(np.mean(times))
-    value = units / (ms / 1e3)
-    sample = (f"{idx.size} of {w.S} sequences ({units} obs*models) per step, "
-              "forward+Viterbi over all K models, labelled adjoint + logit gradient, FP64")
+    value = float(np.sum(units)) / float(np.sum(times))
+    sample = f"{what}: {int(np.mean(units))} obs*models per step on average"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batched-recognition K=10 N=16 M=32 S=4096 T~U{30..300}",
-                   "sample_sequences": int(idx.size), "l2": "n/a (host)"},
+        "config": {"workload": cfg, "sample_sequences": int(len(draws[-1])), "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -217,18 +247,16 @@ def traffic_for(kernel: str):
     return rec["bytes_per_launch_full_workload"]
 
 
-def run_gpu(args):
+def run_gpu(args, emit=True):
     import torch
     import torch.distributed as dist
     from paper_1310_3322_gb300 import hmm, synth
 
     rank, local, world = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = synth.make_workload(WORKLOAD, n_seqs=args.n_seqs, seed=synth.SEEDS[WORKLOAD] + rank)
+    w = synth.make_workload("batched", n_seqs=args.n_seqs, seed=synth.SEEDS["batched"] + rank)
     K, N, M = w.K, w.N, w.M
     units = units_of(w)
     sumT = int(w.lengths.astype(np.int64).sum())
@@ -478,9 +506,10 @@ def run_gpu(args):
             "phases": phases,
             "kernel_ms_per_step": step_kernel_ms,
         }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+        if emit:
+            print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 def measured_peak_bf16():
@@ -492,25 +521,129 @@ def measured_peak_bf16():
         return 1900.0, "fallback"
 
 
-def run_large(args):
-    """The large-state configuration on the tensor cores: one step = the
-    forward of every sequence against all K models with the argmax
-    (recognition) plus the forward-backward adjoint of every sequence against
-    its labelled model; units = sum_s T_s (K + 1). One JSON line; the
-    forward-only and adjoint-only kernels are reported beside it."""
+def plan_launches(K: int, labelled: bool) -> int:
+    """Kernel launches of the adjoint's tile plan: row compaction (count,
+    scan, place), 3 launches per 8-bit radix pass over (model, length) keys
+    (an even number of passes), and the tile stage."""
+    bits = 10
+    if labelled:
+        while bits < 32 and ((K - 1) >> (bits - 10)) != 0:
+            bits += 1
+    passes = (bits + 7) // 8
+    passes += passes & 1
+    return 3 + 3 * passes + 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def fma_peak(torch, dev):
+    """Measured FP32 FMA throughput (TFLOP/s) from the library's probe kernel:
+    best of 5 launches per mode (scalar FFMA, packed FFMA2), CUDA events."""
+    from paper_1310_3322_gb300 import hmm
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = sms * 4, 256, 20000
+    out = torch.empty(blocks, device=dev)
+    res = {}
+    for mode, name in ((0, "ffma"), (1, "ffma2")):
+        hmm.hmm_fma_probe(blocks, threads, 100, mode, out)
+        best = float("inf")
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fl = hmm.hmm_fma_probe(blocks, threads, iters, mode, out)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        res[name] = fl / (best / 1e3) / 1e12
+    assert bool(torch.isfinite(out).all())
+    return max(res.values()), res
+
+
+def tf32_peak(torch, dev):
+    """Dense TF32 GEMM throughput (TFLOP/s): torch.matmul of 8192^3 FP32
+    operands with TF32 tensor cores allowed, best of 5 (the TF32 forward's
+    roofline denominator, measured as the BF16 one was)."""
+    n = 8192
+    a = torch.randn(n, n, device=dev)
+    b = torch.randn(n, n, device=dev)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    del a, b
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
+def large_sample(w, n, longest, seed):
+    """n sequences of the batch: its `longest` longest and a seeded draw."""
+    order = np.argsort(-w.lengths, kind="stable")
+    rest = np.random.default_rng(seed).choice(order[longest:], size=n - longest, replace=False)
+    return np.sort(np.concatenate([order[:longest], rest]))
+
+
+def oracle_large_step(w, idx, nthreads):
+    """The large step's arithmetic on the FP64 CPU oracle for sequences idx:
+    forward of every model (the argmax is its by-product) and the labelled
+    forward-backward counts."""
+    import oracle
+    P = oracle.params(w.pi, w.A, w.B)
+    sub = (w.symbols, w.offsets[idx], w.lengths[idx])
+    oracle.forward(P, *sub, nthreads=nthreads)
+    oracle.forward_backward(P, *sub, w.labels[idx], nthreads=nthreads)
+
+
+def error_stats(ll, ref, lengths):
+    """max and mean |delta log P| / T over the compared pairs."""
+    T = np.maximum(np.asarray(lengths, np.float64), 1.0)
+    if ll.ndim == 2:
+        T = T[:, None]
+    e = np.abs(np.asarray(ll, np.float64) - ref) / T
+    return {"max_abs_per_obs": float(e.max()), "mean_abs_per_obs": float(e.mean())}
+
+
+def run_large(args, emit=True):
+    """The large-state configuration (K=4, N=128, M=256, 16384 sequences,
+    T ~ U{100..2000}) on the tensor cores. One step = the BF16 forward of
+    every sequence against all K models with the argmax (recognition) and the
+    BF16 forward-backward adjoint of every sequence against its labelled model
+    (the E-step's expected counts, i.e. the log-likelihood gradient); units =
+    sum_s T_s (K + 1). The TF32 forward and the Viterbi decoding of the same
+    batch are timed beside it, with the error of each precision against the
+    FP64 oracle on a sample."""
     import torch
+    import torch.distributed as dist
     from paper_1310_3322_gb300 import hmm, synth
 
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = synth.make_workload(args.workload, n_seqs=args.n_seqs,
-                            seed=synth.SEEDS[args.workload] + rank)
+    w = synth.make_workload("large", n_seqs=args.n_seqs, seed=synth.SEEDS["large"] + rank)
     K, N, M = w.K, w.N, w.M
     sumT = int(w.lengths.astype(np.int64).sum())
     units = sumT * (K + 1)
     seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets, w.lengths, device=dev)
-    lab = seqs.labelled(torch.from_numpy(w.labels).to(dev))
+    labels = torch.from_numpy(w.labels).to(dev)
+    lab = seqs.labelled(labels)
     pi, A, B = (torch.from_numpy(x).to(dev) for x in (w.pi, w.A, w.B))
     ll = torch.empty((w.S, K), device=dev)
     am = torch.empty(w.S, dtype=torch.int32, device=dev)
@@ -519,49 +652,73 @@ def run_large(args):
     ws = [hmm.Workspace(dev), hmm.Workspace(dev)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     prec = hmm.HMM_BF16_MMA
-
-    def fwd():
-        hmm.hmm_forward(pi, A, B, seqs, precision=prec, loglik=ll, argmax=am, workspace=ws[0])
-
-    def adj():
-        hmm.hmm_forward_backward(pi, A, B, lab, precision=prec, loglik=fll, counts=cnts,
-                                 workspace=ws[1])
-
-    # the adjoint (the longer chain, one tile per SM, SMs idle once its short
-    # tiles end) is launched first; the recognition forward runs beside it on a
-    # second stream and takes SMs as they free up
+    # the recognition forward runs beside the adjoint on a second stream
     rec = torch.cuda.Stream(device=dev)
 
-    def step(concurrent=True):
+    def step(sq=seqs, lb=lab, concurrent=True):
         cur = torch.cuda.current_stream()
-        if not concurrent:
-            fwd()
-            adj()
-            return
-        rec.wait_stream(cur)
-        adj()
-        with torch.cuda.stream(rec):
-            fwd()
-        cur.wait_stream(rec)
+        if concurrent:
+            rec.wait_stream(cur)
+        # the adjoint (the longer chain) is launched first
+        hmm.hmm_forward_backward(pi, A, B, lb, precision=prec, loglik=fll, counts=cnts,
+                                 workspace=ws[1])
+        with torch.cuda.stream(rec if concurrent else cur):
+            hmm.hmm_forward(pi, A, B, sq, precision=prec, loglik=ll, argmax=am, workspace=ws[0])
+        if concurrent:
+            cur.wait_stream(rec)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     assert hmm.hmm_get_device_status(ws[0]) == 0 and hmm.hmm_get_device_status(ws[1]) == 0
+
+    # ---- timed region: CUDA events on the launching stream, L2 flushed ----
     clocks = Clocks(local)
+    cur = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
     clocks.start()
     time.sleep(0.3)
-    ms = _time_steps(torch, step, args.steps, flush)
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)          # L2 flush, outside the timed events
+        evs[i][0].record(cur)
+        step()
+        evs[i][1].record(cur)
+    barrier()
     clk = clocks.stop()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    t_max = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = units * world / (ms_max / 1e3)
+    ll_bf16 = ll.cpu().numpy()
+    am_bf16 = am.cpu().numpy()
+    fll_bf16 = fll.cpu().numpy()
+
+    # ---- per-kernel times: each launch timed alone (serialised eager step)
     hmm.hmm_timing_reset()
     hmm.hmm_timing_enable(True)
     _time_steps(torch, lambda: step(concurrent=False), args.steps, flush)
     kt = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     kms = {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]}
-    # the TF32 forward on the same data, beside the BF16 one
+    # forward: setup + kernel; adjoint: setup (validation only), plan, kernel,
+    # two-level count reduction
+    launches_per_step = (setup_launches(w.S) + 1) + (setup_launches(w.S, ordered=False)
+                                                     + plan_launches(K, True) + 1 + 2)
+
+    # ---- the TF32 forward on the same data ----------------------------------
+    ll32 = torch.empty_like(ll)
+
     def fwd_tf32():
-        hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_TF32_MMA, loglik=ll, argmax=am,
+        hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_TF32_MMA, loglik=ll32, argmax=am,
                         workspace=ws[0])
     fwd_tf32()
     hmm.hmm_timing_reset()
@@ -570,8 +727,9 @@ def run_large(args):
     kt32 = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     tf32_ms = kt32["forward"][1] / max(kt32["forward"][0], 1)
-    # Viterbi of every sequence against all K models (FP32 SIMT, one warp per
-    # pair above 64 states): scores, decoded model, best path
+    ll_tf32 = ll32.cpu().numpy()
+
+    # ---- Viterbi of every sequence against all K models (FP32 SIMT) --------
     vsc = torch.empty((w.S, K), device=dev)
     vbest = torch.empty(w.S, dtype=torch.int32, device=dev)
     vpath = torch.empty(max(w.total_obs, 1), dtype=torch.int32, device=dev)
@@ -588,47 +746,143 @@ def run_large(args):
     ktv = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     vkms = {k2: v[1] / v[0] for k2, v in ktv.items() if v[0]}
+
+    # ---- peaks: measured BF16 (pool file), FP32 FMA probe, TF32 GEMM -------
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_nominal = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak, fp32_modes = fma_peak(torch, dev)
+    tf32_tflops = tf32_peak(torch, dev)
+    peak, basis = measured_peak_bf16()
     vs_tf = 2.0 * N * N * sumT * K / (vkms["viterbi_scores"] / 1e3) / 1e12
     f_tf = 2.0 * N * N * sumT * K / (kms["forward"] / 1e3) / 1e12
-    a_tf = (8.0 * N * N + 10 * N) * sumT / (kms["adjoint"] / 1e3) / 1e12
+    f32_tf = 2.0 * N * N * sumT * K / (tf32_ms / 1e3) / 1e12
+    a_flop = (8.0 * N * N + 10 * N) * sumT
+    a_tf = a_flop / (kms["adjoint"] / 1e3) / 1e12
     dom = "adjoint" if kms["adjoint"] >= kms["forward"] else "forward"
     achieved = a_tf if dom == "adjoint" else f_tf
-    peak, basis = measured_peak_bf16()
+
+    # ---- error of each precision against the FP64 oracle (a sample) --------
+    import oracle
+    cores = os.cpu_count() or 1
+    eidx = large_sample(w, min(32, w.S), min(8, w.S), 21)
+    P = oracle.params(w.pi, w.A, w.B)
+    ref, ref_am, _ = oracle.forward(P, w.symbols, w.offsets[eidx], w.lengths[eidx],
+                                    nthreads=cores)
+    lab_ref = ref[np.arange(eidx.size), w.labels[eidx]]
+    err = {"sample": f"{eidx.size} sequences (the {min(8, w.S)} longest and a seeded draw), "
+                     f"all {K} models, FP64 oracle",
+           "bf16_forward": error_stats(ll_bf16[eidx], ref, w.lengths[eidx]),
+           "tf32_forward": error_stats(ll_tf32[eidx], ref, w.lengths[eidx]),
+           "bf16_adjoint_loglik": error_stats(fll_bf16[eidx], lab_ref, w.lengths[eidx]),
+           "argmax_agreement_bf16": float(np.mean(am_bf16[eidx] == ref_am))}
+
+    # ---- end to end through the public API (host buffers) ------------------
+    e2e = None
+    if not args.skip_e2e:
+        h_in = [torch.from_numpy(x).pin_memory() for x in (w.symbols, w.offsets, w.lengths,
+                                                            w.labels)]
+        d_in = [torch.empty_like(x, device=dev) for x in h_in]
+        sq2 = hmm.Sequences(d_in[0], d_in[1], d_in[2], seqs.max_len)
+        lb2 = sq2.labelled(d_in[3])
+        outs = [ll, am, fll] + cnts
+        h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in outs]
+        bi = sum(t.numel() * t.element_size() for t in h_in)
+        bo = sum(t.numel() * t.element_size() for t in h_out)
+        times = []
+        barrier()
+        for i in range(max(args.warmup, 3) + args.steps):
+            flush.fill_(i & 0xff)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for d, h in zip(d_in, h_in):
+                d.copy_(h, non_blocking=True)
+            step(sq2, lb2)
+            for h, d in zip(h_out, outs):
+                h.copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        barrier()
+        e_ms = float(np.mean(times[max(args.warmup, 3):])) * 1e3
+        t_e = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        e2e = {"value": units * world / (float(t_e.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+               "ms_per_step": float(t_e.item()),
+               "copies": "H2D symbols, offsets, lengths, labels (pinned); D2H log-likelihoods "
+                         "[S][K], argmax [S], labelled log-likelihoods [S], counts"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1): a sample, extrapolated -------
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cidx = large_sample(w, min(48, w.S), min(4, w.S), 22)
+        c_units = int(w.lengths[cidx].astype(np.int64).sum()) * (K + 1)
+        t0 = time.perf_counter()
+        oracle_large_step(w, cidx, cores)
+        dt = time.perf_counter() - t0
+        c1idx = large_sample(w, min(4, w.S), 0, 23)
+        c1_units = int(w.lengths[c1idx].astype(np.int64).sum()) * (K + 1)
+        t0 = time.perf_counter()
+        oracle_large_step(w, c1idx, 1)
+        dt1 = time.perf_counter() - t0
+        cpu = {"value": c_units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{cidx.size} of {w.S} sequences ({c_units} obs*models): FP64 "
+                         f"log-space forward over all {K} models + labelled forward-backward "
+                         f"counts, {cores} threads, {dt:.1f} s; the full step extrapolated "
+                         "linearly in sum T*K*N^2",
+               "full_step_seconds_extrapolated": dt * units / c_units,
+               "value_1thread": c1_units / dt1,
+               "sample_1thread": f"{c1idx.size} sequences ({c1_units} obs*models), 1 thread, "
+                                 f"{dt1:.1f} s",
+               "cpu_model": cpu_model()}
+
     line = {
-        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} K={K} N={N} M={M} S={w.S} (forward of all "
-                               "K models + argmax, and the adjoint against the labelled "
-                               "model; tcgen05 BF16)", "units_per_step": units,
+        "config": {"workload": f"large K={K} N={N} M={M} S={w.S} T~U{{100..2000}} "
+                               "(BF16 forward of all K models + argmax, and the BF16 "
+                               "forward-backward adjoint against the labelled model)",
+                   "precision": "BF16 tensor-core operands (tcgen05 kind::f16), FP32 "
+                                "accumulation, FP64 final log",
+                   "units_per_step": units, "sum_T": sumT,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "timing": "eager step (adjoint and forward on two streams), CUDA events; "
-                             "per-kernel times from an eager pass with the kernels serialised"},
+                             "per-kernel times from an eager pass with the kernels "
+                             "serialised", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "tensor", "kernel": dom + "_mma", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "launch_ms": kms[dom], "peak_basis": f"dense BF16, {basis} (burst)",
-                     "traffic": None},
-        "phases": {"forward": {"ms": kms["forward"], "tflops": f_tf,
+                     "algorithmic": "adjoint 8N^2+10N flop per obs (forward, recompute, "
+                                    "backward, xi), forward 2N^2 per obs*model",
+                     "traffic": traffic_for("hmm_fb_mma" if dom == "adjoint" else
+                                            "hmm_forward_mma")},
+        "error_vs_oracle": err,
+        "phases": {"forward": {"ms": kms["forward"], "tflops": f_tf, "frac_bf16": f_tf / peak,
                                "obs_models_per_s": sumT * K / (kms["forward"] / 1e3)},
-                   "adjoint": {"ms": kms["adjoint"], "tflops": a_tf,
+                   "adjoint": {"ms": kms["adjoint"], "tflops": a_tf, "frac_bf16": a_tf / peak,
                                "obs_per_s": sumT / (kms["adjoint"] / 1e3)},
-                   "forward_tf32": {"ms": tf32_ms,
-                                    "tflops": 2.0 * N * N * sumT * K / (tf32_ms / 1e3) / 1e12},
+                   "forward_tf32": {"ms": tf32_ms, "tflops": f32_tf,
+                                    "frac_tf32": f32_tf / tf32_tflops,
+                                    "obs_models_per_s": sumT * K / (tf32_ms / 1e3)},
                    "viterbi": {"ms": vit_ms, "kernel_ms": vkms,
                                "obs_models_per_s": sumT * K / (vit_ms / 1e3),
                                "scores_tflops": vs_tf, "scores_frac_fp32": vs_tf / fp32_peak,
                                "note": "FP32 SIMT max-plus (2N^2 ops per obs*model), all K "
                                        "models + decoded model + best path"},
                    **{k: {"ms": v} for k, v in kms.items() if k not in ("forward", "adjoint")}},
+        "peaks": {"bf16_tflops": peak, "bf16_basis": basis, "tf32_tflops_measured": tf32_tflops,
+                  "fp32_tflops_measured": fp32_peak, "fp32_probe": fp32_modes,
+                  "fp32_tflops_nominal_max_clock": fp32_nominal},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
         "clocks": clk,
-        # forward: setup, kernel; adjoint: setup (validation only), plan, kernel, reduce x2
-        "gpu_launches": (setup_launches(w.S) + 6) * args.steps,
-        "note": "forward_tf32 is timed separately (TF32 operands, 2N^2 flop per obs*model)",
+        "gpu_launches": launches_per_step * args.steps,
     }
-    print(json.dumps(line), flush=True)
+    if emit and rank == 0:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def _time_steps(torch, step, steps, flush):
@@ -645,7 +899,7 @@ def _time_steps(torch, step, steps, flush):
     return float(np.mean([x.elapsed_time(y) for x, y in evs]))
 
 
-def run_learning(args):
+def run_learning(args, emit=True):
     """One learning step on the gradient / training configurations: softmax
     rows -> forward + adjoint of every sequence against its labelled model ->
     logit gradient -> Adam, captured in a CUDA graph; units = sum_s T_s. The
@@ -793,9 +1047,17 @@ def run_learning(args):
         "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]},
         "forward_all_models": fwd,
         "baum_welch": bw,
-        "gpu_launches": 8 * args.steps,
+        # softmax, setup, (tensor cores: tile plan), adjoint (the SIMT one with
+        # segment ranges: two kernels), two-level count reduction, gradient, Adam
+        "gpu_launches": (1 + setup_launches(w.S, ordered=not mma)
+                         + (plan_launches(K, True) if mma else 0)
+                         + (1 if mma or hmm.hmm_get_tuning(hmm.HMM_TUNE_FB_RANGES,
+                                                           tune.n_pad(N)) == 1 else 2)
+                         + 2 + 1 + 1) * args.steps,
     }
-    print(json.dumps(line), flush=True)
+    if emit and rank == 0:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_teamwork(args):
@@ -1104,6 +1366,19 @@ def run_longseq(args):
     print(json.dumps(line), flush=True)
 
 
+def summary(line):
+    """The headline numbers of another configuration's line."""
+    if not line:
+        return None
+    keep = ("metric", "value", "unit", "ms_per_step", "dtype")
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = line["config"]["workload"]
+    r = line.get("roofline") or {}
+    out["roofline"] = {k: r.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit",
+                                             "frac", "launch_ms")}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1111,8 +1386,38 @@ def main():
         return
     import __graft_entry__
     __graft_entry__.build()
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        dispatch(args, rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+def dispatch(args, rank):
     if args.workload == "large":
-        run_large(args)
+        line = run_large(args, emit=False)
+        if not args.skip_others and args.n_seqs is None:
+            # the batched-recognition and training configurations, shortly:
+            # their headline numbers beside the large one (own full lines with
+            # --workload batched / training)
+            import copy
+            import torch
+            others = {}
+            for name, fn in (("batched", run_gpu), ("training", run_learning)):
+                a2 = copy.copy(args)
+                a2.workload, a2.steps, a2.skip_cpu, a2.skip_e2e = name, min(args.steps, 10), True, True
+                torch.cuda.empty_cache()
+                others[name] = summary(fn(a2, emit=False))
+            line["other_configs"] = others
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         return
     if args.workload in ("gradient", "training"):
         run_learning(args)

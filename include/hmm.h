@@ -329,6 +329,17 @@ int hmm_tuning_candidates(int32_t op, int32_t n_pad, int32_t* out, int32_t cap);
 int hmm_set_wait_limit(uint32_t polls);
 uint32_t hmm_get_wait_limit(void);
 
+/* FP32 FMA throughput probe: the measured denominator of the roofline of the
+ * FP32 (SIMT) kernels, which are bound by FP32 issue (not part of the
+ * paper's method). blocks x threads threads (threads a multiple of 32, at
+ * most 1024) each run `iters` rounds of 16 independent FMA chains: mode 0
+ * scalar fma.rn.f32 (blocks*threads*iters*32 flop per launch), mode 1 the
+ * packed two-lane fma.rn.f32x2 (twice that). out [blocks] (device) receives
+ * per-block sums of the chains. The caller times the launch; returns
+ * HMM_ERR_ARG for bad arguments. */
+int hmm_fma_probe(int32_t blocks, int32_t threads, int64_t iters, int32_t mode, float* out,
+                  hmm_stream_t stream);
+
 /* Kernel timing (host-side tracing). While enabled, every kernel launch of
  * the library is bracketed by two CUDA events recorded on the launch stream;
  * hmm_timing_read() synchronises those events and reports, per kernel kind,

@@ -86,6 +86,7 @@ _SIG = {
     "hmm_get_tuning": (_I32, [_I32, _I32, ctypes.POINTER(_I32)]),
     "hmm_tuning_candidates": (_I32, [_I32, _I32, ctypes.POINTER(_I32), _I32]),
     "hmm_last_error": (ctypes.c_char_p, []),
+    "hmm_fma_probe": (_I32, [_I32, _I32, ctypes.c_int64, _I32, _VP, _VP]),
     "hmm_set_wait_limit": (_I32, [ctypes.c_uint32]),
     "hmm_get_wait_limit": (ctypes.c_uint32, []),
     "hmm_timing_enable": (_I32, [_I32]),
@@ -451,6 +452,13 @@ def hmm_tuning_candidates(op: int, n_pad: int) -> list:
     buf = (ctypes.c_int32 * 16)()
     n = _check(lib().hmm_tuning_candidates(op, n_pad, buf, 16))
     return [int(buf[i]) for i in range(min(n, 16))]
+
+
+def hmm_fma_probe(blocks: int, threads: int, iters: int, mode: int, out, stream=None):
+    """FP32 FMA throughput probe; returns the flop count of the launch."""
+    _check(lib().hmm_fma_probe(int(blocks), int(threads), int(iters), int(mode), _ptr(out),
+                               _stream(stream)))
+    return blocks * threads * iters * 32 * (2 if mode == 1 else 1)
 
 
 def hmm_set_wait_limit(polls: int = 0):

@@ -11,6 +11,12 @@ and accumulates in FP32. Two checks:
 * against the oracle on the exact model, every term of every step is a sum of
   non-negative products whose factors carry relative errors <= u, so
   |delta log P| <= 2 u T is a hard bound; the mean per-step error is reported.
+* that hard bound is far above what the kernel does: each step's rounding
+  error is a sum of N independently signed terms, so per sequence
+  |delta log P| <= (u / 4) T + 2 u is required as well (2 u: one step's worth
+  of slack for short sequences); measured values are printed.
+* recognition: the argmax over models must agree wherever the top two models
+  of the exact model are more than twice that per-sequence cap apart.
 """
 import numpy as np
 import pytest
@@ -42,6 +48,11 @@ def tf32_round(x):
 
 PRECISIONS = {"bf16": (hmm.HMM_BF16_MMA, U_BF16, bf16_round),
               "tf32": (hmm.HMM_TF32_MMA, U_TF32, tf32_round)}
+
+
+def seq_cap(u, lengths):
+    """Per-sequence bound |delta log P| <= (u / 4) T + 2 u (see the module text)."""
+    return (u / 4) * np.asarray(lengths, np.float64) + 2 * u
 
 
 CASES = [
@@ -96,12 +107,14 @@ def test_tensor_core_forward_matches_oracle(case, prec):
     assert np.all(err <= 2 * u * T + ll_tol(w.lengths)[:, None]), (err / T).max()
     print(f"{prec} {name} N={w.N}: max|d|/T vs exact {np.max(err / T):.2e}, "
           f"mean {np.mean(err / T):.2e}; vs rounded-A {np.max(err_r / T):.2e}")
+    cap = seq_cap(u, w.lengths)[:, None]
+    assert np.all(err <= cap), f"max |d| / cap = {np.max(err / cap):.3f}"
     # recognition: argmax agrees where the top two models are well separated
     if w.K == 1:
         np.testing.assert_array_equal(am.cpu().numpy(), np.where(np.isnan(ll[:, 0]), -1, 0))
         return
     srt = np.sort(ref, axis=1)
-    clear = srt[:, -1] - srt[:, -2] > 4 * u * T[:, 0] + 2 * ll_tol(w.lengths)
+    clear = srt[:, -1] - srt[:, -2] > 2 * cap[:, 0]
     np.testing.assert_array_equal(am.cpu().numpy()[clear], ref_am[clear])
 
 

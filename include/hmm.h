@@ -317,16 +317,20 @@ int hmm_tuning_candidates(int32_t op, int32_t n_pad, int32_t* out, int32_t cap);
 /* Failure detection of the tensor-core kernels (HMM_BF16_MMA / HMM_TF32_MMA
  * forward and adjoint). Their threads hand each time step to one another
  * through shared-memory mbarriers; every such wait polls at most `polls`
- * times (0 = the default, 2^24, seconds of polling) and then gives up: the
- * kernel sets HMM_STATUS_TIMEOUT in the workspace's status word, first waits
- * (with the default limit) for the matrix products and copies it has already
- * started, frees its tensor memory and returns; the outputs of that call are
- * invalid (log-likelihoods of unfinished rows NaN). No wait ever traps or
- * spins forever. A small limit makes the waits give up on purpose, which is
- * how the give-up path is tested. Process-wide, read at each launch (not
- * inside a captured graph's replays); returns HMM_OK. hmm_get_wait_limit
- * returns the limit in force. */
-int hmm_set_wait_limit(uint32_t polls);
+ * times and then gives up: the kernel sets HMM_STATUS_TIMEOUT in the
+ * workspace's status word, first waits (with the default limit) for the
+ * matrix products and copies it has already started, frees its tensor memory
+ * and returns; the outputs of that call are invalid (log-likelihoods of the
+ * rows it gave up on are NaN). No wait ever traps or spins forever.
+ *   polls < 0  the default, 2^24 polls (seconds: far beyond any healthy step)
+ *   polls = 0  no poll at all: every such wait gives up at once -- the way the
+ *              give-up path is tested
+ *   polls > 0  that many polls (the first never suspends the thread; the
+ *              others may, for a hardware-defined time), capped at 2^32 - 1
+ * Process-wide, read when a call launches its kernels (a captured graph keeps
+ * the value of its capture); returns HMM_OK. hmm_get_wait_limit returns the
+ * limit in force. */
+int hmm_set_wait_limit(int64_t polls);
 uint32_t hmm_get_wait_limit(void);
 
 /* FP32 FMA throughput probe: the measured denominator of the roofline of the

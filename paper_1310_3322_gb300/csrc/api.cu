@@ -43,12 +43,9 @@ static int cuda_fail(cudaError_t e, const char* what) {
   return fail(HMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-static std::atomic<uint32_t> g_wait_limit{0};  // 0 = kDrainPolls
+static std::atomic<uint32_t> g_wait_limit{kDrainPolls};
 
-uint32_t wait_limit_polls() {
-  const uint32_t v = g_wait_limit.load(std::memory_order_relaxed);
-  return v ? v : kDrainPolls;
-}
+uint32_t wait_limit_polls() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 int num_sms() {
   static int cache[64] = {0};
@@ -1246,9 +1243,11 @@ int hmm_get_device_status(const void* ws, hmm_stream_t stream, int32_t* status) 
   return HMM_OK;
 }
 
-int hmm_set_wait_limit(uint32_t polls) {
+int hmm_set_wait_limit(int64_t polls) {
   g_err[0] = 0;
-  g_wait_limit.store(polls, std::memory_order_relaxed);
+  const uint32_t v = polls < 0 ? kDrainPolls
+                               : (polls > (int64_t)0xffffffff ? 0xffffffffu : (uint32_t)polls);
+  g_wait_limit.store(v, std::memory_order_relaxed);
   return HMM_OK;
 }
 

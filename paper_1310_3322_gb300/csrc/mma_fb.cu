@@ -208,13 +208,13 @@ __device__ __forceinline__ float fwd_epilogue(float (&y)[COLS], const float* b, 
   return tree_sum<COLS>(y);
 }
 
-// Bounded mbarrier wait (`limit` polls) that also gives up once another
-// thread has recorded an abort; a timeout records one.
+// Bounded mbarrier wait (`limit` polls, the first one never suspending the
+// thread; 0: none) that also gives up once another thread has recorded an
+// abort; a timeout records one.
 __device__ __forceinline__ bool fb_wait(uint64_t* bar, uint32_t parity,
                                         volatile int32_t* abort_flag, uint32_t limit) {
-  if (tc::mbar_probe(bar, parity)) return true;  // first poll: never suspends
-  for (uint32_t i = 1; i < limit; ++i) {
-    if (tc::mbar_test(bar, parity)) return true;
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (i == 0 ? tc::mbar_probe(bar, parity) : tc::mbar_test(bar, parity)) return true;
     if ((i & 31) == 31 && *abort_flag) return false;
   }
   *abort_flag = 1;

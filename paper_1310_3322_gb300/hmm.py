@@ -87,7 +87,7 @@ _SIG = {
     "hmm_tuning_candidates": (_I32, [_I32, _I32, ctypes.POINTER(_I32), _I32]),
     "hmm_last_error": (ctypes.c_char_p, []),
     "hmm_fma_probe": (_I32, [_I32, _I32, ctypes.c_int64, _I32, _VP, _VP]),
-    "hmm_set_wait_limit": (_I32, [ctypes.c_uint32]),
+    "hmm_set_wait_limit": (_I32, [ctypes.c_int64]),
     "hmm_get_wait_limit": (ctypes.c_uint32, []),
     "hmm_timing_enable": (_I32, [_I32]),
     "hmm_timing_reset": (_I32, []),
@@ -461,8 +461,9 @@ def hmm_fma_probe(blocks: int, threads: int, iters: int, mode: int, out, stream=
     return blocks * threads * iters * 32 * (2 if mode == 1 else 1)
 
 
-def hmm_set_wait_limit(polls: int = 0):
-    """Polls before a tensor-core kernel's step wait gives up (0 = default)."""
+def hmm_set_wait_limit(polls: int = -1):
+    """Polls before a tensor-core kernel's step wait gives up (< 0: the
+    default; 0: every such wait gives up at once)."""
     _check(lib().hmm_set_wait_limit(int(polls)))
 
 

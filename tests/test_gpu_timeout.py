@@ -2,9 +2,8 @@
 
 Every per-step mbarrier wait of the tensor-core forward (N <= 128 and the
 wide one above), and of the tensor-core adjoint, polls at most
-hmm_set_wait_limit() times. A limit of one poll (one non-blocking check,
-made right after the MMAs it waits for were issued) makes the waits give up
-on purpose. The kernel must then set HMM_STATUS_TIMEOUT, wait for the matrix
+hmm_set_wait_limit() times. A limit of zero polls makes every such wait give
+up at once, while the matrix products it waits for are still in flight. The kernel must then set HMM_STATUS_TIMEOUT, wait for the matrix
 products and copies it already started, free its tensor memory and return:
 the call's outputs are invalid (NaN log-likelihoods for the rows it did not
 finish), the device stays usable, and the next call with the default limit on
@@ -50,12 +49,12 @@ def test_wait_limit_gives_up_then_next_call_is_exact(name):
     assert hmm.hmm_get_device_status(ws) == 0
     assert hmm.hmm_get_wait_limit() == 1 << 24
     try:
-        hmm.hmm_set_wait_limit(1)
-        assert hmm.hmm_get_wait_limit() == 1
+        hmm.hmm_set_wait_limit(0)
+        assert hmm.hmm_get_wait_limit() == 0
         out = [t.cpu().numpy() for t in _run(op, prec, seqs, lab, pi, A, B, ws)]
         status = hmm.hmm_get_device_status(ws)
     finally:
-        hmm.hmm_set_wait_limit(0)
+        hmm.hmm_set_wait_limit(-1)
     assert hmm.hmm_get_wait_limit() == 1 << 24
     assert status & hmm.HMM_STATUS_TIMEOUT, f"status {status:#x}"
     # rows the kernel gave up on report NaN (rows it had finished keep their

@@ -522,16 +522,17 @@ def measured_peak_bf16():
 
 
 def plan_launches(K: int, labelled: bool) -> int:
-    """Kernel launches of the adjoint's tile plan: row compaction (count,
-    scan, place), 3 launches per 8-bit radix pass over (model, length) keys
-    (an even number of passes), and the tile stage."""
+    """Kernel launches of the tensor-core adjoint's tile plan: row compaction
+    (count, scan, place), 3 launches per 8-bit radix pass over (model,
+    length) keys (an even number of passes), the tile stage and the work
+    lists of its two kernels."""
     bits = 10
     if labelled:
         while bits < 32 and ((K - 1) >> (bits - 10)) != 0:
             bits += 1
     passes = (bits + 7) // 8
     passes += passes & 1
-    return 3 + 3 * passes + 1
+    return 3 + 3 * passes + 2
 
 
 def cpu_model() -> str:
@@ -709,10 +710,14 @@ def run_large(args, emit=True):
     kt = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     kms = {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0]}
-    # forward: setup + kernel; adjoint: setup (validation only), plan, kernel,
-    # two-level count reduction
+    # the adjoint is two kernels: the forward/backward passes and the segment
+    # ranges; its algorithmic work is counted against the pair
+    kms["adjoint_ranges"] = kms["adjoint"]
+    kms["adjoint"] = kms["adjoint_ranges"] + kms.get("adjoint_pass", 0.0)
+    # forward: setup + kernel; adjoint: setup (validation only), plan, the two
+    # kernels, two-level count reduction
     launches_per_step = (setup_launches(w.S) + 1) + (setup_launches(w.S, ordered=False)
-                                                     + plan_launches(K, True) + 1 + 2)
+                                                     + plan_launches(K, True) + 2 + 2)
 
     # ---- the TF32 forward on the same data ----------------------------------
     ll32 = torch.empty_like(ll)
@@ -855,14 +860,17 @@ def run_large(args, emit=True):
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "launch_ms": kms[dom], "peak_basis": f"dense BF16, {basis} (burst)",
                      "algorithmic": "adjoint 8N^2+10N flop per obs (forward, recompute, "
-                                    "backward, xi), forward 2N^2 per obs*model",
-                     "traffic": traffic_for("hmm_fb_mma" if dom == "adjoint" else
-                                            "hmm_forward_mma")},
+                                    "backward, xi) over its two launches (passes + segment "
+                                    "ranges); forward 2N^2 per obs*model",
+                     "traffic": traffic_for("adjoint_mma" if dom == "adjoint" else
+                                            "forward_mma")},
         "error_vs_oracle": err,
         "phases": {"forward": {"ms": kms["forward"], "tflops": f_tf, "frac_bf16": f_tf / peak,
                                "obs_models_per_s": sumT * K / (kms["forward"] / 1e3)},
                    "adjoint": {"ms": kms["adjoint"], "tflops": a_tf, "frac_bf16": a_tf / peak,
-                               "obs_per_s": sumT / (kms["adjoint"] / 1e3)},
+                               "obs_per_s": sumT / (kms["adjoint"] / 1e3),
+                               "pass_ms": kms.get("adjoint_pass"),
+                               "ranges_ms": kms["adjoint_ranges"]},
                    "forward_tf32": {"ms": tf32_ms, "tflops": f32_tf,
                                     "frac_tf32": f32_tf / tf32_tflops,
                                     "obs_models_per_s": sumT * K / (tf32_ms / 1e3)},
@@ -871,7 +879,8 @@ def run_large(args, emit=True):
                                "scores_tflops": vs_tf, "scores_frac_fp32": vs_tf / fp32_peak,
                                "note": "FP32 SIMT max-plus (2N^2 ops per obs*model), all K "
                                        "models + decoded model + best path"},
-                   **{k: {"ms": v} for k, v in kms.items() if k not in ("forward", "adjoint")}},
+                   **{k: {"ms": v} for k, v in kms.items()
+                      if k not in ("forward", "adjoint", "adjoint_pass", "adjoint_ranges")}},
         "peaks": {"bf16_tflops": peak, "bf16_basis": basis, "tf32_tflops_measured": tf32_tflops,
                   "fp32_tflops_measured": fp32_peak, "fp32_probe": fp32_modes,
                   "fp32_tflops_nominal_max_clock": fp32_nominal},
@@ -977,6 +986,8 @@ def run_learning(args, emit=True):
     kt = hmm.hmm_timing_read()
     hmm.hmm_timing_enable(False)
     adj_ms = kt["adjoint"][1] / max(kt["adjoint"][0], 1)
+    if kt.get("adjoint_pass", (0, 0.0))[0]:  # tensor cores: passes + segment ranges
+        adj_ms += kt["adjoint_pass"][1] / kt["adjoint_pass"][0]
     flops = (8 * N * N + 10 * N) * sumT
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     if mma:
@@ -1051,8 +1062,8 @@ def run_learning(args, emit=True):
         # segment ranges: two kernels), two-level count reduction, gradient, Adam
         "gpu_launches": (1 + setup_launches(w.S, ordered=not mma)
                          + (plan_launches(K, True) if mma else 0)
-                         + (1 if mma or hmm.hmm_get_tuning(hmm.HMM_TUNE_FB_RANGES,
-                                                           tune.n_pad(N)) == 1 else 2)
+                         + (2 if mma or hmm.hmm_get_tuning(hmm.HMM_TUNE_FB_RANGES,
+                                                           tune.n_pad(N)) > 1 else 1)
                          + 2 + 1 + 1) * args.steps,
     }
     if emit and rank == 0:

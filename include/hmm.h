@@ -229,8 +229,11 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
  * precision: HMM_FP32 runs the FP32 SIMT adjoint (N <= 64); HMM_BF16_MMA the
  * tensor-core adjoint (32 < N <= 128, M <= 256: BF16 operands, FP32
  * accumulation, per-row messages renormalised every step, checkpoint stride
- * capped at 16 while T <= 8192); HMM_AUTO chooses the tensor cores above
- * N = 32. Its errors against FP64 are of order the BF16 unit roundoff 2^-8
+ * capped at 16 while T <= 8192) as two kernels: the forward and the backward
+ * recursion of every 128-row tile run as independent chains keeping
+ * checkpoints of both, then every range of a tile's checkpoint segments is a
+ * separate work item (recompute, backward, counts); HMM_AUTO chooses the
+ * tensor cores above N = 32. Its errors against FP64 are of order the BF16 unit roundoff 2^-8
  * relative per count (|delta log P| <= 2^-7 T).
  * Above 128 states (N <= 512, the cited cuHMM shape of Sec. 5.6) the
  * tensor-core forward and backward passes keep every step's rescaled alpha
@@ -348,11 +351,13 @@ int hmm_fma_probe(int32_t blocks, int32_t threads, int64_t iters, int32_t mode, 
  * the library is bracketed by two CUDA events recorded on the launch stream;
  * hmm_timing_read() synchronises those events and reports, per kernel kind,
  * the number of launches and their summed duration since the last reset.
- * Kinds: 0 setup, 1 forward, 2 viterbi-scores, 3 viterbi-paths, 4 adjoint,
- * 5 count-reduce, 6 softmax-rows, 7 softmax-grad, 8 adam, 9 mstep,
- * 10 scan-chunks, 11 scan-combine. Not for use inside CUDA-graph capture; not
- * thread-safe against concurrent launches. */
-#define HMM_TIMING_KINDS 12
+ * Kinds: 0 setup, 1 forward, 2 viterbi-scores, 3 viterbi-paths, 4 adjoint
+ * (the tensor-core adjoint: its segment-range kernel), 5 count-reduce,
+ * 6 softmax-rows, 7 softmax-grad, 8 adam, 9 mstep, 10 scan-chunks,
+ * 11 scan-combine, 12 adjoint-pass (the tensor-core adjoint's forward and
+ * backward passes). Not for use inside CUDA-graph capture; not thread-safe
+ * against concurrent launches. */
+#define HMM_TIMING_KINDS 13
 int hmm_timing_enable(int on);
 int hmm_timing_reset(void);
 int hmm_timing_read(int32_t kind, int64_t* launches, double* total_ms);

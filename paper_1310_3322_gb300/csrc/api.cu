@@ -137,6 +137,18 @@ static int fb_mma_nsmax(int max_len) {
   return ns < 1 ? 1 : ns;
 }
 
+// Checkpoint segments per range item of the tensor-core adjoint: enough
+// items (about 12 per SM for the tiles the batch can have) that the ranges of
+// the longest tiles spread over the GPU, at least two segments each so an
+// item's fixed costs (its restart step, loading its model, writing its count
+// slot) stay small against its steps.
+static int fb_mma_spr(int nsmax, int tiles) {
+  const int64_t want = (int64_t)12 * num_sms();
+  int spr = (int)(((int64_t)nsmax * tiles + want - 1) / want);
+  if (spr < 2) spr = 2;
+  return spr > nsmax ? (nsmax > 0 ? nsmax : 1) : spr;
+}
+
 static int fb_mma_tile_cap(const hmm_dims_t& d, const hmm_seqs_t& q) {
   const int64_t chunks = ((int64_t)(q.S > 0 ? q.S : 0) + 127) / 128;
   const int64_t cap = q.model_of_seq ? chunks + d.K : chunks * d.K;
@@ -260,29 +272,46 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.w_Ep = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * d.M * 4);
     L.w_Pp = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * 4);
   } else if (op == HMM_OP_FORWARD_BACKWARD && mma) {
-    // tensor-core adjoint: tile plan, per-tile count slots, per-CTA buffers
+    // tensor-core adjoint: tile plan and work lists; per tile the pass
+    // kernel's checkpoints (alpha and Y images, exponents, last row sums);
+    // per range item a count slot; per CTA of the range kernel its buffers
     const int cap = fb_mma_tile_cap(d, q);
     const size_t img = (size_t)128 * NP * 2;
+    const int max_len = q.max_len > 0 ? q.max_len : 1;
+    const int nsmax = fb_mma_nsmax(max_len);
+    L.m_group = NP == 64 ? 4 : 2;
+    L.m_spr = fb_mma_spr(nsmax, cap);
+    L.m_pass_cap = cap;
+    L.m_rng_cap = cap * ((nsmax + L.m_spr - 1) / L.m_spr);
     L.slot_floats = (int64_t)NP + (int64_t)NP * NP + (int64_t)NP * d.M;
-    L.slots = cap;
-    L.nchunks = first_chunks(cap);
+    L.slots = L.m_rng_cap;
+    L.nchunks = first_chunks(L.m_rng_cap);
     L.m_sorted = off; off = align256(off + S * 4);
     L.m_tmp = off; off = align256(off + S * 4);
     L.m_keys = off; off = align256(off + 2 * (size_t)std::max<int64_t>(S, cap) * 4);
     L.m_tiles = off; off = align256(off + ((size_t)cap * 6 + (size_t)d.K * 2) * 4);
     L.m_ntiles = off; off = align256(off + 4);
     L.m_pscr = off; off = align256(off + mma_plan_scratch_bytes((int64_t)S));
+    L.m_pass = off; off = align256(off + (size_t)cap * L.m_group * 4);
+    L.m_ptmp = off; off = align256(off + (size_t)cap * 2 * 4);
+    L.m_npass = off; off = align256(off + 4);
+    L.m_rtile = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_rseg = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_rmodel = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_rlen = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_nrng = off; off = align256(off + 4);
     L.partial = off; off = align256(off + (size_t)(L.slots * L.slot_floats * 4));
     L.red1 = off; off = align256(off + (size_t)L.nchunks * d.K * L.slot_floats * 4);
-    const int grid = fb_mma_grid(d, NP);
-    const int max_len = q.max_len > 0 ? q.max_len : 1;
-    L.m_grid = grid;
-    L.m_ckpt_bytes = (int64_t)fb_mma_nsmax(max_len) * img;
-    L.m_scr_bytes = (int64_t)fb_mma_segment(max_len) * img;
+    L.m_ckpt_bytes = (int64_t)nsmax * img;
     L.m_gexp_bytes = (int64_t)align256((size_t)max_len * 128);
-    L.m_ckpt = off; off = align256(off + (size_t)grid * L.m_ckpt_bytes);
+    L.m_ckpt = off; off = align256(off + (size_t)cap * L.m_ckpt_bytes);
+    L.m_cky = off; off = align256(off + (size_t)cap * L.m_ckpt_bytes);
+    L.m_gexp = off; off = align256(off + (size_t)cap * L.m_gexp_bytes);
+    L.m_slast = off; off = align256(off + (size_t)cap * 128 * 4);
+    const int grid = fb_mma_grid(d, NP);
+    L.m_grid = grid;
+    L.m_scr_bytes = (int64_t)fb_mma_segment(max_len) * img;
     L.m_scr = off; off = align256(off + (size_t)grid * L.m_scr_bytes);
-    L.m_gexp = off; off = align256(off + (size_t)grid * L.m_gexp_bytes);
     L.m_gbuf = off; off = align256(off + (size_t)grid * 128 * NP * 4);
   }
   L.total = off;
@@ -434,7 +463,7 @@ static bool use_mma_fb(const hmm_dims_t& d, int precision) {
 // ---------------------------------------------------------------------------
 enum {
   T_SETUP = 0, T_FORWARD, T_VSCORES, T_VPATHS, T_FB, T_REDUCE, T_SOFTMAX, T_SGRAD, T_ADAM, T_MSTEP,
-  T_SCAN_CHUNKS, T_SCAN_COMBINE
+  T_SCAN_CHUNKS, T_SCAN_COMBINE, T_FB_PASS
 };
 
 struct EventPair {
@@ -604,9 +633,10 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
   s.skip_order = 1;  // the tile plan orders the sequences itself
   const bool labelled = seqs->model_of_seq != nullptr;
-  const int cap = (int)L.slots;
+  const int cap = L.m_pass_cap;  // tiles the plan can form
   int32_t* tiles = at<int32_t>(ws, L.m_tiles);
   MmaPlanArgs p;
+  memset(&p, 0, sizeof(p));
   p.S = seqs->S; p.K = dims.K; p.labelled = labelled ? 1 : 0;
   p.seqlen = at<int32_t>(ws, L.seqlen);
   p.model_of_seq = seqs->model_of_seq;
@@ -620,6 +650,18 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   p.group_start = tiles + 6 * cap; p.group_end = p.group_start + dims.K;
   p.n_tiles_cap = cap;
   p.n_tiles = at<int32_t>(ws, L.m_ntiles);
+  p.group = L.m_group;
+  p.spr = L.m_spr;
+  p.pass_tiles = at<int32_t>(ws, L.m_pass);
+  p.pass_tmp = at<int32_t>(ws, L.m_ptmp);
+  p.n_pass = at<int32_t>(ws, L.m_npass);
+  p.pass_cap = L.m_pass_cap;
+  p.rng_tile = at<int32_t>(ws, L.m_rtile);
+  p.rng_seg = at<int32_t>(ws, L.m_rseg);
+  p.rng_model = at<int32_t>(ws, L.m_rmodel);
+  p.rng_len = at<int32_t>(ws, L.m_rlen);
+  p.n_rng = at<int32_t>(ws, L.m_nrng);
+  p.rng_cap = L.m_rng_cap;
   {
     const int nb = (int)((seqs->S + 4095) / 4096 > 0 ? (seqs->S + 4095) / 4096 : 1);
     p.bcnt = at<int32_t>(ws, L.m_pscr);
@@ -634,31 +676,57 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   }
   if (e != cudaSuccess) return cuda_fail(e, "setup launch");
 
+  MmaPassLaunch pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.seq = seq_args(dims, *seqs, L, ws);
+  pa.mod = model_args(L, ws);
+  pa.sorted = p.sorted;
+  pa.tile_start = p.tile_start; pa.tile_rows = p.tile_rows; pa.tile_model = p.tile_model;
+  pa.tile_len = p.tile_len;
+  pa.pass_tiles = p.pass_tiles;
+  pa.n_pass = p.n_pass;
+  pa.labelled = p.labelled;
+  pa.loglik = loglik;
+  pa.ckx = at<uint8_t>(ws, L.m_ckpt);
+  pa.cky = at<uint8_t>(ws, L.m_cky);
+  pa.ck_stride = L.m_ckpt_bytes;
+  pa.gexp = at<int8_t>(ws, L.m_gexp);
+  pa.gexp_stride = L.m_gexp_bytes;
+  pa.s_last = at<float>(ws, L.m_slast);
+  pa.queue = &at<WsHeader>(ws, 0)->queue[5];
+  pa.status = &at<WsHeader>(ws, 0)->status;
+  pa.wait_limit = wait_limit_polls();
+  {
+    Timed tm(T_FB_PASS, st);
+    e = launch_fb_pass(NP, pa, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint pass launch");
+
   MmaFbLaunch f;
-  f.seq = seq_args(dims, *seqs, L, ws);
-  f.mod = model_args(L, ws);
+  memset(&f, 0, sizeof(f));
+  f.seq = pa.seq;
+  f.mod = pa.mod;
   f.weight = weight;
-  f.loglik = loglik;
   f.sorted = p.sorted;
   f.tile_start = p.tile_start; f.tile_rows = p.tile_rows; f.tile_model = p.tile_model;
-  f.tile_len = p.tile_len; f.tile_order = p.tile_order; f.n_tiles = p.n_tiles;
+  f.tile_len = p.tile_len;
+  f.rng_tile = p.rng_tile; f.rng_seg = p.rng_seg; f.n_rng = p.n_rng;
   f.labelled = p.labelled;
   f.slots = at<float>(ws, L.partial);
   f.slot_floats = L.slot_floats;
-  f.ckpt = at<uint8_t>(ws, L.m_ckpt);
+  f.ckx = pa.ckx; f.cky = pa.cky; f.ck_stride = pa.ck_stride;
+  f.gexp = pa.gexp; f.gexp_stride = pa.gexp_stride;
+  f.s_last = pa.s_last;
   f.scr = at<uint8_t>(ws, L.m_scr);
-  f.gexp = at<int8_t>(ws, L.m_gexp);
   f.gbuf = at<float>(ws, L.m_gbuf);
-  f.ckpt_bytes = L.m_ckpt_bytes;
   f.scr_bytes = L.m_scr_bytes;
-  f.gexp_bytes = L.m_gexp_bytes;
   f.queue = &at<WsHeader>(ws, 0)->queue[3];
   f.status = &at<WsHeader>(ws, 0)->status;
   f.wait_limit = wait_limit_polls();
-  const int grid = cap < L.m_grid ? cap : L.m_grid;
   {
     Timed tm(T_FB, st);
-    e = launch_fb_mma(NP, dims.M, grid, f, st);
+    e = launch_fb_mma(NP, dims.M, L.m_grid, f, st);
     tm.stop();
   }
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint launch");
@@ -666,9 +734,9 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   ReduceLaunch r;
   r.partial = f.slots;
   r.red1 = at<float>(ws, L.red1);
-  r.model_of_seq = p.tile_model;  // every slot is one tile of one model
-  r.seqlen = p.tile_len;          // -1 marks unused slots
-  r.S = cap; r.K = dims.K; r.N = dims.N; r.M = dims.M; r.NP = NP;
+  r.model_of_seq = p.rng_model;   // every slot is one range of one tile of one model
+  r.seqlen = p.rng_len;           // -1 marks unused slots
+  r.S = L.m_rng_cap; r.K = dims.K; r.N = dims.N; r.M = dims.M; r.NP = NP;
   r.planes = 1;
   r.slot_floats = L.slot_floats;
   r.nchunks = L.nchunks;

@@ -50,6 +50,10 @@ struct WsLayout {
   int s_planes;        // largest number of ranges per pair the workspace holds
   int64_t m_ckpt_bytes, m_scr_bytes, m_gexp_bytes;
   int m_grid;
+  // the tensor-core adjoint's two kernels: work lists, per-tile Y checkpoints
+  // and last-step row sums
+  size_t m_pass, m_ptmp, m_npass, m_rtile, m_rseg, m_rmodel, m_rlen, m_nrng, m_cky, m_slast;
+  int m_pass_cap, m_rng_cap, m_spr, m_group;
 };
 
 // ---------------------------------------------------------------------------
@@ -587,6 +591,19 @@ struct MmaPlanArgs {
   int32_t* bcnt;                // [ceil(S / 4096)] valid rows per block, then offsets
   int32_t* hist;                // [256][ceil(S / 4096)] digit counts, then offsets
   int32_t* n_valid;             // device count of rows with T >= 1
+  // work lists of the two adjoint kernels (plan_items_kernel)
+  int group;                    // tiles per pass group (the pass kernel's tiles per CTA)
+  int spr;                      // checkpoint segments per range item
+  int32_t* pass_tiles;          // [pass_cap][group] tile ids (-1: none), longest group first
+  int32_t* pass_tmp;            // [2][pass_cap] scratch
+  int32_t* n_pass;              // device count of pass groups
+  int pass_cap;
+  int32_t* rng_tile;            // [rng_cap] tile of each range item (longest tiles first)
+  int32_t* rng_seg;             // [rng_cap] first | last segment << 16
+  int32_t* rng_model;           // [rng_cap] model (0 for unused entries)
+  int32_t* rng_len;             // [rng_cap] the tile's length (-1 for unused entries)
+  int32_t* n_rng;               // device count of range items
+  int rng_cap;
 };
 // Plan scratch bytes for S sequences (bcnt, hist, n_valid).
 inline size_t mma_plan_scratch_bytes(int64_t S) {
@@ -595,26 +612,62 @@ inline size_t mma_plan_scratch_bytes(int64_t S) {
 }
 cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st);
 
+// The adjoint's pass kernel (mma_pass.cu): for every group of tiles of one
+// model, the forward recursion (direction 0: checkpoints of alpha, per-step
+// exponents, log P and the last row sum) or the backward recursion run as the
+// forward one with A in place of A^T in reversed time (direction 1:
+// checkpoints of the beta-side operand Y_t = b(o_t) . beta_t, scaled).
+struct MmaPassLaunch {
+  SeqArgs seq;
+  ModelArgs mod;                // probability tables padded to NP
+  const int32_t* sorted;        // plan: tile rows
+  const int32_t* tile_start;
+  const int32_t* tile_rows;
+  const int32_t* tile_model;
+  const int32_t* tile_len;
+  const int32_t* pass_tiles;    // [groups][NT] tile ids (-1: none)
+  const int32_t* n_pass;        // device count of groups; items = 2 * groups
+  int labelled;
+  float* loglik;                // [S] or [S][K]
+  uint8_t* ckx;                 // per tile: alpha images at t = c C, c = 0 .. NS - 1
+  uint8_t* cky;                 // per tile: Y images at t = c C, c = 1 .. NS - 1
+  int64_t ck_stride;            // bytes per tile (of each of ckx, cky)
+  int8_t* gexp;                 // per tile: [max_len][128] forward scale exponents
+  int64_t gexp_stride;          // bytes per tile
+  float* s_last;                // per tile: [128] row sum at the row's last step (0: none,
+                                // NaN: invalid row)
+  int32_t* queue;
+  int32_t* status;
+  uint32_t wait_limit;
+};
+cudaError_t launch_fb_pass(int NP, const MmaPassLaunch& a, cudaStream_t st);
+
+// The adjoint's second kernel (mma_fb.cu): one work item per (tile, range of
+// checkpoint segments), from the pass kernel's checkpoints.
 struct MmaFbLaunch {
   SeqArgs seq;
   ModelArgs mod;                // probability tables padded to NP
   const float* weight;          // [S] or [S][K], NULL = 1
-  float* loglik;                // [S] or [S][K]
   const int32_t* sorted;
   const int32_t* tile_start;
   const int32_t* tile_rows;
   const int32_t* tile_model;
   const int32_t* tile_len;
-  const int32_t* tile_order;
-  const int32_t* n_tiles;
+  const int32_t* rng_tile;      // [items] tile of each item
+  const int32_t* rng_seg;       // [items] first | last segment << 16
+  const int32_t* n_rng;         // device count of items
   int labelled;
-  float* slots;                 // [tile][slot_floats] per-tile counts
+  float* slots;                 // [item][slot_floats] per-item counts
   int64_t slot_floats;
-  uint8_t* ckpt;                // per CTA: checkpoint images
+  const uint8_t* ckx;           // per tile: alpha checkpoint images (the pass kernel's)
+  const uint8_t* cky;           // per tile: Y checkpoint images
+  int64_t ck_stride;
+  const int8_t* gexp;           // per tile: [max_len][128] forward scale exponents
+  int64_t gexp_stride;
+  const float* s_last;          // per tile: [128] row sum at the row's last step
   uint8_t* scr;                 // per CTA: recomputed segment images
-  int8_t* gexp;                 // per CTA: [max_len][128] forward scale exponents
   float* gbuf;                  // per CTA: [128][NP] gamma_1 rows
-  int64_t ckpt_bytes, scr_bytes, gexp_bytes;  // per-CTA strides
+  int64_t scr_bytes;            // per-CTA stride of scr
   int32_t* queue;
   int32_t* status;
   uint32_t wait_limit;          // polls before a step's mbarrier wait gives up

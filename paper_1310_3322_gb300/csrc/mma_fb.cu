@@ -1,11 +1,18 @@
-// mma_fb.cu -- forward-backward adjoint on the tensor cores for N = 64 or 128
-// states (Sec. 2.7 "Baum-Welch", its E-step; Rabiner 1989 eqs. 24-25
-// backward variable, 37 xi, 38 gamma), the tensor-core twin of fb.cu.
+// mma_fb.cu -- the second kernel of the forward-backward adjoint on the tensor
+// cores for N = 64 or 128 states (Sec. 2.7 "Baum-Welch", its E-step; Rabiner
+// 1989 eqs. 24-25 backward variable, 37 xi, 38 gamma), the tensor-core twin
+// of fb_seg.cu's segment kernel.
 //
 // A tile is 128 (sequence, model) pairs of ONE model (the plan kernel groups
 // them, rows sorted by decreasing length bucket; the tile runs for its longest
-// row). Per time step every product of the
-// recursion is a dense contraction over those 128 rows or over the states:
+// row Lt), cut into NS checkpoint segments of C steps. The pass kernel
+// (mma_pass.cu) has run the tile's forward recursion, keeping alpha at every
+// segment start and every step's scale exponent, and its backward recursion,
+// keeping the backward operand Y at every segment start. A work item here is
+// one RANGE of consecutive segments of one tile (the plan's range items), so
+// the segments of a long tile are processed side by side on many SMs instead
+// of as one chain. Per time step every product is a dense contraction over the
+// tile's 128 rows or over the states:
 //   forward    D[m][j]  = sum_i X_{t-1}[m][i] a_ij         (M=128, N=NP, K=NP)
 //   backward   D[m][i]  = sum_j Y_{t+1}[m][j] a_ij         (M=128, N=NP, K=NP)
 //   xi         XI[i][j] += sum_m X_t[m][i] Y_{t+1}[m][j]   (M=128, N=NP, K=128 rows)
@@ -15,37 +22,38 @@
 // 128 x NP BF16 "row images" (row m contiguous in 8-column groups); the same
 // bytes are the K-major operand of the per-row products and the MN-major
 // operand of the contractions over rows, so no operand is ever transposed.
-// XI and CB accumulate over the whole tile in tensor memory and are written
-// once per tile to the tile's slot; the slots are summed in a fixed order
+// XI and CB accumulate over the whole item in tensor memory and are written
+// once per item to the item's slot; the slots are summed in a fixed order
 // (bitwise reproducible). At N = 64 the xi product uses M = 128 with rows
 // 64..127 of the A operand running into the next buffer: those accumulator
 // rows are never read.
 //
-// Scaling. The forward pass is the one of mma_forward.cu: X_t = bf16(D_t .
-// b(o_t) . 2^-g_t) with the exponent g_t of the previous step's row sum
-// (one step late, clamped), log P = ln sigma_{T-1} + (sum g) ln 2. The
-// exponents are stored (one byte per row and step) so the recompute repeats
-// phase 1 bit for bit. Backward, with Bt_t = A Y_{t+1} (Bt_{T-1} = 1):
-//   G_t = X_t . Bt_t . c_t,    Y_t = b(o_t) . Bt_t . 2^-g_t . c_t,
-// with c_{T-1} = w / sigma_{T-1} and c_t = w / (c_{t+1} rho_{t+1}),
-// rho_t = sum_i X_t(i) Bt_t(i). In exact arithmetic rho_t = c_{t+1} rho_{t+1},
-// so every step's gamma sums to the row weight w; using the previous step's
-// measured sum keeps the BF16 rounding of one step from accumulating over T
-// (the same one-step-late idea as the forward scaling, and no extra barrier).
-//
-// Memory (Sec. 2.7, checkpointed adjoint): phase 1 keeps X every C steps,
-// C = ceil(sqrt(L)) for the tile's longest row L (at most 16 while L <= 8192,
-// so one segment's recomputed images stay in L2); phase 2 walks the
-// segments backwards, recomputing a segment's X images into a per-CTA buffer
-// and then running the backward recursion over it.
+// Per segment (from the range's last to its first): the X images of the
+// segment are recomputed from its checkpoint with the pass kernel's exponents
+// (the same rounding as the pass: X_t = bf16(D_t . b(o_t) . 2^-f_t)), then the
+// backward recursion runs over it. With Bt_t = A Y_{t+1} (Bt_{T-1} = 1):
+//   G_t = X_t . Bt_t . c_t,    Y_t = b(o_t) . Bt_t . 2^-f_t . c_t,
+// with c_{T-1} = w / sigma_{T-1} (sigma from the pass) and
+// c_t = w / (c_{t+1} rho_{t+1}), rho_t = sum_i X_t(i) Bt_t(i). In exact
+// arithmetic rho_t = c_{t+1} rho_{t+1}, so every step's gamma sums to the row
+// weight w; using the previous step's measured sum keeps the BF16 rounding of
+// one step from accumulating over T (no extra barrier per step).
+// A range that ends before its tile's last segment starts from the pass
+// kernel's Y at its end, t1 = (last segment + 1) C, which carries an arbitrary
+// scale per row: one extra product D = Y_{t1} A^T gives
+// rho = sum_i X_{t1-1}(i) D(i), Y_{t1} is rescaled in place by w / rho, and
+// the recursion continues with c = 1 -- step t1 - 1 then looks exactly as if
+// the recursion had come from the sequence's end. (Rows whose last step lies
+// inside the range start there from Bt = 1, as in any range.)
 //
 // Ordering per backward step (single-buffered operands): the step's MMAs are
 // issued as [emissions of step t+1, xi of step t, backward of step t] under
 // one commit, so when the epilogue of step t starts every operand buffer is
-// free to be rewritten. Every mbarrier wait is bounded; on timeout the kernel
-// sets HMM_STATUS_TIMEOUT, waits (bounded) for its own MMAs and copies and
-// leaves.
+// free to be rewritten (N = 64: beta first on double-buffered operand sets).
+// Every mbarrier wait is bounded; on timeout the kernel sets
+// HMM_STATUS_TIMEOUT, waits (bounded) for its own MMAs and copies and leaves.
 #include "hmm_internal.cuh"
+#include "mma_rows.cuh"
 #include "tc.cuh"
 
 namespace hmmgb {
@@ -92,11 +100,6 @@ static_assert(MmaFbCfg<128, 2>::TMEM_USED <= 512, "tensor memory budget");
 
 constexpr uint32_t kFbWaitLimit = 1u << 24;  // polls of the drain waits after an abort
 
-// Byte offset of 8-column group c8 of row m in a 128 x NP row image.
-template <int NP>
-__device__ __forceinline__ uint32_t img_off(int m, int c8) {
-  return (uint32_t)((m & 7) * 16 + c8 * 128 + (m >> 3) * NP * 16);
-}
 
 // COLS consecutive FP32 values from tensor memory (one row = one lane).
 template <int COLS>
@@ -108,33 +111,6 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[COLS]) {
 
 __device__ __forceinline__ float2 unpack_bf16(uint32_t w) {
   return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
-
-__device__ __forceinline__ int exponent_of_fb(float s) {
-  if (s < 0x1p-120f) return frexp2(s * 0x1p64f) - 64;
-  return frexp2(s);
-}
-
-// Forward-pass row state (identical in all threads of a row).
-struct FbRow {
-  int F;          // sum of applied exponents
-  int f;          // exponent for the next step
-  bool dead, bad, written;
-  int err;
-  float ll;       // log-likelihood
-  float S_last;   // row sum at the last step
-};
-
-__device__ __forceinline__ void fb_close(FbRow& st, float sigma, int t, int T) {
-  if (t >= T || st.dead || st.bad) return;
-  if (sigma == 0.f) { st.dead = true; return; }
-  if (!(sigma > 0.f) || isinf(sigma)) { st.bad = true; st.err |= HMM_STATUS_PARAM; return; }
-  if (t == T - 1) {
-    st.ll = (float)(log((double)sigma) + (double)st.F * 0.69314718055994530942);
-    st.S_last = sigma;
-    st.written = true;
-  }
-  st.f = min(126, max(-126, exponent_of_fb(sigma)));
 }
 
 // Per-thread view of one tile row: the row, its column range (in sub-chunks
@@ -248,7 +224,8 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
   uint64_t* b_seg = bars + 4;    // segment-end emission product: control only
   uint64_t* b_g = bars + 5;      // checkpoint -> forward operand
   uint64_t* b_x = bars + 6;      // [2] X_t images
-  uint64_t* b_fin = bars + 8;    // teardown after an abort (bars + 9 unused)
+  uint64_t* b_fin = bars + 8;    // teardown after an abort
+  uint64_t* b_y = bars + 9;      // Y checkpoint -> backward operand (a range's start)
   volatile int32_t* misc = reinterpret_cast<volatile int32_t*>(smem + L::OFF_MISC);
   enum { M_TMEM = 0, M_ITEM = 1, M_ABORT = 2 };
 
@@ -284,19 +261,17 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
   const uint32_t aY = tc::smem_u32(sY), aG = tc::smem_u32(sG), aOH = tc::smem_u32(sOH);
   constexpr uint32_t SBO = NP * 16;
 
-  uint8_t* ckpt = a.ckpt + (size_t)blockIdx.x * a.ckpt_bytes;
   uint8_t* scr = a.scr + (size_t)blockIdx.x * a.scr_bytes;
-  int8_t* gexp = a.gexp + (size_t)blockIdx.x * a.gexp_bytes;
   float* gbuf = a.gbuf + (size_t)blockIdx.x * 128 * NP;
 
   // barrier phases: the epilogue threads track b_done and b_x, the control
   // lane every barrier it waits on (each waiter waits every phase, in order)
   uint32_t ph_done = 0, ph_x[2] = {0, 0};
-  uint32_t c_rdy = 0, c_aux[2] = {0, 0}, c_seg = 0, c_g = 0;
+  uint32_t c_rdy = 0, c_aux[2] = {0, 0}, c_seg = 0, c_g = 0, c_y = 0;
   uint32_t c_x[2] = {0, 0};      // parity the next load into each X buffer completes
   uint32_t c_xpar[2] = {0, 0};   // ... and that of the last one issued
-  bool c_xpend[2] = {false, false}, c_gpend = false;
-  uint32_t c_gpar = 0;
+  bool c_xpend[2] = {false, false}, c_gpend = false, c_ypend = false;
+  uint32_t c_gpar = 0, c_ypar = 0;
   int cur_model = -1;
   volatile int32_t* abortp = misc + M_ABORT;
 
@@ -305,8 +280,9 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
     if (tid == 0) misc[M_ITEM] = atomicAdd(a.queue, 1);
     __syncthreads();
     const int item = misc[M_ITEM];
-    if (item >= __ldcg(a.n_tiles) || misc[M_ABORT]) break;
-    const int tile = a.tile_order[item];
+    if (item >= __ldcg(a.n_rng) || misc[M_ABORT]) break;
+    const int tile = a.rng_tile[item];
+    const int seg_lo = a.rng_seg[item] & 0xffff, seg_hi = a.rng_seg[item] >> 16;
     const int k = a.tile_model[tile];
     const int start = a.tile_start[tile];
     const int nrows = a.tile_rows[tile];
@@ -334,6 +310,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
     }
     const int C = fb_mma_segment(Lt);
     const int NS = (Lt + C - 1) / C;
+    // a range that stops short of the tile's last segment restarts the
+    // backward recursion from the pass kernel's Y checkpoint at its end
+    const bool cont = seg_hi < NS - 1;
+    const uint8_t* ckx = a.ckx + (size_t)tile * a.ck_stride;
+    const uint8_t* cky = a.cky + (size_t)tile * a.ck_stride;
+    const int8_t* gexp = a.gexp + (size_t)tile * a.gexp_stride;
 
     if (ctrl) {
       // ======================= control lane: every MMA and copy =======================
@@ -367,19 +349,19 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         auto wait_aux = [&](int b) {
           if (aux_pend[b] && ok) { wait_c(&b_aux[b], c_aux[b]); aux_pend[b] = false; }
         };
-        // phase 1
-        for (int t = 1; t < Lt && ok; ++t) {
-          if (!wait_c(b_rdy, c_rdy)) break;
-          issue_fwd();
-        }
-        if (ok) wait_c(b_rdy, c_rdy);  // phase 1 finished, checkpoints in memory
-        // phase 2
-        for (int seg = NS - 1; seg >= 0 && ok; --seg) {
+        for (int seg = seg_hi; seg >= seg_lo && ok; --seg) {
           const int t0 = seg * C, t1 = min(t0 + C, Lt);
-          const uint8_t* ck = ckpt + (size_t)seg * IMG;
+          const uint8_t* ck = ckx + (size_t)seg * IMG;
           auto img_of = [&](int t) -> const uint8_t* {
             return t == t0 ? ck : scr + (size_t)(t - t0) * IMG;
           };
+          const bool restart = seg == seg_hi && cont;
+          if (restart) {  // Y_{t1} of the pass kernel into the operand set of step t1
+            tc::mbar_arrive_expect_tx(b_y, IMG);
+            tc::bulk_g2s(aY + (t1 % NB) * IMG, cky + (size_t)(seg + 1) * IMG, IMG, b_y);
+            c_ypend = true;
+            c_ypar = c_y;
+          }
           if (t1 - t0 > 1) {  // recompute from the checkpoint
             tc::mbar_arrive_expect_tx(b_g, IMG);
             tc::bulk_g2s(aXO, ck, IMG, b_g);
@@ -394,7 +376,20 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             if (!ok || !wait_c(b_rdy, c_rdy)) break;  // images of the segment in memory
           }
           // backward
-          if (XIB == 2 || t1 - 1 < Lt - 1) load_x(t1 - 1, img_of(t1 - 1));
+          load_x(t1 - 1, img_of(t1 - 1));
+          if (restart) {
+            // D = Y_{t1} . A^T once, for the epilogue's renormalisation of Y_{t1}
+            if (!wait_c(b_y, c_y)) break;
+            c_ypend = false;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < NP / 16; ++ks)
+              tc::mma_bf16(d_tm, tc::smem_desc(aY + (t1 % NB) * IMG + ks * 256, 128, SBO),
+                           tc::smem_desc(aAT + ks * 32 * NP, NP * 16, 128), id_km,
+                           ks > 0 ? 1u : 0u);
+            tc::mma_commit(b_done);
+            if (!wait_c(b_rdy, c_rdy)) break;  // Y_{t1} rescaled in place
+          }
           bool cb_pending = false;
           for (int t = t1 - 1; t >= t0 && ok; --t) {
             const int S1 = (t + 1) % NB;  // operand set written by the previous step
@@ -488,6 +483,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           tc::mma_commit(b_fin);  // arrives once every MMA issued so far is done
           tc::mbar_wait_bounded(b_fin, 0, kFbWaitLimit);
           if (c_gpend) tc::mbar_wait_bounded(b_g, c_gpar, kFbWaitLimit);
+          if (c_ypend) tc::mbar_wait_bounded(b_y, c_ypar, kFbWaitLimit);
           for (int b = 0; b < XIB; ++b)
             if (c_xpend[b]) tc::mbar_wait_bounded(&b_x[b], c_xpar[b], kFbWaitLimit);
         }
@@ -502,6 +498,9 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
       const size_t oidx = a.labelled ? (size_t)s : (size_t)s * K + k;
       const float w = has ? (a.weight ? a.weight[oidx] : 1.f) : 0.f;
       const int32_t* o = a.seq.symbols + (has ? a.seq.offsets[s] : 0);
+      // the pass kernel's row sum at the row's last step: 0 = no counts
+      // (impossible sequence), NaN = invalid row
+      const float s_last = a.s_last[(size_t)tile * 128 + row];
       auto sym_at = [&](int t) -> int {  // symbol at step t (0 past the row's end)
         if (t >= T) return 0;
         const int v = __ldg(o + t);
@@ -544,73 +543,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         return sum;
       };
       bool run = true;
-
-      // ---------------- phase 1: forward, checkpoints every C steps ----------------
-      FbRow st;
-      st.F = 0; st.f = 0; st.dead = false; st.bad = false; st.written = false;
-      st.err = 0; st.ll = 0.f; st.S_last = 0.f;
-      {
-        int o0 = T > 0 ? __ldg(o) : 0;
-        if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
-        const bool live = T > 0 && !st.bad;
-        if constexpr (!L::EMIS) me.emis_all(pf, o0);
-        const float* pik = a.mod.pip + (size_t)k * NP + me.col0;
-        float sum = 0.f;
-#pragma unroll
-        for (int sub = 0; sub < NSUB; ++sub) {
-          float y[SUB];
-#pragma unroll
-          for (int i = 0; i < SUB; ++i) y[i] = __ldg(pik + sub * SUB + i);
-          if constexpr (L::EMIS) me.emis_sub(bsm, o0, sub);
-          uint32_t wv[SUB / 2];
-          sum += fwd_epilogue<SUB>(y, L::EMIS ? bsm : pf + sub * SUB, 0, live, wv);
-          me.put(sXO, sub, wv);
-          me.put_global(ckpt, sub, wv);
-        }
-        psum[(0 * TPR + h) * 128 + row] = sum;
-        if (h == 0) __stcg(gexp + row, (int8_t)0);
-      }
-      int o_n1 = (1 < T) ? __ldg(o + 1) : 0;  // symbol of the next step
-      int o_n2 = (2 < T) ? __ldg(o + 2) : 0;  // and the one after
-      if constexpr (!L::EMIS) me.emis_all(pf, (unsigned)o_n1 < (unsigned)M ? o_n1 : 0);
-      tc::fence_proxy_async();
-      if (Lt == 1) tc::fence_proxy_async_all();
-      run = handoff();
-      for (int t = 1; t < Lt && run; ++t) {
-        fb_close(st, row_sum((t - 1) & 1), t - 1, T);
-        const int ot = o_n1;
-        o_n1 = o_n2;
-        o_n2 = (t + 2 < T) ? __ldg(o + t + 2) : 0;
-        if (t < T && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
-        const bool live = t < T && !st.dead && !st.bad;
-        if (live) st.F += st.f;
-        if (h == 0) __stcg(gexp + (size_t)t * 128 + row, (int8_t)st.f);
-        if constexpr (L::EMIS) me.emis_sub(bsm, live ? ot : 0, 0);
-        wait_e(b_done, ph_done);
-        const float sum = fwd_step(st.f, live, t % C == 0 ? ckpt + (size_t)(t / C) * IMG : nullptr);
-        psum[((t & 1) * TPR + h) * 128 + row] = sum;
-        if constexpr (!L::EMIS)
-          me.emis_all(pf, (t + 1 < T && (unsigned)o_n1 < (unsigned)M) ? o_n1 : 0);
-        tc::fence_proxy_async();
-        if (t == Lt - 1) tc::fence_proxy_async_all();  // checkpoints, read by bulk copies
-        run = handoff();
-      }
-      if (run && Lt > 0) fb_close(st, row_sum((Lt - 1) & 1), Lt - 1, T);
-      if (has && h == 0) {
-        float out = st.ll;
-        if (st.bad) out = __int_as_float(0x7fc00000);
-        else if (st.dead) out = -INFINITY;
-        else if (!st.written) out = __int_as_float(0x7fc00000);
-        if (st.bad && st.err) set_status(a.status, st.err);
-        a.loglik[oidx] = out;
-      }
-      if (run) run = tc::bar_and(1, NEP, *abortp == 0);  // sums read before phase 2 writes them
-
-      // ---------------- phase 2: segments backwards ----------------
-      const bool act = has && st.written && !st.dead && !st.bad && w != 0.f;
+      const bool act = has && w != 0.f && s_last > 0.f && !isinf(s_last);
       float c = 0.f;               // this row's current normaliser
       int kprev[2] = {-1, -1};     // one-hot entries set in each operand set
-      for (int seg = NS - 1; seg >= 0 && run; --seg) {
+      for (int seg = seg_hi; seg >= seg_lo && run; --seg) {
         const int t0 = seg * C, t1 = min(t0 + C, Lt);
         // (R) recompute X over the segment from its checkpoint
         if (t1 - t0 > 1) {
@@ -641,6 +577,56 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           if (!run) break;
         }
 
+        // (P) a range's restart: D = Y_{t1} A^T from the pass kernel's
+        // checkpoint of Y_{t1} (any positive scale per row). With
+        // rho = sum_i X_{t1-1}(i) D(i), Y_{t1} <- Y_{t1} w / rho makes step
+        // t1 - 1 normalised as if the recursion had come from the sequence's
+        // end (its gamma and xi then sum to w, and c = 1); rows whose last
+        // step lies in this range start there instead and take no Y_{t1}.
+        if (seg == seg_hi && cont) {
+          const int SX = (t1 - 1) % 2, S1 = t1 % NB;
+          // the first backward step waits for the same X image phase again
+          fb_wait(&b_x[SX], ph_x[SX], abortp, a.wait_limit);
+          wait_e(b_done, ph_done);
+          float part = 0.f;
+#pragma unroll
+          for (int sub = 0; sub < NSUB; ++sub) {
+            float dv[SUB];
+            tmem_ld_cols<SUB>(d_tm + my_cols + (uint32_t)(sub * SUB), dv);
+            uint32_t xw[SUB / 2];
+            me.get(sXI + SX * IMG, sub, xw);
+#pragma unroll
+            for (int q = 0; q < SUB / 2; ++q) {
+              const float2 xv = unpack_bf16(xw[q]);
+              part = fmaf(xv.x, dv[2 * q], fmaf(xv.y, dv[2 * q + 1], part));
+            }
+          }
+          psum[((SX & 1) * TPR + h) * 128 + row] = part;
+          tc::bar_sync(1, NEP);
+          const float rho = row_sum(SX & 1);
+          const bool controw = act && T > t1;
+          float kappa = controw ? w / rho : 0.f;
+          if (!(rho > 0.f) || !isfinite(kappa)) kappa = 0.f;
+          const float2 k2 = make_float2(kappa, kappa);
+#pragma unroll
+          for (int sub = 0; sub < NSUB; ++sub) {
+            uint32_t yw[SUB / 2];
+            me.get(sY + S1 * IMG, sub, yw);
+#pragma unroll
+            for (int q = 0; q < SUB / 2; ++q) {
+              const float2 v = __fmul2_rn(unpack_bf16(yw[q]), k2);
+              yw[q] = tc::pack_bf16(v.x, v.y);
+            }
+            me.put(sY + S1 * IMG, sub, yw);
+          }
+          // the first backward step reads c_{t1} rho_{t1} = w (c = 1)
+          psum[(((t1 & 1) * TPR) + h) * 128 + row] = (h == 0 && kappa != 0.f) ? w : 0.f;
+          c = kappa != 0.f ? 1.f : 0.f;
+          tc::fence_proxy_async();
+          run = handoff();
+          if (!run) break;
+        }
+
         // (B) backward over the segment
         int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
         int onx = t1 - 2 >= t0 ? sym_at(t1 - 2) : 0;  // step t - 1, in flight
@@ -655,7 +641,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           if (has_mma) wait_e(b_done, ph_done);
           const bool is_init = act && t == T - 1;
           const bool on = act && t < T - 1;
-          if (is_init) c = w / st.S_last;
+          if (is_init) c = w / s_last;
           else if (on) c = w / (c * rho_prev);
           const bool live = (is_init || on) && isfinite(c);
           const float fc = exp2i(-gcur) * c;  // exact: c times a power of two
@@ -724,13 +710,14 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         run = handoff();
       }
       if (run) {
-        // ---------------- tile counts -> slot ----------------
-        float* slot = a.slots + (size_t)tile * a.slot_floats;
+        // ---------------- item counts -> slot ----------------
+        float* slot = a.slots + (size_t)item * a.slot_floats;
+        const bool xi_any = seg_lo * C < Lt - 1;  // some xi product was issued
         if (wq * 32 < NP) {  // xi rows i = row (warp-uniform)
 #pragma unroll
           for (int sub = 0; sub < NSUB; ++sub) {
             float v[SUB];
-            if (Lt >= 2) {
+            if (xi_any) {
               tmem_ld_cols<SUB>(xi_tm + my_cols + (uint32_t)(sub * SUB), v);
             } else {
 #pragma unroll
@@ -762,9 +749,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           }
         }
         tc::bar_sync(1, NEP);
-        if (tid < NP) {
+        if (tid < NP) {  // gamma_1 rows: only the range holding step 0 has them
           float sum = 0.f;
-          for (int m = 0; m < 128; ++m) sum += __ldcg(gbuf + (size_t)m * NP + tid);
+          if (seg_lo == 0)
+            for (int m = 0; m < 128; ++m) sum += __ldcg(gbuf + (size_t)m * NP + tid);
           slot[tid] = sum;
         }
       }

@@ -48,28 +48,6 @@
 
 namespace hmmgb {
 
-// AB: operand type, 1 = BF16 (kind::f16, two values per 32-bit column of
-// tensor memory), 2 = TF32 (kind::tf32, one value per column).
-// EMIS: the model's emission table lives in shared memory (M padded rows,
-// after the fixed part); otherwise NT tiles of per-row staging slots.
-template <int NP, int NT, int TPR, int AB = 1, bool EMIS = false>
-struct MmaFwdSmem {
-  static constexpr int kB = NP * NP * (AB == 1 ? 2 : 4);  // A^T
-  static constexpr int kES = NP * 4 + 16;         // padded emission row, FP32
-  static constexpr int kE = 128 * kES;            // one tile of emission rows
-  static constexpr int OFF_B = 0;
-  static constexpr int OFF_PS = kB;               // partial row sums [NT][TPR][128]
-  static constexpr int OFF_BAR = OFF_PS + NT * TPR * 128 * 4;  // mma[NT], emission[NT], fin[NT]
-  static constexpr int OFF_MISC = OFF_BAR + 3 * NT * 8;        // tmem, item, abort, last, warp max
-  static constexpr int OFF_E = (OFF_MISC + 24 * 4 + 127) / 128 * 128;  // staging or table
-  static constexpr int FIXED = OFF_E + (EMIS ? 0 : NT * kE);
-  // total bytes for M symbols
-  static constexpr int total(int M) { return FIXED + (EMIS ? M * kES : 0); }
-};
-constexpr int kFwdSmemMax = 227 * 1024;
-static_assert(MmaFwdSmem<128, 2, 2, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
-static_assert(MmaFwdSmem<64, 4, 1, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
-
 constexpr uint32_t kWaitLimit = 1u << 24;  // polls of the teardown's drain waits
 constexpr uint32_t kTmemCols = 512;  // per tile: D (NP cols) then X (NP/2 cols) at (512/NT) * tile
 constexpr int kMmaThreads = 512;

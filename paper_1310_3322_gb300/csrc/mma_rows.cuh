@@ -8,6 +8,37 @@
 
 namespace hmmgb {
 
+// AB: operand type, 1 = BF16 (kind::f16, two values per 32-bit column of
+// tensor memory), 2 = TF32 (kind::tf32, one value per column).
+// EMIS: the model's emission table lives in shared memory (M padded rows,
+// after the fixed part); otherwise NT tiles of per-row staging slots.
+template <int NP, int NT, int TPR, int AB = 1, bool EMIS = false>
+struct MmaFwdSmem {
+  static constexpr int kB = NP * NP * (AB == 1 ? 2 : 4);  // A^T
+  static constexpr int kES = NP * 4 + 16;         // padded emission row, FP32
+  static constexpr int kE = 128 * kES;            // one tile of emission rows
+  static constexpr int OFF_B = 0;
+  static constexpr int OFF_PS = kB;               // partial row sums [NT][TPR][128]
+  static constexpr int OFF_BAR = OFF_PS + NT * TPR * 128 * 4;  // mma[NT], emission[NT], fin[NT]
+  static constexpr int OFF_MISC = OFF_BAR + 3 * NT * 8;        // tmem, item, abort, last, warp max
+  static constexpr int OFF_E = (OFF_MISC + 24 * 4 + 127) / 128 * 128;  // staging or table
+  static constexpr int FIXED = OFF_E + (EMIS ? 0 : NT * kE);
+  // total bytes for M symbols
+  static constexpr int total(int M) { return FIXED + (EMIS ? M * kES : 0); }
+};
+constexpr int kFwdSmemMax = 227 * 1024;
+static_assert(MmaFwdSmem<128, 2, 2, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
+static_assert(MmaFwdSmem<64, 4, 1, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
+
+// Byte offset of 8-column group c8 of row m in a 128 x NP BF16 "row image"
+// (8-row x 16-byte core matrices: row m, columns 8 c8 .. 8 c8 + 7). The same
+// bytes are the K-major operand of a per-row product and the MN-major operand
+// of a contraction over rows; the adjoint's checkpoints are stored this way.
+template <int NP>
+__device__ __forceinline__ uint32_t img_off(int m, int c8) {
+  return (uint32_t)((m & 7) * 16 + c8 * 128 + (m >> 3) * NP * 16);
+}
+
 // Exponent e with s * 2^-e in [1, 2) for finite s > 0 (subnormals included).
 __device__ __forceinline__ int exponent_of(float s) {
   if (s < 0x1p-120f) return frexp2(s * 0x1p64f) - 64;
@@ -21,6 +52,7 @@ struct RowState {
   bool dead, bad, written;
   int err;
   float ll;
+  float slast;  // the row sum at the row's last step (set with ll)
 };
 
 // Starts the bulk copy of emission row `sym` into this row's slot.
@@ -72,6 +104,7 @@ __device__ __forceinline__ void close_step(RowState& st, float sigma, int t, int
   }
   if (t == Tn - 1) {
     st.ll = (float)(log((double)sigma) + (double)st.F * 0.69314718055994530942);
+    st.slast = sigma;
     st.written = true;
   }
   st.f = min(126, max(-126, exponent_of(sigma)));

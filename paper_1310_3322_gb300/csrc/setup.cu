@@ -828,6 +828,90 @@ __global__ void __launch_bounds__(kPlanThreads) plan_tiles_kernel(MmaPlanArgs a)
   if (tid == 0) *a.n_tiles = n_tiles;
 }
 
+// Work lists of the adjoint's two kernels (one block, after the tile stage).
+//  * pass groups: `group` tiles of one model that one CTA of the pass kernel
+//    runs side by side -- the tiles of a model in decreasing-length order
+//    (consecutive tile ids in labelled mode, every K-th id otherwise), cut
+//    into runs of `group`; groups ordered by their longest tile, longest
+//    first (stable in the leader's id);
+//  * range items: every tile's checkpoint segments cut into runs of `spr`
+//    (the last run shorter), tiles in tile_order (longest first).
+__global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(MmaPlanArgs a) {
+  extern __shared__ __align__(16) uint8_t plan_smem[];
+  SortSmem& m = *reinterpret_cast<SortSmem*>(plan_smem);
+  __shared__ int itmp[32];
+  __shared__ int total;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 32 * 256; i += kPlanThreads) m.wh[i] = 0;
+  const int n = *a.n_tiles;
+  const int step = a.labelled ? 1 : a.K;  // id distance of consecutive tiles of a model
+
+  // ---- pass groups: leaders (rank within the model a multiple of group)
+  int n_groups = 0;
+  int32_t* lead = a.pass_tmp;                  // leaders, id order
+  uint32_t* lkey = a.key_tmp;                  // their length keys
+  for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
+    const int id = c0 + tid;
+    int flag = 0;
+    if (id < n) {
+      const int k = a.tile_model[id];
+      const int rank = a.labelled ? (a.tile_start[id] - a.group_start[k]) / 128 : id / a.K;
+      flag = (rank % a.group) == 0 ? 1 : 0;
+    }
+    const int pos = n_groups + block_exclusive_scan<int>(flag, itmp, &total);
+    if (flag && pos < a.pass_cap) {
+      lead[pos] = id;
+      lkey[pos] = (uint32_t)len_key(a.tile_len[id]);
+    }
+    n_groups += total;
+    __syncthreads();
+  }
+  n_groups = min(n_groups, a.pass_cap);
+  int32_t* srt = a.pass_tmp + a.pass_cap;
+  stable_pass(lead, lkey, srt, a.key, n_groups, 0, m);
+  stable_pass(srt, a.key, lead, lkey, n_groups, 8, m);
+  for (int g = tid; g < n_groups; g += kPlanThreads) {
+    const int id = lead[g], k = a.tile_model[id];
+    for (int j = 0; j < a.group; ++j) {
+      const int q = id + j * step;
+      a.pass_tiles[g * a.group + j] = (q < n && a.tile_model[q] == k) ? q : -1;
+    }
+  }
+  if (tid == 0) *a.n_pass = n_groups;
+
+  // ---- range items, tiles longest first
+  int n_items = 0;
+  for (int c0 = 0; c0 < n; c0 += kPlanThreads) {
+    const int j = c0 + tid;
+    int nr = 0, tile = 0, ns = 0;
+    if (j < n) {
+      tile = a.tile_order[j];
+      const int L = a.tile_len[tile];
+      const int C = fb_mma_segment(L);
+      ns = (L + C - 1) / C;
+      nr = (ns + a.spr - 1) / a.spr;
+    }
+    const int base = n_items + block_exclusive_scan<int>(nr, itmp, &total);
+    for (int r = 0; r < nr; ++r) {
+      const int i = base + r;
+      if (i >= a.rng_cap) break;
+      const int lo = r * a.spr, hi = min(ns - 1, lo + a.spr - 1);
+      a.rng_tile[i] = tile;
+      a.rng_seg[i] = lo | (hi << 16);
+      a.rng_model[i] = a.tile_model[tile];
+      a.rng_len[i] = a.tile_len[tile];
+    }
+    n_items += total;
+    __syncthreads();
+  }
+  n_items = min(n_items, a.rng_cap);
+  for (int i = n_items + tid; i < a.rng_cap; i += kPlanThreads) {
+    a.rng_len[i] = -1;
+    a.rng_model[i] = 0;
+  }
+  if (tid == 0) *a.n_rng = n_items;
+}
+
 cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st) {
   const int smem = (int)sizeof(SortSmem);
   cudaError_t e;
@@ -867,6 +951,13 @@ cudaError_t launch_mma_plan(const MmaPlanArgs& a, cudaStream_t st) {
     uint32_t* tk = ck; ck = ok; ok = tk;
   }
   plan_tiles_kernel<<<1, kPlanThreads, smem, st>>>(a);
+  if (a.pass_tiles) {
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(plan_items_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem)))
+      return e;
+    plan_items_kernel<<<1, kPlanThreads, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ _SIG = {
 
 TIMING_KINDS = ("setup", "forward", "viterbi_scores", "viterbi_paths", "adjoint",
                 "count_reduce", "softmax_rows", "softmax_grad", "adam", "mstep", "scan_chunks",
-                "scan_combine")
+                "scan_combine", "adjoint_pass")
 
 
 def lib():

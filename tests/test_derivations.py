@@ -5,6 +5,13 @@ oracle on small random models (CPU only; nothing here touches the library):
   each chunk's product of step matrices A diag(b(o_t)) formed row by row
   from unit vectors with one power-of-two exponent per row, then combined in
   order against the largest term, give log P(O) (Rabiner eqs. 19-21);
+* tensor-core adjoint in segment ranges: the forward rows kept with the
+  one-step-late power-of-two exponents, the backward recursion
+  Y_t = b(o_t) o (A Y_{t+1}) 2^-f_t c_t with c_{T-1} = w / sigma_{T-1},
+  c_t = w / (c_{t+1} rho_{t+1}), run range by range, each range that ends
+  before the sequence restarting from an arbitrarily scaled checkpoint of
+  Y at its end rescaled by w / rho (rho = X_{t1-1} . A Y_{t1}) with c = 1,
+  reproduces the expected counts (Rabiner eqs. 24-25, 37-38);
 * adjoint above 128 states: Y_t = b(o_t) o beta_t obeys the forward
   recursion with A^T run backwards from Y_{T-1} = b(o_{T-1}), and with rows
   of arbitrary power-of-two scale, gamma_t = X_t o Bh_t / z_t and
@@ -148,3 +155,68 @@ def test_counts_from_arbitrarily_scaled_rows():
         z = X[t] @ Bh[t]
         wrong += A * np.outer(X[t] / z, B[:, obs[t + 1]] * Bh[t + 1] * 2.0 ** -f[t + 1])
     assert not np.allclose(wrong, rA[0], rtol=1e-3)
+
+
+def _range_counts(pi, A, B, obs, w, cuts, restart=True, seed=0):
+    """Counts by the segment-range recursion (ranges [cuts[r], cuts[r+1]) of
+    the steps, processed independently, each from checkpoints only)."""
+    T, N, M = obs.size, pi.size, B.shape[1]
+    rng = np.random.default_rng(seed)
+    # forward rows as the pass keeps them: X_t = (X_{t-1} A) o b(o_t) 2^-f_t,
+    # f_t the exponent of the previous row sum (one step late)
+    X = np.zeros((T, N))
+    f = np.zeros(T, int)
+    X[0] = pi * B[:, obs[0]]
+    for t in range(1, T):
+        f[t] = int(np.floor(np.log2(X[t - 1].sum())))
+        X[t] = (X[t - 1] @ A) * B[:, obs[t]] * 2.0 ** -f[t]
+    sigma = X[T - 1].sum()
+    # backward operand checkpoints: Y_t = b(o_t) o beta_t at an arbitrary scale
+    beta = np.ones((T, N))
+    for t in range(T - 2, -1, -1):
+        beta[t] = A @ (B[:, obs[t + 1]] * beta[t + 1])
+    Yck = {t: B[:, obs[t]] * beta[t] * 2.0 ** int(rng.integers(-30, 30)) for t in cuts[1:-1]}
+    cpi, cA, cB = np.zeros(N), np.zeros((N, N)), np.zeros((N, M))
+    for lo, t1 in zip(cuts[:-1], cuts[1:]):
+        c, rho_prev, Ynext = 0.0, 0.0, None
+        if t1 < T:
+            Ynext = Yck[t1]
+            rho = X[t1 - 1] @ (A @ Ynext)
+            if restart:
+                Ynext = Ynext * (w / rho)
+            c, rho_prev = 1.0, w
+        for t in range(t1 - 1, lo - 1, -1):
+            if t == T - 1:
+                c, Bt = w / sigma, np.ones(N)
+            else:
+                c, Bt = w / (c * rho_prev), A @ Ynext
+            G = X[t] * Bt * c
+            rho_prev = X[t] @ Bt
+            cB[:, obs[t]] += G
+            if t == 0:
+                cpi += G
+            if t < T - 1:
+                cA += A * np.outer(X[t], Ynext)
+            Ynext = B[:, obs[t]] * Bt * 2.0 ** -f[t] * c
+    return cpi, cA, cB
+
+
+@pytest.mark.parametrize("ranges", [1, 2, 3, 5, 11])
+def test_segment_ranges_restarted_from_scaled_checkpoints(ranges):
+    pi, A, B, obs = _case(13 + ranges, N=5, M=6, T=44)
+    T = obs.size
+    cuts = [int(round(r * T / ranges)) for r in range(ranges + 1)]
+    w = 1.7
+    cpi, cA, cB = _range_counts(pi, A, B, obs, w, cuts)
+    P = oracle.params(pi[None], A[None], B[None])
+    _, rpi, rA, rB, _ = oracle.forward_backward(P, obs, np.array([0], np.int64),
+                                                np.array([T], np.int32), None,
+                                                np.array([w], np.float64))
+    np.testing.assert_allclose(cpi, rpi[0], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(cA, rA[0], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(cB, rB[0], rtol=1e-9, atol=1e-12)
+    if ranges > 1:
+        # without the renormalisation the arbitrary checkpoint scale leaks
+        # into the counts of every range but the last
+        wpi, wA, wB = _range_counts(pi, A, B, obs, w, cuts, restart=False)
+        assert not np.allclose(wB, rB[0], rtol=1e-3)

@@ -87,6 +87,8 @@ def parse():
                          "cuhmm: the 512-state forward")
     ap.add_argument("--skip-others", action="store_true",
                     help="large: skip the batched and training summaries")
+    ap.add_argument("--quick", action="store_true",
+                    help="large: the timed step and per-kernel times only (profiling runs)")
     return ap.parse_args()
 
 
@@ -718,6 +720,14 @@ def run_large(args, emit=True):
     # kernels, two-level count reduction
     launches_per_step = (setup_launches(w.S) + 1) + (setup_launches(w.S, ordered=False)
                                                      + plan_launches(K, True) + 2 + 2)
+
+    if args.quick:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_max,
+                "config": {"workload": f"large K={K} N={N} M={M} S={w.S} (quick)"},
+                "kernel_ms": kms, "clocks": clk, "gpu_launches": launches_per_step * args.steps}
+        if emit and rank == 0:
+            print(json.dumps(line), flush=True)
+        return line
 
     # ---- the TF32 forward on the same data ----------------------------------
     ll32 = torch.empty_like(ll)
@@ -1414,7 +1424,7 @@ def main():
 def dispatch(args, rank):
     if args.workload == "large":
         line = run_large(args, emit=False)
-        if not args.skip_others and args.n_seqs is None:
+        if not args.skip_others and not args.quick and args.n_seqs is None:
             # the batched-recognition and training configurations, shortly:
             # their headline numbers beside the large one (own full lines with
             # --workload batched / training)

@@ -279,7 +279,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     const size_t img = (size_t)128 * NP * 2;
     const int max_len = q.max_len > 0 ? q.max_len : 1;
     const int nsmax = fb_mma_nsmax(max_len);
-    L.m_group = NP == 64 ? 4 : 2;
+    L.m_group = fb_pass_tiles_per_cta(NP, cap);
     L.m_spr = fb_mma_spr(nsmax, cap);
     L.m_pass_cap = cap;
     L.m_rng_cap = cap * ((nsmax + L.m_spr - 1) / L.m_spr);
@@ -313,6 +313,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.m_scr_bytes = (int64_t)fb_mma_segment(max_len) * img;
     L.m_scr = off; off = align256(off + (size_t)grid * L.m_scr_bytes);
     L.m_gbuf = off; off = align256(off + (size_t)grid * 128 * NP * 4);
+    L.m_psum = off; off = align256(off + (size_t)grid * 2 * 4 * 128 * 4);
   }
   L.total = off;
   return L;
@@ -698,7 +699,7 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   pa.wait_limit = wait_limit_polls();
   {
     Timed tm(T_FB_PASS, st);
-    e = launch_fb_pass(NP, pa, st);
+    e = launch_fb_pass(NP, L.m_group, pa, st);
     tm.stop();
   }
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint pass launch");
@@ -720,6 +721,7 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   f.s_last = pa.s_last;
   f.scr = at<uint8_t>(ws, L.m_scr);
   f.gbuf = at<float>(ws, L.m_gbuf);
+  f.psum = at<float>(ws, L.m_psum);
   f.scr_bytes = L.m_scr_bytes;
   f.queue = &at<WsHeader>(ws, 0)->queue[3];
   f.status = &at<WsHeader>(ws, 0)->status;

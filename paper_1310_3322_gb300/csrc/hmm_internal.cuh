@@ -53,6 +53,7 @@ struct WsLayout {
   // the tensor-core adjoint's two kernels: work lists, per-tile Y checkpoints
   // and last-step row sums
   size_t m_pass, m_ptmp, m_npass, m_rtile, m_rseg, m_rmodel, m_rlen, m_nrng, m_cky, m_slast;
+  size_t m_psum;
   int m_pass_cap, m_rng_cap, m_spr, m_group;
 };
 
@@ -640,7 +641,10 @@ struct MmaPassLaunch {
   int32_t* status;
   uint32_t wait_limit;
 };
-cudaError_t launch_fb_pass(int NP, const MmaPassLaunch& a, cudaStream_t st);
+// Tiles per CTA of the pass kernel for a batch of up to `tiles` tiles (the
+// plan's pass groups have this many tiles).
+int fb_pass_tiles_per_cta(int NP, int tiles);
+cudaError_t launch_fb_pass(int NP, int tiles_per_cta, const MmaPassLaunch& a, cudaStream_t st);
 
 // The adjoint's second kernel (mma_fb.cu): one work item per (tile, range of
 // checkpoint segments), from the pass kernel's checkpoints.
@@ -667,6 +671,7 @@ struct MmaFbLaunch {
   const float* s_last;          // per tile: [128] row sum at the row's last step
   uint8_t* scr;                 // per CTA: recomputed segment images
   float* gbuf;                  // per CTA: [128][NP] gamma_1 rows
+  float* psum;                  // per CTA: [2][4][128] row partial sums
   int64_t scr_bytes;            // per-CTA stride of scr
   int32_t* queue;
   int32_t* status;

@@ -60,13 +60,12 @@ namespace hmmgb {
 
 template <int NP, int MB>
 struct MmaFbCfg {
-  // epilogue threads per row: 4 at N = 64 (17 warps: at most 96 registers a
-  // thread), 2 at N = 128 (9 warps, room for 64 prefetched emission values)
-  static constexpr int TPR = NP == 64 ? 4 : 2;
+  // four epilogue threads per row (16 warps, at most 120 registers a thread)
+  static constexpr int TPR = 4;
   static constexpr int NEP = 128 * TPR;          // epilogue threads
   static constexpr int NTH = NEP + 32;           // + the control warp (MMAs and copies)
-  static constexpr int COLS = NP / TPR;          // columns per epilogue thread (16 or 64)
-  static constexpr int SUB = COLS < 32 ? COLS : 32;  // columns per tensor-memory load
+  static constexpr int COLS = NP / TPR;          // columns per epilogue thread (16 or 32)
+  static constexpr int SUB = 16;                 // columns per tensor-memory load
   static constexpr int NSUB = COLS / SUB;
   static constexpr int IMG = 128 * NP * 2;       // one 128-row BF16 image
   static constexpr int MAT = NP * NP * 2;        // the BF16 transition image
@@ -82,9 +81,8 @@ struct MmaFbCfg {
   static constexpr int OFF_OH = OFF_G + NB * IMG;      // one-hot [k][m] sets, MB blocks of 128 x 128
   static constexpr int OFF_XOP = OFF_OH + NB * MB * 32768;  // forward X operand (else aliases gamma)
   static constexpr int OFF_B = OFF_XOP + (DB ? IMG : 0);    // emission rows b(k), k < 128 (EMIS)
-  static constexpr int OFF_PS = OFF_B + (EMIS ? 128 * ES : 0);  // row partial sums [2][TPR][128]
   static constexpr int NBAR = 10;                // mbarriers (see the kernel)
-  static constexpr int OFF_BAR = OFF_PS + 2 * TPR * 128 * 4;
+  static constexpr int OFF_BAR = OFF_B + (EMIS ? 128 * ES : 0);
   static constexpr int OFF_MISC = OFF_BAR + 128;
   static_assert(NBAR * 8 <= OFF_MISC - OFF_BAR, "mbarrier area");
   static constexpr int TOTAL = OFF_MISC + 64;
@@ -133,12 +131,48 @@ struct FbThread {
       b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
     }
   }
-  __device__ __forceinline__ void emis_all(float (&b)[L::COLS], int sym) const {
-    const float4* p = reinterpret_cast<const float4*>(Bk + (size_t)sym * NP + col0);
+  // This thread's COLS columns of emission row `sym` from memory, in two
+  // halves so the loads' latency hides behind the next MMA wait: emis_load
+  // at the end of a step, emis_ready after the next step's wait. The 32
+  // lanes of a warp are 32 rows with unrelated symbols, so a per-lane load
+  // would touch 32 cache lines per warp instruction. Instead the Q = COLS / 8
+  // lanes of a group load the Q rows of the group in turn, 32 contiguous
+  // bytes per lane (32 / Q lines per warp instruction), and a Q x Q butterfly
+  // transpose within the group (element = 8 values) hands every lane its own
+  // row. Every lane of the warp must call both (full-warp shuffles).
+  __device__ __forceinline__ void emis_load(float (&w)[L::COLS], int sym) const {
+    constexpr int Q = L::COLS / 8;
+    const int lane = threadIdx.x & 31, j = lane & (Q - 1);
 #pragma unroll
-    for (int q = 0; q < L::COLS / 4; ++q) {
-      const float4 v = __ldg(p + q);
-      b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+    for (int i = 0; i < Q; ++i) {
+      const int si = __shfl_sync(HMM_FULL_MASK, sym, (lane & ~(Q - 1)) | i);
+      const float* p = Bk + (size_t)si * NP + col0 + 8 * j;  // 32-byte aligned
+      asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=f"(w[8 * i]), "=f"(w[8 * i + 1]), "=f"(w[8 * i + 2]), "=f"(w[8 * i + 3]),
+                     "=f"(w[8 * i + 4]), "=f"(w[8 * i + 5]), "=f"(w[8 * i + 6]), "=f"(w[8 * i + 7])
+                   : "l"(p));
+    }
+  }
+  __device__ __forceinline__ void emis_ready(float (&w)[L::COLS]) const {
+    constexpr int Q = L::COLS / 8;
+    const int j = threadIdx.x & (Q - 1);
+    // lane j holds chunk j of rows 0..Q-1 of the group; swap the lane bit and
+    // the row bit, one bit at a time, so that lane j holds row j's chunks
+#pragma unroll
+    for (int bit = 1; bit < Q; bit <<= 1) {
+      const bool hi = (j & bit) != 0;
+#pragma unroll
+      for (int i0 = 0; i0 < Q; ++i0) {
+        if (i0 & bit) continue;
+        const int i1 = i0 | bit;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float y =
+              __shfl_xor_sync(HMM_FULL_MASK, hi ? w[8 * i0 + e] : w[8 * i1 + e], bit);
+          if (hi) w[8 * i0 + e] = y;
+          else w[8 * i1 + e] = y;
+        }
+      }
     }
   }
   // sub-chunk `sub` of this thread's columns of a row image (BF16 pairs)
@@ -189,8 +223,9 @@ __device__ __forceinline__ float fwd_epilogue(float (&y)[COLS], const float* b, 
 // abort; a timeout records one.
 __device__ __forceinline__ bool fb_wait(uint64_t* bar, uint32_t parity,
                                         volatile int32_t* abort_flag, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (i == 0 ? tc::mbar_probe(bar, parity) : tc::mbar_test(bar, parity)) return true;
+  if (limit > 0 && tc::mbar_probe(bar, parity)) return true;
+  for (uint32_t i = 1; i < limit; ++i) {
+    if (tc::mbar_test(bar, parity)) return true;
     if ((i & 31) == 31 && *abort_flag) return false;
   }
   *abort_flag = 1;
@@ -216,7 +251,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
   uint8_t* sG = smem + L::OFF_G;
   uint8_t* sOH = smem + L::OFF_OH;
   uint8_t* sXO = smem + L::XOP;
-  float* psum = reinterpret_cast<float*>(smem + L::OFF_PS);  // [2][TPR][128]
+  // row partial sums [2][TPR][128], per CTA in memory (L2): written at a
+  // step's end, read at the next step's start and needed only after its MMA
+  // wait, so the loads' latency hides behind that wait
+  float* psum = a.psum + (size_t)blockIdx.x * 2 * TPR * 128;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   uint64_t* b_rdy = bars + 0;    // epilogue -> control: operands written
   uint64_t* b_done = bars + 1;   // the products the epilogue waits for
@@ -522,7 +560,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
       auto row_sum = [&](int par) {
         float sum = 0.f;
 #pragma unroll
-        for (int q = 0; q < TPR; ++q) sum += psum[(par * TPR + q) * 128 + row];
+        for (int q = 0; q < TPR; ++q) sum += __ldcg(psum + (par * TPR + q) * 128 + row);
         return sum;
       };
       // one forward step's epilogue over this thread's columns: D (tensor
@@ -555,7 +593,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           int on = sym_at(t0 + 1);
           int fn2 = t0 + 2 < t1 ? (int)__ldcg(gexp + (size_t)(t0 + 2) * 128 + row) : 0;
           int on2 = t0 + 2 < t1 ? sym_at(t0 + 2) : 0;
-          if constexpr (!L::EMIS) me.emis_all(pf, on);
+          if constexpr (!L::EMIS) me.emis_load(pf, on);
           for (int t = t0 + 1; t < t1 && run; ++t) {
             const int f = fn;
             const int ot = on;
@@ -567,9 +605,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             }
             if constexpr (L::EMIS) me.emis_sub(bsm, ot, 0);
             wait_e(b_done, ph_done);
+            if constexpr (!L::EMIS) me.emis_ready(pf);
             fwd_step(f, act && t < T, scr + (size_t)(t - t0) * IMG);
             if constexpr (!L::EMIS)
-              if (t + 1 < t1) me.emis_all(pf, on);
+              if (t + 1 < t1) me.emis_load(pf, on);
             tc::fence_proxy_async();
             if (t == t1 - 1) tc::fence_proxy_async_all();  // images read by bulk copies
             run = handoff();
@@ -631,7 +670,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
         int onx = t1 - 2 >= t0 ? sym_at(t1 - 2) : 0;  // step t - 1, in flight
         int gnx = t1 - 2 >= t0 ? (int)__ldcg(gexp + (size_t)(t1 - 2) * 128 + row) : 0;
-        if constexpr (!L::EMIS) me.emis_all(pf, ocur);
+        if constexpr (!L::EMIS) me.emis_load(pf, ocur);
         for (int t = t1 - 1; t >= t0 && run; --t) {
           const bool has_mma = t < Lt - 1;
           const int S = t % NB;
@@ -639,6 +678,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           if constexpr (L::EMIS) me.emis_sub(bsm, ocur, 0);
           wait_e(&b_x[t % 2], ph_x[t % 2]);
           if (has_mma) wait_e(b_done, ph_done);
+          if constexpr (!L::EMIS) me.emis_ready(pf);
           const bool is_init = act && t == T - 1;
           const bool on = act && t < T - 1;
           if (is_init) c = w / s_last;
@@ -700,7 +740,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               onx = sym_at(t - 2);
               gnx = (int)__ldcg(gexp + (size_t)(t - 2) * 128 + row);
             }
-            if constexpr (!L::EMIS) me.emis_all(pf, ocur);
+            if constexpr (!L::EMIS) me.emis_load(pf, ocur);
           }
           tc::fence_proxy_async();
           run = handoff();

@@ -106,6 +106,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) hmm_fb_pass_mma(MmaPassLaunch
   constexpr uint32_t SBO = NP * 16;
   uint32_t mphase = 0, ephase = 0;
   int cur_key = -1;
+  auto row_total = [&]() {  // the row sum of the last step (its TPR partial sums)
+    float sum = psum[row];
+#pragma unroll
+    for (int q = 1; q < TPR; ++q) sum += psum[q * 128 + row];
+    return sum;
+  };
 
   for (;;) {
     __syncthreads();
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) hmm_fb_pass_mma(MmaPassLaunch
                           tc::smem_desc(b_base + ks * 256, 128, SBO), idesc, ks > 0 ? 1u : 0u);
         tc::mma_commit(mbar);
       }
-      const float sig = TPR == 2 ? psum[row] + psum[128 + row] : psum[row];
+      const float sig = row_total();
       if (!dir) {
         close_step(st, sig, t - 1, T);
       } else if (has && t - 1 >= u0 && !st.dead) {
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) hmm_fb_pass_mma(MmaPassLaunch
     }
     tc::bar_sync(1 + wg, WGT);
     if (!dir && !aborted && Tmax > 0)
-      close_step(st, TPR == 2 ? psum[row] + psum[128 + row] : psum[row], Tmax - 1, T);
+      close_step(st, row_total(), Tmax - 1, T);
     if (aborted && lane == 0 && h == 0) {
       misc[2] = 1;
       set_status(a.status, HMM_STATUS_TIMEOUT);
@@ -343,9 +349,19 @@ static cudaError_t launch_pass_e(const MmaPassLaunch& a, cudaStream_t st) {
   return launch_pass_t<NP, NT, TPR, false>(a, st);
 }
 
-cudaError_t launch_fb_pass(int NP, const MmaPassLaunch& a, cudaStream_t st) {
-  if (NP == 64) return launch_pass_e<64, 4, 1>(a, st);
-  if (NP == 128) return launch_pass_e<128, 2, 2>(a, st);
+int fb_pass_tiles_per_cta(int NP, int tiles) {
+  // N = 128: one tile per CTA (four threads per row) while the batch's forward
+  // and backward chains fit about one per SM -- each chain's steps are then
+  // shorter, and the pass is bound by its longest chain; two tiles per CTA
+  // otherwise, trading step latency for throughput
+  if (NP == 128) return 2 * tiles <= 2 * num_sms() ? 1 : 2;
+  return 4;
+}
+
+cudaError_t launch_fb_pass(int NP, int tiles_per_cta, const MmaPassLaunch& a, cudaStream_t st) {
+  if (NP == 64 && tiles_per_cta == 4) return launch_pass_e<64, 4, 1>(a, st);
+  if (NP == 128 && tiles_per_cta == 2) return launch_pass_e<128, 2, 2>(a, st);
+  if (NP == 128 && tiles_per_cta == 1) return launch_pass_e<128, 1, 4>(a, st);
   return cudaErrorInvalidValue;
 }
 

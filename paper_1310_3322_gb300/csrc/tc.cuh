@@ -57,8 +57,10 @@ __device__ __forceinline__ bool mbar_probe(uint64_t* bar, uint32_t parity) {
 // poll never suspends the thread (a limit of 1 is one instantaneous check);
 // the others may, for a hardware-defined time. A limit of 0 gives up at once.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i)
-    if (i == 0 ? mbar_probe(bar, parity) : mbar_test(bar, parity)) return true;
+  if (limit == 0) return false;
+  if (mbar_probe(bar, parity)) return true;
+  for (uint32_t i = 1; i < limit; ++i)
+    if (mbar_test(bar, parity)) return true;
   return false;
 }
 

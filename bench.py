@@ -232,8 +232,8 @@ def setup_launches(S: int, ordered: bool = True) -> int:
 
 
 def traffic_for(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from a committed ncu capture, or None
-    when the kernel's source changed since that capture."""
+    """Per-launch DRAM bytes of `kernel` (for the adjoint: its two launches)
+    from a committed ncu capture, or None when a source changed since."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f).get(kernel)
@@ -241,11 +241,12 @@ def traffic_for(kernel: str):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1310_3322_gb300", "csrc", rec["source"])
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    if sha != rec.get("source_sha"):
-        return None
+    srcs = rec.get("sources") or [rec["source"]]
+    want = rec["source_sha"] if isinstance(rec["source_sha"], list) else [rec["source_sha"]]
+    for name, sha_want in zip(srcs, want):
+        with open(os.path.join(ROOT, "paper_1310_3322_gb300", "csrc", name), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != sha_want:
+                return None
     return rec["bytes_per_launch_full_workload"]
 
 

@@ -677,6 +677,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           const float rho_prev = row_sum((t + 1) & 1);
           if constexpr (L::EMIS) me.emis_sub(bsm, ocur, 0);
           wait_e(&b_x[t % 2], ph_x[t % 2]);
+          // this step's X image is in shared memory now and its copy in memory
+          // (checkpoint or recomputed image) is never read again: drop its
+          // L2 lines instead of letting them be written back
+          if (tid < IMG / 128)
+            tc::discard_l2((t == t0 ? ckx + (size_t)seg * IMG : scr + (size_t)(t - t0) * IMG) +
+                           (size_t)tid * 128);
           if (has_mma) wait_e(b_done, ph_done);
           if constexpr (!L::EMIS) me.emis_ready(pf);
           const bool is_init = act && t == T - 1;

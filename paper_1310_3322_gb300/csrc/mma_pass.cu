@@ -355,11 +355,12 @@ int fb_pass_tiles_per_cta(int NP, int tiles) {
   // shorter, and the pass is bound by its longest chain; two tiles per CTA
   // otherwise, trading step latency for throughput
   if (NP == 128) return 2 * tiles <= 2 * num_sms() ? 1 : 2;
-  return 4;
+  return 2;
 }
 
 cudaError_t launch_fb_pass(int NP, int tiles_per_cta, const MmaPassLaunch& a, cudaStream_t st) {
   if (NP == 64 && tiles_per_cta == 4) return launch_pass_e<64, 4, 1>(a, st);
+  if (NP == 64 && tiles_per_cta == 2) return launch_pass_e<64, 2, 2>(a, st);
   if (NP == 128 && tiles_per_cta == 2) return launch_pass_e<128, 2, 2>(a, st);
   if (NP == 128 && tiles_per_cta == 1) return launch_pass_e<128, 1, 4>(a, st);
   return cudaErrorInvalidValue;

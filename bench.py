@@ -404,6 +404,10 @@ def run_gpu(args, emit=True):
     per_launch = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in kt.items()}
     totals = {k: v[1] for k, v in kt.items()}
     step_kernel_ms = sum(totals.values()) / max(args.steps, 1)
+    if kt["adjoint_pass"][0]:  # segment ranges: the adjoint is its passes + ranges
+        per_launch["adjoint_ranges"] = per_launch["adjoint"]
+        per_launch["adjoint"] += per_launch["adjoint_pass"]
+        totals["adjoint"] += totals["adjoint_pass"]
     flops = {
         "forward": (2 * N * N + 3 * N) * sumT * K,
         "viterbi_scores": 2 * N * N * sumT * K,

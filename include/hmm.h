@@ -352,9 +352,10 @@ int hmm_fma_probe(int32_t blocks, int32_t threads, int64_t iters, int32_t mode, 
  * hmm_timing_read() synchronises those events and reports, per kernel kind,
  * the number of launches and their summed duration since the last reset.
  * Kinds: 0 setup, 1 forward, 2 viterbi-scores, 3 viterbi-paths, 4 adjoint
- * (the tensor-core adjoint: its segment-range kernel), 5 count-reduce,
+ * (for the two-kernel adjoints, the tensor-core one and the FP32 one with
+ * segment ranges: their segment-range kernel), 5 count-reduce,
  * 6 softmax-rows, 7 softmax-grad, 8 adam, 9 mstep, 10 scan-chunks,
- * 11 scan-combine, 12 adjoint-pass (the tensor-core adjoint's forward and
+ * 11 scan-combine, 12 adjoint-pass (the two-kernel adjoints' forward and
  * backward passes). Not for use inside CUDA-graph capture; not thread-safe
  * against concurrent launches. */
 #define HMM_TIMING_KINDS 13

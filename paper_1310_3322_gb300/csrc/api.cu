@@ -1201,9 +1201,16 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
     f.nck = NC;
     f.spar = spar;
     f.spg = spg;
-    Timed tm(T_FB, st);
-    e = launch_fb_seg(L.NP, G, f, st);
-    tm.stop();
+    {
+      Timed tm(T_FB_PASS, st);
+      e = launch_fb_seg(L.NP, G, f, 0, st);
+      tm.stop();
+    }
+    if (e == cudaSuccess) {
+      Timed tm(T_FB, st);
+      e = launch_fb_seg(L.NP, G, f, 1, st);
+      tm.stop();
+    }
   } else {
     FbLaunch f;
     f.seq = seq_args(dims, *seqs, L, ws);

@@ -16,16 +16,22 @@
 // shared memory: O(sqrt(T) N) floats per pair.
 //
 // Scaling: alpha_t and beta_t each carry an exact power-of-two scale that is
-// never divided out. With u_{t+1}(j) = b_j(o_{t+1}) beta_{t+1}(j) and the
-// forward exponent e_{t+1} removed at step t+1,
-//   Z_t = sum_j (alpha_t A)_j u_{t+1}(j) = 2^{e_{t+1}} D_{t+1},
+// never divided out, and the scale is applied lazily: a step multiplies its
+// result by 2^-f, f the exponent of the sum of its INPUT row, which every lane
+// of the pair adds up itself from the row it reads from shared memory for the
+// product anyway. The recursion's critical path is then the product alone
+// (no cross-lane reduction), and since a power of two commutes with rounding
+// the stored values are those of a step-by-step normalisation up to an exact
+// power of two. With the forward's f_t stored as e_{t+1} (the exponent applied
+// to produce alpha_{t+1}), u_{t+1}(j) = b_j(o_{t+1}) beta_{t+1}(j) 2^-e_{t+1}:
+//   Z_t = sum_j (alpha_t A)_j b_j(o_{t+1}) beta_{t+1}(j) = 2^{e_{t+1}} D_{t+1},
 //   D_{t+1} = sum_j alpha_{t+1}(j) beta_{t+1}(j),
-// so with v(j) = u_{t+1}(j) / Z_t
-//   xi_t(i,j)      = alpha_t(i) a_ij v(j)          (a_ij applied at the flush)
+//   xi_t(i,j)      = alpha_t(i) a_ij u_{t+1}(j) / D_{t+1}   (a_ij applied at the flush)
 //   gamma_{t+1}(j) = alpha_{t+1}(j) beta_{t+1}(j) / D_{t+1}
-//   beta_t(i)     ~ sum_j a_ij v(j)                (then rescaled),
-// and the weight w multiplies only what is accumulated. D_t comes out of the
-// same butterfly as the sum that rescales beta_t (one reduction per step).
+//   beta_t(i)     ~ sum_j a_ij u_{t+1}(j)                  (then scaled),
+// and the weight w multiplies only what is accumulated. D_t is the one
+// cross-lane reduction per backward step; it feeds only the accumulations of
+// the next step, not the beta recursion.
 // Lane ownership: lane r of the pair owns states [rJ, rJ+J) both as columns
 // (forward: column slice of A) and as rows (backward: row slice of A, row
 // slice of the xi accumulator), so every step needs one broadcast vector.
@@ -108,6 +114,8 @@ hmm_fb_simt(FbLaunch a) {
     const int32_t* o = a.seq.symbols + ((has && T >= 0) ? a.seq.offsets[s] : 0);
 
     // ---------------- phase 1: forward with checkpoints ----------------
+    // x = alpha_t 2^-E; step t -> t+1 multiplies by 2^-f_t (f_t the exponent of
+    // sum x_t), so E grows by f_t, and e_{t+1} = f_t is kept with checkpoints.
     float x[J];
     int E = 0;
     bool dead = false, bad = T < 0;
@@ -120,64 +128,63 @@ hmm_fb_simt(FbLaunch a) {
       load_vec<J>(pv, a.mod.pip + (size_t)k * NP + j0);
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) x[jj] = pv[jj] * b[jj];
-      const float gs = group_sum<G>(tree_sum<J>(x));
-      if (Tn > 0 && !bad) {
-        if (gs == 0.f) dead = true;
-        else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
-        else {
-          const int e = rescale_pow2<J>(x, gs);
-          E += e;
-          store_vec<J>(ck + j0, x);
-          if (r == 0) cke[0] = e;
-        }
+      if (Tn > 0) {
+        store_vec<J>(ck + j0, x);
+        if (r == 0) cke[0] = 0;
       }
     }
     const int Tmax = __reduce_max_sync(HMM_FULL_MASK, Tn);
     {
+      // branch-free steps: flags and selects instead of per-pair branches
       float bn[J];
-      int on = 0;
-      if (1 < Tn) {
-        on = __ldg(o + 1);
-        if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
-      }
+      int on = (1 < Tn) ? __ldg(o + 1) : 0;
+      bool symbad = (unsigned)on >= (unsigned)M;
+      on = symbad ? 0 : on;
       load_vec<J>(bn, Bk + (size_t)on * NP);
       int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
+      int cls = 0;         // OR of sum_class over the active steps
+      int cc = 0, ci = 0;  // steps since the last checkpoint, its index
       for (int t = 1; t < Tmax; ++t) {
-        const bool act = t < Tn && !dead && !bad;
+        const bool act = t < Tn;
         float* xw = xf + (t & 1) * XS;
         store_vec<J>(xw + j0, x);
         __syncwarp();
-        float nx[J];
-        matvec_cols<NP, J>(xw, ac, nx);
+        float nx[J], sx;
+        matvec_cols_sum<NP, J>(xw, ac, nx, sx);
         float b[J];
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) b[jj] = bn[jj];
-        if (t + 1 < Tn) {
-          on = o2;
-          if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
+        {
+          const bool nb_ = (unsigned)o2 >= (unsigned)M;
+          symbad |= nb_ && t + 1 < Tn;
+          on = nb_ ? 0 : o2;
           load_vec<J>(bn, Bk + (size_t)on * NP);
           if (t + 2 < Tn) o2 = __ldg(o + t + 2);
         }
+        int f;
+        const float sc = pow2_scale(sx, f);
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) nx[jj] *= b[jj];
-        const float gs = group_sum<G>(tree_sum<J>(nx));
-        if (act) {
-          if (gs == 0.f) dead = true;
-          else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
-          else {
-            const int e = rescale_pow2<J>(nx, gs);
-            E += e;
+        for (int jj = 0; jj < J; ++jj) nx[jj] = (nx[jj] * sc) * b[jj];
+        if (++cc == C) { cc = 0; ++ci; }
+        // x_{t-1} is checked here, x_{Tn-1} after the loop
+        cls |= act ? sum_class(sx) : 0;
+        E += act ? f : 0;
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) x[jj] = nx[jj];
-            if (t % C == 0) {
-              store_vec<J>(ck + (t / C) * NP + j0, x);
-              if (r == 0) cke[t / C] = e;
-            }
-          }
+        for (int jj = 0; jj < J; ++jj) x[jj] = act ? nx[jj] : x[jj];
+        if (act && cc == 0) {
+          store_vec<J>(ck + ci * NP + j0, x);
+          if (r == 0) cke[ci] = f;
         }
       }
+      if (symbad) { bad = true; err |= HMM_STATUS_SYMBOL; }
+      if (cls & 2) { bad = true; err |= HMM_STATUS_PARAM; }
+      else if (cls & 1) dead = true;
     }
     const float fs = group_sum<G>(tree_sum<J>(x));
+    if (Tn > 0 && !bad && !dead) {
+      if (fs == 0.f) dead = true;
+      else if (!(fs > 0.f) || isinf(fs)) { bad = true; err |= HMM_STATUS_PARAM; }
+    }
     if (has && r == 0) {
       float out;
       if (bad) { out = __int_as_float(0x7fc00000); if (err) set_status(a.status, err); }
@@ -218,18 +225,18 @@ hmm_fb_simt(FbLaunch a) {
         float* xw = xf + (t & 1) * XS;
         store_vec<J>(xw + j0, xr);
         __syncwarp();
-        float nx[J], b[J];
-        matvec_cols<NP, J>(xw, ac, nx);
+        float nx[J], b[J], sx;
+        matvec_cols_sum<NP, J>(xw, ac, nx, sx);
         load_vec<J>(b, Bk + (size_t)sym(t) * NP);
+        int f;
+        const float sc = pow2_scale(sx, f);
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) nx[jj] *= b[jj];
-        const float gs = group_sum<G>(tree_sum<J>(nx));
+        for (int jj = 0; jj < J; ++jj) nx[jj] = (nx[jj] * sc) * b[jj];
         if (act) {
-          const int e = rescale_pow2<J>(nx, gs);
 #pragma unroll
           for (int jj = 0; jj < J; ++jj) xr[jj] = nx[jj];
           store_vec<J>(sg + (t - t0) * NP + j0, xr);
-          if (r == 0) se[t - t0] = e;
+          if (r == 0) se[t - t0] = f;
         }
       }
       __syncwarp();
@@ -262,6 +269,15 @@ hmm_fb_simt(FbLaunch a) {
       float br[J];
       load_vec<J>(br, Bk + (size_t)sr_next * NP);
       sr_next = rc_on ? sym(r0 + 2) : 0;
+      // alpha rows and exponents of the backward steps, one iteration ahead:
+      // a1 = alpha_{t+1}, e1 = e_{t+1} (the next checkpoint at the segment's
+      // end), a0 = alpha_t, e0 = e_t; indices clamped into the buffers (the
+      // steps outside a pair's range are masked by bact)
+      float a1[J], a0[J];
+      load_vec_smem<J>(a1, ck + min(c + 1, NC - 1) * NP + j0);
+      int e1 = cke[min(c + 1, NC - 1)];
+      load_vec_smem<J>(a0, cur + (t1 - t0) * NP + j0);
+      int e0 = cure[t1 - t0];
 
       for (int u = 0; u < C; ++u) {
         const int tb = t1 - u;
@@ -269,28 +285,30 @@ hmm_fb_simt(FbLaunch a) {
         const int tr = r0 + 1 + u;
         const bool ract = rc_on && u <= C - 2 && alive && tr <= Tb - 1;
 
-        // backward: publish v = u_{t+1} / Z_t, count gamma_{t+1} emissions
-        float a1[J], a0[J], v[J];
-        int e1 = 0;
-        if (bact) {
-          if (tb + 1 <= t1) {
-            load_vec_smem<J>(a1, cur + (tb + 1 - t0) * NP + j0);
-            e1 = cure[tb + 1 - t0];
-          } else {
-            load_vec_smem<J>(a1, ck + (c + 1) * NP + j0);
-            e1 = cke[c + 1];
-          }
-          load_vec_smem<J>(a0, cur + (tb - t0) * NP + j0);
-          const float invD = 1.f / D;
-          const float wd = w * invD;
+        // backward: publish u_{t+1} = b beta_{t+1} 2^-e_{t+1}, count gamma_{t+1}.
+        // Branch-free (selects), so that the compiler can interleave the two
+        // chains and the accumulations.
+        const int nidx = max(tb - 1 - t0, 0);
+        float a0n[J];
+        load_vec_smem<J>(a0n, cur + nidx * NP + j0);
+        const int e0n = cure[nidx];
+        float aw[J], v[J];
+        const float invD = __frcp_rn(D);
+        const float se1 = exp2i(-e1);
+        const float wd = w * invD;
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) {
-            cb[(j0 + jj) * MP + sb] += wd * a1[jj] * beta[jj];
-            v[jj] = mul_pow2(bb[jj] * beta[jj], -e1) * invD;
-          }
-        } else {
+        for (int jj = 0; jj < J; ++jj) {
+          const float gam = wd * a1[jj] * beta[jj];
+          float* cbp = cb + (j0 + jj) * MP + sb;
+          if (bact) *cbp += gam;
+          v[jj] = bact ? (bb[jj] * beta[jj]) * se1 : 0.f;
+          aw[jj] = bact ? (w * a0[jj]) * invD : 0.f;
+        }
+        float a0s[J], a0m[J];  // alpha_t (kept for the next step), masked copy
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) { a0[jj] = 0.f; v[jj] = 0.f; }
+        for (int jj = 0; jj < J; ++jj) {
+          a0s[jj] = a0[jj];
+          a0m[jj] = bact ? a0[jj] : 0.f;
         }
         float* vw = xv + (u & 1) * XS;
         float* xw = xf + (u & 1) * XS;
@@ -308,38 +326,47 @@ hmm_fb_simt(FbLaunch a) {
         __syncwarp();
 
         // recompute step of segment c-1 (independent chain)
-        float nx[J];
-        matvec_cols<NP, J>(xw, ac, nx);
+        float nx[J], sx;
+        matvec_cols_sum<NP, J>(xw, ac, nx, sx);
+        int fr;
+        const float scr = pow2_scale(sx, fr);
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) nx[jj] *= br[jj];
-        const float rs = group_sum<G>(tree_sum<J>(nx));
+        for (int jj = 0; jj < J; ++jj) nx[jj] = (nx[jj] * scr) * br[jj];
 
-        // backward step: beta_t and the xi accumulator
-        float aw[J], nb[J];
-#pragma unroll
-        for (int ii = 0; ii < J; ++ii) aw[ii] = w * a0[ii];
-        rows_step<NP, J>(vw, ar, aw, xa, nb);
+        // backward step: beta_t (scaled by the exponent of sum u) and the xi
+        // accumulator, normalised by D_{t+1}
+        float nb[J], su;
+        rows_step_sum<NP, J>(vw, ar, aw, xa, nb, su);
+        int fu;
+        const float sg = pow2_scale(su, fu);
         float ad[J];
 #pragma unroll
-        for (int ii = 0; ii < J; ++ii) ad[ii] = a0[ii] * nb[ii];
-        const float2 red = group_sum2<G>(make_float2(tree_sum<J>(nb), tree_sum<J>(ad)));
+        for (int ii = 0; ii < J; ++ii) {
+          nb[ii] *= sg;
+          ad[ii] = a0m[ii] * nb[ii];
+        }
+        const float Dn = group_sum<G>(tree_sum<J>(ad));
 
         if (ract) {
-          const int e = rescale_pow2<J>(nx, rs);
-#pragma unroll
-          for (int jj = 0; jj < J; ++jj) xr[jj] = nx[jj];
-          store_vec<J>(nxt + (u + 1) * NP + j0, xr);
-          if (r == 0) nxte[u + 1] = e;
+          store_vec<J>(nxt + (u + 1) * NP + j0, nx);
+          if (r == 0) nxte[u + 1] = fr;
         }
-        if (bact && red.x > 0.f && !isinf(red.x)) {
-          const int e = rescale_pow2<J>(nb, red.x);
 #pragma unroll
-          for (int ii = 0; ii < J; ++ii) beta[ii] = nb[ii];
-          D = mul_pow2(red.y, -e);
-        }
+        for (int jj = 0; jj < J; ++jj) xr[jj] = ract ? nx[jj] : xr[jj];
+        const bool bok = bact && su > 0.f && !isinf(su);
+#pragma unroll
+        for (int ii = 0; ii < J; ++ii) beta[ii] = bok ? nb[ii] : beta[ii];
+        D = bok ? Dn : D;
         sb = sb_cur;
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) { bb[jj] = bbn[jj]; br[jj] = brn[jj]; }
+        for (int jj = 0; jj < J; ++jj) {
+          bb[jj] = bbn[jj];
+          br[jj] = brn[jj];
+          a1[jj] = a0s[jj];
+          a0[jj] = a0n[jj];
+        }
+        e1 = e0;
+        e0 = e0n;
       }
       __syncwarp();
     }

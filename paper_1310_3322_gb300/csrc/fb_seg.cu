@@ -518,8 +518,8 @@ size_t fb_seg_smem_bytes(int NP, int G, int C, int M, int warps) {
 }
 
 template <int NP, int G>
-static cudaError_t launch_fb_seg_t(const FbSegLaunch& a, cudaStream_t st) {
-  {
+static cudaError_t launch_fb_seg_t(const FbSegLaunch& a, int phase, cudaStream_t st) {
+  if (phase == 0) {
     auto kern = hmm_fb_pass<NP, G>;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
@@ -530,7 +530,7 @@ static cudaError_t launch_fb_seg_t(const FbSegLaunch& a, cudaStream_t st) {
     const int need = (a.n_items_pass + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > need) blocks = need > 0 ? need : 1;
     kern<<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    return cudaGetLastError();
   }
   auto kern = hmm_fb_seg<NP, G>;
   int warps = kWarpsPerBlock;
@@ -550,9 +550,9 @@ static cudaError_t launch_fb_seg_t(const FbSegLaunch& a, cudaStream_t st) {
 }
 
 #define HMM_FBS_CASE(NPV, GV) \
-  if (NP == NPV && G == GV) return launch_fb_seg_t<NPV, GV>(a, st);
+  if (NP == NPV && G == GV) return launch_fb_seg_t<NPV, GV>(a, phase, st);
 
-cudaError_t launch_fb_seg(int NP, int G, const FbSegLaunch& a, cudaStream_t st) {
+cudaError_t launch_fb_seg(int NP, int G, const FbSegLaunch& a, int phase, cudaStream_t st) {
   HMM_FBS_CASE(4, 2) HMM_FBS_CASE(4, 4)
   HMM_FBS_CASE(8, 4) HMM_FBS_CASE(8, 8)
   HMM_FBS_CASE(16, 8) HMM_FBS_CASE(16, 16)

@@ -464,7 +464,8 @@ struct FbSegLaunch {
   int ckpt, nck;       // segment length C, segments of the longest sequence
   int spar, spg;       // ranges per pair, segments per range
 };
-cudaError_t launch_fb_seg(int NP, int G, const FbSegLaunch& a, cudaStream_t st);
+// phase 0: the forward and backward passes; phase 1: the segment ranges
+cudaError_t launch_fb_seg(int NP, int G, const FbSegLaunch& a, int phase, cudaStream_t st);
 
 // Parallel-in-time forward (scan.cu): per-chunk products of the step
 // matrices A diag(b(o_t)), then one ordered combine per pair.

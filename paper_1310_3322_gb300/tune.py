@@ -24,7 +24,8 @@ KERNEL_OF = {hmm.HMM_OP_FORWARD: "forward", hmm.HMM_OP_VITERBI: "viterbi_scores"
              hmm.HMM_OP_FORWARD_BACKWARD: "adjoint",
              hmm.HMM_TUNE_FB_RANGES: "adjoint_ranges"}
 # timing kinds summed for each tuned op
-TIMED = {hmm.HMM_TUNE_FB_RANGES: ("adjoint", "count_reduce")}
+TIMED = {hmm.HMM_OP_FORWARD_BACKWARD: ("adjoint", "adjoint_pass"),
+         hmm.HMM_TUNE_FB_RANGES: ("adjoint", "adjoint_pass", "count_reduce")}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hmmgb_tuning.json")
 
 

@@ -75,7 +75,8 @@ typedef struct CUstream_st* hmm_stream_t;
 
 typedef enum {
   HMM_FP32 = 0,      /* FP32 SIMT recursion (exact power-of-two rescaling) */
-  HMM_BF16_MMA = 1,  /* tensor-core alpha*A, BF16 operands, FP32 accumulation */
+  HMM_BF16_MMA = 1,  /* tensor-core alpha*A, BF16 operands (A and B rounded to BF16),
+                        FP32 accumulation */
   HMM_TF32_MMA = 2,  /* tensor-core alpha*A, TF32 operands, FP32 accumulation */
   HMM_AUTO = 3       /* the library's choice for the given N */
 } hmm_precision_t;
@@ -130,7 +131,10 @@ int hmm_max_states(hmm_op_t op, hmm_precision_t precision);
  * final log is taken in FP64. HMM_BF16_MMA (32 < N <= 512) / HMM_TF32_MMA
  * (32 < N <= 128), every sequence against every model: alpha*A on the tensor
  * cores with BF16 (u = 2^-8) or TF32 (u = 2^-11, round to nearest) operands
- * and FP32 accumulation, |delta log P| <= 2 u T against FP64. Above 128
+ * and FP32 accumulation, |delta log P| <= 2 u T (TF32) or 3 u T (BF16) against
+ * FP64. The BF16 path
+ * computes with the model's A and B both rounded to BF16 (round to nearest
+ * even, once per call); the TF32 path rounds A only. Above 128
  * states (the cited cuHMM kernel's 512-state workload, Sec. 5.6) one CTA
  * holds one 128-sequence tile and streams A^T from a BF16 image the call
  * builds in the workspace. HMM_AUTO: tensor cores (BF16) above N = 64; for
@@ -227,8 +231,9 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
  *   loglik  [S] or [S][K]
  *   counts  overwritten; summed in a fixed order (bitwise reproducible).
  * precision: HMM_FP32 runs the FP32 SIMT adjoint (N <= 64); HMM_BF16_MMA the
- * tensor-core adjoint (32 < N <= 128, M <= 256: BF16 operands, FP32
- * accumulation, per-row messages renormalised every step, checkpoint stride
+ * tensor-core adjoint (32 < N <= 128, M <= 256: BF16 operands, A and B
+ * rounded to BF16 as in hmm_forward, FP32 accumulation, per-row messages
+ * renormalised every step, checkpoint stride
  * capped at 16 while T <= 8192) as two kernels: the forward and the backward
  * recursion of every 128-row tile run as independent chains keeping
  * checkpoints of both, then every range of a tile's checkpoint segments is a

@@ -538,6 +538,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
   SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  s.bf16_b = 1;  // BF16 path: B rounded to BF16 like A
   s.want_bpoff = 1;
   s.bpoff = at<int64_t>(ws, L.bpoff);
   s.bp_cap_rows = L.w_rtot;
@@ -632,6 +633,7 @@ static int fb_mma(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* w
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
   SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  s.bf16_b = 1;      // BF16 path: B rounded to BF16 like A
   s.skip_order = 1;  // the tile plan orders the sequences itself
   const bool labelled = seqs->model_of_seq != nullptr;
   const int cap = L.m_pass_cap;  // tiles the plan can form
@@ -858,6 +860,7 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     const int n_tiles = (seqs->S + 127) / 128;
     if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
     SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+    s.bf16_b = 1;  // BF16 path: B rounded to BF16 like A
     s.ndone = argmax ? n_tiles : 0;
     {
       Timed tm(T_SETUP, st);
@@ -892,6 +895,7 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     const int n_pairs = (n_tiles + nt - 1) / nt;  // tile groups of one CTA
     if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
     SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+    s.bf16_b = precision != HMM_TF32_MMA;  // BF16 path: B rounded to BF16 like A
     s.ndone = argmax ? n_pairs : 0;
     {
       Timed tm(T_SETUP, st);

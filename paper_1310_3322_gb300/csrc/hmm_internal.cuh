@@ -85,6 +85,7 @@ struct SetupArgs {
   int64_t total_obs;
   int max_len;         // sequences longer than this are rejected
   int log_mode;        // 1: tables hold natural logs (Viterbi), 0: probabilities
+  int bf16_b;          // 1: the emission table holds B rounded to BF16 (the BF16 path)
   int want_bpoff;      // 1: compute backpointer offsets (Viterbi)
   int skip_order;      // 1: validate only (the caller builds its own schedule)
   int ndone;           // entries of `done` to clear

@@ -131,13 +131,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
           *reinterpret_cast<uint32_t*>(sB + off) = tc::to_tf32(__ldg(Ak + i * NP + j));
         }
       }
-      if constexpr (EMIS) {  // the model's emission table, rows padded to kES bytes
-        const float4* src = reinterpret_cast<const float4*>(a.mod.Btp + (size_t)k * M * NP);
-        for (int idx = tid; idx < M * NP / 4; idx += kMmaThreads) {
-          const int m = idx / (NP / 4), c = idx % (NP / 4);
-          *reinterpret_cast<float4*>(smem + L::OFF_E + m * L::kES + c * 16) = __ldg(src + idx);
-        }
-      }
+      if constexpr (EMIS)  // the model's emission table, rows padded to kET bytes
+        fill_emission_table<NP, AB, L::kET>(smem + L::OFF_E, a.mod.Btp + (size_t)k * M * NP, M, tid,
+                                            kMmaThreads);
       cur_model = k;
       tc::fence_proxy_async();
       __syncthreads();
@@ -221,7 +217,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
         if (t + 1 < Tn) o_next = __ldg(o + t + 1);
       }
       if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
-      const uint8_t* eb = EMIS ? erow + ((unsigned)ot < (unsigned)M ? ot : 0) * L::kES : erow;
+      const uint8_t* eb = EMIS ? erow + ((unsigned)ot < (unsigned)M ? ot : 0) * L::kET : erow;
       const bool live = t < Tn && !st.dead && !st.bad;
       if (live) st.F += st.f;
       const float2 fac2 = make_float2(exp2i(-st.f), exp2i(-st.f));
@@ -248,9 +244,17 @@ __global__ void __launch_bounds__(kMmaThreads, 1) hmm_forward_mma(MmaFwdLaunch a
         tc::tmem_ld32(d_mine + (uint32_t)(c * 32), y);
         tc::tmem_ld_wait();
         float2 acc = make_float2(0.f, 0.f);
+        float be[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float4 b = *reinterpret_cast<const float4*>(eb + (h * HALF + 32 * c + 4 * q) * 4);
+          float4 b;
+          if constexpr (EMIS) {
+            if ((q & 1) == 0) emission8<AB>(eb, h * HALF + 32 * c + 4 * q, be);
+            b = make_float4(be[4 * (q & 1)], be[4 * (q & 1) + 1], be[4 * (q & 1) + 2],
+                            be[4 * (q & 1) + 3]);
+          } else {
+            b = *reinterpret_cast<const float4*>(eb + (h * HALF + 32 * c + 4 * q) * 4);
+          }
           float2 lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
                                             make_float2(b.x, b.y)), fac2);
           float2 hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),

@@ -133,13 +133,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) hmm_fb_pass_mma(MmaPassLaunch
         *reinterpret_cast<uint32_t*>(sB + off) = tc::pack_bf16(v0, v1);
       }
       if constexpr (EMIS) {
-        if (cur_key < 0 || (cur_key >> 1) != k) {
-          const float4* src = reinterpret_cast<const float4*>(a.mod.Btp + (size_t)k * M * NP);
-          for (int idx = tid; idx < M * NP / 4; idx += kPassThreads) {
-            const int m = idx / (NP / 4), c = idx % (NP / 4);
-            *reinterpret_cast<float4*>(smem + L::OFF_E + m * L::kES + c * 16) = __ldg(src + idx);
-          }
-        }
+        if (cur_key < 0 || (cur_key >> 1) != k)
+          fill_emission_table<NP, 1, L::kET>(smem + L::OFF_E, a.mod.Btp + (size_t)k * M * NP, M,
+                                             tid, kPassThreads);
       }
       cur_key = 2 * k + dir;
       tc::fence_proxy_async();
@@ -243,7 +239,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) hmm_fb_pass_mma(MmaPassLaunch
       }
       const bool inrow = has && t >= u0 && t < u0 + T;
       if (!dir && inrow && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
-      const uint8_t* eb = EMIS ? erow + ((unsigned)ot < (unsigned)M ? ot : 0) * L::kES : erow;
+      const uint8_t* eb = EMIS ? erow + ((unsigned)ot < (unsigned)M ? ot : 0) * L::kET : erow;
       const bool start = dir && t == u0;   // the backward row starts here: beta = 1
       const bool live = inrow && !st.dead && !st.bad;
       const int f = start ? 0 : st.f;
@@ -269,9 +265,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) hmm_fb_pass_mma(MmaPassLaunch
         tc::tmem_ld32(d_mine + (uint32_t)(c * 32), y);
         tc::tmem_ld_wait();
         float2 acc = make_float2(0.f, 0.f);
+        float be[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float4 b = *reinterpret_cast<const float4*>(eb + (h * HALF + 32 * c + 4 * q) * 4);
+          float4 b;
+          if constexpr (EMIS) {
+            if ((q & 1) == 0) emission8<1>(eb, h * HALF + 32 * c + 4 * q, be);
+            b = make_float4(be[4 * (q & 1)], be[4 * (q & 1) + 1], be[4 * (q & 1) + 2],
+                            be[4 * (q & 1) + 3]);
+          } else {
+            b = *reinterpret_cast<const float4*>(eb + (h * HALF + 32 * c + 4 * q) * 4);
+          }
           float2 ylo = make_float2(y[4 * q], y[4 * q + 1]);
           float2 yhi = make_float2(y[4 * q + 2], y[4 * q + 3]);
           if (start) { ylo = make_float2(1.f, 1.f); yhi = ylo; }

@@ -17,6 +17,10 @@ struct MmaFwdSmem {
   static constexpr int kB = NP * NP * (AB == 1 ? 2 : 4);  // A^T
   static constexpr int kES = NP * 4 + 16;         // padded emission row, FP32
   static constexpr int kE = 128 * kES;            // one tile of emission rows
+  // EMIS: padded row of the shared table, BF16 values on the BF16 path (the
+  // values the tables hold are BF16 there, so the conversion is exact), FP32
+  // on the TF32 path
+  static constexpr int kET = (AB == 1 ? NP * 2 : NP * 4) + 16;
   static constexpr int OFF_B = 0;
   static constexpr int OFF_PS = kB;               // partial row sums [NT][TPR][128]
   static constexpr int OFF_BAR = OFF_PS + NT * TPR * 128 * 4;  // mma[NT], emission[NT], fin[NT]
@@ -24,7 +28,7 @@ struct MmaFwdSmem {
   static constexpr int OFF_E = (OFF_MISC + 24 * 4 + 127) / 128 * 128;  // staging or table
   static constexpr int FIXED = OFF_E + (EMIS ? 0 : NT * kE);
   // total bytes for M symbols
-  static constexpr int total(int M) { return FIXED + (EMIS ? M * kES : 0); }
+  static constexpr int total(int M) { return FIXED + (EMIS ? M * kET : 0); }
 };
 constexpr int kFwdSmemMax = 227 * 1024;
 static_assert(MmaFwdSmem<128, 2, 2, 2>::total(0) <= kFwdSmemMax, "shared memory budget");
@@ -54,6 +58,49 @@ struct RowState {
   float ll;
   float slast;  // the row sum at the row's last step (set with ll)
 };
+
+// Copies the model's emission table (M rows of NP FP32 values) into shared
+// memory as rows of kET bytes: BF16 (AB 1) or FP32 (AB 2).
+template <int NP, int AB, int ET>
+__device__ __forceinline__ void fill_emission_table(uint8_t* dst, const float* Bk, int M, int tid,
+                                                    int nthreads) {
+  if constexpr (AB == 1) {
+    const float4* src = reinterpret_cast<const float4*>(Bk);
+    for (int idx = tid; idx < M * NP / 8; idx += nthreads) {
+      const int m = idx / (NP / 8), c = idx % (NP / 8);
+      const float4 lo = __ldg(src + 2 * idx), hi = __ldg(src + 2 * idx + 1);
+      *reinterpret_cast<uint4*>(dst + m * ET + c * 16) =
+          make_uint4(tc::pack_bf16(lo.x, lo.y), tc::pack_bf16(lo.z, lo.w), tc::pack_bf16(hi.x, hi.y),
+                     tc::pack_bf16(hi.z, hi.w));
+    }
+  } else {
+    const float4* src = reinterpret_cast<const float4*>(Bk);
+    for (int idx = tid; idx < M * NP / 4; idx += nthreads) {
+      const int m = idx / (NP / 4), c = idx % (NP / 4);
+      *reinterpret_cast<float4*>(dst + m * ET + c * 16) = __ldg(src + idx);
+    }
+  }
+}
+
+// Eight emission values, columns col .. col + 7 (col a multiple of 8), of one
+// row of the shared table.
+template <int AB>
+__device__ __forceinline__ void emission8(const uint8_t* rowp, int col, float (&b)[8]) {
+  if constexpr (AB == 1) {
+    const uint4 w = *reinterpret_cast<const uint4*>(rowp + col * 2);
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      b[2 * i] = __uint_as_float(u[i] << 16);
+      b[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+    }
+  } else {
+    const float4 lo = *reinterpret_cast<const float4*>(rowp + col * 4);
+    const float4 hi = *reinterpret_cast<const float4*>(rowp + col * 4 + 16);
+    b[0] = lo.x; b[1] = lo.y; b[2] = lo.z; b[3] = lo.w;
+    b[4] = hi.x; b[5] = hi.y; b[6] = hi.z; b[7] = hi.w;
+  }
+}
 
 // Starts the bulk copy of emission row `sym` into this row's slot.
 template <int NP>

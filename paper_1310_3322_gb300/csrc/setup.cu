@@ -11,6 +11,8 @@
 //  * adam: one fused Adam update.
 //  * reduce1 / reduce2: the fixed-order two-level sum of the adjoint's
 //    per-pair count partials (bitwise reproducible).
+#include <cuda_bf16.h>
+
 #include "hmm_internal.cuh"
 
 namespace hmmgb {
@@ -243,8 +245,10 @@ __device__ void prep_blocks(const SetupArgs& a, int blk, int nblk) {
       const long long r = idx - n_pi - n_A;
       const int k = (int)(r / ((long long)a.M * a.NP));
       const int m = (int)((r / a.NP) % a.M), j = (int)(r % a.NP);
-      a.Btp[r] = j < a.N ? prep_value(a.B[((size_t)k * a.N + j) * a.M + m], a.log_mode, a.status)
-                         : pad;
+      float v = j < a.N ? prep_value(a.B[((size_t)k * a.N + j) * a.M + m], a.log_mode, a.status)
+                        : pad;
+      if (a.bf16_b) v = __bfloat162float(__float2bfloat16_rn(v));
+      a.Btp[r] = v;
     }
   }
 }

@@ -1,10 +1,11 @@
 """Adjoint (Baum-Welch E-step) above 128 states vs the FP64 oracle.
 
 Above 128 states the forward and the backward recursions run on the tensor
-cores (BF16 operands, u = 2^-8, FP32 accumulation) and keep every step's
+cores (BF16 operands and BF16-rounded A and B, u = 2^-8, FP32 accumulation)
+and keep every step's
 rescaled rows; gamma and xi are formed from them with a per-step
 normalisation and summed by a fixed-order contraction over all steps. As for
-the adjoint up to 128 states: |delta log P| <= 2 u T, relative L2 error of
+the adjoint up to 128 states: |delta log P| <= 3 u T, relative L2 error of
 each count tensor <= u, count totals invariant to within u, bitwise
 reproducible. Plus the degenerate cases (T = 0, 1, 2, an invalid symbol, an
 impossible sequence) and the argument checks of the path.
@@ -54,7 +55,7 @@ def test_wide_adjoint_all_models_matches_oracle(case):
                                                   None, wts.astype(np.float64), nthreads=16)
     T = np.maximum(w.lengths, 1).astype(np.float64)[:, None]
     err = np.abs(ll - rll)
-    assert np.all(err <= 2 * U_BF16 * T + ll_tol(w.lengths)[:, None]), (err / T).max()
+    assert np.all(err <= 3 * U_BF16 * T + ll_tol(w.lengths)[:, None]), (err / T).max()
     errs = [rel_l2(g, r) for g, r in zip((cpi, cA, cB), (rpi, rA, rB))]
     print(f"N={w.N} M={w.M} K={w.K}: loglik max|d|/T {np.max(err / T):.2e}; "
           f"count rel L2 pi {errs[0]:.2e} A {errs[1]:.2e} B {errs[2]:.2e}")
@@ -79,7 +80,7 @@ def test_wide_adjoint_labelled_single_model_and_signed_weights():
     rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
                                                   w.labels, wts.astype(np.float64), nthreads=16)
     assert ll.shape == (w.S,)
-    assert np.all(np.abs(ll - rll) <= 2 * U_BF16 * np.maximum(w.lengths, 1) + ll_tol(w.lengths))
+    assert np.all(np.abs(ll - rll) <= 3 * U_BF16 * np.maximum(w.lengths, 1) + ll_tol(w.lengths))
     _, upi, uA, uB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
                                                 w.labels, np.abs(wts).astype(np.float64),
                                                 nthreads=16)
@@ -118,7 +119,7 @@ def test_wide_adjoint_deterministic_and_degenerate():
     fin = np.isfinite(rll)
     assert np.array_equal(fin, np.isfinite(ll))
     Tm = np.broadcast_to(np.maximum(lengths, 1)[:, None], ll.shape)
-    assert np.all(np.abs(ll[fin] - rll[fin]) <= 2 * U_BF16 * Tm[fin] + 1e-3)
+    assert np.all(np.abs(ll[fin] - rll[fin]) <= 3 * U_BF16 * Tm[fin] + 1e-3)
     for g, r in zip((cpi, cA, cB), (rpi, rA, rB)):
         assert rel_l2(g, r) <= U_BF16
     # an invalid symbol: NaN log-likelihoods and no counts from that sequence

@@ -5,12 +5,13 @@ times: K = 4 models, N = 128 states, M = 256 symbols, Dirichlet(0.3) rows,
 * the BF16 and TF32 tensor-core forward of every sequence against every
   model, and the BF16 adjoint of every sequence against its labelled model,
   each on the whole batch; 64 sampled sequences (the 16 longest among them)
-  against the FP64 oracle: the hard bound 2 u T, the per-sequence cap
+  against the FP64 oracle: the hard bound 3 u T (BF16) or 2 u T (TF32), the per-sequence cap
   (u / 4) T + 2 u, and the argmax wherever the top two models are apart by
   more than twice that cap; the adjoint's count identities on every model;
 * the BF16 adjoint on a 160-sequence subset that holds the 24 longest
   sequences (tiles of T ~ 2000: 125 checkpoint segments of 16 steps each),
-  element by element against the oracle's expected counts.
+  element by element against the oracle's expected counts on the model the
+  kernel holds (A and B rounded to BF16).
 Tolerances and their derivation: tests/test_gpu_mma.py, tests/test_gpu_mma_fb.py.
 """
 import os
@@ -21,7 +22,7 @@ import pytest
 import oracle
 from helpers import check_counts, ll_tol, oparams, to_gpu
 from paper_1310_3322_gb300 import hmm, synth
-from test_gpu_mma import PRECISIONS, U_BF16, seq_cap
+from test_gpu_mma import N_ROUNDED, PRECISIONS, U_BF16, held_model, seq_cap
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +58,7 @@ def test_full_large_forward_all_models_sampled(large, prec):
                                     nthreads=NTHREADS)
     T = w.lengths[idx].astype(np.float64)[:, None]
     err = np.abs(ll[idx] - ref)
-    assert np.all(err <= 2 * u * T + ll_tol(w.lengths[idx])[:, None])
+    assert np.all(err <= N_ROUNDED[prec] * u * T + ll_tol(w.lengths[idx])[:, None])
     cap = seq_cap(u, w.lengths[idx])[:, None]
     print(f"{prec}: max|d|/T {np.max(err / T):.2e} mean {np.mean(err / T):.2e} "
           f"max |d|/cap {np.max(err / cap):.3f}")
@@ -79,7 +80,7 @@ def test_full_large_adjoint_labelled(large):
                                w.labels[idx], nthreads=NTHREADS)
     T = w.lengths[idx].astype(np.float64)
     err = np.abs(ll[idx] - rll)
-    assert np.all(err <= 2 * U_BF16 * T + ll_tol(w.lengths[idx]))
+    assert np.all(err <= 3 * U_BF16 * T + ll_tol(w.lengths[idx]))
     assert np.all(err <= seq_cap(U_BF16, w.lengths[idx])), np.max(err / T)
     # count identities of every model: sum C_pi = #sequences, sum C_A = sum (T - 1),
     # sum C_B = sum T, every count non-negative
@@ -106,8 +107,9 @@ def test_large_adjoint_longest_subset_elementwise(large):
     ll, cpi, cA, cB = (t.cpu().numpy() for t in hmm.hmm_forward_backward(
         pi, A, B, seqs, weight=torch.from_numpy(wts).cuda(), precision=hmm.HMM_BF16_MMA))
     assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
-    rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets[idx],
-                                                  w.lengths[idx], w.labels[idx],
+    # against the model the kernel holds (A and B rounded to BF16)
+    rll, rpi, rA, rB, _ = oracle.forward_backward(held_model(w, "bf16"), w.symbols,
+                                                  w.offsets[idx], w.lengths[idx], w.labels[idx],
                                                   wts.astype(np.float64), nthreads=NTHREADS)
     assert np.all(np.abs(ll - rll) <= seq_cap(U_BF16, w.lengths[idx]))
     worst = check_counts((cpi, cA, cB), (rpi, rA, rB), rtol=U_BF16, what="longest subset")

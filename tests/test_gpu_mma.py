@@ -2,15 +2,17 @@
 
 The tensor-core path rounds the transition matrix A and the rescaled forward
 variable to BF16 (unit roundoff u = 2^-8) or TF32 (u = 2^-11, round to nearest)
-and accumulates in FP32. Two checks:
+and accumulates in FP32; the BF16 path rounds the emission table B to BF16 as
+well (TF32 keeps B in FP32). Two checks:
 
-* against the oracle run on the same model with A rounded to BF16 (the
-  systematic part of the error removed), the remaining difference comes from
-  rounding alpha each step and must stay within the FP32 bound
-  FP32 bound 1e-4 * max(T, 1) nats plus u T;
+* against the oracle run on the model as the kernel holds it (A, and on the
+  BF16 path B, rounded: the systematic part of the error removed), the
+  remaining difference comes from rounding alpha each step and must stay
+  within the FP32 bound 1e-4 * max(T, 1) nats plus u T;
 * against the oracle on the exact model, every term of every step is a sum of
-  non-negative products whose factors carry relative errors <= u, so
-  |delta log P| <= 2 u T is a hard bound; the mean per-step error is reported.
+  non-negative products whose factors carry relative errors <= u (alpha and A,
+  and b on the BF16 path), so |delta log P| <= 2 u T (TF32) or 3 u T (BF16)
+  is a hard bound; the mean per-step error is reported.
 * that hard bound is far above what the kernel does: each step's rounding
   error is a sum of N independently signed terms, so per sequence
   |delta log P| <= (u / 4) T + 2 u is required as well (2 u: one step's worth
@@ -48,6 +50,15 @@ def tf32_round(x):
 
 PRECISIONS = {"bf16": (hmm.HMM_BF16_MMA, U_BF16, bf16_round),
               "tf32": (hmm.HMM_TF32_MMA, U_TF32, tf32_round)}
+# rounded factors per product term: alpha, A and (BF16 only) b
+N_ROUNDED = {"bf16": 3, "tf32": 2}
+
+
+def held_model(w, prec):
+    """The model as the tensor-core path holds it: A rounded to the operand
+    type, and B rounded to BF16 on the BF16 path."""
+    _, _, rnd = PRECISIONS[prec]
+    return oracle.params(w.pi, rnd(w.A), bf16_round(w.B) if prec == "bf16" else w.B)
 
 
 def seq_cap(u, lengths):
@@ -92,21 +103,20 @@ def test_tensor_core_forward_matches_oracle(case, prec):
     assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
     ll = ll.cpu().numpy()
     T = np.maximum(w.lengths, 1).astype(np.float64)[:, None]
-    # systematic rounding of A removed: only the per-step rounding of alpha
-    # (relative <= u per term, all terms non-negative) remains
-    Pr = oracle.params(w.pi, rnd(w.A), w.B)
-    ref_r, _, _ = oracle.forward(Pr, w.symbols, w.offsets, w.lengths, nthreads=8)
+    # systematic rounding of the model removed: only the per-step rounding of
+    # alpha (relative <= u per term, all terms non-negative) remains
+    ref_r, _, _ = oracle.forward(held_model(w, prec), w.symbols, w.offsets, w.lengths, nthreads=8)
     err_r = np.abs(ll - ref_r)
     assert np.all(err_r <= u * T + ll_tol(w.lengths)[:, None]), (err_r / T).max()
     # ... and it is a random-signed error far below that bound on average
     assert np.mean(err_r / T) <= u / 8 + 1e-5, np.mean(err_r / T)
-    # exact model: hard bound 2 u T
+    # exact model: hard bound 2 u T (TF32) or 3 u T (BF16)
     ref, ref_am, _ = oracle.forward(oracle.params(w.pi, w.A, w.B), w.symbols, w.offsets,
                                     w.lengths, nthreads=8)
     err = np.abs(ll - ref)
-    assert np.all(err <= 2 * u * T + ll_tol(w.lengths)[:, None]), (err / T).max()
+    assert np.all(err <= N_ROUNDED[prec] * u * T + ll_tol(w.lengths)[:, None]), (err / T).max()
     print(f"{prec} {name} N={w.N}: max|d|/T vs exact {np.max(err / T):.2e}, "
-          f"mean {np.mean(err / T):.2e}; vs rounded-A {np.max(err_r / T):.2e}")
+          f"mean {np.mean(err / T):.2e}; vs held model {np.max(err_r / T):.2e}")
     cap = seq_cap(u, w.lengths)[:, None]
     assert np.all(err <= cap), f"max |d| / cap = {np.max(err / cap):.3f}"
     # recognition: argmax agrees where the top two models are well separated
@@ -136,7 +146,7 @@ def test_bf16_forward_degenerate_and_errors():
     assert np.all(ll[0] == 0.0) and np.all(np.isnan(ll[2])) and am.cpu().numpy()[2] == -1
     ref, _, _ = oracle.forward(oracle.params(pi, A, B), sym, offsets, lengths)
     ok = np.array([True, True, False, True, True])
-    assert np.all(np.abs(ll[ok] - ref[ok]) <= 2 * U_BF16 * np.maximum(lengths[ok], 1)[:, None])
+    assert np.all(np.abs(ll[ok] - ref[ok]) <= 3 * U_BF16 * np.maximum(lengths[ok], 1)[:, None])
     # labelled mode and small N are not served by the tensor-core path
     with pytest.raises(hmm.HmmError):
         hmm.hmm_forward(*t, seqs.labelled(torch.zeros(5, dtype=torch.int32, device="cuda")),
@@ -148,7 +158,7 @@ def test_bf16_forward_degenerate_and_errors():
 
 def test_wide_forward_full_cuhmm_shape_sampled():
     """The 512-state x 512-sequence workload the bench times: sampled
-    sequences against the oracle (exact model, 2uT bound)."""
+    sequences against the oracle (exact model, 3uT bound)."""
     w = synth.make_workload("cuhmm")
     seqs, pi, A, B = to_gpu(w)
     ll, am = hmm.hmm_forward(pi, A, B, seqs, precision=hmm.HMM_BF16_MMA)
@@ -159,4 +169,4 @@ def test_wide_forward_full_cuhmm_shape_sampled():
     ref, _, _ = oracle.forward(oparams(w), w.symbols, w.offsets[idx], w.lengths[idx],
                                nthreads=8)
     T = w.lengths[idx].astype(np.float64)[:, None]
-    assert np.all(np.abs(ll[idx] - ref) <= 2 * U_BF16 * T + ll_tol(w.lengths[idx])[:, None])
+    assert np.all(np.abs(ll[idx] - ref) <= 3 * U_BF16 * T + ll_tol(w.lengths[idx])[:, None])

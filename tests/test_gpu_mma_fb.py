@@ -1,16 +1,18 @@
 """Tensor-core (BF16 tcgen05) forward-backward adjoint vs the FP64 oracle.
 
-The tensor-core adjoint rounds A, the rescaled forward variable, the backward
-messages Y and gamma to BF16 (unit roundoff u = 2^-8) and accumulates every
-product in FP32. Checks:
+The tensor-core adjoint rounds A and B (once per call), the rescaled forward
+variable, the backward messages Y and gamma to BF16 (unit roundoff u = 2^-8)
+and accumulates every product in FP32. Checks:
 
 * log-likelihoods: phase 1 is the tensor-core forward recursion, so the same
-  hard bound |delta log P| <= 2 u T (+ the FP32 bound) holds against the exact
+  hard bound |delta log P| <= 3 u T (+ the FP32 bound) holds against the exact
   model;
 * log-likelihoods also within the per-sequence cap (u / 4) T + 2 u of the
   forward tests, and their mean error per observation against the oracle run
-  on A rounded to BF16 below u / 8 (the forward's check);
-* counts: every count term is a product of a normalised forward and backward
+  on A and B rounded to BF16 below u / 8 (the forward's check);
+* counts (against the oracle on the model as the kernel holds it, A and B
+  rounded, so that the bound covers the per-step rounding of the messages):
+  every count term is a product of a normalised forward and backward
   message and, for xi, one BF16 transition; the normalisation is re-measured
   every step, so the per-term relative error stays O(u) instead of growing
   with T: every entry within u (1 + |ref|) (an expected count is a number of
@@ -25,7 +27,7 @@ import pytest
 
 import oracle
 from helpers import check_counts, ll_tol, oparams, rel_l2, to_gpu
-from test_gpu_mma import bf16_round, seq_cap
+from test_gpu_mma import held_model, seq_cap
 from paper_1310_3322_gb300 import hmm, synth
 
 pytestmark = pytest.mark.gpu
@@ -62,20 +64,23 @@ def test_bf16_adjoint_labelled_matches_oracle(case):
     w = _workload(case)
     wts = np.random.default_rng(5).uniform(0.5, 2.0, size=w.S).astype(np.float32)
     ll, cpi, cA, cB = _run(w, True, wts)
-    rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
-                                                  w.labels, wts.astype(np.float64), nthreads=8)
+    # counts against the model the kernel holds (A and B rounded to BF16):
+    # the per-step rounding of the messages is what they must bound
+    rll_r, rpi, rA, rB, _ = oracle.forward_backward(held_model(w, "bf16"), w.symbols, w.offsets,
+                                                    w.lengths, w.labels, wts.astype(np.float64),
+                                                    nthreads=8)
+    # log-likelihoods against the exact model
+    rll, _, _ = oracle.forward(oparams(w), w.symbols, w.offsets, w.lengths, w.labels, nthreads=8)
     T = np.maximum(w.lengths, 1).astype(np.float64)
     err = np.abs(ll - rll)
-    assert np.all(err <= 2 * U_BF16 * T + ll_tol(w.lengths)), (err / T).max()
+    assert np.all(err <= 3 * U_BF16 * T + ll_tol(w.lengths)), (err / T).max()
     assert np.all(err <= seq_cap(U_BF16, w.lengths)), (err / seq_cap(U_BF16, w.lengths)).max()
-    rll_r, _, _ = oracle.forward(oracle.params(w.pi, bf16_round(w.A), w.B), w.symbols, w.offsets,
-                                 w.lengths, w.labels, nthreads=8)
     mean_r = np.mean(np.abs(ll - rll_r) / T)
     assert mean_r <= U_BF16 / 8 + 1e-5, mean_r
     errs = [rel_l2(g, r) for g, r in zip((cpi, cA, cB), (rpi, rA, rB))]
     worst = check_counts((cpi, cA, cB), (rpi, rA, rB), rtol=U_BF16, what=case[0])
     print(f"{case[0]} N={w.N} M={w.M}: loglik max|d|/T {np.max(err / T):.2e} "
-          f"(mean vs rounded A {mean_r:.2e}); count rel L2 pi {errs[0]:.2e} A {errs[1]:.2e} "
+          f"(mean vs rounded model {mean_r:.2e}); count rel L2 pi {errs[0]:.2e} A {errs[1]:.2e} "
           f"B {errs[2]:.2e}; worst |d|/(1+|ref|) {max(worst):.2e}")
     # invariants per model
     for k in range(w.K):
@@ -104,12 +109,13 @@ def test_bf16_adjoint_all_models_signed_weights(case):
     wts = rng.uniform(-1.0, 1.0, size=(w.S, w.K)).astype(np.float32)
     wts[rng.random(size=wts.shape) < 0.1] = 0.0  # zero weights drop out
     ll, cpi, cA, cB = _run(w, False, wts)
-    rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
+    hm = held_model(w, "bf16")
+    rll, rpi, rA, rB, _ = oracle.forward_backward(hm, w.symbols, w.offsets, w.lengths,
                                                   None, wts.astype(np.float64), nthreads=8)
     T = np.maximum(w.lengths, 1).astype(np.float64)[:, None]
     assert np.all(np.abs(ll - rll) <= 2 * U_BF16 * T + ll_tol(w.lengths)[:, None])
     # signed weights: compare on the scale of the unsigned totals
-    _, upi, uA, uB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
+    _, upi, uA, uB, _ = oracle.forward_backward(hm, w.symbols, w.offsets, w.lengths,
                                                 None, np.abs(wts).astype(np.float64), nthreads=8)
     for g, r, u in zip((cpi, cA, cB), (rpi, rA, rB), (upi, uA, uB)):
         assert np.linalg.norm(g - r) <= U_BF16 * np.linalg.norm(u), np.linalg.norm(g - r) / np.linalg.norm(u)
@@ -121,8 +127,8 @@ def test_bf16_adjoint_rows_longer_than_the_first_row_of_their_tile():
     tile are not in exact length order: every row must still run to its end."""
     w = synth.make_workload("training", n_seqs=300, lengths=("uniform", 256, 263), K=1)
     ll, cpi, cA, cB = _run(w, True)
-    rll, rpi, rA, rB, _ = oracle.forward_backward(oparams(w), w.symbols, w.offsets, w.lengths,
-                                                  w.labels, nthreads=8)
+    rll, rpi, rA, rB, _ = oracle.forward_backward(held_model(w, "bf16"), w.symbols, w.offsets,
+                                                  w.lengths, w.labels, nthreads=8)
     T = w.lengths.astype(np.float64)
     assert np.all(np.abs(ll - rll) <= 2 * U_BF16 * T + ll_tol(w.lengths))
     assert np.all(np.abs(ll - rll) <= seq_cap(U_BF16, w.lengths))
@@ -162,7 +168,7 @@ def test_bf16_adjoint_degenerate_and_errors():
     ok = np.array([0, 1, 3, 4, 6])
     rll, rpi, rA, rB, _ = oracle.forward_backward(oracle.params(pi, A, B), sym, offsets[ok],
                                                   lengths[ok], labels[ok], nthreads=4)
-    assert np.all(np.abs(ll[ok] - rll) <= 2 * U_BF16 * np.maximum(lengths[ok], 1) + 1e-3)
+    assert np.all(np.abs(ll[ok] - rll) <= 3 * U_BF16 * np.maximum(lengths[ok], 1) + 1e-3)
     check_counts((cpi, cA, cB), (rpi, rA, rB), rtol=U_BF16, what="degenerate")
     # small N is not served by the tensor-core adjoint; M above 256 neither
     small = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 2, 16, 5)]
@@ -184,7 +190,7 @@ def test_bf16_adjoint_full_training_size_invariants():
     rll, _, _ = oracle.forward(oparams(w), w.symbols, w.offsets[idx], w.lengths[idx],
                                w.labels[idx], nthreads=8)
     T = np.maximum(w.lengths[idx], 1).astype(np.float64)
-    assert np.all(np.abs(ll[idx] - rll) <= 2 * U_BF16 * T + ll_tol(w.lengths[idx]))
+    assert np.all(np.abs(ll[idx] - rll) <= 3 * U_BF16 * T + ll_tol(w.lengths[idx]))
     for k in range(w.K):
         Tk = w.lengths[w.labels == k].astype(np.float64)
         assert abs(cpi[k].sum() - (Tk > 0).sum()) <= U_BF16 * max(1.0, Tk.size)

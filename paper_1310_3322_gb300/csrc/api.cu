@@ -217,6 +217,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
   L.pip = off; off = align256(off + (size_t)d.K * NP * 4);
   L.Ap = off; off = align256(off + (size_t)d.K * NP * NP * 4);
   L.Btp = off; off = align256(off + (size_t)d.K * d.M * NP * 4);
+  L.Btp16 = off; off = align256(off + (size_t)d.K * d.M * NP * 2);
   if (op == HMM_OP_VITERBI) {
     L.bp_cap = (q.total_obs > 0 ? q.total_obs : 0) * (int64_t)NP;
     L.bp = off; off = align256(off + (size_t)L.bp_cap);
@@ -396,6 +397,7 @@ static SetupArgs setup_args(const hmm_dims_t& d, const hmm_seqs_t& q, const WsLa
   s.lengths = q.lengths; s.offsets = q.offsets; s.model_of_seq = q.model_of_seq;
   s.model_base = q.model_base; s.span = span_of(q, d);
   s.pip = at<float>(ws, L.pip); s.Ap = at<float>(ws, L.Ap); s.Btp = at<float>(ws, L.Btp);
+  s.Btp16 = at<uint16_t>(ws, L.Btp16);
   s.seqlen = at<int32_t>(ws, L.seqlen);
   s.order = at<int32_t>(ws, L.order);
   s.done = at<int32_t>(ws, L.done);
@@ -421,6 +423,7 @@ static ModelArgs model_args(const WsLayout& L, void* ws) {
   m.pip = at<float>(ws, L.pip);
   m.Ap = at<float>(ws, L.Ap);
   m.Btp = at<float>(ws, L.Btp);
+  m.Btp16 = at<uint16_t>(ws, L.Btp16);
   return m;
 }
 

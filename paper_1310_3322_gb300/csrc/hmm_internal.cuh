@@ -30,6 +30,7 @@ static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
 struct WsLayout {
   size_t order, seqlen, done, bpoff, best, pip, Ap, Btp, bp, partial, red1, total;
+  size_t Btp16;          // the emission table as BF16 bits (the BF16 path)
   size_t phist, punits;  // setup plan over many blocks
   size_t vgorder, vgcount;  // Viterbi paths above 64 states: grouping by model
   int NP;
@@ -78,6 +79,7 @@ struct ModelArgs {
   const float* pip;   // [K][NP]
   const float* Ap;    // [K][NP][NP]
   const float* Btp;   // [K][M][NP]  (emission table transposed: symbol-major)
+  const uint16_t* Btp16;  // [K][M][NP]  the same as BF16 bits (BF16 path only)
 };
 
 struct SetupArgs {
@@ -100,6 +102,7 @@ struct SetupArgs {
   float* pip;
   float* Ap;
   float* Btp;
+  uint16_t* Btp16;     // bf16_b: Btp's values as BF16 bits
   int32_t* seqlen;
   int32_t* order;
   int32_t* done;

@@ -120,6 +120,7 @@ struct FbThread {
   int row, col0;
   const uint8_t* sB;   // shared emission table (EMIS)
   const float* Bk;     // global emission table of the model [M][NP]
+  const uint16_t* Bk16;  // the same as BF16 bits
 
   // b_j(sym) for this thread's columns: sub-chunk `sub` from the shared
   // table, or all of them from memory (prefetched a step ahead)
@@ -131,48 +132,53 @@ struct FbThread {
       b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
     }
   }
-  // This thread's COLS columns of emission row `sym` from memory, in two
+  // This thread's COLS columns of emission row `sym` from the BF16 table in
+  // memory (the emission values of the BF16 path are BF16 numbers), in two
   // halves so the loads' latency hides behind the next MMA wait: emis_load
   // at the end of a step, emis_ready after the next step's wait. The 32
   // lanes of a warp are 32 rows with unrelated symbols, so a per-lane load
-  // would touch 32 cache lines per warp instruction. Instead the Q = COLS / 8
+  // would touch 32 cache lines per warp instruction. Instead the Q = COLS / 16
   // lanes of a group load the Q rows of the group in turn, 32 contiguous
-  // bytes per lane (32 / Q lines per warp instruction), and a Q x Q butterfly
-  // transpose within the group (element = 8 values) hands every lane its own
-  // row. Every lane of the warp must call both (full-warp shuffles).
-  __device__ __forceinline__ void emis_load(float (&w)[L::COLS], int sym) const {
-    constexpr int Q = L::COLS / 8;
-    const int lane = threadIdx.x & 31, j = lane & (Q - 1);
+  // bytes (16 values) per lane, and a Q x Q butterfly transpose within the
+  // group (element = 8 words) hands every lane its own row. Every lane of the
+  // warp must call both (full-warp shuffles).
+  static constexpr int QE = L::COLS / 16;
+  __device__ __forceinline__ void emis_load(uint32_t (&w)[L::COLS / 2], int sym) const {
+    const int lane = threadIdx.x & 31, j = lane & (QE - 1);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int si = __shfl_sync(HMM_FULL_MASK, sym, (lane & ~(Q - 1)) | i);
-      const float* p = Bk + (size_t)si * NP + col0 + 8 * j;  // 32-byte aligned
-      asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                   : "=f"(w[8 * i]), "=f"(w[8 * i + 1]), "=f"(w[8 * i + 2]), "=f"(w[8 * i + 3]),
-                     "=f"(w[8 * i + 4]), "=f"(w[8 * i + 5]), "=f"(w[8 * i + 6]), "=f"(w[8 * i + 7])
+    for (int i = 0; i < QE; ++i) {
+      const int si = QE > 1 ? __shfl_sync(HMM_FULL_MASK, sym, (lane & ~(QE - 1)) | i) : sym;
+      const uint16_t* p = Bk16 + (size_t)si * NP + col0 + 16 * j;  // 32-byte aligned
+      asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=r"(w[8 * i]), "=r"(w[8 * i + 1]), "=r"(w[8 * i + 2]), "=r"(w[8 * i + 3]),
+                     "=r"(w[8 * i + 4]), "=r"(w[8 * i + 5]), "=r"(w[8 * i + 6]), "=r"(w[8 * i + 7])
                    : "l"(p));
     }
   }
-  __device__ __forceinline__ void emis_ready(float (&w)[L::COLS]) const {
-    constexpr int Q = L::COLS / 8;
-    const int j = threadIdx.x & (Q - 1);
-    // lane j holds chunk j of rows 0..Q-1 of the group; swap the lane bit and
-    // the row bit, one bit at a time, so that lane j holds row j's chunks
+  __device__ __forceinline__ void emis_ready(uint32_t (&w)[L::COLS / 2], float (&b)[L::COLS]) const {
+    const int j = threadIdx.x & (QE - 1);
+    // lane j holds piece j of rows 0..Q-1 of the group; swap the lane bit and
+    // the row bit, one bit at a time, so that lane j holds row j's pieces
 #pragma unroll
-    for (int bit = 1; bit < Q; bit <<= 1) {
+    for (int bit = 1; bit < QE; bit <<= 1) {
       const bool hi = (j & bit) != 0;
 #pragma unroll
-      for (int i0 = 0; i0 < Q; ++i0) {
+      for (int i0 = 0; i0 < QE; ++i0) {
         if (i0 & bit) continue;
         const int i1 = i0 | bit;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const float y =
+          const uint32_t y =
               __shfl_xor_sync(HMM_FULL_MASK, hi ? w[8 * i0 + e] : w[8 * i1 + e], bit);
           if (hi) w[8 * i0 + e] = y;
           else w[8 * i1 + e] = y;
         }
       }
+    }
+#pragma unroll
+    for (int k = 0; k < L::COLS / 2; ++k) {
+      b[2 * k] = __uint_as_float(w[k] << 16);
+      b[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
     }
   }
   // sub-chunk `sub` of this thread's columns of a row image (BF16 pairs)
@@ -327,6 +333,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
     const int Lt = a.tile_len[tile];
     const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
     me.Bk = a.mod.Btp + (size_t)k * M * NP;
+    me.Bk16 = a.mod.Btp16 + (size_t)k * M * NP;
     if (k != cur_model) {
       // transition image: (n = j, k = i) = a_ij, pairs along i
       for (int idx = tid; idx < NP * NP / 2; idx += L::NTH) {
@@ -566,6 +573,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
       // one forward step's epilogue over this thread's columns: D (tensor
       // memory) -> X_t (operand image, and `gimg` in memory when not null)
       float pf[L::EMIS ? 1 : COLS];  // emission values prefetched from memory
+      uint32_t pw[L::EMIS ? 1 : COLS / 2];  // their BF16 words in flight
       float bsm[SUB];                // emission values from the shared table (EMIS)
       auto fwd_step = [&](int f, bool live, uint8_t* gimg) -> float {
         float sum = 0.f;
@@ -593,7 +601,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           int on = sym_at(t0 + 1);
           int fn2 = t0 + 2 < t1 ? (int)__ldcg(gexp + (size_t)(t0 + 2) * 128 + row) : 0;
           int on2 = t0 + 2 < t1 ? sym_at(t0 + 2) : 0;
-          if constexpr (!L::EMIS) me.emis_load(pf, on);
+          if constexpr (!L::EMIS) me.emis_load(pw, on);
           for (int t = t0 + 1; t < t1 && run; ++t) {
             const int f = fn;
             const int ot = on;
@@ -605,10 +613,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             }
             if constexpr (L::EMIS) me.emis_sub(bsm, ot, 0);
             wait_e(b_done, ph_done);
-            if constexpr (!L::EMIS) me.emis_ready(pf);
+            if constexpr (!L::EMIS) me.emis_ready(pw, pf);
             fwd_step(f, act && t < T, scr + (size_t)(t - t0) * IMG);
             if constexpr (!L::EMIS)
-              if (t + 1 < t1) me.emis_load(pf, on);
+              if (t + 1 < t1) me.emis_load(pw, on);
             tc::fence_proxy_async();
             if (t == t1 - 1) tc::fence_proxy_async_all();  // images read by bulk copies
             run = handoff();
@@ -670,7 +678,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
         int onx = t1 - 2 >= t0 ? sym_at(t1 - 2) : 0;  // step t - 1, in flight
         int gnx = t1 - 2 >= t0 ? (int)__ldcg(gexp + (size_t)(t1 - 2) * 128 + row) : 0;
-        if constexpr (!L::EMIS) me.emis_load(pf, ocur);
+        if constexpr (!L::EMIS) me.emis_load(pw, ocur);
         for (int t = t1 - 1; t >= t0 && run; --t) {
           const bool has_mma = t < Lt - 1;
           const int S = t % NB;
@@ -684,7 +692,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             tc::discard_l2((t == t0 ? ckx + (size_t)seg * IMG : scr + (size_t)(t - t0) * IMG) +
                            (size_t)tid * 128);
           if (has_mma) wait_e(b_done, ph_done);
-          if constexpr (!L::EMIS) me.emis_ready(pf);
+          if constexpr (!L::EMIS) me.emis_ready(pw, pf);
           const bool is_init = act && t == T - 1;
           const bool on = act && t < T - 1;
           if (is_init) c = w / s_last;
@@ -746,7 +754,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               onx = sym_at(t - 2);
               gnx = (int)__ldcg(gexp + (size_t)(t - 2) * 128 + row);
             }
-            if constexpr (!L::EMIS) me.emis_load(pf, ocur);
+            if constexpr (!L::EMIS) me.emis_load(pw, ocur);
           }
           tc::fence_proxy_async();
           run = handoff();

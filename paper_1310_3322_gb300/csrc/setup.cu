@@ -247,7 +247,11 @@ __device__ void prep_blocks(const SetupArgs& a, int blk, int nblk) {
       const int m = (int)((r / a.NP) % a.M), j = (int)(r % a.NP);
       float v = j < a.N ? prep_value(a.B[((size_t)k * a.N + j) * a.M + m], a.log_mode, a.status)
                         : pad;
-      if (a.bf16_b) v = __bfloat162float(__float2bfloat16_rn(v));
+      if (a.bf16_b) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        v = __bfloat162float(h);
+        a.Btp16[r] = *reinterpret_cast<const uint16_t*>(&h);
+      }
       a.Btp[r] = v;
     }
   }

@@ -415,15 +415,12 @@ def run_gpu(args, emit=True):
         "adjoint": (8 * N * N + 10 * N) * sumT,
     }
     dom = max(flops, key=lambda k: totals.get(k, 0.0))
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s at max clock
+    peak, peak_basis, nominal = fp32_peak(torch, dev)
     achieved = flops[dom] / (per_launch[dom] / 1e3) / 1e12
     roofline = {
         "bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak, "traffic": traffic_for(dom),
-        "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
-        "frac_at_measured_clock": (achieved / (peak * clk["sm_mhz"] / SM_MAX_MHZ))
-        if clk.get("sm_mhz") else None,
+        "peak_basis": peak_basis, "frac_of_nominal": achieved / nominal,
         "launch_ms": per_launch[dom],
     }
     phases = {}
@@ -575,6 +572,19 @@ def fma_peak(torch, dev):
         res[name] = fl / (best / 1e3) / 1e12
     assert bool(torch.isfinite(out).all())
     return max(res.values()), res
+
+
+def fp32_peak(torch, dev):
+    """The FP32 roofline denominator of the SIMT kernels: the measured FFMA
+    rate (fma_peak) with its basis, and the nominal SMs x 128 lanes x 2 flop x
+    maximum clock beside it."""
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    nominal = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    measured, modes = fma_peak(torch, dev)
+    basis = (f"measured: hmm_fma_probe, best of scalar FFMA {modes['ffma']:.1f} and packed "
+             f"FFMA2 {modes['ffma2']:.1f} TFLOP/s (nominal {sm_count} SMs x 128 lanes x 2 flop x "
+             f"{SM_MAX_MHZ:.0f} MHz = {nominal:.1f})")
+    return measured, basis, nominal
 
 
 def tf32_peak(torch, dev):
@@ -1009,8 +1019,7 @@ def run_learning(args, emit=True):
         peak, basis = measured_peak_bf16()
         peak_basis = f"dense BF16, {basis} (burst)"
     else:
-        peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        peak_basis = f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
+        peak, peak_basis, _ = fp32_peak(torch, dev)
     achieved = flops / (adj_ms / 1e3) / 1e12
 
     # the plain per-sequence forward kernels on the same data (all K models)
@@ -1187,8 +1196,7 @@ def run_teamwork(args):
     flop_launch = (2.0 * N * N + N) * units / len(roles)
     dom = max(("forward", "viterbi_scores"), key=lambda k: per_launch.get(k, 0.0))
     achieved = flop_launch / (per_launch[dom] / 1e3) / 1e12
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak, peak_basis, _ = fp32_peak(torch, dev)
     line = {
         "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -1205,8 +1213,7 @@ def run_teamwork(args):
                    "l2": "flushed between steps (256 MB write outside the timed events)"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "launch_ms": per_launch[dom],
-                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x "
-                                   f"{SM_MAX_MHZ:.0f} MHz", "traffic": None},
+                     "peak_basis": peak_basis, "traffic": None},
         "clocks": clk,
         "kernel_ms_per_launch": per_launch,
         "gpu_launches": sum(v[0] for v in kt.values())
@@ -1364,8 +1371,7 @@ def run_longseq(args):
     # recursion started from state i); the sequential recursion does 2 N^2
     steps = int((np.maximum(w.lengths.astype(np.int64), 1) - 1).sum()) * K
     achieved = 2.0 * NP ** 3 * steps / (kms["scan_chunks"] / 1e3) / 1e12
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak, peak_basis, _ = fp32_peak(torch, dev)
     L = args.scan_chunk or min(65536, -(-int(np.ceil(np.sqrt(2.0 * w.max_len))) // 16) * 16)
     line = {
         "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
@@ -1381,8 +1387,7 @@ def run_longseq(args):
         "roofline": {"bound": "alu", "kernel": "scan_chunks", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "launch_ms": kms["scan_chunks"],
-                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x "
-                                   f"{SM_MAX_MHZ:.0f} MHz", "traffic": None},
+                     "peak_basis": peak_basis, "traffic": None},
         "kernel_ms": kms,
         "sequential_forward": {"ms": seq_ms, "value": units / (seq_ms / 1e3),
                                "max_abs_diff_nats": diff},

@@ -99,61 +99,61 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmm_fb_pass(FbSegLaunch a
         load_vec<J>(pv, a.mod.pip + (size_t)k * NP + j0);
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) x[jj] = pv[jj] * b[jj];
-        const float gs = group_sum<G>(tree_sum<J>(x));
-        if (Tn > 0 && !bad) {
-          if (gs == 0.f) dead = true;
-          else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
-          else {
-            const int e = rescale_pow2<J>(x, gs);
-            E += e;
-            store_vec<J>(cka, x);
-            if (r == 0) cke[0] = e;
-          }
+        if (Tn > 0) {
+          store_vec<J>(cka, x);
+          if (r == 0) cke[0] = 0;
         }
       }
+      // the steps of fb.cu's first phase: each step scales its result by the
+      // exponent of its input row's sum (lane-local), e_{t+1} = f_t is kept
+      // with the checkpoints, liveness by flags
       float bn[J];
-      int on = 0;
-      if (1 < Tn) {
-        on = __ldg(o + 1);
-        if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
-      }
+      int on = (1 < Tn) ? __ldg(o + 1) : 0;
+      bool symbad = (unsigned)on >= (unsigned)M;
+      on = symbad ? 0 : on;
       load_vec<J>(bn, Bk + (size_t)on * NP);
       int o2 = (2 < Tn) ? __ldg(o + 2) : 0;
+      int cls = 0;
+      int cc = 0, ci = 0;
       for (int t = 1; t < Tmax; ++t) {
-        const bool act = t < Tn && !dead && !bad;
+        const bool act = t < Tn;
         float* xw = &xs[warp][p][t & 1][0];
         store_vec<J>(xw + j0, x);
         __syncwarp();
-        float nx[J];
-        matvec_cols<NP, J>(xw, ac, nx);
+        float nx[J], sx;
+        matvec_cols_sum<NP, J>(xw, ac, nx, sx);
         float b[J];
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) b[jj] = bn[jj];
-        if (t + 1 < Tn) {
-          on = o2;
-          if ((unsigned)on >= (unsigned)M) { bad = true; err |= HMM_STATUS_SYMBOL; on = 0; }
+        {
+          const bool nb_ = (unsigned)o2 >= (unsigned)M;
+          symbad |= nb_ && t + 1 < Tn;
+          on = nb_ ? 0 : o2;
           load_vec<J>(bn, Bk + (size_t)on * NP);
           if (t + 2 < Tn) o2 = __ldg(o + t + 2);
         }
+        int f;
+        const float sc = pow2_scale(sx, f);
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) nx[jj] *= b[jj];
-        const float gs = group_sum<G>(tree_sum<J>(nx));
-        if (act) {
-          if (gs == 0.f) dead = true;
-          else if (!(gs > 0.f) || isinf(gs)) { bad = true; err |= HMM_STATUS_PARAM; }
-          else {
-            const int e = rescale_pow2<J>(nx, gs);
-            E += e;
+        for (int jj = 0; jj < J; ++jj) nx[jj] = (nx[jj] * sc) * b[jj];
+        if (++cc == C) { cc = 0; ++ci; }
+        cls |= act ? sum_class(sx) : 0;
+        E += act ? f : 0;
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) x[jj] = nx[jj];
-            if (t % C == 0) {
-              store_vec<J>(cka + (size_t)(t / C) * NP, x);
-              if (r == 0) cke[t / C] = e;
-            }
-          }
+        for (int jj = 0; jj < J; ++jj) x[jj] = act ? nx[jj] : x[jj];
+        if (act && cc == 0) {
+          store_vec<J>(cka + (size_t)ci * NP, x);
+          if (r == 0) cke[ci] = f;
         }
       }
+      if (symbad) { bad = true; err |= HMM_STATUS_SYMBOL; }
+      if (cls & 2) { bad = true; err |= HMM_STATUS_PARAM; }
+      else if (cls & 1) dead = true;
       const float fs = group_sum<G>(tree_sum<J>(x));
+      if (Tn > 0 && !bad && !dead) {
+        if (fs == 0.f) dead = true;
+        else if (!(fs > 0.f) || isinf(fs)) { bad = true; err |= HMM_STATUS_PARAM; }
+      }
       if (has && r == 0) {
         float out;
         if (bad) { out = __int_as_float(0x7fc00000); if (err) set_status(a.status, err); }
@@ -198,19 +198,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmm_fb_pass(FbSegLaunch a
         float* vw = &xs[warp][p][u & 1][0];
         store_vec<J>(vw + j0, v);
         __syncwarp();
-        float nb[J];
-        rows_matvec<NP, J>(vw, ar, nb);
-        const float gs = group_sum<G>(tree_sum<J>(nb));
-        if (act) {
-          if (!(gs > 0.f) || isinf(gs)) {
-            live = false;  // impossible or invalid: the forward marks the pair skipped
-          } else {
-            rescale_pow2<J>(nb, gs);
+        // beta_t = A v scaled by the exponent of sum v (lane-local)
+        float nb[J], su;
+        rows_matvec_sum<NP, J>(vw, ar, nb, su);
+        int g_;
+        const float sg = pow2_scale(su, g_);
+        // a zero, infinite or invalid row: the forward marks the pair skipped
+        live = live && !(act && (!(su > 0.f) || isinf(su)));
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) beta[jj] = nb[jj];
-            if (t % C == 0) store_vec<J>(ckb + (size_t)(t / C) * NP, beta);
-          }
-        }
+        for (int jj = 0; jj < J; ++jj) beta[jj] = (act && live) ? nb[jj] * sg : beta[jj];
+        if (act && live && t % C == 0) store_vec<J>(ckb + (size_t)(t / C) * NP, beta);
       }
     }
   }
@@ -340,18 +337,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmm_fb_seg(FbSegLaunch a)
           float* xw = xf + (t & 1) * XS;
           store_vec<J>(xw + j0, xr);
           __syncwarp();
-          float nx[J], b[J];
-          matvec_cols<NP, J>(xw, ac, nx);
+          float nx[J], b[J], sx;
+          matvec_cols_sum<NP, J>(xw, ac, nx, sx);
           load_vec<J>(b, Bk + (size_t)sym(t) * NP);
+          int f;
+          const float sc = pow2_scale(sx, f);
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) nx[jj] *= b[jj];
-          const float gs = group_sum<G>(tree_sum<J>(nx));
-          if (ra && gs > 0.f && !isinf(gs)) {
-            const int e = rescale_pow2<J>(nx, gs);
+          for (int jj = 0; jj < J; ++jj) nx[jj] = (nx[jj] * sc) * b[jj];
+          if (ra) {
 #pragma unroll
             for (int jj = 0; jj < J; ++jj) xr[jj] = nx[jj];
             store_vec<J>(sg + (t - t0) * NP + j0, xr);
-            if (r == 0) se[t - t0] = e;
+            if (r == 0) se[t - t0] = f;
           }
         }
         __syncwarp();
@@ -384,34 +381,45 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmm_fb_seg(FbSegLaunch a)
         load_vec<J>(br, Bk + (size_t)sr_next * NP);
         sr_next = rc_on ? sym(r0 + 2) : 0;
 
+        // alpha rows and exponents of the backward steps, one iteration ahead
+        // (fb.cu's second phase): a1 = alpha_{t+1}, e1 = e_{t+1} (the next
+        // segment's checkpoint at the top), a0 = alpha_t, e0 = e_t; indices
+        // clamped into the buffers, steps outside a pair's range masked
+        float a1[J], a0[J];
+        load_vec<J>(a1, cka + (size_t)min(c + 1, NC - 1) * NP);
+        int e1 = act ? cke[min(c + 1, NC - 1)] : 0;
+        load_vec_smem<J>(a0, cur + (t1 - t0) * NP + j0);
+        int e0 = cure[t1 - t0];
+
         for (int u = 0; u < C; ++u) {
           const int tb = t1 - u;
           const bool bact = act && tb >= t0 && c <= c_hi && tb <= Tb - 2;
           const int tr = r0 + 1 + u;
           const bool ract = rc_on && act && u <= C - 2 && tr <= Tb - 1;
 
-          // backward: v = u_{t+1} / Z_t, gamma_{t+1} emissions (not at a range's top)
-          float a1[J], a0[J], v[J];
-          int e1 = 0;
-          if (bact) {
-            if (tb + 1 <= t1) {
-              load_vec_smem<J>(a1, cur + (tb + 1 - t0) * NP + j0);
-              e1 = cure[tb + 1 - t0];
-            } else {
-              load_vec<J>(a1, cka + (size_t)(c + 1) * NP);
-              e1 = cke[c + 1];
-            }
-            load_vec_smem<J>(a0, cur + (tb - t0) * NP + j0);
-            const float invD = 1.f / D;
-            const float wd = w * invD;
+          // backward: publish u_{t+1} = b beta_{t+1} 2^-e_{t+1}, count
+          // gamma_{t+1} (not at a range's top); branch-free
+          const int nidx = max(tb - 1 - t0, 0);
+          float a0n[J];
+          load_vec_smem<J>(a0n, cur + nidx * NP + j0);
+          const int e0n = cure[nidx];
+          float aw[J], v[J];
+          const float invD = __frcp_rn(D);
+          const float se1 = exp2i(-e1);
+          const float wd = w * invD;
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) {
-              if (tb != t_skip) cb[(j0 + jj) * MP + sb] += wd * a1[jj] * beta[jj];
-              v[jj] = mul_pow2(bb[jj] * beta[jj], -e1) * invD;
-            }
-          } else {
+          for (int jj = 0; jj < J; ++jj) {
+            const float gam = wd * a1[jj] * beta[jj];
+            float* cbp = cb + (j0 + jj) * MP + sb;
+            if (bact && tb != t_skip) *cbp += gam;
+            v[jj] = bact ? (bb[jj] * beta[jj]) * se1 : 0.f;
+            aw[jj] = bact ? (w * a0[jj]) * invD : 0.f;
+          }
+          float a0s[J], a0m[J];
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) { a0[jj] = 0.f; v[jj] = 0.f; }
+          for (int jj = 0; jj < J; ++jj) {
+            a0s[jj] = a0[jj];
+            a0m[jj] = bact ? a0[jj] : 0.f;
           }
           float* vw = xv + (u & 1) * XS;
           float* xw = xf + (u & 1) * XS;
@@ -428,38 +436,47 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmm_fb_seg(FbSegLaunch a)
           __syncwarp();
 
           // recompute step of segment c-1 (independent chain)
-          float nx[J];
-          matvec_cols<NP, J>(xw, ac, nx);
+          float nx[J], sx;
+          matvec_cols_sum<NP, J>(xw, ac, nx, sx);
+          int fr;
+          const float scr = pow2_scale(sx, fr);
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) nx[jj] *= br[jj];
-          const float rs = group_sum<G>(tree_sum<J>(nx));
+          for (int jj = 0; jj < J; ++jj) nx[jj] = (nx[jj] * scr) * br[jj];
 
-          // backward step: beta_t and the xi accumulator
-          float aw[J], nb[J];
-#pragma unroll
-          for (int ii = 0; ii < J; ++ii) aw[ii] = w * a0[ii];
-          rows_step<NP, J>(vw, ar, aw, xa, nb);
+          // backward step: beta_t scaled by the exponent of sum u, and the xi
+          // accumulator normalised by D_{t+1}
+          float nb[J], su;
+          rows_step_sum<NP, J>(vw, ar, aw, xa, nb, su);
+          int fu;
+          const float sgu = pow2_scale(su, fu);
           float ad[J];
 #pragma unroll
-          for (int ii = 0; ii < J; ++ii) ad[ii] = a0[ii] * nb[ii];
-          const float2 red = group_sum2<G>(make_float2(tree_sum<J>(nb), tree_sum<J>(ad)));
+          for (int ii = 0; ii < J; ++ii) {
+            nb[ii] *= sgu;
+            ad[ii] = a0m[ii] * nb[ii];
+          }
+          const float Dn = group_sum<G>(tree_sum<J>(ad));
 
-          if (ract && rs > 0.f && !isinf(rs)) {
-            const int e = rescale_pow2<J>(nx, rs);
-#pragma unroll
-            for (int jj = 0; jj < J; ++jj) xr[jj] = nx[jj];
-            store_vec<J>(nxt + (u + 1) * NP + j0, xr);
-            if (r == 0) nxte[u + 1] = e;
+          if (ract) {
+            store_vec<J>(nxt + (u + 1) * NP + j0, nx);
+            if (r == 0) nxte[u + 1] = fr;
           }
-          if (bact && red.x > 0.f && !isinf(red.x)) {
-            const int e = rescale_pow2<J>(nb, red.x);
 #pragma unroll
-            for (int ii = 0; ii < J; ++ii) beta[ii] = nb[ii];
-            D = mul_pow2(red.y, -e);
-          }
+          for (int jj = 0; jj < J; ++jj) xr[jj] = ract ? nx[jj] : xr[jj];
+          const bool bok = bact && su > 0.f && !isinf(su);
+#pragma unroll
+          for (int ii = 0; ii < J; ++ii) beta[ii] = bok ? nb[ii] : beta[ii];
+          D = bok ? Dn : D;
           sb = sb_cur;
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) { bb[jj] = bbn[jj]; br[jj] = brn[jj]; }
+          for (int jj = 0; jj < J; ++jj) {
+            bb[jj] = bbn[jj];
+            br[jj] = brn[jj];
+            a1[jj] = a0s[jj];
+            a0[jj] = a0n[jj];
+          }
+          e1 = e0;
+          e0 = e0n;
         }
         __syncwarp();
       }

@@ -546,11 +546,11 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
       // the pass kernel's row sum at the row's last step: 0 = no counts
       // (impossible sequence), NaN = invalid row
       const float s_last = a.s_last[(size_t)tile * 128 + row];
-      auto sym_at = [&](int t) -> int {  // symbol at step t (0 past the row's end)
-        if (t >= T) return 0;
-        const int v = __ldg(o + t);
-        return (unsigned)v < (unsigned)M ? v : 0;
-      };
+      // symbols: the load of step t (0 past the row's end) is issued a step or
+      // two before its use and range-checked only at the use, so that no
+      // instruction waits for it in between
+      auto sym_raw = [&](int t) -> int { return t < T ? __ldg(o + t) : 0; };
+      auto sym_ok = [&](int v) -> int { return (unsigned)v < (unsigned)M ? v : 0; };
       auto wait_e = [&](uint64_t* bar, uint32_t& ph) {
         fb_wait(bar, ph, abortp, a.wait_limit);
         ph ^= 1;
@@ -598,18 +598,18 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         if (t1 - t0 > 1) {
           // symbol and exponent of steps t + 1 and t + 2 in flight
           int fn = (int)__ldcg(gexp + (size_t)(t0 + 1) * 128 + row);
-          int on = sym_at(t0 + 1);
+          int on = sym_ok(sym_raw(t0 + 1));
           int fn2 = t0 + 2 < t1 ? (int)__ldcg(gexp + (size_t)(t0 + 2) * 128 + row) : 0;
-          int on2 = t0 + 2 < t1 ? sym_at(t0 + 2) : 0;
+          int on2 = t0 + 2 < t1 ? sym_raw(t0 + 2) : 0;
           if constexpr (!L::EMIS) me.emis_load(pw, on);
           for (int t = t0 + 1; t < t1 && run; ++t) {
             const int f = fn;
             const int ot = on;
             fn = fn2;
-            on = on2;
+            on = sym_ok(on2);
             if (t + 2 < t1) {
               fn2 = (int)__ldcg(gexp + (size_t)(t + 2) * 128 + row);
-              on2 = sym_at(t + 2);
+              on2 = sym_raw(t + 2);
             }
             if constexpr (L::EMIS) me.emis_sub(bsm, ot, 0);
             wait_e(b_done, ph_done);
@@ -675,8 +675,8 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         }
 
         // (B) backward over the segment
-        int ocur = sym_at(t1 - 1), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
-        int onx = t1 - 2 >= t0 ? sym_at(t1 - 2) : 0;  // step t - 1, in flight
+        int ocur = sym_ok(sym_raw(t1 - 1)), gcur = (int)__ldcg(gexp + (size_t)(t1 - 1) * 128 + row);
+        int onx = t1 - 2 >= t0 ? sym_raw(t1 - 2) : 0;  // step t - 1, in flight
         int gnx = t1 - 2 >= t0 ? (int)__ldcg(gexp + (size_t)(t1 - 2) * 128 + row) : 0;
         if constexpr (!L::EMIS) me.emis_load(pw, ocur);
         for (int t = t1 - 1; t >= t0 && run; --t) {
@@ -748,10 +748,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           if (!live) c = 0.f;
           // next step's inputs
           if (t > t0) {
-            ocur = onx;
+            ocur = sym_ok(onx);
             gcur = gnx;
             if (t - 2 >= t0) {
-              onx = sym_at(t - 2);
+              onx = sym_raw(t - 2);
               gnx = (int)__ldcg(gexp + (size_t)(t - 2) * 128 + row);
             }
             if constexpr (!L::EMIS) me.emis_load(pw, ocur);

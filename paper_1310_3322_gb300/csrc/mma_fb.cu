@@ -591,7 +591,9 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
       bool run = true;
       const bool act = has && w != 0.f && s_last > 0.f && !isinf(s_last);
       float c = 0.f;               // this row's current normaliser
-      int kprev[2] = {-1, -1};     // one-hot entries set in each operand set
+      // one-hot entries set in each operand set (two registers: an array
+      // indexed by the step's parity would live in local memory)
+      int kprev0 = -1, kprev1 = -1;
       for (int seg = seg_hi; seg >= seg_lo && run; --seg) {
         const int t0 = seg * C, t1 = min(t0 + C, Lt);
         // (R) recompute X over the segment from its checkpoint
@@ -737,12 +739,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           }
           if (h == 0) {
             uint8_t* oh = sOH + S * MB * 32768;
-            if (kprev[S] >= 0) *onehot_at(oh, kprev[S], row) = 0;
-            kprev[S] = -1;
-            if (live) {
-              *onehot_at(oh, ocur, row) = 0x3F80;  // BF16 1.0
-              kprev[S] = ocur;
-            }
+            const int kp = S ? kprev1 : kprev0;
+            if (kp >= 0) *onehot_at(oh, kp, row) = 0;
+            if (live) *onehot_at(oh, ocur, row) = 0x3F80;  // BF16 1.0
+            const int kn = live ? ocur : -1;
+            if (S) kprev1 = kn;
+            else kprev0 = kn;
           }
           psum[((t & 1) * TPR + h) * 128 + row] = live ? part2.x + part2.y : 0.f;
           if (!live) c = 0.f;
@@ -811,8 +813,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         }
       }
       if (h == 0)
-        for (int q = 0; q < NB; ++q)
-          if (kprev[q] >= 0) *onehot_at(sOH + q * MB * 32768, kprev[q], row) = 0;
+        for (int q = 0; q < NB; ++q) {
+          const int kp = q ? kprev1 : kprev0;
+          if (kp >= 0) *onehot_at(sOH + q * MB * 32768, kp, row) = 0;
+        }
       tc::fence_proxy_async();
     }
     tc::fence_before_sync();

@@ -72,8 +72,8 @@ struct MmaFbCfg {
   static constexpr bool EMIS = (NP == 64 && MB == 1);  // emission table in shared memory
   static constexpr bool DB = (NP == 64 && MB == 1);    // two operand sets: beta issued first
   static constexpr int NB = DB ? 2 : 1;                // Y / gamma / one-hot sets
-  static constexpr int XIB = 2;                  // X_t buffers
-  static constexpr int ES = NP * 4 + 16;         // padded emission row (bytes)
+  static constexpr int XIB = DB ? 3 : 2;         // X_t buffers (DB: loaded two steps ahead)
+  static constexpr int ES = NP * 2 + 16;         // padded BF16 emission row (bytes)
   static constexpr int OFF_AT = 0;               // (n=j, k=i) = a_ij: forward K-major, backward MN-major
   static constexpr int OFF_XI = MAT;             // X_t images (xi A operand; epilogue rows)
   static constexpr int OFF_Y = OFF_XI + XIB * IMG;     // Y_t sets
@@ -81,7 +81,7 @@ struct MmaFbCfg {
   static constexpr int OFF_OH = OFF_G + NB * IMG;      // one-hot [k][m] sets, MB blocks of 128 x 128
   static constexpr int OFF_XOP = OFF_OH + NB * MB * 32768;  // forward X operand (else aliases gamma)
   static constexpr int OFF_B = OFF_XOP + (DB ? IMG : 0);    // emission rows b(k), k < 128 (EMIS)
-  static constexpr int NBAR = 10;                // mbarriers (see the kernel)
+  static constexpr int NBAR = 11;                // mbarriers (see the kernel)
   static constexpr int OFF_BAR = OFF_B + (EMIS ? 128 * ES : 0);
   static constexpr int OFF_MISC = OFF_BAR + 128;
   static_assert(NBAR * 8 <= OFF_MISC - OFF_BAR, "mbarrier area");
@@ -122,14 +122,19 @@ struct FbThread {
   const float* Bk;     // global emission table of the model [M][NP]
   const uint16_t* Bk16;  // the same as BF16 bits
 
-  // b_j(sym) for this thread's columns: sub-chunk `sub` from the shared
+  // b_j(sym) for this thread's columns: sub-chunk `sub` from the shared BF16
   // table, or all of them from memory (prefetched a step ahead)
   __device__ __forceinline__ void emis_sub(float (&b)[SUB], int sym, int sub) const {
-    const float4* p = reinterpret_cast<const float4*>(sB + sym * L::ES + (col0 + sub * SUB) * 4);
+    const uint4* p = reinterpret_cast<const uint4*>(sB + sym * L::ES + (col0 + sub * SUB) * 2);
 #pragma unroll
-    for (int q = 0; q < SUB / 4; ++q) {
-      const float4 v = p[q];
-      b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+    for (int q = 0; q < SUB / 8; ++q) {
+      const uint4 v = p[q];
+      const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        b[8 * q + 2 * i] = __uint_as_float(u[i] << 16);
+        b[8 * q + 2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+      }
     }
   }
   // This thread's COLS columns of emission row `sym` from the BF16 table in
@@ -267,9 +272,9 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
   uint64_t* b_aux = bars + 2;    // [2] xi (+ emission) products of even / odd steps: control only
   uint64_t* b_seg = bars + 4;    // segment-end emission product: control only
   uint64_t* b_g = bars + 5;      // checkpoint -> forward operand
-  uint64_t* b_x = bars + 6;      // [2] X_t images
-  uint64_t* b_fin = bars + 8;    // teardown after an abort
-  uint64_t* b_y = bars + 9;      // Y checkpoint -> backward operand (a range's start)
+  uint64_t* b_x = bars + 6;      // [XIB] X_t images
+  uint64_t* b_fin = bars + 9;    // teardown after an abort
+  uint64_t* b_y = bars + 10;     // Y checkpoint -> backward operand (a range's start)
   volatile int32_t* misc = reinterpret_cast<volatile int32_t*>(smem + L::OFF_MISC);
   enum { M_TMEM = 0, M_ITEM = 1, M_ABORT = 2 };
 
@@ -310,11 +315,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
 
   // barrier phases: the epilogue threads track b_done and b_x, the control
   // lane every barrier it waits on (each waiter waits every phase, in order)
-  uint32_t ph_done = 0, ph_x[2] = {0, 0};
+  uint32_t ph_done = 0, ph_xb = 0;  // ph_xb bit b: the phase of X buffer b
   uint32_t c_rdy = 0, c_aux[2] = {0, 0}, c_seg = 0, c_g = 0, c_y = 0;
-  uint32_t c_x[2] = {0, 0};      // parity the next load into each X buffer completes
-  uint32_t c_xpar[2] = {0, 0};   // ... and that of the last one issued
-  bool c_xpend[2] = {false, false}, c_gpend = false, c_ypend = false;
+  // per X buffer b (bit b): the parity the next load into it completes, that
+  // of the last one issued, and whether that one is still unwaited
+  uint32_t c_xb = 0, c_xparb = 0, c_xpendb = 0;
+  bool c_gpend = false, c_ypend = false;
   uint32_t c_gpar = 0, c_ypar = 0;
   int cur_model = -1;
   volatile int32_t* abortp = misc + M_ABORT;
@@ -342,11 +348,11 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         *reinterpret_cast<uint32_t*>(sAT + (j / 8) * SBO + (i / 8) * 128 + (j % 8) * 16 +
                                      (i % 8) * 2) = w;
       }
-      if constexpr (L::EMIS) {  // emission rows of the model, padded
-        for (int idx = tid; idx < M * (NP / 4); idx += L::NTH) {
-          const int sym = idx / (NP / 4), q = idx % (NP / 4);
-          *reinterpret_cast<float4*>(smem + L::OFF_B + sym * L::ES + q * 16) =
-              __ldg(reinterpret_cast<const float4*>(me.Bk + (size_t)sym * NP) + q);
+      if constexpr (L::EMIS) {  // the model's BF16 emission rows, padded
+        for (int idx = tid; idx < M * (NP / 8); idx += L::NTH) {
+          const int sym = idx / (NP / 8), q = idx % (NP / 8);
+          *reinterpret_cast<uint4*>(smem + L::OFF_B + sym * L::ES + q * 16) =
+              __ldg(reinterpret_cast<const uint4*>(me.Bk16 + (size_t)sym * NP) + q);
         }
       }
       cur_model = k;
@@ -383,9 +389,11 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           const int b = t % XIB;
           tc::mbar_arrive_expect_tx(&b_x[b], IMG);
           tc::bulk_g2s(aXI + b * IMG, src, IMG, &b_x[b]);
-          c_xpend[b] = true;   // the epilogue waits for it too; the last step's
-          c_xpar[b] = c_x[b];  // load is waited for by the epilogue alone
-          c_x[b] ^= 1;
+          // the epilogue waits for it too; the last step's load is waited
+          // for by the epilogue alone
+          c_xpendb |= 1u << b;
+          c_xparb = (c_xparb & ~(1u << b)) | (c_xb & (1u << b));
+          c_xb ^= 1u << b;
         };
         bool xi_on = false, cb_on = false;
         // the xi / emission products of step t are committed to b_aux[t % 2]:
@@ -420,8 +428,9 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             }
             if (!ok || !wait_c(b_rdy, c_rdy)) break;  // images of the segment in memory
           }
-          // backward
+          // backward: X images XIB - 1 steps ahead
           load_x(t1 - 1, img_of(t1 - 1));
+          if (XIB == 3 && t1 - 2 >= t0) load_x(t1 - 2, img_of(t1 - 2));
           if (restart) {
             // D = Y_{t1} . A^T once, for the epilogue's renormalisation of Y_{t1}
             if (!wait_c(b_y, c_y)) break;
@@ -449,9 +458,10 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
                                ks > 0 ? 1u : 0u);
               };
               auto issue_xi_cb = [&]() {
-                uint32_t par = c_xpar[t % XIB];
-                if (!wait_c(&b_x[t % XIB], par)) return;
-                c_xpend[t % XIB] = false;
+                const int xb = t % XIB;
+                uint32_t par = (c_xparb >> xb) & 1u;
+                if (!wait_c(&b_x[xb], par)) return;
+                c_xpendb &= ~(1u << xb);
                 tc::fence_after_sync();
 #pragma unroll
                 for (int ks = 0; ks < 8; ++ks)
@@ -477,13 +487,14 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               if (DB) {  // beta first: the epilogue waits for it alone
                 issue_beta();
                 tc::mma_commit(b_done);
-                // the next step's X image (its buffer was last read by the xi
-                // product of step t+1), then this step's xi / emission batch
-                if (t > t0) {
-                  wait_aux((t + 1) & 1);
-                  if (!ok) break;
-                  load_x(t - 1, img_of(t - 1));
-                }
+                // the xi batch of step t+1 is waited for at every step (so that
+                // b_aux[t & 1], which takes this step's batch, never holds two
+                // unwaited phases), then the X image XIB - 1 steps ahead goes
+                // into the buffer that batch read, then this step's xi /
+                // emission batch
+                wait_aux((t + 1) & 1);
+                if (!ok) break;
+                if (t - (XIB - 1) >= t0) load_x(t - (XIB - 1), img_of(t - (XIB - 1)));
                 issue_xi_cb();
               } else {
                 issue_xi_cb();
@@ -492,12 +503,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               }
               if (!ok) break;
             }
-            // the next step's X image: its buffer was last read by the xi
-            // product of step t+1
-            if (t > t0 && !(DB && t < Lt - 1)) {
+            // the X image XIB - 1 steps ahead: its buffer was last read by
+            // the xi product of step t+1
+            if (t - (XIB - 1) >= t0 && !(DB && t < Lt - 1)) {
               wait_aux((t + 1) & 1);
               if (!ok) break;
-              load_x(t - 1, img_of(t - 1));
+              load_x(t - (XIB - 1), img_of(t - (XIB - 1)));
             }
             cb_pending = true;
           }
@@ -530,7 +541,8 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           if (c_gpend) tc::mbar_wait_bounded(b_g, c_gpar, kFbWaitLimit);
           if (c_ypend) tc::mbar_wait_bounded(b_y, c_ypar, kFbWaitLimit);
           for (int b = 0; b < XIB; ++b)
-            if (c_xpend[b]) tc::mbar_wait_bounded(&b_x[b], c_xpar[b], kFbWaitLimit);
+            if ((c_xpendb >> b) & 1u)
+              tc::mbar_wait_bounded(&b_x[b], (c_xparb >> b) & 1u, kFbWaitLimit);
         }
       }
       __syncwarp();
@@ -633,9 +645,9 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
         // end (its gamma and xi then sum to w, and c = 1); rows whose last
         // step lies in this range start there instead and take no Y_{t1}.
         if (seg == seg_hi && cont) {
-          const int SX = (t1 - 1) % 2, S1 = t1 % NB;
+          const int SX = (t1 - 1) % XIB, S1 = t1 % NB;
           // the first backward step waits for the same X image phase again
-          fb_wait(&b_x[SX], ph_x[SX], abortp, a.wait_limit);
+          fb_wait(&b_x[SX], (ph_xb >> SX) & 1u, abortp, a.wait_limit);
           wait_e(b_done, ph_done);
           float part = 0.f;
 #pragma unroll
@@ -650,9 +662,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               part = fmaf(xv.x, dv[2 * q], fmaf(xv.y, dv[2 * q + 1], part));
             }
           }
-          psum[((SX & 1) * TPR + h) * 128 + row] = part;
+          // partial sums in the slot of step t1 - 1 (the first backward step
+          // then writes and reads the slot of step t1)
+          const int PS = (t1 - 1) & 1;
+          psum[(PS * TPR + h) * 128 + row] = part;
           tc::bar_sync(1, NEP);
-          const float rho = row_sum(SX & 1);
+          const float rho = row_sum(PS);
           const bool controw = act && T > t1;
           float kappa = controw ? w / rho : 0.f;
           if (!(rho > 0.f) || !isfinite(kappa)) kappa = 0.f;
@@ -686,7 +701,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
           const int S = t % NB;
           const float rho_prev = row_sum((t + 1) & 1);
           if constexpr (L::EMIS) me.emis_sub(bsm, ocur, 0);
-          wait_e(&b_x[t % 2], ph_x[t % 2]);
+          {
+            const int xb = t % XIB;
+            uint32_t px = (ph_xb >> xb) & 1u;
+            wait_e(&b_x[xb], px);
+            ph_xb ^= 1u << xb;
+          }
           // this step's X image is in shared memory now and its copy in memory
           // (checkpoint or recomputed image) is never read again: drop its
           // L2 lines instead of letting them be written back
@@ -717,7 +737,7 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               for (int i = 0; i < SUB; ++i) bt[i] = 1.f;
             }
             uint32_t xw[SUB / 2];
-            me.get(sXI + (t % 2) * IMG, sub, xw);
+            me.get(sXI + (t % XIB) * IMG, sub, xw);
             const float* bb = L::EMIS ? bsm : pf + sub * SUB;
             uint32_t gp[SUB / 2], yp[SUB / 2];
 #pragma unroll

@@ -627,10 +627,12 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             }
             if constexpr (L::EMIS) me.emis_sub(bsm, ot, 0);
             wait_e(b_done, ph_done);
-            if constexpr (!L::EMIS) me.emis_ready(pw, pf);
-            fwd_step(f, act && t < T, scr + (size_t)(t - t0) * IMG);
-            if constexpr (!L::EMIS)
+            if constexpr (!L::EMIS) {
+              me.emis_ready(pw, pf);
+              // the next step's rows, in flight during this epilogue
               if (t + 1 < t1) me.emis_load(pw, on);
+            }
+            fwd_step(f, act && t < T, scr + (size_t)(t - t0) * IMG);
             tc::fence_proxy_async();
             if (t == t1 - 1) tc::fence_proxy_async_all();  // images read by bulk copies
             run = handoff();
@@ -714,7 +716,11 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
             tc::discard_l2((t == t0 ? ckx + (size_t)seg * IMG : scr + (size_t)(t - t0) * IMG) +
                            (size_t)tid * 128);
           if (has_mma) wait_e(b_done, ph_done);
-          if constexpr (!L::EMIS) me.emis_ready(pw, pf);
+          if constexpr (!L::EMIS) {
+            me.emis_ready(pw, pf);
+            // the next step's rows, in flight during this epilogue
+            if (t > t0) me.emis_load(pw, sym_ok(onx));
+          }
           const bool is_init = act && t == T - 1;
           const bool on = act && t < T - 1;
           if (is_init) c = w / s_last;
@@ -776,7 +782,6 @@ __global__ void __launch_bounds__(MmaFbCfg<NP, MB>::NTH, 1) hmm_fb_mma(MmaFbLaun
               onx = sym_raw(t - 2);
               gnx = (int)__ldcg(gexp + (size_t)(t - 2) * 128 + row);
             }
-            if constexpr (!L::EMIS) me.emis_load(pw, ocur);
           }
           tc::fence_proxy_async();
           run = handoff();

@@ -886,7 +886,10 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     f.wait_limit = wait_limit_polls();
     {
       Timed tm(T_FORWARD, st);
-      e = launch_forward_wide(L.NP, f, st);
+      // the state dimension over a cluster of CTAs where its slices fit, else
+      // one CTA per tile with A^T streamed
+      e = forward_cluster_fits(L.NP, dims.M) ? launch_forward_cluster(L.NP, f, st)
+                                              : launch_forward_wide(L.NP, f, st);
       tm.stop();
     }
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");

@@ -532,6 +532,11 @@ struct MmaWideLaunch {
   int64_t rtot;          // rows per model
   uint32_t wait_limit;   // polls before a step's mbarrier wait gives up
 };
+// The forward above 128 states over a cluster of N_pad / 64 CTAs, each with its
+// column slice of A resident (mma_cluster.cu); serves M symbols when its
+// emission slice fits beside them.
+bool forward_cluster_fits(int NP, int M);
+cudaError_t launch_forward_cluster(int NP, const MmaWideLaunch& a, cudaStream_t st);
 // Counts of the adjoint above 128 states from the two passes' rows (fb_wide.cu).
 struct FbWideArgs {
   int K, N, M, NP, S;

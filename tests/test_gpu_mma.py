@@ -84,6 +84,8 @@ WIDE_CASES = [
     ("large", 130, ("uniform", 20, 60), {"K": 2, "N": 256, "M": 300}),
     ("large", 140, ("uniform", 1, 40), {"K": 2, "N": 333, "M": 64}),    # padded to 512
     ("large", 129, ("uniform", 10, 40), {"K": 1, "N": 512, "M": 32}),
+    # emission slice too large for the cluster kernel: the streamed-A^T kernel
+    ("large", 40, ("uniform", 1, 30), {"K": 2, "N": 400, "M": 200}),
 ]
 
 

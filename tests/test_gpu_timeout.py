@@ -25,6 +25,10 @@ CASES = {
     "forward-tf32-n64": ("forward", hmm.HMM_TF32_MMA, ("training", 300, ("uniform", 20, 200), {"K": 2})),
     "forward-bf16-n256": ("forward", hmm.HMM_BF16_MMA,
                           ("large", 130, ("uniform", 10, 60), {"K": 1, "N": 256, "M": 64})),
+    "forward-bf16-n512": ("forward", hmm.HMM_BF16_MMA,
+                          ("large", 130, ("uniform", 10, 60), {"K": 2, "N": 512, "M": 64})),
+    "forward-bf16-n512-m200": ("forward", hmm.HMM_BF16_MMA,
+                               ("large", 40, ("uniform", 10, 40), {"K": 1, "N": 512, "M": 200})),
     "adjoint-bf16-n64": ("adjoint", hmm.HMM_BF16_MMA, ("training", 300, ("uniform", 20, 200), {"K": 2})),
     "adjoint-bf16-n128": ("adjoint", hmm.HMM_BF16_MMA, ("large", 200, ("uniform", 20, 200), {"K": 2})),
 }

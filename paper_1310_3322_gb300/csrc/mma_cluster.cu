@@ -16,8 +16,11 @@
 //     block (core matrices of 8 rows x 16 bytes, 1 KB per 8 rows);
 //   * after its epilogue a CTA writes its slice of the next X into its own X and
 //     sends it, with its 128 partial row sums, to every other CTA of the
-//     cluster by bulk copies into their shared memory, completing on their
-//     `full` mbarrier; the row sums of a step are the sums of the CL partials,
+//     cluster by bulk copies into their shared memory, completing on the
+//     receiver's `full` mbarrier of that sender; the receiver starts the
+//     product over each slice as soon as it lands (its own slice first, then
+//     in the order the senders send), so the products overlap the exchange;
+//     the row sums of a step are the sums of the CL partials,
 //     added in rank order by every CTA alike, so all CTAs keep the same row
 //     state (exponents, log-likelihood);
 //   * a CTA may write a peer's X only after that peer's product has read it: each
@@ -50,8 +53,8 @@ struct ClusterCfg {
   static constexpr int OFF_PX = OFF_B + BB;                 // row sums [2][CL][128]
   static constexpr int OFF_PS = OFF_PX + 2 * CL * 128 * 4;  // partials [TPR][128]
   static constexpr int OFF_PO = OFF_PS + TPR * 128 * 4;     // this CTA's row sums [128]
-  static constexpr int OFF_BAR = OFF_PO + 128 * 4;          // full, free, mma, fin
-  static constexpr int OFF_MISC = OFF_BAR + 4 * 8;          // tmem, abort, done flag, -, row maxima [4]
+  static constexpr int OFF_BAR = OFF_PO + 128 * 4;          // full [CL], free, mma, fin
+  static constexpr int OFF_MISC = OFF_BAR + (CL + 3) * 8;   // tmem, abort, done flag, sent, row maxima [4]
   static constexpr int OFF_E = (OFF_MISC + 32 + 127) / 128 * 128;  // emission slice [M][ES]
   static constexpr int fixed() { return OFF_E; }
   static constexpr int total(int M) { return OFF_E + M * ES; }
@@ -78,10 +81,10 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
   float* psum = reinterpret_cast<float*>(smem + L::OFF_PS); // [TPR][128]
   float* pout = reinterpret_cast<float*>(smem + L::OFF_PO); // [128]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
-  uint64_t* full = bars;       // X slices + row sums of the other CTAs have arrived
-  uint64_t* freeb = bars + 1;  // every other CTA's product has read its X
-  uint64_t* mmab = bars + 2;   // this step's product
-  uint64_t* fin = bars + 3;    // teardown after an abort
+  uint64_t* full = bars;            // [c]: the X slice + row sums of CTA c have arrived
+  uint64_t* freeb = bars + CL;      // every other CTA's product has read its X
+  uint64_t* mmab = bars + CL + 1;   // this step's product
+  uint64_t* fin = bars + CL + 2;    // teardown
   volatile int32_t* misc = reinterpret_cast<volatile int32_t*>(smem + L::OFF_MISC);
   uint8_t* sE = smem + L::OFF_E;
 
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
 
   if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), 64);
   if (tid == 0) {
-    tc::mbar_init(full, 1);
+    for (int c = 0; c < CL; ++c) tc::mbar_init(full + c, 1);
     tc::mbar_init(freeb, CL - 1);
     tc::mbar_init(mmab, 1);
     tc::mbar_init(fin, 1);
@@ -147,8 +150,9 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
   int Tmax = 0;  // alike in every CTA of the cluster
 #pragma unroll
   for (int w = 0; w < 4; ++w) Tmax = max(Tmax, (int)misc[4 + w]);
-  // thread 0: steps sent, phases of `full` armed and seen complete
-  uint32_t n_sent = 0, n_armed = 0, n_done = 0;
+  // thread 0: steps sent; steps whose slices have all been seen, and the
+  // senders whose slice of the step after those has been seen
+  uint32_t n_sent = 0, n_done = 0, got = 0;
   const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
   RowState st;
   st.F = 0; st.f = 0; st.dead = false; st.bad = bad_seq; st.written = (Tn == 0);
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
 #pragma unroll 1
     for (int p = 1; p < CL; ++p) {
       const uint32_t peer = (rank + (uint32_t)p) % (uint32_t)CL;
-      const uint32_t fb = tc::map_rank(tc::smem_u32(full), peer);
+      const uint32_t fb = tc::map_rank(tc::smem_u32(full + rank), peer);
       const uint32_t xs = aX + rank * SLICE;
       tc::bulk_s2peer(tc::map_rank(xs, peer), xs, SLICE, fb);
       const uint32_t ps = tc::smem_u32(px + (par * CL + (int)rank) * 128);
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     for (int c = 0; c < CL; ++c) v += px[(par * CL + c) * 128 + row];
     return v;
   };
-  constexpr uint32_t kFullTx = (uint32_t)(CL - 1) * (SLICE + 128 * 4);
+  constexpr uint32_t kSliceTx = (uint32_t)(SLICE + 128 * 4);
 
   // t = 0: x_0 = pi . b(o_0), no scaling
   if (Tmax > 0) {
@@ -231,31 +235,50 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     }
     put_row(y, part, 0);
     if (tid == 0) {
-      tc::mbar_arrive_expect_tx(full, kFullTx);
-      ++n_armed;
+      for (int c = 0; c < CL; ++c)
+        if (c != (int)rank) tc::mbar_arrive_expect_tx(full + c, kSliceTx);
       send(0);
     }
   }
 
-  uint32_t ph_full = 0, ph_free = 0, ph_mma = 0;  // thread 0's barrier phases
+  uint32_t ph_free = 0, ph_mma = 0;  // thread 0's barrier phases
   bool aborted = false;
   int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
-  for (int t = 1; t < Tmax; ++t) {
-    // X_{t-1} and its row sums are complete here: the product of step t
+  // step t: the product X_{t-1} . A and the epilogue writing X_t; at t = Tmax
+  // only the row sums of the last step
+  for (int t = 1; t <= Tmax; ++t) {
+    const bool last = t == Tmax;
+    const int ot = o_next;  // the emission row of step t does not wait for X_{t-1}
+    if (t + 1 < Tn) o_next = __ldg(o + t + 1);
+    float b[16];
+    emis16((unsigned)ot < (unsigned)M ? ot : 0, b);
     bool ok = true;
     if (tid == 0) {
-      ok = tc::mbar_wait_cluster(full, ph_full, a.wait_limit);
-      if (ok) {
-        ph_full ^= 1;
-        ++n_done;
-        tc::mbar_arrive_expect_tx(full, kFullTx);  // the exchange of X_t
-        ++n_armed;
-        tc::fence_after_sync();
+      const uint32_t par = (uint32_t)(t - 1) & 1u;
+#pragma unroll 1
+      for (int j = 0; j < CL; ++j) {
+        const int c = (int)((rank + (uint32_t)(CL - j)) % (uint32_t)CL);  // own slice first
+        if (j > 0) {
+          if (!tc::mbar_wait_cluster(full + c, par, a.wait_limit)) {
+            ok = false;
+            break;
+          }
+          got |= 1u << c;
+          if (!last) tc::mbar_arrive_expect_tx(full + c, kSliceTx);  // the exchange of X_t
+        }
+        if (!last) {
+          tc::fence_after_sync();
 #pragma unroll
-        for (int ks = 0; ks < NP / 16; ++ks)
-          tc::mma_bf16(tmem, tc::smem_desc(aX + (ks >> 2) * SLICE + (ks & 3) * 256, 128, 1024),
-                       tc::smem_desc(aB + ks * 256, 128, NP * 16), idesc, ks > 0 ? 1u : 0u);
-        tc::mma_commit(mmab);
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_bf16(tmem, tc::smem_desc(aX + c * SLICE + kk * 256, 128, 1024),
+                         tc::smem_desc(aB + (4 * c + kk) * 256, 128, NP * 16), idesc,
+                         (j | kk) ? 1u : 0u);
+        }
+      }
+      if (ok) {
+        ++n_done;
+        got = 0;
+        if (!last) tc::mma_commit(mmab);
       }
     }
     if (!tc::bar_and(1, L::NTH, ok)) {
@@ -263,14 +286,11 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
       break;
     }
     close_step(st, row_total((t - 1) & 1), t - 1, Tn);
-    const int ot = o_next;
-    if (t + 1 < Tn) o_next = __ldg(o + t + 1);
+    if (last) break;
     if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
     const bool live = t < Tn && !st.dead && !st.bad;
     if (live) st.F += st.f;
     const float2 fac2 = make_float2(exp2i(-st.f), exp2i(-st.f));
-    float b[16];
-    emis16((unsigned)ot < (unsigned)M ? ot : 0, b);
     // the product is done: this CTA's X may be rewritten by the others; wait
     // until every other CTA's product is done too (then the own slice and the
     // row sums may be rewritten and sent)
@@ -306,19 +326,6 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     }
     put_row(y, acc.x + acc.y, t & 1);
     if (tid == 0) send(t & 1);
-  }
-  // the last step's row sums
-  if (!aborted && Tmax > 0) {
-    bool ok = true;
-    if (tid == 0) {
-      ok = tc::mbar_wait_cluster(full, ph_full, a.wait_limit);
-      if (ok) {
-        ph_full ^= 1;
-        ++n_done;
-      }
-    }
-    if (!tc::bar_and(1, L::NTH, ok)) aborted = true;
-    else close_step(st, row_total((Tmax - 1) & 1), Tmax - 1, Tn);
   }
   if (aborted && tid == 0) {
     misc[1] = 1;
@@ -356,29 +363,20 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     }
   }
 
-  // teardown. After the first cluster barrier no CTA sends; a peer that sent
-  // n steps sent the copies of phases 0 .. n-1 of our `full` (the counts of
-  // two CTAs differ by one at most), of which we have seen n_done complete.
+  // teardown. After the first cluster barrier no CTA sends. A peer that sent
+  // n steps sent its slices of X_0 .. X_{n-1}; the counts of two CTAs differ
+  // by one at most, and we have seen the peer's slices up to X_{seen - 1}:
+  // wait (bounded) for the one that may still be on its way.
   if (tid == 0) misc[3] = (int32_t)n_sent;
   tc::cluster_sync();
   if (tid == 0) {
-    uint32_t ns[L::CL];
-#pragma unroll
-    for (int p = 0; p < CL; ++p)
-      ns[p] = p == (int)rank ? 0u
-                             : tc::ld_cluster_u32(tc::map_rank(tc::smem_u32(smem + L::OFF_MISC + 12), (uint32_t)p));
-    uint32_t smax = 0;
-#pragma unroll
-    for (int p = 0; p < CL; ++p) smax = max(smax, ns[p]);
 #pragma unroll 1
-    for (uint32_t ph = n_done; ph < smax; ++ph) {
-      uint32_t senders = 0;
-#pragma unroll
-      for (int p = 0; p < CL; ++p) senders += ns[p] > ph ? 1u : 0u;
-      const uint32_t bytes = senders * (uint32_t)(SLICE + 128 * 4);
-      if (ph >= n_armed) tc::mbar_arrive_expect_tx(full, bytes);
-      else if (bytes < kFullTx) tc::mbar_complete_tx(full, kFullTx - bytes);  // armed for all
-      tc::mbar_wait_cluster(full, ph & 1u, kClusterDrain);
+    for (int c = 0; c < CL; ++c) {
+      if (c == (int)rank) continue;
+      const uint32_t ns = tc::ld_cluster_u32(tc::map_rank(tc::smem_u32(smem + L::OFF_MISC + 12),
+                                                          (uint32_t)c));
+      const uint32_t seen = n_done + ((got >> c) & 1u);
+      if (ns > seen) tc::mbar_wait_cluster(full + c, seen & 1u, kClusterDrain);
     }
     tc::mma_commit(fin);  // arrives once every product issued so far is done
     tc::mbar_wait_bounded(fin, 0, kClusterDrain);

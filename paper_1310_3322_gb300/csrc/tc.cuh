@@ -105,12 +105,6 @@ __device__ __forceinline__ void mbar_arrive_remote(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
                : "memory");
 }
-// Removes `bytes` of expected transactions from the current phase of an
-// mbarrier of this CTA (for copies that will never be sent).
-__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
 // A 32-bit load from the shared memory of a CTA of the cluster.
 __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr_cluster) {
   uint32_t v;

@@ -576,7 +576,8 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   b.loglik = nullptr;
   {
     Timed tm(T_FB, st);
-    e = launch_wide_passes(NP, f, b, st);
+    e = forward_cluster_fits(NP, dims.M) ? launch_cluster_passes(NP, f, b, st)
+                                         : launch_wide_passes(NP, f, b, st);
     tm.stop();
   }
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward/backward launch");

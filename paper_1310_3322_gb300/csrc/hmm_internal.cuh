@@ -537,6 +537,10 @@ struct MmaWideLaunch {
 // emission slice fits beside them.
 bool forward_cluster_fits(int NP, int M);
 cudaError_t launch_forward_cluster(int NP, const MmaWideLaunch& a, cudaStream_t st);
+// Both passes of the adjoint above 128 states on clusters (rows kept in f.xs,
+// b.xs and b.xe like launch_wide_passes), when forward_cluster_fits.
+cudaError_t launch_cluster_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
+                                  cudaStream_t st);
 // Counts of the adjoint above 128 states from the two passes' rows (fb_wide.cu).
 struct FbWideArgs {
   int K, N, M, NP, S;

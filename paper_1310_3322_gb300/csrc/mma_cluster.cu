@@ -70,8 +70,20 @@ __device__ __forceinline__ uint32_t xs_off(int m, int k) {
                     (m & 7) * 16 + (k & 7) * 2);
 }
 
-template <int NP>
-__global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_constant__ MmaWideLaunch a) {
+// One 32-byte store (256-bit vector store, sm_100+).
+__device__ __forceinline__ void st_v8c(float* p, const float* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               :: "l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]),
+                  "f"(v[6]), "f"(v[7]) : "memory");
+}
+
+// The work of one cluster: item `item` of `a`. DIR = 1 runs the backward
+// recursion Y_t = (Y_{t+1} A^T) o b(o_t) from Y_{T-1} = b(o_{T-1}) (the
+// forward recursion with A^T in place of A); STORE keeps every step's row
+// (forward: scaled alpha_t; backward: scaled beta_t before the emission
+// product, with its exponent) for the adjoint's count kernels.
+template <int NP, int DIR, bool STORE>
+__device__ __forceinline__ void cluster_body(const MmaWideLaunch& a, int item) {
   using L = ClusterCfg<NP>;
   constexpr int CL = L::CL, SLICE = L::SLICE;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -94,7 +106,6 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
   const uint32_t rank = tc::cluster_rank();
   const int c0 = 64 * (int)rank;            // this CTA's first state
   const int K = a.seq.K, M = a.seq.M, S = a.seq.S;
-  const int item = (int)(blockIdx.x / CL);
   const int tile = item / K, k = item % K;
 
   if (warp == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(smem + L::OFF_MISC), 64);
@@ -106,13 +117,15 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     misc[1] = 0;
   }
-  // the model's column slice of A (B operand, K-major: (n = j - c0, k = i) = a_ij)
+  // the model's column slice of A (B operand, K-major: (n = j - c0, k = i) =
+  // a_ij; backward: a_ji)
   {
     const float* Ak = a.mod.Ap + (size_t)k * NP * NP;
     for (int idx = tid; idx < 64 * NP / 2; idx += L::NTH) {
       const int n = idx / (NP / 2), i = (idx % (NP / 2)) * 2;
-      const uint32_t w = tc::pack_bf16(__ldg(Ak + (size_t)i * NP + c0 + n),
-                                       __ldg(Ak + (size_t)(i + 1) * NP + c0 + n));
+      const uint32_t w =
+          DIR ? tc::pack_bf16(__ldg(Ak + (size_t)(c0 + n) * NP + i), __ldg(Ak + (size_t)(c0 + n) * NP + i + 1))
+              : tc::pack_bf16(__ldg(Ak + (size_t)i * NP + c0 + n), __ldg(Ak + (size_t)(i + 1) * NP + c0 + n));
       *reinterpret_cast<uint32_t*>(sB + (n >> 3) * (NP * 16) + (i >> 3) * 128 + (n & 7) * 16 +
                                    (i & 7) * 2) = w;
     }
@@ -154,6 +167,13 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
   // senders whose slice of the step after those has been seen
   uint32_t n_sent = 0, n_done = 0, got = 0;
   const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
+  // step t reads symbol o_t (forward) or o_{T-1-t} (backward)
+  auto tix = [&](int t) { return DIR ? Tn - 1 - t : t; };
+  // this thread's 16 columns of the row's per-step output rows
+  float* xrow = (STORE && has && !bad_seq)
+                    ? a.xs + ((size_t)k * a.rtot + (size_t)a.roff[s]) * NP + c0 + 16 * h : nullptr;
+  int32_t* xerow = (STORE && DIR && has && !bad_seq && rank == 0 && h == 0)
+                       ? a.xe + (size_t)k * a.rtot + (size_t)a.roff[s] : nullptr;
   RowState st;
   st.F = 0; st.f = 0; st.dead = false; st.bad = bad_seq; st.written = (Tn == 0);
   st.err = 0; st.ll = 0.f; st.slast = 0.f;
@@ -215,9 +235,9 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
   };
   constexpr uint32_t kSliceTx = (uint32_t)(SLICE + 128 * 4);
 
-  // t = 0: x_0 = pi . b(o_0), no scaling
+  // t = 0: x_0 = pi . b(o_0) (backward: Y_{T-1} = b(o_{T-1}), beta = 1), no scaling
   if (Tmax > 0) {
-    int o0 = Tn > 0 ? __ldg(o) : 0;
+    int o0 = Tn > 0 ? __ldg(o + tix(0)) : 0;
     if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
     const bool live = Tn > 0 && !st.bad;
     float b[16], y[16];
@@ -226,13 +246,21 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     float part = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float4 pp = __ldg(p4 + q);
+      const float4 pp = DIR ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(p4 + q);
       y[4 * q] = live ? pp.x * b[4 * q] : 0.f;
       y[4 * q + 1] = live ? pp.y * b[4 * q + 1] : 0.f;
       y[4 * q + 2] = live ? pp.z * b[4 * q + 2] : 0.f;
       y[4 * q + 3] = live ? pp.w * b[4 * q + 3] : 0.f;
       part += (y[4 * q] + y[4 * q + 1]) + (y[4 * q + 2] + y[4 * q + 3]);
     }
+    if (STORE && xrow && Tn > 0) {
+      float sv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) sv[i] = DIR ? (live ? 1.f : 0.f) : y[i];
+      st_v8c(xrow + (size_t)tix(0) * NP, sv);
+      st_v8c(xrow + (size_t)tix(0) * NP + 8, sv + 8);
+    }
+    if (xerow && Tn > 0) xerow[tix(0)] = 0;
     put_row(y, part, 0);
     if (tid == 0) {
       for (int c = 0; c < CL; ++c)
@@ -243,13 +271,13 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
 
   uint32_t ph_free = 0, ph_mma = 0;  // thread 0's barrier phases
   bool aborted = false;
-  int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
+  int o_next = (1 < Tn) ? __ldg(o + tix(1)) : 0;
   // step t: the product X_{t-1} . A and the epilogue writing X_t; at t = Tmax
   // only the row sums of the last step
   for (int t = 1; t <= Tmax; ++t) {
     const bool last = t == Tmax;
     const int ot = o_next;  // the emission row of step t does not wait for X_{t-1}
-    if (t + 1 < Tn) o_next = __ldg(o + t + 1);
+    if (t + 1 < Tn) o_next = __ldg(o + tix(t + 1));
     float b[16];
     emis16((unsigned)ot < (unsigned)M ? ot : 0, b);
     bool ok = true;
@@ -315,15 +343,32 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     tc::tmem_ld_wait();
     tc::fence_before_sync();  // the next product may overwrite the accumulator
     float2 acc = make_float2(0.f, 0.f);
+    float sv[16];  // the stored row: alpha_t (forward) or beta_t (backward)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      float2 v = __fmul2_rn(__fmul2_rn(make_float2(y[2 * q], y[2 * q + 1]),
-                                       make_float2(b[2 * q], b[2 * q + 1])), fac2);
-      if (!live) v = make_float2(0.f, 0.f);
+      float2 v;
+      if constexpr (DIR == 0) {
+        v = __fmul2_rn(__fmul2_rn(make_float2(y[2 * q], y[2 * q + 1]),
+                                  make_float2(b[2 * q], b[2 * q + 1])), fac2);
+        if (!live) v = make_float2(0.f, 0.f);
+        sv[2 * q] = v.x;
+        sv[2 * q + 1] = v.y;
+      } else {  // beta_t = D 2^-f kept, Y_t = beta_t o b(o_t) is the next operand
+        float2 p = __fmul2_rn(make_float2(y[2 * q], y[2 * q + 1]), fac2);
+        if (!live) p = make_float2(0.f, 0.f);
+        sv[2 * q] = p.x;
+        sv[2 * q + 1] = p.y;
+        v = __fmul2_rn(p, make_float2(b[2 * q], b[2 * q + 1]));
+      }
       acc = __fadd2_rn(acc, v);
       y[2 * q] = v.x;
       y[2 * q + 1] = v.y;
     }
+    if (STORE && xrow && t < Tn) {
+      st_v8c(xrow + (size_t)tix(t) * NP, sv);
+      st_v8c(xrow + (size_t)tix(t) * NP + 8, sv + 8);
+    }
+    if (xerow && t < Tn) xerow[tix(t)] = live ? st.f : 0;
     put_row(y, acc.x + acc.y, t & 1);
     if (tid == 0) send(t & 1);
   }
@@ -331,7 +376,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     misc[1] = 1;
     set_status(a.status, HMM_STATUS_TIMEOUT);
   }
-  if (rank == 0 && has && h == 0) {
+  if (DIR == 0 && rank == 0 && has && h == 0) {
     float out = st.ll;
     if (st.bad || aborted) out = __int_as_float(0x7fc00000);
     else if (st.dead) out = -INFINITY;
@@ -340,7 +385,7 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
     a.loglik[(size_t)s * K + k] = out;
   }
   // recognition: the last model of a tile takes the argmax over models
-  if (rank == 0 && a.argmax) {
+  if (DIR == 0 && rank == 0 && a.argmax) {
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -388,15 +433,32 @@ __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_const
   tc::cluster_sync();  // no CTA leaves while a peer may still read its counts
 }
 
+// Recognition: the forward recursion alone, one item per cluster.
 template <int NP>
-static cudaError_t launch_cluster_t(const MmaWideLaunch& a, cudaStream_t st) {
+__global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_constant__ MmaWideLaunch a) {
+  cluster_body<NP, 0, false>(a, (int)(blockIdx.x / ClusterCfg<NP>::CL));
+}
+
+// Both passes of the adjoint in one launch (they are independent): clusters
+// [0, nf) take the forward items of f, the others the backward items of b.
+template <int NP>
+__global__ void __launch_bounds__(512, 1)
+hmm_cluster_passes(const __grid_constant__ MmaWideLaunch f, const __grid_constant__ MmaWideLaunch b,
+                   int nf) {
+  const int c = (int)(blockIdx.x / ClusterCfg<NP>::CL);
+  if (c < nf) cluster_body<NP, 0, true>(f, c);
+  else cluster_body<NP, 1, true>(b, c - nf);
+}
+
+// Clusters of CL CTAs, one CTA per SM (the shared memory takes it all).
+template <int NP, typename Kern, typename... Args>
+static cudaError_t launch_clusters(Kern kern, int n_clusters, int M, cudaStream_t st, Args... args) {
   using L = ClusterCfg<NP>;
-  auto kern = hmm_forward_cluster<NP>;
-  const int smem = L::total(a.seq.M);
+  const int smem = L::total(M);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(a.n_items * L::CL), 1, 1);
+  cfg.gridDim = dim3((unsigned)(n_clusters * L::CL), 1, 1);
   cfg.blockDim = dim3(L::NTH, 1, 1);
   cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = st;
@@ -407,7 +469,7 @@ static cudaError_t launch_cluster_t(const MmaWideLaunch& a, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, a);
+  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // Whether the cluster forward serves N_pad = NP with M symbols (its emission
@@ -420,8 +482,18 @@ bool forward_cluster_fits(int NP, int M) {
 
 cudaError_t launch_forward_cluster(int NP, const MmaWideLaunch& a, cudaStream_t st) {
   if (a.xs || a.n_items < 1) return cudaErrorInvalidValue;
-  if (NP == 256) return launch_cluster_t<256>(a, st);
-  if (NP == 512) return launch_cluster_t<512>(a, st);
+  if (NP == 256) return launch_clusters<256>(hmm_forward_cluster<256>, a.n_items, a.seq.M, st, a);
+  if (NP == 512) return launch_clusters<512>(hmm_forward_cluster<512>, a.n_items, a.seq.M, st, a);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cluster_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
+                                  cudaStream_t st) {
+  if (!f.xs || !b.xs || !b.xe || !f.roff || f.n_items < 1 || b.n_items != f.n_items)
+    return cudaErrorInvalidValue;
+  const int n = f.n_items + b.n_items;
+  if (NP == 256) return launch_clusters<256>(hmm_cluster_passes<256>, n, f.seq.M, st, f, b, f.n_items);
+  if (NP == 512) return launch_clusters<512>(hmm_cluster_passes<512>, n, f.seq.M, st, f, b, f.n_items);
   return cudaErrorInvalidValue;
 }
 

@@ -255,8 +255,6 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     const int64_t slots = d.K;
     L.w_rtot = rtot;
     L.bpoff = off; off = align256(off + S * 8);
-    L.wimg = off; off = align256(off + (size_t)d.K * NP * NP * 2);
-    L.w_img2 = off; off = align256(off + (size_t)d.K * NP * NP * 2);
     const size_t rowb = (size_t)(slots * rtot) * NP * 4;
     L.w_X = off; off = align256(off + rowb);
     L.w_Bh = off; off = align256(off + rowb);
@@ -531,7 +529,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
                 "above 128 states the adjoint scores every sequence against every model "
                 "(model_of_seq only with K = 1)");
   const int NP = pad_states(dims.N);
-  if (fbw_emis_smem(NP, dims.M) > 227 * 1024)
+  if (fbw_emis_smem(NP, dims.M) > 227 * 1024 || !forward_cluster_fits(NP, dims.M))
     return fail(HMM_ERR_UNSUPPORTED, "adjoint above 128 states: M=%d too large", dims.M);
   const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD, true);
   int rc = check_ws(ws, ws_bytes, L);
@@ -556,7 +554,6 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   memset(&f, 0, sizeof(f));
   f.seq = seq_args(dims, *seqs, L, ws);
   f.mod = model_args(L, ws);
-  f.img = at<uint8_t>(ws, L.wimg);
   f.loglik = loglik;
   f.done = at<int32_t>(ws, L.done);
   f.queue = &at<WsHeader>(ws, 0)->queue[0];
@@ -567,17 +564,14 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   f.roff = at<int64_t>(ws, L.bpoff);
   f.rtot = L.w_rtot;
   f.wait_limit = wait_limit_polls();
-  // the backward pass: own queue, A image and row buffers
+  // the backward pass: own row buffers
   MmaWideLaunch b = f;
-  b.queue = &at<WsHeader>(ws, 0)->queue[1];
-  b.img = at<uint8_t>(ws, L.w_img2);
   b.xs = at<float>(ws, L.w_Bh);
   b.xe = at<int32_t>(ws, L.w_xe);
   b.loglik = nullptr;
   {
     Timed tm(T_FB, st);
-    e = forward_cluster_fits(NP, dims.M) ? launch_cluster_passes(NP, f, b, st)
-                                         : launch_wide_passes(NP, f, b, st);
+    e = launch_cluster_passes(NP, f, b, st);
     tm.stop();
   }
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward/backward launch");

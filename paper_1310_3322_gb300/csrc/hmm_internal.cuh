@@ -43,7 +43,6 @@ struct WsLayout {
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
   size_t sc_coff, sc_P, sc_E;  // parallel-in-time forward: chunk offsets, products
   size_t w_X, w_Bh, w_V, w_G, w_xe, w_sym, w_Cp, w_Ep, w_Pp;  // adjoint above 128 states
-  size_t w_img2;                                              // its backward pass's A image
   int w_nsplit, w_nchunks;
   int64_t w_rtot;
   int64_t sc_cap;              // chunk slots per model slot
@@ -537,8 +536,10 @@ struct MmaWideLaunch {
 // emission slice fits beside them.
 bool forward_cluster_fits(int NP, int M);
 cudaError_t launch_forward_cluster(int NP, const MmaWideLaunch& a, cudaStream_t st);
-// Both passes of the adjoint above 128 states on clusters (rows kept in f.xs,
-// b.xs and b.xe like launch_wide_passes), when forward_cluster_fits.
+// Both passes of the adjoint above 128 states on clusters, in one launch:
+// clusters [0, f.n_items) the forward items of f (rows alpha_t kept in f.xs),
+// the others the backward items of b (rows beta_t in b.xs, their exponents in
+// b.xe); needs forward_cluster_fits.
 cudaError_t launch_cluster_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
                                   cudaStream_t st);
 // Counts of the adjoint above 128 states from the two passes' rows (fb_wide.cu).
@@ -573,12 +574,9 @@ struct FbWideArgs {
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st);
 size_t fbw_emis_smem(int NP, int M);
 
-// The recognition forward (loglik, argmax; dir must be 0 and xs NULL).
-cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st, int dir = 0);
-// the forward (f) and backward (b) passes of the adjoint in one launch, on
-// disjoint halves of the SMs (separate queues, images and row buffers)
-cudaError_t launch_wide_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
-                               cudaStream_t st);
+// The recognition forward above 128 states with A^T streamed, one CTA per
+// tile (loglik, argmax; xs NULL): where the cluster kernel has no room.
+cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st);
 
 // Plan of the tensor-core adjoint: the rows of every 128-row tile share one
 // model, and the tile composition is a deterministic function of the input

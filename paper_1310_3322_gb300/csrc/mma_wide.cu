@@ -22,16 +22,9 @@
 // Every mbarrier wait is bounded; on timeout the kernel records
 // HMM_STATUS_TIMEOUT, waits (bounded) for its own copies and MMAs and leaves.
 //
-// The adjoint above 128 states (Baum-Welch E-step, Rabiner eqs. 24-25) uses
-// the same recursion twice: with Y_t = b(o_t) o beta_t the backward recursion
-// reads Y_t = (Y_{t+1} A^T) o b(o_t), i.e. the forward recursion with A^T in
-// place of A (the image built from A, `transpose`), run from t = T-1 down to
-// 0 from Y_{T-1} = b(o_{T-1}). DIR = 1 selects that direction, and both
-// directions store every step's rescaled row (forward: alpha_t; backward:
-// beta_t before the emission product, with its exponent) for the count
-// kernels of fb_wide.cu. `hmm_wide_passes` runs the two directions side by
-// side in one launch, half of the CTAs each, with separate queues, images and
-// row buffers.
+// This kernel serves the forward when the cluster kernel of mma_cluster.cu
+// (one CTA per 64 columns, A resident) has no room for the emission table
+// slice, i.e. N_pad = 512 with more than 173 symbols.
 #include "hmm_internal.cuh"
 #include "mma_rows.cuh"
 #include "tc.cuh"
@@ -62,21 +55,12 @@ struct WideCfg {
 
 constexpr uint32_t kWideWait = 1u << 24;  // polls of the teardown's drain waits
 
-// One 32-byte store (256-bit vector store, sm_100+): a full sector per lane.
-__device__ __forceinline__ void st_v8(float* p, float4 a, float4 b) {
-  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-               :: "l"(p), "f"(a.x), "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z),
-                  "f"(b.w) : "memory");
-}
-
 // BF16 image of A^T per model, chunk-major: chunk kc holds states i in
 // [32 kc, 32 kc + 32) for every j, element (n = j, k = i) = a_ij at
 //   (j / 8) * 512 + (il / 8) * 128 + (j % 8) * 16 + (il % 8) * 2,  il = i - 32 kc
 // (K-major core matrices of 8 rows x 16 bytes; 512 = 32 K values x 16 bytes).
-// `transpose` builds the image of A instead (element (n = j, k = i) = a_ji),
-// the operand of the backward recursion.
 template <int NP>
-__global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K, int transpose) {
+__global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K) {
   const long long n = (long long)K * NP * NP / 2;  // pairs along i
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -87,16 +71,14 @@ __global__ void wide_image_kernel(const float* Ap, uint8_t* img, int K, int tran
     const int kc = i / 32, il = i % 32;
     const size_t off = (size_t)k * NP * NP * 2 + (size_t)kc * WideCfg<NP>::CHUNK +
                        (size_t)(j / 8) * 512 + (il / 8) * 128 + (j % 8) * 16 + (il % 8) * 2;
-    const float v0 = transpose ? Ak[(size_t)j * NP + i] : Ak[(size_t)i * NP + j];
-    const float v1 = transpose ? Ak[(size_t)j * NP + i + 1] : Ak[(size_t)(i + 1) * NP + j];
+    const float v0 = Ak[(size_t)i * NP + j];
+    const float v1 = Ak[(size_t)(i + 1) * NP + j];
     *reinterpret_cast<uint32_t*>(img + off) = tc::pack_bf16(v0, v1);
   }
 }
 
 // The work of one CTA (all of it: items come from a.queue until it runs dry).
-// STORE: keep every step's row in a.xs (the adjoint); recognition compiles
-// without the store path.
-template <int NP, int DIR, bool STORE>
+template <int NP>
 __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
   using L = WideCfg<NP>;
   constexpr int COLS = L::COLS, CH = L::CH, NKC = L::NKC, RING = L::RING;
@@ -161,11 +143,6 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
     const float* Bk = a.mod.Btp + (size_t)k * M * NP;
     const uint8_t* img = a.img + (size_t)k * NP * NP * 2;
     const int32_t* o = a.seq.symbols + (has && !bad_seq ? a.seq.offsets[s] : 0);
-    // step t reads symbol o_t (forward) or o_{T-1-t} (backward)
-    auto tix = [&](int t) { return DIR ? Tn - 1 - t : t; };
-    // this row's per-step output rows (adjoint above 128 states)
-    float* xrow = (STORE && has && !bad_seq)
-                      ? a.xs + ((size_t)k * a.rtot + (size_t)a.roff[s]) * NP + col0 : nullptr;
     RowState st;
     st.F = 0; st.f = 0; st.dead = false; st.bad = bad_seq; st.written = (Tn == 0);
     st.err = 0; st.ll = 0.f;
@@ -180,9 +157,9 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
       }
     }
 
-    // t = 0: x_0 = pi . b(o_0) (backward: Y_{T-1} = b(o_{T-1}), beta = 1), no scaling
+    // t = 0: x_0 = pi . b(o_0), no scaling
     {
-      int o0 = Tn > 0 ? __ldg(o + tix(0)) : 0;
+      int o0 = Tn > 0 ? __ldg(o) : 0;
       if ((unsigned)o0 >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; o0 = 0; }
       const bool live = Tn > 0 && !st.bad;
       const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)o0 * NP + col0);
@@ -194,15 +171,9 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const float4 bb = __ldg(b4 + 8 * c + q);
-          const float4 pp = DIR ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(p4 + 8 * c + q);
+          const float4 pp = __ldg(p4 + 8 * c + q);
           y[4 * q] = live ? pp.x * bb.x : 0.f; y[4 * q + 1] = live ? pp.y * bb.y : 0.f;
           y[4 * q + 2] = live ? pp.z * bb.z : 0.f; y[4 * q + 3] = live ? pp.w * bb.w : 0.f;
-          if (STORE && xrow && Tn > 0) {
-            const float4 sv = DIR ? make_float4(live ? 1.f : 0.f, live ? 1.f : 0.f,
-                                                live ? 1.f : 0.f, live ? 1.f : 0.f)
-                                  : make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-            *reinterpret_cast<float4*>(xrow + (size_t)tix(0) * NP + 32 * c + 4 * q) = sv;
-          }
         }
         part += tree_sum<32>(y);
         uint32_t w[16];
@@ -213,11 +184,9 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
               make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
       }
       psum[h * 128 + row] = part;
-      if (STORE && DIR && xrow && Tn > 0 && h == 0)
-        a.xe[(size_t)k * a.rtot + a.roff[s] + tix(0)] = 0;
     }
-    int o_next = (1 < Tn) ? __ldg(o + tix(1)) : 0;
-    int o_next2 = (2 < Tn) ? __ldg(o + tix(2)) : 0;
+    int o_next = (1 < Tn) ? __ldg(o + 1) : 0;
+    int o_next2 = (2 < Tn) ? __ldg(o + 2) : 0;
 
     bool aborted = false;
     int g = 0;  // chunk counter of this item
@@ -263,7 +232,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
       close_step(st, psum[row] + psum[128 + row] + psum[256 + row] + psum[384 + row], t - 1, Tn);
       const int ot = o_next;
       o_next = o_next2;
-      if (t + 2 < Tn) o_next2 = __ldg(o + tix(t + 2));
+      if (t + 2 < Tn) o_next2 = __ldg(o + t + 2);
       if (t < Tn && (unsigned)ot >= (unsigned)M) { st.bad = true; st.err |= HMM_STATUS_SYMBOL; }
       const bool live = t < Tn && !st.dead && !st.bad;
       if (live) st.F += st.f;
@@ -293,35 +262,13 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
         tc::tmem_ld32(d_mine + (uint32_t)(c * 32), y);
         tc::tmem_ld_wait();
         float2 acc = make_float2(0.f, 0.f);
-        // (32-byte aligned: rows of NP floats, 32-column chunks)
-        float* xdst = (STORE && xrow && t < Tn) ? xrow + (size_t)tix(t) * NP + 32 * c : nullptr;
-        float4 held = make_float4(0.f, 0.f, 0.f, 0.f);  // the even group, stored with the odd
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          float2 lo, hi;
-          float4 sv;
-          if constexpr (DIR == 0) {
-            lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
-                                       make_float2(bq[q].x, bq[q].y)), fac2);
-            hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
-                                       make_float2(bq[q].z, bq[q].w)), fac2);
-            if (!live) { lo = make_float2(0.f, 0.f); hi = lo; }
-            sv = make_float4(lo.x, lo.y, hi.x, hi.y);
-          } else {  // beta_t = D 2^-f kept, Y_t = beta_t o b(o_t) is the next operand
-            float2 plo = __fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]), fac2);
-            float2 phi = __fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]), fac2);
-            if (!live) { plo = make_float2(0.f, 0.f); phi = plo; }
-            sv = make_float4(plo.x, plo.y, phi.x, phi.y);
-            lo = __fmul2_rn(plo, make_float2(bq[q].x, bq[q].y));
-            hi = __fmul2_rn(phi, make_float2(bq[q].z, bq[q].w));
-          }
-          if constexpr (STORE) {
-            if (q & 1) {
-              if (xdst) st_v8(xdst + 4 * (q - 1), held, sv);
-            } else {
-              held = sv;
-            }
-          }
+          float2 lo = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q], y[4 * q + 1]),
+                                            make_float2(bq[q].x, bq[q].y)), fac2);
+          float2 hi = __fmul2_rn(__fmul2_rn(make_float2(y[4 * q + 2], y[4 * q + 3]),
+                                            make_float2(bq[q].z, bq[q].w)), fac2);
+          if (!live) { lo = make_float2(0.f, 0.f); hi = lo; }
           acc = __fadd2_rn(acc, __fadd2_rn(lo, hi));
           y[4 * q] = lo.x; y[4 * q + 1] = lo.y; y[4 * q + 2] = hi.x; y[4 * q + 3] = hi.y;
         }
@@ -337,8 +284,6 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
           for (int q = 0; q < 8; ++q) bq[q] = bn[q];
       }
       psum[h * 128 + row] = part;
-      if (STORE && DIR && xrow && t < Tn && h == 0)
-        a.xe[(size_t)k * a.rtot + a.roff[s] + tix(t)] = live ? st.f : 0;
     }
     if (tid == 0 && !abort_issue) {  // the last chunk's commit (its MMAs are done by now)
       for (int i = 0; i < RING; ++i)
@@ -356,7 +301,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
       misc[2] = 1;
       set_status(a.status, HMM_STATUS_TIMEOUT);
     }
-    if (DIR == 0 && has && h == 0) {
+    if (has && h == 0) {
       float out = st.ll;
       if (st.bad || aborted) out = __int_as_float(0x7fc00000);
       else if (st.dead) out = -INFINITY;
@@ -365,7 +310,7 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
       a.loglik[(size_t)s * K + k] = out;
     }
     // recognition: the last model of a tile takes the argmax over models
-    if (DIR == 0 && a.argmax) {
+    if (a.argmax) {
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -404,62 +349,23 @@ __device__ __forceinline__ void wide_body(const MmaWideLaunch& a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// Recognition: the forward recursion alone (no row stores).
 template <int NP>
 __global__ void __launch_bounds__(512, 1) hmm_forward_wide(const __grid_constant__ MmaWideLaunch a) {
-  wide_body<NP, 0, false>(a);
-}
-
-// Both passes of the adjoint in one launch (they are independent): CTAs
-// [0, nf) take the forward items of f, the others the backward items of b,
-// each side with its own queue, A image and row buffers.
-template <int NP>
-__global__ void __launch_bounds__(512, 1)
-hmm_wide_passes(const __grid_constant__ MmaWideLaunch f, const __grid_constant__ MmaWideLaunch b,
-                int nf) {
-  if ((int)blockIdx.x < nf) wide_body<NP, 0, true>(f);
-  else wide_body<NP, 1, true>(b);
+  wide_body<NP>(a);
 }
 
 template <int NP>
-static cudaError_t build_wide_image(const MmaWideLaunch& a, int dir, cudaStream_t st) {
+static cudaError_t build_wide_image(const MmaWideLaunch& a, cudaStream_t st) {
   const long long n = (long long)a.seq.K * NP * NP / 2;
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  wide_image_kernel<NP><<<blocks, 256, 0, st>>>(a.mod.Ap, a.img, a.seq.K, dir);
+  wide_image_kernel<NP><<<blocks, 256, 0, st>>>(a.mod.Ap, a.img, a.seq.K);
   return cudaGetLastError();
-}
-
-template <int NP>
-static cudaError_t launch_passes_t(const MmaWideLaunch& f, const MmaWideLaunch& b,
-                                   cudaStream_t st) {
-  using L = WideCfg<NP>;
-  cudaError_t e;
-  if ((e = build_wide_image<NP>(f, 0, st)) != cudaSuccess) return e;
-  if ((e = build_wide_image<NP>(b, 1, st)) != cudaSuccess) return e;
-  auto kern = hmm_wide_passes<NP>;
-  const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;  // one CTA per SM
-  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-      cudaSuccess)
-    return e;
-  const int half = num_sms() / 2 > 0 ? num_sms() / 2 : 1;
-  const int nf = f.n_items < half ? (f.n_items > 0 ? f.n_items : 1) : half;
-  const int nb = b.n_items < half ? (b.n_items > 0 ? b.n_items : 1) : half;
-  kern<<<nf + nb, L::NTH, smem, st>>>(f, b, nf);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_wide_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
-                               cudaStream_t st) {
-  if (!f.xs || !b.xs || !b.xe || f.img == b.img || f.queue == b.queue) return cudaErrorInvalidValue;
-  if (NP == 256) return launch_passes_t<256>(f, b, st);
-  if (NP == 512) return launch_passes_t<512>(f, b, st);
-  return cudaErrorInvalidValue;
 }
 
 template <int NP>
 static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st) {
   using L = WideCfg<NP>;
-  cudaError_t err = build_wide_image<NP>(a, 0, st);
+  cudaError_t err = build_wide_image<NP>(a, st);
   if (err != cudaSuccess) return err;
   auto kern = hmm_forward_wide<NP>;
   const int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;  // one CTA per SM
@@ -471,8 +377,8 @@ static cudaError_t launch_wide_t(const MmaWideLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st, int dir) {
-  if (dir != 0 || a.xs) return cudaErrorInvalidValue;  // the adjoint's passes: launch_wide_passes
+cudaError_t launch_forward_wide(int NP, const MmaWideLaunch& a, cudaStream_t st) {
+  if (a.xs) return cudaErrorInvalidValue;  // the adjoint's passes: launch_cluster_passes
   if (NP == 256) return launch_wide_t<256>(a, st);
   if (NP == 512) return launch_wide_t<512>(a, st);
   return cudaErrorInvalidValue;

@@ -262,7 +262,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.w_G = off; off = align256(off + rowb);
     L.w_xe = off; off = align256(off + (size_t)(slots * rtot) * 4);
     L.w_sym = off; off = align256(off + (size_t)(slots * rtot) * 4);
-    const int tiles = (NP / 128) * (NP / 128);
+    const int tiles = (NP / 128) * (NP / 256);  // output tiles of the count contraction
     int ns = (2 * num_sms() + tiles * d.K - 1) / (tiles * d.K);
     L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
     int nc = (2 * num_sms() + d.K - 1) / d.K;
@@ -595,7 +595,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.A = A;
   c.Cp = at<float>(ws, L.w_Cp);
   c.nsplit = L.w_nsplit;
-  c.rows_per_split = ((L.w_rtot + L.w_nsplit - 1) / L.w_nsplit + 7) / 8 * 8;
+  c.rows_per_split = ((L.w_rtot + L.w_nsplit - 1) / L.w_nsplit + 31) / 32 * 32;
   c.Ep = at<float>(ws, L.w_Ep);
   c.Pp = at<float>(ws, L.w_Pp);
   c.nchunks = L.w_nchunks;
@@ -603,6 +603,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.cnt_pi = cnt_pi;
   c.cnt_A = cnt_A;
   c.cnt_B = cnt_B;
+  c.status = &at<WsHeader>(ws, 0)->status;
   {
     Timed tm(T_REDUCE, st);
     e = launch_fbw_counts(c, st);

@@ -9,17 +9,18 @@
 //   xi_t(i, j) = [X_t(i) / z_t] a_ij [b_j(o_{t+1}) Bh_{t+1}(j) 2^-f_t]
 // so the transition counts of a model are A o (U^T V), U_t = w X_t / z_t and
 // V_t = b(o_{t+1}) o Bh_{t+1} 2^-f_t over every step t < T - 1 of every
-// sequence: one contraction over all rows, run as a split-K SIMT GEMM whose
-// partial tiles are summed in a fixed order. Emission and initial counts are
+// sequence: one contraction over all rows, run on the tensor cores with TF32
+// operands (U and V rounded to TF32, relative error <= 2^-11 each; FP32
+// accumulation) as a split-K GEMM whose partial tiles are summed in a fixed
+// order. Emission and initial counts are
 // sums of gamma rows by symbol and at t = 0, per chunk of rows in shared
 // memory (thread j owns state j: no atomics), then over chunks in a fixed
 // order. Everything is bitwise reproducible.
 #include "hmm_internal.cuh"
+#include "tc.cuh"
 
 namespace hmmgb {
 
-constexpr int kFbwGemmTile = 128;   // output tile of the contraction (128 x 128)
-constexpr int kFbwGemmRows = 8;     // rows per shared-memory stage
 
 // Largest s with roff[s] <= r (roff non-decreasing, roff[0] = 0).
 __device__ __forceinline__ int seq_of_row(const int64_t* roff, int S, int64_t r) {
@@ -101,56 +102,129 @@ __global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
   }
 }
 
-// Cp[k][split] = sum over the split's rows of U[r]^T V[r] (128 x 128 tile
-// per block, 8 x 8 outputs per thread, rows staged 8 at a time).
+// Cp[k][split] = sum over the split's rows of U[r]^T V[r] on the tensor
+// cores: one CTA per (128 x 256 output tile, split, model), D in tensor
+// memory (256 FP32 columns). Rows are taken 32 at a time: 256 threads load
+// the chunk's U columns (128 states) and V columns (256 states) from the
+// row-major buffers -- every warp load reads 32 consecutive states of one
+// row -- round them to TF32 and write them as K-major core matrices (8
+// states x 4 rows, 16 bytes per state) into one of two shared-memory stages;
+// thread 0 then issues four MMAs (M = 128, N = 256, K = 8 rows each,
+// kind::tf32) and commits them to the stage's mbarrier, while the threads
+// load the next chunk into the other stage. Rows past the split's end count
+// as zero. Every wait is bounded; a give-up records HMM_STATUS_TIMEOUT.
+constexpr int kFbwTileN = 256;      // output tile: 128 states i x 256 states j
+constexpr int kFbwRows = 32;        // rows per chunk (K of four MMAs)
+constexpr uint32_t kFbwWait = 1u << 24;
+constexpr int kFbwStageA = 128 * kFbwRows * 4;         // 16 KB
+constexpr int kFbwStageB = kFbwTileN * kFbwRows * 4;   // 32 KB
+constexpr int kFbwSmem = 2 * (kFbwStageA + kFbwStageB) + 64;
+
 template <int NP>
-__global__ void __launch_bounds__(256) fbw_gemm_kernel(FbWideArgs a) {
-  constexpr int TL = kFbwGemmTile, BK = kFbwGemmRows, NT = NP / TL;
-  __shared__ __align__(16) float Us[BK][TL];
-  __shared__ __align__(16) float Vs[BK][TL];
-  const int ti = blockIdx.x / NT, tj = blockIdx.x % NT;
+__global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
+  constexpr int NJ = NP / kFbwTileN;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;                              // [2][kFbwStageA]
+  uint8_t* sB = smem + 2 * kFbwStageA;             // [2][kFbwStageB]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * (kFbwStageA + kFbwStageB));
+  uint64_t* done = bars;      // [2]: the chunk's MMAs have read the stage
+  uint64_t* fin = bars + 2;   // every MMA of the CTA is done
+  volatile uint32_t* slot = reinterpret_cast<volatile uint32_t*>(bars + 3);
+  const int mi = blockIdx.x / NJ, nj = blockIdx.x % NJ;
   const int split = blockIdx.y, k = blockIdx.z;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t r0 = (int64_t)split * a.rows_per_split;
   const int64_t r1 = min(a.rtot, r0 + a.rows_per_split);
-  const float* Uk = a.X + (size_t)k * a.rtot * NP + ti * TL;
-  const float* Vk = a.V + (size_t)k * a.rtot * NP + tj * TL;
-  float acc[8][8];
+  const int nch = r1 > r0 ? (int)((r1 - r0 + kFbwRows - 1) / kFbwRows) : 0;
+  const float* Uk = a.X + (size_t)k * a.rtot * NP + 128 * mi;
+  const float* Vk = a.V + (size_t)k * a.rtot * NP + kFbwTileN * nj;
+
+  if (warp == 0) tc::tmem_alloc(const_cast<uint32_t*>(slot), 256);
+  if (tid == 0) {
+    tc::mbar_init(&done[0], 1);
+    tc::mbar_init(&done[1], 1);
+    tc::mbar_init(fin, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  constexpr uint32_t idesc = tc::instr_desc(2, 128, kFbwTileN);
+  bool ok = true;
+
+  // this thread's share of a chunk: U column ia for row quads qa, qa + 2, ..;
+  // V column tid for every row quad
+  const int ia = tid & 127, qa = tid >> 7;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int st = ch & 1;
+    const int64_t rb = r0 + (int64_t)ch * kFbwRows;
+    float u[4][4], v[8][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+    for (int m = 0; m < 4; ++m)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  const int lr = tid / 32, lc = 4 * (tid % 32);  // staging: row lr, columns lc .. lc + 3
-  for (int64_t rb = r0; rb < r1; rb += BK) {
-    const int64_t rr = rb + lr;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 uv = rr < r1 ? __ldg(reinterpret_cast<const float4*>(Uk + rr * NP + lc)) : z4;
-    const float4 vv = rr < r1 ? __ldg(reinterpret_cast<const float4*>(Vk + rr * NP + lc)) : z4;
+      for (int e = 0; e < 4; ++e) {
+        const int64_t r = rb + 4 * (qa + 2 * m) + e;
+        u[m][e] = r < r1 ? __ldg(Uk + r * NP + ia) : 0.f;
+      }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t r = rb + 4 * q + e;
+        v[q][e] = r < r1 ? __ldg(Vk + r * NP + tid) : 0.f;
+      }
+    // the stage's previous chunk (ch - 2) must have been read by its MMAs
+    if (ch >= 2 && !tc::mbar_wait_bounded(&done[st], (uint32_t)((ch >> 1) + 1) & 1u, kFbwWait))
+      ok = false;
+    uint8_t* A = sA + st * kFbwStageA;
+    uint8_t* B = sB + st * kFbwStageB;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      *reinterpret_cast<uint4*>(A + (ia >> 3) * 1024 + (qa + 2 * m) * 128 + (ia & 7) * 16) =
+          make_uint4(tc::to_tf32(u[m][0]), tc::to_tf32(u[m][1]), tc::to_tf32(u[m][2]),
+                     tc::to_tf32(u[m][3]));
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<uint4*>(B + (tid >> 3) * 1024 + q * 128 + (tid & 7) * 16) =
+          make_uint4(tc::to_tf32(v[q][0]), tc::to_tf32(v[q][1]), tc::to_tf32(v[q][2]),
+                     tc::to_tf32(v[q][3]));
+    tc::fence_proxy_async();  // the stage's generic writes -> tensor core
+    tc::fence_before_sync();
     __syncthreads();
-    *reinterpret_cast<float4*>(&Us[lr][lc]) = uv;
-    *reinterpret_cast<float4*>(&Vs[lr][lc]) = vv;
-    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t aA = tc::smem_u32(A), aB = tc::smem_u32(B);
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&Us[kk][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&Us[kk][ty * 8 + 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Vs[kk][tx * 8]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Vs[kk][tx * 8 + 4]);
-      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int kk = 0; kk < kFbwRows / 8; ++kk)
+        tc::mma_tf32(tmem, tc::smem_desc(aA + kk * 256, 128, 1024),
+                     tc::smem_desc(aB + kk * 256, 128, 1024), idesc, (ch | kk) ? 1u : 0u);
+      tc::mma_commit(&done[st]);
     }
   }
-  float* C = a.Cp + ((size_t)k * a.nsplit + split) * NP * NP;
+  if (tid == 0) tc::mma_commit(fin);  // arrives once every MMA above is done
+  if (!tc::mbar_wait_bounded(fin, 0, kFbwWait)) ok = false;
+  tc::fence_after_sync();
+  if (!ok) set_status(a.status, HMM_STATUS_TIMEOUT);
+  // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (states i), columns
+  // 128 (w / 4) .. + 127 (states j)
+  const int i = 128 * mi + 32 * (warp & 3) + lane;
+  const int jc = 128 * (warp >> 2);
+  float* dst = a.Cp + ((size_t)k * a.nsplit + split) * NP * NP + (size_t)i * NP + kFbwTileN * nj + jc;
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    float y[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(jc + 32 * c), y);
+    tc::tmem_ld_wait();
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    float* dst = C + (size_t)(ti * TL + ty * 8 + i) * NP + tj * TL + tx * 8;
-    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(dst + 32 * c + 4 * q) =
+          nch > 0 ? make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3])
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 // cnt_A[k][i][j] = a_ij * sum over splits (fixed order).
@@ -225,9 +299,13 @@ cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
   else return cudaErrorInvalidValue;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const dim3 gg((a.NP / kFbwGemmTile) * (a.NP / kFbwGemmTile), a.nsplit, a.K);
-  if (a.NP == 256) fbw_gemm_kernel<256><<<gg, 256, 0, st>>>(a);
-  else fbw_gemm_kernel<512><<<gg, 256, 0, st>>>(a);
+  if (a.rows_per_split % kFbwRows) return cudaErrorInvalidValue;
+  const dim3 gg((a.NP / 128) * (a.NP / kFbwTileN), a.nsplit, a.K);
+  auto gk = a.NP == 256 ? fbw_gemm_kernel<256> : fbw_gemm_kernel<512>;
+  if ((e = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, kFbwSmem)) !=
+      cudaSuccess)
+    return e;
+  gk<<<gg, 256, kFbwSmem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   fbw_reduce_a_kernel<<<1024, 256, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

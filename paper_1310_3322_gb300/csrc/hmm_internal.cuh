@@ -570,6 +570,7 @@ struct FbWideArgs {
   float* cnt_pi;
   float* cnt_A;
   float* cnt_B;
+  int32_t* status;
 };
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st);
 size_t fbw_emis_smem(int NP, int M);

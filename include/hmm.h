@@ -135,9 +135,12 @@ int hmm_max_states(hmm_op_t op, hmm_precision_t precision);
  * FP64. The BF16 path
  * computes with the model's A and B both rounded to BF16 (round to nearest
  * even, once per call); the TF32 path rounds A only. Above 128
- * states (the cited cuHMM kernel's 512-state workload, Sec. 5.6) one CTA
- * holds one 128-sequence tile and streams A^T from a BF16 image the call
- * builds in the workspace. HMM_AUTO: tensor cores (BF16) above N = 64; for
+ * states (the cited cuHMM kernel's 512-state workload, Sec. 5.6) each
+ * 128-sequence tile runs on a thread-block cluster of N_pad / 64 CTAs, each
+ * holding its 64-column slices of A and of the emission table resident, the
+ * rows exchanged through distributed shared memory every step; where the
+ * emission slice does not fit (N_pad = 512 with M > 173) one CTA per tile
+ * streams A^T from a BF16 image the call builds in the workspace. HMM_AUTO: tensor cores (BF16) above N = 64; for
  * N <= 32 and a batch of few long sequences (max_len >= 4096, pairs * N_pad^3
  * <= 2^21) the parallel-in-time forward of hmm_forward_scan, when the
  * workspace holds its chunk products (hmm_workspace_size(HMM_OP_FORWARD)
@@ -241,13 +244,14 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
  * tensor cores above N = 32. Its errors against FP64 are of order the BF16 unit roundoff 2^-8
  * relative per count (|delta log P| <= 2^-7 T).
  * Above 128 states (N <= 512, the cited cuHMM shape of Sec. 5.6) the
- * tensor-core forward and backward passes keep every step's rescaled alpha
- * and beta rows in the workspace (4 K total_obs N_pad floats), and the counts
- * are formed from them: xi as one fixed-order contraction over all steps.
- * This path scores every sequence against every model (model_of_seq only
- * with K = 1) and needs N_pad (M + 1) * 4 bytes <= 227 KB (M <= 112 at 512
- * padded states); other requests return HMM_ERR_UNSUPPORTED. Same error
- * bounds.
+ * tensor-core forward and backward passes (on clusters, as the forward) keep
+ * every step's rescaled alpha and beta rows in the workspace (4 K total_obs
+ * N_pad floats), and the counts are formed from them: xi as one fixed-order
+ * contraction over all steps on the tensor cores, its two operands rounded
+ * to TF32 (relative error <= 2^-11 each, FP32 accumulation). This path
+ * scores every sequence against every model (model_of_seq only with K = 1)
+ * and needs N_pad (M + 1) * 4 bytes <= 227 KB (M <= 112 at 512 padded
+ * states); other requests return HMM_ERR_UNSUPPORTED. Same error bounds.
  * Impossible or invalid pairs contribute no counts. */
 int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                          const hmm_seqs_t* seqs, const float* weight,

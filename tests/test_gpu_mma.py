@@ -172,3 +172,40 @@ def test_wide_forward_full_cuhmm_shape_sampled():
                                nthreads=8)
     T = w.lengths[idx].astype(np.float64)[:, None]
     assert np.all(np.abs(ll[idx] - ref) <= 3 * U_BF16 * T + ll_tol(w.lengths[idx])[:, None])
+
+
+@pytest.mark.parametrize("N", [200, 300])
+def test_cluster_forward_degenerate_and_deterministic(N):
+    """Above 128 states (a cluster of N_pad / 64 CTAs per tile): empty,
+    one- and two-step sequences, an invalid symbol, a sequence impossible
+    under one model, rows of different lengths in one tile; two calls agree
+    bit for bit."""
+    import torch
+    rng = np.random.default_rng(12)
+    K, M = 2, 16
+    pi, A, B = synth.random_model(rng, K, N, M, alpha=0.5)
+    B[1, :, 15] = 0.0  # model 1 never emits symbol 15
+    B /= B.sum(axis=2, keepdims=True)
+    lengths = np.array([0, 1, 2, 150, 3, 70, 31], np.int32)
+    offsets = np.concatenate([[0], np.cumsum(lengths.astype(np.int64))[:-1]]).astype(np.int64)
+    sym = rng.integers(0, 15, size=int(lengths.sum())).astype(np.int32)
+    sym[offsets[5] + 33] = 15          # impossible under model 1 only
+    sym[offsets[6] + 7] = M + 3        # invalid symbol in sequence 6
+    t = [torch.from_numpy(x).cuda() for x in (pi, A, B)]
+    seqs = hmm.Sequences.from_numpy(sym, offsets, lengths, device="cuda")
+
+    def run():
+        ll, am = hmm.hmm_forward(*t, seqs, precision=hmm.HMM_BF16_MMA)
+        return ll.cpu().numpy(), am.cpu().numpy(), hmm.hmm_get_device_status(hmm.default_workspace())
+
+    (ll, am, status), (ll2, am2, _) = run(), run()
+    assert np.array_equal(ll, ll2, equal_nan=True) and np.array_equal(am, am2)
+    assert status & hmm.HMM_STATUS_SYMBOL
+    assert np.all(ll[0] == 0.0)
+    assert np.all(np.isnan(ll[6])) and am[6] == -1
+    assert np.isneginf(ll[5, 1]) and np.isfinite(ll[5, 0])
+    ref, ref_am, _ = oracle.forward(oracle.params(pi, A, B), sym, offsets, lengths)
+    ok = np.array([True, True, True, True, True, False, False])
+    T = np.maximum(lengths[ok], 1)[:, None]
+    assert np.all(np.abs(ll[ok] - ref[ok]) <= 3 * U_BF16 * T + ll_tol(lengths[ok])[:, None])
+    assert np.abs(ll[5, 0] - ref[5, 0]) <= 3 * U_BF16 * lengths[5] + ll_tol(lengths[5:6])[0]

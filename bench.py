@@ -1267,10 +1267,11 @@ def run_wide(args):
     kms = {k: v[1] / v[0] for k, v in kt.items() if v[0]}
     achieved = 2.0 * N * N * units / (kms["forward"] / 1e3) / 1e12
     peak, basis = measured_peak_bf16()
-    n_tiles = (w.S + 127) // 128
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     cl = 4 if N <= 256 else 8  # CTAs per cluster: N_pad / 64
-    busy = min(n_tiles * K * cl, sm_count)
+    # rows per tile: the fewest of 32, 64, 128 whose clusters fit one wave
+    rows = next((r for r in (32, 64) if -(-w.S // r) * K * cl <= sm_count), 128)
+    busy = min(-(-w.S // rows) * K * cl, sm_count)
     # one Baum-Welch iteration of the same shape (Sec. 5.6 quotes forward and
     # Baum-Welch): tensor-core forward + backward passes keeping their rows,
     # count contraction, M-step (in place on copies of the parameters)
@@ -1303,8 +1304,8 @@ def run_wide(args):
         "data": "synthetic",
         "config": {"workload": f"cuhmm K={K} N={N} M={M} S={w.S} T~U{{100..500}} (forward of "
                                "every sequence, tcgen05 BF16, one cluster of "
-                               f"{cl} CTAs per 128-row tile)",
-                   "units_per_step": units, "tiles": n_tiles * K,
+                               f"{cl} CTAs per {rows}-row tile)",
+                   "units_per_step": units, "tiles": -(-w.S // rows) * K,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "timing": "eager step, CUDA events"},
         "roofline": {"bound": "tensor", "kernel": "forward_cluster", "achieved": achieved,

@@ -549,7 +549,8 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
     tm.stop();
   }
   if (e != cudaSuccess) return cuda_fail(e, "setup launch");
-  const int n_tiles = (seqs->S + 127) / 128;
+  const int rows = cluster_tile_rows(NP, seqs->S, dims.K, 2);
+  const int n_tiles = (seqs->S + rows - 1) / rows;
   MmaWideLaunch f;
   memset(&f, 0, sizeof(f));
   f.seq = seq_args(dims, *seqs, L, ws);
@@ -559,6 +560,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   f.queue = &at<WsHeader>(ws, 0)->queue[0];
   f.status = &at<WsHeader>(ws, 0)->status;
   f.n_tiles = n_tiles;
+  f.rows = rows;
   f.n_items = n_tiles * dims.K;
   f.xs = at<float>(ws, L.w_X);
   f.roff = at<int64_t>(ws, L.bpoff);
@@ -855,8 +857,12 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
   if (seqs->S == 0) return HMM_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (mma && L.NP >= 256) {  // wide state counts: one tile per CTA, A^T streamed
-    const int n_tiles = (seqs->S + 127) / 128;
+  if (mma && L.NP >= 256) {
+    // wide state counts: each tile on a cluster of CTAs where its slices fit,
+    // else one 128-row tile per CTA with A^T streamed
+    const bool cluster = forward_cluster_fits(L.NP, dims.M);
+    const int rows = cluster ? cluster_tile_rows(L.NP, seqs->S, dims.K, 1) : 128;
+    const int n_tiles = (seqs->S + rows - 1) / rows;
     if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
     SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
     s.bf16_b = 1;  // BF16 path: B rounded to BF16 like A
@@ -878,14 +884,12 @@ int hmm_forward(hmm_dims_t dims, const float* pi, const float* A, const float* B
     f.queue = &at<WsHeader>(ws, 0)->queue[0];
     f.status = &at<WsHeader>(ws, 0)->status;
     f.n_tiles = n_tiles;
+    f.rows = rows;
     f.n_items = n_tiles * dims.K;
     f.wait_limit = wait_limit_polls();
     {
       Timed tm(T_FORWARD, st);
-      // the state dimension over a cluster of CTAs where its slices fit, else
-      // one CTA per tile with A^T streamed
-      e = forward_cluster_fits(L.NP, dims.M) ? launch_forward_cluster(L.NP, f, st)
-                                              : launch_forward_wide(L.NP, f, st);
+      e = cluster ? launch_forward_cluster(L.NP, f, st) : launch_forward_wide(L.NP, f, st);
       tm.stop();
     }
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");

@@ -523,7 +523,8 @@ struct MmaWideLaunch {
   int32_t* queue;
   int32_t* status;
   int n_items;        // n_tiles * K
-  int n_tiles;        // ceil(S / 128)
+  int n_tiles;        // ceil(S / rows)
+  int rows;           // rows per tile: 128 (the cluster kernel: 32, 64 or 128)
   // per-step rows for the adjoint above 128 states (xs NULL: recognition only)
   float* xs;             // [K][rtot][NP] forward: scaled alpha_t; backward: scaled beta_t
   int32_t* xe;           // backward: [K][rtot] power of two removed at each step
@@ -535,6 +536,8 @@ struct MmaWideLaunch {
 // column slice of A resident (mma_cluster.cu); serves M symbols when its
 // emission slice fits beside them.
 bool forward_cluster_fits(int NP, int M);
+// The cluster kernels' rows per tile for S sequences x K models x dirs passes.
+int cluster_tile_rows(int NP, int S, int K, int dirs);
 cudaError_t launch_forward_cluster(int NP, const MmaWideLaunch& a, cudaStream_t st);
 // Both passes of the adjoint above 128 states on clusters, in one launch:
 // clusters [0, f.n_items) the forward items of f (rows alpha_t kept in f.xs),

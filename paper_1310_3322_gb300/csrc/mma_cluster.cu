@@ -82,10 +82,11 @@ __device__ __forceinline__ void st_v8c(float* p, const float* v) {
 // forward recursion with A^T in place of A); STORE keeps every step's row
 // (forward: scaled alpha_t; backward: scaled beta_t before the emission
 // product, with its exponent) for the adjoint's count kernels.
-template <int NP, int DIR, bool STORE>
+template <int NP, int DIR, bool STORE, int TR>
 __device__ __forceinline__ void cluster_body(const MmaWideLaunch& a, int item) {
   using L = ClusterCfg<NP>;
   constexpr int CL = L::CL, SLICE = L::SLICE;
+  static_assert(TR == 32 || TR == 64 || TR == 128, "rows per tile");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sX = smem + L::OFF_X;
   uint8_t* sB = smem + L::OFF_B;
@@ -117,6 +118,9 @@ __device__ __forceinline__ void cluster_body(const MmaWideLaunch& a, int item) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     misc[1] = 0;
   }
+  // rows TR .. 127 of X stay zero (the product is M = 128 rows)
+  if (TR < 128)
+    for (int i = tid; i < L::XB / 16; i += L::NTH) reinterpret_cast<uint4*>(sX)[i] = make_uint4(0, 0, 0, 0);
   // the model's column slice of A (B operand, K-major: (n = j - c0, k = i) =
   // a_ij; backward: a_ji)
   {
@@ -148,9 +152,10 @@ __device__ __forceinline__ void cluster_body(const MmaWideLaunch& a, int item) {
   // the barriers of every CTA are initialised before anyone sends to them
   tc::cluster_sync();
 
-  // this row's state (every CTA keeps all 128 rows, alike)
-  const int pos = tile * 128 + row;
-  const bool has = pos < S;
+  // this row's state (every CTA keeps all TR rows of the tile, alike; rows
+  // TR .. 127 hold nothing and stay zero)
+  const int pos = tile * TR + row;
+  const bool has = row < TR && pos < S;
   const int s = has ? a.seq.order[pos] : 0;
   const int T = has ? a.seq.seqlen[s] : 0;
   const bool bad_seq = T < 0;
@@ -221,9 +226,9 @@ __device__ __forceinline__ void cluster_body(const MmaWideLaunch& a, int item) {
       const uint32_t peer = (rank + (uint32_t)p) % (uint32_t)CL;
       const uint32_t fb = tc::map_rank(tc::smem_u32(full + rank), peer);
       const uint32_t xs = aX + rank * SLICE;
-      tc::bulk_s2peer(tc::map_rank(xs, peer), xs, SLICE, fb);
+      tc::bulk_s2peer(tc::map_rank(xs, peer), xs, TR * 128, fb);  // rows 0 .. TR - 1
       const uint32_t ps = tc::smem_u32(px + (par * CL + (int)rank) * 128);
-      tc::bulk_s2peer(tc::map_rank(ps, peer), tc::smem_u32(pout), 128 * 4, fb);
+      tc::bulk_s2peer(tc::map_rank(ps, peer), tc::smem_u32(pout), TR * 4, fb);
     }
   };
   // sum of the row's CL partial sums of step parity `par` (rank order)
@@ -233,7 +238,7 @@ __device__ __forceinline__ void cluster_body(const MmaWideLaunch& a, int item) {
     for (int c = 0; c < CL; ++c) v += px[(par * CL + c) * 128 + row];
     return v;
   };
-  constexpr uint32_t kSliceTx = (uint32_t)(SLICE + 128 * 4);
+  constexpr uint32_t kSliceTx = (uint32_t)(TR * 128 + TR * 4);
 
   // t = 0: x_0 = pi . b(o_0) (backward: Y_{T-1} = b(o_{T-1}), beta = 1), no scaling
   if (Tmax > 0) {
@@ -434,20 +439,20 @@ __device__ __forceinline__ void cluster_body(const MmaWideLaunch& a, int item) {
 }
 
 // Recognition: the forward recursion alone, one item per cluster.
-template <int NP>
+template <int NP, int TR>
 __global__ void __launch_bounds__(512, 1) hmm_forward_cluster(const __grid_constant__ MmaWideLaunch a) {
-  cluster_body<NP, 0, false>(a, (int)(blockIdx.x / ClusterCfg<NP>::CL));
+  cluster_body<NP, 0, false, TR>(a, (int)(blockIdx.x / ClusterCfg<NP>::CL));
 }
 
 // Both passes of the adjoint in one launch (they are independent): clusters
 // [0, nf) take the forward items of f, the others the backward items of b.
-template <int NP>
+template <int NP, int TR>
 __global__ void __launch_bounds__(512, 1)
 hmm_cluster_passes(const __grid_constant__ MmaWideLaunch f, const __grid_constant__ MmaWideLaunch b,
                    int nf) {
   const int c = (int)(blockIdx.x / ClusterCfg<NP>::CL);
-  if (c < nf) cluster_body<NP, 0, true>(f, c);
-  else cluster_body<NP, 1, true>(b, c - nf);
+  if (c < nf) cluster_body<NP, 0, true, TR>(f, c);
+  else cluster_body<NP, 1, true, TR>(b, c - nf);
 }
 
 // Clusters of CL CTAs, one CTA per SM (the shared memory takes it all).
@@ -480,20 +485,49 @@ bool forward_cluster_fits(int NP, int M) {
   return false;
 }
 
+// Rows per tile: the fewest (32, 64 or 128) for which the clusters of all
+// tiles (times `dirs` directions) still fit the GPU in one wave -- the product
+// stays M = 128 (rows past the tile are zero) while each step's exchange
+// shrinks with the rows; 128 when even that does not fit.
+int cluster_tile_rows(int NP, int S, int K, int dirs) {
+  const int cl = NP / 64;
+  for (int tr = 32; tr < 128; tr *= 2)
+    if ((long long)((S + tr - 1) / tr) * K * dirs * cl <= num_sms()) return tr;
+  return 128;
+}
+
+template <int NP, int TR>
+static cudaError_t forward_cluster_t(const MmaWideLaunch& a, cudaStream_t st) {
+  return launch_clusters<NP>(hmm_forward_cluster<NP, TR>, a.n_items, a.seq.M, st, a);
+}
+template <int NP, int TR>
+static cudaError_t passes_cluster_t(const MmaWideLaunch& f, const MmaWideLaunch& b, cudaStream_t st) {
+  return launch_clusters<NP>(hmm_cluster_passes<NP, TR>, f.n_items + b.n_items, f.seq.M, st, f, b,
+                             f.n_items);
+}
+
 cudaError_t launch_forward_cluster(int NP, const MmaWideLaunch& a, cudaStream_t st) {
-  if (a.xs || a.n_items < 1) return cudaErrorInvalidValue;
-  if (NP == 256) return launch_clusters<256>(hmm_forward_cluster<256>, a.n_items, a.seq.M, st, a);
-  if (NP == 512) return launch_clusters<512>(hmm_forward_cluster<512>, a.n_items, a.seq.M, st, a);
+  if (a.xs || a.n_items < 1 || a.n_tiles != (a.seq.S + a.rows - 1) / a.rows) return cudaErrorInvalidValue;
+  if (NP == 256 && a.rows == 32) return forward_cluster_t<256, 32>(a, st);
+  if (NP == 256 && a.rows == 64) return forward_cluster_t<256, 64>(a, st);
+  if (NP == 256 && a.rows == 128) return forward_cluster_t<256, 128>(a, st);
+  if (NP == 512 && a.rows == 32) return forward_cluster_t<512, 32>(a, st);
+  if (NP == 512 && a.rows == 64) return forward_cluster_t<512, 64>(a, st);
+  if (NP == 512 && a.rows == 128) return forward_cluster_t<512, 128>(a, st);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_cluster_passes(int NP, const MmaWideLaunch& f, const MmaWideLaunch& b,
                                   cudaStream_t st) {
-  if (!f.xs || !b.xs || !b.xe || !f.roff || f.n_items < 1 || b.n_items != f.n_items)
+  if (!f.xs || !b.xs || !b.xe || !f.roff || f.n_items < 1 || b.n_items != f.n_items ||
+      b.rows != f.rows || f.n_tiles != (f.seq.S + f.rows - 1) / f.rows)
     return cudaErrorInvalidValue;
-  const int n = f.n_items + b.n_items;
-  if (NP == 256) return launch_clusters<256>(hmm_cluster_passes<256>, n, f.seq.M, st, f, b, f.n_items);
-  if (NP == 512) return launch_clusters<512>(hmm_cluster_passes<512>, n, f.seq.M, st, f, b, f.n_items);
+  if (NP == 256 && f.rows == 32) return passes_cluster_t<256, 32>(f, b, st);
+  if (NP == 256 && f.rows == 64) return passes_cluster_t<256, 64>(f, b, st);
+  if (NP == 256 && f.rows == 128) return passes_cluster_t<256, 128>(f, b, st);
+  if (NP == 512 && f.rows == 32) return passes_cluster_t<512, 32>(f, b, st);
+  if (NP == 512 && f.rows == 64) return passes_cluster_t<512, 64>(f, b, st);
+  if (NP == 512 && f.rows == 128) return passes_cluster_t<512, 128>(f, b, st);
   return cudaErrorInvalidValue;
 }
 

@@ -28,6 +28,9 @@ CASES = [
     ("cuhmm", 24, ("uniform", 1, 90), {}),
     ("cuhmm", 30, ("uniform", 1, 60), {"K": 2, "N": 300, "M": 32}),
     ("cuhmm", 50, ("uniform", 1, 120), {"K": 3, "N": 200, "M": 48}),
+    # many short sequences: 64- and 128-row tiles of the cluster passes
+    ("cuhmm", 700, ("uniform", 1, 10), {"K": 1, "N": 256, "M": 32}),
+    ("cuhmm", 1300, ("uniform", 1, 8), {"K": 1, "N": 256, "M": 32}),
 ]
 
 

@@ -84,6 +84,10 @@ WIDE_CASES = [
     ("large", 130, ("uniform", 20, 60), {"K": 2, "N": 256, "M": 300}),
     ("large", 140, ("uniform", 1, 40), {"K": 2, "N": 333, "M": 64}),    # padded to 512
     ("large", 129, ("uniform", 10, 40), {"K": 1, "N": 512, "M": 32}),
+    # many short sequences: the cluster kernel's 64- and 128-row tiles (few
+    # sequences take 32-row tiles)
+    ("large", 2000, ("uniform", 1, 12), {"K": 1, "N": 256, "M": 64}),
+    ("large", 5000, ("uniform", 1, 8), {"K": 1, "N": 256, "M": 64}),
     # emission slice too large for the cluster kernel: the streamed-A^T kernel
     ("large", 40, ("uniform", 1, 30), {"K": 2, "N": 400, "M": 200}),
 ]

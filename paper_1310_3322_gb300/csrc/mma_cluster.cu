@@ -26,6 +26,12 @@
 //   * a CTA may write a peer's X only after that peer's product has read it: each
 //     CTA, its product done, arrives on every peer's `free` mbarrier, and waits
 //     on its own for all peers before it overwrites its slice or sends it.
+// A tile has TR = 128 rows, or 32 / 64 when the batch is small enough that the
+// clusters of the smaller tiles still fit the GPU in one wave: the product
+// stays M = 128 (rows TR .. 127 of X are zero in every CTA and never sent), so
+// each step moves TR / 128 of the bytes over the cluster. The same code runs
+// the adjoint's backward recursion (A^T slices, reversed time) and keeps every
+// step's rows for its count kernels (cluster_body's DIR and STORE).
 // 512 threads, four per row (16 columns each); thread 0 issues the products and
 // copies. Every mbarrier wait is bounded; on timeout the kernel records
 // HMM_STATUS_TIMEOUT and leaves the loop. At the end every CTA meets the others

@@ -255,13 +255,24 @@ __global__ void fbw_emis_kernel(FbWideArgs a) {
   const int64_t r1 = min(a.rtot, r0 + a.rows_per_chunk);
   const int32_t* sym = a.sym + (size_t)k * a.rtot;
   const float* G = a.G + (size_t)k * a.rtot * a.NP + j;
-  for (int64_t r = r0; r < r1; ++r) {
-    const int code = __ldg(sym + r);
-    if (code < 0) continue;
-    const float g = __ldg(G + r * a.NP);
+  auto add = [&](int code, float g) {
+    if (code < 0) return;
     acc[j * ld + (code & 0xffffff)] += g;
     if (code >> 30) pacc += g;
+  };
+  int64_t r = r0;
+  // eight rows' loads in flight before their (ordered) shared-memory updates
+  for (; r + 8 <= r1; r += 8) {
+    int code[8];
+    float g[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) code[u] = __ldg(sym + r + u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) g[u] = __ldg(G + (r + u) * a.NP);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) add(code[u], g[u]);
   }
+  for (; r < r1; ++r) add(__ldg(sym + r), __ldg(G + r * a.NP));
   float* E = a.Ep + (((size_t)k * a.nchunks + chunk) * a.NP + j) * a.M;
   for (int m = 0; m < a.M; ++m) E[m] = acc[j * ld + m];
   a.Pp[((size_t)k * a.nchunks + chunk) * a.NP + j] = pacc;

@@ -252,12 +252,26 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
  * scores every sequence against every model (model_of_seq only with K = 1)
  * and needs N_pad (M + 1) * 4 bytes <= 227 KB (M <= 112 at 512 padded
  * states); other requests return HMM_ERR_UNSUPPORTED. Same error bounds.
+ * HMM_TF32_MMA (64 < N <= 128, M <= 256): the forward and the backward
+ * recursion of every tile of the same tile plan with TF32 operands (A
+ * rounded to TF32, round to nearest; B in FP32; FP32 accumulation), keeping
+ * every step's rescaled alpha and beta rows (4 rows x total_obs x 128 floats
+ * when labelled, K times that otherwise: size the workspace with
+ * hmm_forward_backward_workspace_size), then the counts from the rows as
+ * above (xi's operands rounded to TF32). |delta log P| <= 2 u T, u = 2^-11,
+ * counts within 2^-8 relative.
  * Impossible or invalid pairs contribute no counts. */
 int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                          const hmm_seqs_t* seqs, const float* weight,
                          hmm_precision_t precision, float* loglik, float* cnt_pi,
                          float* cnt_A, float* cnt_B, void* workspace, size_t workspace_bytes,
                          hmm_stream_t stream);
+
+/* Workspace bytes hmm_forward_backward needs at `precision` (host only; for
+ * anything but HMM_TF32_MMA the same as hmm_workspace_size with
+ * HMM_OP_FORWARD_BACKWARD). Errors as hmm_workspace_size. */
+int hmm_forward_backward_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs,
+                                        hmm_precision_t precision, size_t* bytes);
 
 /* Row-wise softmax of logits into probabilities (the parameterisation used for
  * learning): pi[k] = softmax(logit_pi[k]), A[k][i] = softmax(logit_A[k][i]),

@@ -26,8 +26,8 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma,
-                            int scan_L);
+static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma = false,
+                            int scan_L = 0, bool tf32 = false);
 // Workspace of hmm_forward without HMM_AUTO's parallel-in-time variant (the
 // static entry point's scratch is sized for this; hmm_forward falls back to
 // the sequential recursion when the scan's storage does not fit).
@@ -190,8 +190,8 @@ static bool scan_preferred(const hmm_dims_t& d, const hmm_seqs_t& q) {
   return pairs * NP * NP * NP <= ((int64_t)1 << 21) && pairs <= (int64_t)num_sms() * 32;
 }
 
-static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma = false,
-                            int scan_L = 0) {
+static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma,
+                            int scan_L, bool tf32) {
   WsLayout L;
   memset(&L, 0, sizeof(L));
   const int NP = pad_states(d.N);
@@ -270,6 +270,51 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.w_Cp = off; off = align256(off + (size_t)slots * L.w_nsplit * NP * NP * 4);
     L.w_Ep = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * d.M * 4);
     L.w_Pp = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * 4);
+  } else if (op == HMM_OP_FORWARD_BACKWARD && mma && tf32) {
+    // TF32 adjoint (N_pad = 128): the tile plan with one tile per pass group,
+    // then every step's rows (model blocks of rtot rows unless labelled), row
+    // offsets and the count partials of fb_wide.cu
+    const int cap = fb_mma_tile_cap(d, q);
+    const int max_len = q.max_len > 0 ? q.max_len : 1;
+    const int nsmax = fb_mma_nsmax(max_len);
+    const int64_t rtot = q.total_obs > 0 ? q.total_obs : 1;
+    const int64_t nrows = q.model_of_seq ? rtot : rtot * d.K;
+    L.m_group = 1;
+    L.m_spr = fb_mma_spr(nsmax, cap);
+    L.m_pass_cap = cap;
+    L.m_rng_cap = cap * ((nsmax + L.m_spr - 1) / L.m_spr);
+    L.w_rtot = rtot;
+    L.m_sorted = off; off = align256(off + S * 4);
+    L.m_tmp = off; off = align256(off + S * 4);
+    L.m_keys = off; off = align256(off + 2 * (size_t)std::max<int64_t>(S, cap) * 4);
+    L.m_tiles = off; off = align256(off + ((size_t)cap * 6 + (size_t)d.K * 2) * 4);
+    L.m_ntiles = off; off = align256(off + 4);
+    L.m_pscr = off; off = align256(off + mma_plan_scratch_bytes((int64_t)S));
+    L.m_pass = off; off = align256(off + (size_t)cap * 4);
+    L.m_ptmp = off; off = align256(off + (size_t)cap * 2 * 4);
+    L.m_npass = off; off = align256(off + 4);
+    L.m_rtile = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_rseg = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_rmodel = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_rlen = off; off = align256(off + (size_t)L.m_rng_cap * 4);
+    L.m_nrng = off; off = align256(off + 4);
+    const size_t rowb = (size_t)nrows * NP * 4;
+    L.w_X = off; off = align256(off + rowb);
+    L.w_Bh = off; off = align256(off + rowb);
+    L.w_V = off; off = align256(off + rowb);
+    L.w_G = off; off = align256(off + rowb);
+    L.w_xe = off; off = align256(off + (size_t)nrows * 4);
+    L.w_sym = off; off = align256(off + (size_t)nrows * 4);
+    L.bpoff = off; off = align256(off + S * 8);                    // rp: first row per sequence
+    L.t_pos = off; off = align256(off + S * 8);                    // first row per plan position
+    L.t_mrow = off; off = align256(off + 2 * ((size_t)d.K + 1) * 8);  // model row ranges
+    int ns = (2 * num_sms() + d.K - 1) / d.K;
+    L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
+    int nc = (2 * num_sms() + d.K - 1) / d.K;
+    L.w_nchunks = nc < 1 ? 1 : (nc > 512 ? 512 : nc);
+    L.w_Cp = off; off = align256(off + (size_t)d.K * L.w_nsplit * NP * NP * 4);
+    L.w_Ep = off; off = align256(off + (size_t)d.K * L.w_nchunks * NP * d.M * 4);
+    L.w_Pp = off; off = align256(off + (size_t)d.K * L.w_nchunks * NP * 4);
   } else if (op == HMM_OP_FORWARD_BACKWARD && mma) {
     // tensor-core adjoint: tile plan and work lists; per tile the pass
     // kernel's checkpoints (alpha and Y images, exponents, last row sums);
@@ -431,7 +476,7 @@ static int max_states(int op, int precision) {
     return 512;
   if (op == HMM_OP_FORWARD_SCAN) return (precision == HMM_FP32 || precision == HMM_AUTO) ? 32 : 0;
   if (op == HMM_OP_FORWARD && (precision == HMM_BF16_MMA || precision == HMM_AUTO)) return 512;
-  if (op == HMM_OP_FORWARD && precision == HMM_TF32_MMA) return 128;
+  if ((op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD) && precision == HMM_TF32_MMA) return 128;
   if (precision != HMM_FP32 && precision != HMM_AUTO) return 0;
   return 64;
 }
@@ -440,7 +485,8 @@ static int check_precision(int precision, int op) {
   if (precision == HMM_FP32 || precision == HMM_AUTO) return HMM_OK;
   if (precision == HMM_BF16_MMA && (op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD))
     return HMM_OK;
-  if (precision == HMM_TF32_MMA && op == HMM_OP_FORWARD) return HMM_OK;
+  if (precision == HMM_TF32_MMA && (op == HMM_OP_FORWARD || op == HMM_OP_FORWARD_BACKWARD))
+    return HMM_OK;
   if (precision == HMM_BF16_MMA || precision == HMM_TF32_MMA)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core precision %d not available for op %d in this build",
                 precision, op);
@@ -597,11 +643,10 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.A = A;
   c.Cp = at<float>(ws, L.w_Cp);
   c.nsplit = L.w_nsplit;
-  c.rows_per_split = ((L.w_rtot + L.w_nsplit - 1) / L.w_nsplit + 31) / 32 * 32;
   c.Ep = at<float>(ws, L.w_Ep);
   c.Pp = at<float>(ws, L.w_Pp);
   c.nchunks = L.w_nchunks;
-  c.rows_per_chunk = (L.w_rtot + L.w_nchunks - 1) / L.w_nchunks;
+  c.nrows = (int64_t)dims.K * L.w_rtot;
   c.cnt_pi = cnt_pi;
   c.cnt_A = cnt_A;
   c.cnt_B = cnt_B;
@@ -794,6 +839,22 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
     if (m > need) need = m;
   }
   *bytes = need;
+  return HMM_OK;
+}
+
+int hmm_forward_backward_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs,
+                                        hmm_precision_t precision, size_t* bytes) {
+  g_err[0] = 0;
+  if (precision != HMM_TF32_MMA)
+    return hmm_workspace_size(dims, seqs, HMM_OP_FORWARD_BACKWARD, bytes);
+  if (!bytes) return fail(HMM_ERR_ARG, "bytes is NULL");
+  int rc = check_dims(dims, max_states(HMM_OP_FORWARD_BACKWARD, HMM_TF32_MMA));
+  if (rc) return rc;
+  if (!seqs) return fail(HMM_ERR_ARG, "seqs is NULL");
+  if (seqs->S < 0 || seqs->total_obs < 0) return fail(HMM_ERR_ARG, "negative S or total_obs");
+  if (pad_states(dims.N) != 128)
+    return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint needs 64 < N <= 128 (N=%d)", dims.N);
+  *bytes = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD, true, 0, true).total;
   return HMM_OK;
 }
 
@@ -1126,6 +1187,142 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
   return HMM_OK;
 }
 
+// hmm_forward_backward with TF32 operands (64 < N <= 128): the tile plan,
+// the TF32 passes keeping every step's rows (mma_pass_tf32.cu), then the
+// count kernels of fb_wide.cu over the rows of each model.
+static int fb_tf32(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* weight,
+                   float* loglik, float* cnt_pi, float* cnt_A, float* cnt_B, void* ws,
+                   size_t ws_bytes, hmm_stream_t stream, const float* pi, const float* A,
+                   const float* B) {
+  const int NP = pad_states(dims.N);
+  if (NP != 128)
+    return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint needs 64 < N <= 128 (N=%d: use HMM_FP32)", dims.N);
+  if (!fb_tf32_supported(NP, dims.M) || fbw_emis_smem(NP, dims.M) > 227 * 1024)
+    return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint: M=%d too large", dims.M);
+  if (seqs->model_of_seq && dims.K > 65536)
+    return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports K <= 65536 labelled models");
+  const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD, true, 0, true);
+  int rc;
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (seqs->S == 0) return zero_counts(dims, cnt_pi, cnt_A, cnt_B, st);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  SetupArgs s = setup_args(dims, *seqs, L, ws, pi, A, B, 0);
+  s.skip_order = 1;  // the tile plan orders the sequences itself
+  const bool labelled = seqs->model_of_seq != nullptr;
+  const int cap = L.m_pass_cap;
+  int32_t* tiles = at<int32_t>(ws, L.m_tiles);
+  MmaPlanArgs p;
+  memset(&p, 0, sizeof(p));
+  p.S = seqs->S; p.K = dims.K; p.labelled = labelled ? 1 : 0;
+  p.seqlen = at<int32_t>(ws, L.seqlen);
+  p.model_of_seq = seqs->model_of_seq;
+  p.loglik = loglik;
+  p.sorted = at<int32_t>(ws, L.m_sorted);
+  p.tmp = at<int32_t>(ws, L.m_tmp);
+  p.key = at<uint32_t>(ws, L.m_keys);
+  p.key_tmp = p.key + std::max<int64_t>(seqs->S, (int64_t)cap);
+  p.tile_start = tiles; p.tile_rows = tiles + cap; p.tile_model = tiles + 2 * cap;
+  p.tile_len = tiles + 3 * cap; p.tile_order = tiles + 4 * cap; p.tile_tmp = tiles + 5 * cap;
+  p.group_start = tiles + 6 * cap; p.group_end = p.group_start + dims.K;
+  p.n_tiles_cap = cap;
+  p.n_tiles = at<int32_t>(ws, L.m_ntiles);
+  p.group = 1;
+  p.spr = L.m_spr;
+  p.pass_tiles = at<int32_t>(ws, L.m_pass);
+  p.pass_tmp = at<int32_t>(ws, L.m_ptmp);
+  p.n_pass = at<int32_t>(ws, L.m_npass);
+  p.pass_cap = L.m_pass_cap;
+  p.rng_tile = at<int32_t>(ws, L.m_rtile);
+  p.rng_seg = at<int32_t>(ws, L.m_rseg);
+  p.rng_model = at<int32_t>(ws, L.m_rmodel);
+  p.rng_len = at<int32_t>(ws, L.m_rlen);
+  p.n_rng = at<int32_t>(ws, L.m_nrng);
+  p.rng_cap = L.m_rng_cap;
+  {
+    const int nb = (int)((seqs->S + 4095) / 4096 > 0 ? (seqs->S + 4095) / 4096 : 1);
+    p.bcnt = at<int32_t>(ws, L.m_pscr);
+    p.hist = p.bcnt + nb;
+    p.n_valid = p.hist + 256 * nb;
+  }
+  {
+    Timed tm(T_SETUP, st);
+    e = launch_setup(s, st);
+    if (e == cudaSuccess) e = launch_mma_plan(p, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+
+  MmaPassLaunch pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.seq = seq_args(dims, *seqs, L, ws);
+  pa.mod = model_args(L, ws);
+  pa.sorted = p.sorted;
+  pa.tile_start = p.tile_start; pa.tile_rows = p.tile_rows; pa.tile_model = p.tile_model;
+  pa.tile_len = p.tile_len;
+  pa.pass_tiles = p.pass_tiles;
+  pa.n_pass = p.n_pass;
+  pa.labelled = p.labelled;
+  pa.loglik = loglik;
+  pa.queue = &at<WsHeader>(ws, 0)->queue[5];
+  pa.status = &at<WsHeader>(ws, 0)->status;
+  pa.wait_limit = wait_limit_polls();
+  pa.xs = at<float>(ws, L.w_X);
+  pa.bhs = at<float>(ws, L.w_Bh);
+  pa.xe = at<int32_t>(ws, L.w_xe);
+  pa.rp = at<int64_t>(ws, L.bpoff);
+  pa.rtot = L.w_rtot;
+  int64_t* pos_row = at<int64_t>(ws, L.t_pos);
+  int64_t* mrow = at<int64_t>(ws, L.t_mrow);
+  {
+    Timed tm(T_FB_PASS, st);
+    e = launch_fb_pass_tf32(NP, pa, p.n_valid, pos_row, mrow, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "TF32 adjoint pass launch");
+
+  FbWideArgs c;
+  memset(&c, 0, sizeof(c));
+  c.K = dims.K; c.N = dims.N; c.M = dims.M; c.NP = NP; c.S = seqs->S;
+  c.labelled = labelled ? 1 : 0;
+  c.rtot = L.w_rtot;
+  c.nrows = labelled ? L.w_rtot : (int64_t)dims.K * L.w_rtot;
+  c.X = pa.xs;
+  c.Bh = pa.bhs;
+  c.V = at<float>(ws, L.w_V);
+  c.G = at<float>(ws, L.w_G);
+  c.xe = pa.xe;
+  c.sym = at<int32_t>(ws, L.w_sym);
+  c.seqlen = at<int32_t>(ws, L.seqlen);
+  c.offsets = seqs->offsets;
+  c.symbols = seqs->symbols;
+  c.Btp = at<float>(ws, L.Btp);
+  c.weight = weight;
+  c.A = A;
+  c.Cp = at<float>(ws, L.w_Cp);
+  c.nsplit = L.w_nsplit;
+  c.Ep = at<float>(ws, L.w_Ep);
+  c.Pp = at<float>(ws, L.w_Pp);
+  c.nchunks = L.w_nchunks;
+  c.cnt_pi = cnt_pi;
+  c.cnt_A = cnt_A;
+  c.cnt_B = cnt_B;
+  c.status = &at<WsHeader>(ws, 0)->status;
+  c.pos_row = pos_row;
+  c.sorted = p.sorted;
+  c.n_valid = p.n_valid;
+  c.model_of_seq = seqs->model_of_seq;
+  c.mrow = mrow;
+  {
+    Timed tm(T_FB, st);
+    e = launch_fbw_counts(c, st);
+    tm.stop();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint count launch");
+  return HMM_OK;
+}
+
 int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const float* B,
                          const hmm_seqs_t* seqs, const float* weight, hmm_precision_t precision,
                          float* loglik, float* cnt_pi, float* cnt_A, float* cnt_B, void* ws,
@@ -1142,6 +1339,8 @@ int hmm_forward_backward(hmm_dims_t dims, const float* pi, const float* A, const
   if (weight && !al(weight, 4)) return fail(HMM_ERR_ARG, "weight misaligned");
   if (seqs->model_base)
     return fail(HMM_ERR_UNSUPPORTED, "model sets apply to recognition; the adjoint takes model_of_seq");
+  if (precision == HMM_TF32_MMA)
+    return fb_tf32(dims, seqs, weight, loglik, cnt_pi, cnt_A, cnt_B, ws, ws_bytes, stream, pi, A, B);
   if (use_mma_fb(dims, precision)) {
     if (dims.N <= 32)
       return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint needs N > 32 (N=%d: use HMM_FP32)", dims.N);

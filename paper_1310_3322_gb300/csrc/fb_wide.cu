@@ -40,12 +40,28 @@ __global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
   constexpr int Q = NP / 128;  // float4 groups per lane
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (r >= (int64_t)a.K * a.rtot) return;
-  const int k = (int)(r / a.rtot);
-  const int64_t rr = r % a.rtot;
-  const int s = seq_of_row(a.roff, a.S, rr);
+  if (r >= a.nrows) return;
+  int k = 0, s = 0;
+  int64_t t64 = -1;
+  if (a.pos_row) {
+    // rows in the plan's order: labelled, one run of rows for all models;
+    // otherwise a block of rtot rows per model
+    const int n = __ldg(a.n_valid);
+    const int64_t rel = a.labelled ? r : r % a.rtot;
+    const int64_t used = a.labelled ? a.mrow[a.K] : a.mrow[a.K + 1] - a.mrow[0];
+    if (n > 0 && rel < used) {
+      const int pos = seq_of_row(a.pos_row, n, rel);
+      s = a.sorted[pos];
+      t64 = rel - a.pos_row[pos];
+      k = a.labelled ? a.model_of_seq[s] : (int)(r / a.rtot);
+    }
+  } else {
+    k = (int)(r / a.rtot);
+    const int64_t rr = r % a.rtot;
+    s = seq_of_row(a.roff, a.S, rr);
+    t64 = rr - a.roff[s];
+  }
   const int T = a.seqlen[s];
-  const int64_t t64 = rr - a.roff[s];
   const bool row_ok = T > 0 && t64 >= 0 && t64 < T;
   const int t = row_ok ? (int)t64 : 0;
   float4* Xr = reinterpret_cast<float4*>(a.X + r * NP);
@@ -62,7 +78,8 @@ __global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(HMM_FULL_MASK, z, o);
-  const float w = (row_ok && a.weight) ? __ldg(a.weight + (size_t)s * a.K + k) : 1.f;
+  const float w = (row_ok && a.weight)
+                      ? __ldg(a.weight + (a.labelled ? (size_t)s : (size_t)s * a.K + k)) : 1.f;
   // impossible, invalid or zero-weight pairs contribute nothing
   const bool use = row_ok && z > 0.f && z < INFINITY && w != 0.f && !isnan(w);
   const bool trans = use && t + 1 < T;
@@ -75,7 +92,7 @@ __global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
     onext = __ldg(o + t + 1);
     if ((unsigned)onext >= (unsigned)a.M) onext = 0;  // flagged by the passes already
   }
-  const int kmod = a.labelled ? 0 : k;  // model of this row's parameters
+  const int kmod = k;  // model of this row's parameters
   const float4* bn = reinterpret_cast<const float4*>(a.Btp + ((size_t)kmod * a.M + onext) * NP);
   const float4* bhn = reinterpret_cast<const float4*>(a.Bh + (r + 1) * NP);
 #pragma unroll
@@ -103,13 +120,16 @@ __global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
 }
 
 // Cp[k][split] = sum over the split's rows of U[r]^T V[r] on the tensor
-// cores: one CTA per (128 x 256 output tile, split, model), D in tensor
-// memory (256 FP32 columns). Rows are taken 32 at a time: 256 threads load
-// the chunk's U columns (128 states) and V columns (256 states) from the
+// cores: one CTA per (128 x TN output tile, split, model; TN = 256, or 128 at
+// N_pad = 128), D in tensor memory (TN FP32 columns). Model k's rows are
+// [mrow[k], mrow[K + 1 + k]) (without mrow, the block k rtot .. (k + 1) rtot),
+// cut into nsplit splits of a multiple of 32 rows. Rows are taken 32 at a
+// time: 256 threads load the chunk's U columns (128 states) and V columns (TN
+// states) from the
 // row-major buffers -- every warp load reads 32 consecutive states of one
 // row -- round them to TF32 and write them as K-major core matrices (8
 // states x 4 rows, 16 bytes per state) into one of two shared-memory stages;
-// thread 0 then issues four MMAs (M = 128, N = 256, K = 8 rows each,
+// thread 0 then issues four MMAs (M = 128, N = TN, K = 8 rows each,
 // kind::tf32) and commits them to the stage's mbarrier, while the threads
 // load the next chunk into the other stage. Rows past the split's end count
 // as zero. Every wait is bounded; a give-up records HMM_STATUS_TIMEOUT.
@@ -120,9 +140,10 @@ constexpr int kFbwStageA = 128 * kFbwRows * 4;         // 16 KB
 constexpr int kFbwStageB = kFbwTileN * kFbwRows * 4;   // 32 KB
 constexpr int kFbwSmem = 2 * (kFbwStageA + kFbwStageB) + 64;
 
-template <int NP>
+template <int NP, int TN>
 __global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
-  constexpr int NJ = NP / kFbwTileN;
+  constexpr int NJ = NP / TN;
+  constexpr int VQ = TN / 32;  // row quads of V per thread (8 or 4)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                              // [2][kFbwStageA]
   uint8_t* sB = smem + 2 * kFbwStageA;             // [2][kFbwStageB]
@@ -133,11 +154,14 @@ __global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
   const int mi = blockIdx.x / NJ, nj = blockIdx.x % NJ;
   const int split = blockIdx.y, k = blockIdx.z;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t r0 = (int64_t)split * a.rows_per_split;
-  const int64_t r1 = min(a.rtot, r0 + a.rows_per_split);
+  const int64_t beg = a.mrow ? a.mrow[k] : (int64_t)k * a.rtot;
+  const int64_t end = a.mrow ? a.mrow[a.K + 1 + k] : beg + a.rtot;
+  const int64_t rps = ((end - beg + a.nsplit - 1) / a.nsplit + kFbwRows - 1) / kFbwRows * kFbwRows;
+  const int64_t r0 = beg + (int64_t)split * rps;
+  const int64_t r1 = min(end, r0 + rps);
   const int nch = r1 > r0 ? (int)((r1 - r0 + kFbwRows - 1) / kFbwRows) : 0;
-  const float* Uk = a.X + (size_t)k * a.rtot * NP + 128 * mi;
-  const float* Vk = a.V + (size_t)k * a.rtot * NP + kFbwTileN * nj;
+  const float* Uk = a.X + 128 * mi;
+  const float* Vk = a.V + TN * nj;
 
   if (warp == 0) tc::tmem_alloc(const_cast<uint32_t*>(slot), 256);
   if (tid == 0) {
@@ -149,16 +173,17 @@ __global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
-  constexpr uint32_t idesc = tc::instr_desc(2, 128, kFbwTileN);
+  constexpr uint32_t idesc = tc::instr_desc(2, 128, TN);
   bool ok = true;
 
   // this thread's share of a chunk: U column ia for row quads qa, qa + 2, ..;
-  // V column tid for every row quad
+  // V column jb for row quads qb, qb + 256 / TN, ..
   const int ia = tid & 127, qa = tid >> 7;
+  const int jb = tid % TN, qb = tid / TN;
   for (int ch = 0; ch < nch; ++ch) {
     const int st = ch & 1;
     const int64_t rb = r0 + (int64_t)ch * kFbwRows;
-    float u[4][4], v[8][4];
+    float u[4][4], v[VQ][4];
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -167,11 +192,11 @@ __global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
         u[m][e] = r < r1 ? __ldg(Uk + r * NP + ia) : 0.f;
       }
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < VQ; ++q)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int64_t r = rb + 4 * q + e;
-        v[q][e] = r < r1 ? __ldg(Vk + r * NP + tid) : 0.f;
+        const int64_t r = rb + 4 * (qb + (256 / TN) * q) + e;
+        v[q][e] = r < r1 ? __ldg(Vk + r * NP + jb) : 0.f;
       }
     // the stage's previous chunk (ch - 2) must have been read by its MMAs
     if (ch >= 2 && !tc::mbar_wait_bounded(&done[st], (uint32_t)((ch >> 1) + 1) & 1u, kFbwWait))
@@ -184,8 +209,8 @@ __global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
           make_uint4(tc::to_tf32(u[m][0]), tc::to_tf32(u[m][1]), tc::to_tf32(u[m][2]),
                      tc::to_tf32(u[m][3]));
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      *reinterpret_cast<uint4*>(B + (tid >> 3) * 1024 + q * 128 + (tid & 7) * 16) =
+    for (int q = 0; q < VQ; ++q)
+      *reinterpret_cast<uint4*>(B + (jb >> 3) * 1024 + (qb + (256 / TN) * q) * 128 + (jb & 7) * 16) =
           make_uint4(tc::to_tf32(v[q][0]), tc::to_tf32(v[q][1]), tc::to_tf32(v[q][2]),
                      tc::to_tf32(v[q][3]));
     tc::fence_proxy_async();  // the stage's generic writes -> tensor core
@@ -206,12 +231,12 @@ __global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
   tc::fence_after_sync();
   if (!ok) set_status(a.status, HMM_STATUS_TIMEOUT);
   // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (states i), columns
-  // 128 (w / 4) .. + 127 (states j)
+  // TN / 2 (w / 4) .. + TN / 2 - 1 (states j)
   const int i = 128 * mi + 32 * (warp & 3) + lane;
-  const int jc = 128 * (warp >> 2);
-  float* dst = a.Cp + ((size_t)k * a.nsplit + split) * NP * NP + (size_t)i * NP + kFbwTileN * nj + jc;
+  const int jc = (TN / 2) * (warp >> 2);
+  float* dst = a.Cp + ((size_t)k * a.nsplit + split) * NP * NP + (size_t)i * NP + TN * nj + jc;
 #pragma unroll 1
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < TN / 64; ++c) {
     float y[32];
     tc::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(jc + 32 * c), y);
     tc::tmem_ld_wait();
@@ -237,8 +262,7 @@ __global__ void fbw_reduce_a_kernel(FbWideArgs a) {
     const float* c = a.Cp + (size_t)k * a.nsplit * a.NP * a.NP + (size_t)i * a.NP + j;
     float sum = 0.f;
     for (int p = 0; p < a.nsplit; ++p) sum += c[(size_t)p * a.NP * a.NP];
-    const int kmod = a.labelled ? 0 : k;
-    a.cnt_A[idx] = sum * __ldg(a.A + ((size_t)kmod * a.N + i) * a.N + j);
+    a.cnt_A[idx] = sum * __ldg(a.A + ((size_t)k * a.N + i) * a.N + j);
   }
 }
 
@@ -251,10 +275,14 @@ __global__ void fbw_emis_kernel(FbWideArgs a) {
   const int ld = a.M + 1;
   for (int m = 0; m < a.M; ++m) acc[j * ld + m] = 0.f;
   float pacc = 0.f;
-  const int64_t r0 = (int64_t)chunk * a.rows_per_chunk;
-  const int64_t r1 = min(a.rtot, r0 + a.rows_per_chunk);
-  const int32_t* sym = a.sym + (size_t)k * a.rtot;
-  const float* G = a.G + (size_t)k * a.rtot * a.NP + j;
+  // model k's rows [beg, end), cut into nchunks chunks
+  const int64_t beg = a.mrow ? a.mrow[k] : (int64_t)k * a.rtot;
+  const int64_t end = a.mrow ? a.mrow[a.K + 1 + k] : beg + a.rtot;
+  const int64_t rpc = (end - beg + a.nchunks - 1) / a.nchunks;
+  const int64_t r0 = beg + (int64_t)chunk * rpc;
+  const int64_t r1 = min(end, r0 + rpc);
+  const int32_t* sym = a.sym;
+  const float* G = a.G + j;
   auto add = [&](int code, float g) {
     if (code < 0) return;
     acc[j * ld + (code & 0xffffff)] += g;
@@ -303,16 +331,17 @@ __global__ void fbw_reduce_b_kernel(FbWideArgs a) {
 size_t fbw_emis_smem(int NP, int M) { return (size_t)NP * (M + 1) * 4; }
 
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
-  const int64_t rows = (int64_t)a.K * a.rtot;
-  const int64_t cblocks = (rows * 32 + 255) / 256;
-  if (a.NP == 256) fbw_combine_kernel<256><<<(unsigned)cblocks, 256, 0, st>>>(a);
+  const int64_t cblocks = (a.nrows * 32 + 255) / 256;
+  if (a.NP == 128) fbw_combine_kernel<128><<<(unsigned)cblocks, 256, 0, st>>>(a);
+  else if (a.NP == 256) fbw_combine_kernel<256><<<(unsigned)cblocks, 256, 0, st>>>(a);
   else if (a.NP == 512) fbw_combine_kernel<512><<<(unsigned)cblocks, 256, 0, st>>>(a);
   else return cudaErrorInvalidValue;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.rows_per_split % kFbwRows) return cudaErrorInvalidValue;
-  const dim3 gg((a.NP / 128) * (a.NP / kFbwTileN), a.nsplit, a.K);
-  auto gk = a.NP == 256 ? fbw_gemm_kernel<256> : fbw_gemm_kernel<512>;
+  const int tn = a.NP == 128 ? 128 : kFbwTileN;
+  const dim3 gg((a.NP / 128) * (a.NP / tn), a.nsplit, a.K);
+  auto gk = a.NP == 128 ? fbw_gemm_kernel<128, 128>
+                        : a.NP == 256 ? fbw_gemm_kernel<256, 256> : fbw_gemm_kernel<512, 256>;
   if ((e = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, kFbwSmem)) !=
       cudaSuccess)
     return e;

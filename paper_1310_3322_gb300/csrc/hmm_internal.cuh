@@ -43,6 +43,7 @@ struct WsLayout {
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
   size_t sc_coff, sc_P, sc_E;  // parallel-in-time forward: chunk offsets, products
   size_t w_X, w_Bh, w_V, w_G, w_xe, w_sym, w_Cp, w_Ep, w_Pp;  // adjoint above 128 states
+  size_t t_pos, t_mrow;                                       // TF32 adjoint: row offsets
   int w_nsplit, w_nchunks;
   int64_t w_rtot;
   int64_t sc_cap;              // chunk slots per model slot
@@ -565,15 +566,20 @@ struct FbWideArgs {
   const float* A;        // caller's [K][N][N]
   float* Cp;             // [K][nsplit][NP][NP]
   int nsplit;
-  int64_t rows_per_split;
   float* Ep;             // [K][nchunks][NP][M]
   float* Pp;             // [K][nchunks][NP]
   int nchunks;
-  int64_t rows_per_chunk;
   float* cnt_pi;
   float* cnt_A;
   float* cnt_B;
   int32_t* status;
+  int64_t nrows;            // rows of the buffers the combine kernel visits
+  // rows in the plan's order (TF32 adjoint, N_pad = 128); NULL: by sequence
+  const int64_t* pos_row;   // [positions] first row of the plan's position p
+  const int32_t* sorted;    // [positions] sequence at position p
+  const int32_t* n_valid;   // device count of positions
+  const int32_t* model_of_seq;  // labelled: [S]
+  const int64_t* mrow;      // [2 (K + 1)] model k's rows [mrow[k], mrow[K + 1 + k])
 };
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st);
 size_t fbw_emis_smem(int NP, int M);
@@ -656,7 +662,18 @@ struct MmaPassLaunch {
   int32_t* queue;
   int32_t* status;
   uint32_t wait_limit;
+  // TF32 adjoint (mma_pass_tf32.cu): every step's rows instead of checkpoints
+  float* xs;                    // [rows][NP] scaled alpha_t
+  float* bhs;                   // [rows][NP] scaled beta_t
+  int32_t* xe;                  // [rows] backward exponents
+  const int64_t* rp;            // [S] first row of each sequence (plan order)
+  int64_t rtot;                 // rows of a model's block (every sequence x every model)
 };
+// The TF32 adjoint's passes (row offsets first: rp, pos_row [positions],
+// mrow [2 (K + 1)]); fb_tf32_supported: its shared memory fits.
+bool fb_tf32_supported(int NP, int M);
+cudaError_t launch_fb_pass_tf32(int NP, const MmaPassLaunch& a, const int32_t* n_valid,
+                                int64_t* pos_row, int64_t* mrow, cudaStream_t st);
 // Tiles per CTA of the pass kernel for a batch of up to `tiles` tiles (the
 // plan's pass groups have this many tiles).
 int fb_pass_tiles_per_cta(int NP, int tiles);

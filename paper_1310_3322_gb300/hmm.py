@@ -64,6 +64,8 @@ _SIG = {
     "hmm_workspace_size": (_I32, [hmm_dims_t, ctypes.POINTER(hmm_seqs_t), _I32,
                                   ctypes.POINTER(ctypes.c_size_t)]),
     "hmm_max_states": (_I32, [_I32, _I32]),
+    "hmm_forward_backward_workspace_size": (_I32, [hmm_dims_t, ctypes.POINTER(hmm_seqs_t), _I32,
+                                                   ctypes.POINTER(ctypes.c_size_t)]),
     "hmm_forward": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _I32, _VP,
                            _VP, _VP, ctypes.c_size_t, _VP]),
     "hmm_forward_static": (_I32, [hmm_dims_t, _VP, _VP, _VP, ctypes.POINTER(hmm_seqs_t), _I32,
@@ -260,6 +262,14 @@ def hmm_workspace_size(dims: hmm_dims_t, seqs: Sequences, op: int) -> int:
     return int(out.value)
 
 
+def hmm_forward_backward_workspace_size(dims: hmm_dims_t, seqs: Sequences, precision: int) -> int:
+    out = ctypes.c_size_t(0)
+    c = seqs.c()
+    _check(lib().hmm_forward_backward_workspace_size(dims, ctypes.byref(c), precision,
+                                                     ctypes.byref(out)))
+    return int(out.value)
+
+
 def hmm_max_states(op: int, precision: int = HMM_FP32) -> int:
     return _check(lib().hmm_max_states(op, precision))
 
@@ -373,7 +383,7 @@ def hmm_forward_backward(pi, A, B, seqs: Sequences, weight=None, precision: int 
                   torch.empty((K, N, N), dtype=torch.float32, device=pi.device),
                   torch.empty((K, N, M), dtype=torch.float32, device=pi.device))
     ws = _ws(workspace, pi.device)
-    buf = ws.get(hmm_workspace_size(dims, seqs, HMM_OP_FORWARD_BACKWARD))
+    buf = ws.get(hmm_forward_backward_workspace_size(dims, seqs, precision))
     c = seqs.c()
     _check(lib().hmm_forward_backward(dims, _ptr(pi), _ptr(A), _ptr(B), ctypes.byref(c),
                                       _ptr(weight), precision, _ptr(loglik), _ptr(counts[0]),

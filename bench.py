@@ -759,6 +759,28 @@ def run_large(args, emit=True):
     tf32_ms = kt32["forward"][1] / max(kt32["forward"][0], 1)
     ll_tf32 = ll32.cpu().numpy()
 
+    # ---- the TF32 adjoint on the same data (every step's rows kept) ---------
+    fll32 = torch.empty_like(fll)
+    cnts32 = [torch.empty_like(c) for c in cnts]
+    ws32 = hmm.Workspace(dev)
+
+    def adj_tf32():
+        hmm.hmm_forward_backward(pi, A, B, lab, precision=hmm.HMM_TF32_MMA, loglik=fll32,
+                                 counts=cnts32, workspace=ws32)
+    adj_tf32()
+    torch.cuda.synchronize()
+    assert hmm.hmm_get_device_status(ws32) == 0
+    hmm.hmm_timing_reset()
+    hmm.hmm_timing_enable(True)
+    _time_steps(torch, adj_tf32, max(2, args.steps // 2), flush)
+    kta = {k2: v[1] / v[0] for k2, v in hmm.hmm_timing_read().items() if v[0]}
+    hmm.hmm_timing_enable(False)
+    fll_tf32 = fll32.cpu().numpy()
+    cnt_diff = [float(torch.linalg.vector_norm(a32 - a16) / torch.linalg.vector_norm(a16))
+                for a32, a16 in zip(cnts32, cnts)]
+    ws32 = None
+    torch.cuda.empty_cache()
+
     # ---- Viterbi of every sequence against all K models (FP32 SIMT) --------
     vsc = torch.empty((w.S, K), device=dev)
     vbest = torch.empty(w.S, dtype=torch.int32, device=dev)
@@ -788,6 +810,7 @@ def run_large(args, emit=True):
     f32_tf = 2.0 * N * N * sumT * K / (tf32_ms / 1e3) / 1e12
     a_flop = (8.0 * N * N + 10 * N) * sumT
     a_tf = a_flop / (kms["adjoint"] / 1e3) / 1e12
+    tf32_adj_ms = kta.get("adjoint_pass", 0.0) + kta.get("adjoint", 0.0)
     dom = "adjoint" if kms["adjoint"] >= kms["forward"] else "forward"
     achieved = a_tf if dom == "adjoint" else f_tf
 
@@ -804,6 +827,8 @@ def run_large(args, emit=True):
            "bf16_forward": error_stats(ll_bf16[eidx], ref, w.lengths[eidx]),
            "tf32_forward": error_stats(ll_tf32[eidx], ref, w.lengths[eidx]),
            "bf16_adjoint_loglik": error_stats(fll_bf16[eidx], lab_ref, w.lengths[eidx]),
+           "tf32_adjoint_loglik": error_stats(fll_tf32[eidx], lab_ref, w.lengths[eidx]),
+           "adjoint_counts_rel_l2_tf32_vs_bf16": cnt_diff,
            "argmax_agreement_bf16": float(np.mean(am_bf16[eidx] == ref_am))}
 
     # ---- end to end through the public API (host buffers) ------------------
@@ -899,6 +924,15 @@ def run_large(args, emit=True):
                    "forward_tf32": {"ms": tf32_ms, "tflops": f32_tf,
                                     "frac_tf32": f32_tf / tf32_tflops,
                                     "obs_models_per_s": sumT * K / (tf32_ms / 1e3)},
+                   "adjoint_tf32": {"ms": tf32_adj_ms, "pass_ms": kta.get("adjoint_pass", 0.0),
+                                    "counts_ms": kta.get("adjoint", 0.0),
+                                    "setup_plan_ms": kta.get("setup", 0.0),
+                                    "tflops": a_flop / (tf32_adj_ms / 1e3) / 1e12,
+                                    "frac_tf32": a_flop / (tf32_adj_ms / 1e3) / 1e12 / tf32_tflops,
+                                    "obs_per_s": sumT / (tf32_adj_ms / 1e3),
+                                    "note": "forward and backward passes (TF32 tcgen05) keeping "
+                                            "every step's rows, then gamma / xi (TF32 "
+                                            "contraction) / emission counts from the rows"},
                    "viterbi": {"ms": vit_ms, "kernel_ms": vkms,
                                "obs_models_per_s": sumT * K / (vit_ms / 1e3),
                                "scores_tflops": vs_tf, "scores_frac_fp32": vs_tf / fp32_peak,

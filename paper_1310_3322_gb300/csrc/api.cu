@@ -190,6 +190,16 @@ static bool scan_preferred(const hmm_dims_t& d, const hmm_seqs_t& q) {
   return pairs * NP * NP * NP <= ((int64_t)1 << 21) && pairs <= (int64_t)num_sms() * 32;
 }
 
+// Row chunks per model of the emission-count kernel above the row buffers:
+// at least two blocks per SM over the models, and about 2048 rows a chunk (a
+// block's rows are summed one after another, eight in flight per thread).
+static int emis_chunks(const hmm_dims_t& d, int64_t rows_per_model) {
+  int64_t nc = (2 * (int64_t)num_sms() + d.K - 1) / d.K;
+  const int64_t by_rows = (rows_per_model + 2047) / 2048;
+  if (by_rows > nc) nc = by_rows;
+  return (int)(nc < 1 ? 1 : (nc > 4096 ? 4096 : nc));
+}
+
 static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma,
                             int scan_L, bool tf32) {
   WsLayout L;
@@ -265,8 +275,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     const int tiles = (NP / 128) * (NP / 256);  // output tiles of the count contraction
     int ns = (2 * num_sms() + tiles * d.K - 1) / (tiles * d.K);
     L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
-    int nc = (2 * num_sms() + d.K - 1) / d.K;
-    L.w_nchunks = nc < 1 ? 1 : (nc > 512 ? 512 : nc);
+    L.w_nchunks = emis_chunks(d, rtot);
     L.w_Cp = off; off = align256(off + (size_t)slots * L.w_nsplit * NP * NP * 4);
     L.w_Ep = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * d.M * 4);
     L.w_Pp = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * 4);
@@ -310,8 +319,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.t_mrow = off; off = align256(off + 2 * ((size_t)d.K + 1) * 8);  // model row ranges
     int ns = (2 * num_sms() + d.K - 1) / d.K;
     L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
-    int nc = (2 * num_sms() + d.K - 1) / d.K;
-    L.w_nchunks = nc < 1 ? 1 : (nc > 512 ? 512 : nc);
+    L.w_nchunks = emis_chunks(d, nrows / (q.model_of_seq ? std::max(d.K, 1) : 1));
     L.w_Cp = off; off = align256(off + (size_t)d.K * L.w_nsplit * NP * NP * 4);
     L.w_Ep = off; off = align256(off + (size_t)d.K * L.w_nchunks * NP * d.M * 4);
     L.w_Pp = off; off = align256(off + (size_t)d.K * L.w_nchunks * NP * 4);
@@ -831,7 +839,8 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
   }
   if (op == HMM_OP_FORWARD_BACKWARD && dims.N > 32) {
     if (pad_states(dims.N) >= 256) {
-      if (fbw_emis_smem(pad_states(dims.N), dims.M) > 227 * 1024)
+      if (fbw_emis_smem(pad_states(dims.N), dims.M) > 227 * 1024 ||
+          !forward_cluster_fits(pad_states(dims.N), dims.M))
         return fail(HMM_ERR_UNSUPPORTED, "adjoint above 128 states: M=%d too large", dims.M);
     } else if (!fb_mma_supported(pad_states(dims.N), dims.M))
       return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports M <= 256 (M=%d)", dims.M);

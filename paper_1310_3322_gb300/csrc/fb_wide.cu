@@ -269,7 +269,9 @@ __global__ void fbw_reduce_a_kernel(FbWideArgs a) {
 // Per chunk of rows: Ep[k][chunk][j][m] = sum of G[r][j] over the chunk's rows
 // with symbol m, Pp[k][chunk][j] the same over rows at t = 0. Thread j owns
 // state j's accumulators (shared memory, row stride M + 1).
-__global__ void fbw_emis_kernel(FbWideArgs a) {
+constexpr int kEmisBatch = 32;
+
+__global__ void __launch_bounds__(512) fbw_emis_kernel(FbWideArgs a) {
   extern __shared__ float acc[];  // [NP][M + 1]
   const int chunk = blockIdx.x, k = blockIdx.y, j = threadIdx.x;
   const int ld = a.M + 1;
@@ -289,16 +291,17 @@ __global__ void fbw_emis_kernel(FbWideArgs a) {
     if (code >> 30) pacc += g;
   };
   int64_t r = r0;
-  // eight rows' loads in flight before their (ordered) shared-memory updates
-  for (; r + 8 <= r1; r += 8) {
-    int code[8];
-    float g[8];
+  // kEmisBatch rows' loads in flight before their (ordered) shared-memory
+  // updates (the accumulators fill shared memory: few blocks share an SM)
+  for (; r + kEmisBatch <= r1; r += kEmisBatch) {
+    int code[kEmisBatch];
+    float g[kEmisBatch];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) code[u] = __ldg(sym + r + u);
+    for (int u = 0; u < kEmisBatch; ++u) code[u] = __ldg(sym + r + u);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) g[u] = __ldg(G + (r + u) * a.NP);
+    for (int u = 0; u < kEmisBatch; ++u) g[u] = __ldg(G + (r + u) * a.NP);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) add(code[u], g[u]);
+    for (int u = 0; u < kEmisBatch; ++u) add(code[u], g[u]);
   }
   for (; r < r1; ++r) add(__ldg(sym + r), __ldg(G + r * a.NP));
   float* E = a.Ep + (((size_t)k * a.nchunks + chunk) * a.NP + j) * a.M;

@@ -31,6 +31,7 @@ CASES = {
                                ("large", 40, ("uniform", 10, 40), {"K": 1, "N": 512, "M": 200})),
     "adjoint-bf16-n64": ("adjoint", hmm.HMM_BF16_MMA, ("training", 300, ("uniform", 20, 200), {"K": 2})),
     "adjoint-bf16-n128": ("adjoint", hmm.HMM_BF16_MMA, ("large", 200, ("uniform", 20, 200), {"K": 2})),
+    "adjoint-tf32-n128": ("adjoint", hmm.HMM_TF32_MMA, ("large", 200, ("uniform", 20, 200), {"K": 2})),
     "adjoint-bf16-n512": ("adjoint", hmm.HMM_BF16_MMA,
                           ("cuhmm", 130, ("uniform", 10, 60), {"K": 1, "M": 64})),
 }

@@ -231,9 +231,12 @@ def setup_launches(S: int, ordered: bool = True) -> int:
     return 1 if (S <= 4096 or not ordered) else 3
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, n_seqs=None):
     """Per-launch DRAM bytes of `kernel` (for the adjoint: its two launches)
-    from a committed ncu capture, or None when a source changed since."""
+    from a committed ncu capture of the full workload, or None when a source
+    changed since or the batch is not the full one (n_seqs set)."""
+    if n_seqs is not None:
+        return None
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f).get(kernel)
@@ -419,7 +422,7 @@ def run_gpu(args, emit=True):
     achieved = flops[dom] / (per_launch[dom] / 1e3) / 1e12
     roofline = {
         "bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-        "frac": achieved / peak, "traffic": traffic_for(dom),
+        "frac": achieved / peak, "traffic": traffic_for(dom, args.n_seqs),
         "peak_basis": peak_basis, "frac_of_nominal": achieved / nominal,
         "launch_ms": per_launch[dom],
     }
@@ -913,7 +916,7 @@ def run_large(args, emit=True):
                                     "backward, xi) over its two launches (passes + segment "
                                     "ranges); forward 2N^2 per obs*model",
                      "traffic": traffic_for("adjoint_mma" if dom == "adjoint" else
-                                            "forward_mma")},
+                                            "forward_mma", args.n_seqs)},
         "error_vs_oracle": err,
         "phases": {"forward": {"ms": kms["forward"], "tflops": f_tf, "frac_bf16": f_tf / peak,
                                "obs_models_per_s": sumT * K / (kms["forward"] / 1e3)},
@@ -1347,7 +1350,7 @@ def run_wide(args):
                      "launch_ms": kms["forward"], "peak_basis": f"dense BF16, {basis} (burst)",
                      "busy_sms": busy,
                      "frac_of_busy_sms": achieved / (peak * busy / sm_count),
-                     "traffic": traffic_for("forward_cluster")},
+                     "traffic": traffic_for("forward_cluster", args.n_seqs)},
         "kernel_ms": kms,
         "baum_welch": {"ms_per_iteration": bw_ms, "value": units / (bw_ms / 1e3), "unit": UNIT,
                        "kernel_ms": bkms, "loglik_sum_first_last": [ll0, ll1],

@@ -190,14 +190,17 @@ static bool scan_preferred(const hmm_dims_t& d, const hmm_seqs_t& q) {
   return pairs * NP * NP * NP <= ((int64_t)1 << 21) && pairs <= (int64_t)num_sms() * 32;
 }
 
-// Row chunks per model of the emission-count kernel above the row buffers:
-// at least two blocks per SM over the models, and about 2048 rows a chunk (a
-// block's rows are summed one after another, eight in flight per thread).
-static int emis_chunks(const hmm_dims_t& d, int64_t rows_per_model) {
-  int64_t nc = (2 * (int64_t)num_sms() + d.K - 1) / d.K;
-  const int64_t by_rows = (rows_per_model + 2047) / 2048;
-  if (by_rows > nc) nc = by_rows;
-  return (int)(nc < 1 ? 1 : (nc > 4096 ? 4096 : nc));
+// Emission-count buffers of the adjoint from per-step rows (fb_wide.cu).
+static void emis_layout(WsLayout& L, size_t& off, const hmm_dims_t& d, int NP, int64_t nrows) {
+  const FbwEmisSizes z = fbw_emis_sizes(d.K, d.M, NP, nrows);
+  L.w_ech = z.ech;
+  L.w_ncc = (int)z.ncc;
+  L.w_ecb = off; off = align256(off + ((size_t)d.K + 1) * 4);
+  L.w_eh = off; off = align256(off + (size_t)z.ehist * 4);
+  L.w_eb = off; off = align256(off + (size_t)z.ebase * 4);
+  L.w_epb = off; off = align256(off + (size_t)z.ebase * 4);
+  L.w_el = off; off = align256(off + (size_t)z.elist * 4);
+  L.w_ep = off; off = align256(off + (size_t)z.epart * 4);
 }
 
 static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bool mma,
@@ -275,10 +278,8 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     const int tiles = (NP / 128) * (NP / 256);  // output tiles of the count contraction
     int ns = (2 * num_sms() + tiles * d.K - 1) / (tiles * d.K);
     L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
-    L.w_nchunks = emis_chunks(d, rtot);
     L.w_Cp = off; off = align256(off + (size_t)slots * L.w_nsplit * NP * NP * 4);
-    L.w_Ep = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * d.M * 4);
-    L.w_Pp = off; off = align256(off + (size_t)slots * L.w_nchunks * NP * 4);
+    emis_layout(L, off, d, NP, slots * rtot);
   } else if (op == HMM_OP_FORWARD_BACKWARD && mma && tf32) {
     // TF32 adjoint (N_pad = 128): the tile plan with one tile per pass group,
     // then every step's rows (model blocks of rtot rows unless labelled), row
@@ -319,10 +320,8 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.t_mrow = off; off = align256(off + 2 * ((size_t)d.K + 1) * 8);  // model row ranges
     int ns = (2 * num_sms() + d.K - 1) / d.K;
     L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
-    L.w_nchunks = emis_chunks(d, nrows / (q.model_of_seq ? std::max(d.K, 1) : 1));
     L.w_Cp = off; off = align256(off + (size_t)d.K * L.w_nsplit * NP * NP * 4);
-    L.w_Ep = off; off = align256(off + (size_t)d.K * L.w_nchunks * NP * d.M * 4);
-    L.w_Pp = off; off = align256(off + (size_t)d.K * L.w_nchunks * NP * 4);
+    emis_layout(L, off, d, NP, nrows);
   } else if (op == HMM_OP_FORWARD_BACKWARD && mma) {
     // tensor-core adjoint: tile plan and work lists; per tile the pass
     // kernel's checkpoints (alpha and Y images, exponents, last row sums);
@@ -570,6 +569,17 @@ static int zero_counts(const hmm_dims_t& d, float* cnt_pi, float* cnt_A, float* 
   return HMM_OK;
 }
 
+static void emis_args(FbWideArgs& c, const WsLayout& L, void* ws) {
+  c.cbase = at<int32_t>(ws, L.w_ecb);
+  c.ehist = at<int32_t>(ws, L.w_eh);
+  c.ebase = at<int32_t>(ws, L.w_eb);
+  c.epbase = at<int32_t>(ws, L.w_epb);
+  c.elist = at<int32_t>(ws, L.w_el);
+  c.epart = at<float>(ws, L.w_ep);
+  c.ncc = L.w_ncc;
+  c.ech = L.w_ech;
+}
+
 // hmm_forward_backward above 128 states (arguments already checked except the
 // workspace): setup, the tensor-core forward and backward passes keeping their
 // per-step rows, then the count kernels of fb_wide.cu.
@@ -583,7 +593,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
                 "above 128 states the adjoint scores every sequence against every model "
                 "(model_of_seq only with K = 1)");
   const int NP = pad_states(dims.N);
-  if (fbw_emis_smem(NP, dims.M) > 227 * 1024 || !forward_cluster_fits(NP, dims.M))
+  if (!forward_cluster_fits(NP, dims.M))
     return fail(HMM_ERR_UNSUPPORTED, "adjoint above 128 states: M=%d too large", dims.M);
   const WsLayout L = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD, true);
   int rc = check_ws(ws, ws_bytes, L);
@@ -651,9 +661,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.A = A;
   c.Cp = at<float>(ws, L.w_Cp);
   c.nsplit = L.w_nsplit;
-  c.Ep = at<float>(ws, L.w_Ep);
-  c.Pp = at<float>(ws, L.w_Pp);
-  c.nchunks = L.w_nchunks;
+  emis_args(c, L, ws);
   c.nrows = (int64_t)dims.K * L.w_rtot;
   c.cnt_pi = cnt_pi;
   c.cnt_A = cnt_A;
@@ -839,8 +847,7 @@ int hmm_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs, hmm_op_t op, siz
   }
   if (op == HMM_OP_FORWARD_BACKWARD && dims.N > 32) {
     if (pad_states(dims.N) >= 256) {
-      if (fbw_emis_smem(pad_states(dims.N), dims.M) > 227 * 1024 ||
-          !forward_cluster_fits(pad_states(dims.N), dims.M))
+      if (!forward_cluster_fits(pad_states(dims.N), dims.M))
         return fail(HMM_ERR_UNSUPPORTED, "adjoint above 128 states: M=%d too large", dims.M);
     } else if (!fb_mma_supported(pad_states(dims.N), dims.M))
       return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports M <= 256 (M=%d)", dims.M);
@@ -1206,7 +1213,7 @@ static int fb_tf32(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   const int NP = pad_states(dims.N);
   if (NP != 128)
     return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint needs 64 < N <= 128 (N=%d: use HMM_FP32)", dims.N);
-  if (!fb_tf32_supported(NP, dims.M) || fbw_emis_smem(NP, dims.M) > 227 * 1024)
+  if (!fb_tf32_supported(NP, dims.M))
     return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint: M=%d too large", dims.M);
   if (seqs->model_of_seq && dims.K > 65536)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports K <= 65536 labelled models");
@@ -1311,9 +1318,7 @@ static int fb_tf32(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.A = A;
   c.Cp = at<float>(ws, L.w_Cp);
   c.nsplit = L.w_nsplit;
-  c.Ep = at<float>(ws, L.w_Ep);
-  c.Pp = at<float>(ws, L.w_Pp);
-  c.nchunks = L.w_nchunks;
+  emis_args(c, L, ws);
   c.cnt_pi = cnt_pi;
   c.cnt_A = cnt_A;
   c.cnt_B = cnt_B;

@@ -13,9 +13,12 @@
 // operands (U and V rounded to TF32, relative error <= 2^-11 each; FP32
 // accumulation) as a split-K GEMM whose partial tiles are summed in a fixed
 // order. Emission and initial counts are
-// sums of gamma rows by symbol and at t = 0, per chunk of rows in shared
-// memory (thread j owns state j: no atomics), then over chunks in a fixed
-// order. Everything is bitwise reproducible.
+// sums of gamma rows by symbol and at t = 0: the rows of each model sorted by
+// symbol (a stable counting sort), whole rows summed per piece of a symbol's
+// rows, then the pieces in a fixed order. Everything is bitwise
+// reproducible.
+#include <algorithm>
+
 #include "hmm_internal.cuh"
 #include "tc.cuh"
 
@@ -266,72 +269,280 @@ __global__ void fbw_reduce_a_kernel(FbWideArgs a) {
   }
 }
 
-// Per chunk of rows: Ep[k][chunk][j][m] = sum of G[r][j] over the chunk's rows
-// with symbol m, Pp[k][chunk][j] the same over rows at t = 0. Thread j owns
-// state j's accumulators (shared memory, row stride M + 1).
-constexpr int kEmisBatch = 32;
+// Emission and initial counts by symbol: a stable counting sort of each
+// model's rows by bucket (bucket m < M: rows whose symbol is m; bucket M: the
+// rows at t = 0, which also sit in their symbol's bucket), then one warp per
+// piece of at most kEmisPiece entries of a bucket sums those gamma rows in
+// registers (whole rows, NP / 4 float4 per row), then the pieces of every
+// bucket are summed in order. The sort and the pieces depend on the symbols
+// only, so the counts are bitwise reproducible.
+constexpr int kEmisPiece = 256;
 
-__global__ void __launch_bounds__(512) fbw_emis_kernel(FbWideArgs a) {
-  extern __shared__ float acc[];  // [NP][M + 1]
-  const int chunk = blockIdx.x, k = blockIdx.y, j = threadIdx.x;
-  const int ld = a.M + 1;
-  for (int m = 0; m < a.M; ++m) acc[j * ld + m] = 0.f;
-  float pacc = 0.f;
-  // model k's rows [beg, end), cut into nchunks chunks
-  const int64_t beg = a.mrow ? a.mrow[k] : (int64_t)k * a.rtot;
-  const int64_t end = a.mrow ? a.mrow[a.K + 1 + k] : beg + a.rtot;
-  const int64_t rpc = (end - beg + a.nchunks - 1) / a.nchunks;
-  const int64_t r0 = beg + (int64_t)chunk * rpc;
-  const int64_t r1 = min(end, r0 + rpc);
-  const int32_t* sym = a.sym;
-  const float* G = a.G + j;
-  auto add = [&](int code, float g) {
-    if (code < 0) return;
-    acc[j * ld + (code & 0xffffff)] += g;
-    if (code >> 30) pacc += g;
-  };
-  int64_t r = r0;
-  // kEmisBatch rows' loads in flight before their (ordered) shared-memory
-  // updates (the accumulators fill shared memory: few blocks share an SM)
-  for (; r + kEmisBatch <= r1; r += kEmisBatch) {
-    int code[kEmisBatch];
-    float g[kEmisBatch];
-#pragma unroll
-    for (int u = 0; u < kEmisBatch; ++u) code[u] = __ldg(sym + r + u);
-#pragma unroll
-    for (int u = 0; u < kEmisBatch; ++u) g[u] = __ldg(G + (r + u) * a.NP);
-#pragma unroll
-    for (int u = 0; u < kEmisBatch; ++u) add(code[u], g[u]);
-  }
-  for (; r < r1; ++r) add(__ldg(sym + r), __ldg(G + r * a.NP));
-  float* E = a.Ep + (((size_t)k * a.nchunks + chunk) * a.NP + j) * a.M;
-  for (int m = 0; m < a.M; ++m) E[m] = acc[j * ld + m];
-  a.Pp[((size_t)k * a.nchunks + chunk) * a.NP + j] = pacc;
+__device__ __forceinline__ void model_rows(const FbWideArgs& a, int k, int64_t& beg,
+                                           int64_t& end) {
+  beg = a.mrow ? a.mrow[k] : (int64_t)k * a.rtot;
+  end = a.mrow ? a.mrow[a.K + 1 + k] : beg + a.rtot;
 }
 
-__global__ void fbw_reduce_b_kernel(FbWideArgs a) {
-  const int64_t nB = (int64_t)a.K * a.N * a.M, nP = (int64_t)a.K * a.N;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nB + nP;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    if (idx < nB) {
-      const int k = (int)(idx / ((int64_t)a.N * a.M));
-      const int j = (int)((idx / a.M) % a.N), m = (int)(idx % a.M);
-      const float* e = a.Ep + ((size_t)k * a.nchunks * a.NP + j) * a.M + m;
-      float sum = 0.f;
-      for (int c = 0; c < a.nchunks; ++c) sum += e[(size_t)c * a.NP * a.M];
-      a.cnt_B[idx] = sum;
-    } else {
-      const int64_t q = idx - nB;
-      const int k = (int)(q / a.N), j = (int)(q % a.N);
-      const float* p = a.Pp + (size_t)k * a.nchunks * a.NP + j;
-      float sum = 0.f;
-      for (int c = 0; c < a.nchunks; ++c) sum += p[(size_t)c * a.NP];
-      a.cnt_pi[q] = sum;
+// Exclusive scan of v over a block of 1024 threads; total = the sum.
+__device__ __forceinline__ int scan1024(int v, int* s, int& total) {
+  const int tid = threadIdx.x;
+  s[tid] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int y = tid >= o ? s[tid - o] : 0;
+    __syncthreads();
+    s[tid] += y;
+    __syncthreads();
+  }
+  total = s[1023];
+  const int r = s[tid] - v;
+  __syncthreads();
+  return r;
+}
+
+// One block: cbase[k] = first chunk of model k (ceil(rows / ech) chunks a
+// model), cbase[K] = all chunks.
+__global__ void __launch_bounds__(1024) fbw_echunks_kernel(FbWideArgs a) {
+  __shared__ int s[1024];
+  const int per = (a.K + 1023) / 1024;
+  const int k0 = min(a.K, (int)threadIdx.x * per), k1 = min(a.K, k0 + per);
+  auto chunks = [&](int k) {
+    int64_t beg, end;
+    model_rows(a, k, beg, end);
+    return end > beg ? (int)((end - beg + a.ech - 1) / a.ech) : 0;
+  };
+  int v = 0;
+  for (int k = k0; k < k1; ++k) v += chunks(k);
+  int total;
+  int o = scan1024(v, s, total);
+  for (int k = k0; k < k1; ++k) {
+    a.cbase[k] = o;
+    o += chunks(k);
+  }
+  if (threadIdx.x == 0) a.cbase[a.K] = total;
+}
+
+// Chunk g (< cbase[K]): its model k (the last one whose first chunk is <= g)
+// and its rows [r0, r1).
+__device__ __forceinline__ int chunk_rows(const FbWideArgs& a, int g, int64_t& r0, int64_t& r1) {
+  int lo = 0, hi = a.K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.cbase[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  int64_t beg, end;
+  model_rows(a, lo, beg, end);
+  r0 = beg + (int64_t)(g - a.cbase[lo]) * a.ech;
+  r1 = min(end, r0 + a.ech);
+  return lo;
+}
+
+// ehist[m][g] = entries of bucket m among the rows of chunk g.
+__global__ void __launch_bounds__(256) fbw_ehist_kernel(FbWideArgs a) {
+  extern __shared__ int h[];  // [M + 1]
+  const int g = blockIdx.x, nb = a.M + 1;
+  if (g >= a.cbase[a.K]) return;
+  for (int m = threadIdx.x; m < nb; m += blockDim.x) h[m] = 0;
+  __syncthreads();
+  int64_t r0, r1;
+  chunk_rows(a, g, r0, r1);
+#pragma unroll 4
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const int code = __ldg(a.sym + r);
+    if (code < 0) continue;
+    atomicAdd(&h[code & 0xffffff], 1);
+    if (code >> 30) atomicAdd(&h[a.M], 1);
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < nb; m += blockDim.x) a.ehist[(size_t)m * a.ncc + g] = h[m];
+}
+
+// One warp per bucket b = (k, m): ehist[m][g] over model k's chunks g
+// becomes the bucket's entries in the chunks before g, ebase[b] its total.
+__global__ void fbw_escan1_kernel(FbWideArgs a) {
+  const int nb = a.M + 1;
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= (int64_t)a.K * nb) return;
+  const int k = (int)(b / nb), m = (int)(b % nb);
+  int* hrow = a.ehist + (size_t)m * a.ncc;
+  const int g1 = min(a.cbase[k + 1], a.ncc);
+  int carry = 0;
+  for (int g0 = a.cbase[k]; g0 < g1; g0 += 32) {
+    const int g = g0 + lane;
+    const int v = g < g1 ? hrow[g] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(HMM_FULL_MASK, x, o);
+      if (lane >= o) x += y;
+    }
+    if (g < g1) hrow[g] = carry + x - v;
+    carry += __shfl_sync(HMM_FULL_MASK, x, 31);
+  }
+  if (lane == 0) a.ebase[b] = carry;
+}
+
+// One block: ebase becomes the first entry of every bucket (ebase[nbk] = all
+// entries) and epbase the first piece (epbase[nbk] = all pieces).
+__global__ void __launch_bounds__(1024) fbw_escan2_kernel(FbWideArgs a) {
+  __shared__ int s[1024];
+  const int nbk = a.K * (a.M + 1);
+  const int per = (nbk + 1023) / 1024;
+  const int b0 = min(nbk, (int)threadIdx.x * per), b1 = min(nbk, b0 + per);
+  int se = 0, sp = 0;
+  for (int b = b0; b < b1; ++b) {
+    const int t = a.ebase[b];
+    se += t;
+    sp += (t + kEmisPiece - 1) / kEmisPiece;
+  }
+  int te, tp;
+  int oe = scan1024(se, s, te);
+  int op = scan1024(sp, s, tp);
+  for (int b = b0; b < b1; ++b) {
+    const int t = a.ebase[b];
+    a.ebase[b] = oe;
+    a.epbase[b] = op;
+    oe += t;
+    op += (t + kEmisPiece - 1) / kEmisPiece;
+  }
+  if (threadIdx.x == 0) {
+    a.ebase[nbk] = te;
+    a.epbase[nbk] = tp;
+  }
+}
+
+// One warp per chunk, its rows in order (256 codes loaded at a time): each
+// entry goes to elist at its bucket's base + the chunk's offset + its rank
+// among the chunk's earlier entries of the bucket.
+__global__ void __launch_bounds__(32) fbw_escatter_kernel(FbWideArgs a) {
+  extern __shared__ int cur[];  // [M + 1] next position per bucket
+  const int g = blockIdx.x, nb = a.M + 1, lane = threadIdx.x;
+  if (g >= a.cbase[a.K]) return;
+  int64_t r0, r1;
+  const int k = chunk_rows(a, g, r0, r1);
+  const int64_t bk = (int64_t)k * nb;
+  for (int m = lane; m < nb; m += 32) cur[m] = a.ebase[bk + m] + a.ehist[(size_t)m * a.ncc + g];
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t rb = r0; rb < r1; rb += 256) {
+    int code[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t r = rb + u * 32 + lane;
+      code[u] = r < r1 ? __ldg(a.sym + r) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int32_t r = (int32_t)(rb + u * 32 + lane);
+      const int key = code[u] < 0 ? -1 : (code[u] & 0xffffff);
+      const unsigned same = __match_any_sync(HMM_FULL_MASK, key);
+      const int pos = key >= 0 ? cur[key] + __popc(same & lt) : 0;
+      __syncwarp();
+      if (key >= 0) {
+        a.elist[pos] = r;
+        if ((same & lt) == 0) cur[key] += __popc(same);  // first lane of the group
+      }
+      const bool first = key >= 0 && (code[u] >> 30) != 0;
+      const unsigned fm = __ballot_sync(HMM_FULL_MASK, first);
+      if (first) a.elist[cur[a.M] + __popc(fm & lt)] = r;
+      __syncwarp();
+      if (lane == 0) cur[a.M] += __popc(fm);
+      __syncwarp();
     }
   }
 }
 
-size_t fbw_emis_smem(int NP, int M) { return (size_t)NP * (M + 1) * 4; }
+// Warps over pieces (grid-stride): piece p of bucket b sums the gamma rows of
+// entries ebase[b] + (p - epbase[b]) kEmisPiece ... (at most kEmisPiece) into
+// epart[p]; lane l holds the float4 groups l, l + 32, ... of a row.
+template <int NP>
+__global__ void __launch_bounds__(256) fbw_epiece_kernel(FbWideArgs a) {
+  constexpr int Q = NP / 128;   // float4 groups per lane
+  constexpr int UN = 8 / Q;     // rows in flight per lane (4 KB per warp)
+  const int nbk = a.K * (a.M + 1);
+  const int npieces = a.epbase[nbk];
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float4* G = reinterpret_cast<const float4*>(a.G);
+  for (int64_t p = wid; p < npieces; p += nw) {
+    int lo = 0, hi = nbk - 1;  // the last bucket whose first piece is <= p
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(a.epbase + mid) <= p) lo = mid;
+      else hi = mid - 1;
+    }
+    const int e0 = __ldg(a.ebase + lo) + (int)(p - __ldg(a.epbase + lo)) * kEmisPiece;
+    const int e1 = min(__ldg(a.ebase + lo + 1), e0 + kEmisPiece);
+    float4 acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int eb = e0; eb < e1; eb += 32) {
+      const int n = min(32, e1 - eb);
+      const int myrow = lane < n ? __ldg(a.elist + eb + lane) : 0;
+      for (int u0 = 0; u0 < n; u0 += UN) {
+        float4 g[UN][Q];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+          const int64_t row = __shfl_sync(HMM_FULL_MASK, myrow, u0 + u);
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+            g[u][q] = u0 + u < n ? __ldg(G + row * (NP / 4) + lane + 32 * q)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < UN; ++u)
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            acc[q].x += g[u][q].x;
+            acc[q].y += g[u][q].y;
+            acc[q].z += g[u][q].z;
+            acc[q].w += g[u][q].w;
+          }
+      }
+    }
+    float4* out = reinterpret_cast<float4*>(a.epart + p * NP);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) out[lane + 32 * q] = acc[q];
+  }
+}
+
+// cnt_B[k][j][m] (bucket m < M) and cnt_pi[k][j] (bucket M): the pieces of
+// the bucket summed in order.
+__global__ void fbw_ereduce_kernel(FbWideArgs a) {
+  const int nb = a.M + 1;
+  const int64_t n = (int64_t)a.K * nb * a.N;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % a.N);
+    const int b = (int)(idx / a.N);
+    const int k = b / nb, m = b % nb;
+    const int p1 = a.epbase[b + 1];
+    float sum = 0.f;
+    for (int p = a.epbase[b]; p < p1; ++p) sum += a.epart[(size_t)p * a.NP + j];
+    if (m < a.M) a.cnt_B[((size_t)k * a.N + j) * a.M + m] = sum;
+    else a.cnt_pi[(size_t)k * a.N + j] = sum;
+  }
+}
+
+FbwEmisSizes fbw_emis_sizes(int K, int M, int NP, int64_t nrows) {
+  FbwEmisSizes z;
+  const int64_t rows = nrows > 0 ? nrows : 1;
+  int64_t ech = (rows + 2047) / 2048;
+  if (ech < 2048) ech = 2048;
+  z.ech = (ech + 255) & ~(int64_t)255;
+  z.ncc = (rows + z.ech - 1) / z.ech + K;  // sum over models of ceil(rows_k / ech)
+  const int64_t nbk = (int64_t)K * (M + 1);
+  z.ehist = (int64_t)(M + 1) * z.ncc;
+  z.ebase = nbk + 1;
+  z.elist = 2 * rows;  // a row is in its symbol's bucket, at t = 0 also in bucket M
+  // sum over buckets of ceil(entries / piece) <= entries / piece + non-empty buckets
+  z.epart = (z.elist / kEmisPiece + 1 + std::min(nbk, z.elist)) * NP;
+  return z;
+}
 
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
   const int64_t cblocks = (a.nrows * 32 + 255) / 256;
@@ -352,13 +563,26 @@ cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   fbw_reduce_a_kernel<<<1024, 256, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smem = fbw_emis_smem(a.NP, a.M);
-  if ((e = cudaFuncSetAttribute(fbw_emis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem)) != cudaSuccess)
-    return e;
-  fbw_emis_kernel<<<dim3(a.nchunks, a.K), a.NP, smem, st>>>(a);
+  const size_t hsm = (size_t)(a.M + 1) * 4;
+  // entries (<= 2 nrows) and row indices are 32-bit
+  if (hsm > 48 * 1024 || 2 * a.nrows > INT32_MAX) return cudaErrorInvalidValue;
+  fbw_echunks_kernel<<<1, 1024, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  fbw_reduce_b_kernel<<<1024, 256, 0, st>>>(a);
+  fbw_ehist_kernel<<<a.ncc, 256, hsm, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int64_t nbk = (int64_t)a.K * (a.M + 1);
+  fbw_escan1_kernel<<<(unsigned)((nbk * 32 + 255) / 256), 256, 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  fbw_escan2_kernel<<<1, 1024, 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  fbw_escatter_kernel<<<a.ncc, 32, hsm, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const unsigned pg = (unsigned)(8 * num_sms());
+  if (a.NP == 128) fbw_epiece_kernel<128><<<pg, 256, 0, st>>>(a);
+  else if (a.NP == 256) fbw_epiece_kernel<256><<<pg, 256, 0, st>>>(a);
+  else fbw_epiece_kernel<512><<<pg, 256, 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  fbw_ereduce_kernel<<<1024, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

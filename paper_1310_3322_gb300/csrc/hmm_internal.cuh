@@ -42,9 +42,11 @@ struct WsLayout {
   size_t m_sorted, m_tmp, m_keys, m_tiles, m_ntiles, m_ckpt, m_scr, m_gexp, m_gbuf, m_pscr;
   size_t wimg;         // tensor-core forward above 128 states: BF16 A^T images
   size_t sc_coff, sc_P, sc_E;  // parallel-in-time forward: chunk offsets, products
-  size_t w_X, w_Bh, w_V, w_G, w_xe, w_sym, w_Cp, w_Ep, w_Pp;  // adjoint above 128 states
+  size_t w_X, w_Bh, w_V, w_G, w_xe, w_sym, w_Cp;  // adjoint above 128 states
+  size_t w_ecb, w_eh, w_eb, w_epb, w_el, w_ep;      // its emission-count sort and pieces
   size_t t_pos, t_mrow;                                       // TF32 adjoint: row offsets
-  int w_nsplit, w_nchunks;
+  int w_nsplit, w_ncc;
+  int64_t w_ech;
   int64_t w_rtot;
   int64_t sc_cap;              // chunk slots per model slot
   size_t s_ckA, s_ckB, s_ckE, s_sig, s_skip;  // SIMT adjoint with segment ranges
@@ -566,9 +568,16 @@ struct FbWideArgs {
   const float* A;        // caller's [K][N][N]
   float* Cp;             // [K][nsplit][NP][NP]
   int nsplit;
-  float* Ep;             // [K][nchunks][NP][M]
-  float* Pp;             // [K][nchunks][NP]
-  int nchunks;
+  // emission counts: model k's rows in chunks of ech rows, chunks of all
+  // models numbered from cbase[k]; bucket (k, m) = row symbol m, (k, M) = t 0
+  int32_t* cbase;        // [K + 1] first chunk of each model
+  int32_t* ehist;        // [M + 1][ncc] entries per (bucket, chunk), then offsets
+  int32_t* ebase;        // [K (M + 1) + 1] first entry of each bucket
+  int32_t* epbase;       // [K (M + 1) + 1] first piece of each bucket
+  int32_t* elist;        // [2 nrows] rows of each bucket in ascending order
+  float* epart;          // [pieces][NP] gamma sums of the pieces
+  int ncc;               // chunk capacity (>= cbase[K])
+  int64_t ech;           // rows per chunk
   float* cnt_pi;
   float* cnt_A;
   float* cnt_B;
@@ -582,7 +591,12 @@ struct FbWideArgs {
   const int64_t* mrow;      // [2 (K + 1)] model k's rows [mrow[k], mrow[K + 1 + k])
 };
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st);
-size_t fbw_emis_smem(int NP, int M);
+// Emission-count buffers of launch_fbw_counts for `nrows` rows (element
+// counts; cbase has K + 1, epbase as many as ebase).
+struct FbwEmisSizes {
+  int64_t ech, ncc, ehist, ebase, elist, epart;
+};
+FbwEmisSizes fbw_emis_sizes(int K, int M, int NP, int64_t nrows);
 
 // The recognition forward above 128 states with A^T streamed, one CTA per
 // tile (loglik, argmax; xs NULL): where the cluster kernel has no room.

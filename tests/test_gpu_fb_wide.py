@@ -31,6 +31,10 @@ CASES = [
     # many short sequences: 64- and 128-row tiles of the cluster passes
     ("cuhmm", 700, ("uniform", 1, 10), {"K": 1, "N": 256, "M": 32}),
     ("cuhmm", 1300, ("uniform", 1, 8), {"K": 1, "N": 256, "M": 32}),
+    # 512 padded states with more symbols than a state-by-symbol table in
+    # shared memory would hold; three symbols: buckets of several pieces
+    ("cuhmm", 40, ("uniform", 1, 50), {"K": 2, "N": 400, "M": 160}),
+    ("cuhmm", 40, ("uniform", 50, 150), {"K": 1, "N": 256, "M": 3}),
 ]
 
 
@@ -149,5 +153,5 @@ def test_wide_adjoint_argument_checks():
     with pytest.raises(hmm.HmmError):  # labelled pairs with K > 1 above 128 states
         hmm.hmm_forward_backward(*two, seqs, precision=hmm.HMM_BF16_MMA)
     big_m = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 1, 300, 200)]
-    with pytest.raises(hmm.HmmError):  # emission accumulators beyond shared memory
+    with pytest.raises(hmm.HmmError):  # emission slice beyond the cluster forward's shared memory
         hmm.hmm_forward_backward(*big_m, seqs.all_models(), precision=hmm.HMM_BF16_MMA)

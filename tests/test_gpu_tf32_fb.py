@@ -40,6 +40,8 @@ CASES = [
     ("large", 90, ("uniform", 1, 200), {"K": 3, "N": 100, "M": 200}),
     ("training", 120, ("uniform", 1, 400), {"K": 3, "N": 65, "M": 40}),
     ("large", 40, ("uniform", 600, 1200), {"K": 2}),
+    # four symbols: every symbol's rows span many pieces of the emission sums
+    ("large", 60, ("uniform", 200, 600), {"K": 2, "N": 128, "M": 4}),
 ]
 
 

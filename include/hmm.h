@@ -250,8 +250,10 @@ int hmm_viterbi(hmm_dims_t dims, const float* pi, const float* A, const float* B
  * contraction over all steps on the tensor cores, its two operands rounded
  * to TF32 (relative error <= 2^-11 each, FP32 accumulation). This path
  * scores every sequence against every model (model_of_seq only with K = 1)
- * and needs N_pad (M + 1) * 4 bytes <= 227 KB (M <= 112 at 512 padded
- * states); other requests return HMM_ERR_UNSUPPORTED. Same error bounds.
+ * and needs the cluster forward's emission slice in shared memory (M <= 173
+ * at 512 padded states); other requests return HMM_ERR_UNSUPPORTED. The
+ * emission and initial counts sum the gamma rows of each symbol (rows sorted
+ * by symbol, fixed-size pieces, pieces summed in order). Same error bounds.
  * HMM_TF32_MMA (64 < N <= 128, M <= 256): the forward and the backward
  * recursion of every tile of the same tile plan with TF32 operands (A
  * rounded to TF32, round to nearest; B in FP32; FP32 accumulation), keeping

@@ -663,6 +663,7 @@ static int fb_wide(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.nsplit = L.w_nsplit;
   emis_args(c, L, ws);
   c.nrows = (int64_t)dims.K * L.w_rtot;
+  c.u_in_x = 1;  // rows of invalid sequences are never written: U replaces X
   c.cnt_pi = cnt_pi;
   c.cnt_A = cnt_A;
   c.cnt_B = cnt_B;
@@ -1304,6 +1305,7 @@ static int fb_tf32(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.labelled = labelled ? 1 : 0;
   c.rtot = L.w_rtot;
   c.nrows = labelled ? L.w_rtot : (int64_t)dims.K * L.w_rtot;
+  c.u_in_x = 0;  // the passes store every row the contraction reads (zeros where dead)
   c.X = pa.xs;
   c.Bh = pa.bhs;
   c.V = at<float>(ws, L.w_V);

@@ -36,16 +36,12 @@ __device__ __forceinline__ int seq_of_row(const int64_t* roff, int S, int64_t r)
   return lo;
 }
 
-// One warp per row (model k, step t of sequence s): U (in place of X), V, G
-// and the row's symbol code (m, or m | 1 << 30 at t = 0; -1 = no counts).
-template <int NP>
-__global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
-  constexpr int Q = NP / 128;  // float4 groups per lane
-  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= a.nrows) return;
-  int k = 0, s = 0;
-  int64_t t64 = -1;
+// Row r's model k, sequence s and step t (t = -1: no row).
+__device__ __forceinline__ void locate_row(const FbWideArgs& a, int64_t r, int& k, int& s,
+                                           int64_t& t) {
+  k = 0;
+  s = 0;
+  t = -1;
   if (a.pos_row) {
     // rows in the plan's order: labelled, one run of rows for all models;
     // otherwise a block of rtot rows per model
@@ -55,70 +51,117 @@ __global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
     if (n > 0 && rel < used) {
       const int pos = seq_of_row(a.pos_row, n, rel);
       s = a.sorted[pos];
-      t64 = rel - a.pos_row[pos];
+      t = rel - a.pos_row[pos];
       k = a.labelled ? a.model_of_seq[s] : (int)(r / a.rtot);
     }
   } else {
     k = (int)(r / a.rtot);
     const int64_t rr = r % a.rtot;
     s = seq_of_row(a.roff, a.S, rr);
-    t64 = rr - a.roff[s];
+    t = rr - a.roff[s];
   }
-  const int T = a.seqlen[s];
-  const bool row_ok = T > 0 && t64 >= 0 && t64 < T;
-  const int t = row_ok ? (int)t64 : 0;
-  float4* Xr = reinterpret_cast<float4*>(a.X + r * NP);
-  const float4* Br = reinterpret_cast<const float4*>(a.Bh + r * NP);
-  float4* Vr = reinterpret_cast<float4*>(a.V + r * NP);
-  float4* Gr = reinterpret_cast<float4*>(a.G + r * NP);
-  float4 x[Q], bh[Q];
-  float z = 0.f;
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    x[q] = row_ok ? Xr[lane + 32 * q] : make_float4(0.f, 0.f, 0.f, 0.f);
-    bh[q] = row_ok ? __ldg(Br + lane + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
-    z += (x[q].x * bh[q].x + x[q].y * bh[q].y) + (x[q].z * bh[q].z + x[q].w * bh[q].w);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(HMM_FULL_MASK, z, o);
-  const float w = (row_ok && a.weight)
-                      ? __ldg(a.weight + (a.labelled ? (size_t)s : (size_t)s * a.K + k)) : 1.f;
-  // impossible, invalid or zero-weight pairs contribute nothing
-  const bool use = row_ok && z > 0.f && z < INFINITY && w != 0.f && !isnan(w);
-  const bool trans = use && t + 1 < T;
-  const float iz = use ? w / z : 0.f;
-  float fac = 0.f;
-  int onext = 0;
-  const int32_t* o = a.symbols + (row_ok ? a.offsets[s] : 0);
-  if (trans) {
-    fac = exp2i(-a.xe[r]);
-    onext = __ldg(o + t + 1);
-    if ((unsigned)onext >= (unsigned)a.M) onext = 0;  // flagged by the passes already
-  }
-  const int kmod = k;  // model of this row's parameters
-  const float4* bn = reinterpret_cast<const float4*>(a.Btp + ((size_t)kmod * a.M + onext) * NP);
-  const float4* bhn = reinterpret_cast<const float4*>(a.Bh + (r + 1) * NP);
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const float4 xv = x[q], bv = bh[q];
-    Gr[lane + 32 * q] = make_float4(xv.x * bv.x * iz, xv.y * bv.y * iz, xv.z * bv.z * iz,
-                                    xv.w * bv.w * iz);
-    float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
-    if (trans) {
-      u = make_float4(xv.x * iz, xv.y * iz, xv.z * iz, xv.w * iz);
-      const float4 e = __ldg(bn + lane + 32 * q), nb = __ldg(bhn + lane + 32 * q);
-      v = make_float4(e.x * nb.x * fac, e.y * nb.y * fac, e.z * nb.z * fac, e.w * nb.w * fac);
+}
+
+// One warp per RW consecutive rows (model k, step t of sequence s): V, G, the
+// row's symbol code (m, or m | 1 << 30 at t = 0; -1 = no counts) and U: in
+// place of X (u_in_x), or, where every row the contraction reads holds a
+// finite X, X itself with w / z_t folded into V (U^T V is the same sum).
+// Lane u < RW locates row u and loads its scalars, so the searches and the
+// scalar loads of the warp's rows overlap; then all rows' loads are issued
+// together (RW NP floats of X and of Bh in flight per warp).
+template <int NP>
+__global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
+  constexpr int Q = NP / 128;   // float4 groups per lane
+  constexpr int RW = 4 / Q;     // rows per warp
+  const int64_t rbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RW;
+  const int lane = threadIdx.x & 31;
+  if (rbase >= a.nrows) return;
+  // per-row scalars, lane u for row rbase + u
+  int k_l = 0, T_l = 0, m_l = -1, on_l = 0, xe_l = 0;
+  int64_t t_l = -1;
+  float w_l = 1.f;
+  if (lane < RW && rbase + lane < a.nrows) {
+    int s = 0;
+    locate_row(a, rbase + lane, k_l, s, t_l);
+    const int T = a.seqlen[s];
+    if (T > 0 && t_l >= 0 && t_l < T) {
+      T_l = T;
+      const int32_t* o = a.symbols + a.offsets[s];
+      const int t = (int)t_l;
+      if (a.weight) w_l = __ldg(a.weight + (a.labelled ? (size_t)s : (size_t)s * a.K + k_l));
+      m_l = __ldg(o + t);
+      if (t + 1 < T) {
+        on_l = __ldg(o + t + 1);
+        if ((unsigned)on_l >= (unsigned)a.M) on_l = 0;  // flagged by the passes already
+        xe_l = a.xe[rbase + lane];
+      }
+    } else {
+      t_l = -1;
     }
-    Xr[lane + 32 * q] = u;
-    Vr[lane + 32 * q] = v;
   }
-  if (lane == 0) {
-    int code = -1;
-    if (use) {
-      const int m = __ldg(o + t);
-      code = (unsigned)m < (unsigned)a.M ? (m | (t == 0 ? (1 << 30) : 0)) : -1;
+  float4 x[RW][Q], bh[RW][Q];
+  bool ok[RW];
+#pragma unroll
+  for (int u = 0; u < RW; ++u) {
+    ok[u] = __shfl_sync(HMM_FULL_MASK, T_l, u) > 0;
+    const int64_t r = rbase + u;
+    const float4* Xr = reinterpret_cast<const float4*>(a.X + r * NP);
+    const float4* Br = reinterpret_cast<const float4*>(a.Bh + r * NP);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      x[u][q] = ok[u] ? Xr[lane + 32 * q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      bh[u][q] = ok[u] ? __ldg(Br + lane + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    a.sym[r] = code;
+  }
+#pragma unroll
+  for (int u = 0; u < RW; ++u) {
+    const int64_t r = rbase + u;
+    if (r >= a.nrows) break;  // the same for the whole warp
+    float z = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      z += (x[u][q].x * bh[u][q].x + x[u][q].y * bh[u][q].y) +
+           (x[u][q].z * bh[u][q].z + x[u][q].w * bh[u][q].w);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(HMM_FULL_MASK, z, o);
+    const int k = __shfl_sync(HMM_FULL_MASK, k_l, u);
+    const int T = __shfl_sync(HMM_FULL_MASK, T_l, u);
+    const int t = __shfl_sync(HMM_FULL_MASK, (int)t_l, u);
+    const float w = __shfl_sync(HMM_FULL_MASK, w_l, u);
+    const int m = __shfl_sync(HMM_FULL_MASK, m_l, u);
+    const int onext = __shfl_sync(HMM_FULL_MASK, on_l, u);
+    const int xe = __shfl_sync(HMM_FULL_MASK, xe_l, u);
+    // impossible, invalid or zero-weight pairs contribute nothing
+    const bool use = ok[u] && z > 0.f && z < INFINITY && w != 0.f && !isnan(w);
+    const bool trans = use && t + 1 < T;
+    const float iz = use ? w / z : 0.f;
+    const float fac = trans ? exp2i(-xe) : 0.f;
+    const float4* bn = reinterpret_cast<const float4*>(a.Btp + ((size_t)k * a.M + onext) * NP);
+    const float4* bhn = reinterpret_cast<const float4*>(a.Bh + (r + 1) * NP);
+    float4* Xw = reinterpret_cast<float4*>(const_cast<float*>(a.X) + r * NP);
+    float4* Vr = reinterpret_cast<float4*>(a.V + r * NP);
+    float4* Gr = reinterpret_cast<float4*>(a.G + r * NP);
+    const float vs = a.u_in_x ? fac : fac * iz;  // V's factor
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float4 xv = x[u][q], bv = bh[u][q];
+      Gr[lane + 32 * q] = make_float4(xv.x * bv.x * iz, xv.y * bv.y * iz, xv.z * bv.z * iz,
+                                      xv.w * bv.w * iz);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (trans) {
+        const float4 e = __ldg(bn + lane + 32 * q), nb = __ldg(bhn + lane + 32 * q);
+        v = make_float4(e.x * nb.x * vs, e.y * nb.y * vs, e.z * nb.z * vs, e.w * nb.w * vs);
+      }
+      Vr[lane + 32 * q] = v;
+      if (a.u_in_x)
+        Xw[lane + 32 * q] = trans ? make_float4(xv.x * iz, xv.y * iz, xv.z * iz, xv.w * iz)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (lane == 0) {
+      int code = -1;
+      if (use) code = (unsigned)m < (unsigned)a.M ? (m | (t == 0 ? (1 << 30) : 0)) : -1;
+      a.sym[r] = code;
+    }
   }
 }
 
@@ -545,7 +588,8 @@ FbwEmisSizes fbw_emis_sizes(int K, int M, int NP, int64_t nrows) {
 }
 
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
-  const int64_t cblocks = (a.nrows * 32 + 255) / 256;
+  const int64_t rw = 4 / (a.NP / 128);  // rows per warp of the combine kernel
+  const int64_t cblocks = ((a.nrows + rw - 1) / rw * 32 + 255) / 256;
   if (a.NP == 128) fbw_combine_kernel<128><<<(unsigned)cblocks, 256, 0, st>>>(a);
   else if (a.NP == 256) fbw_combine_kernel<256><<<(unsigned)cblocks, 256, 0, st>>>(a);
   else if (a.NP == 512) fbw_combine_kernel<512><<<(unsigned)cblocks, 256, 0, st>>>(a);

@@ -553,7 +553,8 @@ struct FbWideArgs {
   int K, N, M, NP, S;
   int labelled;          // model_of_seq given (K == 1)
   int64_t rtot;          // rows per model
-  float* X;              // [K][rtot][NP] forward rows, overwritten by U
+  float* X;              // [K][rtot][NP] forward rows, overwritten by U if u_in_x
+  int u_in_x;            // 1: U replaces X; 0: the contraction reads X, V carries w / z
   const float* Bh;       // [K][rtot][NP] backward rows
   float* V;              // [K][rtot][NP]
   float* G;              // [K][rtot][NP] gamma rows (weighted)

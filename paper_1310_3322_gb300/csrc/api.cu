@@ -318,6 +318,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.bpoff = off; off = align256(off + S * 8);                    // rp: first row per sequence
     L.t_pos = off; off = align256(off + S * 8);                    // first row per plan position
     L.t_mrow = off; off = align256(off + 2 * ((size_t)d.K + 1) * 8);  // model row ranges
+    L.t_rpos = off; off = align256(off + (size_t)rtot * 4);           // position of each row
     int ns = (2 * num_sms() + d.K - 1) / d.K;
     L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
     L.w_Cp = off; off = align256(off + (size_t)d.K * L.w_nsplit * NP * NP * 4);
@@ -1326,6 +1327,7 @@ static int fb_tf32(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   c.cnt_B = cnt_B;
   c.status = &at<WsHeader>(ws, 0)->status;
   c.pos_row = pos_row;
+  c.row_pos = at<int32_t>(ws, L.t_rpos);
   c.sorted = p.sorted;
   c.n_valid = p.n_valid;
   c.model_of_seq = seqs->model_of_seq;

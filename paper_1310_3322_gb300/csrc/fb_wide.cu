@@ -36,6 +36,20 @@ __device__ __forceinline__ int seq_of_row(const int64_t* roff, int S, int64_t r)
   return lo;
 }
 
+// Rows in the plan's order: row_pos[rel] = the position whose rows
+// [pos_row[p], pos_row[p + 1]) (the last: up to the rows used) hold rel --
+// the largest p with pos_row[p] <= rel. One warp per position.
+__global__ void fbw_rowpos_kernel(FbWideArgs a) {
+  const int p = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n = __ldg(a.n_valid);
+  if (p >= n) return;
+  const int64_t used = a.labelled ? a.mrow[a.K] : a.mrow[a.K + 1] - a.mrow[0];
+  const int64_t b = a.pos_row[p];
+  const int64_t e = min(used, p + 1 < n ? a.pos_row[p + 1] : used);
+  for (int64_t r = b + lane; r < e; r += 32) a.row_pos[r] = p;
+}
+
 // Row r's model k, sequence s and step t (t = -1: no row).
 __device__ __forceinline__ void locate_row(const FbWideArgs& a, int64_t r, int& k, int& s,
                                            int64_t& t) {
@@ -49,7 +63,7 @@ __device__ __forceinline__ void locate_row(const FbWideArgs& a, int64_t r, int& 
     const int64_t rel = a.labelled ? r : r % a.rtot;
     const int64_t used = a.labelled ? a.mrow[a.K] : a.mrow[a.K + 1] - a.mrow[0];
     if (n > 0 && rel < used) {
-      const int pos = seq_of_row(a.pos_row, n, rel);
+      const int pos = a.row_pos ? a.row_pos[rel] : seq_of_row(a.pos_row, n, rel);
       s = a.sorted[pos];
       t = rel - a.pos_row[pos];
       k = a.labelled ? a.model_of_seq[s] : (int)(r / a.rtot);
@@ -588,14 +602,19 @@ FbwEmisSizes fbw_emis_sizes(int K, int M, int NP, int64_t nrows) {
 }
 
 cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
+  cudaError_t e;
+  if (a.row_pos) {
+    if (!a.pos_row) return cudaErrorInvalidValue;
+    fbw_rowpos_kernel<<<(unsigned)(((int64_t)a.S * 32 + 255) / 256), 256, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const int64_t rw = 4 / (a.NP / 128);  // rows per warp of the combine kernel
   const int64_t cblocks = ((a.nrows + rw - 1) / rw * 32 + 255) / 256;
   if (a.NP == 128) fbw_combine_kernel<128><<<(unsigned)cblocks, 256, 0, st>>>(a);
   else if (a.NP == 256) fbw_combine_kernel<256><<<(unsigned)cblocks, 256, 0, st>>>(a);
   else if (a.NP == 512) fbw_combine_kernel<512><<<(unsigned)cblocks, 256, 0, st>>>(a);
   else return cudaErrorInvalidValue;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int tn = a.NP == 128 ? 128 : kFbwTileN;
   const dim3 gg((a.NP / 128) * (a.NP / tn), a.nsplit, a.K);
   auto gk = a.NP == 128 ? fbw_gemm_kernel<128, 128>

@@ -44,7 +44,7 @@ struct WsLayout {
   size_t sc_coff, sc_P, sc_E;  // parallel-in-time forward: chunk offsets, products
   size_t w_X, w_Bh, w_V, w_G, w_xe, w_sym, w_Cp;  // adjoint above 128 states
   size_t w_ecb, w_eh, w_eb, w_epb, w_el, w_ep;      // its emission-count sort and pieces
-  size_t t_pos, t_mrow;                                       // TF32 adjoint: row offsets
+  size_t t_pos, t_mrow, t_rpos;                                       // TF32 adjoint: row offsets
   int w_nsplit, w_ncc;
   int64_t w_ech;
   int64_t w_rtot;
@@ -586,6 +586,7 @@ struct FbWideArgs {
   int64_t nrows;            // rows of the buffers the combine kernel visits
   // rows in the plan's order (TF32 adjoint, N_pad = 128); NULL: by sequence
   const int64_t* pos_row;   // [positions] first row of the plan's position p
+  int32_t* row_pos;         // [rtot] position of each row (filled by launch_fbw_counts)
   const int32_t* sorted;    // [positions] sequence at position p
   const int32_t* n_valid;   // device count of positions
   const int32_t* model_of_seq;  // labelled: [S]

@@ -76,95 +76,114 @@ __device__ __forceinline__ void locate_row(const FbWideArgs& a, int64_t r, int& 
   }
 }
 
-// One warp per RW consecutive rows (model k, step t of sequence s): V, G, the
+// Rows of one combine block: 32 KB of X rows (and as many Bh rows plus the
+// one after, whose emission product V needs), staged in shared memory by two
+// bulk copies, beside 32 bytes of scalars per row.
+template <int NP>
+struct CombineCfg {
+  static constexpr int RB = 8192 / NP;          // rows per block: 64, 32, 16
+  static constexpr int XB = RB * NP * 4;        // X rows
+  static constexpr int BB = (RB + 1) * NP * 4;  // Bh rows
+  static constexpr int SC = XB + BB;            // per-row scalars [RB][8] ints
+  static constexpr int BAR = SC + RB * 32;
+  static constexpr int SMEM = BAR + 16;
+};
+constexpr uint32_t kCombineWait = 1u << 24;
+
+// One block per RB consecutive rows (model k, step t of sequence s): V, G, the
 // row's symbol code (m, or m | 1 << 30 at t = 0; -1 = no counts) and U: in
 // place of X (u_in_x), or, where every row the contraction reads holds a
 // finite X, X itself with w / z_t folded into V (U^T V is the same sum).
-// Lane u < RW locates row u and loads its scalars, so the searches and the
-// scalar loads of the warp's rows overlap; then all rows' loads are issued
-// together (RW NP floats of X and of Bh in flight per warp).
+// Thread 0 starts the bulk copies of the block's X and Bh rows; meanwhile
+// thread u < RB locates row u and loads its scalars; then each warp takes
+// every eighth row from shared memory (lane l: float4 groups l, l + 32, ..).
+// The copies' wait is bounded: a give-up records HMM_STATUS_TIMEOUT, waits
+// for the copies once more and leaves the block's rows without counts.
 template <int NP>
 __global__ void __launch_bounds__(256) fbw_combine_kernel(FbWideArgs a) {
-  constexpr int Q = NP / 128;   // float4 groups per lane
-  constexpr int RW = 4 / Q;     // rows per warp
-  const int64_t rbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RW;
-  const int lane = threadIdx.x & 31;
-  if (rbase >= a.nrows) return;
-  // per-row scalars, lane u for row rbase + u
-  int k_l = 0, T_l = 0, m_l = -1, on_l = 0, xe_l = 0;
-  int64_t t_l = -1;
-  float w_l = 1.f;
-  if (lane < RW && rbase + lane < a.nrows) {
-    int s = 0;
-    locate_row(a, rbase + lane, k_l, s, t_l);
-    const int T = a.seqlen[s];
-    if (T > 0 && t_l >= 0 && t_l < T) {
-      T_l = T;
+  using C = CombineCfg<NP>;
+  constexpr int Q = NP / 128;  // float4 groups per lane
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const float4* sX = reinterpret_cast<const float4*>(smem);
+  const float4* sB = reinterpret_cast<const float4*>(smem + C::XB);
+  int* sc = reinterpret_cast<int*>(smem + C::SC);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::BAR);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t rb = (int64_t)blockIdx.x * C::RB;
+  const int n = (int)min((int64_t)C::RB, a.nrows - rb);       // >= 1 (grid)
+  const int nb = (int)min((int64_t)C::RB + 1, a.nrows - rb);
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)((n + nb) * NP * 4));
+    tc::bulk_g2s(tc::smem_u32(smem), a.X + rb * NP, (uint32_t)(n * NP * 4), bar);
+    tc::bulk_g2s(tc::smem_u32(smem + C::XB), a.Bh + rb * NP, (uint32_t)(nb * NP * 4), bar);
+  }
+  if (tid < n) {
+    int k = 0, s = 0, T = 0, m = -1, on = 0, xe = 0;
+    int64_t t = -1;
+    float w = 1.f;
+    locate_row(a, rb + tid, k, s, t);
+    const int Ts = a.seqlen[s];
+    if (Ts > 0 && t >= 0 && t < Ts) {
+      T = Ts;
       const int32_t* o = a.symbols + a.offsets[s];
-      const int t = (int)t_l;
-      if (a.weight) w_l = __ldg(a.weight + (a.labelled ? (size_t)s : (size_t)s * a.K + k_l));
-      m_l = __ldg(o + t);
-      if (t + 1 < T) {
-        on_l = __ldg(o + t + 1);
-        if ((unsigned)on_l >= (unsigned)a.M) on_l = 0;  // flagged by the passes already
-        xe_l = a.xe[rbase + lane];
+      if (a.weight) w = __ldg(a.weight + (a.labelled ? (size_t)s : (size_t)s * a.K + k));
+      m = __ldg(o + t);
+      if (t + 1 < Ts) {
+        on = __ldg(o + t + 1);
+        if ((unsigned)on >= (unsigned)a.M) on = 0;  // flagged by the passes already
+        xe = a.xe[rb + tid];
       }
     } else {
-      t_l = -1;
+      t = -1;
     }
+    int* p = sc + tid * 8;
+    p[0] = k; p[1] = T; p[2] = (int)t; p[3] = __float_as_int(w);
+    p[4] = m; p[5] = on; p[6] = xe;
   }
-  float4 x[RW][Q], bh[RW][Q];
-  bool ok[RW];
-#pragma unroll
-  for (int u = 0; u < RW; ++u) {
-    ok[u] = __shfl_sync(HMM_FULL_MASK, T_l, u) > 0;
-    const int64_t r = rbase + u;
-    const float4* Xr = reinterpret_cast<const float4*>(a.X + r * NP);
-    const float4* Br = reinterpret_cast<const float4*>(a.Bh + r * NP);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      x[u][q] = ok[u] ? Xr[lane + 32 * q] : make_float4(0.f, 0.f, 0.f, 0.f);
-      bh[u][q] = ok[u] ? __ldg(Br + lane + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+  __syncthreads();  // the barrier's init and the scalars
+  bool landed = tc::mbar_wait_bounded(bar, 0, kCombineWait);
+  if (!landed) {
+    if (tid == 0) set_status(a.status, HMM_STATUS_TIMEOUT);
+    tc::mbar_wait_bounded(bar, 0, kCombineWait);  // the copies write this block's memory
   }
-#pragma unroll
-  for (int u = 0; u < RW; ++u) {
-    const int64_t r = rbase + u;
-    if (r >= a.nrows) break;  // the same for the whole warp
+  for (int u = warp; u < n; u += 8) {
+    const int64_t r = rb + u;
+    const int* p = sc + u * 8;
+    const int k = p[0], T = landed ? p[1] : 0, t = p[2];
+    const float w = __int_as_float(p[3]);
+    const int m = p[4], onext = p[5], xe = p[6];
+    const bool ok = T > 0;
+    float4 x[Q], bh[Q];
     float z = 0.f;
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-      z += (x[u][q].x * bh[u][q].x + x[u][q].y * bh[u][q].y) +
-           (x[u][q].z * bh[u][q].z + x[u][q].w * bh[u][q].w);
+    for (int q = 0; q < Q; ++q) {
+      x[q] = ok ? sX[u * (NP / 4) + lane + 32 * q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      bh[q] = ok ? sB[u * (NP / 4) + lane + 32 * q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      z += (x[q].x * bh[q].x + x[q].y * bh[q].y) + (x[q].z * bh[q].z + x[q].w * bh[q].w);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(HMM_FULL_MASK, z, o);
-    const int k = __shfl_sync(HMM_FULL_MASK, k_l, u);
-    const int T = __shfl_sync(HMM_FULL_MASK, T_l, u);
-    const int t = __shfl_sync(HMM_FULL_MASK, (int)t_l, u);
-    const float w = __shfl_sync(HMM_FULL_MASK, w_l, u);
-    const int m = __shfl_sync(HMM_FULL_MASK, m_l, u);
-    const int onext = __shfl_sync(HMM_FULL_MASK, on_l, u);
-    const int xe = __shfl_sync(HMM_FULL_MASK, xe_l, u);
     // impossible, invalid or zero-weight pairs contribute nothing
-    const bool use = ok[u] && z > 0.f && z < INFINITY && w != 0.f && !isnan(w);
+    const bool use = ok && z > 0.f && z < INFINITY && w != 0.f && !isnan(w);
     const bool trans = use && t + 1 < T;
     const float iz = use ? w / z : 0.f;
     const float fac = trans ? exp2i(-xe) : 0.f;
+    const float vs = a.u_in_x ? fac : fac * iz;  // V's factor
     const float4* bn = reinterpret_cast<const float4*>(a.Btp + ((size_t)k * a.M + onext) * NP);
-    const float4* bhn = reinterpret_cast<const float4*>(a.Bh + (r + 1) * NP);
-    float4* Xw = reinterpret_cast<float4*>(const_cast<float*>(a.X) + r * NP);
+    float4* Xw = reinterpret_cast<float4*>(a.X + r * NP);
     float4* Vr = reinterpret_cast<float4*>(a.V + r * NP);
     float4* Gr = reinterpret_cast<float4*>(a.G + r * NP);
-    const float vs = a.u_in_x ? fac : fac * iz;  // V's factor
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const float4 xv = x[u][q], bv = bh[u][q];
+      const float4 xv = x[q], bv = bh[q];
       Gr[lane + 32 * q] = make_float4(xv.x * bv.x * iz, xv.y * bv.y * iz, xv.z * bv.z * iz,
                                       xv.w * bv.w * iz);
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (trans) {
-        const float4 e = __ldg(bn + lane + 32 * q), nb = __ldg(bhn + lane + 32 * q);
-        v = make_float4(e.x * nb.x * vs, e.y * nb.y * vs, e.z * nb.z * vs, e.w * nb.w * vs);
+      if (trans) {  // row u + 1 < nb: the sequence's next step is a row of the buffer
+        const float4 e = __ldg(bn + lane + 32 * q), nbv = sB[(u + 1) * (NP / 4) + lane + 32 * q];
+        v = make_float4(e.x * nbv.x * vs, e.y * nbv.y * vs, e.z * nbv.z * vs, e.w * nbv.w * vs);
       }
       Vr[lane + 32 * q] = v;
       if (a.u_in_x)
@@ -608,13 +627,19 @@ cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
     fbw_rowpos_kernel<<<(unsigned)(((int64_t)a.S * 32 + 255) / 256), 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const int64_t rw = 4 / (a.NP / 128);  // rows per warp of the combine kernel
-  const int64_t cblocks = ((a.nrows + rw - 1) / rw * 32 + 255) / 256;
-  if (a.NP == 128) fbw_combine_kernel<128><<<(unsigned)cblocks, 256, 0, st>>>(a);
-  else if (a.NP == 256) fbw_combine_kernel<256><<<(unsigned)cblocks, 256, 0, st>>>(a);
-  else if (a.NP == 512) fbw_combine_kernel<512><<<(unsigned)cblocks, 256, 0, st>>>(a);
+  auto combine = [&](auto kern, int rb, int sm) {
+    const int64_t blocks = (a.nrows + rb - 1) / rb;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (ce != cudaSuccess) return ce;
+    kern<<<(unsigned)blocks, 256, sm, st>>>(a);
+    return cudaGetLastError();
+  };
+  if (a.nrows <= 0) return cudaErrorInvalidValue;
+  if (a.NP == 128) e = combine(fbw_combine_kernel<128>, CombineCfg<128>::RB, CombineCfg<128>::SMEM);
+  else if (a.NP == 256) e = combine(fbw_combine_kernel<256>, CombineCfg<256>::RB, CombineCfg<256>::SMEM);
+  else if (a.NP == 512) e = combine(fbw_combine_kernel<512>, CombineCfg<512>::RB, CombineCfg<512>::SMEM);
   else return cudaErrorInvalidValue;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (e != cudaSuccess) return e;
   const int tn = a.NP == 128 ? 128 : kFbwTileN;
   const dim3 gg((a.NP / 128) * (a.NP / tn), a.nsplit, a.K);
   auto gk = a.NP == 128 ? fbw_gemm_kernel<128, 128>

@@ -155,3 +155,39 @@ def test_wide_adjoint_argument_checks():
     big_m = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 1, 300, 200)]
     with pytest.raises(hmm.HmmError):  # emission slice beyond the cluster forward's shared memory
         hmm.hmm_forward_backward(*big_m, seqs.all_models(), precision=hmm.HMM_BF16_MMA)
+
+
+def test_wide_adjoint_single_symbol_and_zero_weights():
+    """One symbol (a model's rows all in one bucket of many pieces) and
+    weights of zero (rows without entries), above 128 states."""
+    import torch
+    rng = np.random.default_rng(11)
+    K, N, M, S = 1, 200, 1, 40
+    pi, A, _ = synth.random_model(rng, K, N, 2)
+    B = np.ones((K, N, M), np.float32)
+    lengths = rng.integers(1, 120, size=S).astype(np.int32)
+    offsets = np.concatenate([[0], np.cumsum(lengths.astype(np.int64))[:-1]]).astype(np.int64)
+    sym = np.zeros(int(lengths.sum()), np.int32)
+    wts = rng.uniform(0.5, 2.0, size=(S, K)).astype(np.float32)
+    wts[rng.random(S) < 0.3] = 0.0
+    t = [torch.from_numpy(x).cuda() for x in (pi, A, B)]
+    seqs = hmm.Sequences.from_numpy(sym, offsets, lengths, device="cuda")
+    out = hmm.hmm_forward_backward(*t, seqs, weight=torch.from_numpy(wts).cuda(),
+                                   precision=hmm.HMM_BF16_MMA)
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    ll, cpi, cA, cB = [x.cpu().numpy() for x in out]
+    rll, rpi, rA, rB, _ = oracle.forward_backward(oracle.params(pi, A, B), sym, offsets, lengths,
+                                                  None, wts.astype(np.float64), nthreads=16)
+    # one symbol of probability 1: log P is 0 up to the rounding of A
+    T = np.maximum(lengths, 1).astype(np.float64)[:, None]
+    assert np.all(np.abs(ll - rll) <= 3 * U_BF16 * T + ll_tol(lengths)[:, None])
+    assert np.all(np.abs(rll) <= 1e-4)
+    w0 = wts[:, 0].astype(np.float64)
+    assert abs(cB[0].sum() - (w0 * lengths).sum()) <= U_BF16 * (w0 * lengths).sum()
+    for g, r in zip((cpi, cA, cB), (rpi, rA, rB)):
+        assert rel_l2(g, r) <= U_BF16
+    zero = np.zeros_like(wts)
+    out0 = hmm.hmm_forward_backward(*t, seqs, weight=torch.from_numpy(zero).cuda(),
+                                    precision=hmm.HMM_BF16_MMA)
+    for x in out0[1:]:
+        assert not x.cpu().numpy().any()

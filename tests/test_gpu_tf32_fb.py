@@ -168,3 +168,45 @@ def test_tf32_adjoint_refusals():
     wide = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 1, 200, 8)]
     with pytest.raises(hmm.HmmError):  # above 128 states: BF16 only
         hmm.hmm_forward_backward(*wide, seqs, precision=hmm.HMM_TF32_MMA)
+
+
+def test_tf32_adjoint_empty_model_single_symbol_zero_weights():
+    """Emission sums over the symbol sort: a model no sequence is labelled
+    with (no rows, no chunks), a model whose sequences all carry weight 0
+    (rows but no entries), and one symbol (every row of a model in one
+    bucket, spread over many pieces)."""
+    import torch
+    rng = np.random.default_rng(19)
+    K, N, M, S = 3, 90, 1, 70
+    pi, A, _ = synth.random_model(rng, K, N, 2)
+    B = np.ones((K, N, M), np.float32)
+    lengths = rng.integers(1, 260, size=S).astype(np.int32)
+    lengths[:3] = (0, 1, 2)
+    offsets = np.concatenate([[0], np.cumsum(lengths.astype(np.int64))[:-1]]).astype(np.int64)
+    sym = np.zeros(int(lengths.sum()), np.int32)
+    labels = np.where(rng.random(S) < 0.5, 0, 2).astype(np.int32)
+    wts = rng.uniform(0.5, 2.0, size=S).astype(np.float32)
+    wts[labels == 2] = 0.0
+    wts[rng.random(S) < 0.2] = 0.0
+    t = [torch.from_numpy(x).cuda() for x in (pi, A, B)]
+    seqs = hmm.Sequences.from_numpy(sym, offsets, lengths, model_of_seq=labels, device="cuda")
+    out = hmm.hmm_forward_backward(*t, seqs, weight=torch.from_numpy(wts).cuda(),
+                                   precision=hmm.HMM_TF32_MMA)
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    ll, cpi, cA, cB = [x.cpu().numpy() for x in out]
+    Pm = oracle.params(pi, tf32_round(A), B)
+    rll, rpi, rA, rB, _ = oracle.forward_backward(Pm, sym, offsets, lengths, labels,
+                                                  wts.astype(np.float64), nthreads=8)
+    # one symbol of probability 1: log P is 0 up to the rounding of A
+    T = np.maximum(lengths, 1).astype(np.float64)
+    assert np.all(np.abs(ll - rll) <= 2 * U_TF32 * T + ll_tol(lengths))
+    assert np.all(np.abs(ll) <= 2 * U_TF32 * T + ll_tol(lengths))
+    for k in (1, 2):  # no sequence; only zero weights
+        assert not cpi[k].any() and not cA[k].any() and not cB[k].any()
+    live = (labels == 0) & (lengths > 0) & (wts != 0)
+    Tl = lengths.astype(np.float64)
+    assert abs(cpi[0].sum() - wts[live].sum()) <= CNT_TOL * wts[live].sum()
+    assert abs(cB[0].sum() - (wts[live] * Tl[live]).sum()) <= CNT_TOL * (wts[live] * Tl[live]).sum()
+    check_counts((cpi, cA, cB), (rpi, rA, rB), rtol=CNT_TOL, what="empty model")
+    errs = [rel_l2(g, r) for g, r in zip((cpi, cA, cB), (rpi, rA, rB))]
+    assert max(errs) <= CNT_TOL, errs

@@ -319,7 +319,7 @@ static WsLayout make_layout(const hmm_dims_t& d, const hmm_seqs_t& q, int op, bo
     L.t_pos = off; off = align256(off + S * 8);                    // first row per plan position
     L.t_mrow = off; off = align256(off + 2 * ((size_t)d.K + 1) * 8);  // model row ranges
     L.t_rpos = off; off = align256(off + (size_t)rtot * 4);           // position of each row
-    int ns = (2 * num_sms() + d.K - 1) / d.K;
+    int ns = (num_sms() + d.K - 1) / d.K;  // the contraction runs one CTA per SM
     L.w_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
     L.w_Cp = off; off = align256(off + (size_t)d.K * L.w_nsplit * NP * NP * 4);
     emis_layout(L, off, d, NP, nrows);

@@ -331,6 +331,147 @@ __global__ void __launch_bounds__(256, 1) fbw_gemm_kernel(FbWideArgs a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// The contraction at N_pad = 128 (the TF32 adjoint, one 128 x 128 output
+// tile): whole 32-row chunks of X and V (16 KB each) are copied by thread 0
+// with cp.async.bulk into kFbwRaw shared-memory stages, kFbwRaw - 1 chunks
+// ahead, so about 96 KB of rows are in flight per SM without registers (one
+// CTA per SM); the threads then take the chunk from shared memory and form
+// the operands as the kernel above. A stage is refilled at the top of the
+// chunk after its last reader's barrier. Every wait is bounded; after a
+// give-up the last copy into every stage is awaited once more before exit.
+constexpr int kFbwRaw = 4;
+constexpr int kFbwRawFloats = 2 * kFbwRows * 128;              // X and V rows of a chunk
+constexpr int kFbwOp128 = 2 * kFbwRows * 128 * 4;              // A and B stage: 32 KB
+constexpr int kFbwSmem128 = 2 * kFbwOp128 + kFbwRaw * kFbwRawFloats * 4 + 128;
+
+__global__ void __launch_bounds__(256, 1) fbw_gemm128_kernel(FbWideArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sOp = smem;                                                // [2][A | B]
+  float* sRaw = reinterpret_cast<float*>(smem + 2 * kFbwOp128);       // [kFbwRaw][X | V]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kFbwOp128 + kFbwRaw * kFbwRawFloats * 4);
+  uint64_t* done = bars;            // [2]: the chunk's MMAs have read the operand stage
+  uint64_t* fin = bars + 2;         // every MMA of the CTA is done
+  uint64_t* full = bars + 3;        // [kFbwRaw]: the chunk's rows have landed
+  volatile uint32_t* slot = reinterpret_cast<volatile uint32_t*>(bars + 3 + kFbwRaw);
+  const int split = blockIdx.y, k = blockIdx.z;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t beg = a.mrow ? a.mrow[k] : (int64_t)k * a.rtot;
+  const int64_t end = a.mrow ? a.mrow[a.K + 1 + k] : beg + a.rtot;
+  const int64_t rps = ((end - beg + a.nsplit - 1) / a.nsplit + kFbwRows - 1) / kFbwRows * kFbwRows;
+  const int64_t r0 = beg + (int64_t)split * rps;
+  const int64_t r1 = min(end, r0 + rps);
+  const int nch = r1 > r0 ? (int)((r1 - r0 + kFbwRows - 1) / kFbwRows) : 0;
+  auto issue = [&](int c) {  // thread 0: chunk c into raw stage c % kFbwRaw
+    const int64_t rb = r0 + (int64_t)c * kFbwRows;
+    const uint32_t bytes = (uint32_t)min((int64_t)kFbwRows, r1 - rb) * 512u;
+    float* dst = sRaw + (size_t)(c % kFbwRaw) * kFbwRawFloats;
+    uint64_t* b = &full[c % kFbwRaw];
+    tc::mbar_arrive_expect_tx(b, 2 * bytes);
+    tc::bulk_g2s(tc::smem_u32(dst), a.X + rb * 128, bytes, b);
+    tc::bulk_g2s(tc::smem_u32(dst + kFbwRows * 128), a.V + rb * 128, bytes, b);
+  };
+
+  if (warp == 0) tc::tmem_alloc(const_cast<uint32_t*>(slot), 256);
+  if (tid == 0) {
+    tc::mbar_init(&done[0], 1);
+    tc::mbar_init(&done[1], 1);
+    tc::mbar_init(fin, 1);
+    for (int i = 0; i < kFbwRaw; ++i) tc::mbar_init(&full[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int c = 0; c < kFbwRaw - 1 && c < nch; ++c) issue(c);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  constexpr uint32_t idesc = tc::instr_desc(2, 128, 128);
+  bool ok = true;
+
+  // this thread's share of a chunk: U column ia and V column ia, row quads
+  // qa, qa + 2, ..
+  const int ia = tid & 127, qa = tid >> 7;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int st = ch & 1;
+    if (tid == 0 && ch + kFbwRaw - 1 < nch) issue(ch + kFbwRaw - 1);
+    const int rs = ch % kFbwRaw;
+    const bool landed = tc::mbar_wait_bounded(&full[rs], (uint32_t)(ch / kFbwRaw) & 1u, kFbwWait);
+    if (!landed) ok = false;
+    const float* sX = sRaw + (size_t)rs * kFbwRawFloats;
+    const float* sV = sX + kFbwRows * 128;
+    const int64_t rb = r0 + (int64_t)ch * kFbwRows;
+    float u[4][4], v[4][4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int rl = 4 * (qa + 2 * m) + e;
+        const bool in = landed && rb + rl < r1;
+        u[m][e] = in ? sX[rl * 128 + ia] : 0.f;
+        v[m][e] = in ? sV[rl * 128 + ia] : 0.f;
+      }
+    // the operand stage's previous chunk (ch - 2) must have been read by its MMAs
+    if (ch >= 2 && !tc::mbar_wait_bounded(&done[st], (uint32_t)((ch >> 1) + 1) & 1u, kFbwWait))
+      ok = false;
+    uint8_t* A = sOp + st * kFbwOp128;
+    uint8_t* B = A + kFbwOp128 / 2;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int off = (ia >> 3) * 1024 + (qa + 2 * m) * 128 + (ia & 7) * 16;
+      *reinterpret_cast<uint4*>(A + off) =
+          make_uint4(tc::to_tf32(u[m][0]), tc::to_tf32(u[m][1]), tc::to_tf32(u[m][2]),
+                     tc::to_tf32(u[m][3]));
+      *reinterpret_cast<uint4*>(B + off) =
+          make_uint4(tc::to_tf32(v[m][0]), tc::to_tf32(v[m][1]), tc::to_tf32(v[m][2]),
+                     tc::to_tf32(v[m][3]));
+    }
+    tc::fence_proxy_async();  // the stage's generic writes -> tensor core
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t aA = tc::smem_u32(A), aB = tc::smem_u32(B);
+#pragma unroll
+      for (int kk = 0; kk < kFbwRows / 8; ++kk)
+        tc::mma_tf32(tmem, tc::smem_desc(aA + kk * 256, 128, 1024),
+                     tc::smem_desc(aB + kk * 256, 128, 1024), idesc, (ch | kk) ? 1u : 0u);
+      tc::mma_commit(&done[st]);
+    }
+  }
+  if (tid == 0) tc::mma_commit(fin);  // arrives once every MMA above is done
+  if (!tc::mbar_wait_bounded(fin, 0, kFbwWait)) ok = false;
+  tc::fence_after_sync();
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      set_status(a.status, HMM_STATUS_TIMEOUT);
+      for (int s = 0; s < kFbwRaw && s < nch; ++s) {  // the last copy into each stage
+        const int last = s + kFbwRaw * ((nch - 1 - s) / kFbwRaw);
+        tc::mbar_wait_bounded(&full[s], (uint32_t)(last / kFbwRaw) & 1u, kFbwWait);
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (states i), columns
+  // 64 (w / 4) .. + 63 (states j)
+  const int i = 32 * (warp & 3) + lane;
+  const int jc = 64 * (warp >> 2);
+  float* dst = a.Cp + ((size_t)k * a.nsplit + split) * 128 * 128 + (size_t)i * 128 + jc;
+#pragma unroll 1
+  for (int c = 0; c < 2; ++c) {
+    float y[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(jc + 32 * c), y);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(dst + 32 * c + 4 * q) =
+          nch > 0 ? make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3])
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
 // cnt_A[k][i][j] = a_ij * sum over splits (fixed order).
 __global__ void fbw_reduce_a_kernel(FbWideArgs a) {
   const int64_t n = (int64_t)a.K * a.N * a.N;
@@ -640,14 +781,19 @@ cudaError_t launch_fbw_counts(const FbWideArgs& a, cudaStream_t st) {
   else if (a.NP == 512) e = combine(fbw_combine_kernel<512>, CombineCfg<512>::RB, CombineCfg<512>::SMEM);
   else return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
-  const int tn = a.NP == 128 ? 128 : kFbwTileN;
-  const dim3 gg((a.NP / 128) * (a.NP / tn), a.nsplit, a.K);
-  auto gk = a.NP == 128 ? fbw_gemm_kernel<128, 128>
-                        : a.NP == 256 ? fbw_gemm_kernel<256, 256> : fbw_gemm_kernel<512, 256>;
-  if ((e = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, kFbwSmem)) !=
-      cudaSuccess)
-    return e;
-  gk<<<gg, 256, kFbwSmem, st>>>(a);
+  if (a.NP == 128) {
+    if ((e = cudaFuncSetAttribute(fbw_gemm128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kFbwSmem128)) != cudaSuccess)
+      return e;
+    fbw_gemm128_kernel<<<dim3(1, a.nsplit, a.K), 256, kFbwSmem128, st>>>(a);
+  } else {
+    const dim3 gg((a.NP / 128) * (a.NP / kFbwTileN), a.nsplit, a.K);
+    auto gk = a.NP == 256 ? fbw_gemm_kernel<256, 256> : fbw_gemm_kernel<512, 256>;
+    if ((e = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, kFbwSmem)) !=
+        cudaSuccess)
+      return e;
+    gk<<<gg, 256, kFbwSmem, st>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   fbw_reduce_a_kernel<<<1024, 256, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -11,7 +11,10 @@ times: K = 4 models, N = 128 states, M = 256 symbols, Dirichlet(0.3) rows,
 * the BF16 adjoint on a 160-sequence subset that holds the 24 longest
   sequences (tiles of T ~ 2000: 125 checkpoint segments of 16 steps each),
   element by element against the oracle's expected counts on the model the
-  kernel holds (A and B rounded to BF16).
+  kernel holds (A and B rounded to BF16);
+* the TF32 adjoint on the whole batch (sampled log-likelihoods, count
+  identities, counts against the BF16 adjoint's) and on such a subset,
+  element by element against the oracle on A rounded to TF32.
 Tolerances and their derivation: tests/test_gpu_mma.py, tests/test_gpu_mma_fb.py.
 """
 import os
@@ -114,3 +117,60 @@ def test_large_adjoint_longest_subset_elementwise(large):
     assert np.all(np.abs(ll - rll) <= seq_cap(U_BF16, w.lengths[idx]))
     worst = check_counts((cpi, cA, cB), (rpi, rA, rB), rtol=U_BF16, what="longest subset")
     print(f"longest subset: worst |d|/(1+|ref|) pi {worst[0]:.2e} A {worst[1]:.2e} B {worst[2]:.2e}")
+
+
+def test_full_large_adjoint_tf32_labelled(large):
+    """The TF32 adjoint (every step's rows kept: 4 x 17.35 M rows of 128
+    floats) on the whole batch: 64 sampled log-likelihoods against the oracle
+    on the model the kernel holds (A rounded to TF32), the count identities of
+    every model, and the counts against the BF16 adjoint's (both within their
+    bounds of the exact counts: 2^-8 relative L2 apart at most)."""
+    from test_gpu_mma import U_TF32
+    w, _, lab, pi, A, B = large
+    ll, cpi, cA, cB = (t.cpu().numpy() for t in
+                       hmm.hmm_forward_backward(pi, A, B, lab, precision=hmm.HMM_TF32_MMA))
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    assert np.all(np.isfinite(ll))
+    idx = _sample(w, 64, 16, 15)
+    rll, _, _ = oracle.forward(held_model(w, "tf32"), w.symbols, w.offsets[idx],
+                               w.lengths[idx], w.labels[idx], nthreads=NTHREADS)
+    T = w.lengths[idx].astype(np.float64)
+    err = np.abs(ll[idx] - rll)
+    assert np.all(err <= seq_cap(U_TF32, w.lengths[idx])), np.max(err / T)
+    assert np.mean(err / T) <= U_TF32 / 8, np.mean(err / T)
+    tol = 2.0 ** -8
+    for k in range(w.K):
+        Tk = w.lengths[w.labels == k].astype(np.float64)
+        assert abs(cpi[k].sum() - Tk.size) <= tol * Tk.size
+        assert abs(cA[k].sum() - (Tk - 1).sum()) <= tol * Tk.sum()
+        assert abs(cB[k].sum() - Tk.sum()) <= tol * Tk.sum()
+        assert np.all(cA[k] >= 0) and np.all(cB[k] >= 0) and np.all(cpi[k] >= 0)
+    _, bpi, bA, bB = (t.cpu().numpy() for t in
+                      hmm.hmm_forward_backward(pi, A, B, lab, precision=hmm.HMM_BF16_MMA))
+    for g, r in zip((cpi, cA, cB), (bpi, bA, bB)):
+        assert np.linalg.norm(g - r) <= tol * np.linalg.norm(r)
+
+
+def test_large_adjoint_tf32_longest_subset_elementwise(large):
+    """The TF32 adjoint on a 160-sequence weighted subset that holds the 24
+    longest sequences (T ~ 2000), element by element against the oracle's
+    expected counts on the model the kernel holds."""
+    import torch
+    w = large[0]
+    idx = _sample(w, 160, 24, 16)
+    assert w.lengths[idx].max() == 2000
+    seqs = hmm.Sequences.from_numpy(w.symbols, w.offsets[idx], w.lengths[idx],
+                                    model_of_seq=w.labels[idx])
+    pi, A, B = (torch.from_numpy(x).cuda() for x in (w.pi, w.A, w.B))
+    wts = np.random.default_rng(17).uniform(0.5, 2.0, size=idx.size).astype(np.float32)
+    ll, cpi, cA, cB = (t.cpu().numpy() for t in hmm.hmm_forward_backward(
+        pi, A, B, seqs, weight=torch.from_numpy(wts).cuda(), precision=hmm.HMM_TF32_MMA))
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    rll, rpi, rA, rB, _ = oracle.forward_backward(held_model(w, "tf32"), w.symbols,
+                                                  w.offsets[idx], w.lengths[idx], w.labels[idx],
+                                                  wts.astype(np.float64), nthreads=NTHREADS)
+    from test_gpu_mma import U_TF32
+    assert np.all(np.abs(ll - rll) <= seq_cap(U_TF32, w.lengths[idx]))
+    worst = check_counts((cpi, cA, cB), (rpi, rA, rB), rtol=2.0 ** -8, what="TF32 longest subset")
+    print(f"TF32 longest subset: worst |d|/(1+|ref|) pi {worst[0]:.2e} A {worst[1]:.2e} "
+          f"B {worst[2]:.2e}")

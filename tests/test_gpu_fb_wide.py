@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import ll_tol, oparams, rel_l2, to_gpu
+from helpers import check_counts, ll_tol, oparams, rel_l2, to_gpu
 from paper_1310_3322_gb300 import hmm, synth
 
 pytestmark = pytest.mark.gpu
@@ -191,3 +191,45 @@ def test_wide_adjoint_single_symbol_and_zero_weights():
                                     precision=hmm.HMM_BF16_MMA)
     for x in out0[1:]:
         assert not x.cpu().numpy().any()
+
+
+def test_wide_adjoint_full_cuhmm_shape():
+    """The 512-state x 512-sequence workload the Baum-Welch bench times
+    (K = 1, N = 512, M = 64, T ~ U{100..500}): the E-step on the whole batch
+    (sampled log-likelihoods against the oracle, count identities), and on a
+    weighted subset holding the 12 longest sequences, element by element
+    against the oracle's expected counts on the model the kernel holds (A and
+    B rounded to BF16)."""
+    import torch
+    from test_gpu_mma import held_model, seq_cap
+    w = synth.make_workload("cuhmm")
+    seqs, pi, A, B = to_gpu(w)
+    ll, cpi, cA, cB = (t.cpu().numpy() for t in
+                       hmm.hmm_forward_backward(pi, A, B, seqs, precision=hmm.HMM_BF16_MMA))
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    assert np.all(np.isfinite(ll))
+    idx = np.random.default_rng(20).choice(w.S, size=8, replace=False)
+    ref, _, _ = oracle.forward(oparams(w), w.symbols, w.offsets[idx], w.lengths[idx], nthreads=16)
+    T = w.lengths[idx].astype(np.float64)[:, None]
+    assert np.all(np.abs(ll[idx] - ref) <= 3 * U_BF16 * T + ll_tol(w.lengths[idx])[:, None])
+    Tl = w.lengths.astype(np.float64)
+    assert abs(cpi[0].sum() - w.S) <= U_BF16 * w.S
+    assert abs(cA[0].sum() - (Tl - 1).sum()) <= U_BF16 * Tl.sum()
+    assert abs(cB[0].sum() - Tl.sum()) <= U_BF16 * Tl.sum()
+    assert np.all(cA >= 0) and np.all(cB >= 0) and np.all(cpi >= 0)
+
+    order = np.argsort(-w.lengths, kind="stable")
+    sub = np.sort(np.concatenate([order[:12], np.random.default_rng(21).choice(
+        order[12:], size=12, replace=False)]))
+    wts = np.random.default_rng(22).uniform(0.5, 2.0, size=(sub.size, 1)).astype(np.float32)
+    s2 = hmm.Sequences.from_numpy(w.symbols, w.offsets[sub], w.lengths[sub], device="cuda")
+    ll2, spi, sA, sB = (t.cpu().numpy() for t in hmm.hmm_forward_backward(
+        pi, A, B, s2, weight=torch.from_numpy(wts).cuda(), precision=hmm.HMM_BF16_MMA))
+    assert hmm.hmm_get_device_status(hmm.default_workspace()) == 0
+    rll, rpi, rA, rB, _ = oracle.forward_backward(held_model(w, "bf16"), w.symbols, w.offsets[sub],
+                                                  w.lengths[sub], None, wts.astype(np.float64),
+                                                  nthreads=16)
+    assert np.all(np.abs(ll2 - rll) <= seq_cap(U_BF16, w.lengths[sub])[:, None])
+    worst = check_counts((spi, sA, sB), (rpi, rA, rB), rtol=U_BF16, what="512 states")
+    print(f"512 states, longest subset: worst |d|/(1+|ref|) pi {worst[0]:.2e} "
+          f"A {worst[1]:.2e} B {worst[2]:.2e}")

@@ -190,6 +190,10 @@ static bool scan_preferred(const hmm_dims_t& d, const hmm_seqs_t& q) {
   return pairs * NP * NP * NP <= ((int64_t)1 << 21) && pairs <= (int64_t)num_sms() * 32;
 }
 
+// The TF32 adjoint's symbol range: the M <= 256 of the tensor-core adjoint
+// (its passes' shared memory would take a few more).
+static bool tf32_adjoint_m_ok(int NP, int M) { return M <= 256 && fb_tf32_supported(NP, M); }
+
 // Emission-count buffers of the adjoint from per-step rows (fb_wide.cu).
 static void emis_layout(WsLayout& L, size_t& off, const hmm_dims_t& d, int NP, int64_t nrows) {
   const FbwEmisSizes z = fbw_emis_sizes(d.K, d.M, NP, nrows);
@@ -872,6 +876,8 @@ int hmm_forward_backward_workspace_size(hmm_dims_t dims, const hmm_seqs_t* seqs,
   if (seqs->S < 0 || seqs->total_obs < 0) return fail(HMM_ERR_ARG, "negative S or total_obs");
   if (pad_states(dims.N) != 128)
     return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint needs 64 < N <= 128 (N=%d)", dims.N);
+  if (!tf32_adjoint_m_ok(128, dims.M))
+    return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint: M=%d too large", dims.M);
   *bytes = make_layout(dims, *seqs, HMM_OP_FORWARD_BACKWARD, true, 0, true).total;
   return HMM_OK;
 }
@@ -1215,7 +1221,7 @@ static int fb_tf32(const hmm_dims_t& dims, const hmm_seqs_t* seqs, const float* 
   const int NP = pad_states(dims.N);
   if (NP != 128)
     return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint needs 64 < N <= 128 (N=%d: use HMM_FP32)", dims.N);
-  if (!fb_tf32_supported(NP, dims.M))
+  if (!tf32_adjoint_m_ok(NP, dims.M))
     return fail(HMM_ERR_UNSUPPORTED, "TF32 adjoint: M=%d too large", dims.M);
   if (seqs->model_of_seq && dims.K > 65536)
     return fail(HMM_ERR_UNSUPPORTED, "tensor-core adjoint supports K <= 65536 labelled models");

@@ -281,3 +281,40 @@ def test_python_binding_marshals_model_sets_and_scan_sizes(lib):
     with pytest.raises(ValueError):  # non-contiguous tensors are refused
         hmm.Sequences(symbols=torch.zeros(60, dtype=torch.int32)[::2], offsets=seqs.offsets,
                       lengths=seqs.lengths, max_len=10).c()
+
+
+def test_forward_backward_workspace_size_by_precision(lib):
+    """The adjoint's workspace at each precision (host only): the TF32 path
+    keeps every step's rows (X, Bh, V, G of 128 floats: one block of
+    total_obs rows when labelled, K blocks when every sequence is scored
+    against every model); other precisions as hmm_workspace_size. Limits: the
+    TF32 path takes 64 < N <= 128 and M <= 256; above 128 states the bound on
+    M is the cluster forward's emission slice (M <= 173 at 512 padded states;
+    the emission counts no longer hold a state-by-symbol table)."""
+    f = lib.hmm_forward_backward_workspace_size
+    out, ref = ctypes.c_size_t(), ctypes.c_size_t()
+    total = 100 * 300
+    d = hmm.hmm_dims_t(4, 128, 256)
+    lab = _seqs(S=100, max_len=300, total=total, mos=True)
+    every = _seqs(S=100, max_len=300, total=total)
+    assert f(d, ctypes.byref(lab), hmm.HMM_TF32_MMA, ctypes.byref(out)) == 0
+    t_lab = out.value
+    assert t_lab >= 4 * total * 128 * 4 and t_lab % 256 == 0
+    assert f(d, ctypes.byref(every), hmm.HMM_TF32_MMA, ctypes.byref(out)) == 0
+    assert out.value >= 4 * 4 * total * 128 * 4 and out.value > t_lab
+    for prec in (hmm.HMM_BF16_MMA, hmm.HMM_AUTO):
+        assert f(d, ctypes.byref(lab), prec, ctypes.byref(out)) == 0
+        assert lib.hmm_workspace_size(d, ctypes.byref(lab), hmm.HMM_OP_FORWARD_BACKWARD,
+                                      ctypes.byref(ref)) == 0
+        assert out.value == ref.value
+    for dims in (hmm.hmm_dims_t(4, 64, 32), hmm.hmm_dims_t(4, 129, 32),
+                 hmm.hmm_dims_t(4, 128, 257)):
+        assert f(dims, ctypes.byref(lab), hmm.HMM_TF32_MMA, ctypes.byref(out)) \
+            == hmm.HMM_ERR_UNSUPPORTED
+    one = _seqs(S=100, max_len=300, total=total)
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(1, 300, 173), ctypes.byref(one),
+                                  hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) == 0
+    assert out.value >= 4 * total * 512 * 4
+    assert lib.hmm_workspace_size(hmm.hmm_dims_t(1, 300, 174), ctypes.byref(one),
+                                  hmm.HMM_OP_FORWARD_BACKWARD, ctypes.byref(out)) \
+        == hmm.HMM_ERR_UNSUPPORTED

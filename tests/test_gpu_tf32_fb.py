@@ -168,6 +168,9 @@ def test_tf32_adjoint_refusals():
     wide = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 1, 200, 8)]
     with pytest.raises(hmm.HmmError):  # above 128 states: BF16 only
         hmm.hmm_forward_backward(*wide, seqs, precision=hmm.HMM_TF32_MMA)
+    many = [torch.from_numpy(x).cuda() for x in synth.random_model(rng, 1, 100, 257)]
+    with pytest.raises(hmm.HmmError):  # M <= 256, as the tensor-core adjoint
+        hmm.hmm_forward_backward(*many, seqs, precision=hmm.HMM_TF32_MMA)
 
 
 def test_tf32_adjoint_empty_model_single_symbol_zero_weights():

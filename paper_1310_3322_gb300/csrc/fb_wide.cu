@@ -1,6 +1,8 @@
-// fb_wide.cu -- expected counts of the adjoint above 128 states (Baum-Welch
-// E-step, Sec. 2.7; Rabiner 1989 eqs. 37-38), from the per-step rows the
-// tensor-core forward and backward passes of mma_wide.cu leave in memory:
+// fb_wide.cu -- expected counts of the adjoint from every step's rows
+// (Baum-Welch E-step, Sec. 2.7; Rabiner 1989 eqs. 37-38): above 128 states
+// (BF16 passes of mma_cluster.cu, a block of rows per model) and for the TF32
+// adjoint at N_pad = 128 (passes of mma_pass_tf32.cu, rows in the tile plan's
+// order, each model's rows [mrow[k], mrow[K + 1 + k])). The passes leave:
 //   X_t      scaled alpha_t (any power-of-two scale per step),
 //   Bh_t     scaled beta_t = D_t 2^-f_t, D_t = A (b(o_{t+1}) o Bh_{t+1}) the
 //            backward pass's product, f_t its exponent.
@@ -12,7 +14,8 @@
 // sequence: one contraction over all rows, run on the tensor cores with TF32
 // operands (U and V rounded to TF32, relative error <= 2^-11 each; FP32
 // accumulation) as a split-K GEMM whose partial tiles are summed in a fixed
-// order. Emission and initial counts are
+// order (at N_pad = 128 its row chunks are staged by bulk copies). Emission
+// and initial counts are
 // sums of gamma rows by symbol and at t = 0: the rows of each model sorted by
 // symbol (a stable counting sort), whole rows summed per piece of a symbol's
 // rows, then the pieces in a fixed order. Everything is bitwise

@@ -514,8 +514,11 @@ struct MmaFwdLaunch {
 cudaError_t launch_forward_mma(int NP, bool tf32, const MmaFwdLaunch& a, cudaStream_t st);
 int mma_tiles_per_cta(int NP);  // 128-row tiles one CTA of the tensor-core forward holds
 
-// Tensor-core forward for 128 < N <= 512 (mma_wide.cu): one 128-row tile per
-// CTA, A^T streamed from a BF16 image built per call.
+// Launch arguments of the tensor-core recursions above 128 states: the
+// cluster kernels of mma_cluster.cu (tiles of 32, 64 or 128 rows on N_pad / 64
+// CTAs, forward and the adjoint's passes) and the streamed-A^T forward of
+// mma_wide.cu (one 128-row tile per CTA, A^T from a BF16 image built per
+// call), which serves only what the cluster cannot take.
 struct MmaWideLaunch {
   SeqArgs seq;
   ModelArgs mod;      // probability tables padded to NP (256 or 512)
